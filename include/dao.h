@@ -1,0 +1,222 @@
+/*
+ * dao.h - C ABI of libdao.so: column-generation direct aperture optimisation
+ * (DAO) for IMRT on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Men, Jia & Jiang, "GPU-based ultra-fast direct aperture optimization
+ * for online adaptive radiation therapy" (arXiv:1003.5402).
+ *   - model: dose z_j = sum_k D_kj y_k, y >= 0 (Sec. 2.1, Eqs. 1, 2, 6, 7);
+ *   - objective: one-sided quadratic under/over-dose penalties per structure,
+ *     weights divided by the structure's voxel count (Sec. 4, Eqs. 9-10, the
+ *     per-structure form of Eqs. 3-5);
+ *   - column generation: a master problem over the current aperture pool and a
+ *     pricing sub-problem (Sec. 2.2-2.3, Eq. 8) solved row by row over the MLC.
+ *
+ * Conventions for every call below
+ *   - Beamlet i of beam b, MLC row r, column c is i = off_b + r * cols[b] + c,
+ *     off_b = sum_{b' < b} rows[b'] * cols[b'] (beam-major, row, column).
+ *   - An aperture is given per MLC row of its beam as a half-open range
+ *     [L, R) of open beamlets, 0 <= L <= R <= cols[b]; a closed row is (0, 0).
+ *     leaf_lr arrays hold 2 * rows[b] int32: L_0, R_0, L_1, R_1, ...
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the context's device.  Every call is synchronous with
+ *     respect to host outputs: when it returns, host outputs are written.
+ *   - Errors: calls return a dao_status; no exception or abort crosses the
+ *     ABI.  dao_last_error() gives a message for the calling thread's last
+ *     failed call.  A failed call leaves the context usable unless it returns
+ *     DAO_ECUDA (device state is then undefined; destroy the context).
+ *   - A context is not thread-safe; different contexts are independent.
+ */
+#ifndef DAO_H
+#define DAO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dao_status {
+    DAO_OK = 0,
+    DAO_OPTIMAL = 1,      /* pricing found no aperture with a negative reduced cost (Sec. 2.2) */
+    DAO_DUPLICATE = 2,    /* pricing returned an aperture already in the pool */
+    DAO_EINVAL = -1,      /* invalid argument; nothing changed */
+    DAO_ENOMEM = -2,      /* device or host allocation failed; nothing changed */
+    DAO_ECUDA = -3,       /* a CUDA call failed; destroy the context */
+    DAO_ETIMEOUT = -4,    /* a bounded device-side wait gave up */
+    DAO_EBUSY = -5,       /* no free slot / not enough free device memory */
+    DAO_ESTATE = -6       /* call not valid in the current state (e.g. pool full) */
+} dao_status;
+
+/* D_ij of Eq. 2: voxel-major CSR (row j = voxel, column i = beamlet), host
+ * memory, column indices strictly increasing within a row, values finite.
+ * row_ptr has n_voxels + 1 entries, row_ptr[0] = 0, row_ptr[n_voxels] = nnz. */
+typedef struct dao_csr {
+    int32_t n_voxels;
+    int32_t n_beamlets;
+    int64_t nnz;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const float* val;
+} dao_csr;
+
+/* MLC geometry: beam b has rows[b] MLC rows of cols[b] beamlets (host).
+ * sum_b rows[b] * cols[b] must equal n_beamlets; 1 <= cols[b] <= 32. */
+typedef struct dao_geometry {
+    int32_t n_beams;
+    const int32_t* rows;
+    const int32_t* cols;
+} dao_geometry;
+
+/* Structures of Sec. 4: voxel_struct[j] in [0, n_structures) labels each voxel
+ * with one structure (overlaps resolved by the caller); is_target[s] != 0
+ * marks the targets T (under-dose term of Eq. 9 applies), all structures get
+ * the over-dose term of Eq. 10.  n_structures <= 64.  Host memory. */
+typedef struct dao_structures {
+    int32_t n_structures;
+    const int32_t* voxel_struct;
+    const uint8_t* is_target;
+} dao_structures;
+
+/* Penalty weights of Eqs. 9-10 per structure (host): under_w = alpha_s,
+ * over_w = beta_s, over_thresh = T_s^+.  When normalize_by_volume != 0 the
+ * weights are divided by |v_s| (Eqs. 9-10); otherwise they are the per-voxel
+ * alpha_j, beta_j of Eqs. 3-4.  Weights must be >= 0 and finite. */
+typedef struct dao_weights {
+    const double* under_w;
+    const double* over_w;
+    const double* over_thresh;
+    int32_t normalize_by_volume;
+} dao_weights;
+
+enum { DAO_PREC_FP32 = 0, DAO_PREC_FP16 = 1, DAO_PREC_BF16 = 2 };
+
+/* Solver options; dao_options_default() fills every field. */
+typedef struct dao_options {
+    int32_t k_max;             /* aperture pool capacity, 1..64 (default 64) */
+    int32_t max_master_iters;  /* projected-Newton iterations per master solve (default 100) */
+    double master_tol;         /* stop at ||y - P(y - g)||_inf <= master_tol * max|g(start)| (1e-6) */
+    double price_tol;          /* optimal when reduced cost >= -price_tol * max(D) * ||grad F(0)||_1 (1e-7) */
+    int32_t precision;         /* DAO_PREC_FP32 (others reserved) */
+    int32_t device;            /* CUDA device ordinal (default 0) */
+    void* stream;              /* cudaStream_t to run on; NULL = a stream owned by the context */
+} dao_options;
+
+typedef struct dao_ctx dao_ctx;
+
+void dao_options_default(dao_options* opt);
+
+/* Create a plan context: validates the inputs (DAO_EINVAL on a malformed CSR,
+ * geometry, labels or weights), copies D to the device in its own layout,
+ * builds the transpose D^T (beamlet-major) used by pricing, and expands the
+ * per-structure criteria.  prescriptions[s] is T_s^- for target s (ignored
+ * for non-targets).  The caller keeps ownership of every input; *out is owned
+ * by the caller and released with dao_destroy.  The pool starts empty
+ * (y = [], z = 0). */
+dao_status dao_create(const dao_csr* D, const dao_geometry* g, const dao_structures* s,
+                      const dao_weights* w, const double* prescriptions,
+                      const dao_options* opt, dao_ctx** out);
+
+void dao_destroy(dao_ctx* ctx);
+
+/* Empty the aperture pool (y = [], z = 0) keeping D on the device. */
+dao_status dao_reset(dao_ctx* ctx);
+
+/* Pricing sub-problem (Eq. 8, Sec. 2.3) at the current master optimum:
+ * pi = grad F(z), w = D^T pi, per-MLC-row minimum-sum consecutive interval,
+ * per-beam sum, beam with the smallest sum (lowest index on ties).  Outputs
+ * (host): *beam, leaf_lr[2 * rows[*beam]] (caller allocates 2 * max rows),
+ * *reduced_cost (FP64 sum of the rows' best values).  Returns DAO_OPTIMAL
+ * when the reduced cost is not below -tau, DAO_OK otherwise; the pool is not
+ * changed. */
+dao_status dao_price(dao_ctx* ctx, int32_t* beam, int32_t* leaf_lr, double* reduced_cost);
+
+/* Add aperture (beam, leaf_lr host) to the pool: its dose column D_kj (Eq. 2)
+ * is formed on the device and the master problem is re-solved warm-started
+ * (previous intensities, 0 for the new one).  *objective (host, optional)
+ * receives F at the new master solution.  DAO_ESTATE when the pool is full,
+ * DAO_EINVAL for an invalid aperture. */
+dao_status dao_add_aperture(dao_ctx* ctx, int32_t beam, const int32_t* leaf_lr, double* objective);
+
+/* Column generation (Sec. 2.2-2.3, Fig. 1): up to n_apertures rounds of
+ * pricing + add + master.  *n_done (host) receives the pool size reached;
+ * objective_trace (host, optional, n_apertures entries) receives F after each
+ * added aperture.  Returns DAO_OPTIMAL / DAO_DUPLICATE if pricing stopped
+ * early, DAO_OK otherwise. */
+dao_status dao_solve(dao_ctx* ctx, int32_t n_apertures, int32_t* n_done, double* objective_trace);
+
+/* Final dose z = D x with x_i = sum_{k in K_i} y_k (Eqs. 1, 7) computed by the
+ * full dose SpMV; dose (host, n_voxels floats, optional), *objective (host,
+ * optional) = F(z) of Eq. 5. */
+dao_status dao_dose(dao_ctx* ctx, float* dose, double* objective);
+
+/* Current pool: y (host, FP64, capacity k_max), beams (host int32 [K]),
+ * leaf_lr (host int32 [K][2 * max rows], row-padded with (0, 0)), *k = K. */
+dao_status dao_intensities(dao_ctx* ctx, double* y, int32_t* k);
+dao_status dao_apertures(dao_ctx* ctx, int32_t* beams, int32_t* leaf_lr, int32_t* k);
+
+/* Problem sizes: voxels, beamlets, beams, total MLC rows, the widest row
+ * count of any beam, stored nnz of D (after row padding), and the pool
+ * capacity. */
+dao_status dao_sizes(const dao_ctx* ctx, int32_t* n_voxels, int32_t* n_beamlets, int32_t* n_beams,
+                     int32_t* n_mlc_rows, int32_t* max_rows, int64_t* nnz_stored, int32_t* k_max);
+
+/* ---- kernel-level entry points (device vectors, for parity tests and the
+ * bandwidth benchmark).  All run on the context's stream and read the
+ * context's device copy of D / D^T. ---- */
+
+/* Step a1: z = D x (device float[n_beamlets] -> float[n_voxels]) with the
+ * objective epilogue: grad (device, optional) = grad F(z) (Sec. 2.3's pi) and
+ * *objective (host, optional) = F(z) in FP64 (Eqs. 5, 9, 10). */
+dao_status dao_k_dose(dao_ctx* ctx, const float* x, float* z, float* grad, double* objective);
+
+/* Step a2: w = D^T pi (device float[n_voxels] -> float[n_beamlets]), the
+ * bracketed sum of Eq. 8, from the stored transpose (no atomics). */
+dao_status dao_k_beamlet_prices(dao_ctx* ctx, const float* pi, float* w);
+
+/* Step a3: pricing on a given w (device float[n_beamlets]); outputs as
+ * dao_price plus, when non-NULL, row_best (host double[n_mlc_rows]: each
+ * row's best interval sum v*) and row_lr (host int32[2 * n_mlc_rows]). */
+dao_status dao_k_price(dao_ctx* ctx, const float* w, int32_t* beam, int32_t* leaf_lr,
+                       double* reduced_cost, double* row_best, int32_t* row_lr);
+
+/* Step a4: column D_kj = sum_{i in A_k} D_ij (Eq. 2) of aperture
+ * (beam, leaf_lr host) into out (device float[n_voxels]). */
+dao_status dao_k_aperture_column(dao_ctx* ctx, int32_t beam, const int32_t* leaf_lr, float* out);
+
+/* Current pi = grad F(z) and z of the last master solution (device outputs). */
+dao_status dao_k_state(dao_ctx* ctx, float* z, float* pi);
+
+/* ---- instrumentation: per-kernel-class CUDA-event timing on the context's
+ * stream (off by default). ---- */
+enum {
+    DAO_KC_DOSE = 0,           /* a1 dose SpMV + epilogue */
+    DAO_KC_DT = 1,             /* a2 transposed SpMV */
+    DAO_KC_PRICE = 2,          /* a3 pricing (row scan + beam reduction) */
+    DAO_KC_COLUMN = 3,         /* a4 aperture column */
+    DAO_KC_MASTER_PASS = 4,    /* a5 fused slab pass (z, F, g, H partials) */
+    DAO_KC_MASTER_REDUCE = 5,  /* a5 partial reduction */
+    DAO_KC_MASTER_STEP = 6,    /* a5 Newton step / line search control */
+    DAO_KC_OTHER = 7,
+    DAO_KC_COUNT = 8
+};
+dao_status dao_profile_enable(dao_ctx* ctx, int32_t enable);
+/* launches, summed device milliseconds and the kernel launches counted for
+ * class kc since the last dao_profile_enable(ctx, 1); synchronises. */
+dao_status dao_profile_read(dao_ctx* ctx, int32_t kc, int64_t* launches, double* total_ms);
+/* Every kernel launched by this context since creation (all classes). */
+int64_t dao_launch_count(const dao_ctx* ctx);
+
+/* Per master solve since the last reset, in pool order (host arrays of k_max
+ * entries, each optional): evals = fused slab passes evaluated, status = 1
+ * converged / 2 iteration cap / 3 line search stalled, kkt = final
+ * ||y - P(y - g)||_inf divided by max|g| at the warm start; *k = solves. */
+dao_status dao_master_stats(const dao_ctx* ctx, int32_t* evals, int32_t* status, double* kkt, int32_t* k);
+
+const char* dao_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DAO_H */

@@ -1,0 +1,302 @@
+"""ctypes binding of libdao.so (include/dao.h): argument marshalling only.
+
+Every step of column-generation DAO runs in the library's CUDA kernels; this
+module converts numpy arrays and torch CUDA tensors to the C structs and
+pointers of the ABI and turns status codes into exceptions.  The library must
+be built (``paper_1003_5402_gb300.build.build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdao.so")
+
+DAO_OK, DAO_OPTIMAL, DAO_DUPLICATE = 0, 1, 2
+DAO_EINVAL, DAO_ENOMEM, DAO_ECUDA, DAO_ETIMEOUT, DAO_EBUSY, DAO_ESTATE = -1, -2, -3, -4, -5, -6
+DAO_PREC_FP32, DAO_PREC_FP16, DAO_PREC_BF16 = 0, 1, 2
+KC = {"dose": 0, "dt": 1, "price": 2, "column": 3, "master_pass": 4, "master_reduce": 5, "master_step": 6,
+      "other": 7}
+
+# every function declared in include/dao.h, with (restype, argtypes)
+_P = C.c_void_p
+_I32P = C.POINTER(C.c_int32)
+_F64P = C.POINTER(C.c_double)
+
+
+class dao_csr(C.Structure):
+    _fields_ = [("n_voxels", C.c_int32), ("n_beamlets", C.c_int32), ("nnz", C.c_int64),
+                ("row_ptr", C.POINTER(C.c_int64)), ("col", _I32P), ("val", C.POINTER(C.c_float))]
+
+
+class dao_geometry(C.Structure):
+    _fields_ = [("n_beams", C.c_int32), ("rows", _I32P), ("cols", _I32P)]
+
+
+class dao_structures(C.Structure):
+    _fields_ = [("n_structures", C.c_int32), ("voxel_struct", _I32P), ("is_target", C.POINTER(C.c_uint8))]
+
+
+class dao_weights(C.Structure):
+    _fields_ = [("under_w", _F64P), ("over_w", _F64P), ("over_thresh", _F64P), ("normalize_by_volume", C.c_int32)]
+
+
+class dao_options(C.Structure):
+    _fields_ = [("k_max", C.c_int32), ("max_master_iters", C.c_int32), ("master_tol", C.c_double),
+                ("price_tol", C.c_double), ("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p)]
+
+
+SIGNATURES = {
+    "dao_options_default": (None, [C.POINTER(dao_options)]),
+    "dao_create": (C.c_int, [C.POINTER(dao_csr), C.POINTER(dao_geometry), C.POINTER(dao_structures),
+                             C.POINTER(dao_weights), _F64P, C.POINTER(dao_options), C.POINTER(_P)]),
+    "dao_destroy": (None, [_P]),
+    "dao_reset": (C.c_int, [_P]),
+    "dao_price": (C.c_int, [_P, _I32P, _I32P, _F64P]),
+    "dao_add_aperture": (C.c_int, [_P, C.c_int32, _I32P, _F64P]),
+    "dao_solve": (C.c_int, [_P, C.c_int32, _I32P, _F64P]),
+    "dao_dose": (C.c_int, [_P, C.POINTER(C.c_float), _F64P]),
+    "dao_intensities": (C.c_int, [_P, _F64P, _I32P]),
+    "dao_apertures": (C.c_int, [_P, _I32P, _I32P, _I32P]),
+    "dao_sizes": (C.c_int, [_P, _I32P, _I32P, _I32P, _I32P, _I32P, C.POINTER(C.c_int64), _I32P]),
+    "dao_k_dose": (C.c_int, [_P, _P, _P, _P, _F64P]),
+    "dao_k_beamlet_prices": (C.c_int, [_P, _P, _P]),
+    "dao_k_price": (C.c_int, [_P, _P, _I32P, _I32P, _F64P, _F64P, _I32P]),
+    "dao_k_aperture_column": (C.c_int, [_P, C.c_int32, _I32P, _P]),
+    "dao_k_state": (C.c_int, [_P, _P, _P]),
+    "dao_profile_enable": (C.c_int, [_P, C.c_int32]),
+    "dao_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), _F64P]),
+    "dao_launch_count": (C.c_int64, [_P]),
+    "dao_master_stats": (C.c_int, [_P, _I32P, _I32P, _F64P, _I32P]),
+    "dao_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load():
+    """Load libdao.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1003_5402_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class DaoError(RuntimeError):
+    def __init__(self, status: int, fn: str, msg: str):
+        super().__init__(f"{fn} failed with status {status}: {msg}")
+        self.status = status
+
+
+def _check(st: int, fn: str, ok=(DAO_OK,)):
+    if st in ok:
+        return st
+    raise DaoError(st, fn, load().dao_last_error().decode(errors="replace"))
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _dev(t, dtype_name: str):
+    """Device pointer of a contiguous torch CUDA tensor."""
+    if not getattr(t, "is_cuda", False):
+        raise TypeError("expected a CUDA tensor")
+    if str(t.dtype) != "torch." + dtype_name or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype_name} tensor, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def options(**kw) -> dao_options:
+    o = dao_options()
+    load().dao_options_default(C.byref(o))
+    for k, v in kw.items():
+        if k == "stream":
+            v = C.c_void_p(v)
+        setattr(o, k, v)
+    return o
+
+
+class Plan:
+    """One DAO plan context (dao_create ... dao_destroy).
+
+    ``case`` is any object with the fields of ``phantom.Case`` (voxel-major CSR
+    ``indptr/indices/data``, ``rows/cols``, ``voxel_struct``, ``is_target``,
+    ``under_w/under_t/over_w/over_t``).  Keyword options map to dao_options;
+    ``stream`` is a raw cudaStream_t (e.g. ``torch.cuda.current_stream().cuda_stream``).
+    """
+
+    def __init__(self, case, normalize_by_volume: bool = True, **opt):
+        lib = load()
+        self._keep = []
+        indptr = np.ascontiguousarray(case.indptr, dtype=np.int64)
+        indices = np.ascontiguousarray(case.indices, dtype=np.int32)
+        data = np.ascontiguousarray(case.data, dtype=np.float32)
+        rows = np.ascontiguousarray(case.rows, dtype=np.int32)
+        cols = np.ascontiguousarray(case.cols, dtype=np.int32)
+        vs = np.ascontiguousarray(case.voxel_struct, dtype=np.int32)
+        tgt = np.ascontiguousarray(case.is_target, dtype=np.uint8)
+        uw = np.ascontiguousarray(case.under_w, dtype=np.float64)
+        ow = np.ascontiguousarray(case.over_w, dtype=np.float64)
+        ot = np.ascontiguousarray(case.over_t, dtype=np.float64)
+        rx = np.ascontiguousarray(case.under_t, dtype=np.float64)
+        self._keep += [indptr, indices, data, rows, cols, vs, tgt, uw, ow, ot, rx]
+        D = dao_csr(len(indptr) - 1, int(np.sum(rows.astype(np.int64) * cols)), int(indptr[-1]),
+                    _ptr(indptr, C.c_int64), _ptr(indices, C.c_int32), _ptr(data, C.c_float))
+        g = dao_geometry(len(rows), _ptr(rows, C.c_int32), _ptr(cols, C.c_int32))
+        s = dao_structures(len(uw), _ptr(vs, C.c_int32), _ptr(tgt, C.c_uint8))
+        w = dao_weights(_ptr(uw, C.c_double), _ptr(ow, C.c_double), _ptr(ot, C.c_double), int(normalize_by_volume))
+        o = options(**opt)
+        h = C.c_void_p()
+        _check(lib.dao_create(C.byref(D), C.byref(g), C.byref(s), C.byref(w), _ptr(rx, C.c_double), C.byref(o),
+                              C.byref(h)), "dao_create")
+        self.h = h
+        self._keep = []
+        self.rows = rows.copy()
+        self.cols = cols.copy()
+        sz = self.sizes()
+        self.n_voxels, self.n_beamlets, self.n_beams, self.n_mlc_rows, self.max_rows, self.nnz_stored, self.k_max = sz
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().dao_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- ABI calls
+    def sizes(self) -> Tuple[int, ...]:
+        v = [C.c_int32() for _ in range(5)]
+        nnz = C.c_int64()
+        k = C.c_int32()
+        _check(load().dao_sizes(self.h, *[C.byref(x) for x in v], C.byref(nnz), C.byref(k)), "dao_sizes")
+        return tuple(x.value for x in v) + (nnz.value, k.value)
+
+    def reset(self):
+        _check(load().dao_reset(self.h), "dao_reset")
+
+    def price(self):
+        """(status, beam, leaves [rows, 2], reduced cost)."""
+        beam = C.c_int32()
+        lr = np.zeros(2 * self.max_rows, dtype=np.int32)
+        rc = C.c_double()
+        st = _check(load().dao_price(self.h, C.byref(beam), _ptr(lr, C.c_int32), C.byref(rc)), "dao_price",
+                    (DAO_OK, DAO_OPTIMAL))
+        b = beam.value
+        return st, b, lr[: 2 * self.rows[b]].reshape(-1, 2).copy(), rc.value
+
+    def add_aperture(self, beam: int, leaves) -> float:
+        lr = np.ascontiguousarray(np.asarray(leaves, dtype=np.int32).reshape(-1))
+        F = C.c_double()
+        _check(load().dao_add_aperture(self.h, int(beam), _ptr(lr, C.c_int32), C.byref(F)), "dao_add_aperture")
+        return F.value
+
+    def solve(self, n_apertures: int):
+        """(status, apertures added, objective trace)."""
+        n = C.c_int32()
+        trace = np.full(max(n_apertures, 1), np.nan)
+        st = _check(load().dao_solve(self.h, int(n_apertures), C.byref(n), _ptr(trace, C.c_double)), "dao_solve",
+                    (DAO_OK, DAO_OPTIMAL, DAO_DUPLICATE))
+        return st, n.value, trace[:n_apertures]
+
+    def dose(self):
+        z = np.zeros(self.n_voxels, dtype=np.float32)
+        F = C.c_double()
+        _check(load().dao_dose(self.h, _ptr(z, C.c_float), C.byref(F)), "dao_dose")
+        return z, F.value
+
+    def intensities(self) -> np.ndarray:
+        y = np.zeros(self.k_max)
+        k = C.c_int32()
+        _check(load().dao_intensities(self.h, _ptr(y, C.c_double), C.byref(k)), "dao_intensities")
+        return y[: k.value].copy()
+
+    def apertures(self):
+        beams = np.zeros(self.k_max, dtype=np.int32)
+        lr = np.zeros((self.k_max, 2 * self.max_rows), dtype=np.int32)
+        k = C.c_int32()
+        _check(load().dao_apertures(self.h, _ptr(beams, C.c_int32), _ptr(lr, C.c_int32), C.byref(k)),
+               "dao_apertures")
+        out = []
+        for i in range(k.value):
+            b = int(beams[i])
+            out.append((b, lr[i, : 2 * self.rows[b]].reshape(-1, 2).copy()))
+        return out
+
+    # -- kernel-level calls on torch CUDA tensors
+    def k_dose(self, x, z, grad=None, objective: bool = True):
+        F = C.c_double()
+        _check(load().dao_k_dose(self.h, _dev(x, "float32"), _dev(z, "float32"),
+                                 _dev(grad, "float32") if grad is not None else None,
+                                 C.byref(F) if objective else None), "dao_k_dose")
+        return F.value if objective else None
+
+    def k_beamlet_prices(self, pi, w):
+        _check(load().dao_k_beamlet_prices(self.h, _dev(pi, "float32"), _dev(w, "float32")), "dao_k_beamlet_prices")
+
+    def k_price(self, w):
+        """(status, beam, leaves, reduced cost, row best values, row [L, R))."""
+        beam = C.c_int32()
+        lr = np.zeros(2 * self.max_rows, dtype=np.int32)
+        rc = C.c_double()
+        rv = np.zeros(self.n_mlc_rows)
+        rl = np.zeros(2 * self.n_mlc_rows, dtype=np.int32)
+        st = _check(load().dao_k_price(self.h, _dev(w, "float32"), C.byref(beam), _ptr(lr, C.c_int32), C.byref(rc),
+                                       _ptr(rv, C.c_double), _ptr(rl, C.c_int32)), "dao_k_price",
+                    (DAO_OK, DAO_OPTIMAL))
+        b = beam.value
+        return st, b, lr[: 2 * self.rows[b]].reshape(-1, 2).copy(), rc.value, rv, rl.reshape(-1, 2)
+
+    def k_aperture_column(self, beam: int, leaves, out):
+        lr = np.ascontiguousarray(np.asarray(leaves, dtype=np.int32).reshape(-1))
+        _check(load().dao_k_aperture_column(self.h, int(beam), _ptr(lr, C.c_int32), _dev(out, "float32")),
+               "dao_k_aperture_column")
+
+    def k_state(self, z, pi):
+        _check(load().dao_k_state(self.h, _dev(z, "float32"), _dev(pi, "float32")), "dao_k_state")
+
+    def profile_enable(self, on: bool = True):
+        _check(load().dao_profile_enable(self.h, int(on)), "dao_profile_enable")
+
+    def profile_read(self, kc: str):
+        n = C.c_int64()
+        ms = C.c_double()
+        _check(load().dao_profile_read(self.h, KC[kc], C.byref(n), C.byref(ms)), "dao_profile_read")
+        return n.value, ms.value
+
+    def launch_count(self) -> int:
+        return int(load().dao_launch_count(self.h))
+
+    def master_stats(self):
+        """(evaluations, status, relative KKT residual) per master solve since the last reset."""
+        ev = np.zeros(self.k_max, dtype=np.int32)
+        stt = np.zeros(self.k_max, dtype=np.int32)
+        kkt = np.zeros(self.k_max)
+        k = C.c_int32()
+        _check(load().dao_master_stats(self.h, _ptr(ev, C.c_int32), _ptr(stt, C.c_int32), _ptr(kkt, C.c_double),
+                                       C.byref(k)), "dao_master_stats")
+        n = k.value
+        return ev[:n].copy(), stt[:n].copy(), kkt[:n].copy()

@@ -1,0 +1,833 @@
+// Host side of libdao.so: input validation, the device data layout, the
+// column-generation driver (Sec. 2.2-2.3 of arXiv:1003.5402, Fig. 1) and the
+// C ABI declared in include/dao.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstddef>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dao_internal.h"
+
+using namespace dao;
+
+namespace {
+
+thread_local std::string g_err;
+
+dao_status fail(dao_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define DAO_CU(call)                                                                                    \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) return fail(DAO_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define DAO_TRY(expr)                    \
+    do {                                 \
+        dao_status s_ = (expr);          \
+        if (s_ != DAO_OK) return s_;     \
+    } while (0)
+
+inline int64_t round4(int64_t n) { return (n + 3) / 4 * 4; }
+
+}  // namespace
+
+struct ProfRecord {
+    int kc;
+    cudaEvent_t start, stop;
+    int launches;
+};
+
+struct dao_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    dao_options opt{};
+
+    int V = 0, N = 0, B = 0, R_tot = 0, max_rows = 0, S = 0;
+    int64_t nnz = 0;
+    std::vector<int> rows, cols, beam_off, beam_row0;
+    double tau = 0.0;  // absolute pricing tolerance
+
+    DevCSR D, Dt;
+    int* seg = nullptr;              // (B + 1) x V: start of beam b's entries in row j; [B] = end of real entries
+    uint8_t* vstruct = nullptr;
+    StructTermsF* tf = nullptr;
+    StructTermsD* td = nullptr;
+    int4* row_info = nullptr;        // per MLC row: beam, first beamlet, columns, row within beam
+    int* beam_row0_d = nullptr;
+    int4* binfo = nullptr;           // per beamlet: beam, row, column
+
+    // column-generation state
+    int K = 0, K_cap = 0, ld = 0;
+    float* slab = nullptr;           // K_cap x ld, column k = dose of aperture k (Eq. 2)
+    std::vector<int> ap_beam_h, ap_lr_h;
+    int* ap_beam = nullptr;
+    int* ap_lr = nullptr;            // K_cap x 2*max_rows
+    float* z = nullptr;
+    float* pi = nullptr;
+    float* w = nullptr;
+    float* x = nullptr;
+    float* dose = nullptr;
+    float* mask = nullptr;
+    double* row_v = nullptr;
+    int2* row_lr = nullptr;
+    PriceDev* price = nullptr;
+    MasterBuffers mb;
+    double* F_part = nullptr;
+    int F_blocks = 0;
+    double* F_dev = nullptr;
+
+    // pinned staging
+    unsigned char* pinned = nullptr;
+    size_t off_small = 0, off_rows = 0, off_mask = 0, off_master = 0, pinned_bytes = 0;
+
+    // per master solve: evaluations (fused passes), final status, KKT residual / max|g(start)|
+    std::vector<int> stat_evals, stat_status;
+    std::vector<double> stat_kkt;
+
+    std::vector<void*> dev_allocs;
+    int launches_i = 0;
+    int64_t launches_total = 0;
+
+    // instrumentation
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<ProfRecord> recs;
+    int open_kc = -1;
+    cudaEvent_t open_start = nullptr;
+    int open_launch0 = 0;
+
+    template <class T>
+    dao_status dalloc(T** p, size_t n) {
+        void* q = nullptr;
+        const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DAO_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                        cudaGetErrorString(e));
+        }
+        dev_allocs.push_back(q);
+        *p = static_cast<T*>(q);
+        return DAO_OK;
+    }
+
+    cudaEvent_t event() {
+        if (ev_used == ev_pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            ev_pool.push_back(e);
+        }
+        return ev_pool[ev_used++];
+    }
+    void prof_begin(int kc) {
+        if (!prof_on) return;
+        open_kc = kc;
+        open_start = event();
+        open_launch0 = launches_i;
+        if (open_start) cudaEventRecord(open_start, stream);
+    }
+    void prof_end() {
+        if (!prof_on || open_kc < 0) return;
+        cudaEvent_t stop = event();
+        if (open_start && stop) {
+            cudaEventRecord(stop, stream);
+            recs.push_back({open_kc, open_start, stop, launches_i - open_launch0});
+        }
+        open_kc = -1;
+    }
+    void count_launches() {
+        launches_total += launches_i;
+        launches_i = 0;
+    }
+};
+
+namespace {
+
+dao_status check_ctx(dao_ctx* c) {
+    if (c == nullptr) return fail(DAO_EINVAL, "null context");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return fail(DAO_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    return DAO_OK;
+}
+
+dao_status sync(dao_ctx* c) {
+    DAO_CU(cudaStreamSynchronize(c->stream));
+    return DAO_OK;
+}
+
+// ---- validation ---------------------------------------------------------------
+
+dao_status validate(const dao_csr* D, const dao_geometry* g, const dao_structures* s, const dao_weights* w,
+                    const double* rx, const dao_options* opt) {
+    if (!D || !g || !s || !w || !rx || !opt) return fail(DAO_EINVAL, "null argument");
+    if (D->n_voxels < 1 || D->n_beamlets < 1) return fail(DAO_EINVAL, "need at least one voxel and one beamlet");
+    if (!D->row_ptr || !D->col || !D->val) return fail(DAO_EINVAL, "null CSR array");
+    if (D->row_ptr[0] != 0 || D->row_ptr[D->n_voxels] != D->nnz || D->nnz < 0)
+        return fail(DAO_EINVAL, "row_ptr[0] must be 0 and row_ptr[n_voxels] must equal nnz");
+    for (int j = 0; j < D->n_voxels; ++j) {
+        const int64_t p0 = D->row_ptr[j], p1 = D->row_ptr[j + 1];
+        if (p1 < p0) return fail(DAO_EINVAL, "row_ptr decreases at row " + std::to_string(j));
+        for (int64_t p = p0; p < p1; ++p) {
+            const int32_t c = D->col[p];
+            if (c < 0 || c >= D->n_beamlets)
+                return fail(DAO_EINVAL, "column index out of range at entry " + std::to_string(p));
+            if (p > p0 && c <= D->col[p - 1])
+                return fail(DAO_EINVAL, "columns not strictly increasing in row " + std::to_string(j));
+            if (!std::isfinite(D->val[p])) return fail(DAO_EINVAL, "non-finite value at entry " + std::to_string(p));
+        }
+    }
+    if (g->n_beams < 1 || !g->rows || !g->cols) return fail(DAO_EINVAL, "geometry needs at least one beam");
+    int64_t total = 0;
+    for (int b = 0; b < g->n_beams; ++b) {
+        if (g->rows[b] < 1) return fail(DAO_EINVAL, "beam with no MLC rows");
+        if (g->cols[b] < 1 || g->cols[b] > CMAX)
+            return fail(DAO_EINVAL, "beamlets per MLC row must be in [1, 32]");
+        total += (int64_t)g->rows[b] * g->cols[b];
+    }
+    if (total != D->n_beamlets) return fail(DAO_EINVAL, "sum of rows*cols differs from n_beamlets");
+    if (s->n_structures < 1 || s->n_structures > SMAX || !s->voxel_struct || !s->is_target)
+        return fail(DAO_EINVAL, "n_structures must be in [1, 64]");
+    for (int j = 0; j < D->n_voxels; ++j)
+        if (s->voxel_struct[j] < 0 || s->voxel_struct[j] >= s->n_structures)
+            return fail(DAO_EINVAL, "voxel structure label out of range at voxel " + std::to_string(j));
+    if (!w->under_w || !w->over_w || !w->over_thresh) return fail(DAO_EINVAL, "null weight array");
+    for (int k = 0; k < s->n_structures; ++k) {
+        if (!(w->under_w[k] >= 0) || !std::isfinite(w->under_w[k]) || !(w->over_w[k] >= 0) ||
+            !std::isfinite(w->over_w[k]) || !std::isfinite(w->over_thresh[k]))
+            return fail(DAO_EINVAL, "weights must be finite and >= 0, thresholds finite");
+        if (s->is_target[k] && !std::isfinite(rx[k])) return fail(DAO_EINVAL, "non-finite prescription");
+    }
+    if (opt->k_max < 1 || opt->k_max > KMAX) return fail(DAO_EINVAL, "k_max must be in [1, 64]");
+    if (opt->max_master_iters < 1) return fail(DAO_EINVAL, "max_master_iters must be >= 1");
+    if (!(opt->master_tol > 0) || !(opt->price_tol >= 0)) return fail(DAO_EINVAL, "tolerances must be positive");
+    if (opt->precision != DAO_PREC_FP32) return fail(DAO_EINVAL, "only DAO_PREC_FP32 is implemented");
+    return DAO_OK;
+}
+
+// ---- device data layout -------------------------------------------------------
+
+struct HostCSR {
+    std::vector<int> rowptr, col;
+    std::vector<float> val;
+};
+
+// Rows padded to a multiple of four entries (value 0, column = the row's last).
+void pad_rows(int n_rows, const std::vector<int64_t>& rp, const int32_t* col, const float* val, HostCSR& out) {
+    out.rowptr.assign(n_rows + 1, 0);
+    int64_t acc = 0;
+    for (int r = 0; r < n_rows; ++r) {
+        out.rowptr[r] = (int)acc;
+        acc += round4(rp[r + 1] - rp[r]);
+    }
+    out.rowptr[n_rows] = (int)acc;
+    out.col.assign(acc, 0);
+    out.val.assign(acc, 0.f);
+    for (int r = 0; r < n_rows; ++r) {
+        int64_t q = out.rowptr[r];
+        const int64_t p0 = rp[r], p1 = rp[r + 1];
+        for (int64_t p = p0; p < p1; ++p, ++q) {
+            out.col[q] = col[p];
+            out.val[q] = val[p];
+        }
+        const int last = p1 > p0 ? col[p1 - 1] : 0;
+        for (; q < out.rowptr[r + 1]; ++q) out.col[q] = last;
+    }
+}
+
+template <class T>
+dao_status upload(dao_ctx* c, T** dst, const T* src, size_t n) {
+    DAO_TRY(c->dalloc(dst, n));
+    if (n) DAO_CU(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    return DAO_OK;
+}
+
+dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const dao_structures* s,
+                 const dao_weights* w, const double* rx) {
+    const int V = c->V, N = c->N, B = c->B;
+    // beam geometry
+    c->rows.assign(g->rows, g->rows + B);
+    c->cols.assign(g->cols, g->cols + B);
+    c->beam_off.assign(B + 1, 0);
+    c->beam_row0.assign(B + 1, 0);
+    for (int b = 0; b < B; ++b) {
+        c->beam_off[b + 1] = c->beam_off[b] + c->rows[b] * c->cols[b];
+        c->beam_row0[b + 1] = c->beam_row0[b] + c->rows[b];
+        c->max_rows = std::max(c->max_rows, c->rows[b]);
+    }
+    c->R_tot = c->beam_row0[B];
+    std::vector<int4> ri(c->R_tot), bi(N);
+    for (int b = 0; b < B; ++b)
+        for (int r = 0; r < c->rows[b]; ++r) {
+            ri[c->beam_row0[b] + r] = make_int4(b, c->beam_off[b] + r * c->cols[b], c->cols[b], r);
+            for (int q = 0; q < c->cols[b]; ++q) bi[c->beam_off[b] + r * c->cols[b] + q] = make_int4(b, r, q, 0);
+        }
+
+    // D (voxel-major) with per-row beam segments
+    std::vector<int64_t> rp(Din->row_ptr, Din->row_ptr + V + 1);
+    int64_t padded = 0;
+    for (int j = 0; j < V; ++j) padded += round4(rp[j + 1] - rp[j]);
+    if (padded >= (int64_t)1 << 31) return fail(DAO_EINVAL, "D too large for 32-bit row offsets");
+    HostCSR Dh;
+    pad_rows(V, rp, Din->col, Din->val, Dh);
+    std::vector<int> seg((size_t)(B + 1) * V);
+    for (int j = 0; j < V; ++j) {
+        const int p_end = Dh.rowptr[j] + (int)(rp[j + 1] - rp[j]);
+        // segment starts: first entry with column >= beam_off[b]
+        int q = Dh.rowptr[j];
+        for (int b = 0; b < B; ++b) {
+            while (q < p_end && Dh.col[q] < c->beam_off[b]) ++q;
+            seg[(size_t)b * V + j] = q;
+        }
+        seg[(size_t)B * V + j] = p_end;
+    }
+    // D^T (beamlet-major) by a counting sort over columns; voxels stay in increasing order
+    std::vector<int64_t> cnt(N + 1, 0);
+    for (int64_t p = 0; p < Din->nnz; ++p) ++cnt[Din->col[p] + 1];
+    std::vector<int64_t> trp(N + 1, 0);
+    for (int i = 0; i < N; ++i) trp[i + 1] = trp[i] + cnt[i + 1];
+    std::vector<int32_t> tcol(Din->nnz);
+    std::vector<float> tval(Din->nnz);
+    {
+        std::vector<int64_t> fill(trp.begin(), trp.end() - 1);
+        for (int j = 0; j < V; ++j)
+            for (int64_t p = rp[j]; p < rp[j + 1]; ++p) {
+                const int i = Din->col[p];
+                tcol[fill[i]] = j;
+                tval[fill[i]] = Din->val[p];
+                ++fill[i];
+            }
+    }
+    int64_t tpadded = 0;
+    for (int i = 0; i < N; ++i) tpadded += round4(trp[i + 1] - trp[i]);
+    if (tpadded >= (int64_t)1 << 31) return fail(DAO_EINVAL, "D^T too large for 32-bit row offsets");
+    HostCSR Th;
+    pad_rows(N, trp, tcol.data(), tval.data(), Th);
+
+    // objective terms per structure (Eqs. 9-10)
+    const int S = s->n_structures;
+    c->S = S;
+    std::vector<int64_t> count(S, 0);
+    for (int j = 0; j < V; ++j) ++count[s->voxel_struct[j]];
+    std::vector<StructTermsD> tdh(S);
+    std::vector<StructTermsF> tfh(S);
+    double pi0_l1 = 0.0;
+    for (int k = 0; k < S; ++k) {
+        const double vol = (w->normalize_by_volume && count[k] > 0) ? (double)count[k] : 1.0;
+        const bool tgt = s->is_target[k] != 0;
+        tdh[k].a = tgt ? w->under_w[k] / vol : 0.0;
+        tdh[k].tu = tgt ? rx[k] : 0.0;
+        tdh[k].b = w->over_w[k] / vol;
+        tdh[k].to = w->over_thresh[k];
+        tfh[k] = {(float)tdh[k].a, (float)tdh[k].tu, (float)tdh[k].b, (float)tdh[k].to};
+        // |grad F(0)| summed over the structure's voxels
+        pi0_l1 += (double)count[k] * (2.0 * tdh[k].a * std::max(0.0, tdh[k].tu) + 2.0 * tdh[k].b * std::max(0.0, -tdh[k].to));
+    }
+    float dmax = 0.f;
+    for (int64_t p = 0; p < Din->nnz; ++p) dmax = std::max(dmax, std::fabs(Din->val[p]));
+    c->tau = c->opt.price_tol * (double)dmax * pi0_l1;
+    std::vector<uint8_t> vs(V);
+    for (int j = 0; j < V; ++j) vs[j] = (uint8_t)s->voxel_struct[j];
+
+    // upload
+    c->D.n_rows = V;
+    c->D.n_cols = N;
+    c->D.nnz_stored = padded;
+    DAO_TRY(upload(c, &c->D.rowptr, Dh.rowptr.data(), Dh.rowptr.size()));
+    DAO_TRY(upload(c, &c->D.col, Dh.col.data(), Dh.col.size()));
+    DAO_TRY(upload(c, &c->D.val, Dh.val.data(), Dh.val.size()));
+    c->Dt.n_rows = N;
+    c->Dt.n_cols = V;
+    c->Dt.nnz_stored = tpadded;
+    DAO_TRY(upload(c, &c->Dt.rowptr, Th.rowptr.data(), Th.rowptr.size()));
+    DAO_TRY(upload(c, &c->Dt.col, Th.col.data(), Th.col.size()));
+    DAO_TRY(upload(c, &c->Dt.val, Th.val.data(), Th.val.size()));
+    DAO_TRY(upload(c, &c->seg, seg.data(), seg.size()));
+    DAO_TRY(upload(c, &c->vstruct, vs.data(), vs.size()));
+    DAO_TRY(upload(c, &c->tf, tfh.data(), tfh.size()));
+    DAO_TRY(upload(c, &c->td, tdh.data(), tdh.size()));
+    DAO_TRY(upload(c, &c->row_info, ri.data(), ri.size()));
+    DAO_TRY(upload(c, &c->beam_row0_d, c->beam_row0.data(), c->beam_row0.size()));
+    DAO_TRY(upload(c, &c->binfo, bi.data(), bi.size()));
+    return DAO_OK;
+}
+
+dao_status alloc_state(dao_ctx* c) {
+    c->K_cap = c->opt.k_max;
+    c->ld = (c->V + 63) / 64 * 64;
+    DAO_TRY(c->dalloc(&c->slab, (size_t)c->K_cap * c->ld));
+    DAO_TRY(c->dalloc(&c->ap_beam, c->K_cap));
+    DAO_TRY(c->dalloc(&c->ap_lr, (size_t)c->K_cap * 2 * c->max_rows));
+    DAO_TRY(c->dalloc(&c->z, c->V));
+    DAO_TRY(c->dalloc(&c->pi, c->V));
+    DAO_TRY(c->dalloc(&c->dose, c->V));
+    DAO_TRY(c->dalloc(&c->w, c->N));
+    DAO_TRY(c->dalloc(&c->x, c->N));
+    int nbmax = 0;
+    for (int b = 0; b < c->B; ++b) nbmax = std::max(nbmax, c->rows[b] * c->cols[b]);
+    DAO_TRY(c->dalloc(&c->mask, nbmax));
+    DAO_TRY(c->dalloc(&c->row_v, c->R_tot));
+    DAO_TRY(c->dalloc(&c->row_lr, c->R_tot));
+    DAO_TRY(c->dalloc(&c->price, 1));
+    c->mb.G = std::max(1, std::min(2 * c->num_sms, (c->V + MASTER_TILE - 1) / MASTER_TILE));
+    DAO_TRY(c->dalloc(&c->mb.st, 1));
+    DAO_TRY(c->dalloc(&c->mb.H_part, (size_t)KMAX * KMAX * c->mb.G));
+    DAO_TRY(c->dalloc(&c->mb.g_part, (size_t)KMAX * c->mb.G));
+    DAO_TRY(c->dalloc(&c->mb.F_part, c->mb.G));
+    c->F_blocks = dose_grid(c->V, c->num_sms);
+    DAO_TRY(c->dalloc(&c->F_part, c->F_blocks));
+    DAO_TRY(c->dalloc(&c->F_dev, 1));
+    DAO_CU(cudaMemset(c->mb.st, 0, sizeof(MasterDev)));
+    DAO_CU(cudaMemset(c->ap_lr, 0, (size_t)c->K_cap * 2 * c->max_rows * sizeof(int)));
+    c->off_small = 0;
+    c->off_rows = 256;
+    c->off_mask = c->off_rows + round4((int64_t)c->R_tot * 2) * sizeof(int);
+    c->off_master = round4(c->off_mask + (size_t)nbmax * sizeof(float) + 64) + 64;
+    c->off_master = (c->off_master + 255) / 256 * 256;
+    c->pinned_bytes = c->off_master + sizeof(MasterDev);
+    void* p = nullptr;
+    DAO_CU(cudaMallocHost(&p, c->pinned_bytes));
+    c->pinned = static_cast<unsigned char*>(p);
+    return DAO_OK;
+}
+
+// ---- the column-generation steps ------------------------------------------------
+
+// pi = grad F(z) and z at the current pool's accepted intensities (final pass).
+dao_status refresh_state(dao_ctx* c) {
+    c->prof_begin(DAO_KC_MASTER_PASS);
+    DAO_CU(launch_master_pass(c->slab, c->V, c->ld, c->K, c->mb, c->vstruct, c->tf, c->td, c->S, c->z, c->pi, 1,
+                              c->stream, &c->launches_i));
+    c->prof_end();
+    return DAO_OK;
+}
+
+dao_status master_solve(dao_ctx* c, double* F_out) {
+    DAO_CU(launch_master_init(c->mb.st, c->K, c->stream, &c->launches_i));
+    const int unroll = 4;
+    const int max_passes = c->opt.max_master_iters + 80;
+    int passes = 0;
+    const size_t tail = sizeof(MasterDev) - offsetof(MasterDev, F);
+    MasterDev* shadow = reinterpret_cast<MasterDev*>(c->pinned + c->off_master - offsetof(MasterDev, F));
+    for (;;) {
+        for (int u = 0; u < unroll; ++u) {
+            c->prof_begin(DAO_KC_MASTER_PASS);
+            DAO_CU(launch_master_pass(c->slab, c->V, c->ld, c->K, c->mb, c->vstruct, c->tf, c->td, c->S, nullptr,
+                                      nullptr, 0, c->stream, &c->launches_i));
+            c->prof_end();
+            c->prof_begin(DAO_KC_MASTER_REDUCE);
+            DAO_CU(launch_master_reduce(c->K, c->mb, c->stream, &c->launches_i));
+            c->prof_end();
+            c->prof_begin(DAO_KC_MASTER_STEP);
+            DAO_CU(launch_master_step(c->mb, c->opt.max_master_iters, c->opt.master_tol, c->stream, &c->launches_i));
+            c->prof_end();
+        }
+        passes += unroll;
+        DAO_CU(cudaMemcpyAsync(&shadow->F, &c->mb.st->F, tail, cudaMemcpyDeviceToHost, c->stream));
+        DAO_TRY(sync(c));
+        if (shadow->done) break;
+        if (passes > max_passes) return fail(DAO_ETIMEOUT, "master problem did not stop within its evaluation cap");
+    }
+    DAO_TRY(refresh_state(c));
+    c->stat_evals.push_back(shadow->n_eval);
+    c->stat_status.push_back(shadow->status);
+    c->stat_kkt.push_back(shadow->res / (shadow->tol > 0 ? shadow->tol / c->opt.master_tol : 1.0));
+    if (F_out) *F_out = shadow->F;
+    return DAO_OK;
+}
+
+// pricing on the vector w already on the device; fills host outputs
+dao_status price_on_w(dao_ctx* c, const float* w, int32_t* beam, int32_t* leaf_lr, double* rc, double* row_best,
+                      int32_t* row_lr_out) {
+    c->prof_begin(DAO_KC_PRICE);
+    DAO_CU(launch_price(w, c->row_info, c->R_tot, c->beam_row0_d, c->B, c->row_v, c->row_lr, c->price, c->stream,
+                        &c->launches_i));
+    c->prof_end();
+    PriceDev* pd = reinterpret_cast<PriceDev*>(c->pinned + c->off_small + 16);
+    int* lr = reinterpret_cast<int*>(c->pinned + c->off_rows);
+    DAO_CU(cudaMemcpyAsync(pd, c->price, sizeof(PriceDev), cudaMemcpyDeviceToHost, c->stream));
+    DAO_CU(cudaMemcpyAsync(lr, c->row_lr, sizeof(int2) * c->R_tot, cudaMemcpyDeviceToHost, c->stream));
+    if (row_best) DAO_CU(cudaMemcpyAsync(row_best, c->row_v, sizeof(double) * c->R_tot, cudaMemcpyDeviceToHost, c->stream));
+    DAO_TRY(sync(c));
+    const int b = pd->beam;
+    if (beam) *beam = b;
+    if (rc) *rc = pd->rc;
+    if (leaf_lr)
+        for (int r = 0; r < c->rows[b]; ++r) {
+            leaf_lr[2 * r] = lr[2 * (c->beam_row0[b] + r)];
+            leaf_lr[2 * r + 1] = lr[2 * (c->beam_row0[b] + r) + 1];
+        }
+    if (row_lr_out) std::memcpy(row_lr_out, lr, sizeof(int) * 2 * c->R_tot);
+    return DAO_OK;
+}
+
+dao_status validate_aperture(const dao_ctx* c, int beam, const int32_t* lr) {
+    if (beam < 0 || beam >= c->B || lr == nullptr) return fail(DAO_EINVAL, "invalid beam index");
+    for (int r = 0; r < c->rows[beam]; ++r) {
+        const int L = lr[2 * r], R = lr[2 * r + 1];
+        if (L < 0 || R < L || R > c->cols[beam])
+            return fail(DAO_EINVAL, "leaf range out of bounds in row " + std::to_string(r));
+    }
+    return DAO_OK;
+}
+
+bool is_duplicate(const dao_ctx* c, int beam, const int32_t* lr) {
+    const int stride = 2 * c->max_rows;
+    for (int k = 0; k < c->K; ++k) {
+        if (c->ap_beam_h[k] != beam) continue;
+        bool same = true;
+        for (int r = 0; r < c->rows[beam] && same; ++r) {
+            int L = lr[2 * r], R = lr[2 * r + 1];
+            if (L == R) L = R = 0;
+            same = c->ap_lr_h[(size_t)k * stride + 2 * r] == L && c->ap_lr_h[(size_t)k * stride + 2 * r + 1] == R;
+        }
+        if (same) return true;
+    }
+    return false;
+}
+
+// form the new column (Eq. 2) into slab column K, record the aperture
+dao_status add_column(dao_ctx* c, int beam, const int32_t* lr, float* out) {
+    const int nb = c->rows[beam] * c->cols[beam];
+    float* m = reinterpret_cast<float*>(c->pinned + c->off_mask);
+    for (int i = 0; i < nb; ++i) m[i] = 0.f;
+    for (int r = 0; r < c->rows[beam]; ++r)
+        for (int q = lr[2 * r]; q < lr[2 * r + 1]; ++q) m[r * c->cols[beam] + q] = 1.f;
+    DAO_CU(cudaMemcpyAsync(c->mask, m, sizeof(float) * nb, cudaMemcpyHostToDevice, c->stream));
+    c->prof_begin(DAO_KC_COLUMN);
+    DAO_CU(launch_column(c->D, c->seg + (size_t)beam * c->V, c->seg + (size_t)(beam + 1) * c->V, c->beam_off[beam],
+                         nb, c->mask, out, c->num_sms, c->stream, &c->launches_i));
+    c->prof_end();
+    return DAO_OK;
+}
+
+dao_status add_aperture(dao_ctx* c, int beam, const int32_t* lr, double* F) {
+    if (c->K >= c->K_cap) return fail(DAO_ESTATE, "aperture pool is full (k_max)");
+    DAO_TRY(add_column(c, beam, lr, c->slab + (size_t)c->K * c->ld));
+    const int stride = 2 * c->max_rows;
+    c->ap_beam_h.push_back(beam);
+    c->ap_lr_h.resize((size_t)(c->K + 1) * stride, 0);
+    for (int r = 0; r < c->rows[beam]; ++r) {
+        int L = lr[2 * r], R = lr[2 * r + 1];
+        if (L == R) L = R = 0;
+        c->ap_lr_h[(size_t)c->K * stride + 2 * r] = L;
+        c->ap_lr_h[(size_t)c->K * stride + 2 * r + 1] = R;
+    }
+    DAO_CU(cudaMemcpyAsync(c->ap_beam + c->K, &c->ap_beam_h[c->K], sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    DAO_CU(cudaMemcpyAsync(c->ap_lr + (size_t)c->K * stride, &c->ap_lr_h[(size_t)c->K * stride], sizeof(int) * stride,
+                           cudaMemcpyHostToDevice, c->stream));
+    c->K += 1;
+    return master_solve(c, F);
+}
+
+dao_status reset_state(dao_ctx* c) {
+    c->K = 0;
+    c->stat_evals.clear();
+    c->stat_status.clear();
+    c->stat_kkt.clear();
+    c->ap_beam_h.clear();
+    c->ap_lr_h.clear();
+    DAO_CU(cudaMemsetAsync(c->mb.st, 0, sizeof(MasterDev), c->stream));
+    DAO_TRY(refresh_state(c));
+    DAO_TRY(sync(c));
+    return DAO_OK;
+}
+
+}  // namespace
+
+// ================================ C ABI ==========================================
+
+extern "C" {
+
+void dao_options_default(dao_options* opt) {
+    if (!opt) return;
+    opt->k_max = KMAX;
+    opt->max_master_iters = 100;
+    opt->master_tol = 1e-6;
+    opt->price_tol = 1e-7;
+    opt->precision = DAO_PREC_FP32;
+    opt->device = 0;
+    opt->stream = nullptr;
+}
+
+const char* dao_last_error(void) { return g_err.c_str(); }
+
+dao_status dao_create(const dao_csr* D, const dao_geometry* g, const dao_structures* s, const dao_weights* w,
+                      const double* prescriptions, const dao_options* opt_in, dao_ctx** out) {
+    if (!out) return fail(DAO_EINVAL, "null output pointer");
+    *out = nullptr;
+    dao_options opt;
+    dao_options_default(&opt);
+    if (opt_in) opt = *opt_in;
+    DAO_TRY(validate(D, g, s, w, prescriptions, &opt));
+    dao_ctx* c = new (std::nothrow) dao_ctx();
+    if (!c) return fail(DAO_ENOMEM, "host allocation failed");
+    c->opt = opt;
+    c->device = opt.device;
+    c->V = D->n_voxels;
+    c->N = D->n_beamlets;
+    c->B = g->n_beams;
+    c->nnz = D->nnz;
+    dao_status st = DAO_OK;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) st = fail(DAO_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    if (st == DAO_OK) {
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+        if (opt.stream) {
+            c->stream = static_cast<cudaStream_t>(opt.stream);
+        } else {
+            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) st = fail(DAO_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+            c->own_stream = true;
+        }
+    }
+    if (st == DAO_OK) {
+        e = master_configure();
+        if (e != cudaSuccess) st = fail(DAO_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    }
+    if (st == DAO_OK) st = build(c, D, g, s, w, prescriptions);
+    if (st == DAO_OK) st = alloc_state(c);
+    if (st == DAO_OK) st = reset_state(c);
+    if (st != DAO_OK) {
+        std::string keep = g_err;
+        dao_destroy(c);
+        g_err = keep;
+        return st;
+    }
+    c->count_launches();
+    *out = c;
+    return DAO_OK;
+}
+
+void dao_destroy(dao_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (void* p : c->dev_allocs) cudaFree(p);
+    for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+dao_status dao_reset(dao_ctx* c) {
+    DAO_TRY(check_ctx(c));
+    dao_status st = reset_state(c);
+    c->count_launches();
+    return st;
+}
+
+dao_status dao_sizes(const dao_ctx* c, int32_t* V, int32_t* N, int32_t* B, int32_t* R, int32_t* max_rows,
+                     int64_t* nnz_stored, int32_t* k_max) {
+    if (!c) return fail(DAO_EINVAL, "null context");
+    if (V) *V = c->V;
+    if (N) *N = c->N;
+    if (B) *B = c->B;
+    if (R) *R = c->R_tot;
+    if (max_rows) *max_rows = c->max_rows;
+    if (nnz_stored) *nnz_stored = c->D.nnz_stored;
+    if (k_max) *k_max = c->K_cap;
+    return DAO_OK;
+}
+
+dao_status dao_price(dao_ctx* c, int32_t* beam, int32_t* leaf_lr, double* rc) {
+    DAO_TRY(check_ctx(c));
+    c->prof_begin(DAO_KC_DT);
+    DAO_CU(launch_dt(c->Dt, c->pi, c->w, c->stream, &c->launches_i));
+    c->prof_end();
+    double r = 0.0;
+    dao_status st = price_on_w(c, c->w, beam, leaf_lr, &r, nullptr, nullptr);
+    c->count_launches();
+    if (st != DAO_OK) return st;
+    if (rc) *rc = r;
+    return r < -c->tau ? DAO_OK : DAO_OPTIMAL;
+}
+
+dao_status dao_add_aperture(dao_ctx* c, int32_t beam, const int32_t* leaf_lr, double* objective) {
+    DAO_TRY(check_ctx(c));
+    DAO_TRY(validate_aperture(c, beam, leaf_lr));
+    dao_status st = add_aperture(c, beam, leaf_lr, objective);
+    c->count_launches();
+    return st;
+}
+
+dao_status dao_solve(dao_ctx* c, int32_t n_apertures, int32_t* n_done, double* trace) {
+    DAO_TRY(check_ctx(c));
+    if (n_apertures < 0) return fail(DAO_EINVAL, "negative aperture count");
+    std::vector<int32_t> lr(2 * c->max_rows);
+    dao_status result = DAO_OK;
+    for (int k = 0; k < n_apertures; ++k) {
+        if (c->K >= c->K_cap) {
+            result = fail(DAO_ESTATE, "aperture pool is full (k_max)");
+            break;
+        }
+        c->prof_begin(DAO_KC_DT);
+        DAO_CU(launch_dt(c->Dt, c->pi, c->w, c->stream, &c->launches_i));
+        c->prof_end();
+        int32_t beam = 0;
+        double rc = 0.0;
+        DAO_TRY(price_on_w(c, c->w, &beam, lr.data(), &rc, nullptr, nullptr));
+        if (!(rc < -c->tau)) {
+            result = DAO_OPTIMAL;
+            break;
+        }
+        if (is_duplicate(c, beam, lr.data())) {
+            result = DAO_DUPLICATE;
+            break;
+        }
+        double F = 0.0;
+        DAO_TRY(add_aperture(c, beam, lr.data(), &F));
+        if (trace) trace[k] = F;
+    }
+    if (n_done) *n_done = c->K;
+    c->count_launches();
+    return result;
+}
+
+dao_status dao_dose(dao_ctx* c, float* dose, double* objective) {
+    DAO_TRY(check_ctx(c));
+    DAO_CU(launch_fluence(c->ap_beam, c->ap_lr, 2 * c->max_rows, c->mb.st->y, c->K, c->binfo, c->N, c->x, c->stream,
+                          &c->launches_i));
+    c->prof_begin(DAO_KC_DOSE);
+    DAO_CU(launch_dose(c->D, c->x, c->vstruct, c->tf, c->td, c->S, c->dose, nullptr, c->F_part, c->F_blocks, c->F_dev,
+                       c->num_sms, c->stream, &c->launches_i));
+    c->prof_end();
+    double* f = reinterpret_cast<double*>(c->pinned + c->off_small + 8);
+    DAO_CU(cudaMemcpyAsync(f, c->F_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (dose) DAO_CU(cudaMemcpyAsync(dose, c->dose, sizeof(float) * c->V, cudaMemcpyDeviceToHost, c->stream));
+    DAO_TRY(sync(c));
+    if (objective) *objective = *f;
+    c->count_launches();
+    return DAO_OK;
+}
+
+dao_status dao_intensities(dao_ctx* c, double* y, int32_t* k) {
+    DAO_TRY(check_ctx(c));
+    if (y && c->K > 0) {
+        DAO_CU(cudaMemcpyAsync(y, c->mb.st->y, sizeof(double) * c->K, cudaMemcpyDeviceToHost, c->stream));
+        DAO_TRY(sync(c));
+    }
+    if (k) *k = c->K;
+    return DAO_OK;
+}
+
+dao_status dao_apertures(dao_ctx* c, int32_t* beams, int32_t* leaf_lr, int32_t* k) {
+    if (!c) return fail(DAO_EINVAL, "null context");
+    if (beams) std::memcpy(beams, c->ap_beam_h.data(), sizeof(int) * c->K);
+    if (leaf_lr) std::memcpy(leaf_lr, c->ap_lr_h.data(), sizeof(int) * c->K * 2 * c->max_rows);
+    if (k) *k = c->K;
+    return DAO_OK;
+}
+
+dao_status dao_k_dose(dao_ctx* c, const float* x, float* z, float* grad, double* objective) {
+    DAO_TRY(check_ctx(c));
+    if (!x || !z) return fail(DAO_EINVAL, "null vector");
+    c->prof_begin(DAO_KC_DOSE);
+    DAO_CU(launch_dose(c->D, x, c->vstruct, c->tf, c->td, c->S, z, grad, objective ? c->F_part : nullptr, c->F_blocks,
+                       c->F_dev, c->num_sms, c->stream, &c->launches_i));
+    c->prof_end();
+    if (objective) {
+        double* f = reinterpret_cast<double*>(c->pinned + c->off_small + 8);
+        DAO_CU(cudaMemcpyAsync(f, c->F_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        DAO_TRY(sync(c));
+        *objective = *f;
+    } else {
+        DAO_TRY(sync(c));
+    }
+    c->count_launches();
+    return DAO_OK;
+}
+
+dao_status dao_k_beamlet_prices(dao_ctx* c, const float* pi, float* w) {
+    DAO_TRY(check_ctx(c));
+    if (!pi || !w) return fail(DAO_EINVAL, "null vector");
+    c->prof_begin(DAO_KC_DT);
+    DAO_CU(launch_dt(c->Dt, pi, w, c->stream, &c->launches_i));
+    c->prof_end();
+    DAO_TRY(sync(c));
+    c->count_launches();
+    return DAO_OK;
+}
+
+dao_status dao_k_price(dao_ctx* c, const float* w, int32_t* beam, int32_t* leaf_lr, double* rc, double* row_best,
+                       int32_t* row_lr) {
+    DAO_TRY(check_ctx(c));
+    if (!w) return fail(DAO_EINVAL, "null vector");
+    double r = 0.0;
+    dao_status st = price_on_w(c, w, beam, leaf_lr, &r, row_best, row_lr);
+    c->count_launches();
+    if (st != DAO_OK) return st;
+    if (rc) *rc = r;
+    return r < -c->tau ? DAO_OK : DAO_OPTIMAL;
+}
+
+dao_status dao_k_aperture_column(dao_ctx* c, int32_t beam, const int32_t* leaf_lr, float* out) {
+    DAO_TRY(check_ctx(c));
+    DAO_TRY(validate_aperture(c, beam, leaf_lr));
+    if (!out) return fail(DAO_EINVAL, "null vector");
+    DAO_TRY(add_column(c, beam, leaf_lr, out));
+    DAO_TRY(sync(c));
+    c->count_launches();
+    return DAO_OK;
+}
+
+dao_status dao_k_state(dao_ctx* c, float* z, float* pi) {
+    DAO_TRY(check_ctx(c));
+    if (z) DAO_CU(cudaMemcpyAsync(z, c->z, sizeof(float) * c->V, cudaMemcpyDeviceToDevice, c->stream));
+    if (pi) DAO_CU(cudaMemcpyAsync(pi, c->pi, sizeof(float) * c->V, cudaMemcpyDeviceToDevice, c->stream));
+    DAO_TRY(sync(c));
+    return DAO_OK;
+}
+
+dao_status dao_profile_enable(dao_ctx* c, int32_t enable) {
+    DAO_TRY(check_ctx(c));
+    DAO_TRY(sync(c));
+    c->prof_on = enable != 0;
+    c->recs.clear();
+    c->ev_used = 0;
+    return DAO_OK;
+}
+
+dao_status dao_profile_read(dao_ctx* c, int32_t kc, int64_t* launches, double* total_ms) {
+    DAO_TRY(check_ctx(c));
+    if (kc < 0 || kc >= DAO_KC_COUNT) return fail(DAO_EINVAL, "unknown kernel class");
+    DAO_TRY(sync(c));
+    int64_t n = 0;
+    double ms = 0.0;
+    for (const ProfRecord& r : c->recs) {
+        if (r.kc != kc) continue;
+        float t = 0.f;
+        DAO_CU(cudaEventElapsedTime(&t, r.start, r.stop));
+        ms += t;
+        n += r.launches;
+    }
+    if (launches) *launches = n;
+    if (total_ms) *total_ms = ms;
+    return DAO_OK;
+}
+
+int64_t dao_launch_count(const dao_ctx* c) { return c ? c->launches_total + c->launches_i : 0; }
+
+dao_status dao_master_stats(const dao_ctx* c, int32_t* evals, int32_t* status, double* kkt, int32_t* k) {
+    if (!c) return fail(DAO_EINVAL, "null context");
+    const int n = (int)c->stat_evals.size();
+    for (int i = 0; i < n; ++i) {
+        if (evals) evals[i] = c->stat_evals[i];
+        if (status) status[i] = c->stat_status[i];
+        if (kkt) kkt[i] = c->stat_kkt[i];
+    }
+    if (k) *k = n;
+    return DAO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+// Pricing sub-problem of column-generation DAO (arXiv:1003.5402, Eq. 8 and the
+// one-pass MLC-row search of Sec. 2.3), re-designed as one warp per MLC row.
+//
+// For row w_1..w_n (n <= 32, lane c holds w_{c+1}) the paper's sequential loop
+// keeps the running sum v = S_r, the largest running sum vbar = max(0, S_1..S_r)
+// with its earliest position l, and the best value v* = min_r (S_r - vbar_r)
+// with the earliest r.  The warp computes the same quantities:
+//   1. S_r by lane-serial replay: lane r-1 adds w_1, ..., w_r in that order in
+//      FP64, which is exactly the rounding sequence of the sequential loop;
+//   2. (vbar_r, l_r) by an inclusive shuffle scan whose operator keeps the
+//      earlier element unless the later one is strictly larger (the strict ">"
+//      of the loop), seeded with the empty prefix (0, 0);
+//   3. S_r - vbar_r per lane (the same subtraction as the loop), then a
+//      butterfly minimum that prefers the smaller r on equal values (the
+//      strict "<").
+// The result equals the sequential loop bit for bit for the same FP32 inputs.
+// The per-beam sum adds the rows' v* in row order, and the beam argmin keeps
+// the lowest beam index on ties.
+#include "dao_internal.h"
+
+namespace dao {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// row_info[g] = (beam, first beamlet index, columns, row within the beam)
+__global__ void __launch_bounds__(256) k_price_rows(const float* __restrict__ w, const int4* __restrict__ row_info,
+                                                    int n_rows, double* __restrict__ row_v,
+                                                    int2* __restrict__ row_lr) {
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= n_rows) return;  // uniform per warp
+    const int4 ri = row_info[g];
+    const int n = ri.z;
+    const double wv = lane < n ? (double)w[ri.y + lane] : 0.0;
+
+    // 1. prefix sums in the sequential order
+    double s = 0.0;
+    for (int q = 0; q < n; ++q) {
+        const double t = __shfl_sync(FULL, wv, q);
+        if (q <= lane) s = s + t;
+    }
+
+    // 2. running maximum with the earliest position (1-based prefix index)
+    double m = lane < n ? s : -INFINITY;
+    int mi = lane + 1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double om = __shfl_up_sync(FULL, m, o);
+        const int omi = __shfl_up_sync(FULL, mi, o);
+        if (lane >= o && !(m > om)) {
+            m = om;
+            mi = omi;
+        }
+    }
+    if (!(m > 0.0)) {  // the empty prefix S_0 = 0 at l = 0 comes first
+        m = 0.0;
+        mi = 0;
+    }
+
+    // 3. best (most negative) S_r - vbar_r, earliest r on ties
+    double bd = lane < n ? s - m : INFINITY;
+    int br = lane + 1;
+    int bl = mi;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double od = __shfl_xor_sync(FULL, bd, o);
+        const int orr = __shfl_xor_sync(FULL, br, o);
+        const int ol = __shfl_xor_sync(FULL, bl, o);
+        if (od < bd || (od == bd && orr < br)) {
+            bd = od;
+            br = orr;
+            bl = ol;
+        }
+    }
+    if (lane == 0) {
+        if (bd < 0.0) {
+            row_v[g] = bd;
+            row_lr[g] = make_int2(bl, br);  // open beamlets [l*, r* - 1) in 0-based half-open form
+        } else {
+            row_v[g] = 0.0;
+            row_lr[g] = make_int2(0, 0);
+        }
+    }
+}
+
+// One block: thread b sums beam b's rows in row order; thread 0 takes the argmin.
+__global__ void __launch_bounds__(256) k_price_beams(const double* __restrict__ row_v,
+                                                     const int* __restrict__ beam_row0, int n_beams,
+                                                     PriceDev* __restrict__ out) {
+    extern __shared__ double s_sum[];
+    for (int b = threadIdx.x; b < n_beams; b += blockDim.x) {
+        double t = 0.0;
+        for (int r = beam_row0[b]; r < beam_row0[b + 1]; ++r) t = t + row_v[r];
+        s_sum[b] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int best = 0;
+        for (int b = 1; b < n_beams; ++b)
+            if (s_sum[b] < s_sum[best]) best = b;
+        out->beam = best;
+        out->rc = n_beams > 0 ? s_sum[best] : 0.0;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_price(const float* w, const int4* row_info, int n_rows, const int* beam_row0, int n_beams,
+                         double* row_v, int2* row_lr, PriceDev* out, cudaStream_t stream, int* launches) {
+    const int warps_per_block = 8;
+    const int grid = (n_rows + warps_per_block - 1) / warps_per_block;
+    if (grid > 0) {
+        k_price_rows<<<grid, 32 * warps_per_block, 0, stream>>>(w, row_info, n_rows, row_v, row_lr);
+        ++*launches;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    k_price_beams<<<1, 256, (size_t)(n_beams > 0 ? n_beams : 1) * sizeof(double), stream>>>(row_v, beam_row0,
+                                                                                           n_beams, out);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+}  // namespace dao

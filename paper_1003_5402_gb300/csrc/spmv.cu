@@ -1,0 +1,249 @@
+// Sparse dose kernels of column-generation DAO (arXiv:1003.5402):
+//   a1  z = D x with the objective epilogue (Eqs. 1, 5, 7, 9, 10),
+//   a2  w = D^T pi from the stored transpose (the bracketed sum of Eq. 8),
+//   a4  the dose column of a new aperture, D_kj = sum_{i in A_k} D_ij (Eq. 2),
+//   and the beamlet fluence x_i = sum_{k in K_i} y_k (Eq. 7).
+// All reductions have a fixed order (per-lane sequential, then a fixed
+// shuffle tree, then fixed-order shared-memory combination), so every result
+// is bitwise reproducible for a given launch shape.  No atomics.
+#include "dao_internal.h"
+
+namespace dao {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Sum of one double per thread over the block; the result is valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_sum_f64(double v, double* s_red) {
+    v = warp_sum_f64(v);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) s_red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = lane < NT / 32 ? s_red[lane] : 0.0;
+        t = warp_sum_f64(t);
+    }
+    return t;
+}
+
+// ---- a1 ---------------------------------------------------------------------
+// G lanes per voxel row, rows_per_warp = 32 / G rows per warp; every lane of a
+// warp runs the same number of tile iterations so the shuffles stay converged.
+template <int G, bool SMEM_X>
+__global__ void __launch_bounds__(256) k_dose(const int* __restrict__ rowptr, const int4* __restrict__ col4,
+                                              const float4* __restrict__ val4, int V,
+                                              const float* __restrict__ x, int N,
+                                              const uint8_t* __restrict__ vstruct,
+                                              const StructTermsD* __restrict__ td, int S,
+                                              float* __restrict__ z, float* __restrict__ grad,
+                                              double* __restrict__ F_part) {
+    extern __shared__ float sx[];
+    __shared__ StructTermsD s_td[SMAX];
+    __shared__ double s_red[8];
+    if (SMEM_X)
+        for (int i = threadIdx.x; i < N; i += blockDim.x) sx[i] = x[i];
+    for (int i = threadIdx.x; i < S; i += blockDim.x) s_td[i] = td[i];
+    __syncthreads();
+    const float* xs = SMEM_X ? sx : x;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % G;
+    constexpr int RPW = 32 / G;
+    const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int n_warps = (gridDim.x * blockDim.x) >> 5;
+    const int n_tiles = (V + RPW - 1) / RPW;
+    double facc = 0.0;
+    for (int t = warp_global; t < n_tiles; t += n_warps) {
+        const int row = t * RPW + lane / G;
+        float acc = 0.f;
+        if (row < V) {
+            const int p0 = rowptr[row] >> 2, p1 = rowptr[row + 1] >> 2;
+            for (int p = p0 + sub; p < p1; p += G) {
+                const int4 c = __ldg(col4 + p);
+                const float4 v = __ldg(val4 + p);
+                acc = fmaf(v.x, xs[c.x], acc);
+                acc = fmaf(v.y, xs[c.y], acc);
+                acc = fmaf(v.z, xs[c.z], acc);
+                acc = fmaf(v.w, xs[c.w], acc);
+            }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        if (row < V && sub == 0) {
+            z[row] = acc;
+            if (grad != nullptr || F_part != nullptr) {
+                const StructTermsD tt = s_td[vstruct[row]];
+                const double zd = acc;
+                const double u = fmax(0.0, tt.tu - zd);
+                const double o = fmax(0.0, zd - tt.to);
+                if (grad != nullptr) grad[row] = (float)(2.0 * (tt.b * o - tt.a * u));
+                facc += tt.a * u * u + tt.b * o * o;
+            }
+        }
+    }
+    if (F_part != nullptr) {
+        const double s = block_sum_f64<256>(facc, s_red);
+        if (threadIdx.x == 0) F_part[blockIdx.x] = s;
+    }
+}
+
+// Fixed-order sum of n doubles by one block.
+__global__ void __launch_bounds__(256) k_sum_f64(const double* __restrict__ part, int n, double* __restrict__ out) {
+    __shared__ double s_red[8];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) v += part[i];
+    const double s = block_sum_f64<256>(v, s_red);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// ---- a2 ---------------------------------------------------------------------
+// One block per beamlet row of D^T; int4/float4 loads of (voxel, value),
+// gathered pi from L2; FP32 products, FP64 combination across threads.
+template <int BT>
+__global__ void __launch_bounds__(BT) k_dt(const int* __restrict__ rowptr, const int4* __restrict__ col4,
+                                           const float4* __restrict__ val4, int N,
+                                           const float* __restrict__ pi, float* __restrict__ w) {
+    __shared__ double s_red[BT / 32];
+    const int row = blockIdx.x;
+    const int p0 = rowptr[row] >> 2, p1 = rowptr[row + 1] >> 2;
+    float acc = 0.f;
+    for (int p = p0 + threadIdx.x; p < p1; p += BT) {
+        const int4 c = __ldg(col4 + p);
+        const float4 v = __ldg(val4 + p);
+        acc = fmaf(v.x, __ldg(pi + c.x), acc);
+        acc = fmaf(v.y, __ldg(pi + c.y), acc);
+        acc = fmaf(v.z, __ldg(pi + c.z), acc);
+        acc = fmaf(v.w, __ldg(pi + c.w), acc);
+    }
+    const double s = block_sum_f64<BT>((double)acc, s_red);
+    if (threadIdx.x == 0) w[row] = (float)s;
+}
+
+// ---- a4 ---------------------------------------------------------------------
+// G lanes per voxel row over the row's segment of beam b (columns base ..
+// base + nb - 1); mask[c] in {0, 1} marks the aperture's open beamlets.
+template <int G>
+__global__ void __launch_bounds__(256) k_column(const int* __restrict__ col, const float* __restrict__ val,
+                                                const int* __restrict__ seg_lo, const int* __restrict__ seg_hi,
+                                                int V, int base, int nb, const float* __restrict__ mask,
+                                                float* __restrict__ out) {
+    extern __shared__ float smask[];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) smask[i] = mask[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % G;
+    constexpr int RPW = 32 / G;
+    const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int n_warps = (gridDim.x * blockDim.x) >> 5;
+    const int n_tiles = (V + RPW - 1) / RPW;
+    for (int t = warp_global; t < n_tiles; t += n_warps) {
+        const int row = t * RPW + lane / G;
+        float acc = 0.f;
+        if (row < V) {
+            const int q1 = seg_hi[row];
+            for (int p = seg_lo[row] + sub; p < q1; p += G) acc = fmaf(__ldg(val + p), smask[__ldg(col + p) - base], acc);
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        if (row < V && sub == 0) out[row] = acc;
+    }
+}
+
+// ---- Eq. 7 ------------------------------------------------------------------
+__global__ void k_fluence(const int* __restrict__ ap_beam, const int* __restrict__ ap_lr, int lr_stride,
+                          const double* __restrict__ y, int K, const int4* __restrict__ binfo, int N,
+                          float* __restrict__ x) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int4 bi = binfo[i];  // beam, MLC row within the beam, column, unused
+    double s = 0.0;
+    for (int k = 0; k < K; ++k) {
+        if (ap_beam[k] != bi.x) continue;
+        const int L = ap_lr[k * lr_stride + 2 * bi.y];
+        const int R = ap_lr[k * lr_stride + 2 * bi.y + 1];
+        if (bi.z >= L && bi.z < R) s += y[k];
+    }
+    x[i] = (float)s;
+}
+
+template <int G>
+cudaError_t dose_g(const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsD* td, int S,
+                   float* z, float* grad, double* F_part, int grid, cudaStream_t stream) {
+    const size_t smem = (size_t)D.n_cols * sizeof(float);
+    if (smem <= 48 * 1024) {
+        k_dose<G, true><<<grid, 256, smem, stream>>>(D.rowptr, reinterpret_cast<const int4*>(D.col),
+                                                     reinterpret_cast<const float4*>(D.val), D.n_rows, x,
+                                                     D.n_cols, vstruct, td, S, z, grad, F_part);
+    } else {
+        k_dose<G, false><<<grid, 256, 0, stream>>>(D.rowptr, reinterpret_cast<const int4*>(D.col),
+                                                   reinterpret_cast<const float4*>(D.val), D.n_rows, x,
+                                                   D.n_cols, vstruct, td, S, z, grad, F_part);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int dose_grid(int n_rows, int num_sms) {
+    (void)n_rows;
+    return num_sms * 8;
+}
+
+cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsF* tf,
+                        const StructTermsD* td, int S, float* z, float* grad, double* F_part, int F_blocks,
+                        double* F_out, int num_sms, cudaStream_t stream, int* launches) {
+    (void)tf;
+    const int grid = dose_grid(D.n_rows, num_sms);
+    if (F_part != nullptr && F_blocks < grid) return cudaErrorInvalidValue;
+    const double mean = D.n_rows > 0 ? (double)D.nnz_stored / (double)D.n_rows : 0.0;
+    cudaError_t e;
+    if (mean <= 24.0)
+        e = dose_g<4>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+    else if (mean <= 64.0)
+        e = dose_g<8>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+    else if (mean <= 160.0)
+        e = dose_g<16>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+    else
+        e = dose_g<32>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+    ++*launches;
+    if (e != cudaSuccess || F_part == nullptr || F_out == nullptr) return e;
+    k_sum_f64<<<1, 256, 0, stream>>>(F_part, grid, F_out);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dt(const DevCSR& Dt, const float* pi, float* w, cudaStream_t stream, int* launches) {
+    if (Dt.n_rows == 0) return cudaSuccess;
+    k_dt<128><<<Dt.n_rows, 128, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
+                                              reinterpret_cast<const float4*>(Dt.val), Dt.n_rows, pi, w);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_column(const DevCSR& D, const int* seg_lo, const int* seg_hi, int base, int nb,
+                          const float* mask, float* out, int num_sms, cudaStream_t stream, int* launches) {
+    if (D.n_rows == 0) return cudaSuccess;
+    const int grid = num_sms * 8;
+    k_column<8><<<grid, 256, (size_t)nb * sizeof(float), stream>>>(D.col, D.val, seg_lo, seg_hi, D.n_rows, base,
+                                                                   nb, mask, out);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fluence(const int* ap_beam, const int* ap_lr, int lr_stride, const double* y, int K,
+                           const int4* binfo, int N, float* x, cudaStream_t stream, int* launches) {
+    if (N == 0) return cudaSuccess;
+    k_fluence<<<(N + 255) / 256, 256, 0, stream>>>(ap_beam, ap_lr, lr_stride, y, K, binfo, N, x);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+}  // namespace dao

@@ -1,0 +1,121 @@
+"""The C ABI without a GPU: libdao.so loads, exports every function that
+include/*.h declares, and rejects malformed inputs on the host (no CUDA call is
+reached before validation)."""
+import ctypes as C
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1003_5402_gb300 import build
+    build.build()
+    from paper_1003_5402_gb300 import binding
+    return binding.load()
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(dao_[A-Za-z0-9_]+)\s*\(", src, re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ["dao_create", "dao_price", "dao_add_aperture", "dao_solve", "dao_dose", "dao_destroy",
+                     "dao_last_error"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1003_5402_gb300 import binding
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert name in binding.SIGNATURES, name
+
+
+def test_options_default_on_host(lib):
+    from paper_1003_5402_gb300 import binding
+    o = binding.options()
+    assert o.k_max == 64 and o.max_master_iters == 100 and o.precision == 0
+    assert o.master_tol == 1e-6
+
+
+def _tiny_inputs():
+    V, N = 6, 8
+    indptr = np.array([0, 2, 3, 3, 5, 6, 8], dtype=np.int64)
+    indices = np.array([0, 3, 1, 2, 7, 5, 0, 4], dtype=np.int32)
+    data = np.ones(8, dtype=np.float32)
+    rows = np.array([2], dtype=np.int32)
+    cols = np.array([4], dtype=np.int32)
+    vs = np.array([0, 0, 1, 1, 1, 1], dtype=np.int32)
+    tgt = np.array([1, 0], dtype=np.uint8)
+    return dict(indptr=indptr, indices=indices, data=data, rows=rows, cols=cols, vs=vs, tgt=tgt,
+                uw=np.array([10.0, 0.0]), ow=np.array([1.0, 1.0]), ot=np.array([1.0, 0.5]),
+                rx=np.array([1.0, 0.0]), V=V, N=N)
+
+
+def _create(lib, d, **opt):
+    from paper_1003_5402_gb300 import binding as b
+    P = lambda a, t: a.ctypes.data_as(C.POINTER(t))
+    D = b.dao_csr(d["V"], d["N"], int(d["indptr"][-1]), P(d["indptr"], C.c_int64), P(d["indices"], C.c_int32),
+                  P(d["data"], C.c_float))
+    g = b.dao_geometry(len(d["rows"]), P(d["rows"], C.c_int32), P(d["cols"], C.c_int32))
+    s = b.dao_structures(len(d["uw"]), P(d["vs"], C.c_int32), P(d["tgt"], C.c_uint8))
+    w = b.dao_weights(P(d["uw"], C.c_double), P(d["ow"], C.c_double), P(d["ot"], C.c_double), 1)
+    o = b.options(**opt)
+    h = C.c_void_p()
+    st = lib.dao_create(C.byref(D), C.byref(g), C.byref(s), C.byref(w), P(d["rx"], C.c_double), C.byref(o),
+                        C.byref(h))
+    if st == 0:
+        lib.dao_destroy(h)
+    return st, lib.dao_last_error().decode()
+
+
+@pytest.mark.parametrize("mutate,needle", [
+    (lambda d: d["indptr"].__setitem__(2, 1), "row_ptr decreases"),
+    (lambda d: d["indices"].__setitem__(0, 9), "out of range"),
+    (lambda d: d["indices"].__setitem__(1, 0), "strictly increasing"),
+    (lambda d: d["data"].__setitem__(3, np.nan), "non-finite"),
+    (lambda d: d["cols"].__setitem__(0, 5), "rows*cols"),
+    (lambda d: d["vs"].__setitem__(4, 7), "label out of range"),
+    (lambda d: d["uw"].__setitem__(0, -1.0), "weights"),
+    (lambda d: d["ot"].__setitem__(1, np.inf), "weights"),
+])
+def test_create_rejects_malformed_inputs(lib, mutate, needle):
+    d = _tiny_inputs()
+    mutate(d)
+    st, msg = _create(lib, d)
+    assert st == -1 and needle in msg, (st, msg)
+
+
+def test_create_rejects_wide_rows_and_pool_sizes(lib):
+    d = _tiny_inputs()
+    d["rows"] = np.array([1], dtype=np.int32)
+    d["cols"] = np.array([8], dtype=np.int32)
+    d["N"] = 8
+    st, _ = _create(lib, d, k_max=0)
+    assert st == -1
+    st, _ = _create(lib, d, k_max=65)
+    assert st == -1
+    d["cols"] = np.array([40], dtype=np.int32)
+    d["N"] = 40
+    st, msg = _create(lib, d)
+    assert st == -1 and "[1, 32]" in msg
+
+
+def test_null_arguments(lib):
+    assert lib.dao_create(None, None, None, None, None, None, None) == -1
+    assert lib.dao_price(None, None, None, None) == -1
+    assert lib.dao_solve(None, 5, None, None) == -1
+    assert lib.dao_launch_count(None) == 0
