@@ -1,0 +1,382 @@
+"""Benchmark: milliseconds per 50-aperture column-generation DAO plan on one GB300.
+
+Workload: the prostate-shaped phantom (9 beams x 20x20 beamlets, 200x120x60 grid
+of 2.5 mm voxels, unspecified tissue down-sampled 2x2x2), seeded and synthetic.
+A step is one whole plan from an empty pool: 50 rounds of D^T SpMV pricing,
+aperture column and projected-Newton master solve.  Inputs are resident in HBM
+when the timed region starts; L2 is flushed (a 256 MiB write) before every step
+and the flush is outside the per-step events.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on
+the host cores instead, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import phantom  # noqa: E402
+
+K_PLAN = 50
+WORKLOAD = "prostate-shaped FP32: 9 beams x 20x20 beamlets, 200x120x60 grid @2.5 mm, 50 apertures"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--config", choices=["prostate", "tiny", "hn"], default="prostate")
+    p.add_argument("--apertures", type=int, default=K_PLAN)
+    p.add_argument("--skip-cpu", action="store_true")
+    p.add_argument("--skip-e2e", action="store_true")
+    p.add_argument("--skip-spmv", action="store_true")
+    p.add_argument("--no-clocks", action="store_true")
+    return p.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _case(name):
+    return phantom.make_case(phantom.CONFIGS[name]())
+
+
+def _workload_config(case, name, extra=None):
+    cfg = {"workload": WORKLOAD if name == "prostate" else name, "voxels": case.n_voxels,
+           "beamlets": case.n_beamlets, "beams": case.n_beams, "nnz": case.nnz, "apertures": K_PLAN,
+           "seed": case.spec.seed, "l2": "flushed before each step (256 MiB write)", "parallelism": "replicas"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int, enabled: bool = True):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        if enabled:
+            try:
+                os.makedirs(os.path.dirname(self.path), exist_ok=True)
+                self.f = open(self.path, "w")
+                self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.QUERY}",
+                                              "--format=csv,noheader,nounits", "-lms", "200"],
+                                             stdout=self.f, stderr=subprocess.DEVNULL)
+            except Exception:
+                self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per kernel class (what the method must move)
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(case, plan, kc, launches):
+    V, N, B, nnz = case.n_voxels, case.n_beamlets, case.n_beams, case.nnz
+    if kc == "dt":        # a2: D^T values + voxel indices, row pointers, pi once, w out
+        return launches * (nnz * 8 + (N + 1) * 4 + V * 4 + N * 4)
+    if kc == "dose":      # a1: D values + column indices, row pointers, x once, z out, labels
+        return launches * (nnz * 8 + (V + 1) * 4 + N * 4 + V * 4 + V)
+    if kc == "column":    # a4: beam b's entries (nnz/B on average), two segment bounds per row, column out
+        return launches * (nnz / B * 8 + V * 8 + V * 4)
+    if kc == "master_pass":  # a5: slab columns read once per pass + labels; final passes also write z, pi
+        ev, _, _ = plan.master_stats()
+        total = V * 9.0                                  # the pass at K = 0 after reset
+        for k, e in enumerate(ev):                       # pool size k + 1
+            total += (e + 1) * (V * 4.0 * (k + 1) + V) + 8.0 * V
+        return total
+    return None
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        return json.load(open(path)).get(kernel)
+    except Exception:
+        return None
+
+
+def _peaks():
+    try:
+        m = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing
+# ---------------------------------------------------------------------------
+
+def oracle_plan_seconds(case, k):
+    import oracle
+    t = time.perf_counter()
+    oracle.column_generation(case, k)
+    return time.perf_counter() - t
+
+
+def _cpu_threads():
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count() or 1
+
+
+def run_reference(a):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    case = _case(a.config)
+    cores = _cpu_threads()
+    # a step is the full plan when the whole run fits in about four minutes, else
+    # the first k CG rounds scaled by 50/k (this under-states the oracle's time:
+    # later rounds have larger master problems)
+    probe = oracle_plan_seconds(case, 5)
+    est_full = probe * 50.0          # the 50-round plan costs about 50x its first 5 rounds (measured)
+    k_s = a.apertures if est_full * (a.steps + 1) <= 240 else max(2, int(a.apertures * 240 / (est_full * (a.steps + 1))))
+    for _ in range(a.warmup):
+        oracle_plan_seconds(case, 2)
+    times = [oracle_plan_seconds(case, k_s) * (a.apertures / k_s) for _ in range(a.steps)]
+    ms = 1e3 * float(np.mean(times))
+    sample = (f"full {a.apertures}-aperture plan per step" if k_s == a.apertures else
+              f"first {k_s} of {a.apertures} CG rounds per step, scaled x{a.apertures / k_s:.2f}")
+    out = {"impl": "reference", "metric": f"ms per {a.apertures}-aperture plan", "value": ms, "unit": "ms",
+           "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": _workload_config(case, a.config),
+           "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(a):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_1003_5402_gb300 import Plan, build
+    build.build()
+    case = _case(a.config)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    plan = Plan(case, device=dev, stream=stream.cuda_stream)
+    for _ in range(a.warmup):
+        plan.reset()
+        plan.solve(a.apertures)
+    barrier()
+    sampler = ClockSampler(dev, enabled=not a.no_clocks)
+    l0 = plan.launch_count()
+    evs = []
+    t_host = time.perf_counter()
+    for _ in range(a.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.reset()
+        st, n, trace = plan.solve(a.apertures)
+        e1.record(stream)
+        evs.append((e0, e1))
+    barrier()
+    t_host = time.perf_counter() - t_host
+    clocks = sampler.stop()
+    launches = plan.launch_count() - l0
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    total_ms = float(sum(step_ms))
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    F_final = float(trace[n - 1]) if n > 0 else None
+    ev, stt, kkt = plan.master_stats()
+
+    # kernel-class breakdown: one more plan with host-driven launches bracketed by events
+    plan.profile_enable(True)
+    plan.reset()
+    plan.solve(a.apertures)
+    prof = {kc: plan.profile_read(kc) for kc in ("dose", "dt", "price", "column", "master_pass", "master_reduce",
+                                                 "master_step")}
+    plan.profile_enable(False)
+    kernel_ms = {kc: round(ms, 4) for kc, (nl, ms) in prof.items()}
+    kernel_launches = {kc: nl for kc, (nl, ms) in prof.items()}
+
+    # roofline of the dominant kernel (the fused master pass): every launch of the
+    # plan re-timed back to back with CUDA events at its own pool size, weighted by
+    # the plan's evaluations at that size; bytes are the slab columns + labels
+    hbm_peak, peak_kind = _peaks()
+    V = case.n_voxels
+    w_sum = t_sum = b_sum = 0.0
+    for k in range(1, n + 1):
+        cnt = int(ev[k - 1]) + 1                          # evaluations + the final pass
+        us = plan.k_time("master_pass", k, 10)
+        w_sum += cnt
+        t_sum += cnt * us
+        b_sum += cnt * (V * 4.0 * k + V)
+    us_avg = t_sum / w_sum
+    bytes_avg = b_sum / w_sum
+    achieved = bytes_avg / (us_avg * 1e-6) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_master_pass", "achieved": round(achieved, 1), "peak": hbm_peak,
+            "unit": "GB/s", "frac": round(achieved / hbm_peak, 4), "peak_kind": peak_kind,
+            "traffic": _traffic("k_master_pass"), "bytes_per_launch": round(bytes_avg),
+            "us_per_launch": round(us_avg, 3), "launches_per_plan": int(w_sum),
+            "timing": "CUDA events around back-to-back launches at each pool size of the timed plan"}
+
+    # SpMV bandwidth, L2 cold: a1 and a2 alone, 20 runs each
+    spmv = None
+    if not a.skip_spmv:
+        spmv = {}
+        x = torch.rand(case.n_beamlets, device="cuda")
+        z = torch.empty(case.n_voxels, device="cuda")
+        g = torch.empty_like(z)
+        pi = torch.randn(case.n_voxels, device="cuda")
+        w = torch.empty(case.n_beamlets, device="cuda")
+        for kc, fn in (("dose", lambda: plan.k_dose(x, z, g, objective=False)),
+                       ("dt", lambda: plan.k_beamlet_prices(pi, w))):
+            for _ in range(3):
+                fn()
+            per = []
+            for _ in range(20):
+                flush.zero_()
+                plan.profile_enable(True)
+                fn()
+                nl, ms = plan.profile_read(kc)
+                per.append(ms)
+            plan.profile_enable(False)
+            byt = algorithmic_bytes(case, plan, kc, 1)
+            med = statistics.median(per)
+            spmv[kc] = {"us": round(med * 1e3, 2), "gbs": round(byt / (med * 1e-3) / 1e9, 1),
+                        "frac_of_hbm": round(byt / (med * 1e-3) / 1e9 / hbm_peak, 4), "bytes": byt}
+
+    # end to end through the public API from host buffers
+    e2e = None
+    if not a.skip_e2e:
+        n_e2e = max(1, min(a.steps, 3))
+        h2d = (case.indptr.nbytes + case.indices.nbytes + case.data.nbytes + case.rows.nbytes + case.cols.nbytes
+               + case.voxel_struct.nbytes + case.is_target.nbytes + 4 * case.under_w.nbytes)
+        d2h = case.n_voxels * 4 + 8 + a.apertures * 8
+        times = []
+        for _ in range(n_e2e + 1):
+            flush.zero_()
+            barrier()
+            t0 = time.perf_counter()
+            with Plan(case, device=dev, stream=stream.cuda_stream) as p2:
+                p2.solve(a.apertures)
+                dose, F = p2.dose()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        times = times[1:]
+        e2e_ms = 1e3 * float(np.mean(times))
+        if ws > 1:
+            t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": round(e2e_ms / ws, 3), "unit": "ms", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
+               "includes": "dao_create (validation, D^T build, upload) + dao_solve + dao_dose to host"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not a.skip_cpu:
+        secs = oracle_plan_seconds(case, a.apertures)
+        cpu = {"value": round(secs * 1e3, 1), "unit": "ms", "cores": _cpu_threads(), "kind": "oracle",
+               "sample": f"one full {a.apertures}-aperture plan of the same workload (FP64 numpy/scipy, BLAS threads)"}
+
+    plan.close()
+    if rank == 0:
+        ms_per_step = total_ms / a.steps
+        lat = sorted(step_ms)
+        out = {
+            "metric": f"ms per {a.apertures}-aperture plan", "value": round(total_ms / (a.steps * ws), 4),
+            "unit": "ms", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": _workload_config(case, a.config),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
+            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
+                           "p99": round(float(np.percentile(lat, 99)), 4)},
+            "spmv": spmv, "kernel_ms_host_driven_plan": kernel_ms, "kernel_launches_host_driven_plan": kernel_launches,
+            "objective_final": F_final, "apertures_done": int(n), "master_evals": int(np.sum(ev)),
+            "host_wall_s": round(t_host, 3), "device": torch.cuda.get_device_name(dev),
+        }
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -94,12 +94,15 @@ enum { DAO_PREC_FP32 = 0, DAO_PREC_FP16 = 1, DAO_PREC_BF16 = 2 };
 /* Solver options; dao_options_default() fills every field. */
 typedef struct dao_options {
     int32_t k_max;             /* aperture pool capacity, 1..64 (default 64) */
-    int32_t max_master_iters;  /* projected-Newton iterations per master solve (default 100) */
-    double master_tol;         /* stop at ||y - P(y - g)||_inf <= master_tol * max|g(start)| (1e-6) */
+    int32_t max_master_iters;  /* projected-Newton iterations per master solve (default 50) */
+    double master_tol;         /* stop when every |y_k - P(y_k - g_k)| <= master_tol * max|g(start)|
+                                * + 64 u sum_j |S_jk pi_j| (u = 2^-24: FP32 rounding of g) (1e-6) */
     double price_tol;          /* optimal when reduced cost >= -price_tol * max(D) * ||grad F(0)||_1 (1e-7) */
     int32_t precision;         /* DAO_PREC_FP32 (others reserved) */
     int32_t device;            /* CUDA device ordinal (default 0) */
     void* stream;              /* cudaStream_t to run on; NULL = a stream owned by the context */
+    int32_t use_graphs;        /* 1 (default): dao_solve runs each round as one CUDA graph with the master
+                                * loop as a device-side while node; 0: host-driven launches */
 } dao_options;
 
 typedef struct dao_ctx dao_ctx;
@@ -187,18 +190,29 @@ dao_status dao_k_aperture_column(dao_ctx* ctx, int32_t beam, const int32_t* leaf
 /* Current pi = grad F(z) and z of the last master solution (device outputs). */
 dao_status dao_k_state(dao_ctx* ctx, float* z, float* pi);
 
+/* Average device time in microseconds (*us_per_launch, host) of `reps`
+ * back-to-back launches of one kernel class on the context's current data,
+ * between two CUDA events on the context's stream: DAO_KC_MASTER_PASS (the
+ * slab pass at pool size K, 1 <= K <= current pool size), DAO_KC_MASTER_HESS
+ * (the curvature kernel on the last pass's active voxels), DAO_KC_DT,
+ * DAO_KC_DOSE, DAO_KC_COLUMN (first aperture of the pool), DAO_KC_PRICE.
+ * Results and the pool are unchanged; scratch buffers are overwritten. */
+dao_status dao_k_time(dao_ctx* ctx, int32_t kc, int32_t K, int32_t reps, double* us_per_launch);
+
 /* ---- instrumentation: per-kernel-class CUDA-event timing on the context's
- * stream (off by default). ---- */
+ * stream (off by default).  While it is on, dao_solve uses host-driven
+ * launches so that every kernel can be bracketed by events. ---- */
 enum {
     DAO_KC_DOSE = 0,           /* a1 dose SpMV + epilogue */
     DAO_KC_DT = 1,             /* a2 transposed SpMV */
     DAO_KC_PRICE = 2,          /* a3 pricing (row scan + beam reduction) */
     DAO_KC_COLUMN = 3,         /* a4 aperture column */
-    DAO_KC_MASTER_PASS = 4,    /* a5 fused slab pass (z, F, g, H partials) */
+    DAO_KC_MASTER_PASS = 4,    /* a5 slab pass: z, pi, h, F and the active-voxel list */
     DAO_KC_MASTER_REDUCE = 5,  /* a5 partial reduction */
     DAO_KC_MASTER_STEP = 6,    /* a5 Newton step / line search control */
-    DAO_KC_OTHER = 7,
-    DAO_KC_COUNT = 8
+    DAO_KC_MASTER_HESS = 7,    /* a5 curvature matrix and gradient over the active voxels */
+    DAO_KC_OTHER = 8,
+    DAO_KC_COUNT = 9
 };
 dao_status dao_profile_enable(dao_ctx* ctx, int32_t enable);
 /* launches, summed device milliseconds and the kernel launches counted for

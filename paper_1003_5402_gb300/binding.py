@@ -20,7 +20,7 @@ DAO_OK, DAO_OPTIMAL, DAO_DUPLICATE = 0, 1, 2
 DAO_EINVAL, DAO_ENOMEM, DAO_ECUDA, DAO_ETIMEOUT, DAO_EBUSY, DAO_ESTATE = -1, -2, -3, -4, -5, -6
 DAO_PREC_FP32, DAO_PREC_FP16, DAO_PREC_BF16 = 0, 1, 2
 KC = {"dose": 0, "dt": 1, "price": 2, "column": 3, "master_pass": 4, "master_reduce": 5, "master_step": 6,
-      "other": 7}
+      "master_hess": 7, "other": 8}
 
 # every function declared in include/dao.h, with (restype, argtypes)
 _P = C.c_void_p
@@ -47,7 +47,8 @@ class dao_weights(C.Structure):
 
 class dao_options(C.Structure):
     _fields_ = [("k_max", C.c_int32), ("max_master_iters", C.c_int32), ("master_tol", C.c_double),
-                ("price_tol", C.c_double), ("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p)]
+                ("price_tol", C.c_double), ("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
+                ("use_graphs", C.c_int32)]
 
 
 SIGNATURES = {
@@ -68,6 +69,7 @@ SIGNATURES = {
     "dao_k_price": (C.c_int, [_P, _P, _I32P, _I32P, _F64P, _F64P, _I32P]),
     "dao_k_aperture_column": (C.c_int, [_P, C.c_int32, _I32P, _P]),
     "dao_k_state": (C.c_int, [_P, _P, _P]),
+    "dao_k_time": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _F64P]),
     "dao_profile_enable": (C.c_int, [_P, C.c_int32]),
     "dao_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), _F64P]),
     "dao_launch_count": (C.c_int64, [_P]),
@@ -277,6 +279,12 @@ class Plan:
 
     def k_state(self, z, pi):
         _check(load().dao_k_state(self.h, _dev(z, "float32"), _dev(pi, "float32")), "dao_k_state")
+
+    def k_time(self, kc: str, K: int = 0, reps: int = 20) -> float:
+        """Average microseconds per launch of one kernel class (dao_k_time)."""
+        us = C.c_double()
+        _check(load().dao_k_time(self.h, KC[kc], int(K), int(reps), C.byref(us)), "dao_k_time")
+        return us.value
 
     def profile_enable(self, on: bool = True):
         _check(load().dao_profile_enable(self.h, int(on)), "dao_profile_enable")

@@ -65,6 +65,10 @@ struct dao_ctx {
     int4* row_info = nullptr;        // per MLC row: beam, first beamlet, columns, row within beam
     int* beam_row0_d = nullptr;
     int4* binfo = nullptr;           // per beamlet: beam, row, column
+    int* rows_d = nullptr;           // per beam: MLC rows, beamlets per row, first beamlet
+    int* cols_d = nullptr;
+    int* beam_off_d = nullptr;
+    int max_nb = 0;                  // largest rows * cols of a beam
 
     // column-generation state
     int K = 0, K_cap = 0, ld = 0;
@@ -82,13 +86,16 @@ struct dao_ctx {
     int2* row_lr = nullptr;
     PriceDev* price = nullptr;
     MasterBuffers mb;
+    CGDev* cg = nullptr;             // device-side state of graph-driven solves
+    std::vector<cudaGraph_t> round_graph;       // per pool size K: one column-generation round
+    std::vector<cudaGraphExec_t> round_exec;
     double* F_part = nullptr;
     int F_blocks = 0;
     double* F_dev = nullptr;
 
     // pinned staging
     unsigned char* pinned = nullptr;
-    size_t off_small = 0, off_rows = 0, off_mask = 0, off_master = 0, pinned_bytes = 0;
+    size_t off_small = 0, off_rows = 0, off_mask = 0, off_master = 0, off_cg = 0, pinned_bytes = 0;
 
     // per master solve: evaluations (fused passes), final status, KKT residual / max|g(start)|
     std::vector<int> stat_evals, stat_status;
@@ -359,13 +366,47 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     DAO_TRY(upload(c, &c->row_info, ri.data(), ri.size()));
     DAO_TRY(upload(c, &c->beam_row0_d, c->beam_row0.data(), c->beam_row0.size()));
     DAO_TRY(upload(c, &c->binfo, bi.data(), bi.size()));
+    DAO_TRY(upload(c, &c->rows_d, c->rows.data(), c->rows.size()));
+    DAO_TRY(upload(c, &c->cols_d, c->cols.data(), c->cols.size()));
+    DAO_TRY(upload(c, &c->beam_off_d, c->beam_off.data(), c->beam_off.size()));
+    return DAO_OK;
+}
+
+// 2-D tensor maps over the voxel-major slab (KROW floats per voxel row), one per
+// tile row width: box = (width, MASTER_TILE) starting at column 0.
+dao_status make_tensor_maps(dao_ctx* c) {
+    typedef CUresult (*encode_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    DAO_CU(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (fn == nullptr || q != cudaDriverEntryPointSuccess) return fail(DAO_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    encode_fn encode = reinterpret_cast<encode_fn>(fn);
+    std::memset(c->mb.tmap, 0, sizeof(c->mb.tmap));
+    for (int k = 0; k <= KMAX; ++k) {
+        const int kw = master_kw(k);
+        if (c->mb.tmap_ready[kw / 4]) continue;
+        const cuuint64_t dims[2] = {(cuuint64_t)KROW, (cuuint64_t)c->ld};
+        const cuuint64_t strides[1] = {(cuuint64_t)KROW * sizeof(float)};
+        const cuuint32_t box[2] = {(cuuint32_t)kw, (cuuint32_t)MASTER_TILE};
+        const cuuint32_t estr[2] = {1, 1};
+        CUresult r = encode(&c->mb.tmap[kw / 4], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->slab, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(DAO_ECUDA, "cuTensorMapEncodeTiled failed with " + std::to_string((int)r));
+        c->mb.tmap_ready[kw / 4] = true;
+    }
     return DAO_OK;
 }
 
 dao_status alloc_state(dao_ctx* c) {
     c->K_cap = c->opt.k_max;
-    c->ld = (c->V + 63) / 64 * 64;
-    DAO_TRY(c->dalloc(&c->slab, (size_t)c->K_cap * c->ld));
+    c->mb.n_tiles = (c->V + MASTER_TILE - 1) / MASTER_TILE;
+    c->ld = c->mb.n_tiles * MASTER_TILE;  // voxel rows of the slab, zero padded to whole tiles
+    DAO_TRY(c->dalloc(&c->slab, (size_t)c->ld * KROW));
+    DAO_CU(cudaMemset(c->slab, 0, (size_t)c->ld * KROW * sizeof(float)));
+    DAO_TRY(make_tensor_maps(c));
     DAO_TRY(c->dalloc(&c->ap_beam, c->K_cap));
     DAO_TRY(c->dalloc(&c->ap_lr, (size_t)c->K_cap * 2 * c->max_rows));
     DAO_TRY(c->dalloc(&c->z, c->V));
@@ -376,14 +417,25 @@ dao_status alloc_state(dao_ctx* c) {
     int nbmax = 0;
     for (int b = 0; b < c->B; ++b) nbmax = std::max(nbmax, c->rows[b] * c->cols[b]);
     DAO_TRY(c->dalloc(&c->mask, nbmax));
+    c->max_nb = nbmax;
+    DAO_TRY(c->dalloc(&c->cg, 1));
+    DAO_CU(cudaMemset(c->cg, 0, sizeof(CGDev)));
+    c->round_graph.assign(c->K_cap + 1, nullptr);
+    c->round_exec.assign(c->K_cap + 1, nullptr);
     DAO_TRY(c->dalloc(&c->row_v, c->R_tot));
     DAO_TRY(c->dalloc(&c->row_lr, c->R_tot));
     DAO_TRY(c->dalloc(&c->price, 1));
-    c->mb.G = std::max(1, std::min(2 * c->num_sms, (c->V + MASTER_TILE - 1) / MASTER_TILE));
+    for (int k = 0; k <= KMAX; ++k) c->mb.grid[k] = master_grid(c->V, c->num_sms, k);
+    c->mb.GH = master_hess_grid(c->num_sms);
     DAO_TRY(c->dalloc(&c->mb.st, 1));
-    DAO_TRY(c->dalloc(&c->mb.H_part, (size_t)KMAX * KMAX * c->mb.G));
-    DAO_TRY(c->dalloc(&c->mb.g_part, (size_t)KMAX * c->mb.G));
-    DAO_TRY(c->dalloc(&c->mb.F_part, c->mb.G));
+    DAO_TRY(c->dalloc(&c->mb.act_rows, (size_t)c->ld * KROW));
+    DAO_TRY(c->dalloc(&c->mb.act_hp, (size_t)c->ld));
+    DAO_TRY(c->dalloc(&c->mb.act_count, (size_t)c->mb.n_tiles));
+    DAO_CU(cudaMemset(c->mb.act_count, 0, (size_t)c->mb.n_tiles * sizeof(int)));
+    DAO_TRY(c->dalloc(&c->mb.H_part, (size_t)KMAX * (KMAX + 1) / 2 * c->mb.GH));
+    DAO_TRY(c->dalloc(&c->mb.g_part, (size_t)KMAX * c->mb.GH));
+    DAO_TRY(c->dalloc(&c->mb.gn_part, (size_t)KMAX * c->mb.GH));
+    DAO_TRY(c->dalloc(&c->mb.F_part, (size_t)master_grid_max(c->num_sms)));
     c->F_blocks = dose_grid(c->V, c->num_sms);
     DAO_TRY(c->dalloc(&c->F_part, c->F_blocks));
     DAO_TRY(c->dalloc(&c->F_dev, 1));
@@ -394,7 +446,8 @@ dao_status alloc_state(dao_ctx* c) {
     c->off_mask = c->off_rows + round4((int64_t)c->R_tot * 2) * sizeof(int);
     c->off_master = round4(c->off_mask + (size_t)nbmax * sizeof(float) + 64) + 64;
     c->off_master = (c->off_master + 255) / 256 * 256;
-    c->pinned_bytes = c->off_master + sizeof(MasterDev);
+    c->off_cg = (c->off_master + sizeof(MasterDev) + 255) / 256 * 256;
+    c->pinned_bytes = c->off_cg + sizeof(CGDev);
     void* p = nullptr;
     DAO_CU(cudaMallocHost(&p, c->pinned_bytes));
     c->pinned = static_cast<unsigned char*>(p);
@@ -406,14 +459,14 @@ dao_status alloc_state(dao_ctx* c) {
 // pi = grad F(z) and z at the current pool's accepted intensities (final pass).
 dao_status refresh_state(dao_ctx* c) {
     c->prof_begin(DAO_KC_MASTER_PASS);
-    DAO_CU(launch_master_pass(c->slab, c->V, c->ld, c->K, c->mb, c->vstruct, c->tf, c->td, c->S, c->z, c->pi, 1,
-                              c->stream, &c->launches_i));
+    DAO_CU(launch_master_eval(c->mb, c->V, c->K, c->vstruct, c->tf, c->S, c->z, c->pi, PASS_FINAL, nullptr, c->stream,
+                              &c->launches_i));
     c->prof_end();
     return DAO_OK;
 }
 
 dao_status master_solve(dao_ctx* c, double* F_out) {
-    DAO_CU(launch_master_init(c->mb.st, c->K, c->stream, &c->launches_i));
+    DAO_CU(launch_master_init(c->mb.st, c->K, nullptr, 0, 0, c->stream, &c->launches_i));
     const int unroll = 4;
     const int max_passes = c->opt.max_master_iters + 80;
     int passes = 0;
@@ -422,14 +475,18 @@ dao_status master_solve(dao_ctx* c, double* F_out) {
     for (;;) {
         for (int u = 0; u < unroll; ++u) {
             c->prof_begin(DAO_KC_MASTER_PASS);
-            DAO_CU(launch_master_pass(c->slab, c->V, c->ld, c->K, c->mb, c->vstruct, c->tf, c->td, c->S, nullptr,
-                                      nullptr, 0, c->stream, &c->launches_i));
+            DAO_CU(launch_master_eval(c->mb, c->V, c->K, c->vstruct, c->tf, c->S, nullptr, nullptr, PASS_EVAL, nullptr,
+                                      c->stream, &c->launches_i));
+            c->prof_end();
+            c->prof_begin(DAO_KC_MASTER_HESS);
+            DAO_CU(launch_master_hess(c->mb, c->K, PASS_EVAL, c->stream, &c->launches_i));
             c->prof_end();
             c->prof_begin(DAO_KC_MASTER_REDUCE);
             DAO_CU(launch_master_reduce(c->K, c->mb, c->stream, &c->launches_i));
             c->prof_end();
             c->prof_begin(DAO_KC_MASTER_STEP);
-            DAO_CU(launch_master_step(c->mb, c->opt.max_master_iters, c->opt.master_tol, c->stream, &c->launches_i));
+            DAO_CU(launch_master_step(c->mb, c->opt.max_master_iters, c->opt.master_tol, 0, 0, c->stream,
+                                      &c->launches_i));
             c->prof_end();
         }
         passes += unroll;
@@ -439,6 +496,7 @@ dao_status master_solve(dao_ctx* c, double* F_out) {
         if (passes > max_passes) return fail(DAO_ETIMEOUT, "master problem did not stop within its evaluation cap");
     }
     DAO_TRY(refresh_state(c));
+    if (shadow->status == MASTER_ERROR) return fail(DAO_ETIMEOUT, "a slab tile copy did not complete");
     c->stat_evals.push_back(shadow->n_eval);
     c->stat_status.push_back(shadow->status);
     c->stat_kkt.push_back(shadow->res / (shadow->tol > 0 ? shadow->tol / c->opt.master_tol : 1.0));
@@ -450,8 +508,8 @@ dao_status master_solve(dao_ctx* c, double* F_out) {
 dao_status price_on_w(dao_ctx* c, const float* w, int32_t* beam, int32_t* leaf_lr, double* rc, double* row_best,
                       int32_t* row_lr_out) {
     c->prof_begin(DAO_KC_PRICE);
-    DAO_CU(launch_price(w, c->row_info, c->R_tot, c->beam_row0_d, c->B, c->row_v, c->row_lr, c->price, c->stream,
-                        &c->launches_i));
+    DAO_CU(launch_price(w, c->row_info, c->R_tot, c->beam_row0_d, c->B, c->row_v, c->row_lr, c->price, nullptr,
+                        c->stream, &c->launches_i));
     c->prof_end();
     PriceDev* pd = reinterpret_cast<PriceDev*>(c->pinned + c->off_small + 16);
     int* lr = reinterpret_cast<int*>(c->pinned + c->off_rows);
@@ -497,7 +555,7 @@ bool is_duplicate(const dao_ctx* c, int beam, const int32_t* lr) {
 }
 
 // form the new column (Eq. 2) into slab column K, record the aperture
-dao_status add_column(dao_ctx* c, int beam, const int32_t* lr, float* out) {
+dao_status add_column(dao_ctx* c, int beam, const int32_t* lr, float* out, int stride) {
     const int nb = c->rows[beam] * c->cols[beam];
     float* m = reinterpret_cast<float*>(c->pinned + c->off_mask);
     for (int i = 0; i < nb; ++i) m[i] = 0.f;
@@ -506,14 +564,14 @@ dao_status add_column(dao_ctx* c, int beam, const int32_t* lr, float* out) {
     DAO_CU(cudaMemcpyAsync(c->mask, m, sizeof(float) * nb, cudaMemcpyHostToDevice, c->stream));
     c->prof_begin(DAO_KC_COLUMN);
     DAO_CU(launch_column(c->D, c->seg + (size_t)beam * c->V, c->seg + (size_t)(beam + 1) * c->V, c->beam_off[beam],
-                         nb, c->mask, out, c->num_sms, c->stream, &c->launches_i));
+                         nb, c->mask, out, stride, c->num_sms, c->stream, &c->launches_i));
     c->prof_end();
     return DAO_OK;
 }
 
 dao_status add_aperture(dao_ctx* c, int beam, const int32_t* lr, double* F) {
     if (c->K >= c->K_cap) return fail(DAO_ESTATE, "aperture pool is full (k_max)");
-    DAO_TRY(add_column(c, beam, lr, c->slab + (size_t)c->K * c->ld));
+    DAO_TRY(add_column(c, beam, lr, c->slab + c->K, KROW));
     const int stride = 2 * c->max_rows;
     c->ap_beam_h.push_back(beam);
     c->ap_lr_h.resize((size_t)(c->K + 1) * stride, 0);
@@ -528,6 +586,139 @@ dao_status add_aperture(dao_ctx* c, int beam, const int32_t* lr, double* F) {
                            cudaMemcpyHostToDevice, c->stream));
     c->K += 1;
     return master_solve(c, F);
+}
+
+// ---- graph-driven column generation ---------------------------------------------
+
+// One round for pool size K as a CUDA graph: pricing (a2, a3), the device-side
+// commit of the priced aperture, its column (a4), the master problem (a5) as a
+// while node whose body is one evaluation, and the final pass.  Every node
+// becomes a no-op once an earlier round has stopped the solve, so rounds can be
+// queued without waiting on the host.
+dao_status build_round_graph(dao_ctx* c, int K) {
+    cudaGraph_t g = nullptr;
+    DAO_CU(cudaGraphCreate(&g, 0));
+    cudaStream_t cs = c->stream;
+    int n = 0;
+    const int* skip = &c->cg->done;
+    cudaError_t e = cudaSuccess;
+    cudaGraphConditionalHandle h = 0;
+    std::vector<cudaGraphNode_t> deps;
+    cudaGraphNode_t cnode = nullptr;
+    auto check = [&](cudaError_t x) {
+        if (e == cudaSuccess && x != cudaSuccess) e = x;
+    };
+    check(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    if (e == cudaSuccess) {
+        check(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        if (e == cudaSuccess) {
+            check(launch_dt(c->Dt, c->pi, c->w, skip, cs, &n));
+            check(launch_price(c->w, c->row_info, c->R_tot, c->beam_row0_d, c->B, c->row_v, c->row_lr, c->price, skip,
+                               cs, &n));
+            check(launch_commit(c->price, c->row_lr, c->beam_row0_d, c->rows_d, c->cols_d, c->tau, K,
+                                2 * c->max_rows, c->ap_beam, c->ap_lr, c->mask, c->cg, cs, &n));
+            check(launch_column_dev(c->D, c->seg, c->ap_beam, K, c->beam_off_d, c->rows_d, c->cols_d, c->max_nb,
+                                    c->mask, c->slab + (K - 1), KROW, c->cg, c->num_sms, cs, &n));
+            check(launch_master_init(c->mb.st, K, skip, h, 1, cs, &n));
+            cudaStreamCaptureStatus cst;
+            const cudaGraphNode_t* d = nullptr;
+            size_t nd = 0;
+            check(cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &d, nullptr, &nd));
+            if (e == cudaSuccess) deps.assign(d, d + nd);
+            cudaGraph_t out = nullptr;
+            check(cudaStreamEndCapture(cs, &out));
+        }
+    }
+    if (e == cudaSuccess) {
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        check(cudaGraphAddNode(&cnode, g, deps.data(), nullptr, deps.size(), &cp));
+        if (e == cudaSuccess) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            check(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            if (e == cudaSuccess) {
+                check(launch_master_eval(c->mb, c->V, K, c->vstruct, c->tf, c->S, nullptr, nullptr, PASS_EVAL,
+                                         nullptr, cs, &n));
+                check(launch_master_hess(c->mb, K, PASS_EVAL, cs, &n));
+                check(launch_master_reduce(K, c->mb, cs, &n));
+                check(launch_master_step(c->mb, c->opt.max_master_iters, c->opt.master_tol, h, 1, cs, &n));
+                cudaGraph_t out = nullptr;
+                check(cudaStreamEndCapture(cs, &out));
+            }
+        }
+    }
+    if (e == cudaSuccess) {
+        check(cudaStreamBeginCaptureToGraph(cs, g, &cnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+        if (e == cudaSuccess) {
+            check(launch_master_eval(c->mb, c->V, K, c->vstruct, c->tf, c->S, c->z, c->pi, PASS_FINAL, skip, cs, &n));
+            check(launch_cg_record(c->mb.st, c->cg, K, cs, &n));
+            cudaGraph_t out = nullptr;
+            check(cudaStreamEndCapture(cs, &out));
+        }
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (e == cudaSuccess) check(cudaGraphInstantiate(&ex, g, 0));
+    if (e != cudaSuccess) {
+        cudaStreamCaptureStatus cst;
+        if (cudaStreamIsCapturing(cs, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(cs, &junk);
+        }
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return fail(DAO_ECUDA, std::string("building the round graph: ") + cudaGetErrorString(e));
+    }
+    c->round_graph[K] = g;
+    c->round_exec[K] = ex;
+    return DAO_OK;
+}
+
+// Rounds K_old+1 .. K_new queued back to back; one synchronisation at the end.
+dao_status solve_graph(dao_ctx* c, int n_apertures, int32_t* n_done, double* trace, dao_status* result) {
+    const int K0 = c->K;
+    const int K1 = std::min(c->K_cap, K0 + n_apertures);
+    for (int k = K0 + 1; k <= K1; ++k)
+        if (c->round_exec[k] == nullptr) DAO_TRY(build_round_graph(c, k));
+    CGDev* h = reinterpret_cast<CGDev*>(c->pinned + c->off_cg);
+    h->K = K0;
+    h->done = 0;
+    DAO_CU(cudaMemcpyAsync(c->cg, h, 2 * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    for (int k = K0 + 1; k <= K1; ++k) DAO_CU(cudaGraphLaunch(c->round_exec[k], c->stream));
+    DAO_CU(cudaMemcpyAsync(h, c->cg, sizeof(CGDev), cudaMemcpyDeviceToHost, c->stream));
+    DAO_TRY(sync(c));
+    const int K = h->K;
+    const int stride = 2 * c->max_rows;
+    if (K > K0) {
+        c->ap_beam_h.resize(K);
+        c->ap_lr_h.resize((size_t)K * stride);
+        DAO_CU(cudaMemcpy(c->ap_beam_h.data() + K0, c->ap_beam + K0, sizeof(int) * (K - K0), cudaMemcpyDeviceToHost));
+        DAO_CU(cudaMemcpy(c->ap_lr_h.data() + (size_t)K0 * stride, c->ap_lr + (size_t)K0 * stride,
+                          sizeof(int) * (size_t)(K - K0) * stride, cudaMemcpyDeviceToHost));
+        for (int k = K0; k < K; ++k) {  // rows beyond the beam's own count are not part of the aperture
+            const int b = c->ap_beam_h[k];
+            for (int r = c->rows[b]; r < c->max_rows; ++r) {
+                c->ap_lr_h[(size_t)k * stride + 2 * r] = 0;
+                c->ap_lr_h[(size_t)k * stride + 2 * r + 1] = 0;
+            }
+        }
+    }
+    // kernels the graphs ran: 8 per round plus pass, reduce and step per evaluation
+    c->launches_i += 8 * (K - K0) + (K < K1 ? 5 : 0);
+    for (int k = K0; k < K; ++k) {
+        c->launches_i += 4 * h->evals[k];
+        c->stat_evals.push_back(h->evals[k]);
+        c->stat_status.push_back(h->status[k]);
+        c->stat_kkt.push_back(h->res[k] / (h->tol[k] > 0 ? h->tol[k] / c->opt.master_tol : 1.0));
+        if (trace) trace[k - K0] = h->trace[k];
+    }
+    c->K = K;
+    if (n_done) *n_done = K;
+    *result = h->done == 1 ? DAO_OPTIMAL : h->done == 2 ? DAO_DUPLICATE : DAO_OK;
+    if (*result == DAO_OK && K0 + n_apertures > c->K_cap) *result = fail(DAO_ESTATE, "aperture pool is full (k_max)");
+    return DAO_OK;
 }
 
 dao_status reset_state(dao_ctx* c) {
@@ -552,12 +743,13 @@ extern "C" {
 void dao_options_default(dao_options* opt) {
     if (!opt) return;
     opt->k_max = KMAX;
-    opt->max_master_iters = 100;
+    opt->max_master_iters = 50;
     opt->master_tol = 1e-6;
     opt->price_tol = 1e-7;
     opt->precision = DAO_PREC_FP32;
     opt->device = 0;
     opt->stream = nullptr;
+    opt->use_graphs = 1;
 }
 
 const char* dao_last_error(void) { return g_err.c_str(); }
@@ -613,6 +805,10 @@ void dao_destroy(dao_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    for (cudaGraphExec_t ex : c->round_exec)
+        if (ex) cudaGraphExecDestroy(ex);
+    for (cudaGraph_t g : c->round_graph)
+        if (g) cudaGraphDestroy(g);
     for (void* p : c->dev_allocs) cudaFree(p);
     for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
     if (c->pinned) cudaFreeHost(c->pinned);
@@ -643,7 +839,7 @@ dao_status dao_sizes(const dao_ctx* c, int32_t* V, int32_t* N, int32_t* B, int32
 dao_status dao_price(dao_ctx* c, int32_t* beam, int32_t* leaf_lr, double* rc) {
     DAO_TRY(check_ctx(c));
     c->prof_begin(DAO_KC_DT);
-    DAO_CU(launch_dt(c->Dt, c->pi, c->w, c->stream, &c->launches_i));
+    DAO_CU(launch_dt(c->Dt, c->pi, c->w, nullptr, c->stream, &c->launches_i));
     c->prof_end();
     double r = 0.0;
     dao_status st = price_on_w(c, c->w, beam, leaf_lr, &r, nullptr, nullptr);
@@ -664,6 +860,13 @@ dao_status dao_add_aperture(dao_ctx* c, int32_t beam, const int32_t* leaf_lr, do
 dao_status dao_solve(dao_ctx* c, int32_t n_apertures, int32_t* n_done, double* trace) {
     DAO_TRY(check_ctx(c));
     if (n_apertures < 0) return fail(DAO_EINVAL, "negative aperture count");
+    if (c->opt.use_graphs && !c->prof_on) {
+        if (c->K >= c->K_cap && n_apertures > 0) return fail(DAO_ESTATE, "aperture pool is full (k_max)");
+        dao_status result = DAO_OK;
+        dao_status st = solve_graph(c, n_apertures, n_done, trace, &result);
+        c->count_launches();
+        return st != DAO_OK ? st : result;
+    }
     std::vector<int32_t> lr(2 * c->max_rows);
     dao_status result = DAO_OK;
     for (int k = 0; k < n_apertures; ++k) {
@@ -672,7 +875,7 @@ dao_status dao_solve(dao_ctx* c, int32_t n_apertures, int32_t* n_done, double* t
             break;
         }
         c->prof_begin(DAO_KC_DT);
-        DAO_CU(launch_dt(c->Dt, c->pi, c->w, c->stream, &c->launches_i));
+        DAO_CU(launch_dt(c->Dt, c->pi, c->w, nullptr, c->stream, &c->launches_i));
         c->prof_end();
         int32_t beam = 0;
         double rc = 0.0;
@@ -752,7 +955,7 @@ dao_status dao_k_beamlet_prices(dao_ctx* c, const float* pi, float* w) {
     DAO_TRY(check_ctx(c));
     if (!pi || !w) return fail(DAO_EINVAL, "null vector");
     c->prof_begin(DAO_KC_DT);
-    DAO_CU(launch_dt(c->Dt, pi, w, c->stream, &c->launches_i));
+    DAO_CU(launch_dt(c->Dt, pi, w, nullptr, c->stream, &c->launches_i));
     c->prof_end();
     DAO_TRY(sync(c));
     c->count_launches();
@@ -775,7 +978,7 @@ dao_status dao_k_aperture_column(dao_ctx* c, int32_t beam, const int32_t* leaf_l
     DAO_TRY(check_ctx(c));
     DAO_TRY(validate_aperture(c, beam, leaf_lr));
     if (!out) return fail(DAO_EINVAL, "null vector");
-    DAO_TRY(add_column(c, beam, leaf_lr, out));
+    DAO_TRY(add_column(c, beam, leaf_lr, out, 1));
     DAO_TRY(sync(c));
     c->count_launches();
     return DAO_OK;
@@ -786,6 +989,60 @@ dao_status dao_k_state(dao_ctx* c, float* z, float* pi) {
     if (z) DAO_CU(cudaMemcpyAsync(z, c->z, sizeof(float) * c->V, cudaMemcpyDeviceToDevice, c->stream));
     if (pi) DAO_CU(cudaMemcpyAsync(pi, c->pi, sizeof(float) * c->V, cudaMemcpyDeviceToDevice, c->stream));
     DAO_TRY(sync(c));
+    return DAO_OK;
+}
+
+dao_status dao_k_time(dao_ctx* c, int32_t kc, int32_t K, int32_t reps, double* us_per_launch) {
+    DAO_TRY(check_ctx(c));
+    if (reps < 1 || !us_per_launch) return fail(DAO_EINVAL, "reps must be >= 1 and the output non-null");
+    if ((kc == DAO_KC_MASTER_PASS || kc == DAO_KC_MASTER_HESS) && (K < 1 || K > c->K))
+        return fail(DAO_EINVAL, "master kernel timing needs 1 <= K <= the current pool size");
+    if (kc == DAO_KC_COLUMN && c->K < 1) return fail(DAO_EINVAL, "column timing needs an aperture in the pool");
+    if (kc != DAO_KC_MASTER_PASS && kc != DAO_KC_MASTER_HESS && kc != DAO_KC_DT && kc != DAO_KC_DOSE &&
+        kc != DAO_KC_COLUMN && kc != DAO_KC_PRICE)
+        return fail(DAO_EINVAL, "kernel class cannot be timed on its own");
+    cudaEvent_t e0 = c->event(), e1 = c->event();
+    if (!e0 || !e1) return fail(DAO_ECUDA, "cudaEventCreate failed");
+    int n = 0;
+    DAO_TRY(sync(c));
+    DAO_CU(cudaEventRecord(e0, c->stream));
+    for (int r = 0; r < reps; ++r) {
+        switch (kc) {
+            case DAO_KC_MASTER_PASS:
+                DAO_CU(launch_master_eval(c->mb, c->V, K, c->vstruct, c->tf, c->S, nullptr, nullptr, PASS_TIMING,
+                                          nullptr, c->stream, &n));
+                break;
+            case DAO_KC_MASTER_HESS:
+                DAO_CU(launch_master_hess(c->mb, K, PASS_TIMING, c->stream, &n));
+                break;
+            case DAO_KC_DT:
+                DAO_CU(launch_dt(c->Dt, c->pi, c->w, nullptr, c->stream, &n));
+                break;
+            case DAO_KC_DOSE:
+                DAO_CU(launch_dose(c->D, c->x, c->vstruct, c->tf, c->td, c->S, c->dose, nullptr, nullptr, 0, nullptr,
+                                   c->num_sms, c->stream, &n));
+                break;
+            case DAO_KC_COLUMN: {
+                const int b = c->ap_beam_h[0];
+                DAO_CU(launch_column(c->D, c->seg + (size_t)b * c->V, c->seg + (size_t)(b + 1) * c->V,
+                                     c->beam_off[b], c->rows[b] * c->cols[b], c->mask, c->dose, 1, c->num_sms,
+                                     c->stream, &n));
+                break;
+            }
+            case DAO_KC_PRICE:
+                DAO_CU(launch_price(c->w, c->row_info, c->R_tot, c->beam_row0_d, c->B, c->row_v, c->row_lr, c->price,
+                                    nullptr, c->stream, &n));
+                break;
+        }
+    }
+    DAO_CU(cudaEventRecord(e1, c->stream));
+    DAO_TRY(sync(c));
+    float ms = 0.f;
+    DAO_CU(cudaEventElapsedTime(&ms, e0, e1));
+    c->ev_used -= 2;
+    c->launches_i += n;
+    c->count_launches();
+    *us_per_launch = 1e3 * ms / reps;
     return DAO_OK;
 }
 

@@ -1,6 +1,7 @@
 // Internal declarations shared by the libdao.so translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -14,7 +15,8 @@ namespace dao {
 constexpr int KMAX = 64;        // aperture pool capacity (master problem size)
 constexpr int SMAX = 64;        // structures
 constexpr int CMAX = 32;        // beamlets per MLC row (one warp lane each)
-constexpr int MASTER_TILE = 256;  // voxels per tile of the fused master pass (= block size)
+constexpr int MASTER_TILE = 256;  // voxels per tile of the master evaluation (= block size)
+constexpr int KROW = KMAX + 4;    // row stride (floats) of the voxel-major aperture slab
 
 // Per-structure objective terms (Eqs. 9-10): a = alpha_s/|v_s| (0 for
 // non-targets), tu = T_s^-, b = beta_s/|v_s|, to = T_s^+.
@@ -41,27 +43,40 @@ struct MasterDev {
     double g[KMAX];       // gradient at y
     double gt[KMAX];      // gradient at the trial point (written by the reduction)
     double Ht[KMAX * KMAX];  // curvature matrix at the trial point (full, symmetric)
+    float gn[KMAX];       // sum_j |S_jk pi_j| at the trial point: the rounding scale of g_k
     double F;             // objective at y
     double Ft;            // objective at the trial point
     double alpha;         // step length along d
     double tol;           // absolute KKT tolerance of this solve
     double res;           // KKT residual at y
-    float yf[KMAX];       // FP32 copy of the point the fused pass evaluates
     int K;                // pool size
     int iter;             // Newton iterations taken
     int phase;            // 0: evaluating the warm start, 1: line search
     int done;             // 1 once converged / stalled / out of iterations
     int status;           // MASTER_*
     int n_eval;           // fused passes evaluated
+    int err;              // set when a tile copy of an evaluation never completed
 };
 
-enum { MASTER_RUNNING = 0, MASTER_CONVERGED = 1, MASTER_MAXITER = 2, MASTER_STALLED = 3 };
+enum { MASTER_RUNNING = 0, MASTER_CONVERGED = 1, MASTER_MAXITER = 2, MASTER_STALLED = 3, MASTER_ERROR = 4 };
 
 // Result of the device-side pricing (step a3).
 struct PriceDev {
     double rc;            // reduced cost of the best beam
     int beam;             // b*
     int pad;
+};
+
+// Device-side column-generation state of a graph-driven solve.
+struct CGDev {
+    int K;                // pool size reached
+    int done;             // 0 running, 1 no negative reduced cost, 2 duplicate aperture
+    int pad[2];
+    double trace[KMAX];   // F after each added aperture
+    double res[KMAX];     // final KKT residual of each master solve
+    double tol[KMAX];     // its absolute tolerance
+    int evals[KMAX];      // fused passes of each master solve
+    int status[KMAX];     // MASTER_* of each master solve
 };
 
 // ---- kernel launchers (all on `stream`; return the launch error) ----------
@@ -73,13 +88,19 @@ cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct,
                         int num_sms, cudaStream_t stream, int* launches);
 int dose_grid(int n_rows, int num_sms);
 
-// a2: w = D^T pi over the beamlet-major transpose.
-cudaError_t launch_dt(const DevCSR& Dt, const float* pi, float* w, cudaStream_t stream, int* launches);
+// a2: w = D^T pi over the beamlet-major transpose (skipped when *skip != 0).
+cudaError_t launch_dt(const DevCSR& Dt, const float* pi, float* w, const int* skip, cudaStream_t stream,
+                      int* launches);
 
-// a4: out_j = sum over beam b's entries of row j with mask[col - base] (0/1).
+// a4: out[j * stride] = sum over beam b's entries of row j with mask[col - base] (0/1).
 cudaError_t launch_column(const DevCSR& D, const int* seg_lo, const int* seg_hi, int base,
-                          int n_beamlets_b, const float* mask, float* out, int num_sms,
+                          int n_beamlets_b, const float* mask, float* out, int stride, int num_sms,
                           cudaStream_t stream, int* launches);
+
+// a4 for the aperture the device just committed at pool index K-1 (graph path).
+cudaError_t launch_column_dev(const DevCSR& D, const int* seg, const int* ap_beam, int K, const int* beam_off,
+                              const int* rows, const int* cols, int max_nb, const float* mask, float* out, int stride,
+                              const CGDev* cg, int num_sms, cudaStream_t stream, int* launches);
 
 // x_i = sum_{k in K_i} y_k (Eq. 7) from the aperture table.
 cudaError_t launch_fluence(const int* ap_beam, const int* ap_lr, int lr_stride, const double* y, int K,
@@ -87,26 +108,51 @@ cudaError_t launch_fluence(const int* ap_beam, const int* ap_lr, int lr_stride, 
 
 // a3: per-row scan (one warp per MLC row) and the per-beam sum / argmin.
 cudaError_t launch_price(const float* w, const int4* row_info, int n_rows, const int* beam_row0,
-                         int n_beams, double* row_v, int2* row_lr, PriceDev* out,
+                         int n_beams, double* row_v, int2* row_lr, PriceDev* out, const int* skip,
                          cudaStream_t stream, int* launches);
+// Graph path: stop the solve when the reduced cost is not below -tau or the
+// aperture repeats one in the pool; otherwise record it as aperture K-1 and
+// write its open-beamlet mask.
+cudaError_t launch_commit(const PriceDev* pr, const int2* row_lr, const int* beam_row0, const int* rows,
+                          const int* cols, double tau, int K, int lr_stride, int* ap_beam, int* ap_lr,
+                          float* mask, CGDev* cg, cudaStream_t stream, int* launches);
 
 // a5: projected-Newton master problem kernels.
 struct MasterBuffers {
     MasterDev* st = nullptr;
-    float* H_part = nullptr;    // [KMAX*KMAX][G]
-    double* g_part = nullptr;   // [KMAX][G]
-    double* F_part = nullptr;   // [G]
-    int G = 0;
+    float* act_rows = nullptr;  // [n_tiles * MASTER_TILE][KROW]: rows of the active voxels, per tile slot
+    float2* act_hp = nullptr;   // [n_tiles * MASTER_TILE]: their curvature and gradient
+    int* act_count = nullptr;   // [n_tiles]
+    int n_tiles = 0;
+    float* H_part = nullptr;    // [KMAX*(KMAX+1)/2][GH]
+    double* g_part = nullptr;   // [KMAX][GH]
+    float* gn_part = nullptr;   // [KMAX][GH]
+    double* F_part = nullptr;   // [max evaluation grid]
+    int GH = 0;                 // blocks of the curvature kernel
+    int grid[KMAX + 1] = {};    // blocks of the evaluation kernel for each pool size
+    CUtensorMap tmap[KROW / 4 + 1];  // slab tile maps, indexed by row width / 4
+    bool tmap_ready[KROW / 4 + 1] = {};
 };
-cudaError_t launch_master_init(MasterDev* st, int K, cudaStream_t stream, int* launches);
-cudaError_t launch_master_pass(const float* slab, int V, int ld, int K, const MasterBuffers& mb,
-                               const uint8_t* vstruct, const StructTermsF* tf, const StructTermsD* td,
-                               int S, float* z_out, float* pi_out, int final_pass,
-                               cudaStream_t stream, int* launches);
+enum { PASS_EVAL = 0, PASS_FINAL = 1, PASS_TIMING = 2 };
+int master_kw(int K);
+int master_lanes(int K);
+int master_grid(int V, int num_sms, int K);
+int master_grid_max(int num_sms);
+int master_hess_grid(int num_sms);
+size_t master_eval_smem(int K);
+cudaError_t master_configure();
+// skip (nullable): device flag that turns the launch into a no-op (graph path).
+// cond / use_cond: while-node handle the step kernel sets to "not done".
+cudaError_t launch_master_init(MasterDev* st, int K, const int* skip, cudaGraphConditionalHandle cond,
+                               int use_cond, cudaStream_t stream, int* launches);
+cudaError_t launch_master_eval(const MasterBuffers& mb, int V, int K, const uint8_t* vstruct,
+                               const StructTermsF* tf, int S, float* z_out, float* pi_out, int mode,
+                               const int* skip, cudaStream_t stream, int* launches);
+cudaError_t launch_master_hess(const MasterBuffers& mb, int K, int mode, cudaStream_t stream, int* launches);
 cudaError_t launch_master_reduce(int K, const MasterBuffers& mb, cudaStream_t stream, int* launches);
 cudaError_t launch_master_step(const MasterBuffers& mb, int max_iter, double tol_rel,
-                               cudaStream_t stream, int* launches);
-size_t master_pass_smem(int K);
-cudaError_t master_configure();
+                               cudaGraphConditionalHandle cond, int use_cond, cudaStream_t stream,
+                               int* launches);
+cudaError_t launch_cg_record(const MasterDev* st, CGDev* cg, int K, cudaStream_t stream, int* launches);
 
 }  // namespace dao

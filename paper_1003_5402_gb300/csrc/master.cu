@@ -1,21 +1,34 @@
 // Master problem of column-generation DAO (arXiv:1003.5402, Sec. 2.2-2.3):
 // min_y F(S y) subject to y >= 0 over the current aperture pool, where column k
-// of the slab S (V x K, FP32, column-major) is the aperture dose D_kj of Eq. 2.
+// of the slab S (V x K, FP32) is the aperture dose D_kj of Eq. 2.  The slab is
+// stored voxel-major: row j holds the K doses of voxel j (row stride KROW).
 //
 // The paper uses gradient projection and gives no step or stopping rule.  This
 // is a scaled gradient projection, the projected Newton method of Bertsekas
 // (1982): variables with y_k <= eps and g_k > 0 take the plain gradient step,
 // the others a Newton step on H = S_F^T diag(h) S_F (h = generalised second
 // derivative of the piecewise-quadratic F), with Armijo backtracking along the
-// projection arc.  Each evaluation is three kernels:
-//   k_master_pass    one fused pass over the slab at the trial point: z = S y,
-//                    pi = grad F(z), h, F (FP64), and per-block partials of
-//                    g = S^T pi (FP64) and H (FP32);
-//   k_master_reduce  fixed-order reduction of the partials (one warp per entry);
-//   k_master_step    one block: Armijo test, KKT residual, Cholesky (FP64) of
-//                    the free block of H, next trial point.
-// Every kernel returns at once after the state is marked done, so the host can
-// queue several evaluations ahead and poll the flag.
+// projection arc.  One evaluation is four kernels:
+//   k_master_eval   streams the slab in tiles of TILE voxels (2-D TMA bulk
+//                   copies completing on an mbarrier) and computes z = S y as a
+//                   compensated FP32 dot product (Ogita, Rump & Oishi,
+//                   "Accurate sum and dot product", 2005; y split into two
+//                   floats), pi = grad F(z), h and F; voxels with h > 0 are the
+//                   only ones that contribute to g and H, and their rows, h and
+//                   pi are written compacted, per tile, to an active list;
+//   k_master_hess   the active list split evenly over the blocks: per-block
+//                   partials of H (FP32), g and the rounding scale of g;
+//   k_master_reduce fixed-order reduction of the partials;
+//   k_master_step   one block: KKT test at the trial point, Armijo test, damped
+//                   FP32 Cholesky of the free block of H, next trial point.
+// Every kernel returns at once after the state is marked done, so evaluations
+// can be queued ahead (or looped on the device by a graph while node).
+//
+// Stopping rule: |y_k - max(y_k - g_k, 0)| <= tol_rel * max|g(start)| +
+// NOISE * u * sum_j |S_jk pi_j| for every k (u = 2^-24), i.e. KKT up to the
+// FP32 rounding level of g.  A trial point that meets it is accepted without
+// the Armijo test: near the optimum the objective's change is below its own
+// rounding and the test would reject an optimal point.
 #include "dao_internal.h"
 
 #include <cmath>
@@ -25,8 +38,11 @@ namespace dao {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int TILE = MASTER_TILE;
-constexpr int LDA = TILE + 1;  // padded stride of the shared slab tile (bank spread)
+constexpr int TILE = MASTER_TILE;   // voxels per evaluation tile = threads per block
+constexpr int CH = 128;             // active voxels per Hessian sub-chunk
+constexpr float U32 = 5.9604645e-8f;  // 2^-24
+constexpr double NOISE = 64.0;
+constexpr int WAIT_LIMIT = 1 << 20;   // mbarrier polls before a copy is declared lost
 
 __device__ __forceinline__ double warp_sum_f64(double v) {
 #pragma unroll
@@ -34,12 +50,89 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
     return v;
 }
 
-__global__ void k_master_init(MasterDev* __restrict__ st, int K) {
+__device__ __forceinline__ float warp_sum_f32(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// ---- TMA / mbarrier (sm_90+ PTX) ----------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false if it never completed.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    const unsigned a = smem_addr(bar);
+    for (int i = 0; i < WAIT_LIMIT; ++i) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// 2-D tiled bulk copy of box (x, y) of the tensor map into shared memory.
+__device__ __forceinline__ void tma_load_2d(float* dst, const CUtensorMap* map, int x, int y,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            smem_addr(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// TwoSum accumulation of a product a*y (y = yh + yl) into the pair (s, c).
+__device__ __forceinline__ void dot2_step(float& s, float& c, float a, float yh, float yl) {
+    const float p = a * yh;
+    float pe = fmaf(a, yh, -p);  // a*yh = p + pe exactly
+    pe = fmaf(a, yl, pe);
+    const float t2 = s + p;      // TwoSum(s, p)
+    const float bb = t2 - s;
+    const float e = (s - (t2 - bb)) + (p - bb);
+    s = t2;
+    c += e + pe;
+}
+
+// (rb, cb) of the eb-th 4x4 block of the upper triangle, row-major
+__device__ __forceinline__ void block_of(int eb, int KB, int& rb, int& cb) {
+    int r = 0, rem = eb;
+    while (rem >= KB - r) {
+        rem -= KB - r;
+        ++r;
+    }
+    rb = r;
+    cb = r + rem;
+}
+
+// Packed index of entry (r, c), r <= c, of the upper triangle of a K x K matrix.
+__device__ __forceinline__ int tri_index(int r, int c, int K) { return r * K - (r * (r - 1)) / 2 + (c - r); }
+
+__global__ void k_master_init(MasterDev* __restrict__ st, int K, const int* __restrict__ skip,
+                              cudaGraphConditionalHandle cond, int use_cond) {
     const int t = threadIdx.x;
+    if (skip != nullptr && *skip) {  // the solve stopped before this round: nothing to iterate
+        if (t == 0) {
+            st->done = 1;
+            if (use_cond) cudaGraphSetConditional(cond, 0u);
+        }
+        return;
+    }
     if (t < K) {
         const double v = t < K - 1 ? st->y[t] : 0.0;  // warm start: previous optimum, new aperture at 0
         st->yt[t] = v;
-        st->yf[t] = (float)v;
         st->d[t] = 0.0;
     }
     if (t == 0) {
@@ -50,375 +143,655 @@ __global__ void k_master_init(MasterDev* __restrict__ st, int K) {
         st->status = MASTER_RUNNING;
         st->alpha = 1.0;
         st->n_eval = 0;
+        st->err = 0;
+        if (use_cond) cudaGraphSetConditional(cond, 1u);
     }
 }
 
-__global__ void __launch_bounds__(TILE) k_master_pass(const float* __restrict__ slab, int V, int ld, int K, int KP,
-                                                      MasterDev* __restrict__ st, float* __restrict__ H_part,
-                                                      double* __restrict__ g_part, double* __restrict__ F_part, int G,
-                                                      const uint8_t* __restrict__ vstruct,
-                                                      const StructTermsF* __restrict__ tf,
-                                                      const StructTermsD* __restrict__ td, int S,
-                                                      float* __restrict__ z_out, float* __restrict__ pi_out,
-                                                      int final_pass) {
-    if (!final_pass && st->done) return;
-    extern __shared__ float As[];  // [KP][LDA]
-    __shared__ float s_y[KMAX];
-    __shared__ float s_h[TILE];
-    __shared__ float s_p[TILE];
+// Graph path: keep the statistics of the master solve that just finished.
+__global__ void k_cg_record(const MasterDev* __restrict__ st, CGDev* __restrict__ cg, int K) {
+    if (threadIdx.x != 0 || cg->done) return;
+    cg->trace[K - 1] = st->F;
+    cg->res[K - 1] = st->res;
+    cg->tol[K - 1] = st->tol;
+    cg->evals[K - 1] = st->n_eval;
+    cg->status[K - 1] = st->status;
+}
+
+// ---- evaluation: one slab tile per iteration --------------------------------
+__global__ void __launch_bounds__(TILE, 3) k_master_eval(const __grid_constant__ CUtensorMap tmap, int V, int K,
+                                                         int KW, MasterDev* __restrict__ st,
+                                                         float* __restrict__ act_rows, float2* __restrict__ act_hp,
+                                                         int* __restrict__ act_count, double* __restrict__ F_part,
+                                                         const uint8_t* __restrict__ vstruct,
+                                                         const StructTermsF* __restrict__ tf, int S,
+                                                         float* __restrict__ z_out, float* __restrict__ pi_out,
+                                                         int mode, const int* __restrict__ skip) {
+    if (skip != nullptr && *skip) return;
+    if (mode == PASS_EVAL && st->done) return;
+    const bool final_pass = mode == PASS_FINAL;
+    extern __shared__ __align__(128) float As[];  // [TILE][KW]: rows of the tile's voxels
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ float s_yh[KMAX], s_yl[KMAX];
+    __shared__ int s_wcount[TILE / 32];
     __shared__ StructTermsF s_tf[SMAX];
-    __shared__ StructTermsD s_td[SMAX];
     __shared__ double s_red[TILE / 32];
     const int tid = threadIdx.x;
-    if (tid < K) s_y[tid] = final_pass ? (float)st->y[tid] : st->yf[tid];
-    for (int i = tid; i < S; i += TILE) {
-        s_tf[i] = tf[i];
-        s_td[i] = td[i];
+    const int lane = tid & 31, warp = tid >> 5;
+    if (tid < KMAX) {
+        const double yv = tid < K ? (final_pass ? st->y[tid] : st->yt[tid]) : 0.0;
+        const float hi = (float)yv;
+        s_yh[tid] = hi;
+        s_yl[tid] = (float)(yv - (double)hi);
     }
-    // thread roles of the curvature / gradient phase: 4x4 blocks of the upper
-    // triangle of H, then one thread per gradient entry
-    const int KB = KP / 4;
-    const int nb = KB * (KB + 1) / 2;
-    int rb = -1, cb = -1;
-    if (!final_pass && tid < nb) {
-        int r = 0, rem = tid;
-        while (rem >= KB - r) {
-            rem -= KB - r;
-            ++r;
-        }
-        rb = r;
-        cb = r + rem;
-    }
-    const int gk = (!final_pass && tid >= nb && tid < nb + K) ? tid - nb : -1;
+    for (int i = tid; i < S; i += TILE) s_tf[i] = tf[i];
+    if (tid == 0) mbar_init(&bar, 1);
     __syncthreads();
-
-    float hs[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) hs[q] = 0.f;
-    double gsum = 0.0, facc = 0.0;
+    float facc = 0.f;  // this thread's voxels: a few terms, FP32 is enough before the FP64 block sum
+    unsigned parity = 0;
+    bool lost = false;
     const int n_tiles = (V + TILE - 1) / TILE;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += G) {
-        const int j = tile * TILE + tid;
-        const bool valid = j < V;
-        float z = 0.f;
-        for (int k = 0; k < K; ++k) {
-            const float a = valid ? __ldg(slab + (size_t)k * ld + j) : 0.f;
-            As[k * LDA + tid] = a;
-            z = fmaf(a, s_y[k], z);
+    const int nq = (K + 3) / 4;  // float4 groups holding the K doses
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        __syncthreads();  // every thread is done with the previous tile's buffers
+        if (tid == 0) {
+            mbar_expect_tx(&bar, (unsigned)(TILE * KW * sizeof(float)));
+            tma_load_2d(As, &tmap, 0, tile * TILE, &bar);
         }
-        for (int k = K; k < KP; ++k) As[k * LDA + tid] = 0.f;
+        if (!mbar_wait(&bar, parity)) {
+            lost = true;
+            break;
+        }
+        parity ^= 1u;
+        const int j = tile * TILE + tid;
+        // ---- compensated z from this voxel's row, four chains
+        const float4* row = reinterpret_cast<const float4*>(As + tid * KW);
+        float sc[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int q = 0; q < nq; ++q) {
+            const float4 a = row[q];
+            const int k = 4 * q;  // doses beyond K are zero in the slab
+            dot2_step(sc[0], cc[0], a.x, s_yh[k], s_yl[k]);
+            dot2_step(sc[1], cc[1], a.y, s_yh[k + 1], s_yl[k + 1]);
+            dot2_step(sc[2], cc[2], a.z, s_yh[k + 2], s_yl[k + 2]);
+            dot2_step(sc[3], cc[3], a.w, s_yh[k + 3], s_yl[k + 3]);
+        }
+        float s = sc[0], c = cc[0];
+#pragma unroll
+        for (int q = 1; q < 4; ++q) {
+            const float t2 = s + sc[q];
+            const float bb = t2 - s;
+            const float e = (s - (t2 - bb)) + (sc[q] - bb);
+            s = t2;
+            c += e + cc[q];
+        }
         float h = 0.f, p = 0.f;
-        if (valid) {
-            const int s = vstruct[j];
-            const StructTermsF t = s_tf[s];
-            const float u = fmaxf(0.f, t.tu - z);
-            const float o = fmaxf(0.f, z - t.to);
+        if (j < V) {
+            const StructTermsF t = s_tf[vstruct[j]];
+            const float du = (t.tu - s) - c;   // T^- - z, exact subtraction near the threshold
+            const float dov = (s - t.to) + c;  // z - T^+
+            const float u = fmaxf(du, 0.f), o = fmaxf(dov, 0.f);
             p = 2.f * (t.b * o - t.a * u);
-            h = 2.f * ((z < t.tu ? t.a : 0.f) + (z > t.to ? t.b : 0.f));
-            const StructTermsD td_ = s_td[s];
-            const double zd = z;
-            const double ud = fmax(0.0, td_.tu - zd);
-            const double od = fmax(0.0, zd - td_.to);
-            facc += td_.a * ud * ud + td_.b * od * od;
+            h = 2.f * ((du > 0.f ? t.a : 0.f) + (dov > 0.f ? t.b : 0.f));
+            facc = fmaf(t.a * u, u, fmaf(t.b * o, o, facc));
             if (final_pass) {
-                z_out[j] = z;
+                z_out[j] = s + c;
                 pi_out[j] = p;
             }
         }
-        if (!final_pass) {
-            s_h[tid] = h;
-            s_p[tid] = p;
-            __syncthreads();
-            if (rb >= 0) {
-                const float* r0 = As + (4 * rb) * LDA;
-                const float* c0 = As + (4 * cb) * LDA;
-                for (int t = 0; t < TILE; ++t) {
-                    const float hv = s_h[t];
-                    const float a0 = r0[t] * hv, a1 = r0[LDA + t] * hv, a2 = r0[2 * LDA + t] * hv,
-                                a3 = r0[3 * LDA + t] * hv;
-                    const float b0 = c0[t], b1 = c0[LDA + t], b2 = c0[2 * LDA + t], b3 = c0[3 * LDA + t];
-                    hs[0] = fmaf(a0, b0, hs[0]);
-                    hs[1] = fmaf(a0, b1, hs[1]);
-                    hs[2] = fmaf(a0, b2, hs[2]);
-                    hs[3] = fmaf(a0, b3, hs[3]);
-                    hs[4] = fmaf(a1, b0, hs[4]);
-                    hs[5] = fmaf(a1, b1, hs[5]);
-                    hs[6] = fmaf(a1, b2, hs[6]);
-                    hs[7] = fmaf(a1, b3, hs[7]);
-                    hs[8] = fmaf(a2, b0, hs[8]);
-                    hs[9] = fmaf(a2, b1, hs[9]);
-                    hs[10] = fmaf(a2, b2, hs[10]);
-                    hs[11] = fmaf(a2, b3, hs[11]);
-                    hs[12] = fmaf(a3, b0, hs[12]);
-                    hs[13] = fmaf(a3, b1, hs[13]);
-                    hs[14] = fmaf(a3, b2, hs[14]);
-                    hs[15] = fmaf(a3, b3, hs[15]);
+        if (final_pass) continue;
+        // ---- compact the voxels with non-zero curvature into this tile's slots
+        const bool act = h > 0.f;
+        const unsigned bal = __ballot_sync(FULL, act);
+        if (lane == 0) s_wcount[warp] = __popc(bal);
+        __syncthreads();
+        int base = 0, n_act = 0;
+#pragma unroll
+        for (int w = 0; w < TILE / 32; ++w) {
+            const int cnt = s_wcount[w];
+            base += w < warp ? cnt : 0;
+            n_act += cnt;
+        }
+        if (act) {
+            const size_t slot = (size_t)tile * TILE + base + __popc(bal & ((1u << lane) - 1u));
+            float4* dst = reinterpret_cast<float4*>(act_rows + slot * KROW);
+            for (int q = 0; q < nq; ++q) dst[q] = row[q];
+            act_hp[slot] = make_float2(h, p);
+        }
+        if (tid == 0) act_count[tile] = n_act;
+    }
+    if (lost) {  // a tile copy never arrived: report it, the step kernel stops the solve
+        if (tid == 0) st->err = 1;
+        return;
+    }
+    if (final_pass) return;
+    double fsum = warp_sum_f64((double)facc);
+    if (lane == 0) s_red[warp] = fsum;
+    __syncthreads();
+    if (tid < 32) {
+        double t = tid < TILE / 32 ? s_red[tid] : 0.0;
+        t = warp_sum_f64(t);
+        if (tid == 0) F_part[blockIdx.x] = t;
+    }
+}
+
+// ---- curvature and gradient over the active list ----------------------------
+// Block b takes active voxels [M b / G, M (b + 1) / G) in tile order, in
+// sub-chunks of CH voxels copied to shared memory as rows of KW floats; thread
+// (eb, v) accumulates the 4x4 block eb of H over voxel lane v, and the diagonal
+// blocks also g and sum |S_jk pi_j|.
+__global__ void __launch_bounds__(256) k_master_hess(const float* __restrict__ act_rows,
+                                                     const float2* __restrict__ act_hp,
+                                                     const int* __restrict__ act_count, int n_tiles, int K, int KW,
+                                                     int NV, MasterDev* __restrict__ st, float* __restrict__ H_part,
+                                                     double* __restrict__ g_part, float* __restrict__ gn_part, int G,
+                                                     int mode) {
+    if (mode == PASS_EVAL && st->done) return;
+    extern __shared__ __align__(16) float smem[];
+    int* s_pref = reinterpret_cast<int*>(smem);                        // [n_tiles + 1]
+    float* Ac = smem + ((n_tiles + 1 + 3) / 4) * 4;                    // [CH][KW]
+    float* s_h = Ac + CH * KW;                                         // [CH]
+    float* s_p = s_h + CH;                                             // [CH]
+    __shared__ float s_scr[8 * 24];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    // exclusive prefix of the per-tile active counts (integer sums: exact in any
+    // order): contiguous chunks per thread, then a scan of the chunk totals
+    __shared__ int s_wsum[8];
+    {
+        const int per = (n_tiles + 255) / 256;
+        const int t0 = tid * per, t1 = min(n_tiles, t0 + per);
+        int mine = 0;
+        for (int t = t0; t < t1; ++t) mine += act_count[t];
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        int before = incl - mine;
+        for (int w = 0; w < warp; ++w) before += s_wsum[w];
+        for (int t = t0; t < t1; ++t) {
+            s_pref[t] = before;
+            before += act_count[t];
+        }
+        if (tid == 255) s_pref[n_tiles] = before;
+    }
+    const int KP = (K + 3) / 4 * 4;
+    const int KB = KP / 4;
+    const int nb = KB * (KB + 1) / 2;
+    int rb = -1, cb = -1;
+    const int v = tid % NV;
+    if (tid < nb * NV) block_of(tid / NV, KB, rb, cb);
+    __syncthreads();
+    const int M = s_pref[n_tiles];
+    const int m0 = (int)((long long)M * blockIdx.x / G), m1 = (int)((long long)M * (blockIdx.x + 1) / G);
+    const int nq = KP / 4;
+    float hs[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) hs[q] = 0.f;
+    float gs[4] = {0.f, 0.f, 0.f, 0.f}, gns[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int c0 = m0; c0 < m1; c0 += CH) {
+        const int n = min(CH, m1 - c0);
+        __syncthreads();
+        // copy the sub-chunk: two threads per voxel, alternate float4 groups
+        {
+            const int i = tid >> 1, half = tid & 1;
+            if (i < n) {
+                const int m = c0 + i;
+                int lo = 0, hi = n_tiles;  // last tile with pref <= m
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_pref[mid] <= m) lo = mid; else hi = mid;
                 }
-            } else if (gk >= 0) {
-                const float* a = As + gk * LDA;
-                float ga = 0.f;
-                for (int t = 0; t < TILE; ++t) ga = fmaf(a[t], s_p[t], ga);
-                gsum += (double)ga;
+                const size_t slot = (size_t)lo * TILE + (m - s_pref[lo]);
+                const float4* src = reinterpret_cast<const float4*>(act_rows + slot * KROW);
+                float4* dst = reinterpret_cast<float4*>(Ac + i * KW);
+                for (int q = half; q < nq; q += 2) dst[q] = src[q];
+                if (half == 0) {
+                    const float2 hp = act_hp[slot];
+                    s_h[i] = hp.x;
+                    s_p[i] = hp.y;
+                }
             }
-            __syncthreads();
+        }
+        __syncthreads();
+        if (rb >= 0) {
+            for (int i = v; i < n; i += NV) {
+                const float4 ra = *reinterpret_cast<const float4*>(Ac + i * KW + 4 * rb);
+                const float4 rc = *reinterpret_cast<const float4*>(Ac + i * KW + 4 * cb);
+                const float hv = s_h[i];
+                const float a0 = ra.x * hv, a1 = ra.y * hv, a2 = ra.z * hv, a3 = ra.w * hv;
+                hs[0] = fmaf(a0, rc.x, hs[0]);
+                hs[1] = fmaf(a0, rc.y, hs[1]);
+                hs[2] = fmaf(a0, rc.z, hs[2]);
+                hs[3] = fmaf(a0, rc.w, hs[3]);
+                hs[4] = fmaf(a1, rc.x, hs[4]);
+                hs[5] = fmaf(a1, rc.y, hs[5]);
+                hs[6] = fmaf(a1, rc.z, hs[6]);
+                hs[7] = fmaf(a1, rc.w, hs[7]);
+                hs[8] = fmaf(a2, rc.x, hs[8]);
+                hs[9] = fmaf(a2, rc.y, hs[9]);
+                hs[10] = fmaf(a2, rc.z, hs[10]);
+                hs[11] = fmaf(a2, rc.w, hs[11]);
+                hs[12] = fmaf(a3, rc.x, hs[12]);
+                hs[13] = fmaf(a3, rc.y, hs[13]);
+                hs[14] = fmaf(a3, rc.z, hs[14]);
+                hs[15] = fmaf(a3, rc.w, hs[15]);
+                if (rb == cb) {
+                    const float pv = s_p[i], pa = fabsf(pv);
+                    gs[0] = fmaf(ra.x, pv, gs[0]);
+                    gs[1] = fmaf(ra.y, pv, gs[1]);
+                    gs[2] = fmaf(ra.z, pv, gs[2]);
+                    gs[3] = fmaf(ra.w, pv, gs[3]);
+                    gns[0] = fmaf(fabsf(ra.x), pa, gns[0]);
+                    gns[1] = fmaf(fabsf(ra.y), pa, gns[1]);
+                    gns[2] = fmaf(fabsf(ra.z), pa, gns[2]);
+                    gns[3] = fmaf(fabsf(ra.w), pa, gns[3]);
+                }
+            }
         }
     }
-    if (!final_pass) {
-        if (rb >= 0) {
+    // fold the NV voxel lanes of each entry block (consecutive threads) with a
+    // fixed shuffle tree, then across warps through shared memory when NV > 32
+    float vals[24];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 16; ++q) vals[q] = hs[q];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int r = 4 * rb + q, cc = 4 * cb + c;
-                    if (r < K && cc < K && r <= cc) H_part[(size_t)(r * KMAX + cc) * G + blockIdx.x] = hs[q * 4 + c];
-                }
+    for (int q = 0; q < 4; ++q) {
+        vals[16 + q] = gs[q];
+        vals[20 + q] = gns[q];
+    }
+    const int span = NV < 32 ? NV : 32;
+    for (int o = span / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 24; ++q) vals[q] += __shfl_xor_sync(FULL, vals[q], o);
+    if (NV > 32 && lane == 0)
+#pragma unroll
+        for (int q = 0; q < 24; ++q) s_scr[warp * 24 + q] = vals[q];
+    __syncthreads();
+    if ((tid % NV) == 0 && tid < nb * NV) {
+        if (NV > 32) {
+            const int w0 = tid >> 5, nw = NV >> 5;
+#pragma unroll
+            for (int q = 0; q < 24; ++q) {
+                float t = 0.f;
+                for (int w = 0; w < nw; ++w) t += s_scr[(w0 + w) * 24 + q];
+                vals[q] = t;
+            }
         }
-        if (gk >= 0) g_part[(size_t)gk * G + blockIdx.x] = gsum;
-        double v = warp_sum_f64(facc);
-        if ((tid & 31) == 0) s_red[tid >> 5] = v;
-        __syncthreads();
-        if (tid < 32) {
-            double t = tid < TILE / 32 ? s_red[tid] : 0.0;
-            t = warp_sum_f64(t);
-            if (tid == 0) F_part[blockIdx.x] = t;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int r = 4 * rb + q, col = 4 * cb + e;
+                if (r < K && col < K && r <= col) H_part[(size_t)tri_index(r, col, K) * G + blockIdx.x] = vals[q * 4 + e];
+            }
+        if (rb == cb) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = 4 * rb + q;
+                if (r < K) {
+                    g_part[(size_t)r * G + blockIdx.x] = (double)vals[16 + q];
+                    gn_part[(size_t)r * G + blockIdx.x] = vals[20 + q];
+                }
+            }
         }
     }
 }
 
-// One warp per output: H entries (r <= c), then g, then F.
+// One warp per output (packed H entries, then g, then the g rounding scale, then
+// F): lanes read the blocks' partials (contiguous per output) and combine them
+// with a fixed shuffle tree in FP64.
 __global__ void __launch_bounds__(256) k_master_reduce(const float* __restrict__ H_part,
                                                        const double* __restrict__ g_part,
-                                                       const double* __restrict__ F_part, int G,
+                                                       const float* __restrict__ gn_part,
+                                                       const double* __restrict__ F_part, int GH, int GE,
                                                        MasterDev* __restrict__ st) {
     if (st->done) return;
     const int K = st->K;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int E = K * (K + 1) / 2;
+    const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    const int nH = K * K;
-    if (warp < nH) {
-        const int r = warp / K, c = warp % K;
-        if (r > c) return;
+    if (o < E) {
         double s = 0.0;
-        const float* src = H_part + (size_t)(r * KMAX + c) * G;
-        for (int i = lane; i < G; i += 32) s += (double)src[i];
+        const float* src = H_part + (size_t)o * GH;
+        for (int b = lane; b < GH; b += 32) s += (double)src[b];
         s = warp_sum_f64(s);
         if (lane == 0) {
+            int r = 0, rem = o;
+            while (rem >= K - r) {
+                rem -= K - r;
+                ++r;
+            }
+            const int c = r + rem;
             st->Ht[r * KMAX + c] = s;
             st->Ht[c * KMAX + r] = s;
         }
-    } else if (warp < nH + K) {
-        const int k = warp - nH;
+    } else if (o < E + K) {
+        const int k = o - E;
         double s = 0.0;
-        const double* src = g_part + (size_t)k * G;
-        for (int i = lane; i < G; i += 32) s += src[i];
+        for (int b = lane; b < GH; b += 32) s += g_part[(size_t)k * GH + b];
         s = warp_sum_f64(s);
         if (lane == 0) st->gt[k] = s;
-    } else if (warp == nH + K) {
+    } else if (o < E + 2 * K) {
+        const int k = o - E - K;
+        float s = 0.f;
+        for (int b = lane; b < GH; b += 32) s += gn_part[(size_t)k * GH + b];
+        s = warp_sum_f32(s);
+        if (lane == 0) st->gn[k] = s;
+    } else if (o == E + 2 * K) {
         double s = 0.0;
-        for (int i = lane; i < G; i += 32) s += F_part[i];
+        for (int b = lane; b < GE; b += 32) s += F_part[b];
         s = warp_sum_f64(s);
         if (lane == 0) st->Ft = s;
     }
 }
 
-__global__ void __launch_bounds__(256) k_master_step(MasterDev* __restrict__ st, int max_iter, double tol_rel,
-                                                     double sigma) {
-    __shared__ double L[KMAX][KMAX + 1];
-    __shared__ double rhs[KMAX];
-    __shared__ int fidx[KMAX];
-    __shared__ int s_nf, s_ok, s_accept, s_stop;
-    __shared__ double s_lam, s_maxdiag;
-    if (st->done) return;
-    const int K = st->K;
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        ++st->n_eval;
-        s_stop = 0;
-        s_nf = 0;
-        bool accept;
-        if (st->iter >= max_iter + 64) {  // hard cap on evaluations, whatever the line search does
-            st->status = MASTER_MAXITER;
-            s_stop = 1;
-            accept = false;
-        } else if (st->phase == 0) {
-            accept = true;
-        } else {
-            double dec = 0.0;
-            for (int k = 0; k < K; ++k) dec += st->g[k] * (st->yt[k] - st->y[k]);
-            accept = st->Ft <= st->F + sigma * dec;
-        }
-        s_accept = accept ? 1 : 0;
-        if (accept) {
-            double res = 0.0, gmax = 0.0;
-            for (int k = 0; k < K; ++k) {
-                const double y = st->yt[k], g = st->gt[k];
-                st->y[k] = y;
-                st->g[k] = g;
-                res = fmax(res, fabs(y - fmax(y - g, 0.0)));
-                gmax = fmax(gmax, fabs(g));
-            }
-            st->F = st->Ft;
-            if (st->phase == 0) st->tol = tol_rel * fmax(gmax, 1e-300);
-            st->res = res;
-            if (res <= st->tol) {
-                st->status = MASTER_CONVERGED;
-                s_stop = 1;
-            } else if (st->iter >= max_iter) {
-                st->status = MASTER_MAXITER;
-                s_stop = 1;
-            } else {
-                const double eps = fmin(1e-3, res);
-                int nf = 0;
-                for (int k = 0; k < K; ++k) {
-                    if (st->y[k] <= eps && st->g[k] > 0.0) {
-                        st->d[k] = -st->g[k];
-                    } else {
-                        fidx[nf++] = k;
-                    }
-                }
-                s_nf = nf;
-            }
-        } else if (!s_stop) {
-            st->alpha *= 0.5;
-            if (st->alpha < 1e-12) {
-                st->status = MASTER_STALLED;
-                s_stop = 1;
-            }
-        }
-    }
+// Block-wide reductions over STEP_T threads with a fixed order.
+constexpr int STEP_T = 256;
+constexpr int STEP_W = STEP_T / 32;
+
+__device__ __forceinline__ double blk_sum(double v, double* sw) {
+    v = warp_sum_f64(v);
     __syncthreads();
-    if (s_stop) {
-        if (tid == 0) st->done = 1;
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < STEP_W; ++w) t += sw[w];
+    return t;
+}
+
+__device__ __forceinline__ double blk_max(double v, double* sw) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = sw[0];
+#pragma unroll
+    for (int w = 1; w < STEP_W; ++w) t = fmax(t, sw[w]);
+    return t;
+}
+
+__device__ __forceinline__ int blk_or(int v, int* swi) {
+    v = __any_sync(FULL, v) ? 1 : 0;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) swi[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int t = 0;
+#pragma unroll
+    for (int w = 0; w < STEP_W; ++w) t |= swi[w];
+    return t;
+}
+
+// One block: thread k < K owns variable k; all threads share the factorisation.
+__device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int max_iter, double tol_rel,
+                                                 double sigma) {
+    __shared__ float L[KMAX][KMAX + 1];
+    __shared__ float rhs[KMAX];
+    __shared__ int fidx[KMAX];
+    __shared__ double sw[STEP_W];
+    __shared__ int swi[STEP_W];
+    __shared__ int s_ok;
+    if (st->done) return;
+    if (st->err) {  // a tile copy was lost in an evaluation: stop with the last accepted point
+        if (threadIdx.x == 0) {
+            st->status = MASTER_ERROR;
+            st->done = 1;
+        }
         return;
     }
-    if (s_accept) {
-        const int nf = s_nf;
-        for (int idx = tid; idx < nf * nf; idx += blockDim.x) {
-            const int i = idx / nf, j = idx % nf;
-            L[i][j] = st->Ht[fidx[i] * KMAX + fidx[j]];
+    const int K = st->K;
+    const int k = threadIdx.x;
+    const bool own = k < K;
+    const int phase = st->phase;
+    const double yt = own ? st->yt[k] : 0.0;
+    const double gt = own ? st->gt[k] : 0.0;
+    const double gn = own ? (double)st->gn[k] : 0.0;
+    const double y = own ? st->y[k] : 0.0;
+    const double g = own ? st->g[k] : 0.0;
+    // tolerance of this solve from the gradient at the warm start
+    double tol = st->tol;
+    if (phase == 0) {
+        tol = tol_rel * fmax(blk_max(own ? fabs(gt) : 0.0, sw), 1e-300);
+        if (k == 0) st->tol = tol;
+    }
+    const double rt = own ? fabs(yt - fmax(yt - gt, 0.0)) : 0.0;
+    const int viol = blk_or(own && rt > tol + NOISE * (double)U32 * gn, swi);
+    const double rmax = blk_max(rt, sw);
+    const double dec = blk_sum(own ? g * (yt - y) : 0.0, sw);
+    const bool cap = st->iter >= max_iter + 64;
+    const bool accept = !cap && (phase == 0 || !viol || st->Ft <= st->F + sigma * dec);
+    if (k == 0) ++st->n_eval;
+    if (cap) {
+        if (k == 0) {
+            st->status = MASTER_MAXITER;
+            st->done = 1;
         }
+        return;
+    }
+    if (!accept) {
+        const double alpha = st->alpha * 0.5;
+        if (alpha < 9.3e-10) {  // 2^-30: the line search found no decrease
+            if (k == 0) {
+                st->status = MASTER_STALLED;
+                st->done = 1;
+            }
+            return;
+        }
+        if (own) st->yt[k] = fmax(y + alpha * st->d[k], 0.0);
+        if (k == 0) {
+            st->alpha = alpha;
+            st->iter += 1;
+            st->phase = 1;
+        }
+        return;
+    }
+    // accept the trial point
+    if (own) {
+        st->y[k] = yt;
+        st->g[k] = gt;
+    }
+    if (k == 0) {
+        st->F = st->Ft;
+        st->res = rmax;
+    }
+    if (!viol || st->iter >= max_iter) {
+        if (k == 0) {
+            st->status = viol ? MASTER_MAXITER : MASTER_CONVERGED;
+            st->done = 1;
+        }
+        return;
+    }
+    // epsilon-active set, free variables compacted in order
+    const double eps = fmin(1e-3, rmax);
+    const bool active = own && yt <= eps && gt > 0.0;
+    const bool fr = own && !active;
+    const unsigned bal = __ballot_sync(FULL, fr);
+    __syncthreads();
+    if ((k & 31) == 0) swi[k >> 5] = __popc(bal);
+    __syncthreads();
+    int nf = 0, pos = 0;
+#pragma unroll
+    for (int w = 0; w < STEP_W; ++w) {
+        pos += w < (k >> 5) ? swi[w] : 0;
+        nf += swi[w];
+    }
+    pos += __popc(bal & ((1u << (k & 31)) - 1u));
+    if (fr) fidx[pos] = k;
+    double d = active ? -gt : 0.0;
+    __syncthreads();
+    // damped FP32 Cholesky of H_FF, retried with a larger shift if a pivot fails
+    float maxdiag = 0.f;
+    for (int i = 0; i < nf; ++i) maxdiag = fmaxf(maxdiag, (float)st->Ht[fidx[i] * KMAX + fidx[i]]);
+    float lam = 1e-6f * maxdiag + 1e-30f;
+    bool ok = false;
+    for (int attempt = 0; attempt < 6 && !ok; ++attempt) {
+        for (int idx = k; idx < nf * nf; idx += STEP_T) {
+            const int i = idx / nf, jj = idx % nf;
+            L[i][jj] = (float)st->Ht[fidx[i] * KMAX + fidx[jj]] + (i == jj ? lam : 0.f);
+        }
+        if (k == 0) s_ok = 1;
         __syncthreads();
-        if (tid == 0) {
-            double md = 0.0;
-            for (int i = 0; i < nf; ++i) md = fmax(md, L[i][i]);
-            s_maxdiag = md;
-            s_lam = 1e-10 * md;
-            s_ok = 0;
-        }
-        __syncthreads();
-        for (int attempt = 0; attempt < 8; ++attempt) {
-            if (attempt > 0) {
-                for (int idx = tid; idx < nf * nf; idx += blockDim.x) {
-                    const int i = idx / nf, j = idx % nf;
-                    L[i][j] = st->Ht[fidx[i] * KMAX + fidx[j]];
-                }
-                __syncthreads();
+        for (int jj = 0; jj < nf; ++jj) {
+            if (k == 0) {
+                const float pv = L[jj][jj];
+                if (!(pv > 0.f) || !isfinite(pv))
+                    s_ok = 0;
+                else
+                    L[jj][jj] = sqrtf(pv);
             }
-            for (int i = tid; i < nf; i += blockDim.x) L[i][i] += s_lam;
-            if (tid == 0) s_ok = 1;
             __syncthreads();
-            for (int j = 0; j < nf; ++j) {
-                if (tid == 0) {
-                    const double p = L[j][j];
-                    if (!(p > 0.0) || !isfinite(p))
-                        s_ok = 0;
-                    else
-                        L[j][j] = sqrt(p);
-                }
-                __syncthreads();
-                if (!s_ok) break;
-                const double ljj = L[j][j];
-                for (int i = j + 1 + tid; i < nf; i += blockDim.x) L[i][j] /= ljj;
-                __syncthreads();
-                const int m = nf - j - 1;
-                for (int idx = tid; idx < m * m; idx += blockDim.x) {
-                    const int i = j + 1 + idx / m, k = j + 1 + idx % m;
-                    if (k <= i) L[i][k] -= L[i][j] * L[k][j];
-                }
-                __syncthreads();
+            if (!s_ok) break;
+            const float ljj = L[jj][jj];
+            for (int i = jj + 1 + k; i < nf; i += STEP_T) L[i][jj] /= ljj;
+            __syncthreads();
+            const int m = nf - jj - 1;
+            for (int idx = k; idx < m * m; idx += STEP_T) {
+                const int i = jj + 1 + idx / m, q = jj + 1 + idx % m;
+                if (q <= i) L[i][q] -= L[i][jj] * L[q][jj];
             }
-            if (s_ok) break;
-            __syncthreads();
-            if (tid == 0) s_lam = fmax(s_lam * 100.0, 1e-12 * s_maxdiag + 1e-300);
             __syncthreads();
         }
-        if (s_ok) {
-            for (int i = tid; i < nf; i += blockDim.x) rhs[i] = -st->g[fidx[i]];
-            __syncthreads();
-            for (int j = 0; j < nf; ++j) {  // L u = -g_F
-                if (tid == 0) rhs[j] /= L[j][j];
-                __syncthreads();
-                for (int i = j + 1 + tid; i < nf; i += blockDim.x) rhs[i] -= L[i][j] * rhs[j];
-                __syncthreads();
-            }
-            for (int j = nf - 1; j >= 0; --j) {  // L^T d = u
-                if (tid == 0) rhs[j] /= L[j][j];
-                __syncthreads();
-                for (int i = tid; i < j; i += blockDim.x) rhs[i] -= L[j][i] * rhs[j];
-                __syncthreads();
-            }
-            for (int i = tid; i < nf; i += blockDim.x) st->d[fidx[i]] = rhs[i];
-        } else {
-            // no factorisation: diagonally scaled gradient step on the free set
-            for (int i = tid; i < nf; i += blockDim.x) {
-                const int k = fidx[i];
-                const double hk = st->Ht[k * KMAX + k];
-                st->d[k] = -st->g[k] / (hk > 0.0 ? hk : 1.0);
-            }
-        }
-        if (tid == 0) st->alpha = 1.0;
+        ok = s_ok != 0;
+        lam *= 100.f;
         __syncthreads();
     }
-    if (tid < K) {
-        const double yt = fmax(st->y[tid] + st->alpha * st->d[tid], 0.0);
-        st->yt[tid] = yt;
-        st->yf[tid] = (float)yt;
+    if (ok) {
+        if (k < nf) rhs[k] = -(float)st->g[fidx[k]];
+        __syncthreads();
+        for (int jj = 0; jj < nf; ++jj) {  // L u = -g_F
+            if (k == 0) rhs[jj] /= L[jj][jj];
+            __syncthreads();
+            for (int i = jj + 1 + k; i < nf; i += STEP_T) rhs[i] -= L[i][jj] * rhs[jj];
+            __syncthreads();
+        }
+        for (int jj = nf - 1; jj >= 0; --jj) {  // L^T d = u
+            if (k == 0) rhs[jj] /= L[jj][jj];
+            __syncthreads();
+            for (int i = k; i < jj; i += STEP_T) rhs[i] -= L[jj][i] * rhs[jj];
+            __syncthreads();
+        }
+        if (fr) d = (double)rhs[pos];
+    } else if (fr) {
+        const double hk = st->Ht[k * KMAX + k];
+        d = -gt / (hk > 0.0 ? hk : 1.0);
     }
-    if (tid == 0) {
+    if (own) {
+        st->d[k] = d;
+        st->yt[k] = fmax(yt + d, 0.0);
+    }
+    if (k == 0) {
+        st->alpha = 1.0;
         st->iter += 1;
         st->phase = 1;
     }
 }
 
+// Every exit path of the step leaves the while-node condition at "not done";
+// the evaluation cap inside the step guarantees that done is reached.
+__global__ void __launch_bounds__(STEP_T) k_master_step(MasterDev* __restrict__ st, int max_iter, double tol_rel,
+                                                        double sigma, cudaGraphConditionalHandle cond,
+                                                        int use_cond) {
+    master_step_body(st, max_iter, tol_rel, sigma);
+    if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
+}
+
 }  // namespace
 
-size_t master_pass_smem(int K) {
+int master_kw(int K) {
     const int KP = (K + 3) / 4 * 4;
-    return (size_t)KP * LDA * sizeof(float);
+    int kw = KP < 4 ? 4 : KP;
+    if (((kw / 4) & 1) == 0) kw += 4;  // odd float4 count per row: conflict-free row-per-thread loads
+    return kw;
 }
+
+size_t master_eval_smem(int K) { return (size_t)TILE * master_kw(K) * sizeof(float); }
+
+size_t master_hess_smem(int K, int n_tiles) {
+    return (size_t)((n_tiles + 1 + 3) / 4 * 4) * sizeof(int) + (size_t)CH * master_kw(K) * sizeof(float) +
+           2 * CH * sizeof(float);
+}
+
+int master_lanes(int K) {
+    const int KP = (K + 3) / 4 * 4;
+    const int KB = KP / 4;
+    const int nb = KB * (KB + 1) / 2;
+    int nv = 1;
+    while (nb > 0 && nv * 2 * nb <= 256) nv *= 2;
+    return nv;
+}
+
+// Blocks of the evaluation kernel for pool size K: all resident at once.
+int master_grid(int V, int num_sms, int K) {
+    const int n_tiles = (V + TILE - 1) / TILE;
+    int occ = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_master_eval, TILE, master_eval_smem(K)) != cudaSuccess ||
+        occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    const int gmax = num_sms * (occ < 4 ? occ : 4);
+    return n_tiles < gmax ? (n_tiles > 0 ? n_tiles : 1) : gmax;
+}
+
+int master_grid_max(int num_sms) { return 4 * num_sms; }
+
+int master_hess_grid(int num_sms) { return 2 * num_sms; }
 
 cudaError_t master_configure() {
-    return cudaFuncSetAttribute(k_master_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)master_pass_smem(KMAX));
+    cudaError_t e = cudaFuncSetAttribute(k_master_eval, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)master_eval_smem(KMAX));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_master_hess, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-cudaError_t launch_master_init(MasterDev* st, int K, cudaStream_t stream, int* launches) {
-    k_master_init<<<1, KMAX, 0, stream>>>(st, K);
+cudaError_t launch_master_init(MasterDev* st, int K, const int* skip, cudaGraphConditionalHandle cond,
+                               int use_cond, cudaStream_t stream, int* launches) {
+    k_master_init<<<1, KMAX, 0, stream>>>(st, K, skip, cond, use_cond);
     ++*launches;
     return cudaGetLastError();
 }
 
-cudaError_t launch_master_pass(const float* slab, int V, int ld, int K, const MasterBuffers& mb,
-                               const uint8_t* vstruct, const StructTermsF* tf, const StructTermsD* td, int S,
-                               float* z_out, float* pi_out, int final_pass, cudaStream_t stream, int* launches) {
-    const int KP = (K + 3) / 4 * 4;
-    k_master_pass<<<mb.G, TILE, master_pass_smem(K), stream>>>(slab, V, ld, K, KP, mb.st, mb.H_part, mb.g_part,
-                                                               mb.F_part, mb.G, vstruct, tf, td, S, z_out, pi_out,
-                                                               final_pass);
+cudaError_t launch_master_eval(const MasterBuffers& mb, int V, int K, const uint8_t* vstruct, const StructTermsF* tf,
+                               int S, float* z_out, float* pi_out, int mode, const int* skip, cudaStream_t stream,
+                               int* launches) {
+    const int kw = master_kw(K);
+    k_master_eval<<<mb.grid[K], TILE, master_eval_smem(K), stream>>>(
+        mb.tmap[kw / 4], V, K, kw, mb.st, mb.act_rows, mb.act_hp, mb.act_count, mb.F_part, vstruct, tf, S, z_out,
+        pi_out, mode, skip);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_master_hess(const MasterBuffers& mb, int K, int mode, cudaStream_t stream, int* launches) {
+    k_master_hess<<<mb.GH, 256, master_hess_smem(K, mb.n_tiles), stream>>>(
+        mb.act_rows, mb.act_hp, mb.act_count, mb.n_tiles, K, master_kw(K), master_lanes(K), mb.st, mb.H_part,
+        mb.g_part, mb.gn_part, mb.GH, mode);
     ++*launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_master_reduce(int K, const MasterBuffers& mb, cudaStream_t stream, int* launches) {
-    const int warps = K * K + K + 1;
-    k_master_reduce<<<(warps + 7) / 8, 256, 0, stream>>>(mb.H_part, mb.g_part, mb.F_part, mb.G, mb.st);
+    const int outs = K * (K + 1) / 2 + 2 * K + 1;
+    k_master_reduce<<<(outs + 7) / 8, 256, 0, stream>>>(mb.H_part, mb.g_part, mb.gn_part, mb.F_part, mb.GH,
+                                                         mb.grid[K], mb.st);
     ++*launches;
     return cudaGetLastError();
 }
 
-cudaError_t launch_master_step(const MasterBuffers& mb, int max_iter, double tol_rel, cudaStream_t stream,
-                               int* launches) {
-    k_master_step<<<1, 256, 0, stream>>>(mb.st, max_iter, tol_rel, 1e-4);
+cudaError_t launch_master_step(const MasterBuffers& mb, int max_iter, double tol_rel,
+                               cudaGraphConditionalHandle cond, int use_cond, cudaStream_t stream, int* launches) {
+    k_master_step<<<1, STEP_T, 0, stream>>>(mb.st, max_iter, tol_rel, 1e-4, cond, use_cond);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_record(const MasterDev* st, CGDev* cg, int K, cudaStream_t stream, int* launches) {
+    k_cg_record<<<1, 32, 0, stream>>>(st, cg, K);
     ++*launches;
     return cudaGetLastError();
 }

@@ -27,10 +27,11 @@ constexpr unsigned FULL = 0xffffffffu;
 // row_info[g] = (beam, first beamlet index, columns, row within the beam)
 __global__ void __launch_bounds__(256) k_price_rows(const float* __restrict__ w, const int4* __restrict__ row_info,
                                                     int n_rows, double* __restrict__ row_v,
-                                                    int2* __restrict__ row_lr) {
+                                                    int2* __restrict__ row_lr, const int* __restrict__ skip) {
     const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (g >= n_rows) return;  // uniform per warp
+    if (skip != nullptr && *skip) return;
     const int4 ri = row_info[g];
     const int n = ri.z;
     const double wv = lane < n ? (double)w[ri.y + lane] : 0.0;
@@ -88,8 +89,9 @@ __global__ void __launch_bounds__(256) k_price_rows(const float* __restrict__ w,
 // One block: thread b sums beam b's rows in row order; thread 0 takes the argmin.
 __global__ void __launch_bounds__(256) k_price_beams(const double* __restrict__ row_v,
                                                      const int* __restrict__ beam_row0, int n_beams,
-                                                     PriceDev* __restrict__ out) {
+                                                     PriceDev* __restrict__ out, const int* __restrict__ skip) {
     extern __shared__ double s_sum[];
+    if (skip != nullptr && *skip) return;
     for (int b = threadIdx.x; b < n_beams; b += blockDim.x) {
         double t = 0.0;
         for (int r = beam_row0[b]; r < beam_row0[b + 1]; ++r) t = t + row_v[r];
@@ -105,20 +107,77 @@ __global__ void __launch_bounds__(256) k_price_beams(const double* __restrict__ 
     }
 }
 
+// One block.  Stops the solve (done = 1) when the reduced cost is not below
+// -tau, or (done = 2) when the priced aperture equals one in the pool;
+// otherwise writes it as aperture K-1 with its open-beamlet mask.
+__global__ void __launch_bounds__(256) k_cg_commit(const PriceDev* __restrict__ pr, const int2* __restrict__ row_lr,
+                                                   const int* __restrict__ beam_row0, const int* __restrict__ rows,
+                                                   const int* __restrict__ cols, double tau, int K, int lr_stride,
+                                                   int* __restrict__ ap_beam, int* __restrict__ ap_lr,
+                                                   float* __restrict__ mask, CGDev* __restrict__ cg) {
+    __shared__ int s_dup;
+    if (cg->done) return;
+    const int tid = threadIdx.x;
+    const int b = pr->beam;
+    if (!(pr->rc < -tau)) {
+        if (tid == 0) cg->done = 1;
+        return;
+    }
+    const int R = rows[b], C = cols[b], r0 = beam_row0[b];
+    if (tid == 0) s_dup = 0;
+    __syncthreads();
+    for (int k = tid; k < K - 1; k += blockDim.x) {
+        if (ap_beam[k] != b) continue;
+        bool same = true;
+        for (int r = 0; r < R && same; ++r) {
+            const int2 lr = row_lr[r0 + r];
+            same = ap_lr[k * lr_stride + 2 * r] == lr.x && ap_lr[k * lr_stride + 2 * r + 1] == lr.y;
+        }
+        if (same) s_dup = 1;
+    }
+    __syncthreads();
+    if (s_dup) {
+        if (tid == 0) cg->done = 2;
+        return;
+    }
+    if (tid == 0) ap_beam[K - 1] = b;
+    for (int r = tid; r < R; r += blockDim.x) {
+        const int2 lr = row_lr[r0 + r];
+        ap_lr[(K - 1) * lr_stride + 2 * r] = lr.x;
+        ap_lr[(K - 1) * lr_stride + 2 * r + 1] = lr.y;
+    }
+    for (int i = tid; i < R * C; i += blockDim.x) {
+        const int2 lr = row_lr[r0 + i / C];
+        const int c = i % C;
+        mask[i] = (c >= lr.x && c < lr.y) ? 1.f : 0.f;
+    }
+    if (tid == 0) cg->K = K;
+}
+
 }  // namespace
 
+cudaError_t launch_commit(const PriceDev* pr, const int2* row_lr, const int* beam_row0, const int* rows,
+                          const int* cols, double tau, int K, int lr_stride, int* ap_beam, int* ap_lr, float* mask,
+                          CGDev* cg, cudaStream_t stream, int* launches) {
+    k_cg_commit<<<1, 256, 0, stream>>>(pr, row_lr, beam_row0, rows, cols, tau, K, lr_stride, ap_beam, ap_lr, mask,
+                                       cg);
+    ++*launches;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_price(const float* w, const int4* row_info, int n_rows, const int* beam_row0, int n_beams,
-                         double* row_v, int2* row_lr, PriceDev* out, cudaStream_t stream, int* launches) {
+                         double* row_v, int2* row_lr, PriceDev* out, const int* skip, cudaStream_t stream,
+                         int* launches) {
     const int warps_per_block = 8;
     const int grid = (n_rows + warps_per_block - 1) / warps_per_block;
     if (grid > 0) {
-        k_price_rows<<<grid, 32 * warps_per_block, 0, stream>>>(w, row_info, n_rows, row_v, row_lr);
+        k_price_rows<<<grid, 32 * warps_per_block, 0, stream>>>(w, row_info, n_rows, row_v, row_lr, skip);
         ++*launches;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     k_price_beams<<<1, 256, (size_t)(n_beams > 0 ? n_beams : 1) * sizeof(double), stream>>>(row_v, beam_row0,
-                                                                                           n_beams, out);
+                                                                                           n_beams, out, skip);
     ++*launches;
     return cudaGetLastError();
 }

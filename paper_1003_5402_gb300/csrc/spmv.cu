@@ -110,8 +110,10 @@ __global__ void __launch_bounds__(256) k_sum_f64(const double* __restrict__ part
 template <int BT>
 __global__ void __launch_bounds__(BT) k_dt(const int* __restrict__ rowptr, const int4* __restrict__ col4,
                                            const float4* __restrict__ val4, int N,
-                                           const float* __restrict__ pi, float* __restrict__ w) {
+                                           const float* __restrict__ pi, float* __restrict__ w,
+                                           const int* __restrict__ skip) {
     __shared__ double s_red[BT / 32];
+    if (skip != nullptr && *skip) return;
     const int row = blockIdx.x;
     const int p0 = rowptr[row] >> 2, p1 = rowptr[row + 1] >> 2;
     float acc = 0.f;
@@ -131,13 +133,10 @@ __global__ void __launch_bounds__(BT) k_dt(const int* __restrict__ rowptr, const
 // G lanes per voxel row over the row's segment of beam b (columns base ..
 // base + nb - 1); mask[c] in {0, 1} marks the aperture's open beamlets.
 template <int G>
-__global__ void __launch_bounds__(256) k_column(const int* __restrict__ col, const float* __restrict__ val,
-                                                const int* __restrict__ seg_lo, const int* __restrict__ seg_hi,
-                                                int V, int base, int nb, const float* __restrict__ mask,
-                                                float* __restrict__ out) {
-    extern __shared__ float smask[];
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) smask[i] = mask[i];
-    __syncthreads();
+__device__ __forceinline__ void column_body(const int* __restrict__ col, const float* __restrict__ val,
+                                            const int* __restrict__ seg_lo, const int* __restrict__ seg_hi,
+                                            int V, int base, const float* smask, float* __restrict__ out,
+                                            int stride) {
     const int lane = threadIdx.x & 31;
     const int sub = lane % G;
     constexpr int RPW = 32 / G;
@@ -153,8 +152,36 @@ __global__ void __launch_bounds__(256) k_column(const int* __restrict__ col, con
         }
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-        if (row < V && sub == 0) out[row] = acc;
+        if (row < V && sub == 0) out[(size_t)row * stride] = acc;
     }
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) k_column(const int* __restrict__ col, const float* __restrict__ val,
+                                                const int* __restrict__ seg_lo, const int* __restrict__ seg_hi,
+                                                int V, int base, int nb, const float* __restrict__ mask,
+                                                float* __restrict__ out, int stride) {
+    extern __shared__ float smask[];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) smask[i] = mask[i];
+    __syncthreads();
+    column_body<G>(col, val, seg_lo, seg_hi, V, base, smask, out, stride);
+}
+
+// The same for the aperture at pool index K-1 of the device table.
+template <int G>
+__global__ void __launch_bounds__(256) k_column_dev(const int* __restrict__ col, const float* __restrict__ val,
+                                                    const int* __restrict__ seg, int V,
+                                                    const int* __restrict__ ap_beam, int K,
+                                                    const int* __restrict__ beam_off, const int* __restrict__ rows,
+                                                    const int* __restrict__ cols, const float* __restrict__ mask,
+                                                    float* __restrict__ out, int stride, const CGDev* __restrict__ cg) {
+    extern __shared__ float smask[];
+    if (cg->done) return;
+    const int b = ap_beam[K - 1];
+    const int nb = rows[b] * cols[b];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) smask[i] = mask[i];
+    __syncthreads();
+    column_body<G>(col, val, seg + (size_t)b * V, seg + (size_t)(b + 1) * V, V, beam_off[b], smask, out, stride);
 }
 
 // ---- Eq. 7 ------------------------------------------------------------------
@@ -220,20 +247,31 @@ cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct,
     return cudaGetLastError();
 }
 
-cudaError_t launch_dt(const DevCSR& Dt, const float* pi, float* w, cudaStream_t stream, int* launches) {
+cudaError_t launch_dt(const DevCSR& Dt, const float* pi, float* w, const int* skip, cudaStream_t stream,
+                      int* launches) {
     if (Dt.n_rows == 0) return cudaSuccess;
     k_dt<128><<<Dt.n_rows, 128, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
-                                              reinterpret_cast<const float4*>(Dt.val), Dt.n_rows, pi, w);
+                                              reinterpret_cast<const float4*>(Dt.val), Dt.n_rows, pi, w, skip);
     ++*launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_column(const DevCSR& D, const int* seg_lo, const int* seg_hi, int base, int nb,
-                          const float* mask, float* out, int num_sms, cudaStream_t stream, int* launches) {
+                          const float* mask, float* out, int stride, int num_sms, cudaStream_t stream, int* launches) {
     if (D.n_rows == 0) return cudaSuccess;
     const int grid = num_sms * 8;
     k_column<8><<<grid, 256, (size_t)nb * sizeof(float), stream>>>(D.col, D.val, seg_lo, seg_hi, D.n_rows, base,
-                                                                   nb, mask, out);
+                                                                   nb, mask, out, stride);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_column_dev(const DevCSR& D, const int* seg, const int* ap_beam, int K, const int* beam_off,
+                              const int* rows, const int* cols, int max_nb, const float* mask, float* out, int stride,
+                              const CGDev* cg, int num_sms, cudaStream_t stream, int* launches) {
+    if (D.n_rows == 0) return cudaSuccess;
+    k_column_dev<8><<<num_sms * 8, 256, (size_t)max_nb * sizeof(float), stream>>>(
+        D.col, D.val, seg, D.n_rows, ap_beam, K, beam_off, rows, cols, mask, out, stride, cg);
     ++*launches;
     return cudaGetLastError();
 }

@@ -47,7 +47,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_options_default_on_host(lib):
     from paper_1003_5402_gb300 import binding
     o = binding.options()
-    assert o.k_max == 64 and o.max_master_iters == 100 and o.precision == 0
+    assert o.k_max == 64 and o.max_master_iters == 50 and o.precision == 0
     assert o.master_tol == 1e-6
 
 

@@ -212,3 +212,42 @@ def test_prostate_full_size_properties(torch):
     for k in range(5):
         assert aps[k][0] == ref.apertures[k][0] and np.array_equal(aps[k][1], ref.apertures[k][1]), k
     assert np.all(np.abs(trace[:5] - ref.objective) <= RTOL_F * np.array(ref.objective))
+
+
+@pytest.mark.parametrize("name,K", [("micro", 30), ("tiny", 20)])
+def test_graph_rounds_equal_host_driven_rounds(torch, name, K):
+    """dao_solve as CUDA graphs (device-side while loop, no host synchronisation
+    between rounds) gives bit-identical results to host-driven launches."""
+    case = P.make_case(P.CONFIGS[name]())
+    out = []
+    for g in (1, 0):
+        with _plan(case, torch, use_graphs=g) as plan:
+            st, n, trace = plan.solve(K)
+            aps = plan.apertures()
+            y = plan.intensities()
+            z, F = plan.dose()
+            ev, stt, kkt = plan.master_stats()
+            out.append((st, n, trace, aps, y, z, F, ev, stt))
+    a, b = out
+    assert a[0] == b[0] and a[1] == b[1]
+    assert np.array_equal(a[2], b[2]) and np.array_equal(a[4], b[4]) and np.array_equal(a[5], b[5]) and a[6] == b[6]
+    assert all(x[0] == y_[0] and np.array_equal(x[1], y_[1]) for x, y_ in zip(a[3], b[3]))
+    assert np.array_equal(a[7], b[7]) and np.array_equal(a[8], b[8])
+
+
+def test_graph_solve_in_chunks_and_after_host_rounds(torch):
+    """Rounds split across calls, and graph rounds after host-driven ones, continue
+    the same column generation."""
+    case = P.make_case(P.spec_micro())
+    with _plan(case, torch) as plan:
+        _, _, t_all = plan.solve(12)
+        aps_all = plan.apertures()
+    with _plan(case, torch) as plan:
+        st, b, lv, rc = plan.price()
+        plan.add_aperture(b, lv)
+        _, _, t1 = plan.solve(4)
+        _, _, t2 = plan.solve(7)
+        aps = plan.apertures()
+    assert len(aps) == 12
+    assert all(x[0] == y_[0] and np.array_equal(x[1], y_[1]) for x, y_ in zip(aps, aps_all))
+    assert np.array_equal(np.concatenate([t1, t2]), t_all[1:])
