@@ -227,6 +227,37 @@ int64_t dao_launch_count(const dao_ctx* ctx);
  * ||y - P(y - g)||_inf divided by max|g| at the warm start; *k = solves. */
 dao_status dao_master_stats(const dao_ctx* ctx, int32_t* evals, int32_t* status, double* kkt, int32_t* k);
 
+/* ---- allocation-free dose with objective (the paper has no counterpart) ----
+ * For callers that must not allocate device memory while they run, e.g. a
+ * re-planning service that reserves every device buffer before an online
+ * adaptive fraction (so that the fraction cannot fail on an allocation or stall
+ * on the synchronisation cudaMalloc / cudaFree may imply), or an application
+ * whose own allocator owns the device.  It computes what dao_k_dose computes,
+ * z = D x, grad F(z) and F(z) of Eqs. 1, 5, 9, 10, without a context and
+ * without allocating: it calls no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *   D: voxel-major CSR on the device, int32 row_ptr[n_voxels + 1], col[nnz],
+ *      float val[nnz] (rows need no padding); x: device float[n_beamlets];
+ *   voxel_struct: device int32[n_voxels], labels in [0, n_structures);
+ *   terms: host double[n_structures][4] = alpha_s / |v_s|, T_s^-,
+ *      beta_s / |v_s|, T_s^+ (the per-structure form of Eqs. 9-10);
+ *   z: device float[n_voxels]; grad: device float[n_voxels] or NULL;
+ *   objective: device double, F(z); stream: cudaStream_t or NULL.
+ * Limits: n_voxels <= 4,194,304 and n_structures <= 64, else DAO_EINVAL with a
+ * message.  Scratch: the per-block partial sums of F live in a 32 KiB
+ * file-scope device array that every GPU loading the library keeps until the
+ * process exits; every block overwrites its own entry on each call, so nothing
+ * needs clearing, and the array keeps the last call's contents.  All calls on
+ * a device share that array: calls whose kernels overlap on the GPU (for
+ * example on different streams) race and give wrong objectives.  The first
+ * call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  Asynchronous:
+ * results are ready when the stream reaches them. */
+dao_status dao_dose_objective_noalloc(int32_t n_voxels, int32_t n_beamlets, const int32_t* row_ptr,
+                                      const int32_t* col, const float* val, const float* x,
+                                      const int32_t* voxel_struct, int32_t n_structures, const double* terms,
+                                      float* z, float* grad, double* objective, void* stream);
+
 const char* dao_last_error(void);
 
 #ifdef __cplusplus

@@ -74,6 +74,8 @@ SIGNATURES = {
     "dao_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), _F64P]),
     "dao_launch_count": (C.c_int64, [_P]),
     "dao_master_stats": (C.c_int, [_P, _I32P, _I32P, _F64P, _I32P]),
+    "dao_dose_objective_noalloc": (C.c_int, [C.c_int32, C.c_int32, _P, _P, _P, _P, _P, C.c_int32, _F64P, _P, _P,
+                                             _P, _P]),
     "dao_last_error": (C.c_char_p, []),
 }
 
@@ -308,3 +310,16 @@ class Plan:
                                        C.byref(k)), "dao_master_stats")
         n = k.value
         return ev[:n].copy(), stt[:n].copy(), kkt[:n].copy()
+
+
+def dose_objective_noalloc(row_ptr, col, val, x, voxel_struct, terms, z, grad=None, objective=None, stream=None):
+    """dao_dose_objective_noalloc on torch CUDA tensors (int32 row_ptr / col /
+    voxel_struct, float32 val / x / z / grad, float64 objective of one element)
+    and a host float64 terms array [n_structures, 4]; returns the status."""
+    t = np.ascontiguousarray(terms, dtype=np.float64).reshape(-1, 4)
+    st = load().dao_dose_objective_noalloc(
+        int(z.numel()), int(x.numel()), _dev(row_ptr, "int32"), _dev(col, "int32"), _dev(val, "float32"),
+        _dev(x, "float32"), _dev(voxel_struct, "int32"), int(t.shape[0]), _ptr(t, C.c_double), _dev(z, "float32"),
+        _dev(grad, "float32") if grad is not None else None, _dev(objective, "float64"),
+        C.c_void_p(stream) if stream is not None else None)
+    return _check(st, "dao_dose_objective_noalloc")

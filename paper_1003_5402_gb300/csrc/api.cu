@@ -39,6 +39,8 @@ inline int64_t round4(int64_t n) { return (n + 3) / 4 * 4; }
 
 }  // namespace
 
+dao_status dao::set_error(dao_status s, const std::string& msg) { return fail(s, msg); }
+
 struct ProfRecord {
     int kc;
     cudaEvent_t start, stop;

@@ -12,6 +12,9 @@
 
 namespace dao {
 
+// Record the calling thread's error message for dao_last_error(); returns s.
+dao_status set_error(dao_status s, const std::string& msg);
+
 constexpr int KMAX = 64;        // aperture pool capacity (master problem size)
 constexpr int SMAX = 64;        // structures
 constexpr int CMAX = 32;        // beamlets per MLC row (one warp lane each)
