@@ -374,8 +374,8 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     return DAO_OK;
 }
 
-// 2-D tensor maps over the voxel-major slab (KROW floats per voxel row), one per
-// tile row width: box = (width, MASTER_TILE) starting at column 0.
+// 2-D tensor maps over the column-major slab (column k = aperture k, stride
+// ld floats): box = (MASTER_TILE voxels, KP columns), one map per KP.
 dao_status make_tensor_maps(dao_ctx* c) {
     typedef CUresult (*encode_fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -386,18 +386,15 @@ dao_status make_tensor_maps(dao_ctx* c) {
     if (fn == nullptr || q != cudaDriverEntryPointSuccess) return fail(DAO_ECUDA, "cuTensorMapEncodeTiled unavailable");
     encode_fn encode = reinterpret_cast<encode_fn>(fn);
     std::memset(c->mb.tmap, 0, sizeof(c->mb.tmap));
-    for (int k = 0; k <= KMAX; ++k) {
-        const int kw = master_kw(k);
-        if (c->mb.tmap_ready[kw / 4]) continue;
-        const cuuint64_t dims[2] = {(cuuint64_t)KROW, (cuuint64_t)c->ld};
-        const cuuint64_t strides[1] = {(cuuint64_t)KROW * sizeof(float)};
-        const cuuint32_t box[2] = {(cuuint32_t)kw, (cuuint32_t)MASTER_TILE};
+    for (int kp = 4; kp <= KMAX; kp += 4) {
+        const cuuint64_t dims[2] = {(cuuint64_t)c->ld, (cuuint64_t)KMAX};
+        const cuuint64_t strides[1] = {(cuuint64_t)c->ld * sizeof(float)};
+        const cuuint32_t box[2] = {(cuuint32_t)MASTER_TILE, (cuuint32_t)kp};
         const cuuint32_t estr[2] = {1, 1};
-        CUresult r = encode(&c->mb.tmap[kw / 4], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->slab, dims, strides, box, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+        CUresult r = encode(&c->mb.tmap[kp / 4], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->slab, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(DAO_ECUDA, "cuTensorMapEncodeTiled failed with " + std::to_string((int)r));
-        c->mb.tmap_ready[kw / 4] = true;
     }
     return DAO_OK;
 }
@@ -405,9 +402,9 @@ dao_status make_tensor_maps(dao_ctx* c) {
 dao_status alloc_state(dao_ctx* c) {
     c->K_cap = c->opt.k_max;
     c->mb.n_tiles = (c->V + MASTER_TILE - 1) / MASTER_TILE;
-    c->ld = c->mb.n_tiles * MASTER_TILE;  // voxel rows of the slab, zero padded to whole tiles
-    DAO_TRY(c->dalloc(&c->slab, (size_t)c->ld * KROW));
-    DAO_CU(cudaMemset(c->slab, 0, (size_t)c->ld * KROW * sizeof(float)));
+    c->ld = c->mb.n_tiles * MASTER_TILE;  // column stride: voxels zero padded to whole tiles
+    DAO_TRY(c->dalloc(&c->slab, (size_t)c->ld * KMAX));
+    DAO_CU(cudaMemset(c->slab, 0, (size_t)c->ld * KMAX * sizeof(float)));
     DAO_TRY(make_tensor_maps(c));
     DAO_TRY(c->dalloc(&c->ap_beam, c->K_cap));
     DAO_TRY(c->dalloc(&c->ap_lr, (size_t)c->K_cap * 2 * c->max_rows));
@@ -573,7 +570,7 @@ dao_status add_column(dao_ctx* c, int beam, const int32_t* lr, float* out, int s
 
 dao_status add_aperture(dao_ctx* c, int beam, const int32_t* lr, double* F) {
     if (c->K >= c->K_cap) return fail(DAO_ESTATE, "aperture pool is full (k_max)");
-    DAO_TRY(add_column(c, beam, lr, c->slab + c->K, KROW));
+    DAO_TRY(add_column(c, beam, lr, c->slab + (size_t)c->K * c->ld, 1));
     const int stride = 2 * c->max_rows;
     c->ap_beam_h.push_back(beam);
     c->ap_lr_h.resize((size_t)(c->K + 1) * stride, 0);
@@ -620,7 +617,7 @@ dao_status build_round_graph(dao_ctx* c, int K) {
             check(launch_commit(c->price, c->row_lr, c->beam_row0_d, c->rows_d, c->cols_d, c->tau, K,
                                 2 * c->max_rows, c->ap_beam, c->ap_lr, c->mask, c->cg, cs, &n));
             check(launch_column_dev(c->D, c->seg, c->ap_beam, K, c->beam_off_d, c->rows_d, c->cols_d, c->max_nb,
-                                    c->mask, c->slab + (K - 1), KROW, c->cg, c->num_sms, cs, &n));
+                                    c->mask, c->slab + (size_t)(K - 1) * c->ld, 1, c->cg, c->num_sms, cs, &n));
             check(launch_master_init(c->mb.st, K, skip, h, 1, cs, &n));
             cudaStreamCaptureStatus cst;
             const cudaGraphNode_t* d = nullptr;
@@ -994,6 +991,33 @@ dao_status dao_k_state(dao_ctx* c, float* z, float* pi) {
     return DAO_OK;
 }
 
+namespace {
+// One launch of kernel class kc for dao_k_time.
+cudaError_t time_one(dao_ctx* c, int kc, int K, cudaStream_t s, int* n) {
+    switch (kc) {
+        case DAO_KC_MASTER_PASS:
+            return launch_master_eval(c->mb, c->V, K, c->vstruct, c->tf, c->S, nullptr, nullptr, PASS_TIMING, nullptr,
+                                      s, n);
+        case DAO_KC_MASTER_HESS:
+            return launch_master_hess(c->mb, K, PASS_TIMING, s, n);
+        case DAO_KC_DT:
+            return launch_dt(c->Dt, c->pi, c->w, nullptr, s, n);
+        case DAO_KC_DOSE:
+            return launch_dose(c->D, c->x, c->vstruct, c->tf, c->td, c->S, c->dose, nullptr, nullptr, 0, nullptr,
+                               c->num_sms, s, n);
+        case DAO_KC_COLUMN: {
+            const int b = c->ap_beam_h[0];
+            return launch_column(c->D, c->seg + (size_t)b * c->V, c->seg + (size_t)(b + 1) * c->V, c->beam_off[b],
+                                 c->rows[b] * c->cols[b], c->mask, c->dose, 1, c->num_sms, s, n);
+        }
+        case DAO_KC_PRICE:
+            return launch_price(c->w, c->row_info, c->R_tot, c->beam_row0_d, c->B, c->row_v, c->row_lr, c->price,
+                                nullptr, s, n);
+    }
+    return cudaErrorInvalidValue;
+}
+}  // namespace
+
 dao_status dao_k_time(dao_ctx* c, int32_t kc, int32_t K, int32_t reps, double* us_per_launch) {
     DAO_TRY(check_ctx(c));
     if (reps < 1 || !us_per_launch) return fail(DAO_EINVAL, "reps must be >= 1 and the output non-null");
@@ -1003,46 +1027,32 @@ dao_status dao_k_time(dao_ctx* c, int32_t kc, int32_t K, int32_t reps, double* u
     if (kc != DAO_KC_MASTER_PASS && kc != DAO_KC_MASTER_HESS && kc != DAO_KC_DT && kc != DAO_KC_DOSE &&
         kc != DAO_KC_COLUMN && kc != DAO_KC_PRICE)
         return fail(DAO_EINVAL, "kernel class cannot be timed on its own");
-    cudaEvent_t e0 = c->event(), e1 = c->event();
-    if (!e0 || !e1) return fail(DAO_ECUDA, "cudaEventCreate failed");
+    // the reps launches are captured into a graph so that they run back to back on
+    // the device, without host launch gaps, between the two events
+    DAO_TRY(sync(c));
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
     int n = 0;
-    DAO_TRY(sync(c));
-    DAO_CU(cudaEventRecord(e0, c->stream));
-    for (int r = 0; r < reps; ++r) {
-        switch (kc) {
-            case DAO_KC_MASTER_PASS:
-                DAO_CU(launch_master_eval(c->mb, c->V, K, c->vstruct, c->tf, c->S, nullptr, nullptr, PASS_TIMING,
-                                          nullptr, c->stream, &n));
-                break;
-            case DAO_KC_MASTER_HESS:
-                DAO_CU(launch_master_hess(c->mb, K, PASS_TIMING, c->stream, &n));
-                break;
-            case DAO_KC_DT:
-                DAO_CU(launch_dt(c->Dt, c->pi, c->w, nullptr, c->stream, &n));
-                break;
-            case DAO_KC_DOSE:
-                DAO_CU(launch_dose(c->D, c->x, c->vstruct, c->tf, c->td, c->S, c->dose, nullptr, nullptr, 0, nullptr,
-                                   c->num_sms, c->stream, &n));
-                break;
-            case DAO_KC_COLUMN: {
-                const int b = c->ap_beam_h[0];
-                DAO_CU(launch_column(c->D, c->seg + (size_t)b * c->V, c->seg + (size_t)(b + 1) * c->V,
-                                     c->beam_off[b], c->rows[b] * c->cols[b], c->mask, c->dose, 1, c->num_sms,
-                                     c->stream, &n));
-                break;
-            }
-            case DAO_KC_PRICE:
-                DAO_CU(launch_price(c->w, c->row_info, c->R_tot, c->beam_row0_d, c->B, c->row_v, c->row_lr, c->price,
-                                    nullptr, c->stream, &n));
-                break;
-        }
-    }
-    DAO_CU(cudaEventRecord(e1, c->stream));
-    DAO_TRY(sync(c));
+    DAO_CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = time_one(c, kc, K, c->stream, &n);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    cudaEvent_t e0 = c->event(), e1 = c->event();
     float ms = 0.f;
-    DAO_CU(cudaEventElapsedTime(&ms, e0, e1));
-    c->ev_used -= 2;
-    c->launches_i += n;
+    if (e == cudaSuccess && (!e0 || !e1)) e = cudaErrorUnknown;
+    if (e == cudaSuccess) e = cudaGraphLaunch(ex, c->stream);  // warm
+    if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ex, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (ex) cudaGraphExecDestroy(ex);
+    if (g) cudaGraphDestroy(g);
+    if (e0 && e1) c->ev_used -= 2;
+    if (e != cudaSuccess) return fail(DAO_ECUDA, std::string("dao_k_time: ") + cudaGetErrorString(e));
+    c->launches_i += 2 * n;
     c->count_launches();
     *us_per_launch = 1e3 * ms / reps;
     return DAO_OK;

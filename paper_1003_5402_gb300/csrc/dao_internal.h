@@ -19,7 +19,7 @@ constexpr int KMAX = 64;        // aperture pool capacity (master problem size)
 constexpr int SMAX = 64;        // structures
 constexpr int CMAX = 32;        // beamlets per MLC row (one warp lane each)
 constexpr int MASTER_TILE = 256;  // voxels per tile of the master evaluation (= block size)
-constexpr int KROW = KMAX + 4;    // row stride (floats) of the voxel-major aperture slab
+constexpr int KROW = KMAX + 4;    // row stride (floats) of the active-voxel rows (odd float4 count)
 
 // Per-structure objective terms (Eqs. 9-10): a = alpha_s/|v_s| (0 for
 // non-targets), tu = T_s^-, b = beta_s/|v_s|, to = T_s^+.
@@ -33,9 +33,13 @@ struct DevCSR {
     int n_rows = 0;
     int n_cols = 0;
     int64_t nnz_stored = 0;
-    int* rowptr = nullptr;   // n_rows + 1, multiples of 4
-    int* col = nullptr;
-    float* val = nullptr;
+    int prec = 0;            // DAO_PREC_FP32 / FP16 / BF16
+    int* rowptr = nullptr;   // n_rows + 1; multiples of 4 (FP32) or 8 (16-bit values)
+    int* col = nullptr;      // FP32 layout, and the voxel indices of a 16-bit D^T
+    float* val = nullptr;    // FP32 values
+    unsigned short* col16 = nullptr;  // 16-bit layout of D: beamlet indices
+    unsigned short* val16 = nullptr;  // 16-bit values D_ij / s_i (FP16 or BF16 bits)
+    const float* scale = nullptr;     // 16-bit layout: per-beamlet scale s_i (length n_beamlets)
 };
 
 // Projected-Newton master state (device memory, one per context).
@@ -133,8 +137,7 @@ struct MasterBuffers {
     double* F_part = nullptr;   // [max evaluation grid]
     int GH = 0;                 // blocks of the curvature kernel
     int grid[KMAX + 1] = {};    // blocks of the evaluation kernel for each pool size
-    CUtensorMap tmap[KROW / 4 + 1];  // slab tile maps, indexed by row width / 4
-    bool tmap_ready[KROW / 4 + 1] = {};
+    CUtensorMap tmap[KMAX / 4 + 1];  // slab tile maps, indexed by columns / 4
 };
 enum { PASS_EVAL = 0, PASS_FINAL = 1, PASS_TIMING = 2 };
 int master_kw(int K);

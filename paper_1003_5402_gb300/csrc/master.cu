@@ -1,7 +1,7 @@
 // Master problem of column-generation DAO (arXiv:1003.5402, Sec. 2.2-2.3):
 // min_y F(S y) subject to y >= 0 over the current aperture pool, where column k
-// of the slab S (V x K, FP32) is the aperture dose D_kj of Eq. 2.  The slab is
-// stored voxel-major: row j holds the K doses of voxel j (row stride KROW).
+// of the slab S (V x K, FP32, column-major with stride ld) is the aperture dose
+// D_kj of Eq. 2.
 //
 // The paper uses gradient projection and gives no step or stopping rule.  This
 // is a scaled gradient projection, the projected Newton method of Bertsekas
@@ -159,8 +159,11 @@ __global__ void k_cg_record(const MasterDev* __restrict__ st, CGDev* __restrict_
 }
 
 // ---- evaluation: one slab tile per iteration --------------------------------
+// The slab is column-major (column k = the doses of aperture k over all voxels,
+// stride ld); a tile is the box of KP columns x TILE voxels, landing in shared
+// memory as [KP][TILE].
 __global__ void __launch_bounds__(TILE, 3) k_master_eval(const __grid_constant__ CUtensorMap tmap, int V, int K,
-                                                         int KW, MasterDev* __restrict__ st,
+                                                         int KP, MasterDev* __restrict__ st,
                                                          float* __restrict__ act_rows, float2* __restrict__ act_hp,
                                                          int* __restrict__ act_count, double* __restrict__ F_part,
                                                          const uint8_t* __restrict__ vstruct,
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(TILE, 3) k_master_eval(const __grid_constant__
     if (skip != nullptr && *skip) return;
     if (mode == PASS_EVAL && st->done) return;
     const bool final_pass = mode == PASS_FINAL;
-    extern __shared__ __align__(128) float As[];  // [TILE][KW]: rows of the tile's voxels
+    extern __shared__ __align__(128) float As[];  // [KP][TILE]
     __shared__ __align__(8) unsigned long long bar;
     __shared__ float s_yh[KMAX], s_yl[KMAX];
     __shared__ int s_wcount[TILE / 32];
@@ -191,29 +194,27 @@ __global__ void __launch_bounds__(TILE, 3) k_master_eval(const __grid_constant__
     unsigned parity = 0;
     bool lost = false;
     const int n_tiles = (V + TILE - 1) / TILE;
-    const int nq = (K + 3) / 4;  // float4 groups holding the K doses
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         __syncthreads();  // every thread is done with the previous tile's buffers
-        if (tid == 0) {
-            mbar_expect_tx(&bar, (unsigned)(TILE * KW * sizeof(float)));
-            tma_load_2d(As, &tmap, 0, tile * TILE, &bar);
+        if (tid == 0 && KP > 0) {
+            mbar_expect_tx(&bar, (unsigned)(TILE * KP * sizeof(float)));
+            tma_load_2d(As, &tmap, tile * TILE, 0, &bar);
         }
-        if (!mbar_wait(&bar, parity)) {
-            lost = true;
-            break;
+        if (KP > 0) {
+            if (!mbar_wait(&bar, parity)) {
+                lost = true;
+                break;
+            }
+            parity ^= 1u;
         }
-        parity ^= 1u;
         const int j = tile * TILE + tid;
-        // ---- compensated z from this voxel's row, four chains
-        const float4* row = reinterpret_cast<const float4*>(As + tid * KW);
+        // ---- compensated z from this voxel's column of the tile, four chains
         float sc[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int q = 0; q < nq; ++q) {
-            const float4 a = row[q];
-            const int k = 4 * q;  // doses beyond K are zero in the slab
-            dot2_step(sc[0], cc[0], a.x, s_yh[k], s_yl[k]);
-            dot2_step(sc[1], cc[1], a.y, s_yh[k + 1], s_yl[k + 1]);
-            dot2_step(sc[2], cc[2], a.z, s_yh[k + 2], s_yl[k + 2]);
-            dot2_step(sc[3], cc[3], a.w, s_yh[k + 3], s_yl[k + 3]);
+        for (int k = 0; k < KP; k += 4) {  // doses of columns K..KP-1 meet y = 0
+            dot2_step(sc[0], cc[0], As[k * TILE + tid], s_yh[k], s_yl[k]);
+            dot2_step(sc[1], cc[1], As[(k + 1) * TILE + tid], s_yh[k + 1], s_yl[k + 1]);
+            dot2_step(sc[2], cc[2], As[(k + 2) * TILE + tid], s_yh[k + 2], s_yl[k + 2]);
+            dot2_step(sc[3], cc[3], As[(k + 3) * TILE + tid], s_yh[k + 3], s_yl[k + 3]);
         }
         float s = sc[0], c = cc[0];
 #pragma unroll
@@ -254,7 +255,9 @@ __global__ void __launch_bounds__(TILE, 3) k_master_eval(const __grid_constant__
         if (act) {
             const size_t slot = (size_t)tile * TILE + base + __popc(bal & ((1u << lane) - 1u));
             float4* dst = reinterpret_cast<float4*>(act_rows + slot * KROW);
-            for (int q = 0; q < nq; ++q) dst[q] = row[q];
+            for (int k = 0; k < KP; k += 4)
+                dst[k / 4] = make_float4(As[k * TILE + tid], As[(k + 1) * TILE + tid], As[(k + 2) * TILE + tid],
+                                         As[(k + 3) * TILE + tid]);
             act_hp[slot] = make_float2(h, p);
         }
         if (tid == 0) act_count[tile] = n_act;
@@ -531,6 +534,7 @@ __device__ __forceinline__ int blk_or(int v, int* swi) {
 __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int max_iter, double tol_rel,
                                                  double sigma) {
     __shared__ float L[KMAX][KMAX + 1];
+    __shared__ float Hf[KMAX][KMAX + 1];
     __shared__ float rhs[KMAX];
     __shared__ int fidx[KMAX];
     __shared__ double sw[STEP_W];
@@ -624,57 +628,79 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     if (fr) fidx[pos] = k;
     double d = active ? -gt : 0.0;
     __syncthreads();
-    // damped FP32 Cholesky of H_FF, retried with a larger shift if a pivot fails
+    // damped FP32 Cholesky of H_FF (right-looking, one barrier per column: every
+    // thread takes the pivot's square root itself, and a column is scaled one
+    // step late, when no thread reads it any more), retried with a larger shift
+    // if a pivot fails
+    for (int idx = k; idx < nf * nf; idx += STEP_T) {
+        const int i = idx / nf, jj = idx % nf;
+        Hf[i][jj] = (float)st->Ht[fidx[i] * KMAX + fidx[jj]];
+    }
+    __syncthreads();
     float maxdiag = 0.f;
-    for (int i = 0; i < nf; ++i) maxdiag = fmaxf(maxdiag, (float)st->Ht[fidx[i] * KMAX + fidx[i]]);
+    for (int i = 0; i < nf; ++i) maxdiag = fmaxf(maxdiag, Hf[i][i]);
     float lam = 1e-6f * maxdiag + 1e-30f;
     bool ok = false;
     for (int attempt = 0; attempt < 6 && !ok; ++attempt) {
         for (int idx = k; idx < nf * nf; idx += STEP_T) {
             const int i = idx / nf, jj = idx % nf;
-            L[i][jj] = (float)st->Ht[fidx[i] * KMAX + fidx[jj]] + (i == jj ? lam : 0.f);
+            L[i][jj] = Hf[i][jj] + (i == jj ? lam : 0.f);
         }
-        if (k == 0) s_ok = 1;
         __syncthreads();
+        ok = true;
         for (int jj = 0; jj < nf; ++jj) {
-            if (k == 0) {
-                const float pv = L[jj][jj];
-                if (!(pv > 0.f) || !isfinite(pv))
-                    s_ok = 0;
-                else
-                    L[jj][jj] = sqrtf(pv);
+            const float pv = L[jj][jj];
+            if (!(pv > 0.f) || !isfinite(pv)) {  // every thread sees the same pivot
+                ok = false;
+                break;
             }
-            __syncthreads();
-            if (!s_ok) break;
-            const float ljj = L[jj][jj];
-            for (int i = jj + 1 + k; i < nf; i += STEP_T) L[i][jj] /= ljj;
-            __syncthreads();
+            const float inv = 1.f / sqrtf(pv);
             const int m = nf - jj - 1;
             for (int idx = k; idx < m * m; idx += STEP_T) {
                 const int i = jj + 1 + idx / m, q = jj + 1 + idx % m;
-                if (q <= i) L[i][q] -= L[i][jj] * L[q][jj];
+                if (q <= i) L[i][q] -= (L[i][jj] * inv) * (L[q][jj] * inv);
             }
             __syncthreads();
         }
-        ok = s_ok != 0;
+        if (ok) {  // scale the columns: L[i][j] /= sqrt(pivot j); the diagonal becomes sqrt(pivot)
+            for (int idx = k; idx < nf * nf; idx += STEP_T) {
+                const int i = idx / nf, jj = idx % nf;
+                if (jj < i) L[i][jj] = L[i][jj] / sqrtf(L[jj][jj]);
+            }
+            __syncthreads();
+            for (int i = k; i < nf; i += STEP_T) L[i][i] = sqrtf(L[i][i]);
+            __syncthreads();
+        }
         lam *= 100.f;
         __syncthreads();
     }
     if (ok) {
-        if (k < nf) rhs[k] = -(float)st->g[fidx[k]];
+        // forward and back substitution by warp 0, lanes owning rows lane and lane + 32
+        if (k < 32) {
+            float b0 = k < nf ? -(float)st->g[fidx[k]] : 0.f;
+            float b1 = k + 32 < nf ? -(float)st->g[fidx[k + 32]] : 0.f;
+            for (int jj = 0; jj < nf; ++jj) {  // L u = -g_F
+                const float bj = __shfl_sync(FULL, jj < 32 ? b0 : b1, jj & 31);
+                const float xj = bj / L[jj][jj];
+                if (k == (jj & 31)) {
+                    if (jj < 32) b0 = xj; else b1 = xj;
+                }
+                if (k > jj && k < nf) b0 -= L[k][jj] * xj;
+                if (k + 32 > jj && k + 32 < nf) b1 -= L[k + 32][jj] * xj;
+            }
+            for (int jj = nf - 1; jj >= 0; --jj) {  // L^T d = u
+                const float bj = __shfl_sync(FULL, jj < 32 ? b0 : b1, jj & 31);
+                const float xj = bj / L[jj][jj];
+                if (k == (jj & 31)) {
+                    if (jj < 32) b0 = xj; else b1 = xj;
+                }
+                if (k < jj) b0 -= L[jj][k] * xj;
+                if (k + 32 < jj) b1 -= L[jj][k + 32] * xj;
+            }
+            rhs[k] = b0;
+            rhs[k + 32] = b1;
+        }
         __syncthreads();
-        for (int jj = 0; jj < nf; ++jj) {  // L u = -g_F
-            if (k == 0) rhs[jj] /= L[jj][jj];
-            __syncthreads();
-            for (int i = jj + 1 + k; i < nf; i += STEP_T) rhs[i] -= L[i][jj] * rhs[jj];
-            __syncthreads();
-        }
-        for (int jj = nf - 1; jj >= 0; --jj) {  // L^T d = u
-            if (k == 0) rhs[jj] /= L[jj][jj];
-            __syncthreads();
-            for (int i = k; i < jj; i += STEP_T) rhs[i] -= L[jj][i] * rhs[jj];
-            __syncthreads();
-        }
         if (fr) d = (double)rhs[pos];
     } else if (fr) {
         const double hk = st->Ht[k * KMAX + k];
@@ -709,7 +735,10 @@ int master_kw(int K) {
     return kw;
 }
 
-size_t master_eval_smem(int K) { return (size_t)TILE * master_kw(K) * sizeof(float); }
+size_t master_eval_smem(int K) {
+    const int KP = (K + 3) / 4 * 4;
+    return (size_t)TILE * (KP > 0 ? KP : 4) * sizeof(float);
+}
 
 size_t master_hess_smem(int K, int n_tiles) {
     return (size_t)((n_tiles + 1 + 3) / 4 * 4) * sizeof(int) + (size_t)CH * master_kw(K) * sizeof(float) +
@@ -759,9 +788,9 @@ cudaError_t launch_master_init(MasterDev* st, int K, const int* skip, cudaGraphC
 cudaError_t launch_master_eval(const MasterBuffers& mb, int V, int K, const uint8_t* vstruct, const StructTermsF* tf,
                                int S, float* z_out, float* pi_out, int mode, const int* skip, cudaStream_t stream,
                                int* launches) {
-    const int kw = master_kw(K);
+    const int KP = (K + 3) / 4 * 4;
     k_master_eval<<<mb.grid[K], TILE, master_eval_smem(K), stream>>>(
-        mb.tmap[kw / 4], V, K, kw, mb.st, mb.act_rows, mb.act_hp, mb.act_count, mb.F_part, vstruct, tf, S, z_out,
+        mb.tmap[KP / 4], V, K, KP, mb.st, mb.act_rows, mb.act_hp, mb.act_count, mb.F_part, vstruct, tf, S, z_out,
         pi_out, mode, skip);
     ++*launches;
     return cudaGetLastError();

@@ -6,6 +6,9 @@
 // All reductions have a fixed order (per-lane sequential, then a fixed
 // shuffle tree, then fixed-order shared-memory combination), so every result
 // is bitwise reproducible for a given launch shape.  No atomics.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "dao_internal.h"
 
 namespace dao {
@@ -201,6 +204,192 @@ __global__ void k_fluence(const int* __restrict__ ap_beam, const int* __restrict
     x[i] = (float)s;
 }
 
+// ---- 16-bit storage (a6): values D_ij / s_i in FP16 or BF16, per-beamlet FP32
+// scale s_i, FP32 accumulation ------------------------------------------------
+template <bool BF>
+__device__ __forceinline__ float2 unpack2(unsigned w) {
+    if (BF) {
+        __nv_bfloat162 h;
+        *reinterpret_cast<unsigned*>(&h) = w;
+        return __bfloat1622float2(h);
+    } else {
+        __half2 h;
+        *reinterpret_cast<unsigned*>(&h) = w;
+        return __half22float2(h);
+    }
+}
+
+template <bool BF>
+__device__ __forceinline__ float unpack1(unsigned short b) {
+    if (BF) {
+        __nv_bfloat16 h;
+        *reinterpret_cast<unsigned short*>(&h) = b;
+        return __bfloat162float(h);
+    } else {
+        __half h;
+        *reinterpret_cast<unsigned short*>(&h) = b;
+        return __half2float(h);
+    }
+}
+
+// a1 with rows padded to 8 entries: uint4 loads of 8 uint16 columns and 8 values;
+// x pre-multiplied by the beamlet scale in shared memory.
+template <int G, bool BF>
+__global__ void __launch_bounds__(256) k_dose16(const int* __restrict__ rowptr, const uint4* __restrict__ col8,
+                                                const uint4* __restrict__ val8, int V, const float* __restrict__ x,
+                                                const float* __restrict__ scale, int N,
+                                                const uint8_t* __restrict__ vstruct,
+                                                const StructTermsD* __restrict__ td, int S, float* __restrict__ z,
+                                                float* __restrict__ grad, double* __restrict__ F_part) {
+    extern __shared__ float sx[];
+    __shared__ StructTermsD s_td[SMAX];
+    __shared__ double s_red[8];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) sx[i] = x[i] * scale[i];
+    for (int i = threadIdx.x; i < S; i += blockDim.x) s_td[i] = td[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % G;
+    constexpr int RPW = 32 / G;
+    const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int n_warps = (gridDim.x * blockDim.x) >> 5;
+    const int n_tiles = (V + RPW - 1) / RPW;
+    double facc = 0.0;
+    for (int t = warp_global; t < n_tiles; t += n_warps) {
+        const int row = t * RPW + lane / G;
+        float acc = 0.f;
+        if (row < V) {
+            const int p0 = rowptr[row] >> 3, p1 = rowptr[row + 1] >> 3;
+            for (int p = p0 + sub; p < p1; p += G) {
+                const uint4 cw = __ldg(col8 + p);
+                const uint4 vw = __ldg(val8 + p);
+                const unsigned cs[4] = {cw.x, cw.y, cw.z, cw.w};
+                const unsigned vs[4] = {vw.x, vw.y, vw.z, vw.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 v2 = unpack2<BF>(vs[q]);
+                    acc = fmaf(v2.x, sx[cs[q] & 0xffffu], acc);
+                    acc = fmaf(v2.y, sx[cs[q] >> 16], acc);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        if (row < V && sub == 0) {
+            z[row] = acc;
+            if (grad != nullptr || F_part != nullptr) {
+                const StructTermsD tt = s_td[vstruct[row]];
+                const double zd = acc;
+                const double u = fmax(0.0, tt.tu - zd);
+                const double o = fmax(0.0, zd - tt.to);
+                if (grad != nullptr) grad[row] = (float)(2.0 * (tt.b * o - tt.a * u));
+                facc += tt.a * u * u + tt.b * o * o;
+            }
+        }
+    }
+    if (F_part != nullptr) {
+        const double sres = block_sum_f64<256>(facc, s_red);
+        if (threadIdx.x == 0) F_part[blockIdx.x] = sres;
+    }
+}
+
+// a2 with rows padded to 8 entries: two int4 loads of voxel indices and one uint4
+// of values per 8 entries; the row's scale is applied once at the end.
+template <int BT, bool BF>
+__global__ void __launch_bounds__(BT) k_dt16(const int* __restrict__ rowptr, const int4* __restrict__ col4,
+                                             const uint4* __restrict__ val8, const float* __restrict__ scale, int N,
+                                             const float* __restrict__ pi, float* __restrict__ w,
+                                             const int* __restrict__ skip) {
+    __shared__ double s_red[BT / 32];
+    if (skip != nullptr && *skip) return;
+    const int row = blockIdx.x;
+    const int p0 = rowptr[row] >> 3, p1 = rowptr[row + 1] >> 3;
+    float acc = 0.f;
+    for (int p = p0 + threadIdx.x; p < p1; p += BT) {
+        const int4 c0 = __ldg(col4 + 2 * p);
+        const int4 c1 = __ldg(col4 + 2 * p + 1);
+        const uint4 vw = __ldg(val8 + p);
+        const float2 a = unpack2<BF>(vw.x), b = unpack2<BF>(vw.y), c = unpack2<BF>(vw.z), d = unpack2<BF>(vw.w);
+        acc = fmaf(a.x, __ldg(pi + c0.x), acc);
+        acc = fmaf(a.y, __ldg(pi + c0.y), acc);
+        acc = fmaf(b.x, __ldg(pi + c0.z), acc);
+        acc = fmaf(b.y, __ldg(pi + c0.w), acc);
+        acc = fmaf(c.x, __ldg(pi + c1.x), acc);
+        acc = fmaf(c.y, __ldg(pi + c1.y), acc);
+        acc = fmaf(d.x, __ldg(pi + c1.z), acc);
+        acc = fmaf(d.y, __ldg(pi + c1.w), acc);
+    }
+    const double sres = block_sum_f64<BT>((double)acc, s_red);
+    if (threadIdx.x == 0) w[row] = (float)(sres * (double)scale[row]);
+}
+
+// a4 over beam b's segment of each row; the mask is pre-multiplied by the scales.
+template <int G, bool BF>
+__device__ __forceinline__ void column16_body(const unsigned short* __restrict__ col,
+                                              const unsigned short* __restrict__ val,
+                                              const int* __restrict__ seg_lo, const int* __restrict__ seg_hi, int V,
+                                              int base, const float* smask, float* __restrict__ out, int stride) {
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % G;
+    constexpr int RPW = 32 / G;
+    const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int n_warps = (gridDim.x * blockDim.x) >> 5;
+    const int n_tiles = (V + RPW - 1) / RPW;
+    for (int t = warp_global; t < n_tiles; t += n_warps) {
+        const int row = t * RPW + lane / G;
+        float acc = 0.f;
+        if (row < V) {
+            const int q1 = seg_hi[row];
+            for (int p = seg_lo[row] + sub; p < q1; p += G)
+                acc = fmaf(unpack1<BF>(__ldg(val + p)), smask[__ldg(col + p) - base], acc);
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        if (row < V && sub == 0) out[(size_t)row * stride] = acc;
+    }
+}
+
+template <int G, bool BF>
+__global__ void __launch_bounds__(256) k_column16(const unsigned short* __restrict__ col,
+                                                  const unsigned short* __restrict__ val,
+                                                  const int* __restrict__ seg_lo, const int* __restrict__ seg_hi,
+                                                  int V, int base, int nb, const float* __restrict__ mask,
+                                                  const float* __restrict__ scale, float* __restrict__ out,
+                                                  int stride) {
+    extern __shared__ float smask[];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) smask[i] = mask[i] * scale[base + i];
+    __syncthreads();
+    column16_body<G, BF>(col, val, seg_lo, seg_hi, V, base, smask, out, stride);
+}
+
+template <int G, bool BF>
+__global__ void __launch_bounds__(256) k_column16_dev(const unsigned short* __restrict__ col,
+                                                      const unsigned short* __restrict__ val,
+                                                      const int* __restrict__ seg, int V,
+                                                      const int* __restrict__ ap_beam, int K,
+                                                      const int* __restrict__ beam_off,
+                                                      const int* __restrict__ rows, const int* __restrict__ cols,
+                                                      const float* __restrict__ mask, const float* __restrict__ scale,
+                                                      float* __restrict__ out, int stride,
+                                                      const CGDev* __restrict__ cg) {
+    extern __shared__ float smask[];
+    if (cg->done) return;
+    const int b = ap_beam[K - 1];
+    const int nb = rows[b] * cols[b];
+    const int base = beam_off[b];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) smask[i] = mask[i] * scale[base + i];
+    __syncthreads();
+    column16_body<G, BF>(col, val, seg + (size_t)b * V, seg + (size_t)(b + 1) * V, V, base, smask, out, stride);
+}
+
+template <int G, bool BF>
+cudaError_t dose16_g(const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsD* td, int S,
+                     float* z, float* grad, double* F_part, int grid, cudaStream_t stream) {
+    k_dose16<G, BF><<<grid, 256, (size_t)D.n_cols * sizeof(float), stream>>>(
+        D.rowptr, reinterpret_cast<const uint4*>(D.col16), reinterpret_cast<const uint4*>(D.val16), D.n_rows, x,
+        D.scale, D.n_cols, vstruct, td, S, z, grad, F_part);
+    return cudaGetLastError();
+}
+
 template <int G>
 cudaError_t dose_g(const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsD* td, int S,
                    float* z, float* grad, double* F_part, int grid, cudaStream_t stream) {
@@ -232,7 +421,18 @@ cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct,
     if (F_part != nullptr && F_blocks < grid) return cudaErrorInvalidValue;
     const double mean = D.n_rows > 0 ? (double)D.nnz_stored / (double)D.n_rows : 0.0;
     cudaError_t e;
-    if (mean <= 24.0)
+    if (D.prec != DAO_PREC_FP32) {
+        const bool bf = D.prec == DAO_PREC_BF16;
+        if (mean <= 48.0)
+            e = bf ? dose16_g<4, true>(D, x, vstruct, td, S, z, grad, F_part, grid, stream)
+                   : dose16_g<4, false>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+        else if (mean <= 128.0)
+            e = bf ? dose16_g<8, true>(D, x, vstruct, td, S, z, grad, F_part, grid, stream)
+                   : dose16_g<8, false>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+        else
+            e = bf ? dose16_g<16, true>(D, x, vstruct, td, S, z, grad, F_part, grid, stream)
+                   : dose16_g<16, false>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+    } else if (mean <= 24.0)
         e = dose_g<4>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
     else if (mean <= 64.0)
         e = dose_g<8>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
@@ -250,8 +450,17 @@ cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct,
 cudaError_t launch_dt(const DevCSR& Dt, const float* pi, float* w, const int* skip, cudaStream_t stream,
                       int* launches) {
     if (Dt.n_rows == 0) return cudaSuccess;
-    k_dt<128><<<Dt.n_rows, 128, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
-                                              reinterpret_cast<const float4*>(Dt.val), Dt.n_rows, pi, w, skip);
+    if (Dt.prec == DAO_PREC_FP16)
+        k_dt16<128, false><<<Dt.n_rows, 128, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
+                                                          reinterpret_cast<const uint4*>(Dt.val16), Dt.scale,
+                                                          Dt.n_rows, pi, w, skip);
+    else if (Dt.prec == DAO_PREC_BF16)
+        k_dt16<128, true><<<Dt.n_rows, 128, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
+                                                         reinterpret_cast<const uint4*>(Dt.val16), Dt.scale,
+                                                         Dt.n_rows, pi, w, skip);
+    else
+        k_dt<128><<<Dt.n_rows, 128, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
+                                                  reinterpret_cast<const float4*>(Dt.val), Dt.n_rows, pi, w, skip);
     ++*launches;
     return cudaGetLastError();
 }
@@ -260,8 +469,15 @@ cudaError_t launch_column(const DevCSR& D, const int* seg_lo, const int* seg_hi,
                           const float* mask, float* out, int stride, int num_sms, cudaStream_t stream, int* launches) {
     if (D.n_rows == 0) return cudaSuccess;
     const int grid = num_sms * 8;
-    k_column<8><<<grid, 256, (size_t)nb * sizeof(float), stream>>>(D.col, D.val, seg_lo, seg_hi, D.n_rows, base,
-                                                                   nb, mask, out, stride);
+    const size_t sm = (size_t)nb * sizeof(float);
+    if (D.prec == DAO_PREC_FP16)
+        k_column16<8, false><<<grid, 256, sm, stream>>>(D.col16, D.val16, seg_lo, seg_hi, D.n_rows, base, nb, mask,
+                                                         D.scale, out, stride);
+    else if (D.prec == DAO_PREC_BF16)
+        k_column16<8, true><<<grid, 256, sm, stream>>>(D.col16, D.val16, seg_lo, seg_hi, D.n_rows, base, nb, mask,
+                                                        D.scale, out, stride);
+    else
+        k_column<8><<<grid, 256, sm, stream>>>(D.col, D.val, seg_lo, seg_hi, D.n_rows, base, nb, mask, out, stride);
     ++*launches;
     return cudaGetLastError();
 }
@@ -270,8 +486,18 @@ cudaError_t launch_column_dev(const DevCSR& D, const int* seg, const int* ap_bea
                               const int* rows, const int* cols, int max_nb, const float* mask, float* out, int stride,
                               const CGDev* cg, int num_sms, cudaStream_t stream, int* launches) {
     if (D.n_rows == 0) return cudaSuccess;
-    k_column_dev<8><<<num_sms * 8, 256, (size_t)max_nb * sizeof(float), stream>>>(
-        D.col, D.val, seg, D.n_rows, ap_beam, K, beam_off, rows, cols, mask, out, stride, cg);
+    const size_t sm = (size_t)max_nb * sizeof(float);
+    if (D.prec == DAO_PREC_FP16)
+        k_column16_dev<8, false><<<num_sms * 8, 256, sm, stream>>>(D.col16, D.val16, seg, D.n_rows, ap_beam, K,
+                                                                    beam_off, rows, cols, mask, D.scale, out, stride,
+                                                                    cg);
+    else if (D.prec == DAO_PREC_BF16)
+        k_column16_dev<8, true><<<num_sms * 8, 256, sm, stream>>>(D.col16, D.val16, seg, D.n_rows, ap_beam, K,
+                                                                   beam_off, rows, cols, mask, D.scale, out, stride,
+                                                                   cg);
+    else
+        k_column_dev<8><<<num_sms * 8, 256, sm, stream>>>(D.col, D.val, seg, D.n_rows, ap_beam, K, beam_off, rows,
+                                                           cols, mask, out, stride, cg);
     ++*launches;
     return cudaGetLastError();
 }
