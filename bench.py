@@ -123,14 +123,15 @@ class ClockSampler:
 # algorithmic bytes per kernel class (what the method must move)
 # ---------------------------------------------------------------------------
 
-def algorithmic_bytes(case, plan, kc, launches):
+def algorithmic_bytes(case, plan, kc, launches, prec="fp32"):
     V, N, B, nnz = case.n_voxels, case.n_beamlets, case.n_beams, case.nnz
-    if kc == "dt":        # a2: D^T values + voxel indices, row pointers, pi once, w out
-        return launches * (nnz * 8 + (N + 1) * 4 + V * 4 + N * 4)
-    if kc == "dose":      # a1: D values + column indices, row pointers, x once, z out, labels
-        return launches * (nnz * 8 + (V + 1) * 4 + N * 4 + V * 4 + V)
+    wide = prec == "fp32"
+    if kc == "dt":        # a2: D^T values + voxel indices (4+4 or 2+4 B), row pointers, pi once, w out (+ scale)
+        return launches * (nnz * (8 if wide else 6) + (N + 1) * 4 + V * 4 + N * 4 + (0 if wide else N * 4))
+    if kc == "dose":      # a1: D values + column indices (4+4 or 2+2 B), row pointers, x once, z out, labels
+        return launches * (nnz * (8 if wide else 4) + (V + 1) * 4 + N * 4 + V * 4 + V + (0 if wide else N * 4))
     if kc == "column":    # a4: beam b's entries (nnz/B on average), two segment bounds per row, column out
-        return launches * (nnz / B * 8 + V * 8 + V * 4)
+        return launches * (nnz / B * (8 if wide else 4) + V * 8 + V * 4)
     if kc == "master_pass":  # a5: slab columns read once per pass + labels; final passes also write z, pi
         ev, _, _ = plan.master_stats()
         total = V * 9.0                                  # the pass at K = 0 after reset
@@ -212,6 +213,33 @@ def run_reference(a):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def spmv_bandwidth(torch, plan, case, prec, flush, hbm_peak):
+    """Cold-L2 a1 and a2 alone: median of 20 runs, each timed with CUDA events."""
+    out = {}
+    x = torch.rand(case.n_beamlets, device="cuda")
+    z = torch.empty(case.n_voxels, device="cuda")
+    g = torch.empty_like(z)
+    pi = torch.randn(case.n_voxels, device="cuda")
+    w = torch.empty(case.n_beamlets, device="cuda")
+    for kc, fn in (("dose", lambda: plan.k_dose(x, z, g, objective=False)),
+                   ("dt", lambda: plan.k_beamlet_prices(pi, w))):
+        for _ in range(3):
+            fn()
+        per = []
+        for _ in range(20):
+            flush.zero_()
+            plan.profile_enable(True)
+            fn()
+            nl, ms = plan.profile_read(kc)
+            per.append(ms)
+        plan.profile_enable(False)
+        byt = algorithmic_bytes(case, plan, kc, 1, prec)
+        med = statistics.median(per)
+        out[kc] = {"us": round(med * 1e3, 2), "gbs": round(byt / (med * 1e-3) / 1e9, 1),
+                   "frac_of_hbm": round(byt / (med * 1e-3) / 1e9 / hbm_peak, 4), "bytes": int(byt)}
+    return out
+
+
 def run_ours(a):
     import torch
     ws, rank, local = _dist()
@@ -270,7 +298,7 @@ def run_ours(a):
     plan.reset()
     plan.solve(a.apertures)
     prof = {kc: plan.profile_read(kc) for kc in ("dose", "dt", "price", "column", "master_pass", "master_hess",
-                                                 "master_reduce", "master_step")}
+                                                 "master_step")}
     plan.profile_enable(False)
     kernel_ms = {kc: round(ms, 4) for kc, (nl, ms) in prof.items()}
     kernel_launches = {kc: nl for kc, (nl, ms) in prof.items()}
@@ -297,31 +325,33 @@ def run_ours(a):
             "us_per_launch": round(us_avg, 3), "launches_per_plan": int(w_sum),
             "timing": "CUDA events around back-to-back launches at each pool size of the timed plan"}
 
-    # SpMV bandwidth, L2 cold: a1 and a2 alone, 20 runs each
-    spmv = None
+    # SpMV bandwidth, L2 cold: a1 and a2 alone, 20 runs each, FP32 storage and
+    # 16-bit storage (FP16 values + per-beamlet scale, same workload)
+    spmv = mixed = None
     if not a.skip_spmv:
-        spmv = {}
-        x = torch.rand(case.n_beamlets, device="cuda")
-        z = torch.empty(case.n_voxels, device="cuda")
-        g = torch.empty_like(z)
-        pi = torch.randn(case.n_voxels, device="cuda")
-        w = torch.empty(case.n_beamlets, device="cuda")
-        for kc, fn in (("dose", lambda: plan.k_dose(x, z, g, objective=False)),
-                       ("dt", lambda: plan.k_beamlet_prices(pi, w))):
+        spmv = {"fp32": spmv_bandwidth(torch, plan, case, "fp32", flush, hbm_peak)}
+        from paper_1003_5402_gb300 import binding
+        with Plan(case, device=dev, stream=stream.cuda_stream, precision=binding.DAO_PREC_FP16) as p16:
+            spmv["fp16"] = spmv_bandwidth(torch, p16, case, "fp16", flush, hbm_peak)
+            for _ in range(2):
+                p16.reset()
+                p16.solve(a.apertures)
+            t16 = []
             for _ in range(3):
-                fn()
-            per = []
-            for _ in range(20):
                 flush.zero_()
-                plan.profile_enable(True)
-                fn()
-                nl, ms = plan.profile_read(kc)
-                per.append(ms)
-            plan.profile_enable(False)
-            byt = algorithmic_bytes(case, plan, kc, 1)
-            med = statistics.median(per)
-            spmv[kc] = {"us": round(med * 1e3, 2), "gbs": round(byt / (med * 1e-3) / 1e9, 1),
-                        "frac_of_hbm": round(byt / (med * 1e-3) / 1e9 / hbm_peak, 4), "bytes": byt}
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                p16.reset()
+                _, n16, tr16 = p16.solve(a.apertures)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t16.append(e0.elapsed_time(e1))
+        mixed = {"storage": "FP16 values of D and D^T, per-beamlet FP32 scale, FP32 accumulation",
+                 "ms_per_plan": round(statistics.median(t16), 4),
+                 "objective_final": float(tr16[n16 - 1]) if n16 else None,
+                 "objective_rel_diff_vs_fp32": (abs(float(tr16[n16 - 1]) - F_final) / F_final
+                                                if n16 and F_final else None)}
 
     # end to end through the public API from host buffers
     e2e = None
@@ -368,7 +398,7 @@ def run_ours(a):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
             "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
                            "p99": round(float(np.percentile(lat, 99)), 4)},
-            "spmv": spmv, "kernel_ms_host_driven_plan": kernel_ms, "kernel_launches_host_driven_plan": kernel_launches,
+            "spmv": spmv, "mixed_precision": mixed, "kernel_ms_host_driven_plan": kernel_ms, "kernel_launches_host_driven_plan": kernel_launches,
             "objective_final": F_final, "apertures_done": int(n), "master_evals": int(np.sum(ev)),
             "host_wall_s": round(t_host, 3), "device": torch.cuda.get_device_name(dev),
         }

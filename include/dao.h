@@ -208,8 +208,8 @@ enum {
     DAO_KC_PRICE = 2,          /* a3 pricing (row scan + beam reduction) */
     DAO_KC_COLUMN = 3,         /* a4 aperture column */
     DAO_KC_MASTER_PASS = 4,    /* a5 slab pass: z, pi, h, F and the active-voxel list */
-    DAO_KC_MASTER_REDUCE = 5,  /* a5 partial reduction */
-    DAO_KC_MASTER_STEP = 6,    /* a5 Newton step / line search control */
+    DAO_KC_MASTER_REDUCE = 5,  /* a5 partial reduction: now part of DAO_KC_MASTER_STEP, never counted */
+    DAO_KC_MASTER_STEP = 6,    /* a5 partial reduction + Newton step / line search control */
     DAO_KC_MASTER_HESS = 7,    /* a5 curvature matrix and gradient over the active voxels */
     DAO_KC_OTHER = 8,
     DAO_KC_COUNT = 9

@@ -10,6 +10,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "dao_internal.h"
 
 using namespace dao;
@@ -36,6 +39,7 @@ dao_status fail(dao_status s, const std::string& msg) {
     } while (0)
 
 inline int64_t round4(int64_t n) { return (n + 3) / 4 * 4; }
+inline int64_t round_up(int64_t n, int m) { return (n + m - 1) / m * m; }
 
 }  // namespace
 
@@ -220,7 +224,10 @@ dao_status validate(const dao_csr* D, const dao_geometry* g, const dao_structure
     if (opt->k_max < 1 || opt->k_max > KMAX) return fail(DAO_EINVAL, "k_max must be in [1, 64]");
     if (opt->max_master_iters < 1) return fail(DAO_EINVAL, "max_master_iters must be >= 1");
     if (!(opt->master_tol > 0) || !(opt->price_tol >= 0)) return fail(DAO_EINVAL, "tolerances must be positive");
-    if (opt->precision != DAO_PREC_FP32) return fail(DAO_EINVAL, "only DAO_PREC_FP32 is implemented");
+    if (opt->precision != DAO_PREC_FP32 && opt->precision != DAO_PREC_FP16 && opt->precision != DAO_PREC_BF16)
+        return fail(DAO_EINVAL, "precision must be DAO_PREC_FP32, DAO_PREC_FP16 or DAO_PREC_BF16");
+    if (opt->precision != DAO_PREC_FP32 && D->n_beamlets > 65536)
+        return fail(DAO_EINVAL, "16-bit storage keeps beamlet indices in 16 bits: at most 65536 beamlets");
     return DAO_OK;
 }
 
@@ -231,13 +238,14 @@ struct HostCSR {
     std::vector<float> val;
 };
 
-// Rows padded to a multiple of four entries (value 0, column = the row's last).
-void pad_rows(int n_rows, const std::vector<int64_t>& rp, const int32_t* col, const float* val, HostCSR& out) {
+// Rows padded to a multiple of m entries (value 0, column = the row's last).
+void pad_rows(int n_rows, const std::vector<int64_t>& rp, const int32_t* col, const float* val, HostCSR& out,
+              int m) {
     out.rowptr.assign(n_rows + 1, 0);
     int64_t acc = 0;
     for (int r = 0; r < n_rows; ++r) {
         out.rowptr[r] = (int)acc;
-        acc += round4(rp[r + 1] - rp[r]);
+        acc += round_up(rp[r + 1] - rp[r], m);
     }
     out.rowptr[n_rows] = (int)acc;
     out.col.assign(acc, 0);
@@ -283,12 +291,16 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
         }
 
     // D (voxel-major) with per-row beam segments
+    // rows padded to 4 entries (one float4 / int4 load) or, with 16-bit values, to
+    // 8 entries (one 16-byte load of values and of 16-bit columns)
+    const int prec = c->opt.precision;
+    const int pad_m = prec == DAO_PREC_FP32 ? 4 : 8;
     std::vector<int64_t> rp(Din->row_ptr, Din->row_ptr + V + 1);
     int64_t padded = 0;
-    for (int j = 0; j < V; ++j) padded += round4(rp[j + 1] - rp[j]);
+    for (int j = 0; j < V; ++j) padded += round_up(rp[j + 1] - rp[j], pad_m);
     if (padded >= (int64_t)1 << 31) return fail(DAO_EINVAL, "D too large for 32-bit row offsets");
     HostCSR Dh;
-    pad_rows(V, rp, Din->col, Din->val, Dh);
+    pad_rows(V, rp, Din->col, Din->val, Dh, pad_m);
     std::vector<int> seg((size_t)(B + 1) * V);
     for (int j = 0; j < V; ++j) {
         const int p_end = Dh.rowptr[j] + (int)(rp[j + 1] - rp[j]);
@@ -318,10 +330,10 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
             }
     }
     int64_t tpadded = 0;
-    for (int i = 0; i < N; ++i) tpadded += round4(trp[i + 1] - trp[i]);
+    for (int i = 0; i < N; ++i) tpadded += round_up(trp[i + 1] - trp[i], pad_m);
     if (tpadded >= (int64_t)1 << 31) return fail(DAO_EINVAL, "D^T too large for 32-bit row offsets");
     HostCSR Th;
-    pad_rows(N, trp, tcol.data(), tval.data(), Th);
+    pad_rows(N, trp, tcol.data(), tval.data(), Th, pad_m);
 
     // objective terms per structure (Eqs. 9-10)
     const int S = s->n_structures;
@@ -352,15 +364,45 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     c->D.n_rows = V;
     c->D.n_cols = N;
     c->D.nnz_stored = padded;
-    DAO_TRY(upload(c, &c->D.rowptr, Dh.rowptr.data(), Dh.rowptr.size()));
-    DAO_TRY(upload(c, &c->D.col, Dh.col.data(), Dh.col.size()));
-    DAO_TRY(upload(c, &c->D.val, Dh.val.data(), Dh.val.size()));
+    c->D.prec = prec;
     c->Dt.n_rows = N;
     c->Dt.n_cols = V;
     c->Dt.nnz_stored = tpadded;
+    c->Dt.prec = prec;
+    DAO_TRY(upload(c, &c->D.rowptr, Dh.rowptr.data(), Dh.rowptr.size()));
     DAO_TRY(upload(c, &c->Dt.rowptr, Th.rowptr.data(), Th.rowptr.size()));
     DAO_TRY(upload(c, &c->Dt.col, Th.col.data(), Th.col.size()));
-    DAO_TRY(upload(c, &c->Dt.val, Th.val.data(), Th.val.size()));
+    if (prec == DAO_PREC_FP32) {
+        DAO_TRY(upload(c, &c->D.col, Dh.col.data(), Dh.col.size()));
+        DAO_TRY(upload(c, &c->D.val, Dh.val.data(), Dh.val.size()));
+        DAO_TRY(upload(c, &c->Dt.val, Th.val.data(), Th.val.size()));
+    } else {
+        // 16-bit storage: s_i = max_j |D_ij| per beamlet (1 for an empty beamlet),
+        // stored value RN16(D_ij / s_i) with the quotient rounded to FP32 first
+        std::vector<float> scale(N, 0.f);
+        for (int64_t p = 0; p < Din->nnz; ++p) scale[Din->col[p]] = std::max(scale[Din->col[p]], std::fabs(Din->val[p]));
+        for (int i = 0; i < N; ++i)
+            if (!(scale[i] > 0.f)) scale[i] = 1.f;
+        auto q16 = [&](float v, int i) -> uint16_t {
+            const float r = v / scale[i];
+            if (prec == DAO_PREC_FP16) return static_cast<__half_raw>(__float2half_rn(r)).x;
+            return static_cast<__nv_bfloat16_raw>(__float2bfloat16_rn(r)).x;
+        };
+        std::vector<uint16_t> c16(Dh.col.size()), v16(Dh.val.size()), tv16(Th.val.size());
+        for (size_t q = 0; q < Dh.col.size(); ++q) {
+            c16[q] = (uint16_t)Dh.col[q];
+            v16[q] = q16(Dh.val[q], Dh.col[q]);
+        }
+        for (int i = 0; i < N; ++i)
+            for (int q = Th.rowptr[i]; q < Th.rowptr[i + 1]; ++q) tv16[q] = q16(Th.val[q], i);
+        DAO_TRY(upload(c, &c->D.col16, c16.data(), c16.size()));
+        DAO_TRY(upload(c, &c->D.val16, v16.data(), v16.size()));
+        DAO_TRY(upload(c, &c->Dt.val16, tv16.data(), tv16.size()));
+        float* sd = nullptr;
+        DAO_TRY(upload(c, &sd, scale.data(), scale.size()));
+        c->D.scale = sd;
+        c->Dt.scale = sd;
+    }
     DAO_TRY(upload(c, &c->seg, seg.data(), seg.size()));
     DAO_TRY(upload(c, &c->vstruct, vs.data(), vs.size()));
     DAO_TRY(upload(c, &c->tf, tfh.data(), tfh.size()));
@@ -480,11 +522,8 @@ dao_status master_solve(dao_ctx* c, double* F_out) {
             c->prof_begin(DAO_KC_MASTER_HESS);
             DAO_CU(launch_master_hess(c->mb, c->K, PASS_EVAL, c->stream, &c->launches_i));
             c->prof_end();
-            c->prof_begin(DAO_KC_MASTER_REDUCE);
-            DAO_CU(launch_master_reduce(c->K, c->mb, c->stream, &c->launches_i));
-            c->prof_end();
             c->prof_begin(DAO_KC_MASTER_STEP);
-            DAO_CU(launch_master_step(c->mb, c->opt.max_master_iters, c->opt.master_tol, 0, 0, c->stream,
+            DAO_CU(launch_master_step(c->K, c->mb, c->opt.max_master_iters, c->opt.master_tol, 0, 0, c->stream,
                                       &c->launches_i));
             c->prof_end();
         }
@@ -639,11 +678,15 @@ dao_status build_round_graph(dao_ctx* c, int K) {
             cudaGraph_t body = cp.conditional.phGraph_out[0];
             check(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
             if (e == cudaSuccess) {
-                check(launch_master_eval(c->mb, c->V, K, c->vstruct, c->tf, c->S, nullptr, nullptr, PASS_EVAL,
-                                         nullptr, cs, &n));
-                check(launch_master_hess(c->mb, K, PASS_EVAL, cs, &n));
-                check(launch_master_reduce(K, c->mb, cs, &n));
-                check(launch_master_step(c->mb, c->opt.max_master_iters, c->opt.master_tol, h, 1, cs, &n));
+                // two evaluations per iteration of the while node: the node's own
+                // relaunch costs about as much as a kernel, and once the solve is
+                // done the kernels of the second evaluation return at entry
+                for (int u = 0; u < 2; ++u) {
+                    check(launch_master_eval(c->mb, c->V, K, c->vstruct, c->tf, c->S, nullptr, nullptr, PASS_EVAL,
+                                             nullptr, cs, &n));
+                    check(launch_master_hess(c->mb, K, PASS_EVAL, cs, &n));
+                    check(launch_master_step(K, c->mb, c->opt.max_master_iters, c->opt.master_tol, h, 1, cs, &n));
+                }
                 cudaGraph_t out = nullptr;
                 check(cudaStreamEndCapture(cs, &out));
             }
@@ -704,10 +747,11 @@ dao_status solve_graph(dao_ctx* c, int n_apertures, int32_t* n_done, double* tra
             }
         }
     }
-    // kernels the graphs ran: 8 per round plus pass, reduce and step per evaluation
+    // kernels the graphs ran: 8 per round plus pass, curvature and reduce + step per evaluation,
+    // launched in pairs of evaluations
     c->launches_i += 8 * (K - K0) + (K < K1 ? 5 : 0);
     for (int k = K0; k < K; ++k) {
-        c->launches_i += 4 * h->evals[k];
+        c->launches_i += 6 * ((h->evals[k] + 1) / 2);  // two evaluations per while iteration
         c->stat_evals.push_back(h->evals[k]);
         c->stat_status.push_back(h->status[k]);
         c->stat_kkt.push_back(h->res[k] / (h->tol[k] > 0 ? h->tol[k] / c->opt.master_tol : 1.0));

@@ -63,6 +63,7 @@ struct MasterDev {
     int status;           // MASTER_*
     int n_eval;           // fused passes evaluated
     int err;              // set when a tile copy of an evaluation never completed
+    unsigned ticket;      // blocks of the reduce + step kernel that finished their share (0 between launches)
 };
 
 enum { MASTER_RUNNING = 0, MASTER_CONVERGED = 1, MASTER_MAXITER = 2, MASTER_STALLED = 3, MASTER_ERROR = 4 };
@@ -155,10 +156,9 @@ cudaError_t launch_master_eval(const MasterBuffers& mb, int V, int K, const uint
                                const StructTermsF* tf, int S, float* z_out, float* pi_out, int mode,
                                const int* skip, cudaStream_t stream, int* launches);
 cudaError_t launch_master_hess(const MasterBuffers& mb, int K, int mode, cudaStream_t stream, int* launches);
-cudaError_t launch_master_reduce(int K, const MasterBuffers& mb, cudaStream_t stream, int* launches);
-cudaError_t launch_master_step(const MasterBuffers& mb, int max_iter, double tol_rel,
-                               cudaGraphConditionalHandle cond, int use_cond, cudaStream_t stream,
-                               int* launches);
+// Reduction of the partial sums and the projected-Newton step, one launch.
+cudaError_t launch_master_step(int K, const MasterBuffers& mb, int max_iter, double tol_rel,
+                               cudaGraphConditionalHandle cond, int use_cond, cudaStream_t stream, int* launches);
 cudaError_t launch_cg_record(const MasterDev* st, CGDev* cg, int K, cudaStream_t stream, int* launches);
 
 }  // namespace dao

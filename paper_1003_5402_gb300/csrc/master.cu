@@ -144,6 +144,7 @@ __global__ void k_master_init(MasterDev* __restrict__ st, int K, const int* __re
         st->alpha = 1.0;
         st->n_eval = 0;
         st->err = 0;
+        st->ticket = 0;
         if (use_cond) cudaGraphSetConditional(cond, 1u);
     }
 }
@@ -444,57 +445,59 @@ __global__ void __launch_bounds__(256) k_master_hess(const float* __restrict__ a
     }
 }
 
-// One warp per output (packed H entries, then g, then the g rounding scale, then
-// F): lanes read the blocks' partials (contiguous per output) and combine them
-// with a fixed shuffle tree in FP64.
-__global__ void __launch_bounds__(256) k_master_reduce(const float* __restrict__ H_part,
-                                                       const double* __restrict__ g_part,
-                                                       const float* __restrict__ gn_part,
-                                                       const double* __restrict__ F_part, int GH, int GE,
-                                                       MasterDev* __restrict__ st) {
-    if (st->done) return;
-    const int K = st->K;
+// Reduction of the partial sums: one warp per output (packed H entries, then g,
+// then the g rounding scale, then F), outputs strided over the grid's warps;
+// lanes read the blocks' partials (contiguous per output) and combine them with
+// a fixed shuffle tree in FP64.
+__device__ __forceinline__ void master_reduce_part(const float* __restrict__ H_part,
+                                                   const double* __restrict__ g_part,
+                                                   const float* __restrict__ gn_part,
+                                                   const double* __restrict__ F_part, int GH, int GE, int K,
+                                                   MasterDev* __restrict__ st) {
     const int E = K * (K + 1) / 2;
-    const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (o < E) {
-        double s = 0.0;
-        const float* src = H_part + (size_t)o * GH;
-        for (int b = lane; b < GH; b += 32) s += (double)src[b];
-        s = warp_sum_f64(s);
-        if (lane == 0) {
-            int r = 0, rem = o;
-            while (rem >= K - r) {
-                rem -= K - r;
-                ++r;
+    const int n_out = E + 2 * K + 1;
+    for (int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < n_out; o += (gridDim.x * blockDim.x) >> 5) {
+        if (o < E) {
+            double s = 0.0;
+            const float* src = H_part + (size_t)o * GH;
+            for (int b = lane; b < GH; b += 32) s += (double)src[b];
+            s = warp_sum_f64(s);
+            if (lane == 0) {
+                int r = 0, rem = o;
+                while (rem >= K - r) {
+                    rem -= K - r;
+                    ++r;
+                }
+                const int c = r + rem;
+                st->Ht[r * KMAX + c] = s;
+                st->Ht[c * KMAX + r] = s;
             }
-            const int c = r + rem;
-            st->Ht[r * KMAX + c] = s;
-            st->Ht[c * KMAX + r] = s;
+        } else if (o < E + K) {
+            const int k = o - E;
+            double s = 0.0;
+            for (int b = lane; b < GH; b += 32) s += g_part[(size_t)k * GH + b];
+            s = warp_sum_f64(s);
+            if (lane == 0) st->gt[k] = s;
+        } else if (o < E + 2 * K) {
+            const int k = o - E - K;
+            float s = 0.f;
+            for (int b = lane; b < GH; b += 32) s += gn_part[(size_t)k * GH + b];
+            s = warp_sum_f32(s);
+            if (lane == 0) st->gn[k] = s;
+        } else {
+            double s = 0.0;
+            for (int b = lane; b < GE; b += 32) s += F_part[b];
+            s = warp_sum_f64(s);
+            if (lane == 0) st->Ft = s;
         }
-    } else if (o < E + K) {
-        const int k = o - E;
-        double s = 0.0;
-        for (int b = lane; b < GH; b += 32) s += g_part[(size_t)k * GH + b];
-        s = warp_sum_f64(s);
-        if (lane == 0) st->gt[k] = s;
-    } else if (o < E + 2 * K) {
-        const int k = o - E - K;
-        float s = 0.f;
-        for (int b = lane; b < GH; b += 32) s += gn_part[(size_t)k * GH + b];
-        s = warp_sum_f32(s);
-        if (lane == 0) st->gn[k] = s;
-    } else if (o == E + 2 * K) {
-        double s = 0.0;
-        for (int b = lane; b < GE; b += 32) s += F_part[b];
-        s = warp_sum_f64(s);
-        if (lane == 0) st->Ft = s;
     }
 }
 
 // Block-wide reductions over STEP_T threads with a fixed order.
 constexpr int STEP_T = 256;
 constexpr int STEP_W = STEP_T / 32;
+static_assert(STEP_T == 256 && KMAX == 64, "the step kernel maps a 16 x 16 thread grid onto 64 x 64 entries");
 
 __device__ __forceinline__ double blk_sum(double v, double* sw) {
     v = warp_sum_f64(v);
@@ -533,13 +536,16 @@ __device__ __forceinline__ int blk_or(int v, int* swi) {
 // One block: thread k < K owns variable k; all threads share the factorisation.
 __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int max_iter, double tol_rel,
                                                  double sigma) {
-    __shared__ float L[KMAX][KMAX + 1];
-    __shared__ float Hf[KMAX][KMAX + 1];
+    __shared__ __align__(16) float A[KMAX][KMAX + 4];   // working lower triangle
+    __shared__ __align__(16) float Lw[KMAX][KMAX + 4];  // final panel columns, L_ik d_k
+    __shared__ __align__(16) float u[KMAX];             // right-hand side being eliminated
+    __shared__ __align__(16) float ye[KMAX];            // eliminated right-hand side
+    __shared__ float piv[KMAX];
+    __shared__ float rd[KMAX];
     __shared__ float rhs[KMAX];
     __shared__ int fidx[KMAX];
     __shared__ double sw[STEP_W];
     __shared__ int swi[STEP_W];
-    __shared__ int s_ok;
     if (st->done) return;
     if (st->err) {  // a tile copy was lost in an evaluation: stop with the last accepted point
         if (threadIdx.x == 0) {
@@ -552,9 +558,11 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     const int k = threadIdx.x;
     const bool own = k < K;
     const int phase = st->phase;
+    // gt, gn, Ft and Ht were written by other blocks of this launch: read them
+    // through L2 (__ldcg), never from a possibly stale L1 line
     const double yt = own ? st->yt[k] : 0.0;
-    const double gt = own ? st->gt[k] : 0.0;
-    const double gn = own ? (double)st->gn[k] : 0.0;
+    const double gt = own ? __ldcg(&st->gt[k]) : 0.0;
+    const double gn = own ? (double)__ldcg(&st->gn[k]) : 0.0;
     const double y = own ? st->y[k] : 0.0;
     const double g = own ? st->g[k] : 0.0;
     // tolerance of this solve from the gradient at the warm start
@@ -568,7 +576,8 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     const double rmax = blk_max(rt, sw);
     const double dec = blk_sum(own ? g * (yt - y) : 0.0, sw);
     const bool cap = st->iter >= max_iter + 64;
-    const bool accept = !cap && (phase == 0 || !viol || st->Ft <= st->F + sigma * dec);
+    const double Ft = __ldcg(&st->Ft);
+    const bool accept = !cap && (phase == 0 || !viol || Ft <= st->F + sigma * dec);
     if (k == 0) ++st->n_eval;
     if (cap) {
         if (k == 0) {
@@ -600,7 +609,7 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
         st->g[k] = gt;
     }
     if (k == 0) {
-        st->F = st->Ft;
+        st->F = Ft;
         st->res = rmax;
     }
     if (!viol || st->iter >= max_iter) {
@@ -628,74 +637,157 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     if (fr) fidx[pos] = k;
     double d = active ? -gt : 0.0;
     __syncthreads();
-    // damped FP32 Cholesky of H_FF (right-looking, one barrier per column: every
-    // thread takes the pivot's square root itself, and a column is scaled one
-    // step late, when no thread reads it any more), retried with a larger shift
-    // if a pivot fails
-    for (int idx = k; idx < nf * nf; idx += STEP_T) {
-        const int i = idx / nf, jj = idx % nf;
-        Hf[i][jj] = (float)st->Ht[fidx[i] * KMAX + fidx[jj]];
-    }
-    __syncthreads();
-    float maxdiag = 0.f;
-    for (int i = 0; i < nf; ++i) maxdiag = fmaxf(maxdiag, Hf[i][i]);
+    // Damped FP32 L D L^T factorisation of H_FF with the forward solve folded in,
+    // by panels of 4 columns with one barrier per panel.  The working lower
+    // triangle A lives in shared memory.  For panel p (columns c0 = 4p .. c0+3)
+    // the threads that need it factor the 4 x 4 diagonal block themselves
+    // (identical arithmetic everywhere) and map rows through it, w = x L11^-T:
+    //   - thread t < nb(nb+1)/2 owns trailing tile (r, s), s <= r, and subtracts
+    //     w_R D^-1 w_Q^T from it (the trailing part shrinks, so do the threads);
+    //   - threads 128 + r' write the panel's final column entries w (unscaled:
+    //     L_ik d_k) of row block r' into Lw, and the pivots d;
+    //   - thread 160 writes the eliminated right-hand side of the panel into ye,
+    //     threads 161 + r subtract its contribution from row block r of u.
+    // Rows nf .. 4*panels-1 are padding with only the shift on the diagonal.  The
+    // pivots are checked once at the end; a non-positive one restarts the
+    // factorisation with a 100x larger shift.  Then L^T x = D^-1 ye is solved by
+    // warp 0 with the unit lower factor L_ik = Lw_ik / d_k.
+    const int ti = k >> 4, tq = k & 15;
+    const int n_panels = (nf + 3) >> 2;
+    const int n4 = 4 * n_panels;
+    float Hr[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = ti + 16 * a, q = tq + 16 * b;
+            Hr[a][b] = (i < nf && q <= i) ? (float)__ldcg(&st->Ht[fidx[i] * KMAX + fidx[q]]) : 0.f;
+        }
+    const float bk = k < nf ? -(float)st->g[fidx[k]] : 0.f;
+    float dg = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) dg = fmaxf(dg, (ti == tq) ? Hr[a][a] : 0.f);
+    const float maxdiag = (float)blk_max((double)dg, sw);
     float lam = 1e-6f * maxdiag + 1e-30f;
+    // trailing tile of this thread for a panel with nb trailing row blocks
+    int tr_r = (int)((sqrtf(8.f * (float)k + 1.f) - 1.f) * 0.5f);
+    while ((tr_r + 1) * (tr_r + 2) / 2 <= k) ++tr_r;
+    while (tr_r * (tr_r + 1) / 2 > k) --tr_r;
+    const int tr_s = k - tr_r * (tr_r + 1) / 2;
     bool ok = false;
     for (int attempt = 0; attempt < 6 && !ok; ++attempt) {
-        for (int idx = k; idx < nf * nf; idx += STEP_T) {
-            const int i = idx / nf, jj = idx % nf;
-            L[i][jj] = Hf[i][jj] + (i == jj ? lam : 0.f);
-        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int i = ti + 16 * a, q = tq + 16 * b;
+                A[i][q] = Hr[a][b] + ((i == q && i < n4) ? lam : 0.f);
+            }
+        if (k < KMAX) u[k] = bk;
         __syncthreads();
-        ok = true;
-        for (int jj = 0; jj < nf; ++jj) {
-            const float pv = L[jj][jj];
-            if (!(pv > 0.f) || !isfinite(pv)) {  // every thread sees the same pivot
-                ok = false;
-                break;
-            }
-            const float inv = 1.f / sqrtf(pv);
-            const int m = nf - jj - 1;
-            for (int idx = k; idx < m * m; idx += STEP_T) {
-                const int i = jj + 1 + idx / m, q = jj + 1 + idx % m;
-                if (q <= i) L[i][q] -= (L[i][jj] * inv) * (L[q][jj] * inv);
+        for (int p = 0; p < n_panels; ++p) {
+            const int c0 = 4 * p;
+            const int nb = n_panels - p - 1;
+            const bool tile = k < nb * (nb + 1) / 2;
+            const bool colw = k >= 128 && k <= 128 + nb;
+            const bool rhsw = k >= 160 && k <= 160 + nb;
+            if (tile || colw || rhsw) {
+                const float4 a0 = *reinterpret_cast<const float4*>(&A[c0][c0]);
+                const float4 a1 = *reinterpret_cast<const float4*>(&A[c0 + 1][c0]);
+                const float4 a2 = *reinterpret_cast<const float4*>(&A[c0 + 2][c0]);
+                const float4 a3 = *reinterpret_cast<const float4*>(&A[c0 + 3][c0]);
+                const float d0 = a0.x, i0 = 1.f / d0;
+                const float l10 = a1.x * i0;
+                const float d1 = a1.y - l10 * a1.x, i1 = 1.f / d1;
+                const float l20 = a2.x * i0, w21 = a2.y - l10 * a2.x, l21 = w21 * i1;
+                const float d2 = a2.z - l20 * a2.x - l21 * w21, i2 = 1.f / d2;
+                const float l30 = a3.x * i0, w31 = a3.y - l10 * a3.x, l31 = w31 * i1;
+                const float w32 = a3.z - l20 * a3.x - l21 * w31, l32 = w32 * i2;
+                const float d3 = a3.w - l30 * a3.x - l31 * w31 - l32 * w32, i3 = 1.f / d3;
+                auto xform = [&](float4 x) {
+                    float4 w;
+                    w.x = x.x;
+                    w.y = x.y - l10 * w.x;
+                    w.z = x.z - l20 * w.x - l21 * w.y;
+                    w.w = x.w - l30 * w.x - l31 * w.y - l32 * w.z;
+                    return w;
+                };
+                if (tile) {
+                    const int R = c0 + 4 + 4 * tr_r, Q = c0 + 4 + 4 * tr_s;
+                    float4 wq[4];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) wq[b] = xform(*reinterpret_cast<const float4*>(&A[Q + b][c0]));
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        float4 w = xform(*reinterpret_cast<const float4*>(&A[R + a][c0]));
+                        w.x *= i0;
+                        w.y *= i1;
+                        w.z *= i2;
+                        w.w *= i3;
+                        float4 t = *reinterpret_cast<const float4*>(&A[R + a][Q]);
+                        t.x -= w.x * wq[0].x + w.y * wq[0].y + w.z * wq[0].z + w.w * wq[0].w;
+                        t.y -= w.x * wq[1].x + w.y * wq[1].y + w.z * wq[1].z + w.w * wq[1].w;
+                        t.z -= w.x * wq[2].x + w.y * wq[2].y + w.z * wq[2].z + w.w * wq[2].w;
+                        t.w -= w.x * wq[3].x + w.y * wq[3].y + w.z * wq[3].z + w.w * wq[3].w;
+                        *reinterpret_cast<float4*>(&A[R + a][Q]) = t;
+                    }
+                } else if (colw) {
+                    const int R = c0 + 4 * (k - 128);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+                        *reinterpret_cast<float4*>(&Lw[R + a][c0]) =
+                            xform(*reinterpret_cast<const float4*>(&A[R + a][c0]));
+                    if (k == 128) {
+                        piv[c0] = d0;
+                        piv[c0 + 1] = d1;
+                        piv[c0 + 2] = d2;
+                        piv[c0 + 3] = d3;
+                    }
+                } else {
+                    const float4 e = xform(*reinterpret_cast<const float4*>(&u[c0]));
+                    if (k == 160) {
+                        *reinterpret_cast<float4*>(&ye[c0]) = e;
+                    } else {
+                        const int R = c0 + 4 * (k - 160);
+                        const float e0 = e.x * i0, e1 = e.y * i1, e2 = e.z * i2, e3 = e.w * i3;
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            const float4 w = xform(*reinterpret_cast<const float4*>(&A[R + a][c0]));
+                            u[R + a] -= w.x * e0 + w.y * e1 + w.z * e2 + w.w * e3;
+                        }
+                    }
+                }
             }
             __syncthreads();
         }
-        if (ok) {  // scale the columns: L[i][j] /= sqrt(pivot j); the diagonal becomes sqrt(pivot)
-            for (int idx = k; idx < nf * nf; idx += STEP_T) {
-                const int i = idx / nf, jj = idx % nf;
-                if (jj < i) L[i][jj] = L[i][jj] / sqrtf(L[jj][jj]);
-            }
-            __syncthreads();
-            for (int i = k; i < nf; i += STEP_T) L[i][i] = sqrtf(L[i][i]);
-            __syncthreads();
-        }
+        const float pk = k < n4 ? piv[k] : 1.f;
+        ok = __syncthreads_and(pk > 0.f && isfinite(1.f / pk)) != 0;
         lam *= 100.f;
-        __syncthreads();
     }
     if (ok) {
-        // forward and back substitution by warp 0, lanes owning rows lane and lane + 32
+        if (k < KMAX) rd[k] = k < nf ? 1.f / piv[k] : 0.f;
+        __syncthreads();
+        // L^T x = D^-1 ye by warp 0 in panels of 4 rows, last panel first, with
+        // L_ik = Lw_ik / d_k: x_r = (ye_r - sum_{i > r} Lw_ir x_i) / d_r; lanes own
+        // rows lane and lane + 32
         if (k < 32) {
-            float b0 = k < nf ? -(float)st->g[fidx[k]] : 0.f;
-            float b1 = k + 32 < nf ? -(float)st->g[fidx[k + 32]] : 0.f;
-            for (int jj = 0; jj < nf; ++jj) {  // L u = -g_F
-                const float bj = __shfl_sync(FULL, jj < 32 ? b0 : b1, jj & 31);
-                const float xj = bj / L[jj][jj];
-                if (k == (jj & 31)) {
-                    if (jj < 32) b0 = xj; else b1 = xj;
-                }
-                if (k > jj && k < nf) b0 -= L[k][jj] * xj;
-                if (k + 32 > jj && k + 32 < nf) b1 -= L[k + 32][jj] * xj;
-            }
-            for (int jj = nf - 1; jj >= 0; --jj) {  // L^T d = u
-                const float bj = __shfl_sync(FULL, jj < 32 ? b0 : b1, jj & 31);
-                const float xj = bj / L[jj][jj];
-                if (k == (jj & 31)) {
-                    if (jj < 32) b0 = xj; else b1 = xj;
-                }
-                if (k < jj) b0 -= L[jj][k] * xj;
-                if (k + 32 < jj) b1 -= L[jj][k + 32] * xj;
+            float b0 = k < n4 ? ye[k] : 0.f, b1 = k + 32 < n4 ? ye[k + 32] : 0.f;
+            for (int p = n_panels - 1; p >= 0; --p) {
+                const int c0 = 4 * p;
+                const float src = c0 < 32 ? b0 : b1;
+                const float v0 = __shfl_sync(FULL, src, c0 & 31), v1 = __shfl_sync(FULL, src, (c0 + 1) & 31);
+                const float v2 = __shfl_sync(FULL, src, (c0 + 2) & 31), v3 = __shfl_sync(FULL, src, (c0 + 3) & 31);
+                const float x3 = v3 * rd[c0 + 3];
+                const float x2 = (v2 - Lw[c0 + 3][c0 + 2] * x3) * rd[c0 + 2];
+                const float x1 = (v1 - Lw[c0 + 2][c0 + 1] * x2 - Lw[c0 + 3][c0 + 1] * x3) * rd[c0 + 1];
+                const float x0 = (v0 - Lw[c0 + 1][c0] * x1 - Lw[c0 + 2][c0] * x2 - Lw[c0 + 3][c0] * x3) * rd[c0];
+                if (k < c0) b0 -= Lw[c0][k] * x0 + Lw[c0 + 1][k] * x1 + Lw[c0 + 2][k] * x2 + Lw[c0 + 3][k] * x3;
+                if (k + 32 < c0)
+                    b1 -= Lw[c0][k + 32] * x0 + Lw[c0 + 1][k + 32] * x1 + Lw[c0 + 2][k + 32] * x2 +
+                          Lw[c0 + 3][k + 32] * x3;
+                const int r0 = k - c0, r1 = k + 32 - c0;
+                if (r0 >= 0 && r0 < 4) b0 = r0 == 0 ? x0 : r0 == 1 ? x1 : r0 == 2 ? x2 : x3;
+                if (r1 >= 0 && r1 < 4) b1 = r1 == 0 ? x0 : r1 == 1 ? x1 : r1 == 2 ? x2 : x3;
             }
             rhs[k] = b0;
             rhs[k + 32] = b1;
@@ -703,7 +795,7 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
         __syncthreads();
         if (fr) d = (double)rhs[pos];
     } else if (fr) {
-        const double hk = st->Ht[k * KMAX + k];
+        const double hk = __ldcg(&st->Ht[k * KMAX + k]);
         d = -gt / (hk > 0.0 ? hk : 1.0);
     }
     if (own) {
@@ -717,11 +809,32 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     }
 }
 
-// Every exit path of the step leaves the while-node condition at "not done";
-// the evaluation cap inside the step guarantees that done is reached.
-__global__ void __launch_bounds__(STEP_T) k_master_step(MasterDev* __restrict__ st, int max_iter, double tol_rel,
-                                                        double sigma, cudaGraphConditionalHandle cond,
-                                                        int use_cond) {
+// Reduction of the evaluation's partial sums, then the step: every block reduces
+// its share of the outputs, and the block that finishes last (a ticket taken
+// after a memory fence, so all outputs are visible to it) takes the step.  No
+// block waits for another.  The while-node condition is set to "not done" on
+// every path that continues; the evaluation cap inside the step guarantees that
+// done is reached.
+__global__ void __launch_bounds__(STEP_T) k_master_reduce_step(const float* __restrict__ H_part,
+                                                               const double* __restrict__ g_part,
+                                                               const float* __restrict__ gn_part,
+                                                               const double* __restrict__ F_part, int GH, int GE,
+                                                               MasterDev* __restrict__ st, int max_iter,
+                                                               double tol_rel, double sigma,
+                                                               cudaGraphConditionalHandle cond, int use_cond) {
+    __shared__ int s_last;
+    if (st->done) {  // the same for every block: only the last block of a launch changes it
+        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+        return;
+    }
+    master_reduce_part(H_part, g_part, gn_part, F_part, GH, GE, st->K, st);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) st->ticket = 0;
     master_step_body(st, max_iter, tol_rel, sigma);
     if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
 }
@@ -804,17 +917,12 @@ cudaError_t launch_master_hess(const MasterBuffers& mb, int K, int mode, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t launch_master_reduce(int K, const MasterBuffers& mb, cudaStream_t stream, int* launches) {
-    const int outs = K * (K + 1) / 2 + 2 * K + 1;
-    k_master_reduce<<<(outs + 7) / 8, 256, 0, stream>>>(mb.H_part, mb.g_part, mb.gn_part, mb.F_part, mb.GH,
-                                                         mb.grid[K], mb.st);
-    ++*launches;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_master_step(const MasterBuffers& mb, int max_iter, double tol_rel,
+cudaError_t launch_master_step(int K, const MasterBuffers& mb, int max_iter, double tol_rel,
                                cudaGraphConditionalHandle cond, int use_cond, cudaStream_t stream, int* launches) {
-    k_master_step<<<1, STEP_T, 0, stream>>>(mb.st, max_iter, tol_rel, 1e-4, cond, use_cond);
+    const int outs = K * (K + 1) / 2 + 2 * K + 1;
+    k_master_reduce_step<<<(outs + STEP_W - 1) / STEP_W, STEP_T, 0, stream>>>(
+        mb.H_part, mb.g_part, mb.gn_part, mb.F_part, mb.GH, mb.grid[K], mb.st, max_iter, tol_rel, 1e-4, cond,
+        use_cond);
     ++*launches;
     return cudaGetLastError();
 }

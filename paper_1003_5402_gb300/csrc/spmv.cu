@@ -233,8 +233,9 @@ __device__ __forceinline__ float unpack1(unsigned short b) {
 }
 
 // a1 with rows padded to 8 entries: uint4 loads of 8 uint16 columns and 8 values;
-// x pre-multiplied by the beamlet scale in shared memory.
-template <int G, bool BF>
+// x pre-multiplied by the beamlet scale in shared memory (or, when N floats do
+// not fit in 48 KB, the product formed from global memory per entry).
+template <int G, bool BF, bool SMEM_X>
 __global__ void __launch_bounds__(256) k_dose16(const int* __restrict__ rowptr, const uint4* __restrict__ col8,
                                                 const uint4* __restrict__ val8, int V, const float* __restrict__ x,
                                                 const float* __restrict__ scale, int N,
@@ -244,9 +245,11 @@ __global__ void __launch_bounds__(256) k_dose16(const int* __restrict__ rowptr, 
     extern __shared__ float sx[];
     __shared__ StructTermsD s_td[SMAX];
     __shared__ double s_red[8];
-    for (int i = threadIdx.x; i < N; i += blockDim.x) sx[i] = x[i] * scale[i];
+    if (SMEM_X)
+        for (int i = threadIdx.x; i < N; i += blockDim.x) sx[i] = x[i] * scale[i];
     for (int i = threadIdx.x; i < S; i += blockDim.x) s_td[i] = td[i];
     __syncthreads();
+    auto xs = [&](unsigned c) -> float { return SMEM_X ? sx[c] : __ldg(x + c) * __ldg(scale + c); };
     const int lane = threadIdx.x & 31;
     const int sub = lane % G;
     constexpr int RPW = 32 / G;
@@ -267,8 +270,8 @@ __global__ void __launch_bounds__(256) k_dose16(const int* __restrict__ rowptr, 
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const float2 v2 = unpack2<BF>(vs[q]);
-                    acc = fmaf(v2.x, sx[cs[q] & 0xffffu], acc);
-                    acc = fmaf(v2.y, sx[cs[q] >> 16], acc);
+                    acc = fmaf(v2.x, xs(cs[q] & 0xffffu), acc);
+                    acc = fmaf(v2.y, xs(cs[q] >> 16), acc);
                 }
             }
         }
@@ -384,9 +387,15 @@ __global__ void __launch_bounds__(256) k_column16_dev(const unsigned short* __re
 template <int G, bool BF>
 cudaError_t dose16_g(const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsD* td, int S,
                      float* z, float* grad, double* F_part, int grid, cudaStream_t stream) {
-    k_dose16<G, BF><<<grid, 256, (size_t)D.n_cols * sizeof(float), stream>>>(
-        D.rowptr, reinterpret_cast<const uint4*>(D.col16), reinterpret_cast<const uint4*>(D.val16), D.n_rows, x,
-        D.scale, D.n_cols, vstruct, td, S, z, grad, F_part);
+    const size_t smem = (size_t)D.n_cols * sizeof(float);
+    if (smem <= 48 * 1024)
+        k_dose16<G, BF, true><<<grid, 256, smem, stream>>>(
+            D.rowptr, reinterpret_cast<const uint4*>(D.col16), reinterpret_cast<const uint4*>(D.val16), D.n_rows, x,
+            D.scale, D.n_cols, vstruct, td, S, z, grad, F_part);
+    else
+        k_dose16<G, BF, false><<<grid, 256, 0, stream>>>(
+            D.rowptr, reinterpret_cast<const uint4*>(D.col16), reinterpret_cast<const uint4*>(D.val16), D.n_rows, x,
+            D.scale, D.n_cols, vstruct, td, S, z, grad, F_part);
     return cudaGetLastError();
 }
 

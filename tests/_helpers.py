@@ -77,3 +77,42 @@ def need_cuda():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     return torch
+
+
+# ---------------------------------------------------------------------------
+# 16-bit storage of D written out from its definition: per-beamlet scale
+# s_i = max_j |D_ij| (1 for an empty beamlet), stored value RN16(D_ij / s_i)
+# with the quotient first rounded to FP32 (IEEE division), round-to-nearest-even.
+# ---------------------------------------------------------------------------
+
+def bf16_round(x32):
+    """FP32 -> nearest bfloat16 (ties to even), returned as FP32 (finite inputs)."""
+    u = np.ascontiguousarray(x32, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def beamlet_scale(case):
+    N = int(np.sum(np.asarray(case.rows, np.int64) * np.asarray(case.cols, np.int64)))
+    s = np.zeros(N, np.float32)
+    np.maximum.at(s, np.asarray(case.indices, np.int64), np.abs(np.asarray(case.data, np.float32)))
+    s[~(s > 0)] = 1.0
+    return s
+
+
+def quantized_case(case, prec):
+    """A copy of ``case`` whose D holds the dequantised values s_i * RN16(D_ij / s_i)
+    in FP64 (exact: at most 11 + 24 significant bits)."""
+    import copy
+    s = beamlet_scale(case)
+    col = np.asarray(case.indices, np.int64)
+    r = (np.asarray(case.data, np.float32) / s[col]).astype(np.float32)
+    if prec == "fp16":
+        q = r.astype(np.float16).astype(np.float64)
+    elif prec == "bf16":
+        q = bf16_round(r).astype(np.float64)
+    else:
+        raise ValueError(prec)
+    out = copy.copy(case)
+    out.data = q * s[col].astype(np.float64)
+    return out

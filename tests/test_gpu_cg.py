@@ -43,12 +43,16 @@ def _tie_window(case, D, pi_gpu, pi_ref, apertures):
     return tot
 
 
-def _teacher_forced(case, K, torch):
+def _teacher_forced(case, K, torch, plan_kw=None, ref_case=None):
+    """Teacher-forced column generation: the GPU prices from its own state, and
+    the oracle's aperture is added on both sides.  ``ref_case`` (default: case)
+    is the matrix the oracle sees: the dequantised D for 16-bit storage."""
+    gpu_case, case = case, (case if ref_case is None else ref_case)
     D = O.csr64(case)
     steps = []
     ref = O.column_generation(case, K, callback=lambda k, pr, m: steps.append((pr, m)))
     out = {"F_gpu": [], "F_ref": list(ref.objective), "ties": 0, "exact": 0}
-    with _plan(case, torch) as plan:
+    with _plan(gpu_case, torch, **(plan_kw or {})) as plan:
         zbuf = torch.empty(case.n_voxels, dtype=torch.float32, device="cuda")
         pbuf = torch.empty_like(zbuf)
         for k, (b_ref, lv_ref) in enumerate(ref.apertures):
