@@ -49,7 +49,8 @@ struct MasterDev {
     double d[KMAX];       // search direction
     double g[KMAX];       // gradient at y
     double gt[KMAX];      // gradient at the trial point (written by the reduction)
-    double Ht[KMAX * KMAX];  // curvature matrix at the trial point (full, symmetric)
+    float Ht[KMAX * KMAX];   // curvature matrix at the trial point (full, symmetric; FP64 sums
+                             // rounded once to FP32, the precision of the factorisation)
     float gn[KMAX];       // sum_j |S_jk pi_j| at the trial point: the rounding scale of g_k
     double F;             // objective at y
     double Ft;            // objective at the trial point

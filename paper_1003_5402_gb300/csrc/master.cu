@@ -470,8 +470,8 @@ __device__ __forceinline__ void master_reduce_part(const float* __restrict__ H_p
                     ++r;
                 }
                 const int c = r + rem;
-                st->Ht[r * KMAX + c] = s;
-                st->Ht[c * KMAX + r] = s;
+                st->Ht[r * KMAX + c] = (float)s;
+                st->Ht[c * KMAX + r] = (float)s;
             }
         } else if (o < E + K) {
             const int k = o - E;
@@ -499,17 +499,6 @@ constexpr int STEP_T = 256;
 constexpr int STEP_W = STEP_T / 32;
 static_assert(STEP_T == 256 && KMAX == 64, "the step kernel maps a 16 x 16 thread grid onto 64 x 64 entries");
 
-__device__ __forceinline__ double blk_sum(double v, double* sw) {
-    v = warp_sum_f64(v);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double t = 0.0;
-#pragma unroll
-    for (int w = 0; w < STEP_W; ++w) t += sw[w];
-    return t;
-}
-
 __device__ __forceinline__ double blk_max(double v, double* sw) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
@@ -522,16 +511,6 @@ __device__ __forceinline__ double blk_max(double v, double* sw) {
     return t;
 }
 
-__device__ __forceinline__ int blk_or(int v, int* swi) {
-    v = __any_sync(FULL, v) ? 1 : 0;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) swi[threadIdx.x >> 5] = v;
-    __syncthreads();
-    int t = 0;
-#pragma unroll
-    for (int w = 0; w < STEP_W; ++w) t |= swi[w];
-    return t;
-}
 
 // One block: thread k < K owns variable k; all threads share the factorisation.
 __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int max_iter, double tol_rel,
@@ -545,39 +524,62 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     __shared__ float rhs[KMAX];
     __shared__ int fidx[KMAX];
     __shared__ double sw[STEP_W];
+    __shared__ double sw2[STEP_W];
     __shared__ int swi[STEP_W];
-    if (st->done) return;
-    if (st->err) {  // a tile copy was lost in an evaluation: stop with the last accepted point
+    // every value the step reads is loaded up front (independent loads, one round
+    // trip); gt, gn, Ft and Ht were written by other blocks of this launch and
+    // are read through L2 (__ldcg), never from a possibly stale L1 line
+    const int k = threadIdx.x;
+    const int kk = k < KMAX ? k : KMAX - 1;
+    const int done = st->done, err = st->err, K = st->K, phase = st->phase, iter0 = st->iter;
+    const double tol0 = st->tol, F0 = st->F, Ft = __ldcg(&st->Ft);
+    const double yt_ = st->yt[kk], gt_ = __ldcg(&st->gt[kk]), gn_ = (double)__ldcg(&st->gn[kk]);
+    const double y_ = st->y[kk], g_ = st->g[kk];
+    if (done) return;
+    if (err) {  // a tile copy was lost in an evaluation: stop with the last accepted point
         if (threadIdx.x == 0) {
             st->status = MASTER_ERROR;
             st->done = 1;
         }
         return;
     }
-    const int K = st->K;
-    const int k = threadIdx.x;
     const bool own = k < K;
-    const int phase = st->phase;
-    // gt, gn, Ft and Ht were written by other blocks of this launch: read them
-    // through L2 (__ldcg), never from a possibly stale L1 line
-    const double yt = own ? st->yt[k] : 0.0;
-    const double gt = own ? __ldcg(&st->gt[k]) : 0.0;
-    const double gn = own ? (double)__ldcg(&st->gn[k]) : 0.0;
-    const double y = own ? st->y[k] : 0.0;
-    const double g = own ? st->g[k] : 0.0;
+    const double yt = own ? yt_ : 0.0, gt = own ? gt_ : 0.0, gn = own ? gn_ : 0.0;
+    const double y = own ? y_ : 0.0, g = own ? g_ : 0.0;
     // tolerance of this solve from the gradient at the warm start
-    double tol = st->tol;
+    double tol = tol0;
     if (phase == 0) {
         tol = tol_rel * fmax(blk_max(own ? fabs(gt) : 0.0, sw), 1e-300);
         if (k == 0) st->tol = tol;
     }
+    // KKT violation flag, residual and Armijo decrease in one block reduction
     const double rt = own ? fabs(yt - fmax(yt - gt, 0.0)) : 0.0;
-    const int viol = blk_or(own && rt > tol + NOISE * (double)U32 * gn, swi);
-    const double rmax = blk_max(rt, sw);
-    const double dec = blk_sum(own ? g * (yt - y) : 0.0, sw);
-    const bool cap = st->iter >= max_iter + 64;
-    const double Ft = __ldcg(&st->Ft);
-    const bool accept = !cap && (phase == 0 || !viol || Ft <= st->F + sigma * dec);
+    int viol = __any_sync(FULL, own && rt > tol + NOISE * (double)U32 * gn) ? 1 : 0;
+    double rmax = rt;
+    double dec = own ? g * (yt - y) : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rmax = fmax(rmax, __shfl_xor_sync(FULL, rmax, o));
+        dec += __shfl_xor_sync(FULL, dec, o);
+    }
+    __syncthreads();
+    if ((k & 31) == 0) {
+        sw[k >> 5] = rmax;
+        sw2[k >> 5] = dec;
+        swi[k >> 5] = viol;
+    }
+    __syncthreads();
+    rmax = sw[0];
+    dec = sw2[0];
+    viol = swi[0];
+#pragma unroll
+    for (int w = 1; w < STEP_W; ++w) {
+        rmax = fmax(rmax, sw[w]);
+        dec += sw2[w];
+        viol |= swi[w];
+    }
+    const bool cap = iter0 >= max_iter + 64;
+    const bool accept = !cap && (phase == 0 || !viol || Ft <= F0 + sigma * dec);
     if (k == 0) ++st->n_eval;
     if (cap) {
         if (k == 0) {
@@ -612,7 +614,7 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
         st->F = Ft;
         st->res = rmax;
     }
-    if (!viol || st->iter >= max_iter) {
+    if (!viol || iter0 >= max_iter) {
         if (k == 0) {
             st->status = viol ? MASTER_MAXITER : MASTER_CONVERGED;
             st->done = 1;
@@ -661,7 +663,7 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int i = ti + 16 * a, q = tq + 16 * b;
-            Hr[a][b] = (i < nf && q <= i) ? (float)__ldcg(&st->Ht[fidx[i] * KMAX + fidx[q]]) : 0.f;
+            Hr[a][b] = (i < nf && q <= i) ? __ldcg(&st->Ht[fidx[i] * KMAX + fidx[q]]) : 0.f;
         }
     const float bk = k < nf ? -(float)st->g[fidx[k]] : 0.f;
     float dg = 0.f;
@@ -795,7 +797,7 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
         __syncthreads();
         if (fr) d = (double)rhs[pos];
     } else if (fr) {
-        const double hk = __ldcg(&st->Ht[k * KMAX + k]);
+        const double hk = (double)__ldcg(&st->Ht[k * KMAX + k]);
         d = -gt / (hk > 0.0 ? hk : 1.0);
     }
     if (own) {
