@@ -44,6 +44,8 @@ def _args():
     p.add_argument("--skip-e2e", action="store_true")
     p.add_argument("--skip-spmv", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--skip-batch", action="store_true")
+    p.add_argument("--batch", type=int, default=16, help="instances per workload in the batched re-plan leg")
     return p.parse_args()
 
 
@@ -213,6 +215,67 @@ def run_reference(a):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def _make_case_spec(spec):
+    return phantom.make_case(spec)
+
+
+def batch_instances(n_each):
+    """Re-plan instances: n_each prostate-shaped and n_each H&N-shaped phantoms,
+    targets shifted and OARs scaled per instance (seeds 4000 + i), generated in
+    a spawn process pool."""
+    import multiprocessing as mp
+    specs = [phantom.perturb(phantom.spec_prostate(), 4000 + i) for i in range(n_each)]
+    specs += [phantom.perturb(phantom.spec_hn(), 4000 + n_each + i) for i in range(n_each)]
+    workers = max(1, min(len(specs), os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_make_case_spec, specs)
+
+
+def run_batch(torch, dev, flush, cases, n_each, apertures):
+    """Batched re-plans: all instances through dao_batch_solve (each on its own
+    stream, rounds interleaved) against the same plans one after another; H&N
+    instances use FP16 storage.  Launch shapes come from the autotuner."""
+    import tempfile
+    from paper_1003_5402_gb300 import Plan, binding
+    cache = os.path.join(tempfile.gettempdir(), "dao_autotune.txt")
+    plans = []
+    try:
+        for i, c in enumerate(cases):
+            prec = binding.DAO_PREC_FP16 if i >= n_each else binding.DAO_PREC_FP32
+            p = Plan(c, device=dev, precision=prec)
+            p.autotune(cache)
+            plans.append(p)
+        binding.batch_solve(plans, apertures)                   # warm: builds every round graph
+        seq, bat = [], []
+        for _ in range(2):
+            for p in plans:
+                p.reset()
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = binding.batch_solve(plans, apertures)
+            bat.append(time.perf_counter() - t0)
+            for p in plans:
+                p.reset()
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for p in plans:
+                p.solve(apertures)
+            seq.append(time.perf_counter() - t0)
+        n = len(plans)
+        return {"instances": n, "workloads": f"{n_each} prostate-shaped FP32 + {n_each} H&N-shaped FP16, "
+                                             f"perturbed (seeds 4000+i), {apertures} apertures each",
+                "batched_s": round(min(bat), 4), "sequential_s": round(min(seq), 4),
+                "plans_per_s_batched": round(n / min(bat), 2), "plans_per_s_sequential": round(n / min(seq), 2),
+                "speedup": round(min(seq) / min(bat), 3),
+                "apertures_done": [r[1] for r in res],
+                "timing": "host wall clock around the synchronous calls, L2 flushed before each, best of 2"}
+    finally:
+        for p in plans:
+            p.close()
+
+
 def spmv_bandwidth(torch, plan, case, prec, flush, hbm_peak):
     """Cold-L2 a1 and a2 alone: median of 20 runs, each timed with CUDA events."""
     out = {}
@@ -253,6 +316,7 @@ def run_ours(a):
     from paper_1003_5402_gb300 import Plan, build
     build.build()
     case = _case(a.config)
+    batch_cases = batch_instances(a.batch) if (not a.skip_batch and rank == 0) else None
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -380,6 +444,10 @@ def run_ours(a):
                "d2h_bytes_per_step": int(d2h), "steps": n_e2e,
                "includes": "dao_create (validation, D^T build, upload) + dao_solve + dao_dose to host"}
 
+    batch = None
+    if batch_cases is not None:
+        batch = run_batch(torch, dev, flush, batch_cases, a.batch, a.apertures)
+
     cpu = None
     if rank == 0 and ws == 1 and not a.skip_cpu:
         secs = oracle_plan_seconds(case, a.apertures)
@@ -398,7 +466,7 @@ def run_ours(a):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
             "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
                            "p99": round(float(np.percentile(lat, 99)), 4)},
-            "spmv": spmv, "mixed_precision": mixed, "kernel_ms_host_driven_plan": kernel_ms, "kernel_launches_host_driven_plan": kernel_launches,
+            "spmv": spmv, "mixed_precision": mixed, "batch": batch, "kernel_ms_host_driven_plan": kernel_ms, "kernel_launches_host_driven_plan": kernel_launches,
             "objective_final": F_final, "apertures_done": int(n), "master_evals": int(np.sum(ev)),
             "host_wall_s": round(t_host, 3), "device": torch.cuda.get_device_name(dev),
         }

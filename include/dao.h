@@ -227,6 +227,45 @@ int64_t dao_launch_count(const dao_ctx* ctx);
  * ||y - P(y - g)||_inf divided by max|g| at the warm start; *k = solves. */
 dao_status dao_master_stats(const dao_ctx* ctx, int32_t* evals, int32_t* status, double* kkt, int32_t* k);
 
+/* ---- batched plans (many instances at once) ----
+ * Column generation (Sec. 2.3, Fig. 1) for n independent contexts in one call:
+ * the same work as dao_solve(ctxs[i], n_apertures, ...) for every i, with every
+ * context's rounds run as its own CUDA graphs on its own stream and launched
+ * round-interleaved, so that the GPU overlaps the instances' small kernels.
+ * The instances share no device state: each one's apertures, intensities,
+ * objective trace and dose are bitwise those of solving it alone.
+ *   ctxs: n distinct contexts on one device, created with use_graphs and with
+ *         profiling off; contexts that share a stream run one after another;
+ *   n_done: int32[n] or NULL, each instance's pool size afterwards;
+ *   traces: double[n][n_apertures] or NULL, each instance's objective after
+ *         each aperture it added (as dao_solve's trace);
+ *   status: int32[n] or NULL, each instance's dao_solve status (DAO_OK,
+ *         DAO_OPTIMAL, DAO_DUPLICATE, or DAO_ESTATE for a full pool).
+ * Returns DAO_EINVAL for invalid arguments (nothing runs), DAO_ECUDA on a CUDA
+ * error, else DAO_OK with the per-instance outcome in status.  Synchronous. */
+dao_status dao_batch_solve(dao_ctx* const* ctxs, int32_t n, int32_t n_apertures, int32_t* n_done, double* traces,
+                           int32_t* status);
+
+/* ---- autotuner of the SpMV launch shapes ----
+ * Times the dose SpMV (a1, lanes per voxel row: 4/8/16/32, 16-bit storage up to
+ * 16), the transposed SpMV (a2, threads per beamlet row: 64/128/256) and the
+ * aperture column (a4, lanes per voxel row: 4/8/16) on the context's own
+ * matrices (10 launches per candidate, captured into a CUDA graph, timed with
+ * events) and keeps the fastest of each for this context.  cache_path (or
+ * NULL): a text file of "key dose column dt" lines, key = device name,
+ * precision and the log2 size class of voxels, beamlets and the mean row
+ * lengths of D and D^T; a matching entry is applied without timing, a new
+ * choice is appended.  out (or NULL) receives the choice and whether it came
+ * from the cache.  Cached round graphs are rebuilt on the next solve.  Results
+ * are unchanged up to the FP32 summation order of the SpMVs. */
+typedef struct {
+    int32_t dose_lanes;    /* a1 lanes per voxel row */
+    int32_t column_lanes;  /* a4 lanes per voxel row */
+    int32_t dt_threads;    /* a2 threads per beamlet row */
+    int32_t from_cache;    /* 1 when read from cache_path, 0 when timed */
+} dao_tuning;
+dao_status dao_autotune(dao_ctx* ctx, const char* cache_path, dao_tuning* out);
+
 /* ---- allocation-free dose with objective (the paper has no counterpart) ----
  * For callers that must not allocate device memory while they run, e.g. a
  * re-planning service that reserves every device buffer before an online

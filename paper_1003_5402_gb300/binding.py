@@ -51,6 +51,11 @@ class dao_options(C.Structure):
                 ("use_graphs", C.c_int32)]
 
 
+class dao_tuning(C.Structure):
+    _fields_ = [("dose_lanes", C.c_int32), ("column_lanes", C.c_int32), ("dt_threads", C.c_int32),
+                ("from_cache", C.c_int32)]
+
+
 SIGNATURES = {
     "dao_options_default": (None, [C.POINTER(dao_options)]),
     "dao_create": (C.c_int, [C.POINTER(dao_csr), C.POINTER(dao_geometry), C.POINTER(dao_structures),
@@ -76,6 +81,8 @@ SIGNATURES = {
     "dao_master_stats": (C.c_int, [_P, _I32P, _I32P, _F64P, _I32P]),
     "dao_dose_objective_noalloc": (C.c_int, [C.c_int32, C.c_int32, _P, _P, _P, _P, _P, C.c_int32, _F64P, _P, _P,
                                              _P, _P]),
+    "dao_batch_solve": (C.c_int, [C.POINTER(_P), C.c_int32, C.c_int32, _I32P, _F64P, _I32P]),
+    "dao_autotune": (C.c_int, [_P, C.c_char_p, C.POINTER(dao_tuning)]),
     "dao_last_error": (C.c_char_p, []),
 }
 
@@ -300,6 +307,14 @@ class Plan:
     def launch_count(self) -> int:
         return int(load().dao_launch_count(self.h))
 
+    def autotune(self, cache_path: Optional[str] = None) -> dict:
+        """dao_autotune: choose the SpMV launch shapes for this plan (cached by size class)."""
+        t = dao_tuning()
+        path = cache_path.encode() if cache_path else None
+        _check(load().dao_autotune(self.h, path, C.byref(t)), "dao_autotune")
+        return {"dose_lanes": t.dose_lanes, "column_lanes": t.column_lanes, "dt_threads": t.dt_threads,
+                "from_cache": bool(t.from_cache)}
+
     def master_stats(self):
         """(evaluations, status, relative KKT residual) per master solve since the last reset."""
         ev = np.zeros(self.k_max, dtype=np.int32)
@@ -323,3 +338,17 @@ def dose_objective_noalloc(row_ptr, col, val, x, voxel_struct, terms, z, grad=No
         _dev(grad, "float32") if grad is not None else None, _dev(objective, "float64"),
         C.c_void_p(stream) if stream is not None else None)
     return _check(st, "dao_dose_objective_noalloc")
+
+
+def batch_solve(plans: Sequence["Plan"], n_apertures: int):
+    """dao_batch_solve: column generation for several plans at once (each on its
+    own stream).  Returns [(status, pool size, objective trace)] per plan, as
+    Plan.solve returns them (the trace NaN past the apertures added)."""
+    n = len(plans)
+    arr = (C.c_void_p * max(n, 1))(*[p.h.value for p in plans])
+    n_done = np.zeros(max(n, 1), dtype=np.int32)
+    status = np.zeros(max(n, 1), dtype=np.int32)
+    traces = np.full((max(n, 1), max(n_apertures, 1)), np.nan)
+    _check(load().dao_batch_solve(C.cast(arr, C.POINTER(C.c_void_p)), n, int(n_apertures), _ptr(n_done, C.c_int32),
+                                  _ptr(traces, C.c_double), _ptr(status, C.c_int32)), "dao_batch_solve")
+    return [(int(status[i]), int(n_done[i]), traces[i, :n_apertures].copy()) for i in range(n)]

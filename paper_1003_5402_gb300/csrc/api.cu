@@ -719,16 +719,29 @@ dao_status build_round_graph(dao_ctx* c, int K) {
 }
 
 // Rounds K_old+1 .. K_new queued back to back; one synchronisation at the end.
-dao_status solve_graph(dao_ctx* c, int n_apertures, int32_t* n_done, double* trace, dao_status* result) {
-    const int K0 = c->K;
-    const int K1 = std::min(c->K_cap, K0 + n_apertures);
-    for (int k = K0 + 1; k <= K1; ++k)
+// Graph path in three parts so that a batch can interleave the launches of
+// several contexts: prepare (graphs, device-side round state), launch one
+// round, finish (read back, bookkeeping).
+struct GraphSolve {
+    int K0 = 0, K1 = 0;
+};
+
+dao_status solve_graph_begin(dao_ctx* c, int n_apertures, GraphSolve* gs) {
+    gs->K0 = c->K;
+    gs->K1 = std::min(c->K_cap, c->K + n_apertures);
+    for (int k = gs->K0 + 1; k <= gs->K1; ++k)
         if (c->round_exec[k] == nullptr) DAO_TRY(build_round_graph(c, k));
     CGDev* h = reinterpret_cast<CGDev*>(c->pinned + c->off_cg);
-    h->K = K0;
+    h->K = gs->K0;
     h->done = 0;
     DAO_CU(cudaMemcpyAsync(c->cg, h, 2 * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    for (int k = K0 + 1; k <= K1; ++k) DAO_CU(cudaGraphLaunch(c->round_exec[k], c->stream));
+    return DAO_OK;
+}
+
+dao_status solve_graph_end(dao_ctx* c, const GraphSolve& gs, int n_apertures, int32_t* n_done, double* trace,
+                           dao_status* result) {
+    const int K0 = gs.K0, K1 = gs.K1;
+    CGDev* h = reinterpret_cast<CGDev*>(c->pinned + c->off_cg);
     DAO_CU(cudaMemcpyAsync(h, c->cg, sizeof(CGDev), cudaMemcpyDeviceToHost, c->stream));
     DAO_TRY(sync(c));
     const int K = h->K;
@@ -762,6 +775,24 @@ dao_status solve_graph(dao_ctx* c, int n_apertures, int32_t* n_done, double* tra
     *result = h->done == 1 ? DAO_OPTIMAL : h->done == 2 ? DAO_DUPLICATE : DAO_OK;
     if (*result == DAO_OK && K0 + n_apertures > c->K_cap) *result = fail(DAO_ESTATE, "aperture pool is full (k_max)");
     return DAO_OK;
+}
+
+dao_status solve_graph(dao_ctx* c, int n_apertures, int32_t* n_done, double* trace, dao_status* result) {
+    GraphSolve gs;
+    DAO_TRY(solve_graph_begin(c, n_apertures, &gs));
+    for (int k = gs.K0 + 1; k <= gs.K1; ++k) DAO_CU(cudaGraphLaunch(c->round_exec[k], c->stream));
+    return solve_graph_end(c, gs, n_apertures, n_done, trace, result);
+}
+
+// Round graphs embed the launch shapes they were captured with: drop them when
+// the shapes change.
+void drop_round_graphs(dao_ctx* c) {
+    for (size_t k = 0; k < c->round_exec.size(); ++k) {
+        if (c->round_exec[k]) cudaGraphExecDestroy(c->round_exec[k]);
+        if (c->round_graph[k]) cudaGraphDestroy(c->round_graph[k]);
+        c->round_exec[k] = nullptr;
+        c->round_graph[k] = nullptr;
+    }
 }
 
 dao_status reset_state(dao_ctx* c) {
@@ -1035,6 +1066,8 @@ dao_status dao_k_state(dao_ctx* c, float* z, float* pi) {
     return DAO_OK;
 }
 
+}  // extern "C"
+
 namespace {
 // One launch of kernel class kc for dao_k_time.
 cudaError_t time_one(dao_ctx* c, int kc, int K, cudaStream_t s, int* n) {
@@ -1060,26 +1093,18 @@ cudaError_t time_one(dao_ctx* c, int kc, int K, cudaStream_t s, int* n) {
     }
     return cudaErrorInvalidValue;
 }
-}  // namespace
-
-dao_status dao_k_time(dao_ctx* c, int32_t kc, int32_t K, int32_t reps, double* us_per_launch) {
-    DAO_TRY(check_ctx(c));
-    if (reps < 1 || !us_per_launch) return fail(DAO_EINVAL, "reps must be >= 1 and the output non-null");
-    if ((kc == DAO_KC_MASTER_PASS || kc == DAO_KC_MASTER_HESS) && (K < 1 || K > c->K))
-        return fail(DAO_EINVAL, "master kernel timing needs 1 <= K <= the current pool size");
-    if (kc == DAO_KC_COLUMN && c->K < 1) return fail(DAO_EINVAL, "column timing needs an aperture in the pool");
-    if (kc != DAO_KC_MASTER_PASS && kc != DAO_KC_MASTER_HESS && kc != DAO_KC_DT && kc != DAO_KC_DOSE &&
-        kc != DAO_KC_COLUMN && kc != DAO_KC_PRICE)
-        return fail(DAO_EINVAL, "kernel class cannot be timed on its own");
-    // the reps launches are captured into a graph so that they run back to back on
-    // the device, without host launch gaps, between the two events
+// Average microseconds of one launch: reps launches captured into a CUDA graph
+// (so that they run back to back on the device, without host launch gaps), one
+// warm replay, one replay timed with events on the context's stream.
+template <class F>
+dao_status time_graph(dao_ctx* c, int reps, F&& launch, double* us, const char* what) {
     DAO_TRY(sync(c));
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ex = nullptr;
     int n = 0;
     DAO_CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = time_one(c, kc, K, c->stream, &n);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch(&n);
     cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
@@ -1095,10 +1120,69 @@ dao_status dao_k_time(dao_ctx* c, int32_t kc, int32_t K, int32_t reps, double* u
     if (ex) cudaGraphExecDestroy(ex);
     if (g) cudaGraphDestroy(g);
     if (e0 && e1) c->ev_used -= 2;
-    if (e != cudaSuccess) return fail(DAO_ECUDA, std::string("dao_k_time: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(DAO_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
     c->launches_i += 2 * n;
     c->count_launches();
-    *us_per_launch = 1e3 * ms / reps;
+    *us = 1e3 * ms / reps;
+    return DAO_OK;
+}
+
+// Autotuner cache key: device, storage and the size class of the problem
+// (log2 buckets of voxels, beamlets and the mean row lengths of D and D^T).
+std::string tune_key(const dao_ctx* c) {
+    cudaDeviceProp prop;
+    std::string dev = cudaGetDeviceProperties(&prop, c->device) == cudaSuccess ? prop.name : "unknown";
+    for (char& ch : dev)
+        if (ch == ' ' || ch == '\t') ch = '_';
+    auto lb = [](double v) { return (int)std::lround(std::log2(std::max(v, 1.0))); };
+    const double row_d = c->V > 0 ? (double)c->nnz / c->V : 0.0, row_t = c->N > 0 ? (double)c->nnz / c->N : 0.0;
+    return dev + "|prec=" + std::to_string(c->opt.precision) + "|V=" + std::to_string(lb(c->V)) + "|N=" +
+           std::to_string(lb(c->N)) + "|rowD=" + std::to_string(lb(row_d)) + "|rowDt=" + std::to_string(lb(row_t));
+}
+
+bool tune_cache_read(const char* path, const std::string& key, int* dose_g, int* col_g, int* dt_t) {
+    if (!path) return false;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {  // the last entry for a key wins
+        char k[400];
+        int a = 0, b = 0, t = 0;
+        if (std::sscanf(line, "%399s %d %d %d", k, &a, &b, &t) == 4 && key == k) {
+            *dose_g = a;
+            *col_g = b;
+            *dt_t = t;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+template <size_t M>
+bool tune_allowed(const int (&set)[M], int v) {
+    for (size_t i = 0; i < M; ++i)
+        if (set[i] == v) return true;
+    return false;
+}
+
+}  // namespace
+
+extern "C" {
+
+dao_status dao_k_time(dao_ctx* c, int32_t kc, int32_t K, int32_t reps, double* us_per_launch) {
+    DAO_TRY(check_ctx(c));
+    if (reps < 1 || !us_per_launch) return fail(DAO_EINVAL, "reps must be >= 1 and the output non-null");
+    if ((kc == DAO_KC_MASTER_PASS || kc == DAO_KC_MASTER_HESS) && (K < 1 || K > c->K))
+        return fail(DAO_EINVAL, "master kernel timing needs 1 <= K <= the current pool size");
+    if (kc == DAO_KC_COLUMN && c->K < 1) return fail(DAO_EINVAL, "column timing needs an aperture in the pool");
+    if (kc != DAO_KC_MASTER_PASS && kc != DAO_KC_MASTER_HESS && kc != DAO_KC_DT && kc != DAO_KC_DOSE &&
+        kc != DAO_KC_COLUMN && kc != DAO_KC_PRICE)
+        return fail(DAO_EINVAL, "kernel class cannot be timed on its own");
+    double us = 0.0;
+    DAO_TRY(time_graph(c, reps, [&](int* n) { return time_one(c, kc, K, c->stream, n); }, &us, "dao_k_time"));
+    *us_per_launch = us;
     return DAO_OK;
 }
 
@@ -1140,6 +1224,123 @@ dao_status dao_master_stats(const dao_ctx* c, int32_t* evals, int32_t* status, d
         if (kkt) kkt[i] = c->stat_kkt[i];
     }
     if (k) *k = n;
+    return DAO_OK;
+}
+
+dao_status dao_batch_solve(dao_ctx* const* ctxs, int32_t n, int32_t n_apertures, int32_t* n_done, double* traces,
+                           int32_t* status) {
+    if (n < 0 || n_apertures < 0 || (n > 0 && ctxs == nullptr))
+        return fail(DAO_EINVAL, "dao_batch_solve: n >= 0, n_apertures >= 0 and a context array are required");
+    for (int i = 0; i < n; ++i) {
+        if (ctxs[i] == nullptr) return fail(DAO_EINVAL, "dao_batch_solve: null context " + std::to_string(i));
+        if (!ctxs[i]->opt.use_graphs || ctxs[i]->prof_on)
+            return fail(DAO_EINVAL, "dao_batch_solve: every context needs use_graphs and profiling off");
+        if (ctxs[i]->device != ctxs[0]->device)
+            return fail(DAO_EINVAL, "dao_batch_solve: the contexts must be on one device");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return fail(DAO_EINVAL, "dao_batch_solve: context listed twice");
+    }
+    if (n == 0) return DAO_OK;
+    DAO_TRY(check_ctx(ctxs[0]));
+    std::vector<GraphSolve> gs(n);
+    std::vector<char> run(n, 0);
+    int rounds = 0;
+    for (int i = 0; i < n; ++i) {
+        dao_ctx* c = ctxs[i];
+        if (status) status[i] = DAO_OK;
+        if (n_done) n_done[i] = c->K;
+        if (c->K >= c->K_cap && n_apertures > 0) {
+            if (status) status[i] = DAO_ESTATE;
+            continue;
+        }
+        DAO_TRY(solve_graph_begin(c, n_apertures, &gs[i]));
+        run[i] = 1;
+        rounds = std::max(rounds, gs[i].K1 - gs[i].K0);
+    }
+    // interleaved: round r of every instance before round r + 1 of any, each on
+    // its own stream, so that the GPU overlaps the instances' kernels
+    for (int r = 0; r < rounds; ++r)
+        for (int i = 0; i < n; ++i) {
+            if (!run[i]) continue;
+            const int k = gs[i].K0 + 1 + r;
+            if (k <= gs[i].K1) DAO_CU(cudaGraphLaunch(ctxs[i]->round_exec[k], ctxs[i]->stream));
+        }
+    for (int i = 0; i < n; ++i) {
+        if (!run[i]) continue;
+        dao_status res = DAO_OK;
+        DAO_TRY(solve_graph_end(ctxs[i], gs[i], n_apertures, n_done ? n_done + i : nullptr,
+                                traces ? traces + (size_t)i * n_apertures : nullptr, &res));
+        ctxs[i]->count_launches();
+        if (status) status[i] = res;
+    }
+    return DAO_OK;
+}
+
+dao_status dao_autotune(dao_ctx* c, const char* cache_path, dao_tuning* out) {
+    DAO_TRY(check_ctx(c));
+    const std::string key = tune_key(c);
+    int dg = 0, cg = 0, dt = 0;
+    bool cached = tune_cache_read(cache_path, key, &dg, &cg, &dt) && tune_allowed(TUNE_DOSE_G, dg) &&
+                  tune_allowed(TUNE_COL_G, cg) && tune_allowed(TUNE_DT_THREADS, dt);
+    if (cached && c->opt.precision != DAO_PREC_FP32 && dg > 16) cached = false;
+    if (!cached) {
+        const int reps = 10;
+        double best = 1e300;
+        for (int g : TUNE_DOSE_G) {  // a1: lanes per voxel row
+            if (c->opt.precision != DAO_PREC_FP32 && g > 16) continue;
+            c->D.tune_dose_g = g;
+            double us = 0.0;
+            DAO_TRY(time_graph(c, reps, [&](int* nl) {
+                return launch_dose(c->D, c->x, c->vstruct, c->tf, c->td, c->S, c->dose, nullptr, nullptr, 0, nullptr,
+                                   c->num_sms, c->stream, nl);
+            }, &us, "dao_autotune"));
+            if (us < best) {
+                best = us;
+                dg = g;
+            }
+        }
+        best = 1e300;
+        for (int t : TUNE_DT_THREADS) {  // a2: threads per beamlet row
+            c->Dt.tune_dt_threads = t;
+            double us = 0.0;
+            DAO_TRY(time_graph(c, reps, [&](int* nl) { return launch_dt(c->Dt, c->pi, c->w, nullptr, c->stream, nl); },
+                               &us, "dao_autotune"));
+            if (us < best) {
+                best = us;
+                dt = t;
+            }
+        }
+        best = 1e300;
+        for (int g : TUNE_COL_G) {  // a4: lanes per voxel row over beam 0's segment
+            c->D.tune_col_g = g;
+            double us = 0.0;
+            DAO_TRY(time_graph(c, reps, [&](int* nl) {
+                return launch_column(c->D, c->seg, c->seg + (size_t)c->V, c->beam_off[0], c->rows[0] * c->cols[0],
+                                     c->mask, c->dose, 1, c->num_sms, c->stream, nl);
+            }, &us, "dao_autotune"));
+            if (us < best) {
+                best = us;
+                cg = g;
+            }
+        }
+        if (cache_path) {
+            FILE* f = std::fopen(cache_path, "a");
+            if (f) {
+                std::fprintf(f, "%s %d %d %d\n", key.c_str(), dg, cg, dt);
+                std::fclose(f);
+            }
+        }
+    }
+    c->D.tune_dose_g = dg;
+    c->D.tune_col_g = cg;
+    c->Dt.tune_dt_threads = dt;
+    drop_round_graphs(c);
+    if (out) {
+        out->dose_lanes = dg;
+        out->column_lanes = cg;
+        out->dt_threads = dt;
+        out->from_cache = cached ? 1 : 0;
+    }
     return DAO_OK;
 }
 

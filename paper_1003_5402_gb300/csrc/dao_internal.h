@@ -40,7 +40,18 @@ struct DevCSR {
     unsigned short* col16 = nullptr;  // 16-bit layout of D: beamlet indices
     unsigned short* val16 = nullptr;  // 16-bit values D_ij / s_i (FP16 or BF16 bits)
     const float* scale = nullptr;     // 16-bit layout: per-beamlet scale s_i (length n_beamlets)
+    // launch shape chosen by the autotuner (0: built-in rule): lanes per row of the
+    // dose SpMV and of the aperture column (D), threads per row of the transposed
+    // SpMV (D^T)
+    int tune_dose_g = 0;
+    int tune_col_g = 0;
+    int tune_dt_threads = 0;
 };
+
+// Launch shapes the autotuner may choose from.
+constexpr int TUNE_DOSE_G[] = {4, 8, 16, 32};
+constexpr int TUNE_COL_G[] = {4, 8, 16};
+constexpr int TUNE_DT_THREADS[] = {64, 128, 256};
 
 // Projected-Newton master state (device memory, one per context).
 struct MasterDev {

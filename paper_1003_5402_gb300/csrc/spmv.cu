@@ -422,30 +422,97 @@ int dose_grid(int n_rows, int num_sms) {
     return num_sms * 8;
 }
 
+namespace {
+
+// lanes per voxel row of the dose SpMV: the autotuner's choice, else by the mean
+// stored row length (16-bit rows hold 8 entries per load, FP32 rows 4)
+int dose_lanes(const DevCSR& D) {
+    const double mean = D.n_rows > 0 ? (double)D.nnz_stored / (double)D.n_rows : 0.0;
+    int g = D.tune_dose_g;
+    if (g == 0) {
+        if (D.prec != DAO_PREC_FP32)
+            g = mean <= 48.0 ? 4 : mean <= 128.0 ? 8 : 16;
+        else
+            g = mean <= 24.0 ? 4 : mean <= 64.0 ? 8 : mean <= 160.0 ? 16 : 32;
+    }
+    if (D.prec != DAO_PREC_FP32 && g > 16) g = 16;
+    return g;
+}
+
+template <bool BF>
+cudaError_t dose16_any(int g, const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsD* td,
+                       int S, float* z, float* grad, double* F_part, int grid, cudaStream_t stream) {
+    switch (g) {
+        case 4: return dose16_g<4, BF>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+        case 8: return dose16_g<8, BF>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+        default: return dose16_g<16, BF>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+    }
+}
+
+template <int BT>
+void dt_launch(const DevCSR& Dt, const float* pi, float* w, const int* skip, cudaStream_t stream) {
+    if (Dt.prec == DAO_PREC_FP16)
+        k_dt16<BT, false><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
+                                                        reinterpret_cast<const uint4*>(Dt.val16), Dt.scale,
+                                                        Dt.n_rows, pi, w, skip);
+    else if (Dt.prec == DAO_PREC_BF16)
+        k_dt16<BT, true><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
+                                                       reinterpret_cast<const uint4*>(Dt.val16), Dt.scale,
+                                                       Dt.n_rows, pi, w, skip);
+    else
+        k_dt<BT><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
+                                                reinterpret_cast<const float4*>(Dt.val), Dt.n_rows, pi, w, skip);
+}
+
+template <int G>
+void column_launch(const DevCSR& D, const int* seg_lo, const int* seg_hi, int base, int nb, const float* mask,
+                   float* out, int stride, int grid, cudaStream_t stream) {
+    const size_t sm = (size_t)nb * sizeof(float);
+    if (D.prec == DAO_PREC_FP16)
+        k_column16<G, false><<<grid, 256, sm, stream>>>(D.col16, D.val16, seg_lo, seg_hi, D.n_rows, base, nb, mask,
+                                                         D.scale, out, stride);
+    else if (D.prec == DAO_PREC_BF16)
+        k_column16<G, true><<<grid, 256, sm, stream>>>(D.col16, D.val16, seg_lo, seg_hi, D.n_rows, base, nb, mask,
+                                                        D.scale, out, stride);
+    else
+        k_column<G><<<grid, 256, sm, stream>>>(D.col, D.val, seg_lo, seg_hi, D.n_rows, base, nb, mask, out, stride);
+}
+
+template <int G>
+void column_dev_launch(const DevCSR& D, const int* seg, const int* ap_beam, int K, const int* beam_off,
+                       const int* rows, const int* cols, int max_nb, const float* mask, float* out, int stride,
+                       const CGDev* cg, int grid, cudaStream_t stream) {
+    const size_t sm = (size_t)max_nb * sizeof(float);
+    if (D.prec == DAO_PREC_FP16)
+        k_column16_dev<G, false><<<grid, 256, sm, stream>>>(D.col16, D.val16, seg, D.n_rows, ap_beam, K, beam_off,
+                                                             rows, cols, mask, D.scale, out, stride, cg);
+    else if (D.prec == DAO_PREC_BF16)
+        k_column16_dev<G, true><<<grid, 256, sm, stream>>>(D.col16, D.val16, seg, D.n_rows, ap_beam, K, beam_off,
+                                                            rows, cols, mask, D.scale, out, stride, cg);
+    else
+        k_column_dev<G><<<grid, 256, sm, stream>>>(D.col, D.val, seg, D.n_rows, ap_beam, K, beam_off, rows, cols,
+                                                    mask, out, stride, cg);
+}
+
+}  // namespace
+
 cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsF* tf,
                         const StructTermsD* td, int S, float* z, float* grad, double* F_part, int F_blocks,
                         double* F_out, int num_sms, cudaStream_t stream, int* launches) {
     (void)tf;
     const int grid = dose_grid(D.n_rows, num_sms);
     if (F_part != nullptr && F_blocks < grid) return cudaErrorInvalidValue;
-    const double mean = D.n_rows > 0 ? (double)D.nnz_stored / (double)D.n_rows : 0.0;
+    const int g = dose_lanes(D);
     cudaError_t e;
-    if (D.prec != DAO_PREC_FP32) {
-        const bool bf = D.prec == DAO_PREC_BF16;
-        if (mean <= 48.0)
-            e = bf ? dose16_g<4, true>(D, x, vstruct, td, S, z, grad, F_part, grid, stream)
-                   : dose16_g<4, false>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
-        else if (mean <= 128.0)
-            e = bf ? dose16_g<8, true>(D, x, vstruct, td, S, z, grad, F_part, grid, stream)
-                   : dose16_g<8, false>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
-        else
-            e = bf ? dose16_g<16, true>(D, x, vstruct, td, S, z, grad, F_part, grid, stream)
-                   : dose16_g<16, false>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
-    } else if (mean <= 24.0)
+    if (D.prec == DAO_PREC_BF16)
+        e = dose16_any<true>(g, D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+    else if (D.prec == DAO_PREC_FP16)
+        e = dose16_any<false>(g, D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+    else if (g == 4)
         e = dose_g<4>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
-    else if (mean <= 64.0)
+    else if (g == 8)
         e = dose_g<8>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
-    else if (mean <= 160.0)
+    else if (g == 16)
         e = dose_g<16>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
     else
         e = dose_g<32>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
@@ -459,17 +526,11 @@ cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct,
 cudaError_t launch_dt(const DevCSR& Dt, const float* pi, float* w, const int* skip, cudaStream_t stream,
                       int* launches) {
     if (Dt.n_rows == 0) return cudaSuccess;
-    if (Dt.prec == DAO_PREC_FP16)
-        k_dt16<128, false><<<Dt.n_rows, 128, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
-                                                          reinterpret_cast<const uint4*>(Dt.val16), Dt.scale,
-                                                          Dt.n_rows, pi, w, skip);
-    else if (Dt.prec == DAO_PREC_BF16)
-        k_dt16<128, true><<<Dt.n_rows, 128, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
-                                                         reinterpret_cast<const uint4*>(Dt.val16), Dt.scale,
-                                                         Dt.n_rows, pi, w, skip);
-    else
-        k_dt<128><<<Dt.n_rows, 128, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
-                                                  reinterpret_cast<const float4*>(Dt.val), Dt.n_rows, pi, w, skip);
+    switch (Dt.tune_dt_threads) {
+        case 64: dt_launch<64>(Dt, pi, w, skip, stream); break;
+        case 256: dt_launch<256>(Dt, pi, w, skip, stream); break;
+        default: dt_launch<128>(Dt, pi, w, skip, stream); break;
+    }
     ++*launches;
     return cudaGetLastError();
 }
@@ -478,15 +539,11 @@ cudaError_t launch_column(const DevCSR& D, const int* seg_lo, const int* seg_hi,
                           const float* mask, float* out, int stride, int num_sms, cudaStream_t stream, int* launches) {
     if (D.n_rows == 0) return cudaSuccess;
     const int grid = num_sms * 8;
-    const size_t sm = (size_t)nb * sizeof(float);
-    if (D.prec == DAO_PREC_FP16)
-        k_column16<8, false><<<grid, 256, sm, stream>>>(D.col16, D.val16, seg_lo, seg_hi, D.n_rows, base, nb, mask,
-                                                         D.scale, out, stride);
-    else if (D.prec == DAO_PREC_BF16)
-        k_column16<8, true><<<grid, 256, sm, stream>>>(D.col16, D.val16, seg_lo, seg_hi, D.n_rows, base, nb, mask,
-                                                        D.scale, out, stride);
-    else
-        k_column<8><<<grid, 256, sm, stream>>>(D.col, D.val, seg_lo, seg_hi, D.n_rows, base, nb, mask, out, stride);
+    switch (D.tune_col_g) {
+        case 4: column_launch<4>(D, seg_lo, seg_hi, base, nb, mask, out, stride, grid, stream); break;
+        case 16: column_launch<16>(D, seg_lo, seg_hi, base, nb, mask, out, stride, grid, stream); break;
+        default: column_launch<8>(D, seg_lo, seg_hi, base, nb, mask, out, stride, grid, stream); break;
+    }
     ++*launches;
     return cudaGetLastError();
 }
@@ -495,18 +552,19 @@ cudaError_t launch_column_dev(const DevCSR& D, const int* seg, const int* ap_bea
                               const int* rows, const int* cols, int max_nb, const float* mask, float* out, int stride,
                               const CGDev* cg, int num_sms, cudaStream_t stream, int* launches) {
     if (D.n_rows == 0) return cudaSuccess;
-    const size_t sm = (size_t)max_nb * sizeof(float);
-    if (D.prec == DAO_PREC_FP16)
-        k_column16_dev<8, false><<<num_sms * 8, 256, sm, stream>>>(D.col16, D.val16, seg, D.n_rows, ap_beam, K,
-                                                                    beam_off, rows, cols, mask, D.scale, out, stride,
-                                                                    cg);
-    else if (D.prec == DAO_PREC_BF16)
-        k_column16_dev<8, true><<<num_sms * 8, 256, sm, stream>>>(D.col16, D.val16, seg, D.n_rows, ap_beam, K,
-                                                                   beam_off, rows, cols, mask, D.scale, out, stride,
-                                                                   cg);
-    else
-        k_column_dev<8><<<num_sms * 8, 256, sm, stream>>>(D.col, D.val, seg, D.n_rows, ap_beam, K, beam_off, rows,
-                                                           cols, mask, out, stride, cg);
+    const int grid = num_sms * 8;
+    switch (D.tune_col_g) {
+        case 4:
+            column_dev_launch<4>(D, seg, ap_beam, K, beam_off, rows, cols, max_nb, mask, out, stride, cg, grid, stream);
+            break;
+        case 16:
+            column_dev_launch<16>(D, seg, ap_beam, K, beam_off, rows, cols, max_nb, mask, out, stride, cg, grid,
+                                  stream);
+            break;
+        default:
+            column_dev_launch<8>(D, seg, ap_beam, K, beam_off, rows, cols, max_nb, mask, out, stride, cg, grid, stream);
+            break;
+    }
     ++*launches;
     return cudaGetLastError();
 }

@@ -119,3 +119,15 @@ def test_null_arguments(lib):
     assert lib.dao_price(None, None, None, None) == -1
     assert lib.dao_solve(None, 5, None, None) == -1
     assert lib.dao_launch_count(None) == 0
+
+
+def test_batch_and_autotune_validate_on_host(lib):
+    """Null and malformed batch arguments are refused before any CUDA call."""
+    from paper_1003_5402_gb300 import binding
+    assert lib.dao_batch_solve(None, 1, 5, None, None, None) == binding.DAO_EINVAL
+    assert lib.dao_batch_solve(None, -1, 5, None, None, None) == binding.DAO_EINVAL
+    arr = (C.c_void_p * 2)(None, None)
+    assert lib.dao_batch_solve(C.cast(arr, C.POINTER(C.c_void_p)), 2, 5, None, None, None) == binding.DAO_EINVAL
+    assert b"null context" in lib.dao_last_error()
+    assert lib.dao_batch_solve(None, 0, 5, None, None, None) == binding.DAO_OK
+    assert lib.dao_autotune(None, None, None) == binding.DAO_EINVAL
