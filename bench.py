@@ -45,6 +45,9 @@ def _args():
     p.add_argument("--skip-spmv", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--skip-batch", action="store_true")
+    p.add_argument("--skip-serve", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=60,
+                   help="requests of the serving leg (600 for the full Poisson workload)")
     p.add_argument("--batch", type=int, default=16, help="instances per workload in the batched re-plan leg")
     return p.parse_args()
 
@@ -276,6 +279,53 @@ def run_batch(torch, dev, flush, cases, n_each, apertures):
             p.close()
 
 
+def serve_pool(n_each):
+    """Distinct re-plan instances the serving leg draws its requests from: n_each
+    perturbed small (19,200-voxel) and n_each perturbed prostate-shaped phantoms
+    (seeds 9000 + i), generated in a spawn process pool."""
+    import multiprocessing as mp
+    specs = [phantom.perturb(phantom.spec_tiny(), 9000 + i) for i in range(n_each)]
+    specs += [phantom.perturb(phantom.spec_prostate(), 9000 + n_each + i) for i in range(n_each)]
+    workers = max(1, min(len(specs), os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_make_case_spec, specs)
+
+
+def run_serve(dev, pool, n_requests, apertures, rate_per_s=4.0, seed=9000):
+    """Poisson arrivals (rate 4 per second, seeded exponential gaps) of re-plan
+    requests drawn from the pool; each request uploads its D and plans
+    ``apertures`` apertures.  Latency is submission to results on the host."""
+    from paper_1003_5402_gb300 import Server
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate_per_s, size=n_requests)
+    which = rng.integers(0, len(pool), size=n_requests)
+    with Server(max_slots=8, device=dev) as srv:
+        warm = srv.submit(pool[0], apertures)                  # the first context on a fresh process
+        srv.wait(warm)
+        t0 = time.perf_counter()
+        t_next = t0
+        ids = []
+        for g, w in zip(gaps, which):
+            t_next += g
+            d = t_next - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            ids.append(srv.submit(pool[int(w)], apertures))
+        res = [srv.wait(i) for i in ids]
+        makespan = time.perf_counter() - t0
+        st = srv.stats()
+    lat = np.array([r["latency_ms"] for r in res])
+    qms = np.array([r["queue_ms"] for r in res])
+    ok = sum(r["status"] in (0, 1, 2) for r in res)
+    return {"requests": n_requests, "rate_per_s": rate_per_s, "completed_ok": int(ok),
+            "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "queue_p99_ms": round(float(np.percentile(qms, 99)), 3), "max_active": st["max_active"],
+            "plans_per_s": round(ok / makespan, 3), "makespan_s": round(makespan, 3),
+            "workload": f"{len(pool) // 2} perturbed 19,200-voxel + {len(pool) // 2} perturbed prostate-shaped "
+                        f"instances, {apertures} apertures, D uploaded per request",
+            "latency": "submission to results in host memory (dao_create + column generation + dose D2H)"}
+
+
 def spmv_bandwidth(torch, plan, case, prec, flush, hbm_peak):
     """Cold-L2 a1 and a2 alone: median of 20 runs, each timed with CUDA events."""
     out = {}
@@ -317,6 +367,7 @@ def run_ours(a):
     build.build()
     case = _case(a.config)
     batch_cases = batch_instances(a.batch) if (not a.skip_batch and rank == 0) else None
+    serve_cases = serve_pool(8) if (not a.skip_serve and rank == 0) else None
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -447,6 +498,9 @@ def run_ours(a):
     batch = None
     if batch_cases is not None:
         batch = run_batch(torch, dev, flush, batch_cases, a.batch, a.apertures)
+    serve = None
+    if serve_cases is not None:
+        serve = run_serve(dev, serve_cases, a.serve_requests, a.apertures)
 
     cpu = None
     if rank == 0 and ws == 1 and not a.skip_cpu:
@@ -466,7 +520,7 @@ def run_ours(a):
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
             "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
                            "p99": round(float(np.percentile(lat, 99)), 4)},
-            "spmv": spmv, "mixed_precision": mixed, "batch": batch, "kernel_ms_host_driven_plan": kernel_ms, "kernel_launches_host_driven_plan": kernel_launches,
+            "spmv": spmv, "mixed_precision": mixed, "batch": batch, "serve": serve, "kernel_ms_host_driven_plan": kernel_ms, "kernel_launches_host_driven_plan": kernel_launches,
             "objective_final": F_final, "apertures_done": int(n), "master_evals": int(np.sum(ev)),
             "host_wall_s": round(t_host, 3), "device": torch.cuda.get_device_name(dev),
         }

@@ -266,6 +266,85 @@ typedef struct {
 } dao_tuning;
 dao_status dao_autotune(dao_ctx* ctx, const char* cache_path, dao_tuning* out);
 
+/* ---- re-plan serving (continuous batching) ----
+ * A server plans requests as they arrive (the paper's motivation: re-planning
+ * fast enough to adapt a treatment to the day's anatomy, Sec. 1 and Sec. 4).
+ * One host worker thread admits queued requests in arrival order while a slot
+ * is free and the request's device footprint fits (free device memory minus
+ * hbm_reserve_bytes, or the hbm_budget_bytes budget minus the footprints of the
+ * running plans); an admitted request gets its own context and stream, all its
+ * column-generation rounds are queued as CUDA graphs at once, and it runs
+ * alongside the plans already on the GPU; the worker retires each plan as soon
+ * as its last round completes, copies the results into the request's output
+ * buffers and admits the next request, without waiting for the other plans.
+ * A request that can never fit is rejected (DAO_ENOMEM) instead of blocking the
+ * queue; an invalid one fails with dao_create's status.
+ * Simulation (simulate_ms_per_aperture > 0): a host-only stand-in for the GPU
+ * used to test the scheduler; no CUDA call is made, no plan is computed, a
+ * request "runs" for simulate_ms_per_aperture * n_apertures milliseconds and
+ * reports status DAO_OK, n_apertures apertures and a NaN objective; free
+ * memory is hbm_budget_bytes, which must then be > 0. */
+typedef struct dao_server dao_server;
+typedef struct {
+    int32_t max_slots;             /* plans on the GPU at once (>= 1) */
+    int32_t queue_capacity;        /* queued requests beyond which submit returns DAO_EBUSY (>= 1) */
+    int64_t hbm_reserve_bytes;     /* device memory left free when admitting */
+    int64_t hbm_budget_bytes;      /* 0: admit by free device memory; > 0: admit while the
+                                      footprints of the running plans stay within it */
+    int32_t device;
+    double simulate_ms_per_aperture;
+    dao_options plan_options;      /* options of every plan; stream and device are ignored */
+} dao_server_options;
+void dao_server_options_default(dao_server_options* opt);
+
+/* One request: dao_create's arguments, the apertures to add, and caller-owned
+ * output buffers (each may be NULL).  Every array, input or output, must stay
+ * valid until dao_server_poll or dao_server_wait has reported the request. */
+typedef struct {
+    dao_csr D;
+    dao_geometry geometry;
+    dao_structures structures;
+    dao_weights weights;
+    const double* prescriptions;
+    int32_t n_apertures;
+    float* dose_out;               /* [n_voxels] planned dose */
+    double* intensities_out;       /* [plan_options.k_max] y */
+    int32_t* beams_out;            /* [plan_options.k_max] aperture beams */
+    int32_t* leaves_out;           /* [plan_options.k_max][2 * max rows] half-open [L, R) per row */
+} dao_request;
+
+typedef struct {
+    int32_t status;        /* dao_solve's status, or the error that stopped the request */
+    int32_t n_apertures;   /* apertures in the plan */
+    double objective;      /* F of the final plan (Eqs. 9-10) */
+    double queue_ms;       /* submission to admission */
+    double run_ms;         /* admission to results in the output buffers */
+    double latency_ms;     /* submission to results */
+    char error[256];       /* message of a failed request */
+} dao_result;
+
+typedef struct {
+    int64_t submitted, completed, failed, rejected;
+    int32_t active, queued, max_active;
+    int64_t bytes_in_use;  /* footprints of the running plans */
+} dao_server_stats;
+
+dao_status dao_server_create(const dao_server_options* opt, dao_server** out);
+/* Queues a request (DAO_EBUSY when the queue is full, DAO_ESTATE after
+ * shutdown); *id identifies it. */
+dao_status dao_server_submit(dao_server* srv, const dao_request* req, int64_t* id);
+/* DAO_OK and *out once the request has finished (each id is reported once),
+ * DAO_EBUSY while it is queued or running, DAO_EINVAL for an unknown id. */
+dao_status dao_server_poll(dao_server* srv, int64_t id, dao_result* out);
+/* As poll, blocking up to timeout_ms (< 0: no limit); DAO_ETIMEOUT if it ran out. */
+dao_status dao_server_wait(dao_server* srv, int64_t id, double timeout_ms, dao_result* out);
+dao_status dao_server_stats_get(dao_server* srv, dao_server_stats* out);
+/* Device bytes a request's plan holds: the admission footprint. */
+int64_t dao_server_footprint(const dao_request* req, const dao_options* plan_options);
+/* Cancels queued requests (status DAO_ESTATE), waits for the running plans,
+ * stops the worker and frees the server. */
+void dao_server_destroy(dao_server* srv);
+
 /* ---- allocation-free dose with objective (the paper has no counterpart) ----
  * For callers that must not allocate device memory while they run, e.g. a
  * re-planning service that reserves every device buffer before an online

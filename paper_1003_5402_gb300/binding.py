@@ -56,6 +56,30 @@ class dao_tuning(C.Structure):
                 ("from_cache", C.c_int32)]
 
 
+class dao_server_options(C.Structure):
+    _fields_ = [("max_slots", C.c_int32), ("queue_capacity", C.c_int32), ("hbm_reserve_bytes", C.c_int64),
+                ("hbm_budget_bytes", C.c_int64), ("device", C.c_int32), ("simulate_ms_per_aperture", C.c_double),
+                ("plan_options", dao_options)]
+
+
+class dao_request(C.Structure):
+    _fields_ = [("D", dao_csr), ("geometry", dao_geometry), ("structures", dao_structures), ("weights", dao_weights),
+                ("prescriptions", _F64P), ("n_apertures", C.c_int32), ("dose_out", C.POINTER(C.c_float)),
+                ("intensities_out", _F64P), ("beams_out", _I32P), ("leaves_out", _I32P)]
+
+
+class dao_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_apertures", C.c_int32), ("objective", C.c_double),
+                ("queue_ms", C.c_double), ("run_ms", C.c_double), ("latency_ms", C.c_double),
+                ("error", C.c_char * 256)]
+
+
+class dao_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("rejected", C.c_int64),
+                ("active", C.c_int32), ("queued", C.c_int32), ("max_active", C.c_int32),
+                ("bytes_in_use", C.c_int64)]
+
+
 SIGNATURES = {
     "dao_options_default": (None, [C.POINTER(dao_options)]),
     "dao_create": (C.c_int, [C.POINTER(dao_csr), C.POINTER(dao_geometry), C.POINTER(dao_structures),
@@ -83,6 +107,14 @@ SIGNATURES = {
                                              _P, _P]),
     "dao_batch_solve": (C.c_int, [C.POINTER(_P), C.c_int32, C.c_int32, _I32P, _F64P, _I32P]),
     "dao_autotune": (C.c_int, [_P, C.c_char_p, C.POINTER(dao_tuning)]),
+    "dao_server_options_default": (None, [C.POINTER(dao_server_options)]),
+    "dao_server_create": (C.c_int, [C.POINTER(dao_server_options), C.POINTER(_P)]),
+    "dao_server_submit": (C.c_int, [_P, C.POINTER(dao_request), C.POINTER(C.c_int64)]),
+    "dao_server_poll": (C.c_int, [_P, C.c_int64, C.POINTER(dao_result)]),
+    "dao_server_wait": (C.c_int, [_P, C.c_int64, C.c_double, C.POINTER(dao_result)]),
+    "dao_server_stats_get": (C.c_int, [_P, C.POINTER(dao_server_stats)]),
+    "dao_server_footprint": (C.c_int64, [C.POINTER(dao_request), C.POINTER(dao_options)]),
+    "dao_server_destroy": (None, [_P]),
     "dao_last_error": (C.c_char_p, []),
 }
 
@@ -140,6 +172,29 @@ def options(**kw) -> dao_options:
     return o
 
 
+def _case_structs(case, normalize_by_volume: bool = True):
+    """dao_create's argument structs for a case, and the arrays they point into
+    (which must outlive the call)."""
+    indptr = np.ascontiguousarray(case.indptr, dtype=np.int64)
+    indices = np.ascontiguousarray(case.indices, dtype=np.int32)
+    data = np.ascontiguousarray(case.data, dtype=np.float32)
+    rows = np.ascontiguousarray(case.rows, dtype=np.int32)
+    cols = np.ascontiguousarray(case.cols, dtype=np.int32)
+    vs = np.ascontiguousarray(case.voxel_struct, dtype=np.int32)
+    tgt = np.ascontiguousarray(case.is_target, dtype=np.uint8)
+    uw = np.ascontiguousarray(case.under_w, dtype=np.float64)
+    ow = np.ascontiguousarray(case.over_w, dtype=np.float64)
+    ot = np.ascontiguousarray(case.over_t, dtype=np.float64)
+    rx = np.ascontiguousarray(case.under_t, dtype=np.float64)
+    keep = [indptr, indices, data, rows, cols, vs, tgt, uw, ow, ot, rx]
+    D = dao_csr(len(indptr) - 1, int(np.sum(rows.astype(np.int64) * cols)), int(indptr[-1]),
+                _ptr(indptr, C.c_int64), _ptr(indices, C.c_int32), _ptr(data, C.c_float))
+    g = dao_geometry(len(rows), _ptr(rows, C.c_int32), _ptr(cols, C.c_int32))
+    s = dao_structures(len(uw), _ptr(vs, C.c_int32), _ptr(tgt, C.c_uint8))
+    w = dao_weights(_ptr(uw, C.c_double), _ptr(ow, C.c_double), _ptr(ot, C.c_double), int(normalize_by_volume))
+    return D, g, s, w, rx, keep
+
+
 class Plan:
     """One DAO plan context (dao_create ... dao_destroy).
 
@@ -151,32 +206,15 @@ class Plan:
 
     def __init__(self, case, normalize_by_volume: bool = True, **opt):
         lib = load()
-        self._keep = []
-        indptr = np.ascontiguousarray(case.indptr, dtype=np.int64)
-        indices = np.ascontiguousarray(case.indices, dtype=np.int32)
-        data = np.ascontiguousarray(case.data, dtype=np.float32)
-        rows = np.ascontiguousarray(case.rows, dtype=np.int32)
-        cols = np.ascontiguousarray(case.cols, dtype=np.int32)
-        vs = np.ascontiguousarray(case.voxel_struct, dtype=np.int32)
-        tgt = np.ascontiguousarray(case.is_target, dtype=np.uint8)
-        uw = np.ascontiguousarray(case.under_w, dtype=np.float64)
-        ow = np.ascontiguousarray(case.over_w, dtype=np.float64)
-        ot = np.ascontiguousarray(case.over_t, dtype=np.float64)
-        rx = np.ascontiguousarray(case.under_t, dtype=np.float64)
-        self._keep += [indptr, indices, data, rows, cols, vs, tgt, uw, ow, ot, rx]
-        D = dao_csr(len(indptr) - 1, int(np.sum(rows.astype(np.int64) * cols)), int(indptr[-1]),
-                    _ptr(indptr, C.c_int64), _ptr(indices, C.c_int32), _ptr(data, C.c_float))
-        g = dao_geometry(len(rows), _ptr(rows, C.c_int32), _ptr(cols, C.c_int32))
-        s = dao_structures(len(uw), _ptr(vs, C.c_int32), _ptr(tgt, C.c_uint8))
-        w = dao_weights(_ptr(uw, C.c_double), _ptr(ow, C.c_double), _ptr(ot, C.c_double), int(normalize_by_volume))
+        D, g, s, w, rx, self._keep = _case_structs(case, normalize_by_volume)
         o = options(**opt)
         h = C.c_void_p()
         _check(lib.dao_create(C.byref(D), C.byref(g), C.byref(s), C.byref(w), _ptr(rx, C.c_double), C.byref(o),
                               C.byref(h)), "dao_create")
         self.h = h
         self._keep = []
-        self.rows = rows.copy()
-        self.cols = cols.copy()
+        self.rows = np.array(case.rows, dtype=np.int32)
+        self.cols = np.array(case.cols, dtype=np.int32)
         sz = self.sizes()
         self.n_voxels, self.n_beamlets, self.n_beams, self.n_mlc_rows, self.max_rows, self.nnz_stored, self.k_max = sz
 
@@ -352,3 +390,99 @@ def batch_solve(plans: Sequence["Plan"], n_apertures: int):
     _check(load().dao_batch_solve(C.cast(arr, C.POINTER(C.c_void_p)), n, int(n_apertures), _ptr(n_done, C.c_int32),
                                   _ptr(traces, C.c_double), _ptr(status, C.c_int32)), "dao_batch_solve")
     return [(int(status[i]), int(n_done[i]), traces[i, :n_apertures].copy()) for i in range(n)]
+
+
+class Server:
+    """A re-plan server (dao_server_*): requests are queued, admitted while a slot
+    is free and their device footprint fits, planned concurrently on their own
+    streams and returned as they finish.  Keyword options beyond the server's own
+    map to the dao_options of every plan."""
+
+    def __init__(self, max_slots: int = 8, queue_capacity: int = 1024, hbm_reserve_bytes: int = 2 << 30,
+                 hbm_budget_bytes: int = 0, device: int = 0, simulate_ms_per_aperture: float = 0.0, **plan_opt):
+        lib = load()
+        o = dao_server_options()
+        lib.dao_server_options_default(C.byref(o))
+        o.max_slots, o.queue_capacity = int(max_slots), int(queue_capacity)
+        o.hbm_reserve_bytes, o.hbm_budget_bytes = int(hbm_reserve_bytes), int(hbm_budget_bytes)
+        o.device, o.simulate_ms_per_aperture = int(device), float(simulate_ms_per_aperture)
+        o.plan_options = options(**plan_opt)
+        self.k_max = o.plan_options.k_max
+        h = C.c_void_p()
+        _check(lib.dao_server_create(C.byref(o), C.byref(h)), "dao_server_create")
+        self.h = h
+        self._live = {}
+
+    def _request(self, case, n_apertures: int, outputs: bool = True):
+        D, g, s, w, rx, keep = _case_structs(case)
+        out = {}
+        req = dao_request(D, g, s, w, _ptr(rx, C.c_double), int(n_apertures))
+        if outputs:
+            max_rows = int(np.max(np.asarray(case.rows)))
+            out = {"dose": np.zeros(len(case.indptr) - 1, np.float32), "y": np.zeros(self.k_max),
+                   "beams": np.zeros(self.k_max, np.int32),
+                   "leaves": np.zeros((self.k_max, max_rows, 2), np.int32)}
+            req.dose_out = _ptr(out["dose"], C.c_float)
+            req.intensities_out = _ptr(out["y"], C.c_double)
+            req.beams_out = _ptr(out["beams"], C.c_int32)
+            req.leaves_out = _ptr(out["leaves"], C.c_int32)
+        return req, keep, out
+
+    def footprint(self, case, **plan_opt) -> int:
+        req, keep, _ = self._request(case, 0, outputs=False)
+        o = options(**plan_opt)
+        return int(load().dao_server_footprint(C.byref(req), C.byref(o)))
+
+    def submit(self, case, n_apertures: int, outputs: bool = True) -> int:
+        """Queue a request; returns its id.  Raises DaoError(DAO_EBUSY) when the queue is full."""
+        req, keep, out = self._request(case, n_apertures, outputs)
+        rid = C.c_int64()
+        _check(load().dao_server_submit(self.h, C.byref(req), C.byref(rid)), "dao_server_submit")
+        self._live[rid.value] = (req, keep, out)
+        return rid.value
+
+    def _result(self, rid, r):
+        req, keep, out = self._live.pop(rid)
+        res = {"status": r.status, "n_apertures": r.n_apertures, "objective": r.objective, "queue_ms": r.queue_ms,
+               "run_ms": r.run_ms, "latency_ms": r.latency_ms, "error": r.error.decode(errors="replace")}
+        if out:
+            k = max(r.n_apertures, 0)
+            res.update(dose=out["dose"], y=out["y"][:k].copy(), beams=out["beams"][:k].copy(),
+                       leaves=out["leaves"][:k].copy())
+        return res
+
+    def poll(self, rid: int):
+        """The finished request's result (a dict), or None while it is queued or running."""
+        r = dao_result()
+        st = load().dao_server_poll(self.h, int(rid), C.byref(r))
+        if st == DAO_EBUSY:
+            return None
+        _check(st, "dao_server_poll")
+        return self._result(rid, r)
+
+    def wait(self, rid: int, timeout_ms: float = -1.0):
+        r = dao_result()
+        _check(load().dao_server_wait(self.h, int(rid), float(timeout_ms), C.byref(r)), "dao_server_wait")
+        return self._result(rid, r)
+
+    def stats(self) -> dict:
+        t = dao_server_stats()
+        _check(load().dao_server_stats_get(self.h, C.byref(t)), "dao_server_stats_get")
+        return {f: getattr(t, f) for f, _ in dao_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().dao_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -78,6 +78,7 @@ struct dao_ctx {
 
     // column-generation state
     int K = 0, K_cap = 0, ld = 0;
+    int async_K0 = 0, async_K1 = 0;  // rounds launched by solve_async_begin
     float* slab = nullptr;           // K_cap x ld, column k = dose of aperture k (Eq. 2)
     std::vector<int> ap_beam_h, ap_lr_h;
     int* ap_beam = nullptr;
@@ -809,6 +810,41 @@ dao_status reset_state(dao_ctx* c) {
 }
 
 }  // namespace
+
+// ============================ internal hooks (serve.cu) ===========================
+namespace dao {
+
+dao_status check_inputs(const dao_csr* D, const dao_geometry* g, const dao_structures* s, const dao_weights* w,
+                        const double* rx, const dao_options* opt) {
+    dao_options o;
+    dao_options_default(&o);
+    if (opt) o = *opt;
+    return validate(D, g, s, w, rx, &o);
+}
+
+dao_status solve_async_begin(dao_ctx* c, int n_apertures, cudaEvent_t done) {
+    DAO_TRY(check_ctx(c));
+    if (!c->opt.use_graphs || c->prof_on) return fail(DAO_EINVAL, "asynchronous solve needs use_graphs, profiling off");
+    GraphSolve gs;
+    DAO_TRY(solve_graph_begin(c, n_apertures, &gs));
+    for (int k = gs.K0 + 1; k <= gs.K1; ++k) DAO_CU(cudaGraphLaunch(c->round_exec[k], c->stream));
+    DAO_CU(cudaEventRecord(done, c->stream));
+    c->async_K0 = gs.K0;
+    c->async_K1 = gs.K1;
+    return DAO_OK;
+}
+
+dao_status solve_async_end(dao_ctx* c, int n_apertures, int32_t* n_done, dao_status* result) {
+    DAO_TRY(check_ctx(c));
+    GraphSolve gs;
+    gs.K0 = c->async_K0;
+    gs.K1 = c->async_K1;
+    DAO_TRY(solve_graph_end(c, gs, n_apertures, n_done, nullptr, result));
+    c->count_launches();
+    return DAO_OK;
+}
+
+}  // namespace dao
 
 // ================================ C ABI ==========================================
 

@@ -15,6 +15,15 @@ namespace dao {
 // Record the calling thread's error message for dao_last_error(); returns s.
 dao_status set_error(dao_status s, const std::string& msg);
 
+// Host-only validation of dao_create's arguments (no CUDA call).
+dao_status check_inputs(const dao_csr* D, const dao_geometry* g, const dao_structures* s, const dao_weights* w,
+                        const double* rx, const dao_options* opt);
+// Graph path without waiting: launch up to n_apertures rounds on the context's
+// stream and record `done` after them; solve_async_end reads the outcome back
+// once `done` has completed.
+dao_status solve_async_begin(dao_ctx* c, int n_apertures, cudaEvent_t done);
+dao_status solve_async_end(dao_ctx* c, int n_apertures, int32_t* n_done, dao_status* result);
+
 constexpr int KMAX = 64;        // aperture pool capacity (master problem size)
 constexpr int SMAX = 64;        // structures
 constexpr int CMAX = 32;        // beamlets per MLC row (one warp lane each)

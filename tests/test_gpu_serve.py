@@ -1,0 +1,78 @@
+"""The re-plan server on the GPU: every result equals the same plan computed
+alone with dao_solve (bitwise: objective, dose, intensities, apertures), plans
+run concurrently, the admission footprint bounds the device memory a plan
+really holds, and a memory budget that fits any one plan but no two admits one
+plan at a time."""
+import numpy as np
+import pytest
+
+import phantom as P
+from _helpers import need_cuda, random_case
+
+pytestmark = [pytest.mark.gpu, pytest.mark.timeout(600)]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = need_cuda()
+    from paper_1003_5402_gb300 import build
+    build.build()
+    return t
+
+
+def _cases():
+    micro = P.spec_micro()
+    return [P.make_case(micro), P.make_case(P.perturb(micro, 9001)), P.make_case(P.spec_tiny()),
+            random_case(31, 3001, rows=[3, 5, 2], cols=[7, 5, 13], mean_row=9.0),
+            P.make_case(P.perturb(micro, 9002))]
+
+
+def test_server_results_equal_plans_alone(torch):
+    from paper_1003_5402_gb300 import Plan, Server
+    cases = _cases()
+    K = 10
+    alone = []
+    for c in cases:
+        with Plan(c) as p:
+            st, n, trace = p.solve(K)
+            z, F = p.dose()
+            aps = p.apertures()
+            alone.append((st, n, F, z, p.intensities(), aps))
+    with Server(max_slots=3) as s:
+        ids = [s.submit(c, K) for c in cases]
+        res = [s.wait(i, 120_000) for i in ids]
+        stats = s.stats()
+    for r, (st, n, F, z, y, aps) in zip(res, alone):
+        assert r["status"] == st and r["n_apertures"] == n and r["error"] == ""
+        assert r["objective"] == F and np.array_equal(r["dose"], z) and np.array_equal(r["y"], y)
+        for k, (b, lv) in enumerate(aps):
+            assert r["beams"][k] == b and np.array_equal(r["leaves"][k][: len(lv)], lv)
+    assert stats["completed"] == len(cases) and stats["failed"] == 0 and stats["max_active"] >= 2
+
+
+def test_footprint_bounds_the_device_memory_of_a_plan(torch):
+    from paper_1003_5402_gb300 import Plan, Server
+    case = P.make_case(P.spec_prostate())
+    with Server(max_slots=1) as s:
+        fp = s.footprint(case)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    with Plan(case) as p:
+        p.solve(2)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+    used = free0 - free1
+    assert used > 0 and fp >= used and fp <= 2 * used + (64 << 20), (fp, used)
+
+
+def test_budget_of_one_footprint_runs_plans_one_at_a_time(torch):
+    from paper_1003_5402_gb300 import Server
+    cases = _cases()[:3]
+    with Server(max_slots=3) as probe:
+        fps = sorted(probe.footprint(c) for c in cases)
+    budget = fps[-1]                              # every plan fits alone, no two together
+    assert fps[0] + fps[1] > budget
+    with Server(max_slots=3, hbm_budget_bytes=budget) as s:
+        ids = [s.submit(c, 6) for c in cases]
+        assert all(s.wait(i, 120_000)["status"] in (0, 1, 2) for i in ids)
+        assert s.stats()["max_active"] == 1
