@@ -2,12 +2,15 @@
 // column-generation driver (Sec. 2.2-2.3 of arXiv:1003.5402, Fig. 1) and the
 // C ABI declared in include/dao.h.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstddef>
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -189,17 +192,45 @@ dao_status validate(const dao_csr* D, const dao_geometry* g, const dao_structure
     if (!D->row_ptr || !D->col || !D->val) return fail(DAO_EINVAL, "null CSR array");
     if (D->row_ptr[0] != 0 || D->row_ptr[D->n_voxels] != D->nnz || D->nnz < 0)
         return fail(DAO_EINVAL, "row_ptr[0] must be 0 and row_ptr[n_voxels] must equal nnz");
-    for (int j = 0; j < D->n_voxels; ++j) {
-        const int64_t p0 = D->row_ptr[j], p1 = D->row_ptr[j + 1];
-        if (p1 < p0) return fail(DAO_EINVAL, "row_ptr decreases at row " + std::to_string(j));
-        for (int64_t p = p0; p < p1; ++p) {
-            const int32_t c = D->col[p];
-            if (c < 0 || c >= D->n_beamlets)
-                return fail(DAO_EINVAL, "column index out of range at entry " + std::to_string(p));
-            if (p > p0 && c <= D->col[p - 1])
-                return fail(DAO_EINVAL, "columns not strictly increasing in row " + std::to_string(j));
-            if (!std::isfinite(D->val[p])) return fail(DAO_EINVAL, "non-finite value at entry " + std::to_string(p));
-        }
+    {
+        // rows checked by up to 16 host threads; the first bad row in row order is reported
+        const int V = D->n_voxels;
+        auto check_rows = [D](int j0, int j1, std::string* msg) -> int {
+            for (int j = j0; j < j1; ++j) {
+                const int64_t p0 = D->row_ptr[j], p1 = D->row_ptr[j + 1];
+                if (p1 < p0 || p0 < 0 || p1 > D->nnz) {
+                    *msg = "row_ptr decreases or leaves [0, nnz] at row " + std::to_string(j);
+                    return j;
+                }
+                for (int64_t p = p0; p < p1; ++p) {
+                    const int32_t c = D->col[p];
+                    if (c < 0 || c >= D->n_beamlets) {
+                        *msg = "column index out of range at entry " + std::to_string(p);
+                        return j;
+                    }
+                    if (p > p0 && c <= D->col[p - 1]) {
+                        *msg = "columns not strictly increasing in row " + std::to_string(j);
+                        return j;
+                    }
+                    if (!std::isfinite(D->val[p])) {
+                        *msg = "non-finite value at entry " + std::to_string(p);
+                        return j;
+                    }
+                }
+            }
+            return -1;
+        };
+        const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        const int T = D->nnz < (1 << 20) ? 1 : (int)std::min<int64_t>(hw, V);
+        std::vector<int> bad(T, -1);
+        std::vector<std::string> msg(T);
+        std::vector<std::thread> th;
+        for (int t = 1; t < T; ++t)
+            th.emplace_back([&, t] { bad[t] = check_rows((int)((int64_t)V * t / T), (int)((int64_t)V * (t + 1) / T), &msg[t]); });
+        bad[0] = check_rows(0, (int)((int64_t)V / T), &msg[0]);
+        for (std::thread& x : th) x.join();
+        for (int t = 0; t < T; ++t)
+            if (bad[t] >= 0) return fail(DAO_EINVAL, msg[t]);
     }
     if (g->n_beams < 1 || !g->rows || !g->cols) return fail(DAO_EINVAL, "geometry needs at least one beam");
     int64_t total = 0;
@@ -234,39 +265,13 @@ dao_status validate(const dao_csr* D, const dao_geometry* g, const dao_structure
 
 // ---- device data layout -------------------------------------------------------
 
-struct HostCSR {
-    std::vector<int> rowptr, col;
-    std::vector<float> val;
-};
-
-// Rows padded to a multiple of m entries (value 0, column = the row's last).
-void pad_rows(int n_rows, const std::vector<int64_t>& rp, const int32_t* col, const float* val, HostCSR& out,
-              int m) {
-    out.rowptr.assign(n_rows + 1, 0);
-    int64_t acc = 0;
-    for (int r = 0; r < n_rows; ++r) {
-        out.rowptr[r] = (int)acc;
-        acc += round_up(rp[r + 1] - rp[r], m);
-    }
-    out.rowptr[n_rows] = (int)acc;
-    out.col.assign(acc, 0);
-    out.val.assign(acc, 0.f);
-    for (int r = 0; r < n_rows; ++r) {
-        int64_t q = out.rowptr[r];
-        const int64_t p0 = rp[r], p1 = rp[r + 1];
-        for (int64_t p = p0; p < p1; ++p, ++q) {
-            out.col[q] = col[p];
-            out.val[q] = val[p];
-        }
-        const int last = p1 > p0 ? col[p1 - 1] : 0;
-        for (; q < out.rowptr[r + 1]; ++q) out.col[q] = last;
-    }
-}
-
 template <class T>
 dao_status upload(dao_ctx* c, T** dst, const T* src, size_t n) {
+    // ordered on the context's stream (a non-blocking stream does not wait for
+    // copies on the legacy default stream); build() synchronises before the
+    // host arrays go out of scope
     DAO_TRY(c->dalloc(dst, n));
-    if (n) DAO_CU(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    if (n) DAO_CU(cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, c->stream));
     return DAO_OK;
 }
 
@@ -291,50 +296,121 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
             for (int q = 0; q < c->cols[b]; ++q) bi[c->beam_off[b] + r * c->cols[b] + q] = make_int4(b, r, q, 0);
         }
 
-    // D (voxel-major) with per-row beam segments
-    // rows padded to 4 entries (one float4 / int4 load) or, with 16-bit values, to
-    // 8 entries (one 16-byte load of values and of 16-bit columns)
+    // D (voxel-major) with per-row beam segments, and D^T, built on the device
+    // from the caller's CSR (uploaded as is).  Rows are padded to 4 entries (one
+    // float4 / int4 load) or, with 16-bit values, to 8 entries (one 16-byte load
+    // of values and of 16-bit columns).
     const int prec = c->opt.precision;
     const int pad_m = prec == DAO_PREC_FP32 ? 4 : 8;
-    std::vector<int64_t> rp(Din->row_ptr, Din->row_ptr + V + 1);
+    const int64_t nnz = Din->nnz;
+    std::vector<int> prow(V + 1, 0);
     int64_t padded = 0;
-    for (int j = 0; j < V; ++j) padded += round_up(rp[j + 1] - rp[j], pad_m);
-    if (padded >= (int64_t)1 << 31) return fail(DAO_EINVAL, "D too large for 32-bit row offsets");
-    HostCSR Dh;
-    pad_rows(V, rp, Din->col, Din->val, Dh, pad_m);
-    std::vector<int> seg((size_t)(B + 1) * V);
     for (int j = 0; j < V; ++j) {
-        const int p_end = Dh.rowptr[j] + (int)(rp[j + 1] - rp[j]);
-        // segment starts: first entry with column >= beam_off[b]
-        int q = Dh.rowptr[j];
-        for (int b = 0; b < B; ++b) {
-            while (q < p_end && Dh.col[q] < c->beam_off[b]) ++q;
-            seg[(size_t)b * V + j] = q;
+        prow[j] = (int)std::min<int64_t>(padded, INT32_MAX);
+        padded += round_up(Din->row_ptr[j + 1] - Din->row_ptr[j], pad_m);
+    }
+    if (padded >= (int64_t)1 << 31) return fail(DAO_EINVAL, "D too large for 32-bit row offsets");
+    prow[V] = (int)padded;
+    // rows of D per chunk of the transpose: the chunk-by-beamlet counters stay under 16M
+    const int CH = (int)std::max<int64_t>(256, ((int64_t)V * N / (16 << 20) + 31) / 32 * 32);
+    const int n_ch = (V + CH - 1) / CH;
+    cudaStream_t st = c->stream;
+    // temporaries, stream-ordered
+    int64_t* t_rp = nullptr;
+    int* t_col = nullptr;
+    float* t_val = nullptr;
+    int* t_C = nullptr;
+    int* t_cnt = nullptr;
+    unsigned* t_dmax = nullptr;
+    float* t_tval = nullptr;
+    auto free_temps = [&]() {
+        for (void* q : {(void*)t_rp, (void*)t_col, (void*)t_val, (void*)t_C, (void*)t_cnt, (void*)t_dmax,
+                        (void*)(prec == DAO_PREC_FP32 ? nullptr : t_tval)})
+            if (q) cudaFreeAsync(q, st);
+    };
+    auto talloc = [&](auto** q, size_t bytes) -> dao_status {
+        void* v = nullptr;
+        const cudaError_t e = cudaMallocAsync(&v, std::max<size_t>(bytes, 4), st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            free_temps();
+            return fail(DAO_ENOMEM, "cudaMallocAsync of " + std::to_string(bytes) + " bytes failed");
         }
-        seg[(size_t)B * V + j] = p_end;
+        *q = static_cast<std::remove_pointer_t<decltype(q)>>(v);
+        return DAO_OK;
+    };
+    DAO_TRY(talloc(&t_rp, sizeof(int64_t) * (V + 1)));
+    DAO_TRY(talloc(&t_col, sizeof(int) * nnz));
+    DAO_TRY(talloc(&t_val, sizeof(float) * nnz));
+    DAO_TRY(talloc(&t_C, sizeof(int) * (size_t)n_ch * N));
+    DAO_TRY(talloc(&t_cnt, sizeof(int) * N));
+    DAO_TRY(talloc(&t_dmax, sizeof(unsigned)));
+    auto cu = [&](cudaError_t e, const char* what) -> dao_status {
+        if (e == cudaSuccess) return DAO_OK;
+        free_temps();
+        return fail(DAO_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    DAO_TRY(cu(cudaMemcpyAsync(t_rp, Din->row_ptr, sizeof(int64_t) * (V + 1), cudaMemcpyHostToDevice, st), "upload"));
+    DAO_TRY(cu(cudaMemcpyAsync(t_col, Din->col, sizeof(int) * nnz, cudaMemcpyHostToDevice, st), "upload"));
+    DAO_TRY(cu(cudaMemcpyAsync(t_val, Din->val, sizeof(float) * nnz, cudaMemcpyHostToDevice, st), "upload"));
+    c->D.n_rows = V;
+    c->D.n_cols = N;
+    c->D.nnz_stored = padded;
+    c->D.prec = prec;
+    c->Dt.n_rows = N;
+    c->Dt.n_cols = V;
+    c->Dt.prec = prec;
+    float* scale = nullptr;
+    DAO_TRY(c->dalloc(&scale, N));
+    c->D.scale = scale;
+    c->Dt.scale = scale;
+    DAO_TRY(upload(c, &c->D.rowptr, prow.data(), prow.size()));
+    DAO_TRY(upload(c, &c->beam_off_d, c->beam_off.data(), c->beam_off.size()));
+    DAO_TRY(c->dalloc(&c->seg, (size_t)(B + 1) * V));
+    if (prec == DAO_PREC_FP32) {
+        DAO_TRY(c->dalloc(&c->D.col, padded));
+        DAO_TRY(c->dalloc(&c->D.val, padded));
+    } else {
+        DAO_TRY(c->dalloc(&c->D.col16, padded));
+        DAO_TRY(c->dalloc(&c->D.val16, padded));
     }
-    // D^T (beamlet-major) by a counting sort over columns; voxels stay in increasing order
-    std::vector<int64_t> cnt(N + 1, 0);
-    for (int64_t p = 0; p < Din->nnz; ++p) ++cnt[Din->col[p] + 1];
-    std::vector<int64_t> trp(N + 1, 0);
-    for (int i = 0; i < N; ++i) trp[i + 1] = trp[i] + cnt[i + 1];
-    std::vector<int32_t> tcol(Din->nnz);
-    std::vector<float> tval(Din->nnz);
-    {
-        std::vector<int64_t> fill(trp.begin(), trp.end() - 1);
-        for (int j = 0; j < V; ++j)
-            for (int64_t p = rp[j]; p < rp[j + 1]; ++p) {
-                const int i = Din->col[p];
-                tcol[fill[i]] = j;
-                tval[fill[i]] = Din->val[p];
-                ++fill[i];
-            }
-    }
+    DAO_TRY(cu(build_scales(t_col, t_val, nnz, N, reinterpret_cast<unsigned*>(scale), t_dmax, c->num_sms, st),
+               "per-beamlet scales"));
+    DAO_TRY(cu(build_fill_d(prec, t_rp, t_col, t_val, c->D.rowptr, V, scale, c->D, st), "padded D"));
+    DAO_TRY(cu(build_seg(t_rp, t_col, c->D.rowptr, V, c->beam_off_d, B, c->seg, st), "beam segments"));
+    DAO_TRY(cu(build_transpose_count(t_rp, t_col, V, CH, N, n_ch, t_C, t_cnt, st), "transpose counts"));
+    // counts and the largest |D_ij| back to the host: row offsets of D^T, tau
+    std::vector<int> cnt(N);
+    unsigned dmax_bits = 0;
+    DAO_TRY(cu(cudaMemcpyAsync(cnt.data(), t_cnt, sizeof(int) * N, cudaMemcpyDeviceToHost, st), "counts"));
+    DAO_TRY(cu(cudaMemcpyAsync(&dmax_bits, t_dmax, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "max"));
+    DAO_TRY(cu(cudaStreamSynchronize(st), "device build"));
+    std::vector<int> trow(N + 1, 0);
     int64_t tpadded = 0;
-    for (int i = 0; i < N; ++i) tpadded += round_up(trp[i + 1] - trp[i], pad_m);
-    if (tpadded >= (int64_t)1 << 31) return fail(DAO_EINVAL, "D^T too large for 32-bit row offsets");
-    HostCSR Th;
-    pad_rows(N, trp, tcol.data(), tval.data(), Th, pad_m);
+    for (int i = 0; i < N; ++i) {
+        trow[i] = (int)std::min<int64_t>(tpadded, INT32_MAX);
+        tpadded += round_up(cnt[i], pad_m);
+    }
+    if (tpadded >= (int64_t)1 << 31) {
+        free_temps();
+        return fail(DAO_EINVAL, "D^T too large for 32-bit row offsets");
+    }
+    trow[N] = (int)tpadded;
+    c->Dt.nnz_stored = tpadded;
+    DAO_TRY(upload(c, &c->Dt.rowptr, trow.data(), trow.size()));
+    DAO_TRY(c->dalloc(&c->Dt.col, tpadded));
+    if (prec == DAO_PREC_FP32) {
+        DAO_TRY(c->dalloc(&c->Dt.val, tpadded));
+        t_tval = c->Dt.val;
+    } else {
+        DAO_TRY(c->dalloc(&c->Dt.val16, tpadded));
+        DAO_TRY(talloc(&t_tval, sizeof(float) * tpadded));
+    }
+    DAO_TRY(cu(build_transpose_place(prec, t_rp, t_col, t_val, V, CH, N, n_ch, t_C, t_cnt, scale, c->Dt, t_tval, st),
+               "transpose"));
+    free_temps();
+    float dmax = 0.f;
+    std::memcpy(&dmax, &dmax_bits, sizeof(float));
 
     // objective terms per structure (Eqs. 9-10)
     const int S = s->n_structures;
@@ -355,56 +431,10 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
         // |grad F(0)| summed over the structure's voxels
         pi0_l1 += (double)count[k] * (2.0 * tdh[k].a * std::max(0.0, tdh[k].tu) + 2.0 * tdh[k].b * std::max(0.0, -tdh[k].to));
     }
-    float dmax = 0.f;
-    for (int64_t p = 0; p < Din->nnz; ++p) dmax = std::max(dmax, std::fabs(Din->val[p]));
     c->tau = c->opt.price_tol * (double)dmax * pi0_l1;
     std::vector<uint8_t> vs(V);
     for (int j = 0; j < V; ++j) vs[j] = (uint8_t)s->voxel_struct[j];
 
-    // upload
-    c->D.n_rows = V;
-    c->D.n_cols = N;
-    c->D.nnz_stored = padded;
-    c->D.prec = prec;
-    c->Dt.n_rows = N;
-    c->Dt.n_cols = V;
-    c->Dt.nnz_stored = tpadded;
-    c->Dt.prec = prec;
-    DAO_TRY(upload(c, &c->D.rowptr, Dh.rowptr.data(), Dh.rowptr.size()));
-    DAO_TRY(upload(c, &c->Dt.rowptr, Th.rowptr.data(), Th.rowptr.size()));
-    DAO_TRY(upload(c, &c->Dt.col, Th.col.data(), Th.col.size()));
-    if (prec == DAO_PREC_FP32) {
-        DAO_TRY(upload(c, &c->D.col, Dh.col.data(), Dh.col.size()));
-        DAO_TRY(upload(c, &c->D.val, Dh.val.data(), Dh.val.size()));
-        DAO_TRY(upload(c, &c->Dt.val, Th.val.data(), Th.val.size()));
-    } else {
-        // 16-bit storage: s_i = max_j |D_ij| per beamlet (1 for an empty beamlet),
-        // stored value RN16(D_ij / s_i) with the quotient rounded to FP32 first
-        std::vector<float> scale(N, 0.f);
-        for (int64_t p = 0; p < Din->nnz; ++p) scale[Din->col[p]] = std::max(scale[Din->col[p]], std::fabs(Din->val[p]));
-        for (int i = 0; i < N; ++i)
-            if (!(scale[i] > 0.f)) scale[i] = 1.f;
-        auto q16 = [&](float v, int i) -> uint16_t {
-            const float r = v / scale[i];
-            if (prec == DAO_PREC_FP16) return static_cast<__half_raw>(__float2half_rn(r)).x;
-            return static_cast<__nv_bfloat16_raw>(__float2bfloat16_rn(r)).x;
-        };
-        std::vector<uint16_t> c16(Dh.col.size()), v16(Dh.val.size()), tv16(Th.val.size());
-        for (size_t q = 0; q < Dh.col.size(); ++q) {
-            c16[q] = (uint16_t)Dh.col[q];
-            v16[q] = q16(Dh.val[q], Dh.col[q]);
-        }
-        for (int i = 0; i < N; ++i)
-            for (int q = Th.rowptr[i]; q < Th.rowptr[i + 1]; ++q) tv16[q] = q16(Th.val[q], i);
-        DAO_TRY(upload(c, &c->D.col16, c16.data(), c16.size()));
-        DAO_TRY(upload(c, &c->D.val16, v16.data(), v16.size()));
-        DAO_TRY(upload(c, &c->Dt.val16, tv16.data(), tv16.size()));
-        float* sd = nullptr;
-        DAO_TRY(upload(c, &sd, scale.data(), scale.size()));
-        c->D.scale = sd;
-        c->Dt.scale = sd;
-    }
-    DAO_TRY(upload(c, &c->seg, seg.data(), seg.size()));
     DAO_TRY(upload(c, &c->vstruct, vs.data(), vs.size()));
     DAO_TRY(upload(c, &c->tf, tfh.data(), tfh.size()));
     DAO_TRY(upload(c, &c->td, tdh.data(), tdh.size()));
@@ -413,7 +443,7 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     DAO_TRY(upload(c, &c->binfo, bi.data(), bi.size()));
     DAO_TRY(upload(c, &c->rows_d, c->rows.data(), c->rows.size()));
     DAO_TRY(upload(c, &c->cols_d, c->cols.data(), c->cols.size()));
-    DAO_TRY(upload(c, &c->beam_off_d, c->beam_off.data(), c->beam_off.size()));
+    DAO_TRY(sync(c));
     return DAO_OK;
 }
 
@@ -447,7 +477,7 @@ dao_status alloc_state(dao_ctx* c) {
     c->mb.n_tiles = (c->V + MASTER_TILE - 1) / MASTER_TILE;
     c->ld = c->mb.n_tiles * MASTER_TILE;  // column stride: voxels zero padded to whole tiles
     DAO_TRY(c->dalloc(&c->slab, (size_t)c->ld * KMAX));
-    DAO_CU(cudaMemset(c->slab, 0, (size_t)c->ld * KMAX * sizeof(float)));
+    DAO_CU(cudaMemsetAsync(c->slab, 0, (size_t)c->ld * KMAX * sizeof(float), c->stream));
     DAO_TRY(make_tensor_maps(c));
     DAO_TRY(c->dalloc(&c->ap_beam, c->K_cap));
     DAO_TRY(c->dalloc(&c->ap_lr, (size_t)c->K_cap * 2 * c->max_rows));
@@ -461,7 +491,7 @@ dao_status alloc_state(dao_ctx* c) {
     DAO_TRY(c->dalloc(&c->mask, nbmax));
     c->max_nb = nbmax;
     DAO_TRY(c->dalloc(&c->cg, 1));
-    DAO_CU(cudaMemset(c->cg, 0, sizeof(CGDev)));
+    DAO_CU(cudaMemsetAsync(c->cg, 0, sizeof(CGDev), c->stream));
     c->round_graph.assign(c->K_cap + 1, nullptr);
     c->round_exec.assign(c->K_cap + 1, nullptr);
     DAO_TRY(c->dalloc(&c->row_v, c->R_tot));
@@ -473,7 +503,7 @@ dao_status alloc_state(dao_ctx* c) {
     DAO_TRY(c->dalloc(&c->mb.act_rows, (size_t)c->ld * KROW));
     DAO_TRY(c->dalloc(&c->mb.act_hp, (size_t)c->ld));
     DAO_TRY(c->dalloc(&c->mb.act_count, (size_t)c->mb.n_tiles));
-    DAO_CU(cudaMemset(c->mb.act_count, 0, (size_t)c->mb.n_tiles * sizeof(int)));
+    DAO_CU(cudaMemsetAsync(c->mb.act_count, 0, (size_t)c->mb.n_tiles * sizeof(int), c->stream));
     DAO_TRY(c->dalloc(&c->mb.H_part, (size_t)KMAX * (KMAX + 1) / 2 * c->mb.GH));
     DAO_TRY(c->dalloc(&c->mb.g_part, (size_t)KMAX * c->mb.GH));
     DAO_TRY(c->dalloc(&c->mb.gn_part, (size_t)KMAX * c->mb.GH));
@@ -481,8 +511,8 @@ dao_status alloc_state(dao_ctx* c) {
     c->F_blocks = dose_grid(c->V, c->num_sms);
     DAO_TRY(c->dalloc(&c->F_part, c->F_blocks));
     DAO_TRY(c->dalloc(&c->F_dev, 1));
-    DAO_CU(cudaMemset(c->mb.st, 0, sizeof(MasterDev)));
-    DAO_CU(cudaMemset(c->ap_lr, 0, (size_t)c->K_cap * 2 * c->max_rows * sizeof(int)));
+    DAO_CU(cudaMemsetAsync(c->mb.st, 0, sizeof(MasterDev), c->stream));
+    DAO_CU(cudaMemsetAsync(c->ap_lr, 0, (size_t)c->K_cap * 2 * c->max_rows * sizeof(int), c->stream));
     c->off_small = 0;
     c->off_rows = 256;
     c->off_mask = c->off_rows + round4((int64_t)c->R_tot * 2) * sizeof(int);

@@ -177,6 +177,19 @@ cudaError_t launch_master_eval(const MasterBuffers& mb, int V, int K, const uint
                                const StructTermsF* tf, int S, float* z_out, float* pi_out, int mode,
                                const int* skip, cudaStream_t stream, int* launches);
 cudaError_t launch_master_hess(const MasterBuffers& mb, int K, int mode, cudaStream_t stream, int* launches);
+// Device-side construction of the matrices (build.cu).
+cudaError_t build_scales(const int* col, const float* val, int64_t nnz, int N, unsigned* smax, unsigned* dmax,
+                         int num_sms, cudaStream_t s);
+cudaError_t build_fill_d(int prec, const int64_t* rp, const int* col, const float* val, const int* prow, int V,
+                         const float* scale, DevCSR& D, cudaStream_t s);
+cudaError_t build_seg(const int64_t* rp, const int* col, const int* prow, int V, const int* beam_off, int B, int* seg,
+                      cudaStream_t s);
+cudaError_t build_transpose_count(const int64_t* rp, const int* col, int V, int CH, int N, int n_ch, int* C, int* cnt,
+                                  cudaStream_t s);
+cudaError_t build_transpose_place(int prec, const int64_t* rp, const int* col, const float* val, int V, int CH, int N,
+                                  int n_ch, int* C, const int* cnt, const float* scale, DevCSR& Dt, float* tval,
+                                  cudaStream_t s);
+
 // Reduction of the partial sums and the projected-Newton step, one launch.
 cudaError_t launch_master_step(int K, const MasterBuffers& mb, int max_iter, double tol_rel,
                                cudaGraphConditionalHandle cond, int use_cond, cudaStream_t stream, int* launches);
