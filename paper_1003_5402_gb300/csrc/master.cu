@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(TILE, 3) k_master_eval(const __grid_constant__
     __shared__ float s_yh[KMAX], s_yl[KMAX];
     __shared__ int s_wcount[TILE / 32];
     __shared__ StructTermsF s_tf[SMAX];
-    __shared__ double s_red[TILE / 32];
+    __shared__ float s_red[TILE / 32];
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     if (tid < KMAX) {
@@ -268,12 +268,15 @@ __global__ void __launch_bounds__(TILE, 3) k_master_eval(const __grid_constant__
         return;
     }
     if (final_pass) return;
-    double fsum = warp_sum_f64((double)facc);
-    if (lane == 0) s_red[warp] = fsum;
+    // F: FP32 within a warp (32 voxel terms), FP64 across the block's warps
+    // (FP64 runs at 1/64 of the FP32 rate here: keep it to a few lanes)
+    const float fw = warp_sum_f32(facc);
+    if (lane == 0) s_red[warp] = fw;
     __syncthreads();
     if (tid < 32) {
-        double t = tid < TILE / 32 ? s_red[tid] : 0.0;
-        t = warp_sum_f64(t);
+        double t = tid < TILE / 32 ? (double)s_red[tid] : 0.0;
+#pragma unroll
+        for (int o = TILE / 64; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
         if (tid == 0) F_part[blockIdx.x] = t;
     }
 }
@@ -458,11 +461,11 @@ __device__ __forceinline__ void master_reduce_part(const float* __restrict__ H_p
     const int lane = threadIdx.x & 31;
     const int n_out = E + 2 * K + 1;
     for (int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < n_out; o += (gridDim.x * blockDim.x) >> 5) {
-        if (o < E) {
-            double s = 0.0;
+        if (o < E) {  // the factorisation is FP32: so is this sum
+            float s = 0.f;
             const float* src = H_part + (size_t)o * GH;
-            for (int b = lane; b < GH; b += 32) s += (double)src[b];
-            s = warp_sum_f64(s);
+            for (int b = lane; b < GH; b += 32) s += src[b];
+            s = warp_sum_f32(s);
             if (lane == 0) {
                 int r = 0, rem = o;
                 while (rem >= K - r) {
@@ -470,8 +473,8 @@ __device__ __forceinline__ void master_reduce_part(const float* __restrict__ H_p
                     ++r;
                 }
                 const int c = r + rem;
-                st->Ht[r * KMAX + c] = (float)s;
-                st->Ht[c * KMAX + r] = (float)s;
+                st->Ht[r * KMAX + c] = s;
+                st->Ht[c * KMAX + r] = s;
             }
         } else if (o < E + K) {
             const int k = o - E;
@@ -525,6 +528,7 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     __shared__ int fidx[KMAX];
     __shared__ double sw[STEP_W];
     __shared__ double sw2[STEP_W];
+    __shared__ double sw3[STEP_W];
     __shared__ int swi[STEP_W];
     // every value the step reads is loaded up front (independent loads, one round
     // trip); gt, gn, Ft and Ht were written by other blocks of this launch and
@@ -544,36 +548,51 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
         return;
     }
     const bool own = k < K;
+    // only the first nw warps hold variables (K <= 64): they alone run the FP64
+    // reductions, which issue at 1/64 of the FP32 rate on this part
+    const int nw = (K + 31) >> 5;
+    const bool vwarp = (k >> 5) < nw;
     const double yt = own ? yt_ : 0.0, gt = own ? gt_ : 0.0, gn = own ? gn_ : 0.0;
     const double y = own ? y_ : 0.0, g = own ? g_ : 0.0;
     // tolerance of this solve from the gradient at the warm start
     double tol = tol0;
     if (phase == 0) {
-        tol = tol_rel * fmax(blk_max(own ? fabs(gt) : 0.0, sw), 1e-300);
+        if (vwarp) {
+            double m = own ? fabs(gt) : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(FULL, m, o));
+            if ((k & 31) == 0) sw3[k >> 5] = m;
+        }
+        __syncthreads();
+        double m = sw3[0];
+        for (int w = 1; w < nw; ++w) m = fmax(m, sw3[w]);
+        tol = tol_rel * fmax(m, 1e-300);
         if (k == 0) st->tol = tol;
     }
-    // KKT violation flag, residual and Armijo decrease in one block reduction
-    const double rt = own ? fabs(yt - fmax(yt - gt, 0.0)) : 0.0;
-    int viol = __any_sync(FULL, own && rt > tol + NOISE * (double)U32 * gn) ? 1 : 0;
-    double rmax = rt;
-    double dec = own ? g * (yt - y) : 0.0;
+    // KKT violation flag, residual and Armijo decrease in one reduction
+    double rmax = 0.0, dec = 0.0;
+    int viol = 0;
+    if (vwarp) {
+        const double rt = own ? fabs(yt - fmax(yt - gt, 0.0)) : 0.0;
+        viol = __any_sync(FULL, own && rt > tol + NOISE * (double)U32 * gn) ? 1 : 0;
+        rmax = rt;
+        dec = own ? g * (yt - y) : 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        rmax = fmax(rmax, __shfl_xor_sync(FULL, rmax, o));
-        dec += __shfl_xor_sync(FULL, dec, o);
-    }
-    __syncthreads();
-    if ((k & 31) == 0) {
-        sw[k >> 5] = rmax;
-        sw2[k >> 5] = dec;
-        swi[k >> 5] = viol;
+        for (int o = 16; o > 0; o >>= 1) {
+            rmax = fmax(rmax, __shfl_xor_sync(FULL, rmax, o));
+            dec += __shfl_xor_sync(FULL, dec, o);
+        }
+        if ((k & 31) == 0) {
+            sw[k >> 5] = rmax;
+            sw2[k >> 5] = dec;
+            swi[k >> 5] = viol;
+        }
     }
     __syncthreads();
     rmax = sw[0];
     dec = sw2[0];
     viol = swi[0];
-#pragma unroll
-    for (int w = 1; w < STEP_W; ++w) {
+    for (int w = 1; w < nw; ++w) {
         rmax = fmax(rmax, sw[w]);
         dec += sw2[w];
         viol |= swi[w];
@@ -622,8 +641,11 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
         return;
     }
     // epsilon-active set, free variables compacted in order
-    const double eps = fmin(1e-3, rmax);
-    const bool active = own && yt <= eps && gt > 0.0;
+    bool active = false;
+    if (vwarp) {
+        const double eps = fmin(1e-3, rmax);
+        active = own && yt <= eps && gt > 0.0;
+    }
     const bool fr = own && !active;
     const unsigned bal = __ballot_sync(FULL, fr);
     __syncthreads();

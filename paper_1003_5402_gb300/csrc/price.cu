@@ -168,7 +168,9 @@ cudaError_t launch_commit(const PriceDev* pr, const int2* row_lr, const int* bea
 cudaError_t launch_price(const float* w, const int4* row_info, int n_rows, const int* beam_row0, int n_beams,
                          double* row_v, int2* row_lr, PriceDev* out, const int* skip, cudaStream_t stream,
                          int* launches) {
-    const int warps_per_block = 8;
+    // one warp per block: the FP64 prefix sums of a row issue at 1/64 of the FP32
+    // rate, so the rows are spread over every SM rather than packed 8 to a block
+    const int warps_per_block = 1;
     const int grid = (n_rows + warps_per_block - 1) / warps_per_block;
     if (grid > 0) {
         k_price_rows<<<grid, 32 * warps_per_block, 0, stream>>>(w, row_info, n_rows, row_v, row_lr, skip);

@@ -23,6 +23,22 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
     return v;
 }
 
+// Sum over a block: FP32 within each warp, FP64 across the warps (FP64 issues
+// at 1/64 of the FP32 rate on this part, so it is kept to one lane per warp).
+template <int NT>
+__device__ __forceinline__ double block_sum_mixed(float v, double* s_red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) s_red[warp] = (double)v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) t += s_red[w];
+    return t;
+}
+
 // Sum of one double per thread over the block; the result is valid in thread 0.
 template <int NT>
 __device__ __forceinline__ double block_sum_f64(double v, double* s_red) {
@@ -128,7 +144,7 @@ __global__ void __launch_bounds__(BT) k_dt(const int* __restrict__ rowptr, const
         acc = fmaf(v.z, __ldg(pi + c.z), acc);
         acc = fmaf(v.w, __ldg(pi + c.w), acc);
     }
-    const double s = block_sum_f64<BT>((double)acc, s_red);
+    const double s = block_sum_mixed<BT>(acc, s_red);
     if (threadIdx.x == 0) w[row] = (float)s;
 }
 
@@ -321,7 +337,7 @@ __global__ void __launch_bounds__(BT) k_dt16(const int* __restrict__ rowptr, con
         acc = fmaf(d.x, __ldg(pi + c1.z), acc);
         acc = fmaf(d.y, __ldg(pi + c1.w), acc);
     }
-    const double sres = block_sum_f64<BT>((double)acc, s_red);
+    const double sres = block_sum_mixed<BT>(acc, s_red);
     if (threadIdx.x == 0) w[row] = (float)(sres * (double)scale[row]);
 }
 
