@@ -334,22 +334,13 @@ def spmv_bandwidth(torch, plan, case, prec, flush, hbm_peak):
     g = torch.empty_like(z)
     pi = torch.randn(case.n_voxels, device="cuda")
     w = torch.empty(case.n_beamlets, device="cuda")
-    for kc, fn in (("dose", lambda: plan.k_dose(x, z, g, objective=False)),
-                   ("dt", lambda: plan.k_beamlet_prices(pi, w))):
-        for _ in range(3):
-            fn()
-        per = []
-        for _ in range(20):
-            flush.zero_()
-            plan.profile_enable(True)
-            fn()
-            nl, ms = plan.profile_read(kc)
-            per.append(ms)
-        plan.profile_enable(False)
+    plan.k_dose(x, z, g, objective=False)       # the dose kernel times on this fluence
+    plan.k_beamlet_prices(pi, w)
+    for kc in ("dose", "dt"):
+        us = plan.k_time_cold(kc, flush, reps=20)   # graph: [flush, event, kernel, event] x 20, median
         byt = algorithmic_bytes(case, plan, kc, 1, prec)
-        med = statistics.median(per)
-        out[kc] = {"us": round(med * 1e3, 2), "gbs": round(byt / (med * 1e-3) / 1e9, 1),
-                   "frac_of_hbm": round(byt / (med * 1e-3) / 1e9 / hbm_peak, 4), "bytes": int(byt)}
+        out[kc] = {"us": round(us, 2), "gbs": round(byt / (us * 1e-6) / 1e9, 1),
+                   "frac_of_hbm": round(byt / (us * 1e-6) / 1e9 / hbm_peak, 4), "bytes": int(byt)}
     return out
 
 

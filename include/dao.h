@@ -198,6 +198,14 @@ dao_status dao_k_state(dao_ctx* ctx, float* z, float* pi);
  * DAO_KC_DOSE, DAO_KC_COLUMN (first aperture of the pool), DAO_KC_PRICE.
  * Results and the pool are unchanged; scratch buffers are overwritten. */
 dao_status dao_k_time(dao_ctx* ctx, int32_t kc, int32_t K, int32_t reps, double* us_per_launch);
+/* Cold-cache device time of one launch of DAO_KC_DOSE, DAO_KC_DT or
+ * DAO_KC_PRICE: `reps` (1..1024) repetitions of [read all flush_bytes of the
+ * caller's device buffer `flush` (make it larger than L2; reading leaves only
+ * clean lines, so no write-back overlaps the kernel), event, launch, event]
+ * captured into one CUDA graph and replayed once; *us_median (host) receives
+ * the median in microseconds.  K is ignored.  Synchronises. */
+dao_status dao_k_time_cold(dao_ctx* ctx, int32_t kc, int32_t K, int32_t reps, void* flush, int64_t flush_bytes,
+                           double* us_median);
 
 /* ---- instrumentation: per-kernel-class CUDA-event timing on the context's
  * stream (off by default).  While it is on, dao_solve uses host-driven

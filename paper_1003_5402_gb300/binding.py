@@ -99,6 +99,7 @@ SIGNATURES = {
     "dao_k_aperture_column": (C.c_int, [_P, C.c_int32, _I32P, _P]),
     "dao_k_state": (C.c_int, [_P, _P, _P]),
     "dao_k_time": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _F64P]),
+    "dao_k_time_cold": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, _P, C.c_int64, _F64P]),
     "dao_profile_enable": (C.c_int, [_P, C.c_int32]),
     "dao_profile_read": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int64), _F64P]),
     "dao_launch_count": (C.c_int64, [_P]),
@@ -331,6 +332,14 @@ class Plan:
         """Average microseconds per launch of one kernel class (dao_k_time)."""
         us = C.c_double()
         _check(load().dao_k_time(self.h, KC[kc], int(K), int(reps), C.byref(us)), "dao_k_time")
+        return us.value
+
+    def k_time_cold(self, kc: str, flush, reps: int = 20) -> float:
+        """Median cold-cache microseconds of one launch (dao_k_time_cold); ``flush``
+        is a CUDA tensor larger than L2 that each repetition overwrites first."""
+        us = C.c_double()
+        _check(load().dao_k_time_cold(self.h, KC[kc], 0, int(reps), C.c_void_p(flush.data_ptr()),
+                                      int(flush.numel() * flush.element_size()), C.byref(us)), "dao_k_time_cold")
         return us.value
 
     def profile_enable(self, on: bool = True):

@@ -70,7 +70,7 @@ struct dao_ctx {
     int* seg = nullptr;              // (B + 1) x V: start of beam b's entries in row j; [B] = end of real entries
     uint8_t* vstruct = nullptr;
     StructTermsF* tf = nullptr;
-    StructTermsD* td = nullptr;
+    StructTermsS* ts = nullptr;      // FP32 dose-epilogue terms, thresholds split hi + lo
     int4* row_info = nullptr;        // per MLC row: beam, first beamlet, columns, row within beam
     int* beam_row0_d = nullptr;
     int4* binfo = nullptr;           // per beamlet: beam, row, column
@@ -398,6 +398,16 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     trow[N] = (int)tpadded;
     c->Dt.nnz_stored = tpadded;
     DAO_TRY(upload(c, &c->Dt.rowptr, trow.data(), trow.size()));
+    // rows of D^T by decreasing length (ties by index) for the transposed SpMV;
+    // the host copy lives until build() has synchronised
+    std::vector<int> order(N);
+    for (int i = 0; i < N; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cnt[a] > cnt[b]; });
+    {
+        int* od = nullptr;
+        DAO_TRY(upload(c, &od, order.data(), order.size()));
+        c->Dt.order = od;
+    }
     DAO_TRY(c->dalloc(&c->Dt.col, tpadded));
     if (prec == DAO_PREC_FP32) {
         DAO_TRY(c->dalloc(&c->Dt.val, tpadded));
@@ -419,6 +429,7 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     for (int j = 0; j < V; ++j) ++count[s->voxel_struct[j]];
     std::vector<StructTermsD> tdh(S);
     std::vector<StructTermsF> tfh(S);
+    std::vector<StructTermsS> tsh(S);
     double pi0_l1 = 0.0;
     for (int k = 0; k < S; ++k) {
         const double vol = (w->normalize_by_volume && count[k] > 0) ? (double)count[k] : 1.0;
@@ -428,6 +439,9 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
         tdh[k].b = w->over_w[k] / vol;
         tdh[k].to = w->over_thresh[k];
         tfh[k] = {(float)tdh[k].a, (float)tdh[k].tu, (float)tdh[k].b, (float)tdh[k].to};
+        const float tu_hi = (float)tdh[k].tu, to_hi = (float)tdh[k].to;
+        tsh[k] = {(float)tdh[k].a, tu_hi, (float)(tdh[k].tu - (double)tu_hi), (float)tdh[k].b, to_hi,
+                  (float)(tdh[k].to - (double)to_hi), 0.f, 0.f};
         // |grad F(0)| summed over the structure's voxels
         pi0_l1 += (double)count[k] * (2.0 * tdh[k].a * std::max(0.0, tdh[k].tu) + 2.0 * tdh[k].b * std::max(0.0, -tdh[k].to));
     }
@@ -437,7 +451,7 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
 
     DAO_TRY(upload(c, &c->vstruct, vs.data(), vs.size()));
     DAO_TRY(upload(c, &c->tf, tfh.data(), tfh.size()));
-    DAO_TRY(upload(c, &c->td, tdh.data(), tdh.size()));
+    DAO_TRY(upload(c, &c->ts, tsh.data(), tsh.size()));
     DAO_TRY(upload(c, &c->row_info, ri.data(), ri.size()));
     DAO_TRY(upload(c, &c->beam_row0_d, c->beam_row0.data(), c->beam_row0.size()));
     DAO_TRY(upload(c, &c->binfo, bi.data(), bi.size()));
@@ -1042,7 +1056,7 @@ dao_status dao_dose(dao_ctx* c, float* dose, double* objective) {
     DAO_CU(launch_fluence(c->ap_beam, c->ap_lr, 2 * c->max_rows, c->mb.st->y, c->K, c->binfo, c->N, c->x, c->stream,
                           &c->launches_i));
     c->prof_begin(DAO_KC_DOSE);
-    DAO_CU(launch_dose(c->D, c->x, c->vstruct, c->tf, c->td, c->S, c->dose, nullptr, c->F_part, c->F_blocks, c->F_dev,
+    DAO_CU(launch_dose(c->D, c->x, c->vstruct, c->tf, c->ts, c->S, c->dose, nullptr, c->F_part, c->F_blocks, c->F_dev,
                        c->num_sms, c->stream, &c->launches_i));
     c->prof_end();
     double* f = reinterpret_cast<double*>(c->pinned + c->off_small + 8);
@@ -1076,7 +1090,7 @@ dao_status dao_k_dose(dao_ctx* c, const float* x, float* z, float* grad, double*
     DAO_TRY(check_ctx(c));
     if (!x || !z) return fail(DAO_EINVAL, "null vector");
     c->prof_begin(DAO_KC_DOSE);
-    DAO_CU(launch_dose(c->D, x, c->vstruct, c->tf, c->td, c->S, z, grad, objective ? c->F_part : nullptr, c->F_blocks,
+    DAO_CU(launch_dose(c->D, x, c->vstruct, c->tf, c->ts, c->S, z, grad, objective ? c->F_part : nullptr, c->F_blocks,
                        c->F_dev, c->num_sms, c->stream, &c->launches_i));
     c->prof_end();
     if (objective) {
@@ -1146,7 +1160,7 @@ cudaError_t time_one(dao_ctx* c, int kc, int K, cudaStream_t s, int* n) {
         case DAO_KC_DT:
             return launch_dt(c->Dt, c->pi, c->w, nullptr, s, n);
         case DAO_KC_DOSE:
-            return launch_dose(c->D, c->x, c->vstruct, c->tf, c->td, c->S, c->dose, nullptr, nullptr, 0, nullptr,
+            return launch_dose(c->D, c->x, c->vstruct, c->tf, c->ts, c->S, c->dose, nullptr, nullptr, 0, nullptr,
                                c->num_sms, s, n);
         case DAO_KC_COLUMN: {
             const int b = c->ap_beam_h[0];
@@ -1249,6 +1263,53 @@ dao_status dao_k_time(dao_ctx* c, int32_t kc, int32_t K, int32_t reps, double* u
     double us = 0.0;
     DAO_TRY(time_graph(c, reps, [&](int* n) { return time_one(c, kc, K, c->stream, n); }, &us, "dao_k_time"));
     *us_per_launch = us;
+    return DAO_OK;
+}
+
+dao_status dao_k_time_cold(dao_ctx* c, int32_t kc, int32_t K, int32_t reps, void* flush, int64_t flush_bytes,
+                           double* us_median) {
+    DAO_TRY(check_ctx(c));
+    if (reps < 1 || reps > 1024 || !us_median || !flush || flush_bytes < 1)
+        return fail(DAO_EINVAL, "reps in [1, 1024], a flush buffer and an output are required");
+    if (kc == DAO_KC_MASTER_PASS || kc == DAO_KC_MASTER_HESS || kc == DAO_KC_COLUMN ||
+        (kc != DAO_KC_DT && kc != DAO_KC_DOSE && kc != DAO_KC_PRICE))
+        return fail(DAO_EINVAL, "cold timing covers DAO_KC_DOSE, DAO_KC_DT and DAO_KC_PRICE");
+    DAO_TRY(sync(c));
+    std::vector<cudaEvent_t> ev(2 * (size_t)reps, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (auto& x : ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&x);
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    int n = 0;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        // per repetition: read a buffer larger than L2 (clean lines only, so no
+        // write-back overlaps the kernel), then the kernel between two events
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+            e = launch_l2_evict(flush, (size_t)flush_bytes, c->w, c->num_sms, c->stream);
+            // external records: event nodes that the host can time after the replay
+            if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2 * r], c->stream, cudaEventRecordExternal);
+            if (e == cudaSuccess) e = time_one(c, kc, K, c->stream, &n);
+            if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2 * r + 1], c->stream, cudaEventRecordExternal);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ex, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    std::vector<float> ms(reps, 0.f);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaEventElapsedTime(&ms[r], ev[2 * r], ev[2 * r + 1]);
+    if (ex) cudaGraphExecDestroy(ex);
+    if (g) cudaGraphDestroy(g);
+    for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) return fail(DAO_ECUDA, std::string("dao_k_time_cold: ") + cudaGetErrorString(e));
+    c->launches_i += n;
+    c->count_launches();
+    std::sort(ms.begin(), ms.end());
+    *us_median = 1e3 * (reps % 2 ? ms[reps / 2] : 0.5 * (ms[reps / 2 - 1] + ms[reps / 2]));
     return DAO_OK;
 }
 
@@ -1357,7 +1418,7 @@ dao_status dao_autotune(dao_ctx* c, const char* cache_path, dao_tuning* out) {
             c->D.tune_dose_g = g;
             double us = 0.0;
             DAO_TRY(time_graph(c, reps, [&](int* nl) {
-                return launch_dose(c->D, c->x, c->vstruct, c->tf, c->td, c->S, c->dose, nullptr, nullptr, 0, nullptr,
+                return launch_dose(c->D, c->x, c->vstruct, c->tf, c->ts, c->S, c->dose, nullptr, nullptr, 0, nullptr,
                                    c->num_sms, c->stream, nl);
             }, &us, "dao_autotune"));
             if (us < best) {

@@ -34,6 +34,9 @@ constexpr int KROW = KMAX + 4;    // row stride (floats) of the active-voxel row
 // non-targets), tu = T_s^-, b = beta_s/|v_s|, to = T_s^+.
 struct StructTermsF { float a, tu, b, to; };
 struct StructTermsD { double a, tu, b, to; };
+// FP32 terms of the dose epilogue with each threshold split into hi + lo floats,
+// so that T - z is exact near the threshold.
+struct StructTermsS { float a, tu_hi, tu_lo, b, to_hi, to_lo, pad0, pad1; };
 
 // Device copy of a CSR matrix whose rows are padded to a multiple of four
 // entries (padding: value 0, column = the row's last real column), so every
@@ -49,6 +52,7 @@ struct DevCSR {
     unsigned short* col16 = nullptr;  // 16-bit layout of D: beamlet indices
     unsigned short* val16 = nullptr;  // 16-bit values D_ij / s_i (FP16 or BF16 bits)
     const float* scale = nullptr;     // 16-bit layout: per-beamlet scale s_i (length n_beamlets)
+    const int* order = nullptr;       // D^T: rows by decreasing length (block b takes row order[b])
     // launch shape chosen by the autotuner (0: built-in rule): lanes per row of the
     // dose SpMV and of the aperture column (D), threads per row of the transposed
     // SpMV (D^T)
@@ -112,7 +116,7 @@ struct CGDev {
 
 // a1: z = D x, optional grad F(z), FP64 F partials (one per block) reduced into *F_out.
 cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct,
-                        const StructTermsF* tf, const StructTermsD* td, int S,
+                        const StructTermsF* tf, const StructTermsS* ts, int S,
                         float* z, float* grad, double* F_part, int F_blocks, double* F_out,
                         int num_sms, cudaStream_t stream, int* launches);
 int dose_grid(int n_rows, int num_sms);
@@ -177,6 +181,9 @@ cudaError_t launch_master_eval(const MasterBuffers& mb, int V, int K, const uint
                                const StructTermsF* tf, int S, float* z_out, float* pi_out, int mode,
                                const int* skip, cudaStream_t stream, int* launches);
 cudaError_t launch_master_hess(const MasterBuffers& mb, int K, int mode, cudaStream_t stream, int* launches);
+// Read-only pass over a buffer larger than L2 (cold-cache timing).
+cudaError_t launch_l2_evict(const void* buf, size_t bytes, float* sink, int num_sms, cudaStream_t stream);
+
 // Device-side construction of the matrices (build.cu).
 cudaError_t build_scales(const int* col, const float* val, int64_t nnz, int N, unsigned* smax, unsigned* dmax,
                          int num_sms, cudaStream_t s);

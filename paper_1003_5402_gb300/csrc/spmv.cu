@@ -6,6 +6,8 @@
 // All reductions have a fixed order (per-lane sequential, then a fixed
 // shuffle tree, then fixed-order shared-memory combination), so every result
 // is bitwise reproducible for a given launch shape.  No atomics.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -62,15 +64,15 @@ __global__ void __launch_bounds__(256) k_dose(const int* __restrict__ rowptr, co
                                               const float4* __restrict__ val4, int V,
                                               const float* __restrict__ x, int N,
                                               const uint8_t* __restrict__ vstruct,
-                                              const StructTermsD* __restrict__ td, int S,
+                                              const StructTermsS* __restrict__ ts, int S,
                                               float* __restrict__ z, float* __restrict__ grad,
                                               double* __restrict__ F_part) {
     extern __shared__ float sx[];
-    __shared__ StructTermsD s_td[SMAX];
+    __shared__ StructTermsS s_ts[SMAX];
     __shared__ double s_red[8];
     if (SMEM_X)
         for (int i = threadIdx.x; i < N; i += blockDim.x) sx[i] = x[i];
-    for (int i = threadIdx.x; i < S; i += blockDim.x) s_td[i] = td[i];
+    for (int i = threadIdx.x; i < S; i += blockDim.x) s_ts[i] = ts[i];
     __syncthreads();
     const float* xs = SMEM_X ? sx : x;
     const int lane = threadIdx.x & 31;
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(256) k_dose(const int* __restrict__ rowptr, co
     const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n_warps = (gridDim.x * blockDim.x) >> 5;
     const int n_tiles = (V + RPW - 1) / RPW;
-    double facc = 0.0;
+    float facc = 0.f;
     for (int t = warp_global; t < n_tiles; t += n_warps) {
         const int row = t * RPW + lane / G;
         float acc = 0.f;
@@ -99,17 +101,17 @@ __global__ void __launch_bounds__(256) k_dose(const int* __restrict__ rowptr, co
         if (row < V && sub == 0) {
             z[row] = acc;
             if (grad != nullptr || F_part != nullptr) {
-                const StructTermsD tt = s_td[vstruct[row]];
-                const double zd = acc;
-                const double u = fmax(0.0, tt.tu - zd);
-                const double o = fmax(0.0, zd - tt.to);
-                if (grad != nullptr) grad[row] = (float)(2.0 * (tt.b * o - tt.a * u));
-                facc += tt.a * u * u + tt.b * o * o;
+                // FP32 epilogue (FP64 issues at 1/64 of the FP32 rate here)
+                const StructTermsS tt = s_ts[vstruct[row]];
+                const float u = fmaxf((tt.tu_hi - acc) + tt.tu_lo, 0.f);  // T^- - z
+                const float o = fmaxf((acc - tt.to_hi) - tt.to_lo, 0.f);  // z - T^+
+                if (grad != nullptr) grad[row] = 2.f * (tt.b * o - tt.a * u);
+                facc = fmaf(tt.a * u, u, fmaf(tt.b * o, o, facc));
             }
         }
     }
     if (F_part != nullptr) {
-        const double s = block_sum_f64<256>(facc, s_red);
+        const double s = block_sum_mixed<256>(facc, s_red);
         if (threadIdx.x == 0) F_part[blockIdx.x] = s;
     }
 }
@@ -129,20 +131,36 @@ __global__ void __launch_bounds__(256) k_sum_f64(const double* __restrict__ part
 template <int BT>
 __global__ void __launch_bounds__(BT) k_dt(const int* __restrict__ rowptr, const int4* __restrict__ col4,
                                            const float4* __restrict__ val4, int N,
+                                           const int* __restrict__ order,
                                            const float* __restrict__ pi, float* __restrict__ w,
                                            const int* __restrict__ skip) {
     __shared__ double s_red[BT / 32];
     if (skip != nullptr && *skip) return;
-    const int row = blockIdx.x;
+    const int row = order[blockIdx.x];  // longest rows first: they start in the first wave
     const int p0 = rowptr[row] >> 2, p1 = rowptr[row + 1] >> 2;
+    // software pipeline: the next group's indices and values (DRAM) are in
+    // flight while the current group's pi gathers (L2) and products run
     float acc = 0.f;
-    for (int p = p0 + threadIdx.x; p < p1; p += BT) {
-        const int4 c = __ldg(col4 + p);
-        const float4 v = __ldg(val4 + p);
-        acc = fmaf(v.x, __ldg(pi + c.x), acc);
-        acc = fmaf(v.y, __ldg(pi + c.y), acc);
-        acc = fmaf(v.z, __ldg(pi + c.z), acc);
-        acc = fmaf(v.w, __ldg(pi + c.w), acc);
+    int p = p0 + threadIdx.x;
+    int4 cn = make_int4(0, 0, 0, 0);
+    float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (p < p1) {
+        cn = __ldg(col4 + p);
+        vn = __ldg(val4 + p);
+    }
+    while (p < p1) {
+        const int4 c = cn;
+        const float4 v = vn;
+        p += BT;
+        if (p < p1) {
+            cn = __ldg(col4 + p);
+            vn = __ldg(val4 + p);
+        }
+        const float a0 = __ldg(pi + c.x), a1 = __ldg(pi + c.y), a2 = __ldg(pi + c.z), a3 = __ldg(pi + c.w);
+        acc = fmaf(v.x, a0, acc);
+        acc = fmaf(v.y, a1, acc);
+        acc = fmaf(v.z, a2, acc);
+        acc = fmaf(v.w, a3, acc);
     }
     const double s = block_sum_mixed<BT>(acc, s_red);
     if (threadIdx.x == 0) w[row] = (float)s;
@@ -256,14 +274,14 @@ __global__ void __launch_bounds__(256) k_dose16(const int* __restrict__ rowptr, 
                                                 const uint4* __restrict__ val8, int V, const float* __restrict__ x,
                                                 const float* __restrict__ scale, int N,
                                                 const uint8_t* __restrict__ vstruct,
-                                                const StructTermsD* __restrict__ td, int S, float* __restrict__ z,
+                                                const StructTermsS* __restrict__ ts, int S, float* __restrict__ z,
                                                 float* __restrict__ grad, double* __restrict__ F_part) {
     extern __shared__ float sx[];
-    __shared__ StructTermsD s_td[SMAX];
+    __shared__ StructTermsS s_ts[SMAX];
     __shared__ double s_red[8];
     if (SMEM_X)
         for (int i = threadIdx.x; i < N; i += blockDim.x) sx[i] = x[i] * scale[i];
-    for (int i = threadIdx.x; i < S; i += blockDim.x) s_td[i] = td[i];
+    for (int i = threadIdx.x; i < S; i += blockDim.x) s_ts[i] = ts[i];
     __syncthreads();
     auto xs = [&](unsigned c) -> float { return SMEM_X ? sx[c] : __ldg(x + c) * __ldg(scale + c); };
     const int lane = threadIdx.x & 31;
@@ -272,7 +290,7 @@ __global__ void __launch_bounds__(256) k_dose16(const int* __restrict__ rowptr, 
     const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n_warps = (gridDim.x * blockDim.x) >> 5;
     const int n_tiles = (V + RPW - 1) / RPW;
-    double facc = 0.0;
+    float facc = 0.f;
     for (int t = warp_global; t < n_tiles; t += n_warps) {
         const int row = t * RPW + lane / G;
         float acc = 0.f;
@@ -296,17 +314,17 @@ __global__ void __launch_bounds__(256) k_dose16(const int* __restrict__ rowptr, 
         if (row < V && sub == 0) {
             z[row] = acc;
             if (grad != nullptr || F_part != nullptr) {
-                const StructTermsD tt = s_td[vstruct[row]];
-                const double zd = acc;
-                const double u = fmax(0.0, tt.tu - zd);
-                const double o = fmax(0.0, zd - tt.to);
-                if (grad != nullptr) grad[row] = (float)(2.0 * (tt.b * o - tt.a * u));
-                facc += tt.a * u * u + tt.b * o * o;
+                // FP32 epilogue (FP64 issues at 1/64 of the FP32 rate here)
+                const StructTermsS tt = s_ts[vstruct[row]];
+                const float u = fmaxf((tt.tu_hi - acc) + tt.tu_lo, 0.f);  // T^- - z
+                const float o = fmaxf((acc - tt.to_hi) - tt.to_lo, 0.f);  // z - T^+
+                if (grad != nullptr) grad[row] = 2.f * (tt.b * o - tt.a * u);
+                facc = fmaf(tt.a * u, u, fmaf(tt.b * o, o, facc));
             }
         }
     }
     if (F_part != nullptr) {
-        const double sres = block_sum_f64<256>(facc, s_red);
+        const double sres = block_sum_mixed<256>(facc, s_red);
         if (threadIdx.x == 0) F_part[blockIdx.x] = sres;
     }
 }
@@ -316,11 +334,12 @@ __global__ void __launch_bounds__(256) k_dose16(const int* __restrict__ rowptr, 
 template <int BT, bool BF>
 __global__ void __launch_bounds__(BT) k_dt16(const int* __restrict__ rowptr, const int4* __restrict__ col4,
                                              const uint4* __restrict__ val8, const float* __restrict__ scale, int N,
+                                             const int* __restrict__ order,
                                              const float* __restrict__ pi, float* __restrict__ w,
                                              const int* __restrict__ skip) {
     __shared__ double s_red[BT / 32];
     if (skip != nullptr && *skip) return;
-    const int row = blockIdx.x;
+    const int row = order[blockIdx.x];  // longest rows first
     const int p0 = rowptr[row] >> 3, p1 = rowptr[row + 1] >> 3;
     float acc = 0.f;
     for (int p = p0 + threadIdx.x; p < p1; p += BT) {
@@ -400,33 +419,54 @@ __global__ void __launch_bounds__(256) k_column16_dev(const unsigned short* __re
     column16_body<G, BF>(col, val, seg + (size_t)b * V, seg + (size_t)(b + 1) * V, V, base, smask, out, stride);
 }
 
+// Blocks of a grid-stride kernel that are all resident at once (every block
+// runs the same number of row tiles, so a second wave would double the time),
+// capped at `cap`.
+template <class Kern>
+int resident_grid(Kern kern, size_t smem, int num_sms, int cap) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    return std::min(cap, occ * num_sms);
+}
+
 template <int G, bool BF>
-cudaError_t dose16_g(const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsD* td, int S,
-                     float* z, float* grad, double* F_part, int grid, cudaStream_t stream) {
+cudaError_t dose16_g(const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsS* ts, int S,
+                     float* z, float* grad, double* F_part, int& grid, int num_sms, cudaStream_t stream) {
     const size_t smem = (size_t)D.n_cols * sizeof(float);
+    if (smem <= 48 * 1024)
+        grid = resident_grid(k_dose16<G, BF, true>, smem, num_sms, grid);
+    else
+        grid = resident_grid(k_dose16<G, BF, false>, 0, num_sms, grid);
     if (smem <= 48 * 1024)
         k_dose16<G, BF, true><<<grid, 256, smem, stream>>>(
             D.rowptr, reinterpret_cast<const uint4*>(D.col16), reinterpret_cast<const uint4*>(D.val16), D.n_rows, x,
-            D.scale, D.n_cols, vstruct, td, S, z, grad, F_part);
+            D.scale, D.n_cols, vstruct, ts, S, z, grad, F_part);
     else
         k_dose16<G, BF, false><<<grid, 256, 0, stream>>>(
             D.rowptr, reinterpret_cast<const uint4*>(D.col16), reinterpret_cast<const uint4*>(D.val16), D.n_rows, x,
-            D.scale, D.n_cols, vstruct, td, S, z, grad, F_part);
+            D.scale, D.n_cols, vstruct, ts, S, z, grad, F_part);
     return cudaGetLastError();
 }
 
 template <int G>
-cudaError_t dose_g(const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsD* td, int S,
-                   float* z, float* grad, double* F_part, int grid, cudaStream_t stream) {
+cudaError_t dose_g(const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsS* ts, int S,
+                   float* z, float* grad, double* F_part, int& grid, int num_sms, cudaStream_t stream) {
     const size_t smem = (size_t)D.n_cols * sizeof(float);
+    if (smem <= 48 * 1024)
+        grid = resident_grid(k_dose<G, true>, smem, num_sms, grid);
+    else
+        grid = resident_grid(k_dose<G, false>, 0, num_sms, grid);
     if (smem <= 48 * 1024) {
         k_dose<G, true><<<grid, 256, smem, stream>>>(D.rowptr, reinterpret_cast<const int4*>(D.col),
                                                      reinterpret_cast<const float4*>(D.val), D.n_rows, x,
-                                                     D.n_cols, vstruct, td, S, z, grad, F_part);
+                                                     D.n_cols, vstruct, ts, S, z, grad, F_part);
     } else {
         k_dose<G, false><<<grid, 256, 0, stream>>>(D.rowptr, reinterpret_cast<const int4*>(D.col),
                                                    reinterpret_cast<const float4*>(D.val), D.n_rows, x,
-                                                   D.n_cols, vstruct, td, S, z, grad, F_part);
+                                                   D.n_cols, vstruct, ts, S, z, grad, F_part);
     }
     return cudaGetLastError();
 }
@@ -456,12 +496,12 @@ int dose_lanes(const DevCSR& D) {
 }
 
 template <bool BF>
-cudaError_t dose16_any(int g, const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsD* td,
-                       int S, float* z, float* grad, double* F_part, int grid, cudaStream_t stream) {
+cudaError_t dose16_any(int g, const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsS* ts,
+                       int S, float* z, float* grad, double* F_part, int& grid, int num_sms, cudaStream_t stream) {
     switch (g) {
-        case 4: return dose16_g<4, BF>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
-        case 8: return dose16_g<8, BF>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
-        default: return dose16_g<16, BF>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+        case 4: return dose16_g<4, BF>(D, x, vstruct, ts, S, z, grad, F_part, grid, num_sms, stream);
+        case 8: return dose16_g<8, BF>(D, x, vstruct, ts, S, z, grad, F_part, grid, num_sms, stream);
+        default: return dose16_g<16, BF>(D, x, vstruct, ts, S, z, grad, F_part, grid, num_sms, stream);
     }
 }
 
@@ -470,14 +510,15 @@ void dt_launch(const DevCSR& Dt, const float* pi, float* w, const int* skip, cud
     if (Dt.prec == DAO_PREC_FP16)
         k_dt16<BT, false><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
                                                         reinterpret_cast<const uint4*>(Dt.val16), Dt.scale,
-                                                        Dt.n_rows, pi, w, skip);
+                                                        Dt.n_rows, Dt.order, pi, w, skip);
     else if (Dt.prec == DAO_PREC_BF16)
         k_dt16<BT, true><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
                                                        reinterpret_cast<const uint4*>(Dt.val16), Dt.scale,
-                                                       Dt.n_rows, pi, w, skip);
+                                                       Dt.n_rows, Dt.order, pi, w, skip);
     else
         k_dt<BT><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
-                                                reinterpret_cast<const float4*>(Dt.val), Dt.n_rows, pi, w, skip);
+                                                reinterpret_cast<const float4*>(Dt.val), Dt.n_rows, Dt.order, pi, w,
+                                                skip);
 }
 
 template <int G>
@@ -513,25 +554,25 @@ void column_dev_launch(const DevCSR& D, const int* seg, const int* ap_beam, int 
 }  // namespace
 
 cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsF* tf,
-                        const StructTermsD* td, int S, float* z, float* grad, double* F_part, int F_blocks,
+                        const StructTermsS* ts, int S, float* z, float* grad, double* F_part, int F_blocks,
                         double* F_out, int num_sms, cudaStream_t stream, int* launches) {
     (void)tf;
-    const int grid = dose_grid(D.n_rows, num_sms);
+    int grid = dose_grid(D.n_rows, num_sms);  // at most this many; resident_grid trims it
     if (F_part != nullptr && F_blocks < grid) return cudaErrorInvalidValue;
     const int g = dose_lanes(D);
     cudaError_t e;
     if (D.prec == DAO_PREC_BF16)
-        e = dose16_any<true>(g, D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+        e = dose16_any<true>(g, D, x, vstruct, ts, S, z, grad, F_part, grid, num_sms, stream);
     else if (D.prec == DAO_PREC_FP16)
-        e = dose16_any<false>(g, D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+        e = dose16_any<false>(g, D, x, vstruct, ts, S, z, grad, F_part, grid, num_sms, stream);
     else if (g == 4)
-        e = dose_g<4>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+        e = dose_g<4>(D, x, vstruct, ts, S, z, grad, F_part, grid, num_sms, stream);
     else if (g == 8)
-        e = dose_g<8>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+        e = dose_g<8>(D, x, vstruct, ts, S, z, grad, F_part, grid, num_sms, stream);
     else if (g == 16)
-        e = dose_g<16>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+        e = dose_g<16>(D, x, vstruct, ts, S, z, grad, F_part, grid, num_sms, stream);
     else
-        e = dose_g<32>(D, x, vstruct, td, S, z, grad, F_part, grid, stream);
+        e = dose_g<32>(D, x, vstruct, ts, S, z, grad, F_part, grid, num_sms, stream);
     ++*launches;
     if (e != cudaSuccess || F_part == nullptr || F_out == nullptr) return e;
     k_sum_f64<<<1, 256, 0, stream>>>(F_part, grid, F_out);
@@ -542,10 +583,12 @@ cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct,
 cudaError_t launch_dt(const DevCSR& Dt, const float* pi, float* w, const int* skip, cudaStream_t stream,
                       int* launches) {
     if (Dt.n_rows == 0) return cudaSuccess;
+    // one block per beamlet row; 64 threads by default, so that up to 32 blocks
+    // per SM keep every row resident in one wave
     switch (Dt.tune_dt_threads) {
-        case 64: dt_launch<64>(Dt, pi, w, skip, stream); break;
+        case 128: dt_launch<128>(Dt, pi, w, skip, stream); break;
         case 256: dt_launch<256>(Dt, pi, w, skip, stream); break;
-        default: dt_launch<128>(Dt, pi, w, skip, stream); break;
+        default: dt_launch<64>(Dt, pi, w, skip, stream); break;
     }
     ++*launches;
     return cudaGetLastError();
@@ -582,6 +625,25 @@ cudaError_t launch_column_dev(const DevCSR& D, const int* seg, const int* ap_bea
             break;
     }
     ++*launches;
+    return cudaGetLastError();
+}
+
+namespace {
+// Reads a buffer larger than L2 so that L2 holds only clean lines of it
+// (overwriting it instead would leave dirty lines whose write-back overlaps
+// whatever runs next); `sink` is written only for an impossible sum.
+__global__ void __launch_bounds__(256) k_l2_evict(const float4* __restrict__ buf, size_t n, float* __restrict__ sink) {
+    float a = 0.f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float4 v = buf[i];  // default caching: the lines replace what L2 held
+        a += v.x + v.y + v.z + v.w;
+    }
+    if (a == -1.2345e37f) *sink = a;
+}
+}  // namespace
+
+cudaError_t launch_l2_evict(const void* buf, size_t bytes, float* sink, int num_sms, cudaStream_t stream) {
+    k_l2_evict<<<num_sms * 8, 256, 0, stream>>>(static_cast<const float4*>(buf), bytes / sizeof(float4), sink);
     return cudaGetLastError();
 }
 

@@ -54,10 +54,14 @@ def test_dose_spmv_and_epilogue(torch, name, case):
     err = np.abs(z.astype(np.float64) - ref)
     assert np.all(err <= (n + 6) * U32 * bound + U32 * np.abs(ref)), float(np.max(err / np.maximum(bound, 1e-30)))
     vt = O.voxel_terms(case)
-    gref = O.gradient(z.astype(np.float64), vt)           # epilogue at the kernel's own z
-    assert np.all(np.abs(g - gref) <= 2 * U32 * np.abs(gref) + 1e-45)
+    # epilogue at the kernel's own z, in FP32: T - z from a hi + lo split threshold
+    # (<= u), the weight rounded to FP32 and one product (<= u): |g| within 4u;
+    # each F term within 4u, a lane's FP32 sum of its rows and the warp tree add
+    # (rows per lane + 5) u <= 25 u for these sizes: F within 4e-6 relative
+    gref = O.gradient(z.astype(np.float64), vt)
+    assert np.all(np.abs(g - gref) <= 4 * U32 * np.abs(gref) + 1e-45)
     Fref = O.objective(z.astype(np.float64), vt)
-    assert abs(F - Fref) <= 1e-12 * abs(Fref) + 1e-300
+    assert abs(F - Fref) <= 4e-6 * abs(Fref) + 1e-300
     Fex = O.objective(ref, vt)
     assert abs(F - Fex) <= 1e-5 * abs(Fex) + 1e-300
 
