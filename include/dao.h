@@ -98,11 +98,14 @@ typedef struct dao_options {
     double master_tol;         /* stop when every |y_k - P(y_k - g_k)| <= master_tol * max|g(start)|
                                 * + 64 u sum_j |S_jk pi_j| (u = 2^-24: FP32 rounding of g) (1e-6) */
     double price_tol;          /* optimal when reduced cost >= -price_tol * max(D) * ||grad F(0)||_1 (1e-7) */
-    int32_t precision;         /* DAO_PREC_FP32 (others reserved) */
+    int32_t precision;         /* DAO_PREC_FP32 (default), DAO_PREC_FP16 or DAO_PREC_BF16 storage of D */
     int32_t device;            /* CUDA device ordinal (default 0) */
     void* stream;              /* cudaStream_t to run on; NULL = a stream owned by the context */
-    int32_t use_graphs;        /* 1 (default): dao_solve runs each round as one CUDA graph with the master
-                                * loop as a device-side while node; 0: host-driven launches */
+    int32_t use_graphs;        /* 1 (default): dao_solve runs each round as one CUDA graph; 0: host-driven
+                                * launches */
+    int32_t master_persistent; /* 1 (default): each master solve is one cooperative kernel whose blocks
+                                * iterate together (bounded grid barriers); 0, or where a cooperative
+                                * launch is not available: one launch per evaluation kernel */
 } dao_options;
 
 typedef struct dao_ctx dao_ctx;

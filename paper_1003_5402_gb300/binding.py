@@ -48,7 +48,7 @@ class dao_weights(C.Structure):
 class dao_options(C.Structure):
     _fields_ = [("k_max", C.c_int32), ("max_master_iters", C.c_int32), ("master_tol", C.c_double),
                 ("price_tol", C.c_double), ("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
-                ("use_graphs", C.c_int32)]
+                ("use_graphs", C.c_int32), ("master_persistent", C.c_int32)]
 
 
 class dao_tuning(C.Structure):

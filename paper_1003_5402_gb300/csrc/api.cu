@@ -513,6 +513,10 @@ dao_status alloc_state(dao_ctx* c) {
     DAO_TRY(c->dalloc(&c->price, 1));
     for (int k = 0; k <= KMAX; ++k) c->mb.grid[k] = master_grid(c->V, c->num_sms, k);
     c->mb.GH = master_hess_grid(c->num_sms);
+    DAO_TRY(c->dalloc(&c->mb.bar, 1));
+    DAO_CU(cudaMemsetAsync(c->mb.bar, 0, sizeof(GridBar), c->stream));
+    c->mb.GP = c->opt.master_persistent ? master_persist_grid(c->V, c->num_sms) : 0;
+    if (c->mb.GP > c->mb.GH) c->mb.GP = c->mb.GH;  // the partial arrays have GH columns
     DAO_TRY(c->dalloc(&c->mb.st, 1));
     DAO_TRY(c->dalloc(&c->mb.act_rows, (size_t)c->ld * KROW));
     DAO_TRY(c->dalloc(&c->mb.act_hp, (size_t)c->ld));
@@ -552,12 +556,29 @@ dao_status refresh_state(dao_ctx* c) {
 }
 
 dao_status master_solve(dao_ctx* c, double* F_out) {
-    DAO_CU(launch_master_init(c->mb.st, c->K, nullptr, 0, 0, c->stream, &c->launches_i));
+    DAO_CU(launch_master_init(c->mb.st, c->K, nullptr, 0, 0, c->stream, &c->launches_i, c->mb.bar));
+    const size_t tail = sizeof(MasterDev) - offsetof(MasterDev, F);
+    MasterDev* shadow = reinterpret_cast<MasterDev*>(c->pinned + c->off_master - offsetof(MasterDev, F));
+    if (c->mb.GP > 0) {  // the whole solve as one cooperative launch
+        c->prof_begin(DAO_KC_MASTER_PASS);
+        DAO_CU(launch_master_persist(c->mb, c->slab, c->ld, c->V, c->K, c->vstruct, c->tf, c->S,
+                                     c->opt.max_master_iters, c->opt.master_tol, nullptr, c->stream, &c->launches_i));
+        c->prof_end();
+        DAO_CU(cudaMemcpyAsync(&shadow->F, &c->mb.st->F, tail, cudaMemcpyDeviceToHost, c->stream));
+        DAO_TRY(sync(c));
+        DAO_TRY(refresh_state(c));
+        if (shadow->err == 2) return fail(DAO_ETIMEOUT, "a grid barrier of the master solve timed out");
+        if (shadow->status == MASTER_ERROR) return fail(DAO_ETIMEOUT, "the master solve stopped on an error");
+        if (!shadow->done) return fail(DAO_ETIMEOUT, "master problem did not stop");
+        c->stat_evals.push_back(shadow->n_eval);
+        c->stat_status.push_back(shadow->status);
+        c->stat_kkt.push_back(shadow->res / (shadow->tol > 0 ? shadow->tol / c->opt.master_tol : 1.0));
+        if (F_out) *F_out = shadow->F;
+        return DAO_OK;
+    }
     const int unroll = 4;
     const int max_passes = c->opt.max_master_iters + 80;
     int passes = 0;
-    const size_t tail = sizeof(MasterDev) - offsetof(MasterDev, F);
-    MasterDev* shadow = reinterpret_cast<MasterDev*>(c->pinned + c->off_master - offsetof(MasterDev, F));
     for (;;) {
         for (int u = 0; u < unroll; ++u) {
             c->prof_begin(DAO_KC_MASTER_PASS);
@@ -678,7 +699,49 @@ dao_status add_aperture(dao_ctx* c, int beam, const int32_t* lr, double* F) {
 // while node whose body is one evaluation, and the final pass.  Every node
 // becomes a no-op once an earlier round has stopped the solve, so rounds can be
 // queued without waiting on the host.
+// Persistent variant: one captured sequence, the master solve one cooperative
+// kernel node.
+dao_status build_round_graph_persist(dao_ctx* c, int K) {
+    cudaStream_t cs = c->stream;
+    int n = 0;
+    const int* skip = &c->cg->done;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    auto check = [&](cudaError_t x) {
+        if (e == cudaSuccess && x != cudaSuccess) e = x;
+    };
+    if (e == cudaSuccess) {
+        check(launch_dt(c->Dt, c->pi, c->w, skip, cs, &n));
+        check(launch_price(c->w, c->row_info, c->R_tot, c->beam_row0_d, c->B, c->row_v, c->row_lr, c->price, skip, cs,
+                           &n));
+        check(launch_commit(c->price, c->row_lr, c->beam_row0_d, c->rows_d, c->cols_d, c->tau, K, 2 * c->max_rows,
+                            c->ap_beam, c->ap_lr, c->mask, c->cg, cs, &n));
+        check(launch_column_dev(c->D, c->seg, c->ap_beam, K, c->beam_off_d, c->rows_d, c->cols_d, c->max_nb, c->mask,
+                                c->slab + (size_t)(K - 1) * c->ld, 1, c->cg, c->num_sms, cs, &n));
+        check(launch_master_init(c->mb.st, K, skip, 0, 0, cs, &n, c->mb.bar));
+        check(launch_master_persist(c->mb, c->slab, c->ld, c->V, K, c->vstruct, c->tf, c->S, c->opt.max_master_iters,
+                                    c->opt.master_tol, skip, cs, &n));
+        check(launch_master_eval(c->mb, c->V, K, c->vstruct, c->tf, c->S, c->z, c->pi, PASS_FINAL, skip, cs, &n));
+        check(launch_cg_record(c->mb.st, c->cg, K, cs, &n));
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = e2;
+        cudaGraphExec_t ex = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return fail(DAO_ECUDA, std::string("building the round graph: ") + cudaGetErrorString(e));
+        }
+        c->round_graph[K] = g;
+        c->round_exec[K] = ex;
+        return DAO_OK;
+    }
+    cudaGetLastError();
+    return fail(DAO_ECUDA, std::string("building the round graph: ") + cudaGetErrorString(e));
+}
+
 dao_status build_round_graph(dao_ctx* c, int K) {
+    if (c->mb.GP > 0) return build_round_graph_persist(c, K);
     cudaGraph_t g = nullptr;
     DAO_CU(cudaGraphCreate(&g, 0));
     cudaStream_t cs = c->stream;
@@ -807,9 +870,10 @@ dao_status solve_graph_end(dao_ctx* c, const GraphSolve& gs, int n_apertures, in
     }
     // kernels the graphs ran: 8 per round plus pass, curvature and reduce + step per evaluation,
     // launched in pairs of evaluations
-    c->launches_i += 8 * (K - K0) + (K < K1 ? 5 : 0);
+    const bool persist = c->mb.GP > 0;
+    c->launches_i += (persist ? 9 : 8) * (K - K0) + (K < K1 ? (persist ? 6 : 5) : 0);
     for (int k = K0; k < K; ++k) {
-        c->launches_i += 6 * ((h->evals[k] + 1) / 2);  // two evaluations per while iteration
+        if (!persist) c->launches_i += 6 * ((h->evals[k] + 1) / 2);  // two evaluations per while iteration
         c->stat_evals.push_back(h->evals[k]);
         c->stat_status.push_back(h->status[k]);
         c->stat_kkt.push_back(h->res[k] / (h->tol[k] > 0 ? h->tol[k] / c->opt.master_tol : 1.0));
@@ -904,6 +968,7 @@ void dao_options_default(dao_options* opt) {
     opt->device = 0;
     opt->stream = nullptr;
     opt->use_graphs = 1;
+    opt->master_persistent = 1;
 }
 
 const char* dao_last_error(void) { return g_err.c_str(); }

@@ -151,6 +151,14 @@ cudaError_t launch_commit(const PriceDev* pr, const int2* row_lr, const int* bea
                           float* mask, CGDev* cg, cudaStream_t stream, int* launches);
 
 // a5: projected-Newton master problem kernels.
+// Counters of the grid barrier of the persistent master solve (zeroed memory;
+// count returns to 0 after every barrier, gen only increases).
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+    unsigned pad[2];
+};
+
 struct MasterBuffers {
     MasterDev* st = nullptr;
     float* act_rows = nullptr;  // [n_tiles * MASTER_TILE][KROW]: rows of the active voxels, per tile slot
@@ -162,6 +170,8 @@ struct MasterBuffers {
     float* gn_part = nullptr;   // [KMAX][GH]
     double* F_part = nullptr;   // [max evaluation grid]
     int GH = 0;                 // blocks of the curvature kernel
+    GridBar* bar = nullptr;     // grid barrier of the persistent solve
+    int GP = 0;                 // blocks of the persistent solve (co-resident), 0: not available
     int grid[KMAX + 1] = {};    // blocks of the evaluation kernel for each pool size
     CUtensorMap tmap[KMAX / 4 + 1];  // slab tile maps, indexed by columns / 4
 };
@@ -176,7 +186,7 @@ cudaError_t master_configure();
 // skip (nullable): device flag that turns the launch into a no-op (graph path).
 // cond / use_cond: while-node handle the step kernel sets to "not done".
 cudaError_t launch_master_init(MasterDev* st, int K, const int* skip, cudaGraphConditionalHandle cond,
-                               int use_cond, cudaStream_t stream, int* launches);
+                               int use_cond, cudaStream_t stream, int* launches, GridBar* gb = nullptr);
 cudaError_t launch_master_eval(const MasterBuffers& mb, int V, int K, const uint8_t* vstruct,
                                const StructTermsF* tf, int S, float* z_out, float* pi_out, int mode,
                                const int* skip, cudaStream_t stream, int* launches);
@@ -196,6 +206,14 @@ cudaError_t build_transpose_count(const int64_t* rp, const int* col, int V, int 
 cudaError_t build_transpose_place(int prec, const int64_t* rp, const int* col, const float* val, int V, int CH, int N,
                                   int n_ch, int* C, const int* cnt, const float* scale, DevCSR& Dt, float* tval,
                                   cudaStream_t s);
+
+// The whole master solve as one cooperative launch (GP blocks), after
+// launch_master_init; dynamic shared memory per master_persist_smem.
+size_t master_persist_smem(int V, int G);
+int master_persist_grid(int V, int num_sms);
+cudaError_t launch_master_persist(const MasterBuffers& mb, const float* slab, int ld, int V, int K,
+                                  const uint8_t* vstruct, const StructTermsF* tf, int S, int max_iter, double tol_rel,
+                                  const int* skip, cudaStream_t stream, int* launches);
 
 // Reduction of the partial sums and the projected-Newton step, one launch.
 cudaError_t launch_master_step(int K, const MasterBuffers& mb, int max_iter, double tol_rel,

@@ -121,8 +121,9 @@ __device__ __forceinline__ void block_of(int eb, int KB, int& rb, int& cb) {
 __device__ __forceinline__ int tri_index(int r, int c, int K) { return r * K - (r * (r - 1)) / 2 + (c - r); }
 
 __global__ void k_master_init(MasterDev* __restrict__ st, int K, const int* __restrict__ skip,
-                              cudaGraphConditionalHandle cond, int use_cond) {
+                              cudaGraphConditionalHandle cond, int use_cond, GridBar* __restrict__ gb) {
     const int t = threadIdx.x;
+    if (t == 0 && gb != nullptr) gb->count = 0;  // a barrier left by an aborted solve starts empty
     if (skip != nullptr && *skip) {  // the solve stopped before this round: nothing to iterate
         if (t == 0) {
             st->done = 1;
@@ -535,10 +536,13 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     // are read through L2 (__ldcg), never from a possibly stale L1 line
     const int k = threadIdx.x;
     const int kk = k < KMAX ? k : KMAX - 1;
-    const int done = st->done, err = st->err, K = st->K, phase = st->phase, iter0 = st->iter;
-    const double tol0 = st->tol, F0 = st->F, Ft = __ldcg(&st->Ft);
-    const double yt_ = st->yt[kk], gt_ = __ldcg(&st->gt[kk]), gn_ = (double)__ldcg(&st->gn[kk]);
-    const double y_ = st->y[kk], g_ = st->g[kk];
+    // (all through L2: a persistent solve runs the step in whichever block
+    // finishes last, so no L1 line of another iteration may be trusted)
+    const int done = __ldcg(&st->done), err = __ldcg(&st->err), K = __ldcg(&st->K), phase = __ldcg(&st->phase);
+    const int iter0 = __ldcg(&st->iter);
+    const double tol0 = __ldcg(&st->tol), F0 = __ldcg(&st->F), Ft = __ldcg(&st->Ft);
+    const double yt_ = __ldcg(&st->yt[kk]), gt_ = __ldcg(&st->gt[kk]), gn_ = (double)__ldcg(&st->gn[kk]);
+    const double y_ = __ldcg(&st->y[kk]), g_ = __ldcg(&st->g[kk]);
     if (done) return;
     if (err) {  // a tile copy was lost in an evaluation: stop with the last accepted point
         if (threadIdx.x == 0) {
@@ -599,7 +603,7 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     }
     const bool cap = iter0 >= max_iter + 64;
     const bool accept = !cap && (phase == 0 || !viol || Ft <= F0 + sigma * dec);
-    if (k == 0) ++st->n_eval;
+    if (k == 0) st->n_eval = __ldcg(&st->n_eval) + 1;
     if (cap) {
         if (k == 0) {
             st->status = MASTER_MAXITER;
@@ -608,7 +612,7 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
         return;
     }
     if (!accept) {
-        const double alpha = st->alpha * 0.5;
+        const double alpha = __ldcg(&st->alpha) * 0.5;
         if (alpha < 9.3e-10) {  // 2^-30: the line search found no decrease
             if (k == 0) {
                 st->status = MASTER_STALLED;
@@ -616,10 +620,10 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
             }
             return;
         }
-        if (own) st->yt[k] = fmax(y + alpha * st->d[k], 0.0);
+        if (own) st->yt[k] = fmax(y + alpha * __ldcg(&st->d[k]), 0.0);
         if (k == 0) {
             st->alpha = alpha;
-            st->iter += 1;
+            st->iter = iter0 + 1;
             st->phase = 1;
         }
         return;
@@ -687,7 +691,7 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
             const int i = ti + 16 * a, q = tq + 16 * b;
             Hr[a][b] = (i < nf && q <= i) ? __ldcg(&st->Ht[fidx[i] * KMAX + fidx[q]]) : 0.f;
         }
-    const float bk = k < nf ? -(float)st->g[fidx[k]] : 0.f;
+    const float bk = k < nf ? -(float)__ldcg(&st->g[fidx[k]]) : 0.f;
     float dg = 0.f;
 #pragma unroll
     for (int a = 0; a < 4; ++a) dg = fmaxf(dg, (ti == tq) ? Hr[a][a] : 0.f);
@@ -828,7 +832,7 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     }
     if (k == 0) {
         st->alpha = 1.0;
-        st->iter += 1;
+        st->iter = iter0 + 1;
         st->phase = 1;
     }
 }
@@ -861,6 +865,291 @@ __global__ void __launch_bounds__(STEP_T) k_master_reduce_step(const float* __re
     if (threadIdx.x == 0) st->ticket = 0;
     master_step_body(st, max_iter, tol_rel, sigma);
     if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
+}
+
+// ---- the master solve as one persistent cooperative kernel -------------------
+// All blocks are co-resident (cooperative launch).  Block b owns the 32-voxel
+// tiles b, b + G, b + 2G, ... of the slab (interleaved, so the active voxels of
+// a compact target spread evenly over the blocks).  Per Newton iteration:
+//   A. warp w of every block streams its tiles' slab columns from L2 (lane v =
+//      voxel v of the tile) into the compensated z, then pi, h, F; the active
+//      voxels (h > 0) go to the warp's list; the block accumulates its partial
+//      H, g and the rounding scale of g over its lists (rows re-read from L2 in
+//      chunks of CHP) and writes them to column b of the partial arrays;
+//   grid barrier;
+//   B. every block reduces its share of the outputs in a fixed order; the block
+//      that finishes last (ticket after a fence) takes the Newton step;
+//   grid barrier; stop when the step marked the solve done.
+// Every barrier wait is bounded: after GRID_WAIT_LIMIT polls the block reports
+// st->err = 2 and every block leaves at the next barrier or check.
+constexpr int PT = STEP_T;         // threads per block (the step body's layout)
+constexpr int PW = PT / 32;
+constexpr int CHP = 64;            // active voxels per H chunk
+constexpr int GRID_WAIT_LIMIT = 1 << 22;
+constexpr size_t PERSIST_SMEM_MAX = 150 * 1024;  // dynamic shared memory the kernel is configured for
+
+__device__ __forceinline__ bool grid_sync(GridBar* gb, unsigned nblocks, int* s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned g = *reinterpret_cast<volatile unsigned*>(&gb->gen);
+        __threadfence();
+        const unsigned arrived = atomicAdd(&gb->count, 1u) + 1u;
+        int ok = 1;
+        if (arrived == nblocks) {
+            atomicExch(&gb->count, 0u);
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        } else {
+            int i = 0;
+            while (*reinterpret_cast<volatile unsigned*>(&gb->gen) == g && ++i < GRID_WAIT_LIMIT) __nanosleep(64);
+            ok = i < GRID_WAIT_LIMIT;
+        }
+        __threadfence();
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+__global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restrict__ slab, int ld, int V, int K, int KP,
+                                                       int KW, int NV, int capw, MasterDev* __restrict__ st,
+                                                       GridBar* __restrict__ gb, float* __restrict__ H_part,
+                                                       double* __restrict__ g_part, float* __restrict__ gn_part,
+                                                       double* __restrict__ F_part, int GS,
+                                                       const uint8_t* __restrict__ vstruct,
+                                                       const StructTermsF* __restrict__ tf, int S, int max_iter,
+                                                       double tol_rel, double sigma, const int* __restrict__ skip) {
+    extern __shared__ __align__(16) float pm[];
+    int* s_act = reinterpret_cast<int*>(pm);          // [PW][capw] voxel indices
+    float* s_hv = pm + PW * capw;                     // [PW][capw] h
+    float* s_pv = s_hv + PW * capw;                   // [PW][capw] pi
+    float* Ac = s_pv + ((PW * capw + 3) / 4) * 4;     // [CHP][KW]
+    float* s_ch = Ac + CHP * KW;                      // [CHP] h of the chunk
+    float* s_cp = s_ch + CHP;                         // [CHP] pi of the chunk
+    __shared__ float s_yh[KMAX], s_yl[KMAX];
+    __shared__ StructTermsF s_tf[SMAX];
+    __shared__ int s_wn[PW];
+    __shared__ float s_red[PW];
+    __shared__ float s_scr[8 * 24];
+    __shared__ int s_flag, s_last, s_stop;
+    if (skip != nullptr && *skip) return;  // the same for every block
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x;
+    for (int i = tid; i < S; i += PT) s_tf[i] = tf[i];
+    const int KB = KP / 4;
+    const int nb = KB * (KB + 1) / 2;
+    const int nq = KP / 4;
+    int rb = -1, cb = -1;
+    const int vl = tid % NV;
+    if (tid < nb * NV) block_of(tid / NV, KB, rb, cb);
+    const int n32 = (V + 31) / 32;
+    const int tiles_b = blockIdx.x < n32 ? (n32 - 1 - (int)blockIdx.x) / G + 1 : 0;
+    for (;;) {
+        if (tid == 0) s_stop = __ldcg(&st->done) | __ldcg(&st->err);
+        if (tid < KMAX) {
+            const double yv = tid < K ? __ldcg(&st->yt[tid]) : 0.0;
+            const float hi = (float)yv;
+            s_yh[tid] = hi;
+            s_yl[tid] = (float)(yv - (double)hi);
+        }
+        __syncthreads();
+        if (s_stop) break;
+        // ---- A. z, pi, h, F over this block's tiles; active voxels per warp
+        float facc = 0.f;
+        int na = 0;
+        for (int i = warp; i < tiles_b; i += PW) {
+            const int j = (blockIdx.x + i * G) * 32 + lane;
+            const bool in = j < V;
+            float sc[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
+            const float* col = slab + (in ? j : 0);
+            // PB columns in flight per lane (one coalesced 128-byte row each), then
+            // their four compensated chains; columns K..KP-1 are zero and meet y = 0
+            constexpr int PB = 16;
+            for (int k0 = 0; k0 < KP; k0 += PB) {
+                float a[PB];
+#pragma unroll
+                for (int q = 0; q < PB; ++q) a[q] = k0 + q < KP ? __ldcg(col + (size_t)(k0 + q) * ld) : 0.f;
+#pragma unroll
+                for (int q = 0; q < PB; q += 4) {
+                    dot2_step(sc[0], cc[0], a[q], s_yh[k0 + q], s_yl[k0 + q]);
+                    dot2_step(sc[1], cc[1], a[q + 1], s_yh[k0 + q + 1], s_yl[k0 + q + 1]);
+                    dot2_step(sc[2], cc[2], a[q + 2], s_yh[k0 + q + 2], s_yl[k0 + q + 2]);
+                    dot2_step(sc[3], cc[3], a[q + 3], s_yh[k0 + q + 3], s_yl[k0 + q + 3]);
+                }
+            }
+            float s = sc[0], c = cc[0];
+#pragma unroll
+            for (int q = 1; q < 4; ++q) {
+                const float t2 = s + sc[q];
+                const float bb = t2 - s;
+                const float e = (s - (t2 - bb)) + (sc[q] - bb);
+                s = t2;
+                c += e + cc[q];
+            }
+            float h = 0.f, p = 0.f;
+            if (in) {
+                const StructTermsF t = s_tf[vstruct[j]];
+                const float du = (t.tu - s) - c;
+                const float dov = (s - t.to) + c;
+                const float u = fmaxf(du, 0.f), o = fmaxf(dov, 0.f);
+                p = 2.f * (t.b * o - t.a * u);
+                h = 2.f * ((du > 0.f ? t.a : 0.f) + (dov > 0.f ? t.b : 0.f));
+                facc = fmaf(t.a * u, u, fmaf(t.b * o, o, facc));
+            }
+            const bool act = h > 0.f;
+            const unsigned bal = __ballot_sync(FULL, act);
+            if (act) {
+                const int slot = warp * capw + na + __popc(bal & ((1u << lane) - 1u));
+                s_act[slot] = j;
+                s_hv[slot] = h;
+                s_pv[slot] = p;
+            }
+            na += __popc(bal);
+        }
+        if (lane == 0) s_wn[warp] = na;
+        const float fw = warp_sum_f32(facc);
+        if (lane == 0) s_red[warp] = fw;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < PW; ++w) t += (double)s_red[w];
+            F_part[blockIdx.x] = t;
+        }
+        int total = 0;
+#pragma unroll
+        for (int w = 0; w < PW; ++w) total += s_wn[w];
+        // ---- the block's partial H, g and scale of g over its active lists
+        float hs[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) hs[q] = 0.f;
+        float gs[4] = {0.f, 0.f, 0.f, 0.f}, gns[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int c0 = 0; c0 < total; c0 += CHP) {
+            const int n = min(CHP, total - c0);
+            {   // list entry c0 + i (warp lists in order) as row i of Ac
+                const int i = tid & (CHP - 1);
+                if (i < n) {
+                    int m = c0 + i, w = 0;
+                    while (m >= s_wn[w]) {
+                        m -= s_wn[w];
+                        ++w;
+                    }
+                    const int slot = w * capw + m;
+                    const int j = s_act[slot];
+                    if (tid < CHP) {
+                        s_ch[i] = s_hv[slot];
+                        s_cp[i] = s_pv[slot];
+                    }
+                    for (int q = tid / CHP; q < nq; q += PT / CHP)
+                        *reinterpret_cast<float4*>(Ac + i * KW + 4 * q) =
+                            make_float4(__ldcg(slab + (size_t)(4 * q) * ld + j),
+                                        __ldcg(slab + (size_t)(4 * q + 1) * ld + j),
+                                        __ldcg(slab + (size_t)(4 * q + 2) * ld + j),
+                                        __ldcg(slab + (size_t)(4 * q + 3) * ld + j));
+                }
+            }
+            __syncthreads();
+            if (rb >= 0) {
+                for (int i = vl; i < n; i += NV) {
+                    const float4 ra = *reinterpret_cast<const float4*>(Ac + i * KW + 4 * rb);
+                    const float4 rc = *reinterpret_cast<const float4*>(Ac + i * KW + 4 * cb);
+                    const float hv = s_ch[i];
+                    const float a0 = ra.x * hv, a1 = ra.y * hv, a2 = ra.z * hv, a3 = ra.w * hv;
+                    hs[0] = fmaf(a0, rc.x, hs[0]);
+                    hs[1] = fmaf(a0, rc.y, hs[1]);
+                    hs[2] = fmaf(a0, rc.z, hs[2]);
+                    hs[3] = fmaf(a0, rc.w, hs[3]);
+                    hs[4] = fmaf(a1, rc.x, hs[4]);
+                    hs[5] = fmaf(a1, rc.y, hs[5]);
+                    hs[6] = fmaf(a1, rc.z, hs[6]);
+                    hs[7] = fmaf(a1, rc.w, hs[7]);
+                    hs[8] = fmaf(a2, rc.x, hs[8]);
+                    hs[9] = fmaf(a2, rc.y, hs[9]);
+                    hs[10] = fmaf(a2, rc.z, hs[10]);
+                    hs[11] = fmaf(a2, rc.w, hs[11]);
+                    hs[12] = fmaf(a3, rc.x, hs[12]);
+                    hs[13] = fmaf(a3, rc.y, hs[13]);
+                    hs[14] = fmaf(a3, rc.z, hs[14]);
+                    hs[15] = fmaf(a3, rc.w, hs[15]);
+                    if (rb == cb) {
+                        const float pv = s_cp[i], pa = fabsf(pv);
+                        gs[0] = fmaf(ra.x, pv, gs[0]);
+                        gs[1] = fmaf(ra.y, pv, gs[1]);
+                        gs[2] = fmaf(ra.z, pv, gs[2]);
+                        gs[3] = fmaf(ra.w, pv, gs[3]);
+                        gns[0] = fmaf(fabsf(ra.x), pa, gns[0]);
+                        gns[1] = fmaf(fabsf(ra.y), pa, gns[1]);
+                        gns[2] = fmaf(fabsf(ra.z), pa, gns[2]);
+                        gns[3] = fmaf(fabsf(ra.w), pa, gns[3]);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        float vals[24];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) vals[q] = hs[q];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            vals[16 + q] = gs[q];
+            vals[20 + q] = gns[q];
+        }
+        const int span = NV < 32 ? NV : 32;
+        for (int o = span / 2; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 24; ++q) vals[q] += __shfl_xor_sync(FULL, vals[q], o);
+        if (NV > 32 && lane == 0)
+#pragma unroll
+            for (int q = 0; q < 24; ++q) s_scr[warp * 24 + q] = vals[q];
+        __syncthreads();
+        if ((tid % NV) == 0 && tid < nb * NV) {
+            if (NV > 32) {
+                const int w0 = tid >> 5, nw = NV >> 5;
+#pragma unroll
+                for (int q = 0; q < 24; ++q) {
+                    float t = 0.f;
+                    for (int w = 0; w < nw; ++w) t += s_scr[(w0 + w) * 24 + q];
+                    vals[q] = t;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int r = 4 * rb + q, cl = 4 * cb + e;
+                    if (r < K && cl < K && r <= cl) H_part[(size_t)tri_index(r, cl, K) * GS + blockIdx.x] = vals[q * 4 + e];
+                }
+            if (rb == cb) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int r = 4 * rb + q;
+                    if (r < K) {
+                        g_part[(size_t)r * GS + blockIdx.x] = (double)vals[16 + q];
+                        gn_part[(size_t)r * GS + blockIdx.x] = vals[20 + q];
+                    }
+                }
+            }
+        }
+        if (!grid_sync(gb, G, &s_flag)) {
+            if (tid == 0) st->err = 2;
+            break;
+        }
+        // ---- B. reduction by every block, the step by the last one to finish
+        master_reduce_part(H_part, g_part, gn_part, F_part, GS, G, K, st);
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) s_last = atomicAdd(&st->ticket, 1u) == (unsigned)G - 1u;
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            if (tid == 0) st->ticket = 0;
+            master_step_body(st, max_iter, tol_rel, sigma);
+            __threadfence();
+        }
+        if (!grid_sync(gb, G, &s_flag)) {
+            if (tid == 0) st->err = 2;
+            break;
+        }
+    }
 }
 
 }  // namespace
@@ -912,12 +1201,14 @@ cudaError_t master_configure() {
     cudaError_t e = cudaFuncSetAttribute(k_master_eval, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)master_eval_smem(KMAX));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_master_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PERSIST_SMEM_MAX);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_master_hess, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 cudaError_t launch_master_init(MasterDev* st, int K, const int* skip, cudaGraphConditionalHandle cond,
-                               int use_cond, cudaStream_t stream, int* launches) {
-    k_master_init<<<1, KMAX, 0, stream>>>(st, K, skip, cond, use_cond);
+                               int use_cond, cudaStream_t stream, int* launches, GridBar* gb) {
+    k_master_init<<<1, KMAX, 0, stream>>>(st, K, skip, cond, use_cond, gb);
     ++*launches;
     return cudaGetLastError();
 }
@@ -949,6 +1240,72 @@ cudaError_t launch_master_step(int K, const MasterBuffers& mb, int max_iter, dou
         use_cond);
     ++*launches;
     return cudaGetLastError();
+}
+
+size_t master_persist_smem(int V, int G) {
+    const int n32 = (V + 31) / 32;
+    const int tiles = G > 0 ? (n32 + G - 1) / G : n32;
+    const int capw = (tiles + PW - 1) / PW * 32;
+    return (size_t)PW * capw * sizeof(int) + (size_t)(PW * capw * 2 + 3) / 4 * 4 * sizeof(float) +
+           (size_t)CHP * master_kw(KMAX) * sizeof(float) + 2 * CHP * sizeof(float);
+}
+
+// Co-resident blocks of the persistent solve: 2 per SM when they fit, else 1;
+// 0 when a cooperative launch is not possible.
+int master_persist_grid(int V, int num_sms) {
+    int dev = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
+        cudaGetLastError();
+        return 0;
+    }
+    for (int per = 2; per >= 1; --per) {
+        const int G = per * num_sms;
+        const size_t smem = master_persist_smem(V, G);
+        if (smem > PERSIST_SMEM_MAX) continue;
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_master_persist, PT, smem) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (occ >= per) return G;
+    }
+    return 0;
+}
+
+cudaError_t launch_master_persist(const MasterBuffers& mb, const float* slab, int ld, int V, int K,
+                                  const uint8_t* vstruct, const StructTermsF* tf, int S, int max_iter, double tol_rel,
+                                  const int* skip, cudaStream_t stream, int* launches) {
+    const int G = mb.GP;
+    if (G < 1) return cudaErrorInvalidConfiguration;
+    const int KP = (K + 3) / 4 * 4;
+    const int n32 = (V + 31) / 32;
+    const int capw = ((n32 + G - 1) / G + PW - 1) / PW * 32;
+    int KW = master_kw(K), NV = master_lanes(K), GS = mb.GH;  // partial arrays: stride GH >= G
+    double sigma = 1e-4;
+    MasterDev* st = mb.st;
+    GridBar* gb = mb.bar;
+    float* H_part = mb.H_part;
+    double* g_part = mb.g_part;
+    float* gn_part = mb.gn_part;
+    double* F_part = mb.F_part;
+    void* args[] = {(void*)&slab, (void*)&ld, (void*)&V, (void*)&K, (void*)&KP, (void*)&KW, (void*)&NV,
+                    (void*)&capw, (void*)&st, (void*)&gb, (void*)&H_part, (void*)&g_part, (void*)&gn_part,
+                    (void*)&F_part, (void*)&GS, (void*)&vstruct, (void*)&tf, (void*)&S, (void*)&max_iter,
+                    (void*)&tol_rel, (void*)&sigma, (void*)&skip};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(PT);
+    cfg.dynamicSmemBytes = master_persist_smem(V, G);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)k_master_persist, args);
+    ++*launches;
+    return e;
 }
 
 cudaError_t launch_cg_record(const MasterDev* st, CGDev* cg, int K, cudaStream_t stream, int* launches) {

@@ -86,10 +86,13 @@ def ref_z_before(ref, steps, k, case):
     return steps[k - 1][1].z
 
 
+@pytest.mark.parametrize("persistent", [1, 0])
 @pytest.mark.parametrize("name,K", [("micro", 12), ("tiny", 20)])
-def test_teacher_forced_parity(torch, name, K):
+def test_teacher_forced_parity(torch, name, K, persistent):
+    """Both master implementations: one persistent cooperative kernel per solve,
+    and one launch per evaluation kernel."""
     case = P.make_case(P.CONFIGS[name]())
-    r = _teacher_forced(case, K, torch)
+    r = _teacher_forced(case, K, torch, plan_kw={"master_persistent": persistent})
     Fg, Fr = np.array(r["F_gpu"]), np.array(r["F_ref"])
     rel = np.abs(Fg - Fr) / np.abs(Fr)
     assert np.all(rel <= RTOL_F), rel
@@ -128,9 +131,10 @@ def test_free_running_matches_oracle(torch, name, K):
     assert trace[-1] <= ref.objective[-1] * (1 + 1e-3)
 
 
-def test_master_kkt_on_gpu_solution(torch):
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_master_kkt_on_gpu_solution(torch, persistent):
     case = P.make_case(P.spec_tiny())
-    with _plan(case, torch) as plan:
+    with _plan(case, torch, master_persistent=persistent) as plan:
         plan.solve(15)
         aps = plan.apertures()
         y = plan.intensities()
@@ -218,14 +222,16 @@ def test_prostate_full_size_properties(torch):
     assert np.all(np.abs(trace[:5] - ref.objective) <= RTOL_F * np.array(ref.objective))
 
 
+@pytest.mark.parametrize("persistent", [1, 0])
 @pytest.mark.parametrize("name,K", [("micro", 30), ("tiny", 20)])
-def test_graph_rounds_equal_host_driven_rounds(torch, name, K):
-    """dao_solve as CUDA graphs (device-side while loop, no host synchronisation
-    between rounds) gives bit-identical results to host-driven launches."""
+def test_graph_rounds_equal_host_driven_rounds(torch, name, K, persistent):
+    """dao_solve as CUDA graphs (no host synchronisation between rounds) gives
+    bit-identical results to host-driven launches, for both master
+    implementations."""
     case = P.make_case(P.CONFIGS[name]())
     out = []
     for g in (1, 0):
-        with _plan(case, torch, use_graphs=g) as plan:
+        with _plan(case, torch, use_graphs=g, master_persistent=persistent) as plan:
             st, n, trace = plan.solve(K)
             aps = plan.apertures()
             y = plan.intensities()
