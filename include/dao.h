@@ -223,7 +223,8 @@ enum {
     DAO_KC_MASTER_STEP = 6,    /* a5 partial reduction + Newton step / line search control */
     DAO_KC_MASTER_HESS = 7,    /* a5 curvature matrix and gradient over the active voxels */
     DAO_KC_OTHER = 8,
-    DAO_KC_COUNT = 9
+    DAO_KC_MASTER_SOLVE = 9,   /* a5 the whole master solve as one persistent kernel */
+    DAO_KC_COUNT = 10
 };
 dao_status dao_profile_enable(dao_ctx* ctx, int32_t enable);
 /* launches, summed device milliseconds and the kernel launches counted for

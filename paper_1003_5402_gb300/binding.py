@@ -20,7 +20,7 @@ DAO_OK, DAO_OPTIMAL, DAO_DUPLICATE = 0, 1, 2
 DAO_EINVAL, DAO_ENOMEM, DAO_ECUDA, DAO_ETIMEOUT, DAO_EBUSY, DAO_ESTATE = -1, -2, -3, -4, -5, -6
 DAO_PREC_FP32, DAO_PREC_FP16, DAO_PREC_BF16 = 0, 1, 2
 KC = {"dose": 0, "dt": 1, "price": 2, "column": 3, "master_pass": 4, "master_reduce": 5, "master_step": 6,
-      "master_hess": 7, "other": 8}
+      "master_hess": 7, "other": 8, "master_solve": 9}
 
 # every function declared in include/dao.h, with (restype, argtypes)
 _P = C.c_void_p

@@ -560,7 +560,7 @@ dao_status master_solve(dao_ctx* c, double* F_out) {
     const size_t tail = sizeof(MasterDev) - offsetof(MasterDev, F);
     MasterDev* shadow = reinterpret_cast<MasterDev*>(c->pinned + c->off_master - offsetof(MasterDev, F));
     if (c->mb.GP > 0) {  // the whole solve as one cooperative launch
-        c->prof_begin(DAO_KC_MASTER_PASS);
+        c->prof_begin(DAO_KC_MASTER_SOLVE);
         DAO_CU(launch_master_persist(c->mb, c->slab, c->ld, c->V, c->K, c->vstruct, c->tf, c->S,
                                      c->opt.max_master_iters, c->opt.master_tol, nullptr, c->stream, &c->launches_i));
         c->prof_end();

@@ -9,7 +9,9 @@ then times ``--reps`` launches of ``--kernel`` at pool size ``--pool`` with
 dao_k_time (the launches captured into one CUDA graph, one warm replay, one
 timed replay).  The printed ``launches_before`` of the kernel class plus
 ``--reps`` (the warm replay) is the number of launches of that kernel to skip
-when a profiler should see exactly the timed launches.
+when a profiler should see exactly the timed launches.  ``--kernel
+master_solve`` reports the plan's own persistent master launches (one per
+pool size 1 .. apertures) and the evaluations of each.
 """
 from __future__ import annotations
 
@@ -41,13 +43,20 @@ def main(argv=None):
     with Plan(case, stream=stream.cuda_stream, precision=prec) as plan:
         plan.profile_enable(True)
         plan.solve(a.apertures)
-        before = {kc: plan.profile_read(kc)[0] for kc in binding.KC if kc != "other"}
+        before = {kc: plan.profile_read(kc) for kc in binding.KC if kc != "other"}
         plan.profile_enable(False)
+        evals = [int(e) for e in plan.master_stats()[0]]
         K = a.pool or a.apertures
-        us = plan.k_time(a.kernel, K, a.reps)
-    print(json.dumps({"workload": a.workload, "kernel": a.kernel, "pool": K, "reps": a.reps,
-                      "us_per_launch": round(us, 3), "launches_before": before[a.kernel],
-                      "voxels": case.n_voxels, "nnz": case.nnz, "precision": a.precision}))
+        out = {"workload": a.workload, "kernel": a.kernel, "pool": K, "reps": a.reps, "voxels": case.n_voxels,
+               "nnz": case.nnz, "precision": a.precision, "evaluations_per_solve": evals}
+        if a.kernel == "master_solve":
+            # the persistent solve cannot be re-run in place: report the plan's own launches
+            n, ms = before["master_solve"]
+            out.update(us_per_launch=round(1e3 * ms / max(n, 1), 3), launches=n)
+        else:
+            out.update(us_per_launch=round(plan.k_time(a.kernel, K, a.reps), 3),
+                       launches_before=before[a.kernel][0])
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":
