@@ -556,17 +556,16 @@ dao_status refresh_state(dao_ctx* c) {
 }
 
 dao_status master_solve(dao_ctx* c, double* F_out) {
-    DAO_CU(launch_master_init(c->mb.st, c->K, nullptr, 0, 0, c->stream, &c->launches_i, c->mb.bar));
     const size_t tail = sizeof(MasterDev) - offsetof(MasterDev, F);
     MasterDev* shadow = reinterpret_cast<MasterDev*>(c->pinned + c->off_master - offsetof(MasterDev, F));
-    if (c->mb.GP > 0) {  // the whole solve as one cooperative launch
+    if (c->mb.GP > 0) {  // the whole solve as one cooperative launch (warm start, z and pi included)
         c->prof_begin(DAO_KC_MASTER_SOLVE);
         DAO_CU(launch_master_persist(c->mb, c->slab, c->ld, c->V, c->K, c->vstruct, c->tf, c->S,
-                                     c->opt.max_master_iters, c->opt.master_tol, nullptr, c->stream, &c->launches_i));
+                                     c->opt.max_master_iters, c->opt.master_tol, nullptr, c->z, c->pi, nullptr,
+                                     c->stream, &c->launches_i));
         c->prof_end();
         DAO_CU(cudaMemcpyAsync(&shadow->F, &c->mb.st->F, tail, cudaMemcpyDeviceToHost, c->stream));
         DAO_TRY(sync(c));
-        DAO_TRY(refresh_state(c));
         if (shadow->err == 2) return fail(DAO_ETIMEOUT, "a grid barrier of the master solve timed out");
         if (shadow->status == MASTER_ERROR) return fail(DAO_ETIMEOUT, "the master solve stopped on an error");
         if (!shadow->done) return fail(DAO_ETIMEOUT, "master problem did not stop");
@@ -576,6 +575,7 @@ dao_status master_solve(dao_ctx* c, double* F_out) {
         if (F_out) *F_out = shadow->F;
         return DAO_OK;
     }
+    DAO_CU(launch_master_init(c->mb.st, c->K, nullptr, 0, 0, c->stream, &c->launches_i, c->mb.bar));
     const int unroll = 4;
     const int max_passes = c->opt.max_master_iters + 80;
     int passes = 0;
@@ -711,17 +711,13 @@ dao_status build_round_graph_persist(dao_ctx* c, int K) {
     };
     if (e == cudaSuccess) {
         check(launch_dt(c->Dt, c->pi, c->w, skip, cs, &n));
-        check(launch_price(c->w, c->row_info, c->R_tot, c->beam_row0_d, c->B, c->row_v, c->row_lr, c->price, skip, cs,
-                           &n));
-        check(launch_commit(c->price, c->row_lr, c->beam_row0_d, c->rows_d, c->cols_d, c->tau, K, 2 * c->max_rows,
-                            c->ap_beam, c->ap_lr, c->mask, c->cg, cs, &n));
+        check(launch_price_rows(c->w, c->row_info, c->R_tot, c->row_v, c->row_lr, skip, cs, &n));
+        check(launch_price_commit(c->row_v, c->beam_row0_d, c->B, c->price, c->row_lr, c->rows_d, c->cols_d, c->tau,
+                                  K, 2 * c->max_rows, c->ap_beam, c->ap_lr, c->mask, c->cg, cs, &n));
         check(launch_column_dev(c->D, c->seg, c->ap_beam, K, c->beam_off_d, c->rows_d, c->cols_d, c->max_nb, c->mask,
                                 c->slab + (size_t)(K - 1) * c->ld, 1, c->cg, c->num_sms, cs, &n));
-        check(launch_master_init(c->mb.st, K, skip, 0, 0, cs, &n, c->mb.bar));
         check(launch_master_persist(c->mb, c->slab, c->ld, c->V, K, c->vstruct, c->tf, c->S, c->opt.max_master_iters,
-                                    c->opt.master_tol, skip, cs, &n));
-        check(launch_master_eval(c->mb, c->V, K, c->vstruct, c->tf, c->S, c->z, c->pi, PASS_FINAL, skip, cs, &n));
-        check(launch_cg_record(c->mb.st, c->cg, K, cs, &n));
+                                    c->opt.master_tol, skip, c->z, c->pi, c->cg, cs, &n));
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = e2;
@@ -759,10 +755,9 @@ dao_status build_round_graph(dao_ctx* c, int K) {
         check(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         if (e == cudaSuccess) {
             check(launch_dt(c->Dt, c->pi, c->w, skip, cs, &n));
-            check(launch_price(c->w, c->row_info, c->R_tot, c->beam_row0_d, c->B, c->row_v, c->row_lr, c->price, skip,
-                               cs, &n));
-            check(launch_commit(c->price, c->row_lr, c->beam_row0_d, c->rows_d, c->cols_d, c->tau, K,
-                                2 * c->max_rows, c->ap_beam, c->ap_lr, c->mask, c->cg, cs, &n));
+            check(launch_price_rows(c->w, c->row_info, c->R_tot, c->row_v, c->row_lr, skip, cs, &n));
+            check(launch_price_commit(c->row_v, c->beam_row0_d, c->B, c->price, c->row_lr, c->rows_d, c->cols_d,
+                                      c->tau, K, 2 * c->max_rows, c->ap_beam, c->ap_lr, c->mask, c->cg, cs, &n));
             check(launch_column_dev(c->D, c->seg, c->ap_beam, K, c->beam_off_d, c->rows_d, c->cols_d, c->max_nb,
                                     c->mask, c->slab + (size_t)(K - 1) * c->ld, 1, c->cg, c->num_sms, cs, &n));
             check(launch_master_init(c->mb.st, K, skip, h, 1, cs, &n));
@@ -868,10 +863,12 @@ dao_status solve_graph_end(dao_ctx* c, const GraphSolve& gs, int n_apertures, in
             }
         }
     }
-    // kernels the graphs ran: 8 per round plus pass, curvature and reduce + step per evaluation,
-    // launched in pairs of evaluations
+    // kernels the graphs ran: per round D^T, row scans, argmin + commit, column, and then
+    // the persistent solve, or init, the final pass, the record and, per pair of
+    // evaluations, pass, curvature and reduce + step
     const bool persist = c->mb.GP > 0;
-    c->launches_i += (persist ? 9 : 8) * (K - K0) + (K < K1 ? (persist ? 6 : 5) : 0);
+    // every queued round launches its kernels (a stopped solve's rounds return at entry)
+    c->launches_i += (persist ? 5 : 7) * (K1 - K0);
     for (int k = K0; k < K; ++k) {
         if (!persist) c->launches_i += 6 * ((h->evals[k] + 1) / 2);  // two evaluations per while iteration
         c->stat_evals.push_back(h->evals[k]);

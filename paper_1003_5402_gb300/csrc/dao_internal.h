@@ -89,6 +89,7 @@ struct MasterDev {
     int n_eval;           // fused passes evaluated
     int err;              // set when a tile copy of an evaluation never completed
     unsigned ticket;      // blocks of the reduce + step kernel that finished their share (0 between launches)
+    int final_pending;    // the solve stopped at an accepted point other than the last one evaluated
 };
 
 enum { MASTER_RUNNING = 0, MASTER_CONVERGED = 1, MASTER_MAXITER = 2, MASTER_STALLED = 3, MASTER_ERROR = 4 };
@@ -146,6 +147,13 @@ cudaError_t launch_price(const float* w, const int4* row_info, int n_rows, const
 // Graph path: stop the solve when the reduced cost is not below -tau or the
 // aperture repeats one in the pool; otherwise record it as aperture K-1 and
 // write its open-beamlet mask.
+// Graph path: the row scans, then the beam argmin fused with the commit.
+cudaError_t launch_price_rows(const float* w, const int4* row_info, int n_rows, double* row_v, int2* row_lr,
+                              const int* skip, cudaStream_t stream, int* launches);
+cudaError_t launch_price_commit(const double* row_v, const int* beam_row0, int n_beams, PriceDev* pr,
+                                const int2* row_lr, const int* rows, const int* cols, double tau, int K, int lr_stride,
+                                int* ap_beam, int* ap_lr, float* mask, CGDev* cg, cudaStream_t stream,
+                                int* launches);
 cudaError_t launch_commit(const PriceDev* pr, const int2* row_lr, const int* beam_row0, const int* rows,
                           const int* cols, double tau, int K, int lr_stride, int* ap_beam, int* ap_lr,
                           float* mask, CGDev* cg, cudaStream_t stream, int* launches);
@@ -211,9 +219,12 @@ cudaError_t build_transpose_place(int prec, const int64_t* rp, const int* col, c
 // launch_master_init; dynamic shared memory per master_persist_smem.
 size_t master_persist_smem(int V, int G);
 int master_persist_grid(int V, int num_sms);
+// Includes k_master_init's warm start, writes z and pi of the final point, and
+// (cg != nullptr) the round's record.
 cudaError_t launch_master_persist(const MasterBuffers& mb, const float* slab, int ld, int V, int K,
                                   const uint8_t* vstruct, const StructTermsF* tf, int S, int max_iter, double tol_rel,
-                                  const int* skip, cudaStream_t stream, int* launches);
+                                  const int* skip, float* z_out, float* pi_out, CGDev* cg, cudaStream_t stream,
+                                  int* launches);
 
 // Reduction of the partial sums and the projected-Newton step, one launch.
 cudaError_t launch_master_step(int K, const MasterBuffers& mb, int max_iter, double tol_rel,

@@ -146,6 +146,7 @@ __global__ void k_master_init(MasterDev* __restrict__ st, int K, const int* __re
         st->n_eval = 0;
         st->err = 0;
         st->ticket = 0;
+        st->final_pending = 0;
         if (use_cond) cudaGraphSetConditional(cond, 1u);
     }
 }
@@ -547,6 +548,7 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     if (err) {  // a tile copy was lost in an evaluation: stop with the last accepted point
         if (threadIdx.x == 0) {
             st->status = MASTER_ERROR;
+            st->final_pending = 1;
             st->done = 1;
         }
         return;
@@ -607,6 +609,7 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     if (cap) {
         if (k == 0) {
             st->status = MASTER_MAXITER;
+            st->final_pending = 1;
             st->done = 1;
         }
         return;
@@ -616,6 +619,7 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
         if (alpha < 9.3e-10) {  // 2^-30: the line search found no decrease
             if (k == 0) {
                 st->status = MASTER_STALLED;
+                st->final_pending = 1;
                 st->done = 1;
             }
             return;
@@ -918,7 +922,9 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
                                                        double* __restrict__ F_part, int GS,
                                                        const uint8_t* __restrict__ vstruct,
                                                        const StructTermsF* __restrict__ tf, int S, int max_iter,
-                                                       double tol_rel, double sigma, const int* __restrict__ skip) {
+                                                       double tol_rel, double sigma, const int* __restrict__ skip,
+                                                       float* __restrict__ z_out, float* __restrict__ pi_out,
+                                                       CGDev* __restrict__ cg) {
     extern __shared__ __align__(16) float pm[];
     int* s_act = reinterpret_cast<int*>(pm);          // [PW][capw] voxel indices
     float* s_hv = pm + PW * capw;                     // [PW][capw] h
@@ -944,16 +950,45 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
     if (tid < nb * NV) block_of(tid / NV, KB, rb, cb);
     const int n32 = (V + 31) / 32;
     const int tiles_b = blockIdx.x < n32 ? (n32 - 1 - (int)blockIdx.x) / G + 1 : 0;
-    for (;;) {
-        if (tid == 0) s_stop = __ldcg(&st->done) | __ldcg(&st->err);
-        if (tid < KMAX) {
-            const double yv = tid < K ? __ldcg(&st->yt[tid]) : 0.0;
-            const float hi = (float)yv;
-            s_yh[tid] = hi;
-            s_yl[tid] = (float)(yv - (double)hi);
+    // warm start (every block computes it; block 0 also writes the solver
+    // state): the previous optimum, the new aperture K - 1 at 0
+    if (tid < KMAX) {
+        const double yv = tid < K - 1 ? __ldcg(&st->y[tid]) : 0.0;
+        const float hi = (float)yv;
+        s_yh[tid] = hi;
+        s_yl[tid] = (float)(yv - (double)hi);
+        if (blockIdx.x == 0 && tid < K) {
+            st->yt[tid] = yv;
+            st->d[tid] = 0.0;
         }
-        __syncthreads();
-        if (s_stop) break;
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        st->K = K;
+        st->iter = 0;
+        st->phase = 0;
+        st->done = 0;
+        st->status = MASTER_RUNNING;
+        st->alpha = 1.0;
+        st->n_eval = 0;
+        st->err = 0;
+        st->ticket = 0;
+        st->final_pending = 0;
+    }
+    __syncthreads();
+    bool first = true;
+    for (;;) {
+        if (!first) {  // the state of the previous step (all blocks read it after the barrier)
+            if (tid == 0) s_stop = __ldcg(&st->done) | __ldcg(&st->err);
+            if (tid < KMAX) {
+                const double yv = tid < K ? __ldcg(&st->yt[tid]) : 0.0;
+                const float hi = (float)yv;
+                s_yh[tid] = hi;
+                s_yl[tid] = (float)(yv - (double)hi);
+            }
+            __syncthreads();
+            if (s_stop) break;
+        }
+        first = false;
         // ---- A. z, pi, h, F over this block's tiles; active voxels per warp
         float facc = 0.f;
         int na = 0;
@@ -995,6 +1030,8 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
                 p = 2.f * (t.b * o - t.a * u);
                 h = 2.f * ((du > 0.f ? t.a : 0.f) + (dov > 0.f ? t.b : 0.f));
                 facc = fmaf(t.a * u, u, fmaf(t.b * o, o, facc));
+                z_out[j] = s + c;  // the state of the round when this point is the final one
+                pi_out[j] = p;
             }
             const bool act = h > 0.f;
             const unsigned bal = __ballot_sync(FULL, act);
@@ -1150,6 +1187,54 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
             break;
         }
     }
+    if (tid == 0) s_stop = __ldcg(&st->err) == 2;
+    __syncthreads();
+    if (s_stop) return;  // a barrier timed out: the host reports it
+    // the solve stopped at an accepted point other than the last one evaluated:
+    // z and pi of that point
+    if (__ldcg(&st->final_pending)) {
+        if (tid < KMAX) {
+            const double yv = tid < K ? __ldcg(&st->y[tid]) : 0.0;
+            const float hi = (float)yv;
+            s_yh[tid] = hi;
+            s_yl[tid] = (float)(yv - (double)hi);
+        }
+        __syncthreads();
+        for (int i = warp; i < tiles_b; i += PW) {
+            const int j = (blockIdx.x + i * G) * 32 + lane;
+            const bool in = j < V;
+            float sc[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
+            const float* col = slab + (in ? j : 0);
+            for (int k = 0; k < KP; k += 4) {
+                dot2_step(sc[0], cc[0], __ldcg(col + (size_t)k * ld), s_yh[k], s_yl[k]);
+                dot2_step(sc[1], cc[1], __ldcg(col + (size_t)(k + 1) * ld), s_yh[k + 1], s_yl[k + 1]);
+                dot2_step(sc[2], cc[2], __ldcg(col + (size_t)(k + 2) * ld), s_yh[k + 2], s_yl[k + 2]);
+                dot2_step(sc[3], cc[3], __ldcg(col + (size_t)(k + 3) * ld), s_yh[k + 3], s_yl[k + 3]);
+            }
+            float s = sc[0], c = cc[0];
+#pragma unroll
+            for (int q = 1; q < 4; ++q) {
+                const float t2 = s + sc[q];
+                const float bb = t2 - s;
+                const float e = (s - (t2 - bb)) + (sc[q] - bb);
+                s = t2;
+                c += e + cc[q];
+            }
+            if (in) {
+                const StructTermsF t = s_tf[vstruct[j]];
+                const float u = fmaxf((t.tu - s) - c, 0.f), o = fmaxf((s - t.to) + c, 0.f);
+                z_out[j] = s + c;
+                pi_out[j] = 2.f * (t.b * o - t.a * u);
+            }
+        }
+    }
+    if (cg != nullptr && blockIdx.x == 0 && tid == 0) {  // the round's record
+        cg->trace[K - 1] = __ldcg(&st->F);
+        cg->res[K - 1] = __ldcg(&st->res);
+        cg->tol[K - 1] = __ldcg(&st->tol);
+        cg->evals[K - 1] = __ldcg(&st->n_eval);
+        cg->status[K - 1] = __ldcg(&st->status);
+    }
 }
 
 }  // namespace
@@ -1275,7 +1360,8 @@ int master_persist_grid(int V, int num_sms) {
 
 cudaError_t launch_master_persist(const MasterBuffers& mb, const float* slab, int ld, int V, int K,
                                   const uint8_t* vstruct, const StructTermsF* tf, int S, int max_iter, double tol_rel,
-                                  const int* skip, cudaStream_t stream, int* launches) {
+                                  const int* skip, float* z_out, float* pi_out, CGDev* cg, cudaStream_t stream,
+                                  int* launches) {
     const int G = mb.GP;
     if (G < 1) return cudaErrorInvalidConfiguration;
     const int KP = (K + 3) / 4 * 4;
@@ -1292,7 +1378,7 @@ cudaError_t launch_master_persist(const MasterBuffers& mb, const float* slab, in
     void* args[] = {(void*)&slab, (void*)&ld, (void*)&V, (void*)&K, (void*)&KP, (void*)&KW, (void*)&NV,
                     (void*)&capw, (void*)&st, (void*)&gb, (void*)&H_part, (void*)&g_part, (void*)&gn_part,
                     (void*)&F_part, (void*)&GS, (void*)&vstruct, (void*)&tf, (void*)&S, (void*)&max_iter,
-                    (void*)&tol_rel, (void*)&sigma, (void*)&skip};
+                    (void*)&tol_rel, (void*)&sigma, (void*)&skip, (void*)&z_out, (void*)&pi_out, (void*)&cg};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G);
     cfg.blockDim = dim3(PT);

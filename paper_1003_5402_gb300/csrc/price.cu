@@ -154,7 +154,90 @@ __global__ void __launch_bounds__(256) k_cg_commit(const PriceDev* __restrict__ 
     if (tid == 0) cg->K = K;
 }
 
+// k_price_beams and k_cg_commit in one block (the graph path): the beam sums
+// and their argmin, then the stop tests and the new aperture.
+__global__ void __launch_bounds__(256) k_price_commit(const double* __restrict__ row_v,
+                                                      const int* __restrict__ beam_row0, int n_beams,
+                                                      PriceDev* __restrict__ pr, const int2* __restrict__ row_lr,
+                                                      const int* __restrict__ rows, const int* __restrict__ cols,
+                                                      double tau, int K, int lr_stride, int* __restrict__ ap_beam,
+                                                      int* __restrict__ ap_lr, float* __restrict__ mask,
+                                                      CGDev* __restrict__ cg) {
+    extern __shared__ double s_sum[];
+    __shared__ int s_best, s_dup;
+    __shared__ double s_rc;
+    if (cg->done) return;
+    const int tid = threadIdx.x;
+    for (int b = tid; b < n_beams; b += blockDim.x) {
+        double t = 0.0;
+        for (int r = beam_row0[b]; r < beam_row0[b + 1]; ++r) t = t + row_v[r];
+        s_sum[b] = t;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int best = 0;
+        for (int b = 1; b < n_beams; ++b)
+            if (s_sum[b] < s_sum[best]) best = b;
+        s_best = best;
+        s_rc = n_beams > 0 ? s_sum[best] : 0.0;
+        pr->beam = best;
+        pr->rc = s_rc;
+        s_dup = 0;
+    }
+    __syncthreads();
+    const int b = s_best;
+    if (!(s_rc < -tau)) {
+        if (tid == 0) cg->done = 1;
+        return;
+    }
+    const int R = rows[b], C = cols[b], r0 = beam_row0[b];
+    for (int k = tid; k < K - 1; k += blockDim.x) {
+        if (ap_beam[k] != b) continue;
+        bool same = true;
+        for (int r = 0; r < R && same; ++r) {
+            const int2 lr = row_lr[r0 + r];
+            same = ap_lr[k * lr_stride + 2 * r] == lr.x && ap_lr[k * lr_stride + 2 * r + 1] == lr.y;
+        }
+        if (same) s_dup = 1;
+    }
+    __syncthreads();
+    if (s_dup) {
+        if (tid == 0) cg->done = 2;
+        return;
+    }
+    if (tid == 0) ap_beam[K - 1] = b;
+    for (int r = tid; r < R; r += blockDim.x) {
+        const int2 lr = row_lr[r0 + r];
+        ap_lr[(K - 1) * lr_stride + 2 * r] = lr.x;
+        ap_lr[(K - 1) * lr_stride + 2 * r + 1] = lr.y;
+    }
+    for (int i = tid; i < R * C; i += blockDim.x) {
+        const int2 lr = row_lr[r0 + i / C];
+        const int c = i % C;
+        mask[i] = (c >= lr.x && c < lr.y) ? 1.f : 0.f;
+    }
+    if (tid == 0) cg->K = K;
+}
+
 }  // namespace
+
+cudaError_t launch_price_rows(const float* w, const int4* row_info, int n_rows, double* row_v, int2* row_lr,
+                              const int* skip, cudaStream_t stream, int* launches) {
+    if (n_rows == 0) return cudaSuccess;
+    k_price_rows<<<n_rows, 32, 0, stream>>>(w, row_info, n_rows, row_v, row_lr, skip);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_price_commit(const double* row_v, const int* beam_row0, int n_beams, PriceDev* pr,
+                                const int2* row_lr, const int* rows, const int* cols, double tau, int K, int lr_stride,
+                                int* ap_beam, int* ap_lr, float* mask, CGDev* cg, cudaStream_t stream,
+                                int* launches) {
+    k_price_commit<<<1, 256, (size_t)(n_beams > 0 ? n_beams : 1) * sizeof(double), stream>>>(
+        row_v, beam_row0, n_beams, pr, row_lr, rows, cols, tau, K, lr_stride, ap_beam, ap_lr, mask, cg);
+    ++*launches;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_commit(const PriceDev* pr, const int2* row_lr, const int* beam_row0, const int* rows,
                           const int* cols, double tau, int K, int lr_stride, int* ap_beam, int* ap_lr, float* mask,
