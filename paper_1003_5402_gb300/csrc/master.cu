@@ -544,6 +544,12 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     const double tol0 = __ldcg(&st->tol), F0 = __ldcg(&st->F), Ft = __ldcg(&st->Ft);
     const double yt_ = __ldcg(&st->yt[kk]), gt_ = __ldcg(&st->gt[kk]), gn_ = (double)__ldcg(&st->gn[kk]);
     const double y_ = __ldcg(&st->y[kk]), g_ = __ldcg(&st->g[kk]);
+    // the curvature matrix, requested now so that its latency passes behind the
+    // reductions below; stored to shared memory once the free set is known
+    // (entry 256 m + k of the row-major KMAX x KMAX array)
+    float hpre[KMAX * KMAX / STEP_T];
+#pragma unroll
+    for (int m = 0; m < KMAX * KMAX / STEP_T; ++m) hpre[m] = __ldcg(&st->Ht[m * STEP_T + k]);
     if (done) return;
     if (err) {  // a tile copy was lost in an evaluation: stop with the last accepted point
         if (threadIdx.x == 0) {
@@ -667,6 +673,11 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     }
     pos += __popc(bal & ((1u << (k & 31)) - 1u));
     if (fr) fidx[pos] = k;
+#pragma unroll
+    for (int m = 0; m < KMAX * KMAX / STEP_T; ++m) {  // H into Lw (overwritten later by the factorisation)
+        const int idx = m * STEP_T + k;
+        Lw[idx / KMAX][idx % KMAX] = hpre[m];
+    }
     double d = active ? -gt : 0.0;
     __syncthreads();
     // Damped FP32 L D L^T factorisation of H_FF with the forward solve folded in,
@@ -693,7 +704,7 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int i = ti + 16 * a, q = tq + 16 * b;
-            Hr[a][b] = (i < nf && q <= i) ? __ldcg(&st->Ht[fidx[i] * KMAX + fidx[q]]) : 0.f;
+            Hr[a][b] = (i < nf && q <= i) ? Lw[fidx[i]][fidx[q]] : 0.f;
         }
     const float bk = k < nf ? -(float)__ldcg(&st->g[fidx[k]]) : 0.f;
     float dg = 0.f;
