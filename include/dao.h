@@ -123,7 +123,16 @@ dao_status dao_create(const dao_csr* D, const dao_geometry* g, const dao_structu
                       const dao_weights* w, const double* prescriptions,
                       const dao_options* opt, dao_ctx** out);
 
+/* Release a context.  Its device memory goes back to a process-wide
+ * stream-ordered pool on its device, which keeps up to min(16 GiB, 1/16 of the
+ * device) of freed memory mapped for the contexts created after it; its small
+ * page-locked staging block goes to a process-wide free list (at most 64 MiB). */
 void dao_destroy(dao_ctx* ctx);
+
+/* Return the cached memory of device `device` to the system: the pool is
+ * trimmed to the memory of live contexts and the page-locked free list is
+ * emptied.  Safe to call at any time; contexts stay valid. */
+dao_status dao_release_cached_memory(int32_t device);
 
 /* Empty the aperture pool (y = [], z = 0) keeping D on the device. */
 dao_status dao_reset(dao_ctx* ctx);
@@ -351,7 +360,8 @@ dao_status dao_server_poll(dao_server* srv, int64_t id, dao_result* out);
 /* As poll, blocking up to timeout_ms (< 0: no limit); DAO_ETIMEOUT if it ran out. */
 dao_status dao_server_wait(dao_server* srv, int64_t id, double timeout_ms, dao_result* out);
 dao_status dao_server_stats_get(dao_server* srv, dao_server_stats* out);
-/* Device bytes a request's plan holds: the admission footprint. */
+/* Device bytes a request's plan holds at its peak, the temporaries of its
+ * device build included: the admission footprint. */
 int64_t dao_server_footprint(const dao_request* req, const dao_options* plan_options);
 /* Cancels queued requests (status DAO_ESTATE), waits for the running plans,
  * stops the worker and frees the server. */

@@ -6,6 +6,6 @@ compiles it in-tree.  Importing this package does not load the library; the
 first binding call does, and fails loudly if it has not been built.
 """
 from . import binding  # noqa: F401
-from .binding import Plan, Server, DaoError, load  # noqa: F401
+from .binding import Plan, Server, DaoError, load, release_cached_memory  # noqa: F401
 
-__all__ = ["Plan", "Server", "DaoError", "load", "binding"]
+__all__ = ["Plan", "Server", "DaoError", "load", "release_cached_memory", "binding"]

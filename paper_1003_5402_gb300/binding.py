@@ -85,6 +85,7 @@ SIGNATURES = {
     "dao_create": (C.c_int, [C.POINTER(dao_csr), C.POINTER(dao_geometry), C.POINTER(dao_structures),
                              C.POINTER(dao_weights), _F64P, C.POINTER(dao_options), C.POINTER(_P)]),
     "dao_destroy": (None, [_P]),
+    "dao_release_cached_memory": (C.c_int, [C.c_int32]),
     "dao_reset": (C.c_int, [_P]),
     "dao_price": (C.c_int, [_P, _I32P, _I32P, _F64P]),
     "dao_add_aperture": (C.c_int, [_P, C.c_int32, _I32P, _F64P]),
@@ -194,6 +195,12 @@ def _case_structs(case, normalize_by_volume: bool = True):
     s = dao_structures(len(uw), _ptr(vs, C.c_int32), _ptr(tgt, C.c_uint8))
     w = dao_weights(_ptr(uw, C.c_double), _ptr(ow, C.c_double), _ptr(ot, C.c_double), int(normalize_by_volume))
     return D, g, s, w, rx, keep
+
+
+def release_cached_memory(device: int = 0) -> None:
+    """Give the device pool's cached memory and the page-locked free list back
+    to the system (dao_release_cached_memory)."""
+    _check(load().dao_release_cached_memory(int(device)), "dao_release_cached_memory")
 
 
 class Plan:

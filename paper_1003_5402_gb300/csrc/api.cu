@@ -9,7 +9,6 @@
 #include <cstring>
 #include <new>
 #include <string>
-#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -106,6 +105,7 @@ struct dao_ctx {
     // pinned staging
     unsigned char* pinned = nullptr;
     size_t off_small = 0, off_rows = 0, off_mask = 0, off_master = 0, off_cg = 0, pinned_bytes = 0;
+    size_t pinned_block = 0;  // size of the cached block behind pinned
 
     // per master solve: evaluations (fused passes), final status, KKT residual / max|g(start)|
     std::vector<int> stat_evals, stat_status;
@@ -128,10 +128,10 @@ struct dao_ctx {
     dao_status dalloc(T** p, size_t n) {
         void* q = nullptr;
         const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
-        cudaError_t e = cudaMalloc(&q, bytes);
+        cudaError_t e = pool_alloc(&q, bytes, device, stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            return fail(DAO_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+            return fail(DAO_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed: " +
                                         cudaGetErrorString(e));
         }
         dev_allocs.push_back(q);
@@ -185,6 +185,22 @@ dao_status sync(dao_ctx* c) {
 
 // ---- validation ---------------------------------------------------------------
 
+// Message for CSR row j of D (the device check found it to be the first bad
+// row): the first of its faults in entry order.
+std::string row_error(const dao_csr* D, int j) {
+    const int64_t p0 = D->row_ptr[j], p1 = D->row_ptr[j + 1];
+    if (p1 < p0 || p0 < 0 || p1 > D->nnz) return "row_ptr decreases or leaves [0, nnz] at row " + std::to_string(j);
+    for (int64_t p = p0; p < p1; ++p) {
+        const int32_t c = D->col[p];
+        if (c < 0 || c >= D->n_beamlets) return "column index out of range at entry " + std::to_string(p);
+        if (p > p0 && c <= D->col[p - 1]) return "columns not strictly increasing in row " + std::to_string(j);
+        if (!std::isfinite(D->val[p])) return "non-finite value at entry " + std::to_string(p);
+    }
+    return "invalid row " + std::to_string(j);
+}
+
+// Host checks of everything but the per-entry and per-voxel arrays, which the
+// device checks while it builds the plan's layout (build_check).
 dao_status validate(const dao_csr* D, const dao_geometry* g, const dao_structures* s, const dao_weights* w,
                     const double* rx, const dao_options* opt) {
     if (!D || !g || !s || !w || !rx || !opt) return fail(DAO_EINVAL, "null argument");
@@ -192,46 +208,6 @@ dao_status validate(const dao_csr* D, const dao_geometry* g, const dao_structure
     if (!D->row_ptr || !D->col || !D->val) return fail(DAO_EINVAL, "null CSR array");
     if (D->row_ptr[0] != 0 || D->row_ptr[D->n_voxels] != D->nnz || D->nnz < 0)
         return fail(DAO_EINVAL, "row_ptr[0] must be 0 and row_ptr[n_voxels] must equal nnz");
-    {
-        // rows checked by up to 16 host threads; the first bad row in row order is reported
-        const int V = D->n_voxels;
-        auto check_rows = [D](int j0, int j1, std::string* msg) -> int {
-            for (int j = j0; j < j1; ++j) {
-                const int64_t p0 = D->row_ptr[j], p1 = D->row_ptr[j + 1];
-                if (p1 < p0 || p0 < 0 || p1 > D->nnz) {
-                    *msg = "row_ptr decreases or leaves [0, nnz] at row " + std::to_string(j);
-                    return j;
-                }
-                for (int64_t p = p0; p < p1; ++p) {
-                    const int32_t c = D->col[p];
-                    if (c < 0 || c >= D->n_beamlets) {
-                        *msg = "column index out of range at entry " + std::to_string(p);
-                        return j;
-                    }
-                    if (p > p0 && c <= D->col[p - 1]) {
-                        *msg = "columns not strictly increasing in row " + std::to_string(j);
-                        return j;
-                    }
-                    if (!std::isfinite(D->val[p])) {
-                        *msg = "non-finite value at entry " + std::to_string(p);
-                        return j;
-                    }
-                }
-            }
-            return -1;
-        };
-        const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-        const int T = D->nnz < (1 << 20) ? 1 : (int)std::min<int64_t>(hw, V);
-        std::vector<int> bad(T, -1);
-        std::vector<std::string> msg(T);
-        std::vector<std::thread> th;
-        for (int t = 1; t < T; ++t)
-            th.emplace_back([&, t] { bad[t] = check_rows((int)((int64_t)V * t / T), (int)((int64_t)V * (t + 1) / T), &msg[t]); });
-        bad[0] = check_rows(0, (int)((int64_t)V / T), &msg[0]);
-        for (std::thread& x : th) x.join();
-        for (int t = 0; t < T; ++t)
-            if (bad[t] >= 0) return fail(DAO_EINVAL, msg[t]);
-    }
     if (g->n_beams < 1 || !g->rows || !g->cols) return fail(DAO_EINVAL, "geometry needs at least one beam");
     int64_t total = 0;
     for (int b = 0; b < g->n_beams; ++b) {
@@ -243,9 +219,6 @@ dao_status validate(const dao_csr* D, const dao_geometry* g, const dao_structure
     if (total != D->n_beamlets) return fail(DAO_EINVAL, "sum of rows*cols differs from n_beamlets");
     if (s->n_structures < 1 || s->n_structures > SMAX || !s->voxel_struct || !s->is_target)
         return fail(DAO_EINVAL, "n_structures must be in [1, 64]");
-    for (int j = 0; j < D->n_voxels; ++j)
-        if (s->voxel_struct[j] < 0 || s->voxel_struct[j] >= s->n_structures)
-            return fail(DAO_EINVAL, "voxel structure label out of range at voxel " + std::to_string(j));
     if (!w->under_w || !w->over_w || !w->over_thresh) return fail(DAO_EINVAL, "null weight array");
     for (int k = 0; k < s->n_structures; ++k) {
         if (!(w->under_w[k] >= 0) || !std::isfinite(w->under_w[k]) || !(w->over_w[k] >= 0) ||
@@ -297,20 +270,14 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
         }
 
     // D (voxel-major) with per-row beam segments, and D^T, built on the device
-    // from the caller's CSR (uploaded as is).  Rows are padded to 4 entries (one
-    // float4 / int4 load) or, with 16-bit values, to 8 entries (one 16-byte load
-    // of values and of 16-bit columns).
+    // from the caller's CSR (uploaded as is) after the device has checked it.
+    // Rows are padded to 4 entries (one float4 / int4 load) or, with 16-bit
+    // values, to 8 entries (one 16-byte load of values and of 16-bit columns).
     const int prec = c->opt.precision;
     const int pad_m = prec == DAO_PREC_FP32 ? 4 : 8;
     const int64_t nnz = Din->nnz;
-    std::vector<int> prow(V + 1, 0);
-    int64_t padded = 0;
-    for (int j = 0; j < V; ++j) {
-        prow[j] = (int)std::min<int64_t>(padded, INT32_MAX);
-        padded += round_up(Din->row_ptr[j + 1] - Din->row_ptr[j], pad_m);
-    }
-    if (padded >= (int64_t)1 << 31) return fail(DAO_EINVAL, "D too large for 32-bit row offsets");
-    prow[V] = (int)padded;
+    const int S = s->n_structures;
+    c->S = S;
     // rows of D per chunk of the transpose: the chunk-by-beamlet counters stay under 16M
     const int CH = (int)std::max<int64_t>(256, ((int64_t)V * N / (16 << 20) + 31) / 32 * 32);
     const int n_ch = (V + CH - 1) / CH;
@@ -319,40 +286,71 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     int64_t* t_rp = nullptr;
     int* t_col = nullptr;
     float* t_val = nullptr;
+    int* t_lab = nullptr;
+    int64_t* t_plen = nullptr;
+    int64_t* t_bsum = nullptr;
+    BuildCheck* t_chk = nullptr;
     int* t_C = nullptr;
     int* t_cnt = nullptr;
     unsigned* t_dmax = nullptr;
     float* t_tval = nullptr;
     auto free_temps = [&]() {
-        for (void* q : {(void*)t_rp, (void*)t_col, (void*)t_val, (void*)t_C, (void*)t_cnt, (void*)t_dmax,
+        for (void* q : {(void*)t_rp, (void*)t_col, (void*)t_val, (void*)t_lab, (void*)t_plen, (void*)t_bsum,
+                        (void*)t_chk, (void*)t_C, (void*)t_cnt, (void*)t_dmax,
                         (void*)(prec == DAO_PREC_FP32 ? nullptr : t_tval)})
-            if (q) cudaFreeAsync(q, st);
+            if (q) pool_free(q, st);
     };
     auto talloc = [&](auto** q, size_t bytes) -> dao_status {
         void* v = nullptr;
-        const cudaError_t e = cudaMallocAsync(&v, std::max<size_t>(bytes, 4), st);
+        const cudaError_t e = pool_alloc(&v, bytes, c->device, st);
         if (e != cudaSuccess) {
             cudaGetLastError();
             free_temps();
-            return fail(DAO_ENOMEM, "cudaMallocAsync of " + std::to_string(bytes) + " bytes failed");
+            return fail(DAO_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
         }
         *q = static_cast<std::remove_pointer_t<decltype(q)>>(v);
         return DAO_OK;
     };
-    DAO_TRY(talloc(&t_rp, sizeof(int64_t) * (V + 1)));
-    DAO_TRY(talloc(&t_col, sizeof(int) * nnz));
-    DAO_TRY(talloc(&t_val, sizeof(float) * nnz));
-    DAO_TRY(talloc(&t_C, sizeof(int) * (size_t)n_ch * N));
-    DAO_TRY(talloc(&t_cnt, sizeof(int) * N));
-    DAO_TRY(talloc(&t_dmax, sizeof(unsigned)));
     auto cu = [&](cudaError_t e, const char* what) -> dao_status {
         if (e == cudaSuccess) return DAO_OK;
         free_temps();
         return fail(DAO_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
     };
+    DAO_TRY(talloc(&t_rp, sizeof(int64_t) * (V + 1)));
+    DAO_TRY(talloc(&t_col, sizeof(int) * nnz));
+    DAO_TRY(talloc(&t_val, sizeof(float) * nnz));
+    DAO_TRY(talloc(&t_lab, sizeof(int) * V));
+    DAO_TRY(talloc(&t_plen, sizeof(int64_t) * V));
+    DAO_TRY(talloc(&t_bsum, sizeof(int64_t) * check_scan_blocks(V)));
+    DAO_TRY(talloc(&t_chk, sizeof(BuildCheck)));
     DAO_TRY(cu(cudaMemcpyAsync(t_rp, Din->row_ptr, sizeof(int64_t) * (V + 1), cudaMemcpyHostToDevice, st), "upload"));
     DAO_TRY(cu(cudaMemcpyAsync(t_col, Din->col, sizeof(int) * nnz, cudaMemcpyHostToDevice, st), "upload"));
     DAO_TRY(cu(cudaMemcpyAsync(t_val, Din->val, sizeof(float) * nnz, cudaMemcpyHostToDevice, st), "upload"));
+    DAO_TRY(cu(cudaMemcpyAsync(t_lab, s->voxel_struct, sizeof(int) * V, cudaMemcpyHostToDevice, st), "upload"));
+    DAO_TRY(c->dalloc(&c->D.rowptr, (size_t)V + 1));
+    DAO_TRY(c->dalloc(&c->vstruct, V));
+    // checks of every row and label, padded row offsets, voxels per structure
+    BuildCheck chk{};
+    DAO_TRY(cu(build_check(t_rp, t_col, t_val, nnz, V, N, t_lab, S, pad_m, t_plen, t_bsum, c->vstruct, c->D.rowptr,
+                           t_chk, st), "input checks"));
+    DAO_TRY(cu(cudaMemcpyAsync(&chk, t_chk, sizeof(BuildCheck), cudaMemcpyDeviceToHost, st), "check read-back"));
+    DAO_TRY(cu(cudaStreamSynchronize(st), "input checks"));
+    if (chk.bad_row > 0) {
+        free_temps();
+        return fail(DAO_EINVAL, row_error(Din, V - chk.bad_row));
+    }
+    if (chk.bad_label > 0) {
+        free_temps();
+        return fail(DAO_EINVAL, "voxel structure label out of range at voxel " + std::to_string(V - chk.bad_label));
+    }
+    const int64_t padded = chk.padded;
+    if (padded >= (int64_t)1 << 31) {
+        free_temps();
+        return fail(DAO_EINVAL, "D too large for 32-bit row offsets");
+    }
+    DAO_TRY(talloc(&t_C, sizeof(int) * (size_t)n_ch * N));
+    DAO_TRY(talloc(&t_cnt, sizeof(int) * N));
+    DAO_TRY(talloc(&t_dmax, sizeof(unsigned)));
     c->D.n_rows = V;
     c->D.n_cols = N;
     c->D.nnz_stored = padded;
@@ -364,7 +362,6 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     DAO_TRY(c->dalloc(&scale, N));
     c->D.scale = scale;
     c->Dt.scale = scale;
-    DAO_TRY(upload(c, &c->D.rowptr, prow.data(), prow.size()));
     DAO_TRY(upload(c, &c->beam_off_d, c->beam_off.data(), c->beam_off.size()));
     DAO_TRY(c->dalloc(&c->seg, (size_t)(B + 1) * V));
     if (prec == DAO_PREC_FP32) {
@@ -422,17 +419,14 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     float dmax = 0.f;
     std::memcpy(&dmax, &dmax_bits, sizeof(float));
 
-    // objective terms per structure (Eqs. 9-10)
-    const int S = s->n_structures;
-    c->S = S;
-    std::vector<int64_t> count(S, 0);
-    for (int j = 0; j < V; ++j) ++count[s->voxel_struct[j]];
+    // objective terms per structure (Eqs. 9-10); voxel counts from the device check
     std::vector<StructTermsD> tdh(S);
     std::vector<StructTermsF> tfh(S);
     std::vector<StructTermsS> tsh(S);
     double pi0_l1 = 0.0;
     for (int k = 0; k < S; ++k) {
-        const double vol = (w->normalize_by_volume && count[k] > 0) ? (double)count[k] : 1.0;
+        const int64_t count = chk.count[k];
+        const double vol = (w->normalize_by_volume && count > 0) ? (double)count : 1.0;
         const bool tgt = s->is_target[k] != 0;
         tdh[k].a = tgt ? w->under_w[k] / vol : 0.0;
         tdh[k].tu = tgt ? rx[k] : 0.0;
@@ -443,13 +437,10 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
         tsh[k] = {(float)tdh[k].a, tu_hi, (float)(tdh[k].tu - (double)tu_hi), (float)tdh[k].b, to_hi,
                   (float)(tdh[k].to - (double)to_hi), 0.f, 0.f};
         // |grad F(0)| summed over the structure's voxels
-        pi0_l1 += (double)count[k] * (2.0 * tdh[k].a * std::max(0.0, tdh[k].tu) + 2.0 * tdh[k].b * std::max(0.0, -tdh[k].to));
+        pi0_l1 += (double)count * (2.0 * tdh[k].a * std::max(0.0, tdh[k].tu) + 2.0 * tdh[k].b * std::max(0.0, -tdh[k].to));
     }
     c->tau = c->opt.price_tol * (double)dmax * pi0_l1;
-    std::vector<uint8_t> vs(V);
-    for (int j = 0; j < V; ++j) vs[j] = (uint8_t)s->voxel_struct[j];
 
-    DAO_TRY(upload(c, &c->vstruct, vs.data(), vs.size()));
     DAO_TRY(upload(c, &c->tf, tfh.data(), tfh.size()));
     DAO_TRY(upload(c, &c->ts, tsh.data(), tsh.size()));
     DAO_TRY(upload(c, &c->row_info, ri.data(), ri.size()));
@@ -539,8 +530,10 @@ dao_status alloc_state(dao_ctx* c) {
     c->off_cg = (c->off_master + sizeof(MasterDev) + 255) / 256 * 256;
     c->pinned_bytes = c->off_cg + sizeof(CGDev);
     void* p = nullptr;
-    DAO_CU(cudaMallocHost(&p, c->pinned_bytes));
+    size_t got = c->pinned_bytes;
+    DAO_CU(pinned_alloc(&p, &got));
     c->pinned = static_cast<unsigned char*>(p);
+    c->pinned_block = got;
     return DAO_OK;
 }
 
@@ -1025,11 +1018,21 @@ void dao_destroy(dao_ctx* c) {
         if (ex) cudaGraphExecDestroy(ex);
     for (cudaGraph_t g : c->round_graph)
         if (g) cudaGraphDestroy(g);
-    for (void* p : c->dev_allocs) cudaFree(p);
+    // back to the process-wide caches, ordered after the context's last work
+    for (void* p : c->dev_allocs) pool_free(p, c->stream);
     for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
-    if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->pinned) pinned_release(c->pinned, c->pinned_block);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
+}
+
+dao_status dao_release_cached_memory(int32_t device) {
+    int n = 0;
+    DAO_CU(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(DAO_EINVAL, "no such device");
+    DAO_CU(cudaSetDevice(device));
+    DAO_CU(release_cached_memory(device));
+    return DAO_OK;
 }
 
 dao_status dao_reset(dao_ctx* c) {

@@ -1,5 +1,6 @@
 // Device-side construction of a plan's matrices from the caller's CSR of D
-// (uploaded as is): the padded voxel-major layout, the per-row beam segments,
+// (uploaded as is): the checks of the caller's rows and labels, the padded
+// row offsets (a scan), the padded voxel-major layout, the per-row beam segments,
 // the per-beamlet scales of the 16-bit storage, and the beamlet-major
 // transpose D^T by a stable counting sort.
 //
@@ -10,6 +11,8 @@
 // first slot in every row of D^T; then one warp per chunk walks its voxels in
 // order and places each entry at its beamlet's next slot.  Entries of one voxel
 // have distinct beamlets, so the lanes of a warp never share a slot counter.
+#include <climits>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -179,9 +182,152 @@ __global__ void k_quant_t(const float* __restrict__ tval, const int* __restrict_
     for (int q = trow[i] + lane; q < trow[i + 1]; q += 32) tval16[q] = to16<PREC>(tval[q] / s);
 }
 
+// The caller's CSR and labels, one warp per voxel row j: row bounds inside
+// [0, nnz], columns in [0, N) and strictly increasing, finite values, label in
+// [0, S).  A bad row or label is recorded as V - j under atomicMax (so the
+// lowest index wins); a good row writes its padded length, a good label its
+// byte and one count for its structure.  Every read of col / val is inside the
+// row's checked bounds.
+__global__ void k_check(const int64_t* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ val,
+                        int64_t nnz, int V, int N, const int* __restrict__ label, int S, int pad,
+                        int64_t* __restrict__ plen, uint8_t* __restrict__ vs8, BuildCheck* __restrict__ chk) {
+    __shared__ int s_cnt[SMAX];
+    for (int k = threadIdx.x; k < SMAX; k += blockDim.x) s_cnt[k] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int j = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (j < V) {
+        const int64_t p0 = rp[j], p1 = rp[j + 1];
+        bool ok = p0 >= 0 && p1 >= p0 && p1 <= nnz;
+        if (ok) {
+            bool bad = false;
+            for (int64_t p = p0 + lane; p < p1; p += 32) {
+                const int c = col[p];
+                bad |= c < 0 || c >= N || !isfinite(val[p]);
+                if (p > p0) bad |= c <= col[p - 1];
+            }
+            ok = !__any_sync(FULL, bad);
+        }
+        if (lane == 0) {
+            plen[j] = ok ? (p1 - p0 + pad - 1) / pad * pad : 0;
+            if (!ok) atomicMax(&chk->bad_row, V - j);
+            const int l = label[j];
+            if (l < 0 || l >= S) {
+                atomicMax(&chk->bad_label, V - j);
+            } else {
+                vs8[j] = (uint8_t)l;
+                atomicAdd(&s_cnt[l], 1);
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < S; k += blockDim.x)
+        if (s_cnt[k]) atomicAdd(&chk->count[k], s_cnt[k]);
+}
+
+// Exclusive scan of plen in three steps: block totals, a scan of the totals
+// (one block), then each block's scan plus its offset.  SCAN_T threads with
+// SCAN_E consecutive elements each per block.
+constexpr int SCAN_T = 1024, SCAN_E = 4, SCAN_B = SCAN_T * SCAN_E;
+
+// Exclusive scan of one value per thread across the block; returns the block total.
+__device__ __forceinline__ int64_t block_exscan(int64_t v, int64_t* ex) {
+    __shared__ int64_t s_w[SCAN_T / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t t = lane < SCAN_T / 32 ? s_w[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(FULL, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < SCAN_T / 32) s_w[lane] = t;  // inclusive over warps
+    }
+    __syncthreads();
+    const int64_t before = wid > 0 ? s_w[wid - 1] : 0;
+    *ex = before + x - v;
+    const int64_t total = s_w[SCAN_T / 32 - 1];
+    __syncthreads();  // s_w reused by the next call
+    return total;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_totals(const int64_t* __restrict__ plen, int V,
+                                                         int64_t* __restrict__ bsum) {
+    const int64_t i0 = (int64_t)blockIdx.x * SCAN_B + (int64_t)threadIdx.x * SCAN_E;
+    int64_t v = 0;
+#pragma unroll
+    for (int e = 0; e < SCAN_E; ++e)
+        if (i0 + e < V) v += plen[i0 + e];
+    int64_t ex;
+    const int64_t t = block_exscan(v, &ex);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = t;
+}
+
+// One block: bsum becomes exclusive; the grand total goes to chk->padded and
+// (clamped) to prow[V].
+__global__ void __launch_bounds__(SCAN_T) k_scan_offsets(int64_t* __restrict__ bsum, int nb, int V,
+                                                          int* __restrict__ prow, BuildCheck* __restrict__ chk) {
+    int64_t carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += SCAN_T) {
+        const int b = b0 + threadIdx.x;
+        const int64_t v = b < nb ? bsum[b] : 0;
+        int64_t ex;
+        const int64_t t = block_exscan(v, &ex);
+        if (b < nb) bsum[b] = carry + ex;
+        carry += t;
+    }
+    if (threadIdx.x == 0) {
+        chk->padded = carry;
+        prow[V] = (int)min(carry, (int64_t)INT_MAX);
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_apply(const int64_t* __restrict__ plen, int V,
+                                                        const int64_t* __restrict__ bsum, int* __restrict__ prow) {
+    const int64_t i0 = (int64_t)blockIdx.x * SCAN_B + (int64_t)threadIdx.x * SCAN_E;
+    int64_t v[SCAN_E], tot = 0;
+#pragma unroll
+    for (int e = 0; e < SCAN_E; ++e) {
+        v[e] = i0 + e < V ? plen[i0 + e] : 0;
+        tot += v[e];
+    }
+    int64_t ex;
+    block_exscan(tot, &ex);
+    int64_t run = bsum[blockIdx.x] + ex;
+#pragma unroll
+    for (int e = 0; e < SCAN_E; ++e)
+        if (i0 + e < V) {
+            prow[i0 + e] = (int)min(run, (int64_t)INT_MAX);
+            run += v[e];
+        }
+}
+
 inline unsigned blocks_for(int64_t threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
 
 }  // namespace
+
+int check_scan_blocks(int V) { return (int)blocks_for(V, SCAN_B); }
+
+cudaError_t build_check(const int64_t* rp, const int* col, const float* val, int64_t nnz, int V, int N,
+                        const int* label, int S, int pad, int64_t* plen, int64_t* bsum, uint8_t* vs8, int* prow,
+                        BuildCheck* chk, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(chk, 0, sizeof(BuildCheck), s);
+    if (e != cudaSuccess) return e;
+    k_check<<<blocks_for((int64_t)V * 32, 256), 256, 0, s>>>(rp, col, val, nnz, V, N, label, S, pad, plen, vs8, chk);
+    const int nb = check_scan_blocks(V);
+    k_scan_totals<<<nb, SCAN_T, 0, s>>>(plen, V, bsum);
+    k_scan_offsets<<<1, SCAN_T, 0, s>>>(bsum, nb, V, prow, chk);
+    k_scan_apply<<<nb, SCAN_T, 0, s>>>(plen, V, bsum, prow);
+    return cudaGetLastError();
+}
 
 cudaError_t build_scales(const int* col, const float* val, int64_t nnz, int N, unsigned* smax, unsigned* dmax,
                          int num_sms, cudaStream_t s) {

@@ -202,7 +202,36 @@ cudaError_t launch_master_hess(const MasterBuffers& mb, int K, int mode, cudaStr
 // Read-only pass over a buffer larger than L2 (cold-cache timing).
 cudaError_t launch_l2_evict(const void* buf, size_t bytes, float* sink, int num_sms, cudaStream_t stream);
 
+// Process-wide memory caches (memory.cu): a stream-ordered device pool per
+// device that keeps up to POOL_KEEP_MAX bytes (at most 1/16 of the device) of
+// freed memory for reuse, and a free list of page-locked host blocks.
+constexpr unsigned long long POOL_KEEP_MAX = 16ull << 30;
+cudaError_t pool_alloc(void** p, size_t bytes, int device, cudaStream_t s);
+cudaError_t pool_free(void* p, cudaStream_t s);
+// *bytes_io: requested size in, size of the block handed out back.
+cudaError_t pinned_alloc(void** p, size_t* bytes_io);
+void pinned_release(void* p, size_t bytes);
+cudaError_t release_cached_memory(int device);
+
+// Result of the device-side input checks: the first bad CSR row and the first
+// bad structure label as V - index (0: none), the padded entry count of D and
+// the voxels of each structure.
+struct BuildCheck {
+    int bad_row;
+    int bad_label;
+    long long padded;
+    int count[SMAX];
+};
+
 // Device-side construction of the matrices (build.cu).
+// Checks rows and labels, writes the labels as bytes, and the padded row
+// offsets prow[0..V] of D (rows rounded up to pad entries; clamped to INT_MAX,
+// the exact total in chk->padded).  plen: V int64, bsum: check_scan_blocks(V)
+// int64 of scratch.
+int check_scan_blocks(int V);
+cudaError_t build_check(const int64_t* rp, const int* col, const float* val, int64_t nnz, int V, int N,
+                        const int* label, int S, int pad, int64_t* plen, int64_t* bsum, uint8_t* vs8, int* prow,
+                        BuildCheck* chk, cudaStream_t s);
 cudaError_t build_scales(const int* col, const float* val, int64_t nnz, int N, unsigned* smax, unsigned* dmax,
                          int num_sms, cudaStream_t s);
 cudaError_t build_fill_d(int prec, const int64_t* rp, const int* col, const float* val, const int* prow, int V,

@@ -258,7 +258,11 @@ int64_t dao_server_footprint(const dao_request* req, const dao_options* plan_opt
     const int64_t d_bytes = (V + 1) * 4 + (nnz + V * (pad - 1)) * (wide ? 8 : 4);
     const int64_t t_bytes = (N + 1) * 4 + (nnz + N * (pad - 1)) * (wide ? 8 : 6) + (wide ? 0 : N * 4);
     const int64_t master = ld * 4 * (dao::KMAX + dao::KROW) + ld * 8 + V * 4 * 4;
-    return d_bytes + t_bytes + (B + 1) * V * 4 + V + master + N * 64 + ((int64_t)40 << 20);
+    // temporaries of the device build, alive together until the transpose is placed
+    const int64_t CH = std::max<int64_t>(256, (V * N / (16 << 20) + 31) / 32 * 32);
+    const int64_t build = (V + 1) * 8 + nnz * 8 + V * 12 + ((V + CH - 1) / CH) * N * 4 + N * 8 +
+                          (wide ? 0 : (nnz + N * (pad - 1)) * 4);
+    return d_bytes + t_bytes + (B + 1) * V * 4 + V + master + N * 64 + build + ((int64_t)40 << 20);
 }
 
 dao_status dao_server_create(const dao_server_options* opt_in, dao_server** out) {

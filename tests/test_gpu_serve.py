@@ -51,11 +51,14 @@ def test_server_results_equal_plans_alone(torch):
 
 
 def test_footprint_bounds_the_device_memory_of_a_plan(torch):
-    from paper_1003_5402_gb300 import Plan, Server
+    from paper_1003_5402_gb300 import Plan, Server, release_cached_memory
     case = P.make_case(P.spec_prostate())
     with Server(max_slots=1) as s:
         fp = s.footprint(case)
     torch.cuda.synchronize()
+    # destroyed plans' memory stays in the library's pool: empty it, so that the
+    # pool grows by this plan's peak (its build temporaries included)
+    release_cached_memory(0)
     free0, _ = torch.cuda.mem_get_info()
     with Plan(case) as p:
         p.solve(2)
