@@ -371,11 +371,10 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
         DAO_TRY(c->dalloc(&c->D.col16, padded));
         DAO_TRY(c->dalloc(&c->D.val16, padded));
     }
-    DAO_TRY(cu(build_scales(t_col, t_val, nnz, N, reinterpret_cast<unsigned*>(scale), t_dmax, c->num_sms, st),
-               "per-beamlet scales"));
+    DAO_TRY(cu(build_stats(t_rp, t_col, t_val, V, CH, N, n_ch, t_C, t_cnt, reinterpret_cast<unsigned*>(scale), t_dmax,
+                           c->num_sms, st), "transpose counts and scales"));
     DAO_TRY(cu(build_fill_d(prec, t_rp, t_col, t_val, c->D.rowptr, V, scale, c->D, st), "padded D"));
     DAO_TRY(cu(build_seg(t_rp, t_col, c->D.rowptr, V, c->beam_off_d, B, c->seg, st), "beam segments"));
-    DAO_TRY(cu(build_transpose_count(t_rp, t_col, V, CH, N, n_ch, t_C, t_cnt, st), "transpose counts"));
     // counts and the largest |D_ij| back to the host: row offsets of D^T, tau
     std::vector<int> cnt(N);
     unsigned dmax_bits = 0;
@@ -413,7 +412,8 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
         DAO_TRY(c->dalloc(&c->Dt.val16, tpadded));
         DAO_TRY(talloc(&t_tval, sizeof(float) * tpadded));
     }
-    DAO_TRY(cu(build_transpose_place(prec, t_rp, t_col, t_val, V, CH, N, n_ch, t_C, t_cnt, scale, c->Dt, t_tval, st),
+    DAO_TRY(cu(build_transpose_place(prec, t_rp, t_col, t_val, V, CH, N, n_ch, t_C, t_cnt, scale, c->Dt, t_tval,
+                                     c->num_sms, st),
                "transpose"));
     free_temps();
     float dmax = 0.f;

@@ -6,11 +6,12 @@
 //
 // The transpose keeps every row of D^T in increasing voxel order, the order a
 // sequential counting sort gives, without sorting: the voxel rows are cut into
-// chunks; C[chunk][i] counts chunk's entries of beamlet i (integer atomics, so
-// the counts are exact); a scan over chunks turns the counts into each chunk's
-// first slot in every row of D^T; then one warp per chunk walks its voxels in
-// order and places each entry at its beamlet's next slot.  Entries of one voxel
-// have distinct beamlets, so the lanes of a warp never share a slot counter.
+// chunks; C[chunk][i] counts chunk's entries of beamlet i (shared-memory
+// integer atomics, so the counts are exact); a scan over chunks turns the
+// counts into each chunk's first slot in every row of D^T; then one warp per
+// chunk walks its entries in CSR order and places each at its beamlet's next
+// slot, lanes that share a beamlet taking consecutive slots in lane order.
+#include <algorithm>
 #include <climits>
 
 #include <cuda_bf16.h>
@@ -28,14 +29,6 @@ template <int PREC>
 __device__ __forceinline__ unsigned short to16(float r) {
     if (PREC == DAO_PREC_FP16) return __half_as_ushort(__float2half_rn(r));
     return __bfloat16_as_ushort(__float2bfloat16_rn(r));
-}
-
-// s_i = max_j |D_ij| as the bits of a non-negative float (ordered like the
-// floats), and the overall maximum for the pricing tolerance.
-__global__ void k_colmax(const int* __restrict__ col, const float* __restrict__ val, int64_t nnz,
-                         unsigned* __restrict__ smax) {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
-        atomicMax(&smax[col[p]], __float_as_uint(fabsf(val[p])));
 }
 
 // scale_i = s_i, or 1 for a beamlet without entries; dmax = max_i s_i.
@@ -104,58 +97,131 @@ __global__ void k_seg(const int64_t* __restrict__ rp, const int* __restrict__ co
     seg[(size_t)B * V + j] = q0 + len;
 }
 
-// C[chunk][i] += entries of beamlet i in the chunk's voxel rows (warp per row).
-__global__ void k_chunk_count(const int64_t* __restrict__ rp, const int* __restrict__ col, int V, int CH, int N,
-                              int* __restrict__ C) {
-    const int lane = threadIdx.x & 31;
-    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (j >= V) return;
-    int* Cc = C + (size_t)(j / CH) * N;
-    for (int64_t p = rp[j] + lane; p < rp[j + 1]; p += 32) atomicAdd(&Cc[col[p]], 1);
-}
+// Beamlet counters of one block live in shared memory for a tile of TILE_N
+// beamlets; a matrix with more beamlets runs a grid of (chunk, tile) blocks.
+constexpr int TILE_N = 12288;
+constexpr int STATS_T = 256;
 
-// cnt[i] = entries of beamlet i (column of D, row of D^T).
-__global__ void k_col_total(const int* __restrict__ C, int n_ch, int N, int* __restrict__ cnt) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    int s = 0;
-    for (int ch = 0; ch < n_ch; ++ch) s += C[(size_t)ch * N + i];
-    cnt[i] = s;
-}
-
-// C[chunk][i] becomes the chunk's first slot in row i of D^T.
-__global__ void k_chunk_scan(int* __restrict__ C, int n_ch, int N, const int* __restrict__ trow) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    int run = trow[i];
-    for (int ch = 0; ch < n_ch; ++ch) {
-        const int t = C[(size_t)ch * N + i];
-        C[(size_t)ch * N + i] = run;
-        run += t;
-    }
-}
-
-// One warp per chunk, voxel rows in increasing order: each entry goes to its
-// beamlet's next slot.
-__global__ void k_chunk_place(const int64_t* __restrict__ rp, const int* __restrict__ col,
-                              const float* __restrict__ val, int V, int CH, int N, int n_ch, int* __restrict__ C,
-                              int* __restrict__ tcol, float* __restrict__ tval) {
-    const int lane = threadIdx.x & 31;
-    const int ch = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (ch >= n_ch) return;
-    int* Cc = C + (size_t)ch * N;
-    const int j1 = min(V, (ch + 1) * CH);
-    for (int j = ch * CH; j < j1; ++j) {
-        for (int64_t p = rp[j] + lane; p < rp[j + 1]; p += 32) {
-            const int c = col[p];
-            const int pos = Cc[c];
-            Cc[c] = pos + 1;
-            tcol[pos] = j;
-            tval[pos] = val[p];
+// Per (chunk, beamlet tile): C[chunk][i] = the chunk's entries of beamlet i,
+// counted in shared memory, and s_i = max |D_ij| over them folded into smax
+// (bits of a non-negative float, ordered like the floats) with one atomicMax
+// per beamlet the chunk touches.
+__global__ void __launch_bounds__(STATS_T) k_chunk_stats(const int64_t* __restrict__ rp, const int* __restrict__ col,
+                                                         const float* __restrict__ val, int V, int CH, int N,
+                                                         int* __restrict__ C, unsigned* __restrict__ smax) {
+    extern __shared__ unsigned s_stats[];
+    const int ch = blockIdx.x, i0 = blockIdx.y * TILE_N;
+    const int nt = min(TILE_N, N - i0);
+    unsigned* s_cnt = s_stats;
+    unsigned* s_mx = s_stats + nt;
+    for (int t = threadIdx.x; t < 2 * nt; t += STATS_T) s_stats[t] = 0u;
+    __syncthreads();
+    const int64_t p0 = rp[(int64_t)ch * CH], p1 = rp[min((int64_t)V, (int64_t)(ch + 1) * CH)];
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += STATS_T) {
+        const int c = col[p] - i0;
+        if (c >= 0 && c < nt) {
+            atomicAdd(&s_cnt[c], 1u);
+            atomicMax(&s_mx[c], __float_as_uint(fabsf(val[p])));
         }
-        __syncwarp();
+    }
+    __syncthreads();
+    int* Cc = C + (size_t)ch * N + i0;
+    for (int t = threadIdx.x; t < nt; t += STATS_T) {
+        const unsigned n = s_cnt[t];
+        Cc[t] = (int)n;
+        if (n) atomicMax(&smax[i0 + t], s_mx[t]);
     }
 }
+
+// Column i of C becomes each chunk's first slot relative to the start of row
+// i of D^T, and cnt[i] its total.  Block of 32 beamlets x 32 chunk segments:
+// segment sums, a scan over the segments in shared memory, then each segment
+// rewritten from its offset.
+__global__ void __launch_bounds__(1024) k_chunk_scan(int* __restrict__ C, int n_ch, int N, int* __restrict__ cnt) {
+    __shared__ int s_sum[32][33];
+    const int x = threadIdx.x, y = threadIdx.y;
+    const int i = blockIdx.x * 32 + x;
+    const int per = (n_ch + 31) / 32;
+    const int c0 = min(n_ch, y * per), c1 = min(n_ch, c0 + per);
+    int sum = 0;
+    if (i < N)
+        for (int ch = c0; ch < c1; ++ch) sum += C[(size_t)ch * N + i];
+    s_sum[y][x] = sum;
+    __syncthreads();
+    int run = 0;
+    for (int t = 0; t < y; ++t) run += s_sum[t][x];
+    if (i < N) {
+        if (y == 31) cnt[i] = run + sum;
+        for (int ch = c0; ch < c1; ++ch) {
+            const int v = C[(size_t)ch * N + i];
+            C[(size_t)ch * N + i] = run;
+            run += v;
+        }
+    }
+}
+
+// Placement: one warp per (chunk, beamlet tile of width tw) walks the chunk's
+// voxel rows in order, the lanes over a row's entries (distinct beamlets, so no
+// two lanes share a counter).  The next slot of each beamlet of the tile is a
+// shared-memory counter (row start of D^T + the chunk's offset).  Row starts
+// (PL_ROWS rows at a time) and entries (PL_STG at a time) are staged in shared
+// memory with coalesced loads; a row that straddles two stages is finished in
+// the second.  The walk is a chain of shared-memory round trips per row, so
+// the tiles are made narrow enough for about 24 warps per SM.
+constexpr int PL_ROWS = 256, PL_STG = 512;
+
+__global__ void __launch_bounds__(32) k_chunk_place(const int64_t* __restrict__ rp, const int* __restrict__ col,
+                                                    const float* __restrict__ val, int V, int CH, int N, int tw,
+                                                    const int* __restrict__ C, const int* __restrict__ trow,
+                                                    int* __restrict__ tcol, float* __restrict__ tval) {
+    extern __shared__ int s_pl[];
+    const int ch = blockIdx.x, i0 = blockIdx.y * tw;
+    const int nt = min(tw, N - i0);
+    int* s_slot = s_pl;                   // nt next slots
+    int* s_row = s_slot + nt;             // PL_ROWS + 1 row starts, relative to the window's first entry
+    int* s_col = s_row + PL_ROWS + 1;     // PL_STG staged entries: beamlet - i0
+    float* s_val = reinterpret_cast<float*>(s_col + PL_STG);
+    const int lane = threadIdx.x;
+    for (int t = lane; t < nt; t += 32) s_slot[t] = trow[i0 + t] + C[(size_t)ch * N + i0 + t];
+    const int j0 = ch * CH, j1 = (int)min((int64_t)V, (int64_t)j0 + CH);
+    for (int w0 = j0; w0 < j1; w0 += PL_ROWS) {
+        const int nr = min(PL_ROWS, j1 - w0);
+        const int64_t e0 = rp[w0];
+        __syncwarp();
+        for (int r = lane; r <= nr; r += 32) s_row[r] = (int)(rp[w0 + r] - e0);
+        __syncwarp();
+        const int ne = s_row[nr];
+        int r = 0;                        // next row to place (may have started in the previous stage)
+        for (int s0 = 0; s0 < ne; s0 += PL_STG) {
+            const int s1 = min(ne, s0 + PL_STG);
+            __syncwarp();
+#pragma unroll 8
+            for (int q = s0 + lane; q < s1; q += 32) {
+                s_col[q - s0] = col[e0 + q] - i0;
+                s_val[q - s0] = val[e0 + q];
+            }
+            __syncwarp();
+            // rows with entries in [s0, s1); the last may continue in the next stage
+            while (r < nr && s_row[r] < s1) {
+                const int a = max(s_row[r], s0), b = min(s_row[r + 1], s1);
+                for (int q = a + lane; q < b; q += 32) {
+                    const int c = s_col[q - s0];
+                    if (c >= 0 && c < nt) {
+                        const int pos = s_slot[c];
+                        s_slot[c] = pos + 1;
+                        tcol[pos] = w0 + r;
+                        tval[pos] = s_val[q - s0];
+                    }
+                }
+                __syncwarp();
+                if (s_row[r + 1] > s1) break;   // continues in the next stage
+                ++r;
+            }
+        }
+    }
+}
+
+size_t place_smem(int nt) { return sizeof(int) * ((size_t)nt + PL_ROWS + 1 + 2 * PL_STG); }
 
 // Padding of the rows of D^T: the row's last voxel with value 0.
 __global__ void k_pad_t(const int* __restrict__ trow, const int* __restrict__ cnt, int N, int* __restrict__ tcol,
@@ -329,12 +395,16 @@ cudaError_t build_check(const int64_t* rp, const int* col, const float* val, int
     return cudaGetLastError();
 }
 
-cudaError_t build_scales(const int* col, const float* val, int64_t nnz, int N, unsigned* smax, unsigned* dmax,
-                         int num_sms, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(smax, 0, sizeof(unsigned) * N, s);
+cudaError_t build_stats(const int64_t* rp, const int* col, const float* val, int V, int CH, int N, int n_ch,
+                        int* C, int* cnt, unsigned* smax, unsigned* dmax, int num_sms, cudaStream_t s) {
+    const int n_tile = (N + TILE_N - 1) / TILE_N;
+    const size_t sm_stats = 2 * sizeof(unsigned) * (size_t)std::min(N, TILE_N);
+    cudaError_t e = cudaFuncSetAttribute(k_chunk_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stats);
+    if (e == cudaSuccess) e = cudaMemsetAsync(smax, 0, sizeof(unsigned) * N, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(dmax, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    if (nnz > 0) k_colmax<<<num_sms * 8, 256, 0, s>>>(col, val, nnz, smax);
+    k_chunk_stats<<<dim3(n_ch, n_tile), STATS_T, sm_stats, s>>>(rp, col, val, V, CH, N, C, smax);
+    k_chunk_scan<<<(N + 31) / 32, dim3(32, 32), 0, s>>>(C, n_ch, N, cnt);
     k_scale_fix<<<num_sms, 256, 0, s>>>(smax, N, dmax);
     return cudaGetLastError();
 }
@@ -357,20 +427,16 @@ cudaError_t build_seg(const int64_t* rp, const int* col, const int* prow, int V,
     return cudaGetLastError();
 }
 
-cudaError_t build_transpose_count(const int64_t* rp, const int* col, int V, int CH, int N, int n_ch, int* C, int* cnt,
-                                  cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(C, 0, sizeof(int) * (size_t)n_ch * N, s);
-    if (e != cudaSuccess) return e;
-    k_chunk_count<<<blocks_for((int64_t)V * 32, 256), 256, 0, s>>>(rp, col, V, CH, N, C);
-    k_col_total<<<blocks_for(N, 256), 256, 0, s>>>(C, n_ch, N, cnt);
-    return cudaGetLastError();
-}
-
 cudaError_t build_transpose_place(int prec, const int64_t* rp, const int* col, const float* val, int V, int CH, int N,
                                   int n_ch, int* C, const int* cnt, const float* scale, DevCSR& Dt, float* tval,
-                                  cudaStream_t s) {
-    k_chunk_scan<<<blocks_for(N, 256), 256, 0, s>>>(C, n_ch, N, Dt.rowptr);
-    k_chunk_place<<<blocks_for((int64_t)n_ch * 32, 256), 256, 0, s>>>(rp, col, val, V, CH, N, n_ch, C, Dt.col, tval);
+                                  int num_sms, cudaStream_t s) {
+    const int split = std::max(1, std::min(16, (24 * num_sms + n_ch - 1) / n_ch));
+    const int tw = std::min(TILE_N, (N + split - 1) / split);
+    const int n_tile = (N + tw - 1) / tw;
+    const size_t sm_place = place_smem(tw);
+    cudaError_t e = cudaFuncSetAttribute(k_chunk_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_place);
+    if (e != cudaSuccess) return e;
+    k_chunk_place<<<dim3(n_ch, n_tile), 32, sm_place, s>>>(rp, col, val, V, CH, N, tw, C, Dt.rowptr, Dt.col, tval);
     k_pad_t<<<blocks_for((int64_t)N * 32, 256), 256, 0, s>>>(Dt.rowptr, cnt, N, Dt.col, tval);
     if (prec == DAO_PREC_FP16)
         k_quant_t<DAO_PREC_FP16><<<blocks_for((int64_t)N * 32, 256), 256, 0, s>>>(tval, Dt.rowptr, N, scale,

@@ -232,17 +232,17 @@ int check_scan_blocks(int V);
 cudaError_t build_check(const int64_t* rp, const int* col, const float* val, int64_t nnz, int V, int N,
                         const int* label, int S, int pad, int64_t* plen, int64_t* bsum, uint8_t* vs8, int* prow,
                         BuildCheck* chk, cudaStream_t s);
-cudaError_t build_scales(const int* col, const float* val, int64_t nnz, int N, unsigned* smax, unsigned* dmax,
-                         int num_sms, cudaStream_t s);
+// Chunk counts C (relative slots after the call), entries per beamlet cnt,
+// per-beamlet scales (smax, in place) and the largest |D_ij| (dmax).
+cudaError_t build_stats(const int64_t* rp, const int* col, const float* val, int V, int CH, int N, int n_ch,
+                        int* C, int* cnt, unsigned* smax, unsigned* dmax, int num_sms, cudaStream_t s);
 cudaError_t build_fill_d(int prec, const int64_t* rp, const int* col, const float* val, const int* prow, int V,
                          const float* scale, DevCSR& D, cudaStream_t s);
 cudaError_t build_seg(const int64_t* rp, const int* col, const int* prow, int V, const int* beam_off, int B, int* seg,
                       cudaStream_t s);
-cudaError_t build_transpose_count(const int64_t* rp, const int* col, int V, int CH, int N, int n_ch, int* C, int* cnt,
-                                  cudaStream_t s);
 cudaError_t build_transpose_place(int prec, const int64_t* rp, const int* col, const float* val, int V, int CH, int N,
                                   int n_ch, int* C, const int* cnt, const float* scale, DevCSR& Dt, float* tval,
-                                  cudaStream_t s);
+                                  int num_sms, cudaStream_t s);
 
 // The whole master solve as one cooperative launch (GP blocks), after
 // launch_master_init; dynamic shared memory per master_persist_smem.

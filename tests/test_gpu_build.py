@@ -5,13 +5,15 @@ fault: the lowest bad CSR row (its first bad entry), then the lowest bad
 structure label.  The process-wide memory caches stay usable after a refused
 create.  The padded row offsets come from a device scan; a matrix with more
 than 4M voxel rows takes the scan of block totals through several passes, and
-its stored entry count and dose must still be exact.
+its stored entry count and dose must still be exact.  The transpose counts
+beamlets in shared-memory tiles of 12288: a matrix with more beamlets than
+one tile must give the same D^T products as the oracle.
 """
 import numpy as np
 import pytest
 
 import oracle as O
-from _helpers import U32, ArrayCase, need_cuda, random_case, sum_abs_rows
+from _helpers import U32, ArrayCase, need_cuda, random_case, sum_abs_cols, sum_abs_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -155,3 +157,20 @@ def test_tiny_case_faults(torch, mutate, message):
     c = _tiny()
     mutate(c)
     assert _refused(c, torch).endswith(message)
+
+
+def test_transpose_with_more_beamlets_than_one_counter_tile(torch):
+    from paper_1003_5402_gb300 import Plan
+    case = random_case(43, 2500, rows=[300, 210], cols=[32, 31], mean_row=60.0)   # 16110 beamlets
+    assert case.n_beamlets > 12288
+    rng = np.random.default_rng(4)
+    pi = rng.normal(size=case.n_voxels).astype(np.float32)
+    with Plan(case, stream=torch.cuda.current_stream().cuda_stream) as plan:
+        pd = torch.from_numpy(pi).cuda()
+        wd = torch.empty(case.n_beamlets, dtype=torch.float32, device="cuda")
+        plan.k_beamlet_prices(pd, wd)
+        w = wd.cpu().numpy().astype(np.float64)
+    ref = O.beamlet_prices(O.csr64(case), pi.astype(np.float64))
+    bound, n = sum_abs_cols(case, pi)
+    allowed = (np.ceil(n / 128.0) * 4 + 8) * U32 * bound + U32 * np.abs(ref)
+    assert np.all(np.abs(w - ref) <= allowed)
