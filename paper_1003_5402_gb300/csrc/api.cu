@@ -98,6 +98,11 @@ struct dao_ctx {
     CGDev* cg = nullptr;             // device-side state of graph-driven solves
     std::vector<cudaGraph_t> round_graph;       // per pool size K: one column-generation round
     std::vector<cudaGraphExec_t> round_exec;
+    // persistent master: one graph for every solve, a while node over rounds
+    // whose kernels read the pool size from the device
+    cudaGraph_t solve_graph = nullptr;
+    cudaGraphExec_t solve_exec = nullptr;
+    bool solve_tried = false;
     double* F_part = nullptr;
     int F_blocks = 0;
     double* F_dev = nullptr;
@@ -697,18 +702,19 @@ dao_status add_aperture(dao_ctx* c, int beam, const int32_t* lr, double* F) {
 dao_status build_round_graph_persist(dao_ctx* c, int K) {
     cudaStream_t cs = c->stream;
     int n = 0;
-    const int* skip = &c->cg->done;
+    const int* stop = &c->cg->stop;  // D^T and pricing skip once the solve has stopped
+    const int* skip = &c->cg->idle;  // the master solve skips a round that added nothing
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     auto check = [&](cudaError_t x) {
         if (e == cudaSuccess && x != cudaSuccess) e = x;
     };
     if (e == cudaSuccess) {
-        check(launch_dt(c->Dt, c->pi, c->w, skip, cs, &n));
-        check(launch_price_rows(c->w, c->row_info, c->R_tot, c->row_v, c->row_lr, skip, cs, &n));
+        check(launch_dt(c->Dt, c->pi, c->w, stop, cs, &n));
+        check(launch_price_rows(c->w, c->row_info, c->R_tot, c->row_v, c->row_lr, stop, cs, &n));
         check(launch_price_commit(c->row_v, c->beam_row0_d, c->B, c->price, c->row_lr, c->rows_d, c->cols_d, c->tau,
-                                  K, 2 * c->max_rows, c->ap_beam, c->ap_lr, c->mask, c->cg, cs, &n));
+                                  K, 2 * c->max_rows, c->ap_beam, c->ap_lr, c->mask, c->cg, 0, 0, cs, &n));
         check(launch_column_dev(c->D, c->seg, c->ap_beam, K, c->beam_off_d, c->rows_d, c->cols_d, c->max_nb, c->mask,
-                                c->slab + (size_t)(K - 1) * c->ld, 1, c->cg, c->num_sms, cs, &n));
+                                c->slab, c->ld, c->cg, c->num_sms, cs, &n));
         check(launch_master_persist(c->mb, c->slab, c->ld, c->V, K, c->vstruct, c->tf, c->S, c->opt.max_master_iters,
                                     c->opt.master_tol, skip, c->z, c->pi, c->cg, cs, &n));
         cudaGraph_t g = nullptr;
@@ -729,13 +735,87 @@ dao_status build_round_graph_persist(dao_ctx* c, int K) {
     return fail(DAO_ECUDA, std::string("building the round graph: ") + cudaGetErrorString(e));
 }
 
+// Every round of a solve in one graph: a while node whose body is
+// ROUNDS_PER_ITER rounds (D^T, row scans, argmin + commit, column, persistent
+// master solve), the kernels reading the pool size from cg->K.  The commit
+// kernel ends the loop when pricing stops the solve or the pool reaches
+// cg->K_end.  Returns false (and leaves nothing behind) where the driver does
+// not take this form.
+constexpr int ROUNDS_PER_ITER = 4;
+
+bool build_solve_graph_persist(dao_ctx* c) {
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaStream_t cs = c->stream;
+    int n = 0;
+    const int* stop = &c->cg->stop;
+    const int* skip = &c->cg->idle;
+    cudaError_t e = cudaSuccess;
+    auto check = [&](cudaError_t x) {
+        if (e == cudaSuccess && x != cudaSuccess) e = x;
+    };
+    cudaGraphConditionalHandle h = 0;
+    check(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t cnode = nullptr;
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        check(cudaGraphAddNode(&cnode, g, nullptr, nullptr, 0, &cp));
+    }
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        check(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        if (e == cudaSuccess) {
+            // ROUNDS_PER_ITER rounds per iteration: the while node's relaunch costs
+            // about as much as a few kernels, and rounds after the stop return at entry
+            for (int u = 0; u < ROUNDS_PER_ITER; ++u) {
+                check(launch_dt(c->Dt, c->pi, c->w, stop, cs, &n));
+                check(launch_price_rows(c->w, c->row_info, c->R_tot, c->row_v, c->row_lr, stop, cs, &n));
+                check(launch_price_commit(c->row_v, c->beam_row0_d, c->B, c->price, c->row_lr, c->rows_d,
+                                          c->cols_d, c->tau, 0, 2 * c->max_rows, c->ap_beam, c->ap_lr, c->mask,
+                                          c->cg, h, 1, cs, &n));
+                check(launch_column_dev(c->D, c->seg, c->ap_beam, 0, c->beam_off_d, c->rows_d, c->cols_d,
+                                        c->max_nb, c->mask, c->slab, c->ld, c->cg, c->num_sms, cs, &n));
+                check(launch_master_persist(c->mb, c->slab, c->ld, c->V, 0, c->vstruct, c->tf, c->S,
+                                            c->opt.max_master_iters, c->opt.master_tol, skip, c->z, c->pi, c->cg,
+                                            cs, &n));
+            }
+            cudaGraph_t out = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(cs, &out);
+            check(e2);
+        }
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (e == cudaSuccess) check(cudaGraphInstantiate(&ex, g, 0));
+    if (e != cudaSuccess) {
+        cudaStreamCaptureStatus cst;
+        if (cudaStreamIsCapturing(cs, &cst) == cudaSuccess && cst != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(cs, &junk);
+        }
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return false;
+    }
+    c->solve_graph = g;
+    c->solve_exec = ex;
+    return true;
+}
+
 dao_status build_round_graph(dao_ctx* c, int K) {
     if (c->mb.GP > 0) return build_round_graph_persist(c, K);
     cudaGraph_t g = nullptr;
     DAO_CU(cudaGraphCreate(&g, 0));
     cudaStream_t cs = c->stream;
     int n = 0;
-    const int* skip = &c->cg->done;
+    const int* stop = &c->cg->stop;
+    const int* skip = &c->cg->idle;
     cudaError_t e = cudaSuccess;
     cudaGraphConditionalHandle h = 0;
     std::vector<cudaGraphNode_t> deps;
@@ -747,12 +827,13 @@ dao_status build_round_graph(dao_ctx* c, int K) {
     if (e == cudaSuccess) {
         check(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         if (e == cudaSuccess) {
-            check(launch_dt(c->Dt, c->pi, c->w, skip, cs, &n));
-            check(launch_price_rows(c->w, c->row_info, c->R_tot, c->row_v, c->row_lr, skip, cs, &n));
+            check(launch_dt(c->Dt, c->pi, c->w, stop, cs, &n));
+            check(launch_price_rows(c->w, c->row_info, c->R_tot, c->row_v, c->row_lr, stop, cs, &n));
             check(launch_price_commit(c->row_v, c->beam_row0_d, c->B, c->price, c->row_lr, c->rows_d, c->cols_d,
-                                      c->tau, K, 2 * c->max_rows, c->ap_beam, c->ap_lr, c->mask, c->cg, cs, &n));
+                                      c->tau, K, 2 * c->max_rows, c->ap_beam, c->ap_lr, c->mask, c->cg, 0, 0, cs,
+                                      &n));
             check(launch_column_dev(c->D, c->seg, c->ap_beam, K, c->beam_off_d, c->rows_d, c->cols_d, c->max_nb,
-                                    c->mask, c->slab + (size_t)(K - 1) * c->ld, 1, c->cg, c->num_sms, cs, &n));
+                                    c->mask, c->slab, c->ld, c->cg, c->num_sms, cs, &n));
             check(launch_master_init(c->mb.st, K, skip, h, 1, cs, &n));
             cudaStreamCaptureStatus cst;
             const cudaGraphNode_t* d = nullptr;
@@ -825,12 +906,32 @@ struct GraphSolve {
 dao_status solve_graph_begin(dao_ctx* c, int n_apertures, GraphSolve* gs) {
     gs->K0 = c->K;
     gs->K1 = std::min(c->K_cap, c->K + n_apertures);
-    for (int k = gs->K0 + 1; k <= gs->K1; ++k)
-        if (c->round_exec[k] == nullptr) DAO_TRY(build_round_graph(c, k));
+    if (c->mb.GP > 0 && !c->solve_tried) {
+        c->solve_tried = true;
+        build_solve_graph_persist(c);  // else: one graph per round below
+    }
+    if (c->solve_exec == nullptr)
+        for (int k = gs->K0 + 1; k <= gs->K1; ++k)
+            if (c->round_exec[k] == nullptr) DAO_TRY(build_round_graph(c, k));
     CGDev* h = reinterpret_cast<CGDev*>(c->pinned + c->off_cg);
     h->K = gs->K0;
     h->done = 0;
-    DAO_CU(cudaMemcpyAsync(c->cg, h, 2 * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    h->K_end = gs->K1;
+    h->stop = 0;
+    h->idle = 0;
+    DAO_CU(cudaMemcpyAsync(c->cg, h, offsetof(CGDev, pad), cudaMemcpyHostToDevice, c->stream));
+    return DAO_OK;
+}
+
+// Round k (K0 < k <= K1) of a prepared solve; with the single solve graph the
+// first round launches every round.
+dao_status launch_round(dao_ctx* c, const GraphSolve& gs, int k) {
+    if (k <= gs.K0 || k > gs.K1) return DAO_OK;
+    if (c->solve_exec != nullptr) {
+        if (k == gs.K0 + 1) DAO_CU(cudaGraphLaunch(c->solve_exec, c->stream));
+        return DAO_OK;
+    }
+    DAO_CU(cudaGraphLaunch(c->round_exec[k], c->stream));
     return DAO_OK;
 }
 
@@ -860,8 +961,15 @@ dao_status solve_graph_end(dao_ctx* c, const GraphSolve& gs, int n_apertures, in
     // the persistent solve, or init, the final pass, the record and, per pair of
     // evaluations, pass, curvature and reduce + step
     const bool persist = c->mb.GP > 0;
-    // every queued round launches its kernels (a stopped solve's rounds return at entry)
-    c->launches_i += (persist ? 5 : 7) * (K1 - K0);
+    if (c->solve_exec != nullptr) {
+        // the while node ran the rounds that grew the pool and, when pricing
+        // stopped the solve, the round that found it, ROUNDS_PER_ITER to an iteration
+        const int rounds = K - K0 + (h->done != 0 ? 1 : 0);
+        c->launches_i += 5 * ROUNDS_PER_ITER * ((rounds + ROUNDS_PER_ITER - 1) / ROUNDS_PER_ITER);
+    } else {
+        // every queued round launches its kernels (a stopped solve's rounds return at entry)
+        c->launches_i += (persist ? 5 : 7) * (K1 - K0);
+    }
     for (int k = K0; k < K; ++k) {
         if (!persist) c->launches_i += 6 * ((h->evals[k] + 1) / 2);  // two evaluations per while iteration
         c->stat_evals.push_back(h->evals[k]);
@@ -879,13 +987,18 @@ dao_status solve_graph_end(dao_ctx* c, const GraphSolve& gs, int n_apertures, in
 dao_status solve_graph(dao_ctx* c, int n_apertures, int32_t* n_done, double* trace, dao_status* result) {
     GraphSolve gs;
     DAO_TRY(solve_graph_begin(c, n_apertures, &gs));
-    for (int k = gs.K0 + 1; k <= gs.K1; ++k) DAO_CU(cudaGraphLaunch(c->round_exec[k], c->stream));
+    for (int k = gs.K0 + 1; k <= gs.K1; ++k) DAO_TRY(launch_round(c, gs, k));
     return solve_graph_end(c, gs, n_apertures, n_done, trace, result);
 }
 
 // Round graphs embed the launch shapes they were captured with: drop them when
 // the shapes change.
 void drop_round_graphs(dao_ctx* c) {
+    if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+    if (c->solve_graph) cudaGraphDestroy(c->solve_graph);
+    c->solve_exec = nullptr;
+    c->solve_graph = nullptr;
+    c->solve_tried = false;
     for (size_t k = 0; k < c->round_exec.size(); ++k) {
         if (c->round_exec[k]) cudaGraphExecDestroy(c->round_exec[k]);
         if (c->round_graph[k]) cudaGraphDestroy(c->round_graph[k]);
@@ -925,7 +1038,7 @@ dao_status solve_async_begin(dao_ctx* c, int n_apertures, cudaEvent_t done) {
     if (!c->opt.use_graphs || c->prof_on) return fail(DAO_EINVAL, "asynchronous solve needs use_graphs, profiling off");
     GraphSolve gs;
     DAO_TRY(solve_graph_begin(c, n_apertures, &gs));
-    for (int k = gs.K0 + 1; k <= gs.K1; ++k) DAO_CU(cudaGraphLaunch(c->round_exec[k], c->stream));
+    for (int k = gs.K0 + 1; k <= gs.K1; ++k) DAO_TRY(launch_round(c, gs, k));
     DAO_CU(cudaEventRecord(done, c->stream));
     c->async_K0 = gs.K0;
     c->async_K1 = gs.K1;
@@ -1014,10 +1127,7 @@ void dao_destroy(dao_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    for (cudaGraphExec_t ex : c->round_exec)
-        if (ex) cudaGraphExecDestroy(ex);
-    for (cudaGraph_t g : c->round_graph)
-        if (g) cudaGraphDestroy(g);
+    drop_round_graphs(c);
     // back to the process-wide caches, ordered after the context's last work
     for (void* p : c->dev_allocs) pool_free(p, c->stream);
     for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
@@ -1455,7 +1565,7 @@ dao_status dao_batch_solve(dao_ctx* const* ctxs, int32_t n, int32_t n_apertures,
         for (int i = 0; i < n; ++i) {
             if (!run[i]) continue;
             const int k = gs[i].K0 + 1 + r;
-            if (k <= gs[i].K1) DAO_CU(cudaGraphLaunch(ctxs[i]->round_exec[k], ctxs[i]->stream));
+            DAO_TRY(launch_round(ctxs[i], gs[i], k));
         }
     for (int i = 0; i < n; ++i) {
         if (!run[i]) continue;

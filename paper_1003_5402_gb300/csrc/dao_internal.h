@@ -105,7 +105,10 @@ struct PriceDev {
 struct CGDev {
     int K;                // pool size reached
     int done;             // 0 running, 1 no negative reduced cost, 2 duplicate aperture
-    int pad[2];
+    int K_end;            // a device-driven solve stops when the pool reaches this size
+    int stop;             // done set or K_end reached: later rounds skip D^T and pricing
+    int idle;             // this round added no aperture: its column and master solve skip
+    int pad[3];
     double trace[KMAX];   // F after each added aperture
     double res[KMAX];     // final KKT residual of each master solve
     double tol[KMAX];     // its absolute tolerance
@@ -131,9 +134,11 @@ cudaError_t launch_column(const DevCSR& D, const int* seg_lo, const int* seg_hi,
                           int n_beamlets_b, const float* mask, float* out, int stride, int num_sms,
                           cudaStream_t stream, int* launches);
 
-// a4 for the aperture the device just committed at pool index K-1 (graph path).
+// a4 for the aperture the device just committed at pool index K-1 (graph
+// path), written to column K-1 of the slab (column stride ld).  K = 0: the
+// pool size is read from cg->K when the kernel runs.
 cudaError_t launch_column_dev(const DevCSR& D, const int* seg, const int* ap_beam, int K, const int* beam_off,
-                              const int* rows, const int* cols, int max_nb, const float* mask, float* out, int stride,
+                              const int* rows, const int* cols, int max_nb, const float* mask, float* slab, int ld,
                               const CGDev* cg, int num_sms, cudaStream_t stream, int* launches);
 
 // x_i = sum_{k in K_i} y_k (Eq. 7) from the aperture table.
@@ -150,13 +155,13 @@ cudaError_t launch_price(const float* w, const int4* row_info, int n_rows, const
 // Graph path: the row scans, then the beam argmin fused with the commit.
 cudaError_t launch_price_rows(const float* w, const int4* row_info, int n_rows, double* row_v, int2* row_lr,
                               const int* skip, cudaStream_t stream, int* launches);
+// K = 0: the new pool size is cg->K + 1 when the kernel runs.  Sets cg->idle
+// (0 when it added an aperture) and cg->stop (done, or the pool reached
+// cg->K_end).  use_cond: the kernel sets the while-node handle to !stop.
 cudaError_t launch_price_commit(const double* row_v, const int* beam_row0, int n_beams, PriceDev* pr,
                                 const int2* row_lr, const int* rows, const int* cols, double tau, int K, int lr_stride,
-                                int* ap_beam, int* ap_lr, float* mask, CGDev* cg, cudaStream_t stream,
-                                int* launches);
-cudaError_t launch_commit(const PriceDev* pr, const int2* row_lr, const int* beam_row0, const int* rows,
-                          const int* cols, double tau, int K, int lr_stride, int* ap_beam, int* ap_lr,
-                          float* mask, CGDev* cg, cudaStream_t stream, int* launches);
+                                int* ap_beam, int* ap_lr, float* mask, CGDev* cg, cudaGraphConditionalHandle cond,
+                                int use_cond, cudaStream_t stream, int* launches);
 
 // a5: projected-Newton master problem kernels.
 // Counters of the grid barrier of the persistent master solve (zeroed memory;
@@ -184,8 +189,8 @@ struct MasterBuffers {
     CUtensorMap tmap[KMAX / 4 + 1];  // slab tile maps, indexed by columns / 4
 };
 enum { PASS_EVAL = 0, PASS_FINAL = 1, PASS_TIMING = 2 };
-int master_kw(int K);
-int master_lanes(int K);
+__host__ __device__ int master_kw(int K);
+__host__ __device__ int master_lanes(int K);
 int master_grid(int V, int num_sms, int K);
 int master_grid_max(int num_sms);
 int master_hess_grid(int num_sms);
@@ -249,7 +254,8 @@ cudaError_t build_transpose_place(int prec, const int64_t* rp, const int* col, c
 size_t master_persist_smem(int V, int G);
 int master_persist_grid(int V, int num_sms);
 // Includes k_master_init's warm start, writes z and pi of the final point, and
-// (cg != nullptr) the round's record.
+// (cg != nullptr) the round's record.  K = 0: the pool size is read from
+// cg->K when the kernel runs.
 cudaError_t launch_master_persist(const MasterBuffers& mb, const float* slab, int ld, int V, int K,
                                   const uint8_t* vstruct, const StructTermsF* tf, int S, int max_iter, double tol_rel,
                                   const int* skip, float* z_out, float* pi_out, CGDev* cg, cudaStream_t stream,

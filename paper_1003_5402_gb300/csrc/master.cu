@@ -153,7 +153,7 @@ __global__ void k_master_init(MasterDev* __restrict__ st, int K, const int* __re
 
 // Graph path: keep the statistics of the master solve that just finished.
 __global__ void k_cg_record(const MasterDev* __restrict__ st, CGDev* __restrict__ cg, int K) {
-    if (threadIdx.x != 0 || cg->done) return;
+    if (threadIdx.x != 0 || cg->idle) return;
     cg->trace[K - 1] = st->F;
     cg->res[K - 1] = st->res;
     cg->tol[K - 1] = st->tol;
@@ -936,6 +936,12 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
                                                        double tol_rel, double sigma, const int* __restrict__ skip,
                                                        float* __restrict__ z_out, float* __restrict__ pi_out,
                                                        CGDev* __restrict__ cg) {
+    if (K <= 0) {  // pool size from the device (one graph for every round); KW sets the layout below
+        K = __ldcg(&cg->K);
+        KP = (K + 3) / 4 * 4;
+        KW = master_kw(K);
+        NV = master_lanes(K);
+    }
     extern __shared__ __align__(16) float pm[];
     int* s_act = reinterpret_cast<int*>(pm);          // [PW][capw] voxel indices
     float* s_hv = pm + PW * capw;                     // [PW][capw] h
@@ -1250,7 +1256,7 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
 
 }  // namespace
 
-int master_kw(int K) {
+__host__ __device__ int master_kw(int K) {
     const int KP = (K + 3) / 4 * 4;
     int kw = KP < 4 ? 4 : KP;
     if (((kw / 4) & 1) == 0) kw += 4;  // odd float4 count per row: conflict-free row-per-thread loads
@@ -1267,7 +1273,7 @@ size_t master_hess_smem(int K, int n_tiles) {
            2 * CH * sizeof(float);
 }
 
-int master_lanes(int K) {
+__host__ __device__ int master_lanes(int K) {
     const int KP = (K + 3) / 4 * 4;
     const int KB = KP / 4;
     const int nb = KB * (KB + 1) / 2;
@@ -1375,10 +1381,11 @@ cudaError_t launch_master_persist(const MasterBuffers& mb, const float* slab, in
                                   int* launches) {
     const int G = mb.GP;
     if (G < 1) return cudaErrorInvalidConfiguration;
-    const int KP = (K + 3) / 4 * 4;
+    if (K <= 0 && cg == nullptr) return cudaErrorInvalidValue;
+    const int KP = K > 0 ? (K + 3) / 4 * 4 : 0;
     const int n32 = (V + 31) / 32;
     const int capw = ((n32 + G - 1) / G + PW - 1) / PW * 32;
-    int KW = master_kw(K), NV = master_lanes(K), GS = mb.GH;  // partial arrays: stride GH >= G
+    int KW = K > 0 ? master_kw(K) : 0, NV = K > 0 ? master_lanes(K) : 0, GS = mb.GH;  // partial arrays: stride GH >= G
     double sigma = 1e-4;
     MasterDev* st = mb.st;
     GridBar* gb = mb.bar;

@@ -107,67 +107,34 @@ __global__ void __launch_bounds__(256) k_price_beams(const double* __restrict__ 
     }
 }
 
-// One block.  Stops the solve (done = 1) when the reduced cost is not below
-// -tau, or (done = 2) when the priced aperture equals one in the pool;
-// otherwise writes it as aperture K-1 with its open-beamlet mask.
-__global__ void __launch_bounds__(256) k_cg_commit(const PriceDev* __restrict__ pr, const int2* __restrict__ row_lr,
-                                                   const int* __restrict__ beam_row0, const int* __restrict__ rows,
-                                                   const int* __restrict__ cols, double tau, int K, int lr_stride,
-                                                   int* __restrict__ ap_beam, int* __restrict__ ap_lr,
-                                                   float* __restrict__ mask, CGDev* __restrict__ cg) {
-    __shared__ int s_dup;
-    if (cg->done) return;
-    const int tid = threadIdx.x;
-    const int b = pr->beam;
-    if (!(pr->rc < -tau)) {
-        if (tid == 0) cg->done = 1;
-        return;
-    }
-    const int R = rows[b], C = cols[b], r0 = beam_row0[b];
-    if (tid == 0) s_dup = 0;
-    __syncthreads();
-    for (int k = tid; k < K - 1; k += blockDim.x) {
-        if (ap_beam[k] != b) continue;
-        bool same = true;
-        for (int r = 0; r < R && same; ++r) {
-            const int2 lr = row_lr[r0 + r];
-            same = ap_lr[k * lr_stride + 2 * r] == lr.x && ap_lr[k * lr_stride + 2 * r + 1] == lr.y;
-        }
-        if (same) s_dup = 1;
-    }
-    __syncthreads();
-    if (s_dup) {
-        if (tid == 0) cg->done = 2;
-        return;
-    }
-    if (tid == 0) ap_beam[K - 1] = b;
-    for (int r = tid; r < R; r += blockDim.x) {
-        const int2 lr = row_lr[r0 + r];
-        ap_lr[(K - 1) * lr_stride + 2 * r] = lr.x;
-        ap_lr[(K - 1) * lr_stride + 2 * r + 1] = lr.y;
-    }
-    for (int i = tid; i < R * C; i += blockDim.x) {
-        const int2 lr = row_lr[r0 + i / C];
-        const int c = i % C;
-        mask[i] = (c >= lr.x && c < lr.y) ? 1.f : 0.f;
-    }
-    if (tid == 0) cg->K = K;
-}
-
-// k_price_beams and k_cg_commit in one block (the graph path): the beam sums
-// and their argmin, then the stop tests and the new aperture.
+// The beam sums and their argmin (as k_price_beams) in one block with the
+// stop tests and the new aperture (the graph path).
 __global__ void __launch_bounds__(256) k_price_commit(const double* __restrict__ row_v,
                                                       const int* __restrict__ beam_row0, int n_beams,
                                                       PriceDev* __restrict__ pr, const int2* __restrict__ row_lr,
                                                       const int* __restrict__ rows, const int* __restrict__ cols,
                                                       double tau, int K, int lr_stride, int* __restrict__ ap_beam,
                                                       int* __restrict__ ap_lr, float* __restrict__ mask,
-                                                      CGDev* __restrict__ cg) {
+                                                      CGDev* __restrict__ cg, cudaGraphConditionalHandle cond,
+                                                      int use_cond) {
     extern __shared__ double s_sum[];
     __shared__ int s_best, s_dup;
     __shared__ double s_rc;
-    if (cg->done) return;
     const int tid = threadIdx.x;
+    // idle: this round's column and master solve skip; stop: later rounds skip
+    // (the enclosing while node, if any, ends)
+    auto finish = [&](int idle, int stop) {
+        if (tid == 0) {
+            cg->idle = idle;
+            cg->stop = stop;
+            if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
+        }
+    };
+    if (cg->stop) {
+        finish(1, 1);
+        return;
+    }
+    if (K <= 0) K = cg->K + 1;
     for (int b = tid; b < n_beams; b += blockDim.x) {
         double t = 0.0;
         for (int r = beam_row0[b]; r < beam_row0[b + 1]; ++r) t = t + row_v[r];
@@ -188,6 +155,7 @@ __global__ void __launch_bounds__(256) k_price_commit(const double* __restrict__
     const int b = s_best;
     if (!(s_rc < -tau)) {
         if (tid == 0) cg->done = 1;
+        finish(1, 1);
         return;
     }
     const int R = rows[b], C = cols[b], r0 = beam_row0[b];
@@ -203,6 +171,7 @@ __global__ void __launch_bounds__(256) k_price_commit(const double* __restrict__
     __syncthreads();
     if (s_dup) {
         if (tid == 0) cg->done = 2;
+        finish(1, 1);
         return;
     }
     if (tid == 0) ap_beam[K - 1] = b;
@@ -217,6 +186,7 @@ __global__ void __launch_bounds__(256) k_price_commit(const double* __restrict__
         mask[i] = (c >= lr.x && c < lr.y) ? 1.f : 0.f;
     }
     if (tid == 0) cg->K = K;
+    finish(0, K >= cg->K_end ? 1 : 0);
 }
 
 }  // namespace
@@ -231,19 +201,11 @@ cudaError_t launch_price_rows(const float* w, const int4* row_info, int n_rows, 
 
 cudaError_t launch_price_commit(const double* row_v, const int* beam_row0, int n_beams, PriceDev* pr,
                                 const int2* row_lr, const int* rows, const int* cols, double tau, int K, int lr_stride,
-                                int* ap_beam, int* ap_lr, float* mask, CGDev* cg, cudaStream_t stream,
-                                int* launches) {
+                                int* ap_beam, int* ap_lr, float* mask, CGDev* cg, cudaGraphConditionalHandle cond,
+                                int use_cond, cudaStream_t stream, int* launches) {
     k_price_commit<<<1, 256, (size_t)(n_beams > 0 ? n_beams : 1) * sizeof(double), stream>>>(
-        row_v, beam_row0, n_beams, pr, row_lr, rows, cols, tau, K, lr_stride, ap_beam, ap_lr, mask, cg);
-    ++*launches;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_commit(const PriceDev* pr, const int2* row_lr, const int* beam_row0, const int* rows,
-                          const int* cols, double tau, int K, int lr_stride, int* ap_beam, int* ap_lr, float* mask,
-                          CGDev* cg, cudaStream_t stream, int* launches) {
-    k_cg_commit<<<1, 256, 0, stream>>>(pr, row_lr, beam_row0, rows, cols, tau, K, lr_stride, ap_beam, ap_lr, mask,
-                                       cg);
+        row_v, beam_row0, n_beams, pr, row_lr, rows, cols, tau, K, lr_stride, ap_beam, ap_lr, mask, cg, cond,
+        use_cond);
     ++*launches;
     return cudaGetLastError();
 }

@@ -204,21 +204,24 @@ __global__ void __launch_bounds__(256) k_column(const int* __restrict__ col, con
     column_body<G>(col, val, seg_lo, seg_hi, V, base, smask, out, stride);
 }
 
-// The same for the aperture at pool index K-1 of the device table.
+// The same for the aperture at pool index K-1 of the device table, into
+// column K-1 of the slab (K = 0: the pool size in cg->K).
 template <int G>
 __global__ void __launch_bounds__(256) k_column_dev(const int* __restrict__ col, const float* __restrict__ val,
                                                     const int* __restrict__ seg, int V,
                                                     const int* __restrict__ ap_beam, int K,
                                                     const int* __restrict__ beam_off, const int* __restrict__ rows,
                                                     const int* __restrict__ cols, const float* __restrict__ mask,
-                                                    float* __restrict__ out, int stride, const CGDev* __restrict__ cg) {
+                                                    float* __restrict__ slab, int ld, const CGDev* __restrict__ cg) {
     extern __shared__ float smask[];
-    if (cg->done) return;
+    if (cg->idle) return;
+    if (K <= 0) K = cg->K;
     const int b = ap_beam[K - 1];
     const int nb = rows[b] * cols[b];
     for (int i = threadIdx.x; i < nb; i += blockDim.x) smask[i] = mask[i];
     __syncthreads();
-    column_body<G>(col, val, seg + (size_t)b * V, seg + (size_t)(b + 1) * V, V, beam_off[b], smask, out, stride);
+    column_body<G>(col, val, seg + (size_t)b * V, seg + (size_t)(b + 1) * V, V, beam_off[b], smask,
+                   slab + (size_t)(K - 1) * ld, 1);
 }
 
 // ---- Eq. 7 ------------------------------------------------------------------
@@ -407,16 +410,18 @@ __global__ void __launch_bounds__(256) k_column16_dev(const unsigned short* __re
                                                       const int* __restrict__ beam_off,
                                                       const int* __restrict__ rows, const int* __restrict__ cols,
                                                       const float* __restrict__ mask, const float* __restrict__ scale,
-                                                      float* __restrict__ out, int stride,
+                                                      float* __restrict__ slab, int ld,
                                                       const CGDev* __restrict__ cg) {
     extern __shared__ float smask[];
-    if (cg->done) return;
+    if (cg->idle) return;
+    if (K <= 0) K = cg->K;
     const int b = ap_beam[K - 1];
     const int nb = rows[b] * cols[b];
     const int base = beam_off[b];
     for (int i = threadIdx.x; i < nb; i += blockDim.x) smask[i] = mask[i] * scale[base + i];
     __syncthreads();
-    column16_body<G, BF>(col, val, seg + (size_t)b * V, seg + (size_t)(b + 1) * V, V, base, smask, out, stride);
+    column16_body<G, BF>(col, val, seg + (size_t)b * V, seg + (size_t)(b + 1) * V, V, base, smask,
+                         slab + (size_t)(K - 1) * ld, 1);
 }
 
 // Blocks of a grid-stride kernel that are all resident at once (every block
@@ -537,18 +542,18 @@ void column_launch(const DevCSR& D, const int* seg_lo, const int* seg_hi, int ba
 
 template <int G>
 void column_dev_launch(const DevCSR& D, const int* seg, const int* ap_beam, int K, const int* beam_off,
-                       const int* rows, const int* cols, int max_nb, const float* mask, float* out, int stride,
+                       const int* rows, const int* cols, int max_nb, const float* mask, float* slab, int ld,
                        const CGDev* cg, int grid, cudaStream_t stream) {
     const size_t sm = (size_t)max_nb * sizeof(float);
     if (D.prec == DAO_PREC_FP16)
         k_column16_dev<G, false><<<grid, 256, sm, stream>>>(D.col16, D.val16, seg, D.n_rows, ap_beam, K, beam_off,
-                                                             rows, cols, mask, D.scale, out, stride, cg);
+                                                             rows, cols, mask, D.scale, slab, ld, cg);
     else if (D.prec == DAO_PREC_BF16)
         k_column16_dev<G, true><<<grid, 256, sm, stream>>>(D.col16, D.val16, seg, D.n_rows, ap_beam, K, beam_off,
-                                                            rows, cols, mask, D.scale, out, stride, cg);
+                                                            rows, cols, mask, D.scale, slab, ld, cg);
     else
         k_column_dev<G><<<grid, 256, sm, stream>>>(D.col, D.val, seg, D.n_rows, ap_beam, K, beam_off, rows, cols,
-                                                    mask, out, stride, cg);
+                                                    mask, slab, ld, cg);
 }
 
 }  // namespace
@@ -608,20 +613,19 @@ cudaError_t launch_column(const DevCSR& D, const int* seg_lo, const int* seg_hi,
 }
 
 cudaError_t launch_column_dev(const DevCSR& D, const int* seg, const int* ap_beam, int K, const int* beam_off,
-                              const int* rows, const int* cols, int max_nb, const float* mask, float* out, int stride,
+                              const int* rows, const int* cols, int max_nb, const float* mask, float* slab, int ld,
                               const CGDev* cg, int num_sms, cudaStream_t stream, int* launches) {
     if (D.n_rows == 0) return cudaSuccess;
     const int grid = num_sms * 8;
     switch (D.tune_col_g) {
         case 4:
-            column_dev_launch<4>(D, seg, ap_beam, K, beam_off, rows, cols, max_nb, mask, out, stride, cg, grid, stream);
+            column_dev_launch<4>(D, seg, ap_beam, K, beam_off, rows, cols, max_nb, mask, slab, ld, cg, grid, stream);
             break;
         case 16:
-            column_dev_launch<16>(D, seg, ap_beam, K, beam_off, rows, cols, max_nb, mask, out, stride, cg, grid,
-                                  stream);
+            column_dev_launch<16>(D, seg, ap_beam, K, beam_off, rows, cols, max_nb, mask, slab, ld, cg, grid, stream);
             break;
         default:
-            column_dev_launch<8>(D, seg, ap_beam, K, beam_off, rows, cols, max_nb, mask, out, stride, cg, grid, stream);
+            column_dev_launch<8>(D, seg, ap_beam, K, beam_off, rows, cols, max_nb, mask, slab, ld, cg, grid, stream);
             break;
     }
     ++*launches;
