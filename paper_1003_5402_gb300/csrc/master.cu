@@ -504,15 +504,15 @@ constexpr int STEP_T = 256;
 constexpr int STEP_W = STEP_T / 32;
 static_assert(STEP_T == 256 && KMAX == 64, "the step kernel maps a 16 x 16 thread grid onto 64 x 64 entries");
 
-__device__ __forceinline__ double blk_max(double v, double* sw) {
+__device__ __forceinline__ float blk_max_f32(float v, float* sw) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
     __syncthreads();
     if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
     __syncthreads();
-    double t = sw[0];
+    float t = sw[0];
 #pragma unroll
-    for (int w = 1; w < STEP_W; ++w) t = fmax(t, sw[w]);
+    for (int w = 1; w < STEP_W; ++w) t = fmaxf(t, sw[w]);
     return t;
 }
 
@@ -527,6 +527,8 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     __shared__ float piv[KMAX];
     __shared__ float rd[KMAX];
     __shared__ float rhs[KMAX];
+    __shared__ float sg[KMAX];                          // FP32 gradient at the accepted point
+    __shared__ float swf[STEP_W];
     __shared__ int fidx[KMAX];
     __shared__ double sw[STEP_W];
     __shared__ double sw2[STEP_W];
@@ -678,6 +680,7 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
         const int idx = m * STEP_T + k;
         Lw[idx / KMAX][idx % KMAX] = hpre[m];
     }
+    if (k < KMAX) sg[k] = (float)gt;
     double d = active ? -gt : 0.0;
     __syncthreads();
     // Damped FP32 L D L^T factorisation of H_FF with the forward solve folded in,
@@ -706,11 +709,11 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
             const int i = ti + 16 * a, q = tq + 16 * b;
             Hr[a][b] = (i < nf && q <= i) ? Lw[fidx[i]][fidx[q]] : 0.f;
         }
-    const float bk = k < nf ? -(float)__ldcg(&st->g[fidx[k]]) : 0.f;
+    const float bk = k < nf ? -sg[fidx[k]] : 0.f;
     float dg = 0.f;
 #pragma unroll
     for (int a = 0; a < 4; ++a) dg = fmaxf(dg, (ti == tq) ? Hr[a][a] : 0.f);
-    const float maxdiag = (float)blk_max((double)dg, sw);
+    const float maxdiag = blk_max_f32(dg, swf);
     float lam = 1e-6f * maxdiag + 1e-30f;
     // trailing tile of this thread for a panel with nb trailing row blocks
     int tr_r = (int)((sqrtf(8.f * (float)k + 1.f) - 1.f) * 0.5f);
@@ -739,14 +742,16 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
                 const float4 a1 = *reinterpret_cast<const float4*>(&A[c0 + 1][c0]);
                 const float4 a2 = *reinterpret_cast<const float4*>(&A[c0 + 2][c0]);
                 const float4 a3 = *reinterpret_cast<const float4*>(&A[c0 + 3][c0]);
-                const float d0 = a0.x, i0 = 1.f / d0;
+                // __frcp_rn: the correctly rounded 1 / d, the value 1.f / d has,
+                // without the general division's special-case path
+                const float d0 = a0.x, i0 = __frcp_rn(d0);
                 const float l10 = a1.x * i0;
-                const float d1 = a1.y - l10 * a1.x, i1 = 1.f / d1;
+                const float d1 = a1.y - l10 * a1.x, i1 = __frcp_rn(d1);
                 const float l20 = a2.x * i0, w21 = a2.y - l10 * a2.x, l21 = w21 * i1;
-                const float d2 = a2.z - l20 * a2.x - l21 * w21, i2 = 1.f / d2;
+                const float d2 = a2.z - l20 * a2.x - l21 * w21, i2 = __frcp_rn(d2);
                 const float l30 = a3.x * i0, w31 = a3.y - l10 * a3.x, l31 = w31 * i1;
                 const float w32 = a3.z - l20 * a3.x - l21 * w31, l32 = w32 * i2;
-                const float d3 = a3.w - l30 * a3.x - l31 * w31 - l32 * w32, i3 = 1.f / d3;
+                const float d3 = a3.w - l30 * a3.x - l31 * w31 - l32 * w32, i3 = __frcp_rn(d3);
                 auto xform = [&](float4 x) {
                     float4 w;
                     w.x = x.x;
@@ -785,6 +790,10 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
                         piv[c0 + 1] = d1;
                         piv[c0 + 2] = d2;
                         piv[c0 + 3] = d3;
+                        rd[c0] = i0;
+                        rd[c0 + 1] = i1;
+                        rd[c0 + 2] = i2;
+                        rd[c0 + 3] = i3;
                     }
                 } else {
                     const float4 e = xform(*reinterpret_cast<const float4*>(&u[c0]));
@@ -803,12 +812,12 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
             }
             __syncthreads();
         }
-        const float pk = k < n4 ? piv[k] : 1.f;
-        ok = __syncthreads_and(pk > 0.f && isfinite(1.f / pk)) != 0;
+        const float pk = k < n4 ? piv[k] : 1.f, rk = k < n4 ? rd[k] : 1.f;
+        ok = __syncthreads_and(pk > 0.f && isfinite(rk)) != 0;
         lam *= 100.f;
     }
     if (ok) {
-        if (k < KMAX) rd[k] = k < nf ? 1.f / piv[k] : 0.f;
+        if (k >= nf && k < KMAX) rd[k] = 0.f;  // padding rows
         __syncthreads();
         // L^T x = D^-1 ye by warp 0 in panels of 4 rows, last panel first, with
         // L_ik = Lw_ik / d_k: x_r = (ye_r - sum_{i > r} Lw_ir x_i) / d_r; lanes own
