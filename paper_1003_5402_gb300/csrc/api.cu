@@ -76,6 +76,7 @@ struct dao_ctx {
     int* rows_d = nullptr;           // per beam: MLC rows, beamlets per row, first beamlet
     int* cols_d = nullptr;
     int* beam_off_d = nullptr;
+    int* row_cnt = nullptr;          // per MLC row: tickets of the fused D^T + row search
     int max_nb = 0;                  // largest rows * cols of a beam
 
     // column-generation state
@@ -506,6 +507,8 @@ dao_status alloc_state(dao_ctx* c) {
     c->round_exec.assign(c->K_cap + 1, nullptr);
     DAO_TRY(c->dalloc(&c->row_v, c->R_tot));
     DAO_TRY(c->dalloc(&c->row_lr, c->R_tot));
+    DAO_TRY(c->dalloc(&c->row_cnt, c->R_tot));
+    DAO_CU(cudaMemsetAsync(c->row_cnt, 0, (size_t)std::max(c->R_tot, 1) * sizeof(int), c->stream));
     DAO_TRY(c->dalloc(&c->price, 1));
     for (int k = 0; k <= KMAX; ++k) c->mb.grid[k] = master_grid(c->V, c->num_sms, k);
     c->mb.GH = master_hess_grid(c->num_sms);
@@ -712,7 +715,7 @@ dao_status build_round_graph_persist(dao_ctx* c, int K) {
         check(launch_dt(c->Dt, c->pi, c->w, stop, cs, &n));
         check(launch_price_rows(c->w, c->row_info, c->R_tot, c->row_v, c->row_lr, stop, cs, &n));
         check(launch_price_commit(c->row_v, c->beam_row0_d, c->B, c->price, c->row_lr, c->rows_d, c->cols_d, c->tau,
-                                  K, 2 * c->max_rows, c->ap_beam, c->ap_lr, c->mask, c->cg, 0, 0, cs, &n));
+                                  K, 2 * c->max_rows, c->ap_beam, c->ap_lr, c->mask, c->cg, cs, &n));
         check(launch_column_dev(c->D, c->seg, c->ap_beam, K, c->beam_off_d, c->rows_d, c->cols_d, c->max_nb, c->mask,
                                 c->slab, c->ld, c->cg, c->num_sms, cs, &n));
         check(launch_master_persist(c->mb, c->slab, c->ld, c->V, K, c->vstruct, c->tf, c->S, c->opt.max_master_iters,
@@ -736,11 +739,11 @@ dao_status build_round_graph_persist(dao_ctx* c, int K) {
 }
 
 // Every round of a solve in one graph: a while node whose body is
-// ROUNDS_PER_ITER rounds (D^T, row scans, argmin + commit, column, persistent
-// master solve), the kernels reading the pool size from cg->K.  The commit
-// kernel ends the loop when pricing stops the solve or the pool reaches
-// cg->K_end.  Returns false (and leaves nothing behind) where the driver does
-// not take this form.
+// ROUNDS_PER_ITER rounds of three kernels (D^T with the MLC-row search, the
+// beam decision with the new aperture's column, the persistent master solve),
+// which read the pool size from the device.  The decision kernel ends the loop
+// when pricing stops the solve or the pool reaches cg->K_end.  Returns false
+// (and leaves nothing behind) where the driver does not take this form.
 constexpr int ROUNDS_PER_ITER = 4;
 
 bool build_solve_graph_persist(dao_ctx* c) {
@@ -751,7 +754,6 @@ bool build_solve_graph_persist(dao_ctx* c) {
     }
     cudaStream_t cs = c->stream;
     int n = 0;
-    const int* stop = &c->cg->stop;
     const int* skip = &c->cg->idle;
     cudaError_t e = cudaSuccess;
     auto check = [&](cudaError_t x) {
@@ -774,14 +776,28 @@ bool build_solve_graph_persist(dao_ctx* c) {
         if (e == cudaSuccess) {
             // ROUNDS_PER_ITER rounds per iteration: the while node's relaunch costs
             // about as much as a few kernels, and rounds after the stop return at entry
+            const RowTicket rt{c->binfo, c->beam_row0_d, c->cols_d, c->row_info, c->row_cnt, c->row_v, c->row_lr,
+                               c->cg};
+            CommitArgs ca{};
+            ca.row_v = c->row_v;
+            ca.row_lr = c->row_lr;
+            ca.beam_row0 = c->beam_row0_d;
+            ca.rows = c->rows_d;
+            ca.cols = c->cols_d;
+            ca.beam_off = c->beam_off_d;
+            ca.seg = c->seg;
+            ca.n_beams = c->B;
+            ca.lr_stride = 2 * c->max_rows;
+            ca.tau = c->tau;
+            ca.ap_beam = c->ap_beam;
+            ca.ap_lr = c->ap_lr;
+            ca.slab = c->slab;
+            ca.ld = c->ld;
+            ca.cg = c->cg;
+            ca.cond = h;
             for (int u = 0; u < ROUNDS_PER_ITER; ++u) {
-                check(launch_dt(c->Dt, c->pi, c->w, stop, cs, &n));
-                check(launch_price_rows(c->w, c->row_info, c->R_tot, c->row_v, c->row_lr, stop, cs, &n));
-                check(launch_price_commit(c->row_v, c->beam_row0_d, c->B, c->price, c->row_lr, c->rows_d,
-                                          c->cols_d, c->tau, 0, 2 * c->max_rows, c->ap_beam, c->ap_lr, c->mask,
-                                          c->cg, h, 1, cs, &n));
-                check(launch_column_dev(c->D, c->seg, c->ap_beam, 0, c->beam_off_d, c->rows_d, c->cols_d,
-                                        c->max_nb, c->mask, c->slab, c->ld, c->cg, c->num_sms, cs, &n));
+                check(launch_dt_rows(c->Dt, c->pi, c->w, rt, cs, &n));
+                check(launch_commit_column(c->D, ca, c->max_nb, c->num_sms, cs, &n));
                 check(launch_master_persist(c->mb, c->slab, c->ld, c->V, 0, c->vstruct, c->tf, c->S,
                                             c->opt.max_master_iters, c->opt.master_tol, skip, c->z, c->pi, c->cg,
                                             cs, &n));
@@ -830,8 +846,7 @@ dao_status build_round_graph(dao_ctx* c, int K) {
             check(launch_dt(c->Dt, c->pi, c->w, stop, cs, &n));
             check(launch_price_rows(c->w, c->row_info, c->R_tot, c->row_v, c->row_lr, stop, cs, &n));
             check(launch_price_commit(c->row_v, c->beam_row0_d, c->B, c->price, c->row_lr, c->rows_d, c->cols_d,
-                                      c->tau, K, 2 * c->max_rows, c->ap_beam, c->ap_lr, c->mask, c->cg, 0, 0, cs,
-                                      &n));
+                                      c->tau, K, 2 * c->max_rows, c->ap_beam, c->ap_lr, c->mask, c->cg, cs, &n));
             check(launch_column_dev(c->D, c->seg, c->ap_beam, K, c->beam_off_d, c->rows_d, c->cols_d, c->max_nb,
                                     c->mask, c->slab, c->ld, c->cg, c->num_sms, cs, &n));
             check(launch_master_init(c->mb.st, K, skip, h, 1, cs, &n));
@@ -919,6 +934,8 @@ dao_status solve_graph_begin(dao_ctx* c, int n_apertures, GraphSolve* gs) {
     h->K_end = gs->K1;
     h->stop = 0;
     h->idle = 0;
+    h->rs_K = gs->K0;
+    h->rs_stop = 0;
     DAO_CU(cudaMemcpyAsync(c->cg, h, offsetof(CGDev, pad), cudaMemcpyHostToDevice, c->stream));
     return DAO_OK;
 }
@@ -965,7 +982,7 @@ dao_status solve_graph_end(dao_ctx* c, const GraphSolve& gs, int n_apertures, in
         // the while node ran the rounds that grew the pool and, when pricing
         // stopped the solve, the round that found it, ROUNDS_PER_ITER to an iteration
         const int rounds = K - K0 + (h->done != 0 ? 1 : 0);
-        c->launches_i += 5 * ROUNDS_PER_ITER * ((rounds + ROUNDS_PER_ITER - 1) / ROUNDS_PER_ITER);
+        c->launches_i += 3 * ROUNDS_PER_ITER * ((rounds + ROUNDS_PER_ITER - 1) / ROUNDS_PER_ITER);
     } else {
         // every queued round launches its kernels (a stopped solve's rounds return at entry)
         c->launches_i += (persist ? 5 : 7) * (K1 - K0);

@@ -108,7 +108,9 @@ struct CGDev {
     int K_end;            // a device-driven solve stops when the pool reaches this size
     int stop;             // done set or K_end reached: later rounds skip D^T and pricing
     int idle;             // this round added no aperture: its column and master solve skip
-    int pad[3];
+    int rs_K;             // K and stop as the round's D^T kernel found them: the fused
+    int rs_stop;          //   commit kernel reads these while its block 0 updates K and stop
+    int pad;
     double trace[KMAX];   // F after each added aperture
     double res[KMAX];     // final KKT residual of each master solve
     double tol[KMAX];     // its absolute tolerance
@@ -135,8 +137,7 @@ cudaError_t launch_column(const DevCSR& D, const int* seg_lo, const int* seg_hi,
                           cudaStream_t stream, int* launches);
 
 // a4 for the aperture the device just committed at pool index K-1 (graph
-// path), written to column K-1 of the slab (column stride ld).  K = 0: the
-// pool size is read from cg->K when the kernel runs.
+// path), written to column K-1 of the slab (column stride ld).
 cudaError_t launch_column_dev(const DevCSR& D, const int* seg, const int* ap_beam, int K, const int* beam_off,
                               const int* rows, const int* cols, int max_nb, const float* mask, float* slab, int ld,
                               const CGDev* cg, int num_sms, cudaStream_t stream, int* launches);
@@ -155,13 +156,53 @@ cudaError_t launch_price(const float* w, const int4* row_info, int n_rows, const
 // Graph path: the row scans, then the beam argmin fused with the commit.
 cudaError_t launch_price_rows(const float* w, const int4* row_info, int n_rows, double* row_v, int2* row_lr,
                               const int* skip, cudaStream_t stream, int* launches);
-// K = 0: the new pool size is cg->K + 1 when the kernel runs.  Sets cg->idle
-// (0 when it added an aperture) and cg->stop (done, or the pool reached
-// cg->K_end).  use_cond: the kernel sets the while-node handle to !stop.
+// Sets cg->idle (0 when it added aperture K - 1) and cg->stop (done, or the
+// pool reached cg->K_end).
 cudaError_t launch_price_commit(const double* row_v, const int* beam_row0, int n_beams, PriceDev* pr,
                                 const int2* row_lr, const int* rows, const int* cols, double tau, int K, int lr_stride,
-                                int* ap_beam, int* ap_lr, float* mask, CGDev* cg, cudaGraphConditionalHandle cond,
-                                int use_cond, cudaStream_t stream, int* launches);
+                                int* ap_beam, int* ap_lr, float* mask, CGDev* cg, cudaStream_t stream, int* launches);
+
+// The device-driven round (one graph for every round of a solve):
+//  - D^T with the MLC-row search fused: the block that completes the last
+//    beamlet of an MLC row (a per-row ticket) runs that row's search; block 0
+//    snapshots cg->K and cg->stop into rs_K and rs_stop;
+//  - the beam decision fused with the new aperture's column: every block takes
+//    the same decision from the row results, block 0 commits aperture
+//    rs_K (pool size rs_K + 1), writes cg->K, idle, stop, done and the
+//    while-node handle (!stop), and every block computes its share of the
+//    column into the slab.
+struct RowTicket {
+    const int4* binfo;      // per beamlet: beam, MLC row within the beam, column
+    const int* beam_row0;   // first global MLC row of each beam
+    const int* cols;        // beamlets per MLC row of each beam
+    const int4* row_info;   // per MLC row: beam, first beamlet, columns, row
+    int* row_cnt;           // per MLC row: beamlets done this round (the row's last block resets it)
+    double* row_v;
+    int2* row_lr;
+    CGDev* cg;
+};
+cudaError_t launch_dt_rows(const DevCSR& Dt, const float* pi, float* w, const RowTicket& rt, cudaStream_t stream,
+                           int* launches);
+struct CommitArgs {
+    const double* row_v;
+    const int2* row_lr;
+    const int* beam_row0;
+    const int* rows;
+    const int* cols;
+    const int* beam_off;
+    const int* seg;         // (B + 1) x V beam segments of D's rows
+    int n_beams;
+    int lr_stride;
+    double tau;
+    int* ap_beam;
+    int* ap_lr;
+    float* slab;
+    int ld;
+    CGDev* cg;
+    cudaGraphConditionalHandle cond;
+};
+cudaError_t launch_commit_column(const DevCSR& D, const CommitArgs& ca, int max_nb, int num_sms, cudaStream_t stream,
+                                 int* launches);
 
 // a5: projected-Newton master problem kernels.
 // Counters of the grid barrier of the persistent master solve (zeroed memory;

@@ -12,6 +12,7 @@
 #include <cuda_fp16.h>
 
 #include "dao_internal.h"
+#include "pricing.cuh"
 
 namespace dao {
 
@@ -126,6 +127,36 @@ __global__ void __launch_bounds__(256) k_sum_f64(const double* __restrict__ part
 }
 
 // ---- a2 ---------------------------------------------------------------------
+// The device-driven round (rt.row_cnt != nullptr): block 0 snapshots the pool
+// size and the stop flag for the fused commit kernel that follows.
+__device__ __forceinline__ void dt_round_snapshot(const RowTicket& rt) {
+    if (rt.row_cnt != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+        rt.cg->rs_K = rt.cg->K;
+        rt.cg->rs_stop = rt.cg->stop;
+    }
+}
+
+// The fused MLC-row search: thread 0 has published w[row]; it takes the ticket
+// of the row's MLC row, and the block that holds the MLC row's last beamlet
+// runs the row search (warp 0) on the row's w, read through L2.
+__device__ __forceinline__ void dt_row_ticket(const RowTicket& rt, int row, const float* w) {
+    if (rt.row_cnt == nullptr) return;  // uniform
+    __shared__ int s_row;
+    if (threadIdx.x == 0) {
+        __threadfence();  // w[row] is visible before the ticket is
+        const int4 bi = rt.binfo[row];
+        const int g = rt.beam_row0[bi.x] + bi.y;
+        const bool last = atomicAdd(&rt.row_cnt[g], 1) == rt.cols[bi.x] - 1;
+        if (last) rt.row_cnt[g] = 0;  // every other beamlet of the row has taken its ticket
+        s_row = last ? g : -1;
+    }
+    __syncthreads();
+    const int g = s_row;
+    // every other block of the row fenced its w before its ticket; row_best
+    // reads w through L2
+    if (g >= 0 && threadIdx.x < 32) pricing::row_best(w, rt.row_info[g], g, rt.row_v, rt.row_lr);
+}
+
 // One block per beamlet row of D^T; int4/float4 loads of (voxel, value),
 // gathered pi from L2; FP32 products, FP64 combination across threads.
 template <int BT>
@@ -133,8 +164,9 @@ __global__ void __launch_bounds__(BT) k_dt(const int* __restrict__ rowptr, const
                                            const float4* __restrict__ val4, int N,
                                            const int* __restrict__ order,
                                            const float* __restrict__ pi, float* __restrict__ w,
-                                           const int* __restrict__ skip) {
+                                           const int* __restrict__ skip, RowTicket rt) {
     __shared__ double s_red[BT / 32];
+    dt_round_snapshot(rt);
     if (skip != nullptr && *skip) return;
     const int row = order[blockIdx.x];  // longest rows first: they start in the first wave
     const int p0 = rowptr[row] >> 2, p1 = rowptr[row + 1] >> 2;
@@ -164,6 +196,7 @@ __global__ void __launch_bounds__(BT) k_dt(const int* __restrict__ rowptr, const
     }
     const double s = block_sum_mixed<BT>(acc, s_red);
     if (threadIdx.x == 0) w[row] = (float)s;
+    dt_row_ticket(rt, row, w);
 }
 
 // ---- a4 ---------------------------------------------------------------------
@@ -205,7 +238,7 @@ __global__ void __launch_bounds__(256) k_column(const int* __restrict__ col, con
 }
 
 // The same for the aperture at pool index K-1 of the device table, into
-// column K-1 of the slab (K = 0: the pool size in cg->K).
+// column K-1 of the slab.
 template <int G>
 __global__ void __launch_bounds__(256) k_column_dev(const int* __restrict__ col, const float* __restrict__ val,
                                                     const int* __restrict__ seg, int V,
@@ -215,7 +248,6 @@ __global__ void __launch_bounds__(256) k_column_dev(const int* __restrict__ col,
                                                     float* __restrict__ slab, int ld, const CGDev* __restrict__ cg) {
     extern __shared__ float smask[];
     if (cg->idle) return;
-    if (K <= 0) K = cg->K;
     const int b = ap_beam[K - 1];
     const int nb = rows[b] * cols[b];
     for (int i = threadIdx.x; i < nb; i += blockDim.x) smask[i] = mask[i];
@@ -339,8 +371,9 @@ __global__ void __launch_bounds__(BT) k_dt16(const int* __restrict__ rowptr, con
                                              const uint4* __restrict__ val8, const float* __restrict__ scale, int N,
                                              const int* __restrict__ order,
                                              const float* __restrict__ pi, float* __restrict__ w,
-                                             const int* __restrict__ skip) {
+                                             const int* __restrict__ skip, RowTicket rt) {
     __shared__ double s_red[BT / 32];
+    dt_round_snapshot(rt);
     if (skip != nullptr && *skip) return;
     const int row = order[blockIdx.x];  // longest rows first
     const int p0 = rowptr[row] >> 3, p1 = rowptr[row + 1] >> 3;
@@ -361,6 +394,7 @@ __global__ void __launch_bounds__(BT) k_dt16(const int* __restrict__ rowptr, con
     }
     const double sres = block_sum_mixed<BT>(acc, s_red);
     if (threadIdx.x == 0) w[row] = (float)(sres * (double)scale[row]);
+    dt_row_ticket(rt, row, w);
 }
 
 // a4 over beam b's segment of each row; the mask is pre-multiplied by the scales.
@@ -414,7 +448,6 @@ __global__ void __launch_bounds__(256) k_column16_dev(const unsigned short* __re
                                                       const CGDev* __restrict__ cg) {
     extern __shared__ float smask[];
     if (cg->idle) return;
-    if (K <= 0) K = cg->K;
     const int b = ap_beam[K - 1];
     const int nb = rows[b] * cols[b];
     const int base = beam_off[b];
@@ -422,6 +455,76 @@ __global__ void __launch_bounds__(256) k_column16_dev(const unsigned short* __re
     __syncthreads();
     column16_body<G, BF>(col, val, seg + (size_t)b * V, seg + (size_t)(b + 1) * V, V, base, smask,
                          slab + (size_t)(K - 1) * ld, 1);
+}
+
+// The device-driven round's beam decision fused with the new aperture's
+// column (a4): every block takes the same decision from the row results of
+// the D^T kernel (pricing::decide); block 0 commits aperture rs_K, writes
+// cg->K, idle, stop, done and the while-node handle; every block then builds
+// the open-beamlet mask from the rows' leaf positions and computes its rows of
+// the column, with the arithmetic of column_body / column16_body.  Blocks read
+// the round state only from rs_K and rs_stop, which no block of this launch
+// writes.
+template <int G, int PREC>
+__global__ void __launch_bounds__(256) k_commit_column(const int* __restrict__ col, const float* __restrict__ val,
+                                                       const unsigned short* __restrict__ col16,
+                                                       const unsigned short* __restrict__ val16,
+                                                       const float* __restrict__ scale, int V, CommitArgs ca) {
+    extern __shared__ double s_dyn[];
+    double* s_sum = s_dyn;                                        // n_beams
+    float* smask = reinterpret_cast<float*>(s_dyn + ca.n_beams);  // max_nb
+    CGDev* cg = ca.cg;
+    const int tid = threadIdx.x;
+    const bool lead = blockIdx.x == 0 && tid == 0;
+    auto finish = [&](int idle, int stop) {
+        if (lead) {
+            cg->idle = idle;
+            cg->stop = stop;
+            cudaGraphSetConditional(ca.cond, stop ? 0u : 1u);
+        }
+    };
+    if (__ldcg(&cg->rs_stop)) {
+        finish(1, 1);
+        return;
+    }
+    const int K = __ldcg(&cg->rs_K) + 1;  // pool size with the new aperture
+    int b = 0;
+    double rc = 0.0;
+    const int verdict = pricing::decide(ca.row_v, ca.beam_row0, ca.n_beams, ca.row_lr, ca.rows, ca.tau, K,
+                                        ca.lr_stride, ca.ap_beam, ca.ap_lr, s_sum, &b, &rc);
+    if (verdict != pricing::VERDICT_NEW) {
+        if (lead) cg->done = verdict;
+        finish(1, 1);
+        return;
+    }
+    const int R = ca.rows[b], C = ca.cols[b], r0 = ca.beam_row0[b], base = ca.beam_off[b];
+    if (blockIdx.x == 0) {
+        if (tid == 0) ca.ap_beam[K - 1] = b;
+        for (int r = tid; r < R; r += blockDim.x) {
+            const int2 lr = ca.row_lr[r0 + r];
+            ca.ap_lr[(K - 1) * ca.lr_stride + 2 * r] = lr.x;
+            ca.ap_lr[(K - 1) * ca.lr_stride + 2 * r + 1] = lr.y;
+        }
+        if (tid == 0) cg->K = K;
+        finish(0, K >= __ldcg(&cg->K_end) ? 1 : 0);
+    }
+    for (int i = tid; i < R * C; i += blockDim.x) {
+        const int2 lr = ca.row_lr[r0 + i / C];
+        const int c = i % C;
+        const float m = (c >= lr.x && c < lr.y) ? 1.f : 0.f;
+        if constexpr (PREC == DAO_PREC_FP32)
+            smask[i] = m;
+        else
+            smask[i] = m * scale[base + i];
+    }
+    __syncthreads();
+    float* out = ca.slab + (size_t)(K - 1) * ca.ld;
+    const int* seg_lo = ca.seg + (size_t)b * V;
+    const int* seg_hi = ca.seg + (size_t)(b + 1) * V;
+    if constexpr (PREC == DAO_PREC_FP32)
+        column_body<G>(col, val, seg_lo, seg_hi, V, base, smask, out, 1);
+    else
+        column16_body<G, PREC == DAO_PREC_BF16>(col16, val16, seg_lo, seg_hi, V, base, smask, out, 1);
 }
 
 // Blocks of a grid-stride kernel that are all resident at once (every block
@@ -511,19 +614,20 @@ cudaError_t dose16_any(int g, const DevCSR& D, const float* x, const uint8_t* vs
 }
 
 template <int BT>
-void dt_launch(const DevCSR& Dt, const float* pi, float* w, const int* skip, cudaStream_t stream) {
+void dt_launch(const DevCSR& Dt, const float* pi, float* w, const int* skip, const RowTicket& rt,
+               cudaStream_t stream) {
     if (Dt.prec == DAO_PREC_FP16)
         k_dt16<BT, false><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
                                                         reinterpret_cast<const uint4*>(Dt.val16), Dt.scale,
-                                                        Dt.n_rows, Dt.order, pi, w, skip);
+                                                        Dt.n_rows, Dt.order, pi, w, skip, rt);
     else if (Dt.prec == DAO_PREC_BF16)
         k_dt16<BT, true><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
                                                        reinterpret_cast<const uint4*>(Dt.val16), Dt.scale,
-                                                       Dt.n_rows, Dt.order, pi, w, skip);
+                                                       Dt.n_rows, Dt.order, pi, w, skip, rt);
     else
         k_dt<BT><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
                                                 reinterpret_cast<const float4*>(Dt.val), Dt.n_rows, Dt.order, pi, w,
-                                                skip);
+                                                skip, rt);
 }
 
 template <int G>
@@ -585,18 +689,29 @@ cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct,
     return cudaGetLastError();
 }
 
-cudaError_t launch_dt(const DevCSR& Dt, const float* pi, float* w, const int* skip, cudaStream_t stream,
-                      int* launches) {
+static cudaError_t dt_dispatch(const DevCSR& Dt, const float* pi, float* w, const int* skip, const RowTicket& rt,
+                        cudaStream_t stream, int* launches) {
     if (Dt.n_rows == 0) return cudaSuccess;
     // one block per beamlet row; 64 threads by default, so that up to 32 blocks
     // per SM keep every row resident in one wave
     switch (Dt.tune_dt_threads) {
-        case 128: dt_launch<128>(Dt, pi, w, skip, stream); break;
-        case 256: dt_launch<256>(Dt, pi, w, skip, stream); break;
-        default: dt_launch<64>(Dt, pi, w, skip, stream); break;
+        case 128: dt_launch<128>(Dt, pi, w, skip, rt, stream); break;
+        case 256: dt_launch<256>(Dt, pi, w, skip, rt, stream); break;
+        default: dt_launch<64>(Dt, pi, w, skip, rt, stream); break;
     }
     ++*launches;
     return cudaGetLastError();
+}
+
+cudaError_t launch_dt(const DevCSR& Dt, const float* pi, float* w, const int* skip, cudaStream_t stream,
+                      int* launches) {
+    return dt_dispatch(Dt, pi, w, skip, RowTicket{}, stream, launches);
+}
+
+cudaError_t launch_dt_rows(const DevCSR& Dt, const float* pi, float* w, const RowTicket& rt, cudaStream_t stream,
+                           int* launches) {
+    if (rt.row_cnt == nullptr || rt.cg == nullptr) return cudaErrorInvalidValue;
+    return dt_dispatch(Dt, pi, w, &rt.cg->stop, rt, stream, launches);
 }
 
 cudaError_t launch_column(const DevCSR& D, const int* seg_lo, const int* seg_hi, int base, int nb,
@@ -627,6 +742,33 @@ cudaError_t launch_column_dev(const DevCSR& D, const int* seg, const int* ap_bea
         default:
             column_dev_launch<8>(D, seg, ap_beam, K, beam_off, rows, cols, max_nb, mask, slab, ld, cg, grid, stream);
             break;
+    }
+    ++*launches;
+    return cudaGetLastError();
+}
+
+template <int G>
+static void commit_column_launch(const DevCSR& D, const CommitArgs& ca, size_t sm, int grid, cudaStream_t stream) {
+    if (D.prec == DAO_PREC_FP16)
+        k_commit_column<G, DAO_PREC_FP16><<<grid, 256, sm, stream>>>(nullptr, nullptr, D.col16, D.val16, D.scale,
+                                                                      D.n_rows, ca);
+    else if (D.prec == DAO_PREC_BF16)
+        k_commit_column<G, DAO_PREC_BF16><<<grid, 256, sm, stream>>>(nullptr, nullptr, D.col16, D.val16, D.scale,
+                                                                      D.n_rows, ca);
+    else
+        k_commit_column<G, DAO_PREC_FP32><<<grid, 256, sm, stream>>>(D.col, D.val, nullptr, nullptr, D.scale,
+                                                                      D.n_rows, ca);
+}
+
+cudaError_t launch_commit_column(const DevCSR& D, const CommitArgs& ca, int max_nb, int num_sms, cudaStream_t stream,
+                                 int* launches) {
+    if (D.n_rows == 0 || ca.cg == nullptr) return cudaErrorInvalidValue;
+    const int grid = num_sms * 8;
+    const size_t sm = (size_t)std::max(ca.n_beams, 1) * sizeof(double) + (size_t)std::max(max_nb, 1) * sizeof(float);
+    switch (D.tune_col_g) {
+        case 4: commit_column_launch<4>(D, ca, sm, grid, stream); break;
+        case 16: commit_column_launch<16>(D, ca, sm, grid, stream); break;
+        default: commit_column_launch<8>(D, ca, sm, grid, stream); break;
     }
     ++*launches;
     return cudaGetLastError();
