@@ -213,16 +213,26 @@ __device__ __forceinline__ void column_body(const int* __restrict__ col, const f
     const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n_warps = (gridDim.x * blockDim.x) >> 5;
     const int n_tiles = (V + RPW - 1) / RPW;
+    // the next tile's segment bounds are loaded while this tile's entries are
+    int row = warp_global * RPW + lane / G;
+    int lo = 0, hi = 0;
+    if (warp_global < n_tiles && row < V) {
+        lo = seg_lo[row];
+        hi = seg_hi[row];
+    }
     for (int t = warp_global; t < n_tiles; t += n_warps) {
-        const int row = t * RPW + lane / G;
-        float acc = 0.f;
-        if (row < V) {
-            const int q1 = seg_hi[row];
-            for (int p = seg_lo[row] + sub; p < q1; p += G) acc = fmaf(__ldg(val + p), smask[__ldg(col + p) - base], acc);
+        const int row_c = row, lo_c = lo, hi_c = hi;
+        row = (t + n_warps) * RPW + lane / G;
+        lo = hi = 0;
+        if (t + n_warps < n_tiles && row < V) {
+            lo = seg_lo[row];
+            hi = seg_hi[row];
         }
+        float acc = 0.f;
+        for (int p = lo_c + sub; p < hi_c; p += G) acc = fmaf(__ldg(val + p), smask[__ldg(col + p) - base], acc);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-        if (row < V && sub == 0) out[(size_t)row * stride] = acc;
+        if (row_c < V && sub == 0) out[(size_t)row_c * stride] = acc;
     }
 }
 
@@ -409,17 +419,27 @@ __device__ __forceinline__ void column16_body(const unsigned short* __restrict__
     const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n_warps = (gridDim.x * blockDim.x) >> 5;
     const int n_tiles = (V + RPW - 1) / RPW;
+    // the next tile's segment bounds are loaded while this tile's entries are
+    int row = warp_global * RPW + lane / G;
+    int lo = 0, hi = 0;
+    if (warp_global < n_tiles && row < V) {
+        lo = seg_lo[row];
+        hi = seg_hi[row];
+    }
     for (int t = warp_global; t < n_tiles; t += n_warps) {
-        const int row = t * RPW + lane / G;
-        float acc = 0.f;
-        if (row < V) {
-            const int q1 = seg_hi[row];
-            for (int p = seg_lo[row] + sub; p < q1; p += G)
-                acc = fmaf(unpack1<BF>(__ldg(val + p)), smask[__ldg(col + p) - base], acc);
+        const int row_c = row, lo_c = lo, hi_c = hi;
+        row = (t + n_warps) * RPW + lane / G;
+        lo = hi = 0;
+        if (t + n_warps < n_tiles && row < V) {
+            lo = seg_lo[row];
+            hi = seg_hi[row];
         }
+        float acc = 0.f;
+        for (int p = lo_c + sub; p < hi_c; p += G)
+            acc = fmaf(unpack1<BF>(__ldg(val + p)), smask[__ldg(col + p) - base], acc);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-        if (row < V && sub == 0) out[(size_t)row * stride] = acc;
+        if (row_c < V && sub == 0) out[(size_t)row_c * stride] = acc;
     }
 }
 
