@@ -504,6 +504,18 @@ constexpr int STEP_T = 256;
 constexpr int STEP_W = STEP_T / 32;
 static_assert(STEP_T == 256 && KMAX == 64, "the step kernel maps a 16 x 16 thread grid onto 64 x 64 entries");
 
+// Maximum over the warp of non-negative doubles: their IEEE bit patterns order
+// like their values, so a 64-bit integer maximum is exact and stays off the
+// FP64 pipe (1/64 of the FP32 rate on this part).  A NaN counts as 0, as
+// fmax would skip it.
+__device__ __forceinline__ long long nonneg_bits(double v) { return __double_as_longlong(v == v ? v : 0.0); }
+__device__ __forceinline__ double warp_max_nonneg(double v) {
+    long long b = nonneg_bits(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(FULL, b, o));
+    return __longlong_as_double(b);
+}
+
 __device__ __forceinline__ float blk_max_f32(float v, float* sw) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
@@ -572,15 +584,13 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     double tol = tol0;
     if (phase == 0) {
         if (vwarp) {
-            double m = own ? fabs(gt) : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(FULL, m, o));
+            const double m = warp_max_nonneg(own ? fabs(gt) : 0.0);
             if ((k & 31) == 0) sw3[k >> 5] = m;
         }
         __syncthreads();
-        double m = sw3[0];
-        for (int w = 1; w < nw; ++w) m = fmax(m, sw3[w]);
-        tol = tol_rel * fmax(m, 1e-300);
+        long long mb = nonneg_bits(sw3[0]);
+        for (int w = 1; w < nw; ++w) mb = max(mb, nonneg_bits(sw3[w]));
+        tol = tol_rel * fmax(__longlong_as_double(mb), 1e-300);
         if (k == 0) st->tol = tol;
     }
     // KKT violation flag, residual and Armijo decrease in one reduction
@@ -589,13 +599,10 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     if (vwarp) {
         const double rt = own ? fabs(yt - fmax(yt - gt, 0.0)) : 0.0;
         viol = __any_sync(FULL, own && rt > tol + NOISE * (double)U32 * gn) ? 1 : 0;
-        rmax = rt;
+        rmax = warp_max_nonneg(rt);
         dec = own ? g * (yt - y) : 0.0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            rmax = fmax(rmax, __shfl_xor_sync(FULL, rmax, o));
-            dec += __shfl_xor_sync(FULL, dec, o);
-        }
+        for (int o = 16; o > 0; o >>= 1) dec += __shfl_xor_sync(FULL, dec, o);
         if ((k & 31) == 0) {
             sw[k >> 5] = rmax;
             sw2[k >> 5] = dec;
@@ -603,14 +610,15 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
         }
     }
     __syncthreads();
-    rmax = sw[0];
+    long long rb = nonneg_bits(sw[0]);
     dec = sw2[0];
     viol = swi[0];
     for (int w = 1; w < nw; ++w) {
-        rmax = fmax(rmax, sw[w]);
+        rb = max(rb, nonneg_bits(sw[w]));
         dec += sw2[w];
         viol |= swi[w];
     }
+    rmax = __longlong_as_double(rb);
     const bool cap = iter0 >= max_iter + 64;
     const bool accept = !cap && (phase == 0 || !viol || Ft <= F0 + sigma * dec);
     if (k == 0) st->n_eval = __ldcg(&st->n_eval) + 1;
