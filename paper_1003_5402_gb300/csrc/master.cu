@@ -703,8 +703,9 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     //   - thread 160 writes the eliminated right-hand side of the panel into ye,
     //     threads 161 + r subtract its contribution from row block r of u.
     // Rows nf .. 4*panels-1 are padding with only the shift on the diagonal.  The
-    // pivots are checked once at the end; a non-positive one restarts the
-    // factorisation with a 100x larger shift.  Then L^T x = D^-1 ye is solved by
+    // pivots are checked once at the end; one that is not in [2^-126, 2^126]
+    // (non-positive, or outside the range of the reciprocal approximation)
+    // restarts the factorisation with a 100x larger shift.  Then L^T x = D^-1 ye is solved by
     // warp 0 with the unit lower factor L_ik = Lw_ik / d_k.
     const int ti = k >> 4, tq = k & 15;
     const int n_panels = (nf + 3) >> 2;
@@ -750,16 +751,18 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
                 const float4 a1 = *reinterpret_cast<const float4*>(&A[c0 + 1][c0]);
                 const float4 a2 = *reinterpret_cast<const float4*>(&A[c0 + 2][c0]);
                 const float4 a3 = *reinterpret_cast<const float4*>(&A[c0 + 3][c0]);
-                // __frcp_rn: the correctly rounded 1 / d, the value 1.f / d has,
-                // without the general division's special-case path
-                const float d0 = a0.x, i0 = __frcp_rn(d0);
+                // the pivot reciprocals on the chain of every panel: the hardware
+                // approximation (__fdividef, within 2 ulp for pivots in
+                // [2^-126, 2^126]; a pivot outside that range fails the check
+                // below and the factorisation restarts with a larger shift)
+                const float d0 = a0.x, i0 = __fdividef(1.f, d0);
                 const float l10 = a1.x * i0;
-                const float d1 = a1.y - l10 * a1.x, i1 = __frcp_rn(d1);
+                const float d1 = a1.y - l10 * a1.x, i1 = __fdividef(1.f, d1);
                 const float l20 = a2.x * i0, w21 = a2.y - l10 * a2.x, l21 = w21 * i1;
-                const float d2 = a2.z - l20 * a2.x - l21 * w21, i2 = __frcp_rn(d2);
+                const float d2 = a2.z - l20 * a2.x - l21 * w21, i2 = __fdividef(1.f, d2);
                 const float l30 = a3.x * i0, w31 = a3.y - l10 * a3.x, l31 = w31 * i1;
                 const float w32 = a3.z - l20 * a3.x - l21 * w31, l32 = w32 * i2;
-                const float d3 = a3.w - l30 * a3.x - l31 * w31 - l32 * w32, i3 = __frcp_rn(d3);
+                const float d3 = a3.w - l30 * a3.x - l31 * w31 - l32 * w32, i3 = __fdividef(1.f, d3);
                 auto xform = [&](float4 x) {
                     float4 w;
                     w.x = x.x;
@@ -821,7 +824,7 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
             __syncthreads();
         }
         const float pk = k < n4 ? piv[k] : 1.f, rk = k < n4 ? rd[k] : 1.f;
-        ok = __syncthreads_and(pk > 0.f && isfinite(rk)) != 0;
+        ok = __syncthreads_and(pk >= 1.17549435e-38f && pk <= 8.50705917e37f && isfinite(rk)) != 0;
         lam *= 100.f;
     }
     if (ok) {
