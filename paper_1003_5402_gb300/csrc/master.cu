@@ -830,27 +830,24 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     if (ok) {
         if (k >= nf && k < KMAX) rd[k] = 0.f;  // padding rows
         __syncthreads();
-        // L^T x = D^-1 ye by warp 0 in panels of 4 rows, last panel first, with
-        // L_ik = Lw_ik / d_k: x_r = (ye_r - sum_{i > r} Lw_ir x_i) / d_r; lanes own
-        // rows lane and lane + 32
+        // L^T x = D^-1 ye by warp 0, one pivot at a time from the last, with
+        // L_ik = Lw_ik / d_k: lanes keep b_r = ye_r - sum_{i > r, done} Lw_ir x_i
+        // for rows r = lane and lane + 32; x_j = b_j / d_j is broadcast from its
+        // lane and every row above j takes its term (one shuffle and one FMA
+        // per pivot on the dependent chain)
         if (k < 32) {
             float b0 = k < n4 ? ye[k] : 0.f, b1 = k + 32 < n4 ? ye[k + 32] : 0.f;
-            for (int p = n_panels - 1; p >= 0; --p) {
-                const int c0 = 4 * p;
-                const float src = c0 < 32 ? b0 : b1;
-                const float v0 = __shfl_sync(FULL, src, c0 & 31), v1 = __shfl_sync(FULL, src, (c0 + 1) & 31);
-                const float v2 = __shfl_sync(FULL, src, (c0 + 2) & 31), v3 = __shfl_sync(FULL, src, (c0 + 3) & 31);
-                const float x3 = v3 * rd[c0 + 3];
-                const float x2 = (v2 - Lw[c0 + 3][c0 + 2] * x3) * rd[c0 + 2];
-                const float x1 = (v1 - Lw[c0 + 2][c0 + 1] * x2 - Lw[c0 + 3][c0 + 1] * x3) * rd[c0 + 1];
-                const float x0 = (v0 - Lw[c0 + 1][c0] * x1 - Lw[c0 + 2][c0] * x2 - Lw[c0 + 3][c0] * x3) * rd[c0];
-                if (k < c0) b0 -= Lw[c0][k] * x0 + Lw[c0 + 1][k] * x1 + Lw[c0 + 2][k] * x2 + Lw[c0 + 3][k] * x3;
-                if (k + 32 < c0)
-                    b1 -= Lw[c0][k + 32] * x0 + Lw[c0 + 1][k + 32] * x1 + Lw[c0 + 2][k + 32] * x2 +
-                          Lw[c0 + 3][k + 32] * x3;
-                const int r0 = k - c0, r1 = k + 32 - c0;
-                if (r0 >= 0 && r0 < 4) b0 = r0 == 0 ? x0 : r0 == 1 ? x1 : r0 == 2 ? x2 : x3;
-                if (r1 >= 0 && r1 < 4) b1 = r1 == 0 ? x0 : r1 == 1 ? x1 : r1 == 2 ? x2 : x3;
+            const float r0 = rd[k], r1 = rd[k + 32];
+            for (int j = nf - 1; j >= 0; --j) {
+                const float xj = __shfl_sync(FULL, j < 32 ? b0 * r0 : b1 * r1, j & 31);
+                if (k == (j & 31)) {
+                    if (j < 32)
+                        b0 = xj;
+                    else
+                        b1 = xj;
+                }
+                if (k < j) b0 = fmaf(-Lw[j][k], xj, b0);
+                if (k + 32 < j) b1 = fmaf(-Lw[j][k + 32], xj, b1);
             }
             rhs[k] = b0;
             rhs[k + 32] = b1;
