@@ -502,6 +502,10 @@ __device__ __forceinline__ void master_reduce_part(const float* __restrict__ H_p
 // Block-wide reductions over STEP_T threads with a fixed order.
 constexpr int STEP_T = 256;
 constexpr int STEP_W = STEP_T / 32;
+// Thread roles in a panel of the step's factorisation: warps 0-5 update the
+// rows of the trailing tiles, warp 6 writes the panel's final columns and
+// pivots, warp 7 eliminates the right-hand side.
+constexpr int FACT_TILE_T = 192, FACT_COLW = 192, FACT_RHSW = 224;
 static_assert(STEP_T == 256 && KMAX == 64, "the step kernel maps a 16 x 16 thread grid onto 64 x 64 entries");
 
 // Maximum over the warp of non-negative doubles: their IEEE bit patterns order
@@ -696,17 +700,20 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     // triangle A lives in shared memory.  For panel p (columns c0 = 4p .. c0+3)
     // the threads that need it factor the 4 x 4 diagonal block themselves
     // (identical arithmetic everywhere) and map rows through it, w = x L11^-T:
-    //   - thread t < nb(nb+1)/2 owns trailing tile (r, s), s <= r, and subtracts
-    //     w_R D^-1 w_Q^T from it (the trailing part shrinks, so do the threads);
-    //   - threads 128 + r' write the panel's final column entries w (unscaled:
-    //     L_ik d_k) of row block r' into Lw, and the pivots d;
-    //   - thread 160 writes the eliminated right-hand side of the panel into ye,
-    //     threads 161 + r subtract its contribution from row block r of u.
+    //   - work item 4 t + a < 4 nb(nb+1)/2 (threads below FACT_TILE_T, strided)
+    //     takes row a of trailing tile t = (r, s), s <= r, and subtracts
+    //     w_R D^-1 w_Q^T from it (the trailing part shrinks, so do the items);
+    //   - threads FACT_COLW + r' write the panel's final column entries w
+    //     (unscaled: L_ik d_k) of row block r' into Lw, and the pivots d and
+    //     their reciprocals;
+    //   - thread FACT_RHSW writes the eliminated right-hand side of the panel
+    //     into ye, threads FACT_RHSW + r subtract its contribution from row
+    //     block r of u.
     // Rows nf .. 4*panels-1 are padding with only the shift on the diagonal.  The
     // pivots are checked once at the end; one that is not in [2^-126, 2^126]
     // (non-positive, or outside the range of the reciprocal approximation)
-    // restarts the factorisation with a 100x larger shift.  Then L^T x = D^-1 ye is solved by
-    // warp 0 with the unit lower factor L_ik = Lw_ik / d_k.
+    // restarts the factorisation with a 100x larger shift.  Then L^T x = D^-1 ye
+    // is solved by warp 0 with the unit lower factor L_ik = Lw_ik / d_k.
     const int ti = k >> 4, tq = k & 15;
     const int n_panels = (nf + 3) >> 2;
     const int n4 = 4 * n_panels;
@@ -724,11 +731,6 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
     for (int a = 0; a < 4; ++a) dg = fmaxf(dg, (ti == tq) ? Hr[a][a] : 0.f);
     const float maxdiag = blk_max_f32(dg, swf);
     float lam = 1e-6f * maxdiag + 1e-30f;
-    // trailing tile of this thread for a panel with nb trailing row blocks
-    int tr_r = (int)((sqrtf(8.f * (float)k + 1.f) - 1.f) * 0.5f);
-    while ((tr_r + 1) * (tr_r + 2) / 2 <= k) ++tr_r;
-    while (tr_r * (tr_r + 1) / 2 > k) --tr_r;
-    const int tr_s = k - tr_r * (tr_r + 1) / 2;
     bool ok = false;
     for (int attempt = 0; attempt < 6 && !ok; ++attempt) {
 #pragma unroll
@@ -743,10 +745,11 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
         for (int p = 0; p < n_panels; ++p) {
             const int c0 = 4 * p;
             const int nb = n_panels - p - 1;
-            const bool tile = k < nb * (nb + 1) / 2;
-            const bool colw = k >= 128 && k <= 128 + nb;
-            const bool rhsw = k >= 160 && k <= 160 + nb;
-            if (tile || colw || rhsw) {
+            const int ntile4 = 2 * nb * (nb + 1);  // rows of the nb (nb + 1) / 2 trailing tiles
+            const bool tilew = k < FACT_TILE_T && k < ntile4;
+            const bool colw = k >= FACT_COLW && k <= FACT_COLW + nb;
+            const bool rhsw = k >= FACT_RHSW && k <= FACT_RHSW + nb;
+            if (tilew || colw || rhsw) {
                 const float4 a0 = *reinterpret_cast<const float4*>(&A[c0][c0]);
                 const float4 a1 = *reinterpret_cast<const float4*>(&A[c0 + 1][c0]);
                 const float4 a2 = *reinterpret_cast<const float4*>(&A[c0 + 2][c0]);
@@ -771,32 +774,37 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
                     w.w = x.w - l30 * w.x - l31 * w.y - l32 * w.z;
                     return w;
                 };
-                if (tile) {
-                    const int R = c0 + 4 + 4 * tr_r, Q = c0 + 4 + 4 * tr_s;
-                    float4 wq[4];
+                if (tilew) {
+                    // one row a of trailing tile t per work item; the four rows of
+                    // a tile run in parallel
+                    for (int it = k; it < ntile4; it += FACT_TILE_T) {
+                        const int t = it >> 2, a = it & 3;
+                        int r = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+                        while ((r + 1) * (r + 2) / 2 <= t) ++r;
+                        while (r * (r + 1) / 2 > t) --r;
+                        const int R = c0 + 4 + 4 * r, Q = c0 + 4 + 4 * (t - r * (r + 1) / 2);
+                        float4 wq[4];
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) wq[b] = xform(*reinterpret_cast<const float4*>(&A[Q + b][c0]));
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
+                        for (int b = 0; b < 4; ++b) wq[b] = xform(*reinterpret_cast<const float4*>(&A[Q + b][c0]));
                         float4 w = xform(*reinterpret_cast<const float4*>(&A[R + a][c0]));
                         w.x *= i0;
                         w.y *= i1;
                         w.z *= i2;
                         w.w *= i3;
-                        float4 t = *reinterpret_cast<const float4*>(&A[R + a][Q]);
-                        t.x -= w.x * wq[0].x + w.y * wq[0].y + w.z * wq[0].z + w.w * wq[0].w;
-                        t.y -= w.x * wq[1].x + w.y * wq[1].y + w.z * wq[1].z + w.w * wq[1].w;
-                        t.z -= w.x * wq[2].x + w.y * wq[2].y + w.z * wq[2].z + w.w * wq[2].w;
-                        t.w -= w.x * wq[3].x + w.y * wq[3].y + w.z * wq[3].z + w.w * wq[3].w;
-                        *reinterpret_cast<float4*>(&A[R + a][Q]) = t;
+                        float4 tt = *reinterpret_cast<const float4*>(&A[R + a][Q]);
+                        tt.x -= w.x * wq[0].x + w.y * wq[0].y + w.z * wq[0].z + w.w * wq[0].w;
+                        tt.y -= w.x * wq[1].x + w.y * wq[1].y + w.z * wq[1].z + w.w * wq[1].w;
+                        tt.z -= w.x * wq[2].x + w.y * wq[2].y + w.z * wq[2].z + w.w * wq[2].w;
+                        tt.w -= w.x * wq[3].x + w.y * wq[3].y + w.z * wq[3].z + w.w * wq[3].w;
+                        *reinterpret_cast<float4*>(&A[R + a][Q]) = tt;
                     }
                 } else if (colw) {
-                    const int R = c0 + 4 * (k - 128);
+                    const int R = c0 + 4 * (k - FACT_COLW);
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
                         *reinterpret_cast<float4*>(&Lw[R + a][c0]) =
                             xform(*reinterpret_cast<const float4*>(&A[R + a][c0]));
-                    if (k == 128) {
+                    if (k == FACT_COLW) {
                         piv[c0] = d0;
                         piv[c0 + 1] = d1;
                         piv[c0 + 2] = d2;
@@ -808,10 +816,10 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
                     }
                 } else {
                     const float4 e = xform(*reinterpret_cast<const float4*>(&u[c0]));
-                    if (k == 160) {
+                    if (k == FACT_RHSW) {
                         *reinterpret_cast<float4*>(&ye[c0]) = e;
                     } else {
-                        const int R = c0 + 4 * (k - 160);
+                        const int R = c0 + 4 * (k - FACT_RHSW);
                         const float e0 = e.x * i0, e1 = e.y * i1, e2 = e.z * i2, e3 = e.w * i3;
 #pragma unroll
                         for (int a = 0; a < 4; ++a) {
