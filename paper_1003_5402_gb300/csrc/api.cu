@@ -560,6 +560,7 @@ dao_status master_solve(dao_ctx* c, double* F_out) {
     const size_t tail = sizeof(MasterDev) - offsetof(MasterDev, F);
     MasterDev* shadow = reinterpret_cast<MasterDev*>(c->pinned + c->off_master - offsetof(MasterDev, F));
     if (c->mb.GP > 0) {  // the whole solve as one cooperative launch (warm start, z and pi included)
+        DAO_CU(cudaMemsetAsync(c->mb.bar, 0, sizeof(GridBar), c->stream));
         c->prof_begin(DAO_KC_MASTER_SOLVE);
         DAO_CU(launch_master_persist(c->mb, c->slab, c->ld, c->V, c->K, c->vstruct, c->tf, c->S,
                                      c->opt.max_master_iters, c->opt.master_tol, nullptr, c->z, c->pi, nullptr,
@@ -937,6 +938,7 @@ dao_status solve_graph_begin(dao_ctx* c, int n_apertures, GraphSolve* gs) {
     h->rs_K = gs->K0;
     h->rs_stop = 0;
     DAO_CU(cudaMemcpyAsync(c->cg, h, offsetof(CGDev, pad), cudaMemcpyHostToDevice, c->stream));
+    if (c->mb.GP > 0) DAO_CU(cudaMemsetAsync(c->mb.bar, 0, sizeof(GridBar), c->stream));  // barrier counter
     return DAO_OK;
 }
 

@@ -207,9 +207,12 @@ cudaError_t launch_commit_column(const DevCSR& D, const CommitArgs& ca, int max_
 // a5: projected-Newton master problem kernels.
 // Counters of the grid barrier of the persistent master solve (zeroed memory;
 // count returns to 0 after every barrier, gen only increases).
+// Grid barrier of the persistent master solve: a monotonic arrival counter
+// (zeroed by the host before each solve) and a flag a block sets when a wait
+// ran out, after which the solve's later launches return at entry.
 struct GridBar {
     unsigned count;
-    unsigned gen;
+    unsigned broken;
     unsigned pad[2];
 };
 

@@ -123,7 +123,10 @@ __device__ __forceinline__ int tri_index(int r, int c, int K) { return r * K - (
 __global__ void k_master_init(MasterDev* __restrict__ st, int K, const int* __restrict__ skip,
                               cudaGraphConditionalHandle cond, int use_cond, GridBar* __restrict__ gb) {
     const int t = threadIdx.x;
-    if (t == 0 && gb != nullptr) gb->count = 0;  // a barrier left by an aborted solve starts empty
+    if (t == 0 && gb != nullptr) {  // a barrier left by an aborted solve starts empty
+        gb->count = 0;
+        gb->broken = 0;
+    }
     if (skip != nullptr && *skip) {  // the solve stopped before this round: nothing to iterate
         if (t == 0) {
             st->done = 1;
@@ -921,28 +924,36 @@ __global__ void __launch_bounds__(STEP_T) k_master_reduce_step(const float* __re
 //      that finishes last (ticket after a fence) takes the Newton step;
 //   grid barrier; stop when the step marked the solve done.
 // Every barrier wait is bounded: after GRID_WAIT_LIMIT polls the block reports
-// st->err = 2 and every block leaves at the next barrier or check.
+// st->err = 2, marks the barrier broken (later launches of the solve return at
+// entry) and every block leaves at the next barrier or check.
 constexpr int PT = STEP_T;         // threads per block (the step body's layout)
 constexpr int PW = PT / 32;
 constexpr int CHP = 64;            // active voxels per H chunk
 constexpr int GRID_WAIT_LIMIT = 1 << 22;
 constexpr size_t PERSIST_SMEM_MAX = 150 * 1024;  // dynamic shared memory the kernel is configured for
 
-__device__ __forceinline__ bool grid_sync(GridBar* gb, unsigned nblocks, int* s_flag) {
+// Barrier over the blocks of one cooperative launch with one atomic per
+// arrival.  The counter only grows: barrier e of a launch completes when it
+// reaches base + (e + 1) G.  base, the counter at launch, is a multiple of G
+// (each completed barrier adds exactly G), and every block reads it before its
+// first arrival, when fewer than G arrivals can have happened, so
+// base = c - c % G for whatever value c it reads.  Waiters poll the counter.
+// The host zeroes it before each solve; a solve's barriers stay far below
+// 2^32 arrivals.  *s_target is the block's next target.
+__device__ __forceinline__ bool grid_sync(GridBar* gb, unsigned nblocks, unsigned* s_target, int* s_flag) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned g = *reinterpret_cast<volatile unsigned*>(&gb->gen);
-        __threadfence();
+        const unsigned target = *s_target + nblocks;
+        *s_target = target;
+        __threadfence();  // this block's writes before its arrival
         const unsigned arrived = atomicAdd(&gb->count, 1u) + 1u;
         int ok = 1;
-        if (arrived == nblocks) {
-            atomicExch(&gb->count, 0u);
-            __threadfence();
-            atomicAdd(&gb->gen, 1u);
-        } else {
+        if (arrived != target) {
             int i = 0;
-            while (*reinterpret_cast<volatile unsigned*>(&gb->gen) == g && ++i < GRID_WAIT_LIMIT) __nanosleep(64);
+            while ((int)(*reinterpret_cast<volatile unsigned*>(&gb->count) - target) < 0 && ++i < GRID_WAIT_LIMIT)
+                __nanosleep(64);
             ok = i < GRID_WAIT_LIMIT;
+            if (!ok) atomicExch(&gb->broken, 1u);
         }
         __threadfence();
         *s_flag = ok;
@@ -980,9 +991,17 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
     __shared__ float s_red[PW];
     __shared__ float s_scr[8 * 24];
     __shared__ int s_flag, s_last, s_stop;
+    __shared__ unsigned s_target;
     if (skip != nullptr && *skip) return;  // the same for every block
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x;
+    if (tid == 0) {  // barrier base; a solve whose barrier broke runs no further master solve
+        const unsigned c = *reinterpret_cast<volatile unsigned*>(&gb->count);
+        s_target = c - c % (unsigned)G;
+        s_stop = *reinterpret_cast<volatile unsigned*>(&gb->broken) != 0;
+    }
+    __syncthreads();
+    if (s_stop) return;
     for (int i = tid; i < S; i += PT) s_tf[i] = tf[i];
     const int KB = KP / 4;
     const int nb = KB * (KB + 1) / 2;
@@ -1208,7 +1227,7 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
                 }
             }
         }
-        if (!grid_sync(gb, G, &s_flag)) {
+        if (!grid_sync(gb, G, &s_target, &s_flag)) {
             if (tid == 0) st->err = 2;
             break;
         }
@@ -1224,7 +1243,7 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
             master_step_body(st, max_iter, tol_rel, sigma);
             __threadfence();
         }
-        if (!grid_sync(gb, G, &s_flag)) {
+        if (!grid_sync(gb, G, &s_target, &s_flag)) {
             if (tid == 0) st->err = 2;
             break;
         }
