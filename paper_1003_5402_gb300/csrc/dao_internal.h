@@ -207,6 +207,24 @@ cudaError_t launch_commit_column(const DevCSR& D, const CommitArgs& ca, int max_
 // a5: projected-Newton master problem kernels.
 // Counters of the grid barrier of the persistent master solve (zeroed memory;
 // count returns to 0 after every barrier, gen only increases).
+// Device-scope acquire-release atomic add and acquire load.  After a
+// __syncthreads(), thread 0's release covers the writes of every thread of
+// its block (PTX causality order runs through bar.sync); after thread 0's
+// acquire and a __syncthreads(), every thread of the block sees what was
+// released to it.  This is the pattern of the grid barrier and of the
+// last-block tickets; it replaces a full fence (fence.sc) per thread before
+// the atomic and after it.
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // Grid barrier of the persistent master solve: a monotonic arrival counter
 // (zeroed by the host before each solve) and a flag a block sets when a wait
 // ran out, after which the solve's later launches return at entry.

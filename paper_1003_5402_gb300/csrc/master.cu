@@ -899,12 +899,10 @@ __global__ void __launch_bounds__(STEP_T) k_master_reduce_step(const float* __re
         return;
     }
     master_reduce_part(H_part, g_part, gn_part, F_part, GH, GE, st->K, st);
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) s_last = atom_add_acq_rel_gpu(&st->ticket, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
     if (threadIdx.x == 0) st->ticket = 0;
     master_step_body(st, max_iter, tol_rel, sigma);
     if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
@@ -932,8 +930,8 @@ constexpr int CHP = 64;            // active voxels per H chunk
 constexpr int GRID_WAIT_LIMIT = 1 << 22;
 constexpr size_t PERSIST_SMEM_MAX = 150 * 1024;  // dynamic shared memory the kernel is configured for
 
-// Barrier over the blocks of one cooperative launch with one atomic per
-// arrival.  The counter only grows: barrier e of a launch completes when it
+// Barrier over the blocks of one cooperative launch with one acquire-release
+// atomic per arrival.  The counter only grows: barrier e of a launch completes when it
 // reaches base + (e + 1) G.  base, the counter at launch, is a multiple of G
 // (each completed barrier adds exactly G), and every block reads it before its
 // first arrival, when fewer than G arrivals can have happened, so
@@ -945,17 +943,16 @@ __device__ __forceinline__ bool grid_sync(GridBar* gb, unsigned nblocks, unsigne
     if (threadIdx.x == 0) {
         const unsigned target = *s_target + nblocks;
         *s_target = target;
-        __threadfence();  // this block's writes before its arrival
-        const unsigned arrived = atomicAdd(&gb->count, 1u) + 1u;
+        // release: the block's writes (ordered by the __syncthreads above)
+        // before the arrival; acquire: the other blocks' writes after it
+        const unsigned arrived = atom_add_acq_rel_gpu(&gb->count, 1u) + 1u;
         int ok = 1;
         if (arrived != target) {
             int i = 0;
-            while ((int)(*reinterpret_cast<volatile unsigned*>(&gb->count) - target) < 0 && ++i < GRID_WAIT_LIMIT)
-                __nanosleep(64);
+            while ((int)(ld_acquire_gpu(&gb->count) - target) < 0 && ++i < GRID_WAIT_LIMIT) __nanosleep(64);
             ok = i < GRID_WAIT_LIMIT;
             if (!ok) atomicExch(&gb->broken, 1u);
         }
-        __threadfence();
         *s_flag = ok;
     }
     __syncthreads();
@@ -1233,15 +1230,12 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
         }
         // ---- B. reduction by every block, the step by the last one to finish
         master_reduce_part(H_part, g_part, gn_part, F_part, GS, G, K, st);
-        __threadfence();
         __syncthreads();
-        if (tid == 0) s_last = atomicAdd(&st->ticket, 1u) == (unsigned)G - 1u;
+        if (tid == 0) s_last = atom_add_acq_rel_gpu(&st->ticket, 1u) == (unsigned)G - 1u;
         __syncthreads();
         if (s_last) {
-            __threadfence();
             if (tid == 0) st->ticket = 0;
             master_step_body(st, max_iter, tol_rel, sigma);
-            __threadfence();
         }
         if (!grid_sync(gb, G, &s_target, &s_flag)) {
             if (tid == 0) st->err = 2;

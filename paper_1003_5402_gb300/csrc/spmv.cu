@@ -143,16 +143,17 @@ __device__ __forceinline__ void dt_row_ticket(const RowTicket& rt, int row, cons
     if (rt.row_cnt == nullptr) return;  // uniform
     __shared__ int s_row;
     if (threadIdx.x == 0) {
-        __threadfence();  // w[row] is visible before the ticket is
         const int4 bi = rt.binfo[row];
         const int g = rt.beam_row0[bi.x] + bi.y;
-        const bool last = atomicAdd(&rt.row_cnt[g], 1) == rt.cols[bi.x] - 1;
+        // release: w[row] before the ticket; acquire: the row's other prices
+        const bool last = (int)atom_add_acq_rel_gpu(reinterpret_cast<unsigned*>(&rt.row_cnt[g]), 1u) ==
+                          rt.cols[bi.x] - 1;
         if (last) rt.row_cnt[g] = 0;  // every other beamlet of the row has taken its ticket
         s_row = last ? g : -1;
     }
     __syncthreads();
     const int g = s_row;
-    // every other block of the row fenced its w before its ticket; row_best
+    // every other block of the row released its w with its ticket; row_best
     // reads w through L2
     if (g >= 0 && threadIdx.x < 32) pricing::row_best(w, rt.row_info[g], g, rt.row_v, rt.row_lr);
 }
