@@ -457,6 +457,27 @@ __global__ void __launch_bounds__(256) k_master_hess(const float* __restrict__ a
 // then the g rounding scale, then F), outputs strided over the grid's warps;
 // lanes read the blocks' partials (contiguous per output) and combine them with
 // a fixed shuffle tree in FP64.
+// Lane's share src[lane], src[lane + 32], ... of n partial sums, added in that
+// order (as a plain loop would), with the loads of up to RP_LANE of them issued
+// before the first add: in-order issue would otherwise wait for each load at
+// its add.  Through L2: the partials were written by other blocks.
+constexpr int RP_LANE = 12;
+template <class T>
+__device__ __forceinline__ T lane_sum_strided(const T* __restrict__ src, int n, int lane) {
+    T s = T(0);
+    for (int b0 = 0; b0 < n; b0 += 32 * RP_LANE) {
+        T v[RP_LANE];
+#pragma unroll
+        for (int q = 0; q < RP_LANE; ++q) {
+            const int b = b0 + lane + 32 * q;
+            v[q] = b < n ? __ldcg(src + b) : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < RP_LANE; ++q) s += v[q];
+    }
+    return s;
+}
+
 __device__ __forceinline__ void master_reduce_part(const float* __restrict__ H_part,
                                                    const double* __restrict__ g_part,
                                                    const float* __restrict__ gn_part,
@@ -467,9 +488,7 @@ __device__ __forceinline__ void master_reduce_part(const float* __restrict__ H_p
     const int n_out = E + 2 * K + 1;
     for (int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < n_out; o += (gridDim.x * blockDim.x) >> 5) {
         if (o < E) {  // the factorisation is FP32: so is this sum
-            float s = 0.f;
-            const float* src = H_part + (size_t)o * GH;
-            for (int b = lane; b < GH; b += 32) s += src[b];
+            float s = lane_sum_strided(H_part + (size_t)o * GH, GH, lane);
             s = warp_sum_f32(s);
             if (lane == 0) {
                 int r = 0, rem = o;
@@ -483,19 +502,16 @@ __device__ __forceinline__ void master_reduce_part(const float* __restrict__ H_p
             }
         } else if (o < E + K) {
             const int k = o - E;
-            double s = 0.0;
-            for (int b = lane; b < GH; b += 32) s += g_part[(size_t)k * GH + b];
+            double s = lane_sum_strided(g_part + (size_t)k * GH, GH, lane);
             s = warp_sum_f64(s);
             if (lane == 0) st->gt[k] = s;
         } else if (o < E + 2 * K) {
             const int k = o - E - K;
-            float s = 0.f;
-            for (int b = lane; b < GH; b += 32) s += gn_part[(size_t)k * GH + b];
+            float s = lane_sum_strided(gn_part + (size_t)k * GH, GH, lane);
             s = warp_sum_f32(s);
             if (lane == 0) st->gn[k] = s;
         } else {
-            double s = 0.0;
-            for (int b = lane; b < GE; b += 32) s += F_part[b];
+            double s = lane_sum_strided(F_part, GE, lane);
             s = warp_sum_f64(s);
             if (lane == 0) st->Ft = s;
         }
