@@ -1069,6 +1069,7 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
         for (int i = warp; i < tiles_b; i += PW) {
             const int j = (blockIdx.x + i * G) * 32 + lane;
             const bool in = j < V;
+            const int sid = in ? vstruct[j] : 0;  // requested with the first columns
             float sc[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
             const float* col = slab + (in ? j : 0);
             // PB columns in flight per lane (one coalesced 128-byte row each), then
@@ -1097,7 +1098,7 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
             }
             float h = 0.f, p = 0.f;
             if (in) {
-                const StructTermsF t = s_tf[vstruct[j]];
+                const StructTermsF t = s_tf[sid];
                 const float du = (t.tu - s) - c;
                 const float dov = (s - t.to) + c;
                 const float u = fmaxf(du, 0.f), o = fmaxf(dov, 0.f);
@@ -1150,12 +1151,23 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
                         s_ch[i] = s_hv[slot];
                         s_cp[i] = s_pv[slot];
                     }
-                    for (int q = tid / CHP; q < nq; q += PT / CHP)
-                        *reinterpret_cast<float4*>(Ac + i * KW + 4 * q) =
-                            make_float4(__ldcg(slab + (size_t)(4 * q) * ld + j),
-                                        __ldcg(slab + (size_t)(4 * q + 1) * ld + j),
-                                        __ldcg(slab + (size_t)(4 * q + 2) * ld + j),
-                                        __ldcg(slab + (size_t)(4 * q + 3) * ld + j));
+                    // this thread's column groups q = tid / CHP + 4 it of the row,
+                    // all loads issued before the first store
+                    float4 v[KMAX / 4 / (PT / CHP)];
+#pragma unroll
+                    for (int it = 0; it < KMAX / 4 / (PT / CHP); ++it) {
+                        const int q = tid / CHP + it * (PT / CHP);
+                        if (q < nq)
+                            v[it] = make_float4(__ldcg(slab + (size_t)(4 * q) * ld + j),
+                                                __ldcg(slab + (size_t)(4 * q + 1) * ld + j),
+                                                __ldcg(slab + (size_t)(4 * q + 2) * ld + j),
+                                                __ldcg(slab + (size_t)(4 * q + 3) * ld + j));
+                    }
+#pragma unroll
+                    for (int it = 0; it < KMAX / 4 / (PT / CHP); ++it) {
+                        const int q = tid / CHP + it * (PT / CHP);
+                        if (q < nq) *reinterpret_cast<float4*>(Ac + i * KW + 4 * q) = v[it];
+                    }
                 }
             }
             __syncthreads();
