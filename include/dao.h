@@ -134,6 +134,15 @@ void dao_destroy(dao_ctx* ctx);
  * emptied.  Safe to call at any time; contexts stay valid. */
 dao_status dao_release_cached_memory(int32_t device);
 
+/* Diagnostic of the bounded device waits (no context needed): a cooperative
+ * launch of two blocks in which one block never arrives at the grid barrier
+ * the persistent master solve uses.  The other block must give up after the
+ * barrier's poll limit (seconds at most) and mark the barrier broken.
+ * Returns DAO_ETIMEOUT when that happened (the expected outcome; *gave_up and
+ * *passed count the blocks of each kind), DAO_ESTATE if the wait did not give
+ * up, DAO_ECUDA on a CUDA error.  The device stays usable either way. */
+dao_status dao_check_bounded_wait(int32_t device, int32_t* gave_up, int32_t* passed);
+
 /* Empty the aperture pool (y = [], z = 0) keeping D on the device. */
 dao_status dao_reset(dao_ctx* ctx);
 

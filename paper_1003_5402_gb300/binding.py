@@ -86,6 +86,7 @@ SIGNATURES = {
                              C.POINTER(dao_weights), _F64P, C.POINTER(dao_options), C.POINTER(_P)]),
     "dao_destroy": (None, [_P]),
     "dao_release_cached_memory": (C.c_int, [C.c_int32]),
+    "dao_check_bounded_wait": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "dao_reset": (C.c_int, [_P]),
     "dao_price": (C.c_int, [_P, _I32P, _I32P, _F64P]),
     "dao_add_aperture": (C.c_int, [_P, C.c_int32, _I32P, _F64P]),

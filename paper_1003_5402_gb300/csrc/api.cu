@@ -1164,6 +1164,35 @@ dao_status dao_release_cached_memory(int32_t device) {
     return DAO_OK;
 }
 
+dao_status dao_check_bounded_wait(int32_t device, int32_t* gave_up, int32_t* passed) {
+    int n = 0;
+    DAO_CU(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(DAO_EINVAL, "no such device");
+    DAO_CU(cudaSetDevice(device));
+    cudaStream_t s = nullptr;
+    DAO_CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    GridBar* gb = nullptr;
+    int* out = nullptr;
+    cudaError_t e = cudaMalloc(&gb, sizeof(GridBar));
+    if (e == cudaSuccess) e = cudaMalloc(&out, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(gb, 0, sizeof(GridBar), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, 2 * sizeof(int), s);
+    if (e == cudaSuccess) e = launch_barrier_check(gb, 2, 0, out, s);
+    int h[2] = {0, 0};
+    GridBar hb{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, gb, sizeof(hb), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (out) cudaFree(out);
+    if (gb) cudaFree(gb);
+    cudaStreamDestroy(s);
+    if (e != cudaSuccess) return fail(DAO_ECUDA, std::string("barrier check: ") + cudaGetErrorString(e));
+    if (gave_up) *gave_up = h[0];
+    if (passed) *passed = h[1];
+    if (h[0] > 0 && hb.broken) return fail(DAO_ETIMEOUT, "a grid barrier wait gave up as bounded");
+    return fail(DAO_ESTATE, "the bounded barrier wait did not give up");
+}
+
 dao_status dao_reset(dao_ctx* c) {
     DAO_TRY(check_ctx(c));
     dao_status st = reset_state(c);

@@ -314,6 +314,10 @@ cudaError_t build_transpose_place(int prec, const int64_t* rp, const int* col, c
 // The whole master solve as one cooperative launch (GP blocks), after
 // launch_master_init; dynamic shared memory per master_persist_smem.
 size_t master_persist_smem(int V, int G);
+// Diagnostic: a cooperative launch whose block `absent` never arrives at the
+// grid barrier; out[0] counts the blocks whose bounded wait gave up, out[1]
+// those that passed.
+cudaError_t launch_barrier_check(GridBar* gb, int blocks, int absent, int* out, cudaStream_t stream);
 int master_persist_grid(int V, int num_sms);
 // Includes k_master_init's warm start, writes z and pi of the final point, and
 // (cg != nullptr) the round's record.  K = 0: the pool size is read from

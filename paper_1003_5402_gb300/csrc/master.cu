@@ -1365,6 +1365,34 @@ int master_grid_max(int num_sms) { return 4 * num_sms; }
 
 int master_hess_grid(int num_sms) { return 2 * num_sms; }
 
+// Diagnostic of the bounded barrier wait: a cooperative launch of `blocks`
+// blocks meets at grid_sync, except block `absent`, which leaves without
+// arriving.  The others must give up after GRID_WAIT_LIMIT polls, mark the
+// barrier broken and report (out[0] = blocks that gave up, out[1] = blocks
+// that passed).  Nothing faults and every wait ends.
+__global__ void k_barrier_check(GridBar* gb, int absent, int* out) {
+    __shared__ unsigned s_target;
+    __shared__ int s_flag;
+    if (threadIdx.x == 0) s_target = 0;
+    if ((int)blockIdx.x == absent) return;  // the whole block leaves: it never arrives
+    const bool ok = grid_sync(gb, gridDim.x, &s_target, &s_flag);
+    if (threadIdx.x == 0) atomicAdd(&out[ok ? 1 : 0], 1);
+}
+
+cudaError_t launch_barrier_check(GridBar* gb, int blocks, int absent, int* out, cudaStream_t stream) {
+    void* args[] = {(void*)&gb, (void*)&absent, (void*)&out};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(32);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, (const void*)k_barrier_check, args);
+}
+
 cudaError_t master_configure() {
     cudaError_t e = cudaFuncSetAttribute(k_master_eval, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)master_eval_smem(KMAX));
