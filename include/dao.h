@@ -146,6 +146,20 @@ dao_status dao_check_bounded_wait(int32_t device, int32_t* gave_up, int32_t* pas
 /* Empty the aperture pool (y = [], z = 0) keeping D on the device. */
 dao_status dao_reset(dao_ctx* ctx);
 
+/* Append n apertures to the pool and solve the master problem once (Sec. 2.3)
+ * over the enlarged pool: re-planning from a saved pool (dao_apertures,
+ * dao_intensities of an earlier context) on this context's D, or resuming a
+ * solve.  beams[n] and leaf_lr[n][2 * max rows] (host; rows past a beam's
+ * own count are ignored) as dao_add_aperture takes them; their dose columns
+ * come from this context's D.  y_start[n] (host, >= 0, or NULL for zeros)
+ * starts the master on the new apertures, the last of them at 0 as for every
+ * added aperture; the apertures already in the pool start from their current
+ * intensities.  *objective (host, may be NULL) receives F at the master
+ * optimum.  Everything is checked before the pool changes (DAO_EINVAL);
+ * DAO_ESTATE if the pool would exceed k_max.  n = 0 changes nothing. */
+dao_status dao_import_apertures(dao_ctx* ctx, int32_t n, const int32_t* beams, const int32_t* leaf_lr,
+                                const double* y_start, double* objective);
+
 /* Pricing sub-problem (Eq. 8, Sec. 2.3) at the current master optimum:
  * pi = grad F(z), w = D^T pi, per-MLC-row minimum-sum consecutive interval,
  * per-beam sum, beam with the smallest sum (lowest index on ties).  Outputs

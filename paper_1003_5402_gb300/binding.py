@@ -87,6 +87,7 @@ SIGNATURES = {
     "dao_destroy": (None, [_P]),
     "dao_release_cached_memory": (C.c_int, [C.c_int32]),
     "dao_check_bounded_wait": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "dao_import_apertures": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "dao_reset": (C.c_int, [_P]),
     "dao_price": (C.c_int, [_P, _I32P, _I32P, _F64P]),
     "dao_add_aperture": (C.c_int, [_P, C.c_int32, _I32P, _F64P]),
@@ -270,6 +271,23 @@ class Plan:
         lr = np.ascontiguousarray(np.asarray(leaves, dtype=np.int32).reshape(-1))
         F = C.c_double()
         _check(load().dao_add_aperture(self.h, int(beam), _ptr(lr, C.c_int32), C.byref(F)), "dao_add_aperture")
+        return F.value
+
+    def import_apertures(self, apertures, y_start=None) -> float:
+        """Append saved apertures [(beam, leaves [rows, 2]), ...] and solve the master
+        once (dao_import_apertures); returns the objective."""
+        n = len(apertures)
+        stride = 2 * self.max_rows
+        beams = np.array([int(b) for b, _ in apertures], dtype=np.int32)
+        lr = np.zeros((max(n, 1), stride), dtype=np.int32)
+        for i, (_, lv) in enumerate(apertures):
+            flat = np.asarray(lv, dtype=np.int32).reshape(-1)
+            lr[i, : flat.size] = flat
+        y = None if y_start is None else np.ascontiguousarray(np.asarray(y_start, dtype=np.float64))
+        F = C.c_double(float("nan"))
+        _check(load().dao_import_apertures(self.h, n, _ptr(beams, C.c_int32), _ptr(lr, C.c_int32),
+                                           None if y is None else _ptr(y, C.c_double), C.byref(F)),
+               "dao_import_apertures")
         return F.value
 
     def solve(self, n_apertures: int):

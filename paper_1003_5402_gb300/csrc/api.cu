@@ -661,6 +661,8 @@ bool is_duplicate(const dao_ctx* c, int beam, const int32_t* lr) {
 }
 
 // form the new column (Eq. 2) into slab column K, record the aperture
+// The mask goes through the context's pinned staging block: the caller
+// synchronises before the next call refills it.
 dao_status add_column(dao_ctx* c, int beam, const int32_t* lr, float* out, int stride) {
     const int nb = c->rows[beam] * c->cols[beam];
     float* m = reinterpret_cast<float*>(c->pinned + c->off_mask);
@@ -675,8 +677,8 @@ dao_status add_column(dao_ctx* c, int beam, const int32_t* lr, float* out, int s
     return DAO_OK;
 }
 
-dao_status add_aperture(dao_ctx* c, int beam, const int32_t* lr, double* F) {
-    if (c->K >= c->K_cap) return fail(DAO_ESTATE, "aperture pool is full (k_max)");
+// Column and table entry of aperture (beam, lr) at pool index K; no master solve.
+dao_status append_aperture(dao_ctx* c, int beam, const int32_t* lr) {
     DAO_TRY(add_column(c, beam, lr, c->slab + (size_t)c->K * c->ld, 1));
     const int stride = 2 * c->max_rows;
     c->ap_beam_h.push_back(beam);
@@ -691,6 +693,12 @@ dao_status add_aperture(dao_ctx* c, int beam, const int32_t* lr, double* F) {
     DAO_CU(cudaMemcpyAsync(c->ap_lr + (size_t)c->K * stride, &c->ap_lr_h[(size_t)c->K * stride], sizeof(int) * stride,
                            cudaMemcpyHostToDevice, c->stream));
     c->K += 1;
+    return DAO_OK;
+}
+
+dao_status add_aperture(dao_ctx* c, int beam, const int32_t* lr, double* F) {
+    if (c->K >= c->K_cap) return fail(DAO_ESTATE, "aperture pool is full (k_max)");
+    DAO_TRY(append_aperture(c, beam, lr));
     return master_solve(c, F);
 }
 
@@ -1224,6 +1232,36 @@ dao_status dao_price(dao_ctx* c, int32_t* beam, int32_t* leaf_lr, double* rc) {
     if (st != DAO_OK) return st;
     if (rc) *rc = r;
     return r < -c->tau ? DAO_OK : DAO_OPTIMAL;
+}
+
+dao_status dao_import_apertures(dao_ctx* c, int32_t n, const int32_t* beams, const int32_t* leaf_lr,
+                                const double* y_start, double* objective) {
+    DAO_TRY(check_ctx(c));
+    if (n < 0 || (n > 0 && (beams == nullptr || leaf_lr == nullptr)))
+        return fail(DAO_EINVAL, "n >= 0 apertures with their beams and leaves");
+    if (c->K + n > c->K_cap) return fail(DAO_ESTATE, "aperture pool is full (k_max)");
+    const int stride = 2 * c->max_rows;
+    for (int i = 0; i < n; ++i) {  // all checked before the pool changes
+        DAO_TRY(validate_aperture(c, beams[i], leaf_lr + (size_t)i * stride));
+        if (y_start != nullptr && !(y_start[i] >= 0.0 && std::isfinite(y_start[i])))
+            return fail(DAO_EINVAL, "starting intensities must be finite and >= 0");
+    }
+    const int K0 = c->K;
+    for (int i = 0; i < n; ++i) {
+        DAO_TRY(append_aperture(c, beams[i], leaf_lr + (size_t)i * stride));
+        DAO_TRY(sync(c));  // the column's mask is staged in one pinned buffer, refilled by the next aperture
+    }
+    if (n > 0) {
+        // the master starts from y_start on the imported apertures (the last at 0,
+        // as for every added aperture) and from the current optimum on the rest
+        std::vector<double> y0(n, 0.0);
+        if (y_start != nullptr) y0.assign(y_start, y_start + n);
+        DAO_CU(cudaMemcpyAsync(c->mb.st->y + K0, y0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+        const dao_status st = master_solve(c, objective);
+        c->count_launches();
+        return st;
+    }
+    return DAO_OK;  // n = 0: nothing changes, *objective is not written
 }
 
 dao_status dao_add_aperture(dao_ctx* c, int32_t beam, const int32_t* leaf_lr, double* objective) {
