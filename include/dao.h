@@ -101,8 +101,10 @@ typedef struct dao_options {
     int32_t precision;         /* DAO_PREC_FP32 (default), DAO_PREC_FP16 or DAO_PREC_BF16 storage of D */
     int32_t device;            /* CUDA device ordinal (default 0) */
     void* stream;              /* cudaStream_t to run on; NULL = a stream owned by the context */
-    int32_t use_graphs;        /* 1 (default): dao_solve runs each round as one CUDA graph; 0: host-driven
-                                * launches */
+    int32_t use_graphs;        /* 1 (default): dao_solve runs on the device without host synchronisation
+                                * between rounds: with the persistent master one CUDA graph per context
+                                * whose device-side while node runs every round, else one graph per round;
+                                * 0: host-driven launches */
     int32_t master_persistent; /* 1 (default): each master solve is one cooperative kernel whose blocks
                                 * iterate together (bounded grid barriers); 0, or where a cooperative
                                 * launch is not available: one launch per evaluation kernel */

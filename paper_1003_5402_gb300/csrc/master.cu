@@ -902,7 +902,7 @@ __device__ __forceinline__ void master_step_body(MasterDev* __restrict__ st, int
 // block waits for another.  The while-node condition is set to "not done" on
 // every path that continues; the evaluation cap inside the step guarantees that
 // done is reached.
-__global__ void __launch_bounds__(STEP_T) k_master_reduce_step(const float* __restrict__ H_part,
+__global__ void __launch_bounds__(STEP_T, 1) k_master_reduce_step(const float* __restrict__ H_part,
                                                                const double* __restrict__ g_part,
                                                                const float* __restrict__ gn_part,
                                                                const double* __restrict__ F_part, int GH, int GE,
