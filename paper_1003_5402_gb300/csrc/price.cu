@@ -64,14 +64,14 @@ __global__ void __launch_bounds__(256) k_price_commit(const double* __restrict__
     }
     int b = 0;
     double rc = 0.0;
-    const int verdict = pricing::decide(row_v, beam_row0, n_beams, row_lr, rows, tau, K, lr_stride, ap_beam, ap_lr,
+    const int outcome = pricing::decide(row_v, beam_row0, n_beams, row_lr, rows, tau, K, lr_stride, ap_beam, ap_lr,
                                         s_sum, &b, &rc);
     if (tid == 0) {
         pr->beam = b;
         pr->rc = rc;
     }
-    if (verdict != pricing::VERDICT_NEW) {
-        if (tid == 0) cg->done = verdict;
+    if (outcome != pricing::OUTCOME_NEW) {
+        if (tid == 0) cg->done = outcome;
         finish(1, 1);
         return;
     }

@@ -89,11 +89,11 @@ __device__ __forceinline__ void row_best(const float* __restrict__ w, int4 ri, i
     }
 }
 
-enum { VERDICT_NEW = 0, VERDICT_OPTIMAL = 1, VERDICT_DUPLICATE = 2 };
+enum { OUTCOME_NEW = 0, OUTCOME_OPTIMAL = 1, OUTCOME_DUPLICATE = 2 };
 
 // Whole block (every thread calls it): beam sums into s_sum (n_beams doubles
 // of shared memory), argmin, stop test, then the duplicate test against the
-// K - 1 apertures of the pool.  Every thread returns the same verdict, beam
+// K - 1 apertures of the pool.  Every thread returns the same outcome, beam
 // and reduced cost.
 __device__ __forceinline__ int decide(const double* __restrict__ row_v, const int* __restrict__ beam_row0,
                                       int n_beams, const int2* __restrict__ row_lr, const int* __restrict__ rows,
@@ -121,7 +121,7 @@ __device__ __forceinline__ int decide(const double* __restrict__ row_v, const in
     const int b = s_best;
     *beam_out = b;
     *rc_out = s_rc;
-    if (!(s_rc < -tau)) return VERDICT_OPTIMAL;
+    if (!(s_rc < -tau)) return OUTCOME_OPTIMAL;
     const int R = rows[b], r0 = beam_row0[b];
     for (int k = tid; k < K - 1; k += blockDim.x) {
         if (ap_beam[k] != b) continue;
@@ -133,7 +133,7 @@ __device__ __forceinline__ int decide(const double* __restrict__ row_v, const in
         if (same) s_dup = 1;
     }
     __syncthreads();
-    return s_dup ? VERDICT_DUPLICATE : VERDICT_NEW;
+    return s_dup ? OUTCOME_DUPLICATE : OUTCOME_NEW;
 }
 
 }  // namespace pricing

@@ -511,10 +511,10 @@ __global__ void __launch_bounds__(256) k_commit_column(const int* __restrict__ c
     const int K = __ldcg(&cg->rs_K) + 1;  // pool size with the new aperture
     int b = 0;
     double rc = 0.0;
-    const int verdict = pricing::decide(ca.row_v, ca.beam_row0, ca.n_beams, ca.row_lr, ca.rows, ca.tau, K,
+    const int outcome = pricing::decide(ca.row_v, ca.beam_row0, ca.n_beams, ca.row_lr, ca.rows, ca.tau, K,
                                         ca.lr_stride, ca.ap_beam, ca.ap_lr, s_sum, &b, &rc);
-    if (verdict != pricing::VERDICT_NEW) {
-        if (lead) cg->done = verdict;
+    if (outcome != pricing::OUTCOME_NEW) {
+        if (lead) cg->done = outcome;
         finish(1, 1);
         return;
     }
