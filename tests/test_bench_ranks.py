@@ -1,0 +1,74 @@
+"""The multi-GPU path of bench.py on the host: replicas only, so the ranks
+exchange nothing but the timing.  Two gloo ranks on the CPU check that every
+rank gets the slowest rank's time, that the whole-job time per plan divides it
+by steps x ranks, and that under torchrun only rank 0 of the reference arm
+does any work."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+pytestmark = pytest.mark.timeout(120)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, ws, port, local_ms, steps, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        dist.barrier()
+        total = bench.max_over_ranks(local_ms[rank], ws, "cpu")
+        out.put((rank, total, bench.whole_job_ms_per_plan(total, steps, ws)))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    local_ms = [120.0, 95.5]
+    steps = 10
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, local_ms, steps, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=90) for _ in procs)
+    for p in procs:
+        p.join(timeout=30)
+        assert p.exitcode == 0
+    assert [r for r, _, _ in res] == [0, 1]
+    for _, total, per_plan in res:
+        assert total == 120.0
+        assert per_plan == pytest.approx(120.0 / (steps * 2))
+
+
+def test_single_rank_needs_no_process_group():
+    import bench
+    assert bench.max_over_ranks(7.5, 1, "cpu") == 7.5
+    assert bench.whole_job_ms_per_plan(80.0, 10, 1) == 8.0
+
+
+def test_reference_arm_other_ranks_do_nothing(monkeypatch, capsys):
+    import argparse
+
+    import bench
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    called = []
+    monkeypatch.setattr(bench, "oracle_plan_seconds", lambda *a, **k: called.append(a) or 0.0)
+    bench.run_reference(argparse.Namespace(config="tiny", apertures=5, steps=1, warmup=3, gpus=2))
+    assert called == [] and capsys.readouterr().out == ""
