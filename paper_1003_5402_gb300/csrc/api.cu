@@ -336,6 +336,7 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     DAO_TRY(c->dalloc(&c->D.rowptr, (size_t)V + 1));
     DAO_TRY(c->dalloc(&c->vstruct, V));
     // checks of every row and label, padded row offsets, voxels per structure
+    TraceRange range("device checks and layout");
     BuildCheck chk{};
     DAO_TRY(cu(build_check(t_rp, t_col, t_val, nnz, V, N, t_lab, S, pad_m, t_plen, t_bsum, c->vstruct, c->D.rowptr,
                            t_chk, st), "input checks"));
@@ -1105,6 +1106,7 @@ const char* dao_last_error(void) { return g_err.c_str(); }
 
 dao_status dao_create(const dao_csr* D, const dao_geometry* g, const dao_structures* s, const dao_weights* w,
                       const double* prescriptions, const dao_options* opt_in, dao_ctx** out) {
+    TraceRange trace("dao_create");
     if (!out) return fail(DAO_EINVAL, "null output pointer");
     *out = nullptr;
     dao_options opt;
@@ -1236,6 +1238,7 @@ dao_status dao_price(dao_ctx* c, int32_t* beam, int32_t* leaf_lr, double* rc) {
 
 dao_status dao_import_apertures(dao_ctx* c, int32_t n, const int32_t* beams, const int32_t* leaf_lr,
                                 const double* y_start, double* objective) {
+    TraceRange range("dao_import_apertures");
     DAO_TRY(check_ctx(c));
     if (n < 0 || (n > 0 && (beams == nullptr || leaf_lr == nullptr)))
         return fail(DAO_EINVAL, "n >= 0 apertures with their beams and leaves");
@@ -1273,6 +1276,7 @@ dao_status dao_add_aperture(dao_ctx* c, int32_t beam, const int32_t* leaf_lr, do
 }
 
 dao_status dao_solve(dao_ctx* c, int32_t n_apertures, int32_t* n_done, double* trace) {
+    TraceRange range("dao_solve");
     DAO_TRY(check_ctx(c));
     if (n_apertures < 0) return fail(DAO_EINVAL, "negative aperture count");
     if (c->opt.use_graphs && !c->prof_on) {
@@ -1313,6 +1317,7 @@ dao_status dao_solve(dao_ctx* c, int32_t n_apertures, int32_t* n_done, double* t
 }
 
 dao_status dao_dose(dao_ctx* c, float* dose, double* objective) {
+    TraceRange range("dao_dose");
     DAO_TRY(check_ctx(c));
     DAO_CU(launch_fluence(c->ap_beam, c->ap_lr, 2 * c->max_rows, c->mb.st->y, c->K, c->binfo, c->N, c->x, c->stream,
                           &c->launches_i));
@@ -1617,6 +1622,7 @@ dao_status dao_master_stats(const dao_ctx* c, int32_t* evals, int32_t* status, d
 
 dao_status dao_batch_solve(dao_ctx* const* ctxs, int32_t n, int32_t n_apertures, int32_t* n_done, double* traces,
                            int32_t* status) {
+    TraceRange range("dao_batch_solve");
     if (n < 0 || n_apertures < 0 || (n > 0 && ctxs == nullptr))
         return fail(DAO_EINVAL, "dao_batch_solve: n >= 0, n_apertures >= 0 and a context array are required");
     for (int i = 0; i < n; ++i) {
@@ -1665,6 +1671,7 @@ dao_status dao_batch_solve(dao_ctx* const* ctxs, int32_t n, int32_t n_apertures,
 }
 
 dao_status dao_autotune(dao_ctx* c, const char* cache_path, dao_tuning* out) {
+    TraceRange range("dao_autotune");
     DAO_TRY(check_ctx(c));
     const std::string key = tune_key(c);
     int dg = 0, cg = 0, dt = 0;

@@ -1,6 +1,7 @@
 // Internal declarations shared by the libdao.so translation units.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -268,6 +269,16 @@ cudaError_t launch_master_eval(const MasterBuffers& mb, int V, int K, const uint
 cudaError_t launch_master_hess(const MasterBuffers& mb, int K, int mode, cudaStream_t stream, int* launches);
 // Read-only pass over a buffer larger than L2 (cold-cache timing).
 cudaError_t launch_l2_evict(const void* buf, size_t bytes, float* sink, int num_sms, cudaStream_t stream);
+
+// NVTX range for the duration of a scope: the host phases of the library
+// (create, device build, solve, batch, dose, import, autotune) show up on a
+// profiler's timeline; without a profiler attached the calls do nothing.
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Process-wide memory caches (memory.cu): a stream-ordered device pool per
 // device that keeps up to POOL_KEEP_MAX bytes (at most 1/16 of the device) of
