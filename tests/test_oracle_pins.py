@@ -443,3 +443,51 @@ def test_teacher_forcing_reproduces_free_run(micro):
     free = O.column_generation(micro, 8)
     forced = O.column_generation(micro, 8, teacher=free.apertures)
     np.testing.assert_allclose(forced.objective, free.objective, rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Small definitions: the aperture indicator (Eq. 2), the KKT residual of the
+# master's bound-constrained optimality and the pricing tolerance
+# ---------------------------------------------------------------------------
+
+class _Geometry:
+    """Two beams: 2 rows x 3 beamlets, then 3 rows x 2 beamlets (N = 12)."""
+    rows = np.array([2, 3])
+    cols = np.array([3, 2])
+
+
+def test_aperture_mask_by_hand():
+    g = _Geometry()
+    # beam 1 starts at beamlet 6; row r covers beamlets 6 + 2r .. 6 + 2r + 1
+    m = O.aperture_mask(g, 1, [(0, 2), (1, 1), (1, 2)])
+    want = np.zeros(12)
+    want[[6, 7, 11]] = 1.0
+    assert np.array_equal(m, want)
+    # beam 0, row 0 open on [1, 3), row 1 closed
+    m0 = O.aperture_mask(g, 0, [(1, 3), (0, 0)])
+    want0 = np.zeros(12)
+    want0[[1, 2]] = 1.0
+    assert np.array_equal(m0, want0)
+
+
+def test_aperture_value_is_sum_of_open_prices():
+    g = _Geometry()
+    w = np.arange(12, dtype=np.float64) - 5.0
+    assert O.aperture_value(g, w, 1, [(0, 2), (1, 1), (1, 2)]) == w[6] + w[7] + w[11]
+
+
+@pytest.mark.parametrize("y,g,res", [
+    ([0.0, 2.0, 1.0], [3.0, 0.0, -1.0], 1.0),   # bound active with g > 0: 0; free with g = 0: 0; free with g != 0: |g|
+    ([0.0], [-2.5], 2.5),                        # at the bound, descent into the feasible set
+    ([0.4], [1.0], 0.4),                         # the projected step stops at the bound: |y - 0|
+    ([], [], 0.0),
+])
+def test_kkt_residual_of_the_bound_constrained_problem(y, g, res):
+    assert O.kkt_residual(np.array(y), np.array(g)) == res
+
+
+def test_pricing_tolerance_is_rel_max_d_times_l1_of_pi():
+    D = sp.csr_matrix(np.array([[0.5, 0.0, 2.0], [0.0, 1.5, 0.25]]))
+    pi = np.array([-3.0, 4.0])
+    assert O.pricing_tolerance(D, pi, rel=1e-3) == pytest.approx(1e-3 * 2.0 * 7.0, rel=0, abs=1e-18)
+    assert O.pricing_tolerance(sp.csr_matrix((2, 3)), pi) == 0.0
