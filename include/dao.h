@@ -43,7 +43,7 @@ typedef enum dao_status {
     DAO_EINVAL = -1,      /* invalid argument; nothing changed */
     DAO_ENOMEM = -2,      /* device or host allocation failed; nothing changed */
     DAO_ECUDA = -3,       /* a CUDA call failed; destroy the context */
-    DAO_ETIMEOUT = -4,    /* a bounded device-side wait gave up */
+    DAO_ETIMEOUT = -4,    /* a bounded device-side wait gave up; dao_reset the plan */
     DAO_EBUSY = -5,       /* no free slot / not enough free device memory */
     DAO_ESTATE = -6       /* call not valid in the current state (e.g. pool full) */
 } dao_status;

@@ -46,7 +46,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     """Compile and link; returns the library path.  Skips work when the library is
     newer than every source and header."""
     srcs = sources()
-    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     deps.append(os.path.join(ROOT, "include", "dao.h"))
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)

@@ -110,7 +110,7 @@ struct dao_ctx {
 
     // pinned staging
     unsigned char* pinned = nullptr;
-    size_t off_small = 0, off_rows = 0, off_mask = 0, off_master = 0, off_cg = 0, pinned_bytes = 0;
+    size_t off_small = 0, off_rows = 0, off_mask = 0, off_master = 0, off_cg = 0, off_bar = 0, pinned_bytes = 0;
     size_t pinned_block = 0;  // size of the cached block behind pinned
 
     // per master solve: evaluations (fused passes), final status, KKT residual / max|g(start)|
@@ -537,7 +537,8 @@ dao_status alloc_state(dao_ctx* c) {
     c->off_master = round4(c->off_mask + (size_t)nbmax * sizeof(float) + 64) + 64;
     c->off_master = (c->off_master + 255) / 256 * 256;
     c->off_cg = (c->off_master + sizeof(MasterDev) + 255) / 256 * 256;
-    c->pinned_bytes = c->off_cg + sizeof(CGDev);
+    c->off_bar = (c->off_cg + sizeof(CGDev) + 15) / 16 * 16;
+    c->pinned_bytes = c->off_bar + sizeof(GridBar);
     void* p = nullptr;
     size_t got = c->pinned_bytes;
     DAO_CU(pinned_alloc(&p, &got));
@@ -967,8 +968,14 @@ dao_status solve_graph_end(dao_ctx* c, const GraphSolve& gs, int n_apertures, in
                            dao_status* result) {
     const int K0 = gs.K0, K1 = gs.K1;
     CGDev* h = reinterpret_cast<CGDev*>(c->pinned + c->off_cg);
+    GridBar* hb = reinterpret_cast<GridBar*>(c->pinned + c->off_bar);
     DAO_CU(cudaMemcpyAsync(h, c->cg, sizeof(CGDev), cudaMemcpyDeviceToHost, c->stream));
+    if (c->mb.GP > 0) DAO_CU(cudaMemcpyAsync(hb, c->mb.bar, sizeof(GridBar), cudaMemcpyDeviceToHost, c->stream));
     DAO_TRY(sync(c));
+    // a barrier of a cooperative master solve gave up: the rounds after it returned
+    // at entry, so the device pool no longer matches the host's
+    if (c->mb.GP > 0 && hb->broken)
+        return fail(DAO_ETIMEOUT, "a grid barrier of the master solve timed out; reset the plan");
     const int K = h->K;
     const int stride = 2 * c->max_rows;
     if (K > K0) {
