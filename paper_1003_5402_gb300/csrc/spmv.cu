@@ -88,13 +88,27 @@ __global__ void __launch_bounds__(256) k_dose(const int* __restrict__ rowptr, co
         float acc = 0.f;
         if (row < V) {
             const int p0 = rowptr[row] >> 2, p1 = rowptr[row + 1] >> 2;
-            for (int p = p0 + sub; p < p1; p += G) {
+            // two groups of the lane (p, p + G) requested together, summed in order
+            for (int p = p0 + sub; p < p1; p += 2 * G) {
+                const bool two = p + G < p1;
                 const int4 c = __ldg(col4 + p);
                 const float4 v = __ldg(val4 + p);
+                int4 c2 = make_int4(0, 0, 0, 0);
+                float4 v2 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (two) {
+                    c2 = __ldg(col4 + p + G);
+                    v2 = __ldg(val4 + p + G);
+                }
                 acc = fmaf(v.x, xs[c.x], acc);
                 acc = fmaf(v.y, xs[c.y], acc);
                 acc = fmaf(v.z, xs[c.z], acc);
                 acc = fmaf(v.w, xs[c.w], acc);
+                if (two) {
+                    acc = fmaf(v2.x, xs[c2.x], acc);
+                    acc = fmaf(v2.y, xs[c2.y], acc);
+                    acc = fmaf(v2.z, xs[c2.z], acc);
+                    acc = fmaf(v2.w, xs[c2.w], acc);
+                }
             }
         }
 #pragma unroll
@@ -342,17 +356,31 @@ __global__ void __launch_bounds__(256) k_dose16(const int* __restrict__ rowptr, 
         float acc = 0.f;
         if (row < V) {
             const int p0 = rowptr[row] >> 3, p1 = rowptr[row + 1] >> 3;
-            for (int p = p0 + sub; p < p1; p += G) {
+            // two groups of the lane (p, p + G) requested together, summed in order
+            for (int p = p0 + sub; p < p1; p += 2 * G) {
+                const bool two = p + G < p1;
                 const uint4 cw = __ldg(col8 + p);
                 const uint4 vw = __ldg(val8 + p);
-                const unsigned cs[4] = {cw.x, cw.y, cw.z, cw.w};
-                const unsigned vs[4] = {vw.x, vw.y, vw.z, vw.w};
+                uint4 cw2 = make_uint4(0u, 0u, 0u, 0u), vw2 = make_uint4(0u, 0u, 0u, 0u);
+                if (two) {
+                    cw2 = __ldg(col8 + p + G);
+                    vw2 = __ldg(val8 + p + G);
+                }
+                const unsigned cs[8] = {cw.x, cw.y, cw.z, cw.w, cw2.x, cw2.y, cw2.z, cw2.w};
+                const unsigned vs[8] = {vw.x, vw.y, vw.z, vw.w, vw2.x, vw2.y, vw2.z, vw2.w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const float2 v2 = unpack2<BF>(vs[q]);
                     acc = fmaf(v2.x, xs(cs[q] & 0xffffu), acc);
                     acc = fmaf(v2.y, xs(cs[q] >> 16), acc);
                 }
+                if (two)
+#pragma unroll
+                    for (int q = 4; q < 8; ++q) {
+                        const float2 v2 = unpack2<BF>(vs[q]);
+                        acc = fmaf(v2.x, xs(cs[q] & 0xffffu), acc);
+                        acc = fmaf(v2.y, xs(cs[q] >> 16), acc);
+                    }
             }
         }
 #pragma unroll
