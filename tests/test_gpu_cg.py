@@ -189,12 +189,15 @@ def test_add_aperture_validation_and_pool_limit(torch):
         assert e.value.status == -6
 
 
-def test_prostate_full_size_properties(torch):
+@pytest.mark.parametrize("workload", ["prostate", "hn"])
+def test_full_size_properties(torch, workload):
     """The benchmark workload (prostate-shaped, 50 apertures) in the launch
-    configuration the benchmark times: objective non-increasing, dose at sampled
-    voxels equal to the oracle's sum over the plan's beamlets, master KKT with
-    the oracle's FP64 aperture columns, first apertures equal to the oracle's."""
-    case = P.make_case(P.spec_prostate())
+    configuration the benchmark times, and the H&N-shaped workload (280,699
+    voxels, 4,500 beamlets, two targets) in FP32: objective non-increasing,
+    dose at sampled voxels equal to the oracle's sum over the plan's
+    beamlets, master KKT with the oracle's FP64 aperture columns, first
+    apertures and objectives equal to the oracle's."""
+    case = P.make_case(P.spec_prostate() if workload == "prostate" else P.spec_hn())
     K = 50
     with _plan(case, torch) as plan:
         st, n, trace = plan.solve(K)
