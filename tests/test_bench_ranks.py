@@ -72,3 +72,28 @@ def test_reference_arm_other_ranks_do_nothing(monkeypatch, capsys):
     monkeypatch.setattr(bench, "oracle_plan_seconds", lambda *a, **k: called.append(a) or 0.0)
     bench.run_reference(argparse.Namespace(config="tiny", apertures=5, steps=1, warmup=3, gpus=2))
     assert called == [] and capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_one_contract_line(monkeypatch, capsys):
+    """Rank 0 of the reference arm times the oracle on the host and prints one
+    JSON line with the keys of the bench contract (tiny workload, 4 apertures)."""
+    import argparse
+    import json
+
+    import bench
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    bench.run_reference(argparse.Namespace(config="tiny", apertures=4, steps=1, warmup=3, gpus=1))
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["metric"] == "ms per 4-aperture plan" and d["unit"] == "ms"
+    assert d["higher_is_better"] is False and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 3
+    assert d["value"] > 0 and d["ms_per_step"] == d["value"]
+    assert isinstance(d["config"]["workload"], str)
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
