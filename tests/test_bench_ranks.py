@@ -2,7 +2,8 @@
 exchange nothing but the timing.  Two gloo ranks on the CPU check that every
 rank gets the slowest rank's time, that the whole-job time per plan divides it
 by steps x ranks, and that under torchrun only rank 0 of the reference arm
-does any work."""
+does any work.  On one rank the reference arm's line carries the contract's
+keys."""
 import os
 import socket
 import sys
