@@ -23,7 +23,9 @@
  *   - Errors: calls return a dao_status; no exception or abort crosses the
  *     ABI.  dao_last_error() gives a message for the calling thread's last
  *     failed call.  A failed call leaves the context usable unless it returns
- *     DAO_ECUDA (device state is then undefined; destroy the context).
+ *     DAO_ECUDA (device state is then undefined; destroy the context) or
+ *     DAO_ETIMEOUT from a solve (the device pool may hold rounds the host
+ *     did not record; dao_reset the context).
  *   - A context is not thread-safe; different contexts are independent.
  */
 #ifndef DAO_H
