@@ -77,25 +77,61 @@ def _workload_config(case, name, extra=None):
 # ---------------------------------------------------------------------------
 
 class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons every 50 ms, from
+    before the warm-up to the end of the timed region.  ``timed()`` brackets the
+    timed region on the host clock; ``stop()`` summarises the samples taken
+    inside it, or, when the region is shorter than the sampling period, the
+    samples of the warm-up and the timed region together (both under load), and
+    says which.  The CSV goes to $DAO_BENCH_CLOCKS_DIR (default: the temp dir)."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,timestamp")
+    PERIOD_MS = 50
+    TS_FORMAT = "%Y/%m/%d %H:%M:%S.%f"
 
     def __init__(self, index: int, enabled: bool = True):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.tw = self.t0 = self.t1 = None
+        folder = os.environ.get("DAO_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(folder, f"dao_bench_clocks_rank{index}.csv")
         if enabled:
+            self.f = None
             try:
-                os.makedirs(os.path.dirname(self.path), exist_ok=True)
+                os.makedirs(folder, exist_ok=True)
                 self.f = open(self.path, "w")
                 self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.QUERY}",
-                                              "--format=csv,noheader,nounits", "-lms", "200"],
+                                              "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                                              stdout=self.f, stderr=subprocess.DEVNULL)
             except Exception:
                 self.proc = None
+                if self.f is not None:
+                    self.f.close()
+
+    def wait_first_sample(self, limit_s: float = 3.0):
+        """Block until nvidia-smi has written its first sample (at most
+        limit_s), then mark the start of the loaded part of the run."""
+        import datetime
+        t_end = time.perf_counter() + limit_s
+        while self.proc is not None and time.perf_counter() < t_end:
+            try:
+                if os.path.getsize(self.path) > 0:
+                    break
+            except OSError:
+                pass
+            time.sleep(0.01)
+        self.tw = datetime.datetime.now()
+
+    def timed(self, begin: bool):
+        import datetime
+        if begin:
+            self.t0 = datetime.datetime.now()
+        else:
+            self.t1 = datetime.datetime.now()
 
     def stop(self):
+        import datetime
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -104,24 +140,40 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             f = [t.strip() for t in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                sm, mx = float(f[1]), float(f[2])
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
+            try:
+                ts = datetime.datetime.strptime(f[9], self.TS_FORMAT)
+            except ValueError:
+                ts = None
+            rows.append((ts, sm, mx, {nm for nm, v in zip(names, f[5:9]) if v.lower().startswith("active")}))
+        if not rows:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "reasons": sorted(reasons)}
+
+        def between(a, b):
+            return [r for r in rows if a is not None and b is not None and r[0] is not None and a <= r[0] <= b]
+        inside, scope = between(self.t0, self.t1), "timed region"
+        if not inside:
+            inside = between(self.tw, self.t1)
+            scope = "warm-up and timed region (the timed region is shorter than the sampling period)"
+        if not inside and self.t0 is not None:
+            inside = [r for r in rows if r[0] is not None and r[0] >= self.t0][:1]
+            scope = "first sample after the timed region began"
+        if not inside and all(r[0] is None for r in rows):
+            inside, scope = rows, "every sample of the run (timestamps unreadable)"
+        if not inside:
+            return None
+        reasons = set().union(*(r[3] for r in inside))
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "samples": len(inside), "period_ms": self.PERIOD_MS, "scope": scope, "reasons": sorted(reasons)}
 
 
 # ---------------------------------------------------------------------------
@@ -398,13 +450,15 @@ def run_ours(a):
         torch.cuda.synchronize()
 
     plan = Plan(case, device=dev, stream=stream.cuda_stream)
+    sampler = ClockSampler(dev, enabled=not a.no_clocks)
+    sampler.wait_first_sample()
     for _ in range(a.warmup):
         plan.reset()
         plan.solve(a.apertures)
     barrier()
-    sampler = ClockSampler(dev, enabled=not a.no_clocks)
     l0 = plan.launch_count()
     evs = []
+    sampler.timed(True)
     t_host = time.perf_counter()
     for _ in range(a.steps):
         flush.zero_()
@@ -417,6 +471,7 @@ def run_ours(a):
         evs.append((e0, e1))
     barrier()
     t_host = time.perf_counter() - t_host
+    sampler.timed(False)
     clocks = sampler.stop()
     launches = plan.launch_count() - l0
     step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
