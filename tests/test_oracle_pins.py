@@ -491,3 +491,31 @@ def test_pricing_tolerance_is_rel_max_d_times_l1_of_pi():
     pi = np.array([-3.0, 4.0])
     assert O.pricing_tolerance(D, pi, rel=1e-3) == pytest.approx(1e-3 * 2.0 * 7.0, rel=0, abs=1e-18)
     assert O.pricing_tolerance(sp.csr_matrix((2, 3)), pi) == 0.0
+
+
+def test_fluence_of_overlapping_apertures_by_hand():
+    """Eq. 7: a beamlet's fluence is the sum of the intensities of the apertures
+    that leave it open."""
+    g = _Geometry()
+    aps = [(1, [(0, 2), (1, 1), (1, 2)]),   # beamlets 6, 7, 11
+           (1, [(1, 2), (0, 2), (0, 0)]),   # beamlets 7, 8, 9
+           (0, [(0, 3), (0, 0)])]           # beamlets 0, 1, 2
+    x = O.fluence(g, aps, [0.5, 2.0, 1.25])
+    want = np.zeros(12)
+    want[[0, 1, 2]] = 1.25
+    want[6] = 0.5
+    want[7] = 0.5 + 2.0
+    want[[8, 9]] = 2.0
+    want[11] = 0.5
+    assert np.array_equal(x, want)
+    assert np.array_equal(O.fluence(g, [], []), np.zeros(12))
+
+
+def test_curvature_on_each_side_of_the_thresholds():
+    """The generalised second derivative of one voxel's penalty: 2 alpha below
+    T^-, 2 beta above T^+, 0 between them and at either kink (strict
+    inequalities), both terms at once when T^+ < T^-."""
+    vt = O.VoxelTerms(alpha=np.full(6, 3.0), t_under=np.array([1.0, 1.0, 1.0, 1.0, 1.0, 1.0]),
+                      beta=np.full(6, 0.5), t_over=np.array([1.2, 1.2, 1.2, 1.2, 1.2, 0.4]))
+    z = np.array([0.9, 1.0, 1.1, 1.2, 1.3, 0.6])
+    assert np.array_equal(O.curvature(z, vt), [6.0, 0.0, 0.0, 0.0, 1.0, 7.0])
