@@ -100,7 +100,8 @@ typedef struct dao_options {
     double master_tol;         /* stop when every |y_k - P(y_k - g_k)| <= master_tol * max|g(start)|
                                 * + 64 u sum_j |S_jk pi_j| (u = 2^-24: FP32 rounding of g) (1e-6) */
     double price_tol;          /* optimal when reduced cost >= -price_tol * max(D) * ||grad F(0)||_1 (1e-7) */
-    int32_t precision;         /* DAO_PREC_FP32 (default), DAO_PREC_FP16 or DAO_PREC_BF16 storage of D */
+    int32_t precision;         /* DAO_PREC_FP32 (default), DAO_PREC_FP16 or DAO_PREC_BF16 storage of D;
+                                * 16-bit storage keeps beamlet indices in 16 bits (n_beamlets <= 65536) */
     int32_t device;            /* CUDA device ordinal (default 0) */
     void* stream;              /* cudaStream_t to run on; NULL = a stream owned by the context */
     int32_t use_graphs;        /* 1 (default): dao_solve runs on the device without host synchronisation
@@ -117,7 +118,9 @@ typedef struct dao_ctx dao_ctx;
 void dao_options_default(dao_options* opt);
 
 /* Create a plan context: validates the inputs (DAO_EINVAL on a malformed CSR,
- * geometry, labels or weights), copies D to the device in its own layout,
+ * geometry, labels or weights, or on a D whose rows, padded to 4 entries (8
+ * with 16-bit storage), or whose transpose's rows, hold 2^31 entries or more:
+ * the device offsets are 32-bit), copies D to the device in its own layout,
  * builds the transpose D^T (beamlet-major) used by pricing, and expands the
  * per-structure criteria.  prescriptions[s] is T_s^- for target s (ignored
  * for non-targets).  The caller keeps ownership of every input; *out is owned
