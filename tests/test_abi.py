@@ -129,3 +129,15 @@ def test_batch_and_autotune_validate_on_host(lib):
     assert b"null context" in lib.dao_last_error()
     assert lib.dao_batch_solve(None, 0, 5, None, None, None) == binding.DAO_OK
     assert lib.dao_autotune(None, None, None) == binding.DAO_EINVAL
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libdao.so the binding raises at the first call: there is no CPU
+    fallback to route the product path through."""
+    from paper_1003_5402_gb300 import binding
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "libdao.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        binding.load()
+    with pytest.raises(RuntimeError, match="missing"):
+        binding.release_cached_memory(0)
