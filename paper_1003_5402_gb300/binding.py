@@ -157,13 +157,27 @@ def _ptr(a: np.ndarray, ctype):
     return a.ctypes.data_as(C.POINTER(ctype))
 
 
-def _dev(t, dtype_name: str):
-    """Device pointer of a contiguous torch CUDA tensor."""
+def _dev(t, dtype_name: str, n: int = 0, device: int = None):
+    """Device pointer of a contiguous torch CUDA tensor of at least n elements
+    on CUDA device ``device``: the library takes bare pointers, so a short or
+    foreign buffer is refused here rather than read or written out of bounds."""
     if not getattr(t, "is_cuda", False):
         raise TypeError("expected a CUDA tensor")
     if str(t.dtype) != "torch." + dtype_name or not t.is_contiguous():
         raise TypeError(f"expected a contiguous {dtype_name} tensor, got {t.dtype}")
+    if t.numel() < n:
+        raise ValueError(f"expected at least {n} elements, got {t.numel()}")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"expected a tensor on cuda:{device}, got {t.device}")
     return C.c_void_p(t.data_ptr())
+
+
+def _leaves(leaves, n: int) -> np.ndarray:
+    """Flat int32 [L, R) pairs with at least n entries (2 per MLC row read)."""
+    lr = np.ascontiguousarray(np.asarray(leaves, dtype=np.int32).reshape(-1))
+    if lr.size < n:
+        raise ValueError(f"expected {n // 2} (L, R) pairs, got {lr.size // 2}")
+    return lr
 
 
 def options(**kw) -> dao_options:
@@ -225,6 +239,7 @@ class Plan:
         self._keep = []
         self.rows = np.array(case.rows, dtype=np.int32)
         self.cols = np.array(case.cols, dtype=np.int32)
+        self.device = int(o.device)
         sz = self.sizes()
         self.n_voxels, self.n_beamlets, self.n_beams, self.n_mlc_rows, self.max_rows, self.nnz_stored, self.k_max = sz
 
@@ -267,8 +282,13 @@ class Plan:
         b = beam.value
         return st, b, lr[: 2 * self.rows[b]].reshape(-1, 2).copy(), rc.value
 
+    def _rows_of(self, beam: int) -> int:
+        """Leaf entries the library reads for ``beam`` (0 for an invalid beam,
+        which it refuses before reading)."""
+        return 2 * int(self.rows[beam]) if 0 <= int(beam) < len(self.rows) else 0
+
     def add_aperture(self, beam: int, leaves) -> float:
-        lr = np.ascontiguousarray(np.asarray(leaves, dtype=np.int32).reshape(-1))
+        lr = _leaves(leaves, self._rows_of(beam))
         F = C.c_double()
         _check(load().dao_add_aperture(self.h, int(beam), _ptr(lr, C.c_int32), C.byref(F)), "dao_add_aperture")
         return F.value
@@ -325,13 +345,16 @@ class Plan:
     # -- kernel-level calls on torch CUDA tensors
     def k_dose(self, x, z, grad=None, objective: bool = True):
         F = C.c_double()
-        _check(load().dao_k_dose(self.h, _dev(x, "float32"), _dev(z, "float32"),
-                                 _dev(grad, "float32") if grad is not None else None,
+        V, N, d = self.n_voxels, self.n_beamlets, self.device
+        _check(load().dao_k_dose(self.h, _dev(x, "float32", N, d), _dev(z, "float32", V, d),
+                                 _dev(grad, "float32", V, d) if grad is not None else None,
                                  C.byref(F) if objective else None), "dao_k_dose")
         return F.value if objective else None
 
     def k_beamlet_prices(self, pi, w):
-        _check(load().dao_k_beamlet_prices(self.h, _dev(pi, "float32"), _dev(w, "float32")), "dao_k_beamlet_prices")
+        d = self.device
+        _check(load().dao_k_beamlet_prices(self.h, _dev(pi, "float32", self.n_voxels, d),
+                                           _dev(w, "float32", self.n_beamlets, d)), "dao_k_beamlet_prices")
 
     def k_price(self, w):
         """(status, beam, leaves, reduced cost, row best values, row [L, R))."""
@@ -340,19 +363,22 @@ class Plan:
         rc = C.c_double()
         rv = np.zeros(self.n_mlc_rows)
         rl = np.zeros(2 * self.n_mlc_rows, dtype=np.int32)
-        st = _check(load().dao_k_price(self.h, _dev(w, "float32"), C.byref(beam), _ptr(lr, C.c_int32), C.byref(rc),
+        st = _check(load().dao_k_price(self.h, _dev(w, "float32", self.n_beamlets, self.device), C.byref(beam),
+                                       _ptr(lr, C.c_int32), C.byref(rc),
                                        _ptr(rv, C.c_double), _ptr(rl, C.c_int32)), "dao_k_price",
                     (DAO_OK, DAO_OPTIMAL))
         b = beam.value
         return st, b, lr[: 2 * self.rows[b]].reshape(-1, 2).copy(), rc.value, rv, rl.reshape(-1, 2)
 
     def k_aperture_column(self, beam: int, leaves, out):
-        lr = np.ascontiguousarray(np.asarray(leaves, dtype=np.int32).reshape(-1))
-        _check(load().dao_k_aperture_column(self.h, int(beam), _ptr(lr, C.c_int32), _dev(out, "float32")),
+        lr = _leaves(leaves, self._rows_of(beam))
+        _check(load().dao_k_aperture_column(self.h, int(beam), _ptr(lr, C.c_int32),
+                                            _dev(out, "float32", self.n_voxels, self.device)),
                "dao_k_aperture_column")
 
     def k_state(self, z, pi):
-        _check(load().dao_k_state(self.h, _dev(z, "float32"), _dev(pi, "float32")), "dao_k_state")
+        V, d = self.n_voxels, self.device
+        _check(load().dao_k_state(self.h, _dev(z, "float32", V, d), _dev(pi, "float32", V, d)), "dao_k_state")
 
     def k_time(self, kc: str, K: int = 0, reps: int = 20) -> float:
         """Average microseconds per launch of one kernel class (dao_k_time)."""
@@ -405,11 +431,14 @@ def dose_objective_noalloc(row_ptr, col, val, x, voxel_struct, terms, z, grad=No
     voxel_struct, float32 val / x / z / grad, float64 objective of one element)
     and a host float64 terms array [n_structures, 4]; returns the status."""
     t = np.ascontiguousarray(terms, dtype=np.float64).reshape(-1, 4)
+    V, N, d = int(z.numel()), int(x.numel()), z.device.index
+    if col.numel() != val.numel():
+        raise ValueError(f"col and val differ in length ({col.numel()} and {val.numel()})")
     st = load().dao_dose_objective_noalloc(
-        int(z.numel()), int(x.numel()), _dev(row_ptr, "int32"), _dev(col, "int32"), _dev(val, "float32"),
-        _dev(x, "float32"), _dev(voxel_struct, "int32"), int(t.shape[0]), _ptr(t, C.c_double), _dev(z, "float32"),
-        _dev(grad, "float32") if grad is not None else None, _dev(objective, "float64"),
-        C.c_void_p(stream) if stream is not None else None)
+        V, N, _dev(row_ptr, "int32", V + 1, d), _dev(col, "int32", 0, d), _dev(val, "float32", 0, d),
+        _dev(x, "float32", N, d), _dev(voxel_struct, "int32", V, d), int(t.shape[0]), _ptr(t, C.c_double),
+        _dev(z, "float32", V, d), _dev(grad, "float32", V, d) if grad is not None else None,
+        _dev(objective, "float64", 1, d), C.c_void_p(stream) if stream is not None else None)
     return _check(st, "dao_dose_objective_noalloc")
 
 

@@ -141,3 +141,48 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         binding.load()
     with pytest.raises(RuntimeError, match="missing"):
         binding.release_cached_memory(0)
+
+
+class _FakeCudaTensor:
+    """Just the attributes the binding reads from a torch CUDA tensor."""
+
+    def __init__(self, n, dtype="float32", index=0, contiguous=True):
+        self.is_cuda = True
+        self.dtype = "torch." + dtype
+        self._n = n
+        self.device = type("Dev", (), {"index": index, "__str__": lambda s: f"cuda:{index}"})()
+        self._c = contiguous
+
+    def numel(self):
+        return self._n
+
+    def is_contiguous(self):
+        return self._c
+
+    def data_ptr(self):
+        return 4096
+
+
+def test_device_buffers_are_checked_before_the_library_sees_them():
+    """The library takes bare device pointers, so the binding refuses a buffer
+    that is too short, on another device, of another type or strided."""
+    from paper_1003_5402_gb300 import binding
+    assert binding._dev(_FakeCudaTensor(10), "float32", 10, 0).value == 4096
+    assert binding._dev(_FakeCudaTensor(12), "float32", 10, 0).value == 4096
+    with pytest.raises(ValueError, match="at least 10"):
+        binding._dev(_FakeCudaTensor(9), "float32", 10, 0)
+    with pytest.raises(ValueError, match="cuda:1"):
+        binding._dev(_FakeCudaTensor(10, index=0), "float32", 10, 1)
+    with pytest.raises(TypeError):
+        binding._dev(_FakeCudaTensor(10, dtype="float64"), "float32", 10, 0)
+    with pytest.raises(TypeError):
+        binding._dev(_FakeCudaTensor(10, contiguous=False), "float32", 10, 0)
+    with pytest.raises(TypeError, match="CUDA"):
+        binding._dev(np.zeros(10, np.float32), "float32", 10, 0)
+
+
+def test_leaf_arrays_cover_the_rows_the_library_reads():
+    from paper_1003_5402_gb300 import binding
+    assert binding._leaves([(0, 2), (1, 3)], 4).tolist() == [0, 2, 1, 3]
+    with pytest.raises(ValueError, match="expected 3"):
+        binding._leaves([(0, 2), (1, 3)], 6)
