@@ -208,7 +208,10 @@ dao_status dao_sizes(const dao_ctx* ctx, int32_t* n_voxels, int32_t* n_beamlets,
 
 /* ---- kernel-level entry points (device vectors, for parity tests and the
  * bandwidth benchmark).  All run on the context's stream and read the
- * context's device copy of D / D^T. ---- */
+ * context's device copy of D / D^T.  Device pointers are caller-owned memory
+ * of the context's device holding at least the stated number of elements; the
+ * library cannot check either, and a shorter buffer is read or written out of
+ * bounds. ---- */
 
 /* Step a1: z = D x (device float[n_beamlets] -> float[n_voxels]) with the
  * objective epilogue: grad (device, optional) = grad F(z) (Sec. 2.3's pi) and
@@ -229,7 +232,8 @@ dao_status dao_k_price(dao_ctx* ctx, const float* w, int32_t* beam, int32_t* lea
  * (beam, leaf_lr host) into out (device float[n_voxels]). */
 dao_status dao_k_aperture_column(dao_ctx* ctx, int32_t beam, const int32_t* leaf_lr, float* out);
 
-/* Current pi = grad F(z) and z of the last master solution (device outputs). */
+/* Current pi = grad F(z) and z of the last master solution (device outputs,
+ * float[n_voxels] each). */
 dao_status dao_k_state(dao_ctx* ctx, float* z, float* pi);
 
 /* Average device time in microseconds (*us_per_launch, host) of `reps`
