@@ -3,7 +3,7 @@ exchange nothing but the timing.  Two gloo ranks on the CPU check that every
 rank gets the slowest rank's time, that the whole-job time per plan divides it
 by steps x ranks, and that under torchrun only rank 0 of the reference arm
 does any work.  On one rank the reference arm's line carries the contract's
-keys."""
+keys, and the SpMV bandwidth record is assembled from a stand-in plan."""
 import os
 import socket
 import sys
@@ -98,3 +98,31 @@ def test_reference_arm_prints_one_contract_line(monkeypatch, capsys):
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_spmv_bandwidth_record_from_a_stand_in_plan():
+    """The SpMV record's arithmetic: algorithmic bytes over the cold median
+    time, as a fraction of the measured copy peak and of the nominal HBM rate."""
+    import types
+
+    import numpy as np
+
+    import bench
+    case = types.SimpleNamespace(n_voxels=1000, n_beamlets=100, n_beams=4, nnz=50_000)
+    fake_torch = types.SimpleNamespace(rand=lambda n, device=None: np.zeros(n, np.float32),
+                                       randn=lambda n, device=None: np.zeros(n, np.float32),
+                                       empty=lambda n, device=None: np.zeros(n, np.float32),
+                                       empty_like=lambda a: np.zeros_like(a))
+    calls = []
+    plan = types.SimpleNamespace(k_dose=lambda x, z, g, objective=True: calls.append("dose"),
+                                 k_beamlet_prices=lambda pi, w: calls.append("dt"),
+                                 k_time_cold=lambda kc, flush, reps=20: {"dose": 2.0, "dt": 4.0}[kc])
+    out = bench.spmv_bandwidth(fake_torch, plan, case, "fp32", None, 5000.0)
+    assert calls == ["dose", "dt"]
+    b_dose = 8 * 50_000 + 4 * 1001 + 4 * 100 + 4 * 1000 + 1000
+    assert out["dose"]["bytes"] == b_dose and out["dose"]["us"] == 2.0
+    assert out["dose"]["gbs"] == round(b_dose / 2e-6 / 1e9, 1)
+    assert out["dose"]["frac_of_hbm"] == round(b_dose / 2e-6 / 1e9 / 5000.0, 4)
+    assert out["dose"]["frac_of_nominal"] == round(b_dose / 2e-6 / 1e9 / bench.HBM_NOMINAL_GBS, 4)
+    b_dt = 8 * 50_000 + 4 * 101 + 4 * 1000 + 4 * 100
+    assert out["dt"]["bytes"] == b_dt and out["dt"]["us"] == 4.0
