@@ -126,3 +126,36 @@ def test_spmv_bandwidth_record_from_a_stand_in_plan():
     assert out["dose"]["frac_of_nominal"] == round(b_dose / 2e-6 / 1e9 / bench.HBM_NOMINAL_GBS, 4)
     b_dt = 8 * 50_000 + 4 * 101 + 4 * 1000 + 4 * 100
     assert out["dt"]["bytes"] == b_dt and out["dt"]["us"] == 4.0
+
+
+def test_pinned_inputs_keep_every_array_dao_create_reads():
+    """The e2e leg's page-locked copy of a case: every array dao_create reads,
+    equal to the original, with the dtype the binding passes through without a
+    further copy (so the pointers it hands over are the page-locked ones)."""
+    import types
+
+    import numpy as np
+
+    import bench
+    import phantom
+    from paper_1003_5402_gb300 import binding
+    case = phantom.make_case(phantom.spec_micro())
+
+    class _T:
+        def __init__(self, a):
+            self.a = a
+
+        def pin_memory(self):
+            return _T(self.a.copy())
+
+        def numpy(self):
+            return self.a
+
+    c = bench.pinned_inputs(types.SimpleNamespace(from_numpy=_T), case)
+    for name in ("indptr", "indices", "data", "rows", "cols", "voxel_struct", "is_target", "under_w", "under_t",
+                 "over_w", "over_t"):
+        assert np.array_equal(getattr(c, name), getattr(case, name)), name
+    assert len(c.pinned_tensors) == 11
+    D, g, s, w, rx, keep = binding._case_structs(c)
+    assert keep[0] is c.indptr and keep[1] is c.indices and keep[2] is c.data and keep[5] is c.voxel_struct
+    assert D.n_voxels == case.n_voxels and D.nnz == int(case.indptr[-1])
