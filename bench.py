@@ -233,6 +233,26 @@ def oracle_plan_seconds(case, k):
     return time.perf_counter() - t
 
 
+ONE_THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+                  "NUMEXPR_NUM_THREADS", "VECLIB_MAXIMUM_THREADS")
+
+
+def oracle_plan_seconds_one_thread(config: str, k: int, timeout_s: float = 600.0):
+    """The oracle's k-round plan on one host thread: a child interpreter with
+    every BLAS / OpenMP thread count set to 1 (numpy reads them at import, so
+    the parent's pools are untouched).  Seconds, or None if the child failed."""
+    code = ("import bench, json; case = bench._case(%r); "
+            "print(json.dumps(bench.oracle_plan_seconds(case, %d)))" % (config, int(k)))
+    env = dict(os.environ)
+    env.update({v: "1" for v in ONE_THREAD_ENV})
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=timeout_s)
+        return float(json.loads(r.stdout.strip().splitlines()[-1])) if r.returncode == 0 else None
+    except Exception:
+        return None
+
+
 def _cpu_threads():
     for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         if os.environ.get(var):
@@ -627,8 +647,10 @@ def run_ours(a):
     cpu = None
     if rank == 0 and ws == 1 and not a.skip_cpu:
         secs = oracle_plan_seconds(case, a.apertures)
+        secs1 = oracle_plan_seconds_one_thread(a.config, a.apertures)
         cpu = {"value": round(secs * 1e3, 1), "unit": "ms", "cores": _cpu_threads(), "kind": "oracle",
-               "sample": f"one full {a.apertures}-aperture plan of the same workload (FP64 numpy/scipy, BLAS threads)"}
+               "sample": f"one full {a.apertures}-aperture plan of the same workload (FP64 numpy/scipy, BLAS threads)",
+               "value_1_thread": None if secs1 is None else round(secs1 * 1e3, 1)}
 
     plan.close()
     if rank == 0:

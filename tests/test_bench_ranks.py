@@ -159,3 +159,12 @@ def test_pinned_inputs_keep_every_array_dao_create_reads():
     D, g, s, w, rx, keep = binding._case_structs(c)
     assert keep[0] is c.indptr and keep[1] is c.indices and keep[2] is c.data and keep[5] is c.voxel_struct
     assert D.n_voxels == case.n_voxels and D.nnz == int(case.indptr[-1])
+
+
+def test_one_thread_oracle_timing_runs_in_a_child():
+    """The 1-thread oracle figure: a child interpreter with every thread count
+    at 1 times a short plan of the small workload and reports seconds."""
+    import bench
+    secs = bench.oracle_plan_seconds_one_thread("tiny", 2, timeout_s=120)
+    assert secs is not None and 0.0 < secs < 120.0
+    assert bench.oracle_plan_seconds_one_thread("no-such-workload", 2, timeout_s=60) is None
