@@ -29,7 +29,7 @@ if ROOT not in sys.path:
 import phantom  # noqa: E402
 
 K_PLAN = 50
-WORKLOAD = "prostate-shaped FP32: 9 beams x 20x20 beamlets, 200x120x60 grid @2.5 mm, 50 apertures"
+WORKLOAD = "prostate-shaped FP32: 9 beams x 20x20 beamlets, 200x120x60 grid @2.5 mm, {} apertures"
 
 
 def _args():
@@ -63,9 +63,9 @@ def _case(name):
     return phantom.make_case(phantom.CONFIGS[name]())
 
 
-def _workload_config(case, name, extra=None):
-    cfg = {"workload": WORKLOAD if name == "prostate" else name, "voxels": case.n_voxels,
-           "beamlets": case.n_beamlets, "beams": case.n_beams, "nnz": case.nnz, "apertures": K_PLAN,
+def _workload_config(case, name, apertures=K_PLAN, extra=None):
+    cfg = {"workload": WORKLOAD.format(int(apertures)) if name == "prostate" else name, "voxels": case.n_voxels,
+           "beamlets": case.n_beamlets, "beams": case.n_beams, "nnz": case.nnz, "apertures": int(apertures),
            "seed": case.spec.seed, "l2": "flushed before each step (256 MiB write)", "parallelism": "replicas"}
     if extra:
         cfg.update(extra)
@@ -281,7 +281,7 @@ def run_reference(a):
     out = {"impl": "reference", "metric": f"ms per {a.apertures}-aperture plan", "value": ms, "unit": "ms",
            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": _workload_config(case, a.config),
+           "config": _workload_config(case, a.config, a.apertures),
            "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -660,7 +660,7 @@ def run_ours(a):
             "metric": f"ms per {a.apertures}-aperture plan", "value": round(whole_job_ms_per_plan(total_ms, a.steps, ws), 4),
             "unit": "ms", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_per_step, 4),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": _workload_config(case, a.config),
+            "data": "synthetic", "config": _workload_config(case, a.config, a.apertures),
             "roofline": roof, "roofline_eval_kernel": roof_eval, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
             "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
                            "p99": round(float(np.percentile(lat, 99)), 4)},

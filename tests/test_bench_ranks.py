@@ -94,7 +94,7 @@ def test_reference_arm_prints_one_contract_line(monkeypatch, capsys):
     assert d["impl"] == "reference" and d["metric"] == "ms per 4-aperture plan" and d["unit"] == "ms"
     assert d["higher_is_better"] is False and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 3
     assert d["value"] > 0 and d["ms_per_step"] == d["value"]
-    assert isinstance(d["config"]["workload"], str)
+    assert d["config"]["workload"] == "tiny" and d["config"]["apertures"] == 4
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
