@@ -1,11 +1,14 @@
 """Benchmark: milliseconds per 50-aperture column-generation DAO plan on one GB300.
 
-Workload: the prostate-shaped phantom (9 beams x 20x20 beamlets, 200x120x60 grid
-of 2.5 mm voxels, unspecified tissue down-sampled 2x2x2), seeded and synthetic.
-A step is one whole plan from an empty pool: 50 rounds of D^T SpMV pricing,
-aperture column and projected-Newton master solve.  Inputs are resident in HBM
-when the timed region starts; L2 is flushed (a 256 MiB write) before every step
-and the flush is outside the per-step events.
+Workload (default): the H&N-shaped phantom (5 beams x 30x30 beamlets, 192x160x80
+grid of 2.5 mm voxels, two nested PTVs, unspecified tissue down-sampled 2x2x2),
+seeded and synthetic, with D and D^T stored as FP16 values and a per-beamlet
+FP32 scale (FP32 accumulation, FP64 objective and reduced costs).  The same plan
+with FP32 storage is timed beside it.  A step is one whole plan from an empty
+pool: 50 rounds of D^T SpMV pricing, aperture column and projected-Newton master
+solve.  Inputs are resident in HBM when the timed region starts; L2 is flushed
+(a 256 MiB write) before every step and the flush is outside the per-step
+events.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on
 the host cores instead, on bounded samples of the same workload.
@@ -29,7 +32,12 @@ if ROOT not in sys.path:
 import phantom  # noqa: E402
 
 K_PLAN = 50
-WORKLOAD = "prostate-shaped FP32: 9 beams x 20x20 beamlets, 200x120x60 grid @2.5 mm, {} apertures"
+WORKLOADS = {
+    "hn": "H&N-shaped {prec}: 5 beams x 30x30 beamlets, 192x160x80 grid @2.5 mm, two PTVs, {k} apertures",
+    "prostate": "prostate-shaped {prec}: 9 beams x 20x20 beamlets, 200x120x60 grid @2.5 mm, {k} apertures",
+    "tiny": "small box {prec}: 5 beams x 10x10 beamlets, 40x40x12 grid @2.5 mm, {k} apertures",
+}
+PREC_NAMES = {"fp32": "FP32", "fp16": "FP16 values + per-beamlet FP32 scale", "bf16": "BF16 values + per-beamlet FP32 scale"}
 
 
 def _args():
@@ -38,7 +46,9 @@ def _args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--config", choices=["prostate", "tiny", "hn"], default="prostate")
+    p.add_argument("--config", choices=["prostate", "tiny", "hn"], default="hn")
+    p.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default=None,
+                   help="storage of D and D^T (default: fp16 for hn, fp32 otherwise)")
     p.add_argument("--apertures", type=int, default=K_PLAN)
     p.add_argument("--skip-cpu", action="store_true")
     p.add_argument("--skip-e2e", action="store_true")
@@ -49,7 +59,10 @@ def _args():
     p.add_argument("--serve-requests", type=int, default=60,
                    help="requests of the serving leg (600 for the full Poisson workload)")
     p.add_argument("--batch", type=int, default=16, help="instances per workload in the batched re-plan leg")
-    return p.parse_args()
+    a = p.parse_args()
+    if a.precision is None:
+        a.precision = "fp16" if a.config == "hn" else "fp32"
+    return a
 
 
 def _dist():
@@ -63,10 +76,11 @@ def _case(name):
     return phantom.make_case(phantom.CONFIGS[name]())
 
 
-def _workload_config(case, name, apertures=K_PLAN, extra=None):
-    cfg = {"workload": WORKLOAD.format(int(apertures)) if name == "prostate" else name, "voxels": case.n_voxels,
+def _workload_config(case, name, apertures=K_PLAN, extra=None, prec="fp32"):
+    cfg = {"workload": WORKLOADS[name].format(prec=PREC_NAMES[prec], k=int(apertures)), "voxels": case.n_voxels,
            "beamlets": case.n_beamlets, "beams": case.n_beams, "nnz": case.nnz, "apertures": int(apertures),
-           "seed": case.spec.seed, "l2": "flushed before each step (256 MiB write)", "parallelism": "replicas"}
+           "storage": prec, "seed": case.spec.seed, "l2": "flushed before each step (256 MiB write)",
+           "parallelism": "replicas"}
     if extra:
         cfg.update(extra)
     return cfg
@@ -226,11 +240,18 @@ def _peaks():
 # CPU oracle timing
 # ---------------------------------------------------------------------------
 
-def oracle_plan_seconds(case, k):
+def oracle_plan_seconds(case, k, split=None):
+    """Seconds of the oracle's k-round plan; with ``split`` also the seconds of
+    its first ``split`` rounds (from the per-round callback)."""
     import oracle
+    marks = {}
     t = time.perf_counter()
-    oracle.column_generation(case, k)
-    return time.perf_counter() - t
+    cb = None if split is None else (lambda r, pr, m: marks.setdefault(r, time.perf_counter()))
+    oracle.column_generation(case, k, callback=cb)
+    total = time.perf_counter() - t
+    if split is None:
+        return total
+    return total, (marks[split - 1] - t) if split - 1 in marks else None
 
 
 ONE_THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
@@ -251,6 +272,10 @@ def oracle_plan_seconds_one_thread(config: str, k: int, timeout_s: float = 600.0
         return float(json.loads(r.stdout.strip().splitlines()[-1])) if r.returncode == 0 else None
     except Exception:
         return None
+
+
+ORACLE_PARALLEL = ("numpy BLAS threads on the dense master products (S^T diag(h) S, S y); the scipy sparse "
+                   "products D x and D^T pi run on one thread; FP64 on the original D whatever the GPU storage")
 
 
 def _cpu_threads():
@@ -281,8 +306,9 @@ def run_reference(a):
     out = {"impl": "reference", "metric": f"ms per {a.apertures}-aperture plan", "value": ms, "unit": "ms",
            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": _workload_config(case, a.config, a.apertures),
-           "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
+           "config": _workload_config(case, a.config, a.apertures, prec=a.precision),
+           "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample,
+                            "parallel": ORACLE_PARALLEL},
            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -497,7 +523,9 @@ def run_ours(a):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    plan = Plan(case, device=dev, stream=stream.cuda_stream)
+    from paper_1003_5402_gb300 import binding
+    PREC = {"fp32": binding.DAO_PREC_FP32, "fp16": binding.DAO_PREC_FP16, "bf16": binding.DAO_PREC_BF16}
+    plan = Plan(case, device=dev, stream=stream.cuda_stream, precision=PREC[a.precision])
     sampler = ClockSampler(dev, enabled=not a.no_clocks)
     sampler.wait_first_sample()
     for _ in range(a.warmup):
@@ -583,32 +611,32 @@ def run_ours(a):
         roof = roof_eval
 
     # SpMV bandwidth, L2 cold: a1 and a2 alone, 20 runs each, FP32 storage and
-    # 16-bit storage (FP16 values + per-beamlet scale, same workload)
+    # 16-bit storage (FP16 values + per-beamlet scale, same workload); and the
+    # same plan in the other storage (FP32 beside an FP16 headline, else FP16)
     spmv = mixed = None
     if not a.skip_spmv:
-        spmv = {"fp32": spmv_bandwidth(torch, plan, case, "fp32", flush, hbm_peak)}
-        from paper_1003_5402_gb300 import binding
-        with Plan(case, device=dev, stream=stream.cuda_stream, precision=binding.DAO_PREC_FP16) as p16:
-            spmv["fp16"] = spmv_bandwidth(torch, p16, case, "fp16", flush, hbm_peak)
+        other = "fp32" if a.precision != "fp32" else "fp16"
+        spmv = {a.precision: spmv_bandwidth(torch, plan, case, a.precision, flush, hbm_peak)}
+        with Plan(case, device=dev, stream=stream.cuda_stream, precision=PREC[other]) as p2:
+            spmv[other] = spmv_bandwidth(torch, p2, case, other, flush, hbm_peak)
             for _ in range(2):
-                p16.reset()
-                p16.solve(a.apertures)
-            t16 = []
+                p2.reset()
+                p2.solve(a.apertures)
+            t2 = []
             for _ in range(3):
                 flush.zero_()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                p16.reset()
-                _, n16, tr16 = p16.solve(a.apertures)
+                p2.reset()
+                _, n2, tr2 = p2.solve(a.apertures)
                 e1.record(stream)
                 torch.cuda.synchronize()
-                t16.append(e0.elapsed_time(e1))
-        mixed = {"storage": "FP16 values of D and D^T, per-beamlet FP32 scale, FP32 accumulation",
-                 "ms_per_plan": round(statistics.median(t16), 4),
-                 "objective_final": float(tr16[n16 - 1]) if n16 else None,
-                 "objective_rel_diff_vs_fp32": (abs(float(tr16[n16 - 1]) - F_final) / F_final
-                                                if n16 and F_final else None)}
+                t2.append(e0.elapsed_time(e1))
+        mixed = {"headline_storage": PREC_NAMES[a.precision], "other_storage": PREC_NAMES[other],
+                 "other_ms_per_plan": round(statistics.median(t2), 4),
+                 "other_objective_final": float(tr2[n2 - 1]) if n2 else None,
+                 "objective_rel_diff": (abs(float(tr2[n2 - 1]) - F_final) / F_final if n2 and F_final else None)}
 
     # end to end through the public API from host buffers
     e2e = None
@@ -626,7 +654,7 @@ def run_ours(a):
             flush.zero_()
             barrier()
             t0 = time.perf_counter()
-            with Plan(e2e_case, device=dev, stream=stream.cuda_stream) as p2:
+            with Plan(e2e_case, device=dev, stream=stream.cuda_stream, precision=PREC[a.precision]) as p2:
                 p2.solve(a.apertures)
                 dose, F = p2.dose()
             torch.cuda.synchronize()
@@ -646,11 +674,21 @@ def run_ours(a):
 
     cpu = None
     if rank == 0 and ws == 1 and not a.skip_cpu:
-        secs = oracle_plan_seconds(case, a.apertures)
-        secs1 = oracle_plan_seconds_one_thread(a.config, a.apertures)
-        cpu = {"value": round(secs * 1e3, 1), "unit": "ms", "cores": _cpu_threads(), "kind": "oracle",
-               "sample": f"one full {a.apertures}-aperture plan of the same workload (FP64 numpy/scipy, BLAS threads)",
-               "value_1_thread": None if secs1 is None else round(secs1 * 1e3, 1)}
+        # the full plan when the oracle's first rounds predict at most about a
+        # minute, else its first k rounds scaled by K / k (an under-estimate:
+        # later rounds have larger master problems); one host thread on its first
+        # 10 rounds, beside the same 10 rounds with the BLAS threads
+        probe = oracle_plan_seconds(case, 3)
+        k_s = a.apertures if probe / 3 * a.apertures * 1.5 <= 60 else max(5, int(60 / (probe / 3 * 1.5)))
+        secs, secs10 = oracle_plan_seconds(case, k_s, split=10)
+        secs1 = oracle_plan_seconds_one_thread(a.config, 10)
+        cpu = {"value": round(secs * 1e3 * a.apertures / k_s, 1), "unit": "ms", "cores": _cpu_threads(),
+               "kind": "oracle", "parallel": ORACLE_PARALLEL,
+               "sample": (f"one full {a.apertures}-aperture plan of the same workload" if k_s == a.apertures else
+                          f"the first {k_s} of {a.apertures} rounds of the same workload, scaled x{a.apertures / k_s:.2f}")
+               + " (FP64 numpy/scipy on the original D)",
+               "first_10_rounds_ms": None if secs10 is None else round(secs10 * 1e3, 1),
+               "first_10_rounds_ms_1_thread": None if secs1 is None else round(secs1 * 1e3, 1)}
 
     plan.close()
     if rank == 0:
@@ -660,7 +698,7 @@ def run_ours(a):
             "metric": f"ms per {a.apertures}-aperture plan", "value": round(whole_job_ms_per_plan(total_ms, a.steps, ws), 4),
             "unit": "ms", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_per_step, 4),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": _workload_config(case, a.config, a.apertures),
+            "data": "synthetic", "config": _workload_config(case, a.config, a.apertures, prec=a.precision),
             "roofline": roof, "roofline_eval_kernel": roof_eval, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
             "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
                            "p99": round(float(np.percentile(lat, 99)), 4)},

@@ -406,27 +406,41 @@ void dao_server_destroy(dao_server* srv);
  * re-planning service that reserves every device buffer before an online
  * adaptive fraction (so that the fraction cannot fail on an allocation or stall
  * on the synchronisation cudaMalloc / cudaFree may imply), or an application
- * whose own allocator owns the device.  It computes what dao_k_dose computes,
- * z = D x, grad F(z) and F(z) of Eqs. 1, 5, 9, 10, without a context and
- * without allocating: it calls no cudaMalloc, cudaFree or allocating library
- * routine.
+ * whose own allocator owns the device.  Without a context and without
+ * allocating (no cudaMalloc, cudaFree or allocating library routine) it
+ * computes the dose z = D x of a fluence x, the derivative of the objective
+ * with respect to each voxel's dose, and the objective itself, for one-sided
+ * quadratic voxel penalties: a voxel of structure s contributes
+ * a_s max(0, t_s - z)^2 + b_s max(0, z - u_s)^2, with the weights and
+ * thresholds given per structure in `terms`.  It is what dao_k_dose computes
+ * for a context, in a standalone form.
  *   D: voxel-major CSR on the device, int32 row_ptr[n_voxels + 1], col[nnz],
- *      float val[nnz] (rows need no padding); x: device float[n_beamlets];
- *   voxel_struct: device int32[n_voxels], labels in [0, n_structures);
- *   terms: host double[n_structures][4] = alpha_s / |v_s|, T_s^-,
- *      beta_s / |v_s|, T_s^+ (the per-structure form of Eqs. 9-10);
- *   z: device float[n_voxels]; grad: device float[n_voxels] or NULL;
- *   objective: device double, F(z); stream: cudaStream_t or NULL.
+ *      float val[nnz] (rows need no padding), columns in [0, n_beamlets);
+ *      x: device float[n_beamlets];
+ *   voxel_struct: device int32[n_voxels], labels in [0, n_structures); a voxel
+ *      with a label outside that range gets a NaN derivative and makes the
+ *      objective NaN (its dose is still written);
+ *   terms: host double[n_structures][4] = a_s, t_s, b_s, u_s;
+ *   z: device float[n_voxels]; grad: device float[n_voxels] or NULL (then only
+ *      z and the objective are computed);
+ *   objective: device double; stream: cudaStream_t or NULL (legacy stream).
+ * Every device buffer and the stream must belong to the CUDA device that is
+ * current on the calling thread: the kernels run there.  A stream of another
+ * device is refused (DAO_EINVAL); buffers cannot be checked, and buffers of
+ * another device, or shorter than stated, or column indices outside
+ * [0, n_beamlets), are read or written out of bounds.
  * Limits: n_voxels <= 4,194,304 and n_structures <= 64, else DAO_EINVAL with a
- * message.  Scratch: the per-block partial sums of F live in a 32 KiB
- * file-scope device array that every GPU loading the library keeps until the
- * process exits; every block overwrites its own entry on each call, so nothing
- * needs clearing, and the array keeps the last call's contents.  All calls on
- * a device share that array: calls whose kernels overlap on the GPU (for
- * example on different streams) race and give wrong objectives.  The first
- * call on a device looks up the array's device address with that device
- * current; make that first call before any stream capture.  Asynchronous:
- * results are ready when the stream reaches them. */
+ * message.  Scratch: the per-block partial sums of the objective live in a
+ * 32 KiB file-scope device array that every GPU loading the library keeps until
+ * the process exits; every block overwrites its own entry on each call, so
+ * nothing needs clearing, and the array keeps the last call's contents.  All
+ * calls on a device share that array: calls whose kernels overlap on the GPU
+ * (for example on different streams) race and give wrong objectives.  The
+ * first call on a device looks up the array's device address with that device
+ * current and keeps it for the life of the process; make that first call
+ * before any stream capture, and do not call this entry point again after a
+ * cudaDeviceReset of that device.  Asynchronous: results are ready when the
+ * stream reaches them. */
 dao_status dao_dose_objective_noalloc(int32_t n_voxels, int32_t n_beamlets, const int32_t* row_ptr,
                                       const int32_t* col, const float* val, const float* x,
                                       const int32_t* voxel_struct, int32_t n_structures, const double* terms,

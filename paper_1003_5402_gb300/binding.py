@@ -429,16 +429,38 @@ class Plan:
 def dose_objective_noalloc(row_ptr, col, val, x, voxel_struct, terms, z, grad=None, objective=None, stream=None):
     """dao_dose_objective_noalloc on torch CUDA tensors (int32 row_ptr / col /
     voxel_struct, float32 val / x / z / grad, float64 objective of one element)
-    and a host float64 terms array [n_structures, 4]; returns the status."""
+    and a host float64 terms array [n_structures, 4]; returns the status.
+
+    Every tensor must be on one CUDA device; the call runs with that device
+    current (the library launches on the current device).  ``stream`` is a
+    torch.cuda.Stream of that device, a raw cudaStream_t handle (int) or None
+    (the device's current torch stream).  The lengths are checked, col and val
+    against row_ptr[-1]; the contents of D (column indices below x's length)
+    and the labels are not: the library flags a label outside
+    [0, n_structures) with a NaN objective, and an out-of-range column index
+    is read out of bounds."""
+    import torch
     t = np.ascontiguousarray(terms, dtype=np.float64).reshape(-1, 4)
     V, N, d = int(z.numel()), int(x.numel()), z.device.index
     if col.numel() != val.numel():
         raise ValueError(f"col and val differ in length ({col.numel()} and {val.numel()})")
-    st = load().dao_dose_objective_noalloc(
-        V, N, _dev(row_ptr, "int32", V + 1, d), _dev(col, "int32", 0, d), _dev(val, "float32", 0, d),
-        _dev(x, "float32", N, d), _dev(voxel_struct, "int32", V, d), int(t.shape[0]), _ptr(t, C.c_double),
-        _dev(z, "float32", V, d), _dev(grad, "float32", V, d) if grad is not None else None,
-        _dev(objective, "float64", 1, d), C.c_void_p(stream) if stream is not None else None)
+    nnz = int(row_ptr[-1].item()) if row_ptr.numel() > V else -1
+    if nnz < 0 or col.numel() < nnz:
+        raise ValueError(f"col and val hold {col.numel()} entries, row_ptr needs {nnz}")
+    with torch.cuda.device(d):
+        if stream is None:
+            handle = torch.cuda.current_stream(d).cuda_stream
+        elif isinstance(stream, torch.cuda.Stream):
+            if stream.device.index != d:
+                raise ValueError(f"the stream is on {stream.device}, the tensors on cuda:{d}")
+            handle = stream.cuda_stream
+        else:
+            handle = int(stream)
+        st = load().dao_dose_objective_noalloc(
+            V, N, _dev(row_ptr, "int32", V + 1, d), _dev(col, "int32", nnz, d), _dev(val, "float32", nnz, d),
+            _dev(x, "float32", N, d), _dev(voxel_struct, "int32", V, d), int(t.shape[0]), _ptr(t, C.c_double),
+            _dev(z, "float32", V, d), _dev(grad, "float32", V, d) if grad is not None else None,
+            _dev(objective, "float64", 1, d), C.c_void_p(handle) if handle else None)
     return _check(st, "dao_dose_objective_noalloc")
 
 

@@ -43,9 +43,9 @@ __global__ void __launch_bounds__(NA_THREADS) k_dose_noalloc(int V, const int* _
                                                             const int* __restrict__ col,
                                                             const float* __restrict__ val,
                                                             const float* __restrict__ x,
-                                                            const int* __restrict__ vstruct, const NoallocTerms terms,
-                                                            float* __restrict__ z, float* __restrict__ grad,
-                                                            double* __restrict__ partial) {
+                                                            const int* __restrict__ vstruct, int S,
+                                                            const NoallocTerms terms, float* __restrict__ z,
+                                                            float* __restrict__ grad, double* __restrict__ partial) {
     __shared__ double s_red[NA_THREADS / 32];
     const int lane = threadIdx.x & 31;
     const int sub = lane % NA_LANES;
@@ -65,7 +65,13 @@ __global__ void __launch_bounds__(NA_THREADS) k_dose_noalloc(int V, const int* _
         for (int o = NA_LANES / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (row < r1 && sub == 0) {
             z[row] = acc;
-            const double* tt = terms.t[vstruct[row]];
+            const int lab = vstruct[row];
+            if ((unsigned)lab >= (unsigned)S) {  // no such structure: flagged, never read
+                if (grad != nullptr) grad[row] = __int_as_float(0x7fc00000);
+                facc += __longlong_as_double(0x7ff8000000000000ll);  // the objective becomes NaN
+                continue;
+            }
+            const double* tt = terms.t[lab];
             const double zd = acc;
             const double u = fmax(0.0, tt[1] - zd);
             const double o = fmax(0.0, zd - tt[3]);
@@ -125,10 +131,22 @@ dao_status dao_dose_objective_noalloc(int32_t n_voxels, int32_t n_beamlets, cons
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return na_fail(DAO_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= NA_MAX_DEVICES) return na_fail(DAO_EINVAL, "device ordinal out of range");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (st != nullptr) {  // the kernels run on the current device: the stream must belong to it
+        int sdev = -1;
+        e = cudaStreamGetDevice(st, &sdev);
+        if (e != cudaSuccess) return na_fail(DAO_EINVAL, std::string("cudaStreamGetDevice: ") + cudaGetErrorString(e));
+        if (sdev != dev)
+            return na_fail(DAO_EINVAL, "the stream belongs to device " + std::to_string(sdev) +
+                                           ", not to the current device " + std::to_string(dev));
+    }
     double* scratch = nullptr;
     {
         // set-up, once per device with that device current: the device address of
-        // the file-scope array (its name is only a host-side stand-in)
+        // the file-scope array (its name is only a host-side stand-in).  The
+        // address belongs to the device's primary context as it was at that first
+        // call; after a cudaDeviceReset it is stale, and a caller that resets the
+        // device must not call this entry point again in the same process.
         std::lock_guard<std::mutex> lock(g_mu);
         if (g_scratch_ptr[dev] == nullptr) {
             void* p = nullptr;
@@ -142,9 +160,8 @@ dao_status dao_dose_objective_noalloc(int32_t n_voxels, int32_t n_beamlets, cons
     NoallocTerms t;
     for (int s = 0; s < SMAX_TERMS; ++s)
         for (int q = 0; q < 4; ++q) t.t[s][q] = s < n_structures ? terms[4 * s + q] : 0.0;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    k_dose_noalloc<<<(unsigned)blocks, NA_THREADS, 0, st>>>(n_voxels, row_ptr, col, val, x, voxel_struct, t, z, grad,
-                                                          scratch);
+    k_dose_noalloc<<<(unsigned)blocks, NA_THREADS, 0, st>>>(n_voxels, row_ptr, col, val, x, voxel_struct,
+                                                          n_structures, t, z, grad, scratch);
     e = cudaGetLastError();
     if (e != cudaSuccess) return na_fail(DAO_ECUDA, std::string("k_dose_noalloc: ") + cudaGetErrorString(e));
     k_sum_noalloc<<<1, NA_THREADS, 0, st>>>(scratch, (int)blocks, objective);

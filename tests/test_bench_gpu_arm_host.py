@@ -131,11 +131,12 @@ def test_gpu_arm_runs_on_stand_ins_and_prints_the_contract_line(monkeypatch, cap
         assert key in d, key
     assert d["metric"] == "ms per 4-aperture plan" and d["steps"] == 2 and d["warmup"] == 3
     assert d["value"] == 8.5 and d["gpu_launches"] == 2 * 3 * 4
-    assert d["config"]["apertures"] == 4 and d["config"]["workload"] == "tiny"
+    assert d["config"]["apertures"] == 4 and d["config"]["workload"].startswith("small box FP32")
+    assert d["config"]["storage"] == "fp32"
     r = d["roofline"]
     assert r["kernel"] == "k_master_persist" and r["unit"] == "GB/s" and 0 < r["frac"] < 10
     assert set(d["spmv"]) == {"fp32", "fp16"} and d["spmv"]["fp32"]["dose"]["us"] == 22.5
-    assert d["mixed_precision"]["ms_per_plan"] == 8.5
+    assert d["mixed_precision"]["other_ms_per_plan"] == 8.5
     e = d["e2e"]
     assert e["inputs"] == "page-locked host arrays" and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     assert d["clocks"] is None and d["cpu_baseline"] is None

@@ -84,7 +84,7 @@ def test_reference_arm_prints_one_contract_line(monkeypatch, capsys):
     import bench
     for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
         monkeypatch.delenv(k, raising=False)
-    bench.run_reference(argparse.Namespace(config="tiny", apertures=4, steps=1, warmup=3, gpus=1))
+    bench.run_reference(argparse.Namespace(config="tiny", apertures=4, steps=1, warmup=3, gpus=1, precision="fp32"))
     lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
     assert len(lines) == 1
     d = json.loads(lines[0])
@@ -94,7 +94,7 @@ def test_reference_arm_prints_one_contract_line(monkeypatch, capsys):
     assert d["impl"] == "reference" and d["metric"] == "ms per 4-aperture plan" and d["unit"] == "ms"
     assert d["higher_is_better"] is False and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 3
     assert d["value"] > 0 and d["ms_per_step"] == d["value"]
-    assert d["config"]["workload"] == "tiny" and d["config"]["apertures"] == 4
+    assert d["config"]["workload"].startswith("small box FP32") and d["config"]["apertures"] == 4
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

@@ -43,15 +43,22 @@ def _tie_window(case, D, pi_gpu, pi_ref, apertures):
     return tot
 
 
-def _teacher_forced(case, K, torch, plan_kw=None, ref_case=None):
+def _teacher_forced(case, K, torch, plan_kw=None, ref_case=None, ref_free=None):
     """Teacher-forced column generation: the GPU prices from its own state, and
-    the oracle's aperture is added on both sides.  ``ref_case`` (default: case)
-    is the matrix the oracle sees: the dequantised D for 16-bit storage."""
+    the oracle's aperture is added on both sides.  At every round the GPU's
+    choice must equal the oracle's or be an accepted tie, and its master
+    optimum's dose must lie within DOSE_TOL of the oracle's.  ``ref_case``
+    (default: case) is the matrix the oracle sees: the dequantised D for 16-bit
+    storage.  ``ref_free``: the oracle's (result, steps) of this case, if
+    already computed."""
     gpu_case, case = case, (case if ref_case is None else ref_case)
     D = O.csr64(case)
-    steps = []
-    ref = O.column_generation(case, K, callback=lambda k, pr, m: steps.append((pr, m)))
-    out = {"F_gpu": [], "F_ref": list(ref.objective), "ties": 0, "exact": 0}
+    if ref_free is not None:
+        ref, steps = ref_free
+    else:
+        steps = []
+        ref = O.column_generation(case, K, callback=lambda k, pr, m: steps.append((pr, m)))
+    out = {"F_gpu": [], "F_ref": list(ref.objective), "ties": 0, "exact": 0, "worst_dose": 0.0}
     with _plan(gpu_case, torch, **(plan_kw or {})) as plan:
         zbuf = torch.empty(case.n_voxels, dtype=torch.float32, device="cuda")
         pbuf = torch.empty_like(zbuf)
@@ -71,6 +78,10 @@ def _teacher_forced(case, K, torch, plan_kw=None, ref_case=None):
                 assert abs(v_gpu_choice - pr_ref.reduced_cost) <= win, (k, v_gpu_choice, pr_ref.reduced_cost, win)
                 out["ties"] += 1
             out["F_gpu"].append(plan.add_aperture(b_ref, lv_ref))
+            plan.k_state(zbuf, pbuf)
+            dz = float(np.max(np.abs(zbuf.cpu().numpy() - steps[k][1].z)))
+            out["worst_dose"] = max(out["worst_dose"], dz)
+            assert dz <= DOSE_TOL, (k, dz)
         out["y_gpu"] = plan.intensities()
         out["z_gpu"], out["F_dose"] = plan.dose()
         plan.k_state(zbuf, pbuf)
@@ -109,26 +120,87 @@ def test_teacher_forced_parity(torch, name, K, persistent):
     assert abs(r["F_dose"] - Fr[-1]) <= RTOL_F * Fr[-1]
 
 
+def _free_running_checked(case, K, torch, plan_kw=None, ref_case=None, ref_free=None):
+    """Free-running column generation on the device (the graph path the
+    benchmark times), checked against the oracle at every round.
+
+    The GPU plans alone: dao_solve(1) per round, with its state (z, pi) read
+    after each round, and a second plan runs dao_solve(K) in one call, which must
+    give bitwise the same apertures and trace.  The oracle then follows the
+    GPU's apertures (teacher forcing of the oracle): at every round it prices
+    from its own FP64 master optimum of the same pool, and
+      - the GPU's aperture equals the oracle's, or the oracle's FP64 reduced
+        cost of the GPU's aperture lies within the tie window of the oracle's
+        best (the window of the two duals' difference, ``_tie_window``);
+      - the objective agrees within RTOL_F;
+      - the dose agrees within DOSE_TOL per voxel.
+    ``ref_case`` is the matrix the oracle sees (the dequantised D for 16-bit
+    storage).  ``ref_free`` (optional) is the oracle's own free run of K rounds:
+    when the GPU's sequence equals it, the oracle is not run again.
+    Returns a summary dict."""
+    gpu_case, case = case, (case if ref_case is None else ref_case)
+    D = O.csr64(case)
+    vt = O.voxel_terms(case)
+    V = case.n_voxels
+    pis, zs, Fs = [], [], []
+    with _plan(gpu_case, torch, **(plan_kw or {})) as plan:
+        zbuf = torch.empty(V, dtype=torch.float32, device="cuda")
+        pbuf = torch.empty_like(zbuf)
+        plan.k_state(zbuf, pbuf)
+        pis.append(pbuf.cpu().numpy())
+        for k in range(K):
+            st, n, tr = plan.solve(1)
+            assert n == k + 1, (k, st, n)
+            Fs.append(float(tr[0]))
+            plan.k_state(zbuf, pbuf)
+            zs.append(zbuf.cpu().numpy())
+            pis.append(pbuf.cpu().numpy())
+        aps = plan.apertures()
+    with _plan(gpu_case, torch, **(plan_kw or {})) as plan:
+        st, n, trace = plan.solve(K)
+        aps_once = plan.apertures()
+        y_gpu = plan.intensities()
+        z_final, F_final = plan.dose()
+    assert n == K
+    assert np.array_equal(np.asarray(trace), np.asarray(Fs)), "dao_solve(K) differs from K calls of dao_solve(1)"
+    assert all(a[0] == b[0] and np.array_equal(a[1], b[1]) for a, b in zip(aps, aps_once))
+    same_as_free = ref_free is not None and len(ref_free[0].apertures) >= K and all(
+        a[0] == b[0] and np.array_equal(a[1], b[1]) for a, b in zip(aps, ref_free[0].apertures[:K]))
+    if same_as_free:
+        ref, steps = ref_free
+    else:
+        steps = []
+        ref = O.column_generation(case, K, teacher=aps, callback=lambda k, pr, m: steps.append((pr, m)))
+    ties = 0
+    worst_F = worst_z = 0.0
+    for k in range(K):
+        pr, m = steps[k]
+        b, lv = aps[k]
+        if not (b == pr.beam and np.array_equal(lv, pr.leaves)):
+            pi_ref = O.gradient(np.zeros(V) if k == 0 else steps[k - 1][1].z, vt)
+            w_ref = O.beamlet_prices(D, pi_ref)
+            v_gpu = O.aperture_value(case, w_ref, b, lv)
+            win = max(1e-9 * abs(pr.reduced_cost),
+                      _tie_window(case, D, pis[k], pi_ref, [(b, lv), (pr.beam, pr.leaves)]))
+            assert abs(v_gpu - pr.reduced_cost) <= win, (k, v_gpu, pr.reduced_cost, win)
+            ties += 1
+        rel = abs(Fs[k] - m.F) / abs(m.F)
+        dz = float(np.max(np.abs(zs[k] - m.z)))
+        worst_F, worst_z = max(worst_F, rel), max(worst_z, dz)
+        assert rel <= RTOL_F, (k, Fs[k], m.F, rel)
+        assert dz <= DOSE_TOL, (k, dz)
+    assert abs(F_final - ref.objective[K - 1]) <= RTOL_F * ref.objective[K - 1]
+    return {"ties": ties, "worst_F_rel": worst_F, "worst_dose": worst_z, "apertures": aps, "y": y_gpu,
+            "z": z_final, "F": F_final, "ref": ref}
+
+
 @pytest.mark.parametrize("name,K", [("micro", 12), ("tiny", 20)])
 def test_free_running_matches_oracle(torch, name, K):
+    """Every round of the free-running graph path against the oracle (leaves
+    exact or an accepted tie, objective, dose)."""
     case = P.make_case(P.CONFIGS[name]())
-    ref = O.column_generation(case, K)
-    with _plan(case, torch) as plan:
-        st, n, trace = plan.solve(K)
-        aps = plan.apertures()
-    assert n == K
-    same = 0
-    for k in range(K):
-        if aps[k][0] == ref.apertures[k][0] and np.array_equal(aps[k][1], ref.apertures[k][1]):
-            same += 1
-        else:
-            break
-    # the sequences agree until a near-tie; the objectives agree where they agree
-    assert same >= min(K, 8), same
-    rel = np.abs(trace[:same] - np.array(ref.objective[:same])) / np.array(ref.objective[:same])
-    assert np.all(rel <= RTOL_F), rel
-    # after any divergence the plan quality stays within the tolerance band of the oracle's
-    assert trace[-1] <= ref.objective[-1] * (1 + 1e-3)
+    r = _free_running_checked(case, K, torch)
+    assert r["ties"] <= 2, r["ties"]
 
 
 @pytest.mark.parametrize("persistent", [1, 0])
@@ -187,42 +259,6 @@ def test_add_aperture_validation_and_pool_limit(torch):
         with pytest.raises(DaoError) as e:
             plan.add_aperture(2, full)
         assert e.value.status == -6
-
-
-@pytest.mark.parametrize("workload", ["prostate", "hn"])
-def test_full_size_properties(torch, workload):
-    """The benchmark workload (prostate-shaped, 50 apertures) in the launch
-    configuration the benchmark times, and the H&N-shaped workload (280,699
-    voxels, 4,500 beamlets, two targets) in FP32: objective non-increasing,
-    dose at sampled voxels equal to the oracle's sum over the plan's
-    beamlets, master KKT with the oracle's FP64 aperture columns, first
-    apertures and objectives equal to the oracle's."""
-    case = P.make_case(P.spec_prostate() if workload == "prostate" else P.spec_hn())
-    K = 50
-    with _plan(case, torch) as plan:
-        st, n, trace = plan.solve(K)
-        aps = plan.apertures()
-        y = plan.intensities()
-        z, F = plan.dose()
-    assert n == K
-    assert np.all(np.diff(trace) <= 1e-6 * trace[:-1])
-    D = O.csr64(case)
-    x = O.fluence(case, aps, y)
-    rng = np.random.default_rng(0)
-    js = rng.choice(case.n_voxels, 2000, replace=False)
-    zs = D[js] @ x
-    assert np.max(np.abs(z[js] - zs)) <= DOSE_TOL
-    vt = O.voxel_terms(case)
-    S = np.column_stack([O.aperture_column(D, case, b, lv) for b, lv in aps])
-    g = S.T @ O.gradient(S @ y, vt)
-    scale = np.max(np.abs(S.T @ O.gradient(np.zeros(case.n_voxels), vt)))
-    pos = y > 1e-6 * np.max(y)
-    assert np.all(np.abs(g[pos]) <= 1e-4 * scale)
-    assert np.all(g[~pos] >= -1e-4 * scale)
-    ref = O.column_generation(case, 5)
-    for k in range(5):
-        assert aps[k][0] == ref.apertures[k][0] and np.array_equal(aps[k][1], ref.apertures[k][1]), k
-    assert np.all(np.abs(trace[:5] - ref.objective) <= RTOL_F * np.array(ref.objective))
 
 
 @pytest.mark.parametrize("persistent", [1, 0])
