@@ -130,6 +130,30 @@ dao_status dao_create(const dao_csr* D, const dao_geometry* g, const dao_structu
                       const dao_weights* w, const double* prescriptions,
                       const dao_options* opt, dao_ctx** out);
 
+/* Re-optimisation mode (Sec. 4): the criteria of Eqs. 3-4 with a weight and a
+ * threshold per voxel instead of per structure.  The paper re-plans on the
+ * day's anatomy with alpha_j = beta_j = 1 and T_j = the planned dose deformed
+ * onto that anatomy, so that the new plan reproduces the original dose.
+ * Voxel j contributes under_w[j] max(0, under_t[j] - z_j)^2 +
+ * over_w[j] max(0, z_j - over_t[j])^2 to F (Eq. 5); the weights are used as
+ * given (no division by a structure volume).  The paper's mode is under_w = 1
+ * on target voxels (Eq. 3 applies to V_T only; 0 elsewhere), over_w = 1 and
+ * under_t = over_t = T_j.  Arrays: host double[n_voxels], weights >= 0 and
+ * finite, thresholds finite (DAO_EINVAL otherwise); on the device each voxel
+ * keeps FP32 weights and its thresholds as FP32 hi + lo pairs. */
+typedef struct dao_voxel_terms {
+    const double* under_w;
+    const double* under_t;
+    const double* over_w;
+    const double* over_t;
+} dao_voxel_terms;
+
+/* As dao_create, with the objective of dao_voxel_terms in place of structures,
+ * weights and prescriptions.  Every other call works on the context as on one
+ * made by dao_create. */
+dao_status dao_create_voxelwise(const dao_csr* D, const dao_geometry* g, const dao_voxel_terms* t,
+                                const dao_options* opt, dao_ctx** out);
+
 /* Release a context.  Its device memory goes back to a process-wide
  * stream-ordered pool on its device, which keeps up to min(16 GiB, 1/16 of the
  * device) of freed memory mapped for the contexts created after it; its small

@@ -16,7 +16,7 @@ Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 certificates, an independent library solver); none is "parity unpinned".
 """
 from .dao import (  # noqa: F401
-    VoxelTerms, voxel_terms, objective, gradient, curvature, csr64, dose, beamlet_prices,
+    VoxelTerms, voxel_terms, reoptimisation_terms, objective, gradient, curvature, csr64, dose, beamlet_prices,
     kadane_row, Pricing, price, aperture_mask, aperture_column, fluence, MasterResult,
     solve_master, CGResult, column_generation, fmo, kkt_residual, pricing_tolerance,
     aperture_value,

@@ -56,6 +56,16 @@ def voxel_terms(case, normalize_by_volume: bool = True) -> VoxelTerms:
                       beta=b_s[s], t_over=np.asarray(case.over_t, np.float64)[s])
 
 
+def reoptimisation_terms(T, target_mask=None) -> VoxelTerms:
+    """The re-optimisation mode of Sec. 4: Eqs. 3-4 with alpha_j = beta_j = 1 and
+    T_j = the planned dose deformed onto the day's anatomy, used as both the
+    under- and the over-dose threshold.  Reading: Eq. 3 applies to target
+    voxels only (``target_mask``; None means every voxel), Eq. 4 to all."""
+    T = np.asarray(T, dtype=np.float64)
+    a = np.ones_like(T) if target_mask is None else np.asarray(target_mask, dtype=bool).astype(np.float64)
+    return VoxelTerms(alpha=a, t_under=T.copy(), beta=np.ones_like(T), t_over=T.copy())
+
+
 def objective(z: np.ndarray, vt: VoxelTerms) -> float:
     """F(z) of Eq. 5: sum over voxels of alpha_j max(0, T^-_j - z_j)^2 (Eq. 3/9)
     plus beta_j max(0, z_j - T^+_j)^2 (Eq. 4/10)."""
@@ -329,7 +339,7 @@ class CGResult:
 
 
 def column_generation(case, k_max: int, normalize_by_volume: bool = True, tol_rel: float = 1e-12,
-                      tau_rel: float = 1e-12, teacher=None, callback=None) -> CGResult:
+                      tau_rel: float = 1e-12, teacher=None, callback=None, vt: Optional[VoxelTerms] = None) -> CGResult:
     """Column generation for DAO (Sec. 2.2-2.3): start from an empty pool (y = [],
     z = 0); each iteration prices with pi = grad F(z) (Eq. 8), stops when the
     best reduced cost is not negative (the current plan is optimal over all
@@ -341,11 +351,13 @@ def column_generation(case, k_max: int, normalize_by_volume: bool = True, tol_re
     priced aperture (pricing still runs and is recorded); used to compare
     another solver's masters on an identical aperture sequence.
     ``callback(k, pricing, result)`` is called after each iteration.
+    ``vt``: per-voxel terms used in place of the case's structures (for example
+    ``reoptimisation_terms``, the re-optimisation mode of Sec. 4).
     Reading: an aperture identical to one already in the pool ends the loop with
     status "duplicate" (its reduced cost is >= 0 at an exact master optimum).
     """
     D = csr64(case)
-    vt = voxel_terms(case, normalize_by_volume)
+    vt = voxel_terms(case, normalize_by_volume) if vt is None else vt
     V = D.shape[0]
     res = CGResult()
     S = np.zeros((V, 0))
@@ -387,7 +399,8 @@ def column_generation(case, k_max: int, normalize_by_volume: bool = True, tol_re
     return res
 
 
-def fmo(case, normalize_by_volume: bool = True, tol_rel: float = 1e-12, max_iter: int = 500) -> MasterResult:
+def fmo(case, normalize_by_volume: bool = True, tol_rel: float = 1e-12, max_iter: int = 500,
+        vt: Optional[VoxelTerms] = None) -> MasterResult:
     """Beamlet-level fluence map optimisation min_{x >= 0} F(D x), the model the
     paper calls mathematically the same as DAO with beamlets as the decision
     variables (Sec. 2.2).  Solved by ``solve_master`` with S = D.  Its optimum
@@ -395,5 +408,5 @@ def fmo(case, normalize_by_volume: bool = True, tol_rel: float = 1e-12, max_iter
     column generation runs to optimality (any non-negative fluence map is a
     non-negative sum of consecutive-leaf apertures)."""
     D = csr64(case).tocsc()
-    vt = voxel_terms(case, normalize_by_volume)
+    vt = voxel_terms(case, normalize_by_volume) if vt is None else vt
     return solve_master(D, vt, np.zeros(D.shape[1]), tol_rel=tol_rel, max_iter=max_iter)

@@ -62,6 +62,10 @@ class dao_server_options(C.Structure):
                 ("plan_options", dao_options)]
 
 
+class dao_voxel_terms(C.Structure):
+    _fields_ = [("under_w", _F64P), ("under_t", _F64P), ("over_w", _F64P), ("over_t", _F64P)]
+
+
 class dao_request(C.Structure):
     _fields_ = [("D", dao_csr), ("geometry", dao_geometry), ("structures", dao_structures), ("weights", dao_weights),
                 ("prescriptions", _F64P), ("n_apertures", C.c_int32), ("dose_out", C.POINTER(C.c_float)),
@@ -84,6 +88,8 @@ SIGNATURES = {
     "dao_options_default": (None, [C.POINTER(dao_options)]),
     "dao_create": (C.c_int, [C.POINTER(dao_csr), C.POINTER(dao_geometry), C.POINTER(dao_structures),
                              C.POINTER(dao_weights), _F64P, C.POINTER(dao_options), C.POINTER(_P)]),
+    "dao_create_voxelwise": (C.c_int, [C.POINTER(dao_csr), C.POINTER(dao_geometry), C.POINTER(dao_voxel_terms),
+                                       C.POINTER(dao_options), C.POINTER(_P)]),
     "dao_destroy": (None, [_P]),
     "dao_release_cached_memory": (C.c_int, [C.c_int32]),
     "dao_check_bounded_wait": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
@@ -228,13 +234,24 @@ class Plan:
     ``stream`` is a raw cudaStream_t (e.g. ``torch.cuda.current_stream().cuda_stream``).
     """
 
-    def __init__(self, case, normalize_by_volume: bool = True, **opt):
+    def __init__(self, case, normalize_by_volume: bool = True, voxel_terms=None, **opt):
         lib = load()
         D, g, s, w, rx, self._keep = _case_structs(case, normalize_by_volume)
         o = options(**opt)
         h = C.c_void_p()
-        _check(lib.dao_create(C.byref(D), C.byref(g), C.byref(s), C.byref(w), _ptr(rx, C.c_double), C.byref(o),
-                              C.byref(h)), "dao_create")
+        if voxel_terms is None:
+            _check(lib.dao_create(C.byref(D), C.byref(g), C.byref(s), C.byref(w), _ptr(rx, C.c_double), C.byref(o),
+                                  C.byref(h)), "dao_create")
+        else:
+            # re-optimisation mode: per-voxel (under_w, under_t, over_w, over_t),
+            # each n_voxels long, in place of the case's structures and weights
+            V = len(case.indptr) - 1
+            arr = [np.ascontiguousarray(a, dtype=np.float64) for a in voxel_terms]
+            if len(arr) != 4 or any(a.shape != (V,) for a in arr):
+                raise ValueError(f"voxel_terms: four arrays of {V} values")
+            t = dao_voxel_terms(*[_ptr(a, C.c_double) for a in arr])
+            _check(lib.dao_create_voxelwise(C.byref(D), C.byref(g), C.byref(t), C.byref(o), C.byref(h)),
+                   "dao_create_voxelwise")
         self.h = h
         self._keep = []
         self.rows = np.array(case.rows, dtype=np.int32)

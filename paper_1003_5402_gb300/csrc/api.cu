@@ -255,7 +255,7 @@ dao_status upload(dao_ctx* c, T** dst, const T* src, size_t n) {
 }
 
 dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const dao_structures* s,
-                 const dao_weights* w, const double* rx) {
+                 const dao_weights* w, const double* rx, const dao_voxel_terms* vt) {
     const int V = c->V, N = c->N, B = c->B;
     // beam geometry
     c->rows.assign(g->rows, g->rows + B);
@@ -445,6 +445,22 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
                   (float)(tdh[k].to - (double)to_hi), 0.f, 0.f};
         // |grad F(0)| summed over the structure's voxels
         pi0_l1 += (double)count * (2.0 * tdh[k].a * std::max(0.0, tdh[k].tu) + 2.0 * tdh[k].b * std::max(0.0, -tdh[k].to));
+    }
+    if (vt != nullptr) {
+        // re-optimisation form of Eqs. 3-4: every voxel its own weights and
+        // thresholds (the kernels read terms[j] when S < 0); no volume division
+        tfh.assign(V, StructTermsF{});
+        tsh.assign(V, StructTermsS{});
+        pi0_l1 = 0.0;
+        for (int j = 0; j < V; ++j) {
+            const double a = vt->under_w[j], tu = vt->under_t[j], b = vt->over_w[j], to = vt->over_t[j];
+            tfh[j] = {(float)a, (float)tu, (float)b, (float)to};
+            const float tu_hi = (float)tu, to_hi = (float)to;
+            tsh[j] = {(float)a, tu_hi, (float)(tu - (double)tu_hi), (float)b, to_hi, (float)(to - (double)to_hi),
+                      0.f, 0.f};
+            pi0_l1 += 2.0 * a * std::max(0.0, tu) + 2.0 * b * std::max(0.0, -to);
+        }
+        c->S = -1;
     }
     c->tau = c->opt.price_tol * (double)dmax * pi0_l1;
 
@@ -1111,9 +1127,12 @@ void dao_options_default(dao_options* opt) {
 
 const char* dao_last_error(void) { return g_err.c_str(); }
 
-dao_status dao_create(const dao_csr* D, const dao_geometry* g, const dao_structures* s, const dao_weights* w,
-                      const double* prescriptions, const dao_options* opt_in, dao_ctx** out) {
-    TraceRange trace("dao_create");
+}  // extern "C"
+
+namespace {
+dao_status create_common(const dao_csr* D, const dao_geometry* g, const dao_structures* s, const dao_weights* w,
+                         const double* prescriptions, const dao_voxel_terms* vt, const dao_options* opt_in,
+                         dao_ctx** out) {
     if (!out) return fail(DAO_EINVAL, "null output pointer");
     *out = nullptr;
     dao_options opt;
@@ -1145,7 +1164,7 @@ dao_status dao_create(const dao_csr* D, const dao_geometry* g, const dao_structu
         e = master_configure();
         if (e != cudaSuccess) st = fail(DAO_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     }
-    if (st == DAO_OK) st = build(c, D, g, s, w, prescriptions);
+    if (st == DAO_OK) st = build(c, D, g, s, w, prescriptions, vt);
     if (st == DAO_OK) st = alloc_state(c);
     if (st == DAO_OK) st = reset_state(c);
     if (st != DAO_OK) {
@@ -1157,6 +1176,40 @@ dao_status dao_create(const dao_csr* D, const dao_geometry* g, const dao_structu
     c->count_launches();
     *out = c;
     return DAO_OK;
+}
+}  // namespace
+
+extern "C" {
+
+dao_status dao_create(const dao_csr* D, const dao_geometry* g, const dao_structures* s, const dao_weights* w,
+                      const double* prescriptions, const dao_options* opt_in, dao_ctx** out) {
+    TraceRange trace("dao_create");
+    return create_common(D, g, s, w, prescriptions, nullptr, opt_in, out);
+}
+
+dao_status dao_create_voxelwise(const dao_csr* D, const dao_geometry* g, const dao_voxel_terms* t,
+                                const dao_options* opt_in, dao_ctx** out) {
+    TraceRange trace("dao_create_voxelwise");
+    if (!out) return fail(DAO_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (!D || !t) return fail(DAO_EINVAL, "null argument");
+    if (!t->under_w || !t->under_t || !t->over_w || !t->over_t) return fail(DAO_EINVAL, "null voxel term array");
+    if (D->n_voxels < 1) return fail(DAO_EINVAL, "need at least one voxel and one beamlet");
+    for (int j = 0; j < D->n_voxels; ++j) {
+        if (!(t->under_w[j] >= 0) || !std::isfinite(t->under_w[j]) || !(t->over_w[j] >= 0) ||
+            !std::isfinite(t->over_w[j]))
+            return fail(DAO_EINVAL, "voxel weights must be finite and >= 0 (voxel " + std::to_string(j) + ")");
+        if (!std::isfinite(t->under_t[j]) || !std::isfinite(t->over_t[j]))
+            return fail(DAO_EINVAL, "voxel thresholds must be finite (voxel " + std::to_string(j) + ")");
+    }
+    // one structure that every voxel belongs to: the labels and per-structure
+    // weights the common path checks; the terms themselves come from t
+    std::vector<int32_t> labels((size_t)D->n_voxels, 0);
+    const uint8_t tgt = 0;
+    const double zero = 0.0;
+    const dao_structures s{1, labels.data(), &tgt};
+    const dao_weights w{&zero, &zero, &zero, 0};
+    return create_common(D, g, &s, &w, &zero, t, opt_in, out);
 }
 
 void dao_destroy(dao_ctx* c) {

@@ -39,6 +39,15 @@ struct StructTermsD { double a, tu, b, to; };
 // so that T - z is exact near the threshold.
 struct StructTermsS { float a, tu_hi, tu_lo, b, to_hi, to_lo, pad0, pad1; };
 
+// Every kernel that reads objective terms takes (labels, terms, S): with S >= 0
+// voxel j's terms are terms[labels[j]] (S structures, staged in shared
+// memory); with S < 0 (per-voxel weights and thresholds, the re-optimisation
+// form of Eqs. 3-4) they are terms[j] and the labels are not read.
+__device__ __forceinline__ StructTermsF voxel_terms(const StructTermsF* __restrict__ tf, int j) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(tf) + j);
+    return StructTermsF{v.x, v.y, v.z, v.w};
+}
+
 // Device copy of a CSR matrix whose rows are padded to a multiple of four
 // entries (padding: value 0, column = the row's last real column), so every
 // row starts on a 16-byte boundary for int4/float4 loads.

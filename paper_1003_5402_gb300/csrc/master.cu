@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(TILE, 3) k_master_eval(const __grid_constant__
         }
         float h = 0.f, p = 0.f;
         if (j < V) {
-            const StructTermsF t = s_tf[vstruct[j]];
+            const StructTermsF t = S >= 0 ? s_tf[vstruct[j]] : voxel_terms(tf, j);
             const float du = (t.tu - s) - c;   // T^- - z, exact subtraction near the threshold
             const float dov = (s - t.to) + c;  // z - T^+
             const float u = fmaxf(du, 0.f), o = fmaxf(dov, 0.f);
@@ -1069,7 +1069,9 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
         for (int i = warp; i < tiles_b; i += PW) {
             const int j = (blockIdx.x + i * G) * 32 + lane;
             const bool in = j < V;
-            const int sid = in ? vstruct[j] : 0;  // requested with the first columns
+            // requested with the first columns: the label, or the voxel's own terms
+            const int sid = in && S >= 0 ? vstruct[j] : 0;
+            const StructTermsF tv = in && S < 0 ? voxel_terms(tf, j) : StructTermsF{0.f, 0.f, 0.f, 0.f};
             float sc[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
             const float* col = slab + (in ? j : 0);
             // PB columns in flight per lane (one coalesced 128-byte row each), then
@@ -1098,7 +1100,7 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
             }
             float h = 0.f, p = 0.f;
             if (in) {
-                const StructTermsF t = s_tf[sid];
+                const StructTermsF t = S >= 0 ? s_tf[sid] : tv;
                 const float du = (t.tu - s) - c;
                 const float dov = (s - t.to) + c;
                 const float u = fmaxf(du, 0.f), o = fmaxf(dov, 0.f);
@@ -1304,7 +1306,7 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
                 c += e + cc[q];
             }
             if (in) {
-                const StructTermsF t = s_tf[vstruct[j]];
+                const StructTermsF t = S >= 0 ? s_tf[vstruct[j]] : voxel_terms(tf, j);
                 const float u = fmaxf((t.tu - s) - c, 0.f), o = fmaxf((s - t.to) + c, 0.f);
                 z_out[j] = s + c;
                 pi_out[j] = 2.f * (t.b * o - t.a * u);

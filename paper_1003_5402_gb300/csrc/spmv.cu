@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) k_dose(const int* __restrict__ rowptr, co
             z[row] = acc;
             if (grad != nullptr || F_part != nullptr) {
                 // FP32 epilogue (FP64 issues at 1/64 of the FP32 rate here)
-                const StructTermsS tt = s_ts[vstruct[row]];
+                const StructTermsS tt = S >= 0 ? s_ts[vstruct[row]] : ts[row];
                 const float u = fmaxf((tt.tu_hi - acc) + tt.tu_lo, 0.f);  // T^- - z
                 const float o = fmaxf((acc - tt.to_hi) - tt.to_lo, 0.f);  // z - T^+
                 if (grad != nullptr) grad[row] = 2.f * (tt.b * o - tt.a * u);
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(256) k_dose16(const int* __restrict__ rowptr, 
             z[row] = acc;
             if (grad != nullptr || F_part != nullptr) {
                 // FP32 epilogue (FP64 issues at 1/64 of the FP32 rate here)
-                const StructTermsS tt = s_ts[vstruct[row]];
+                const StructTermsS tt = S >= 0 ? s_ts[vstruct[row]] : ts[row];
                 const float u = fmaxf((tt.tu_hi - acc) + tt.tu_lo, 0.f);  // T^- - z
                 const float o = fmaxf((acc - tt.to_hi) - tt.to_lo, 0.f);  // z - T^+
                 if (grad != nullptr) grad[row] = 2.f * (tt.b * o - tt.a * u);

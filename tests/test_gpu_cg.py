@@ -43,21 +43,23 @@ def _tie_window(case, D, pi_gpu, pi_ref, apertures):
     return tot
 
 
-def _teacher_forced(case, K, torch, plan_kw=None, ref_case=None, ref_free=None):
+def _teacher_forced(case, K, torch, plan_kw=None, ref_case=None, ref_free=None, vt=None):
     """Teacher-forced column generation: the GPU prices from its own state, and
     the oracle's aperture is added on both sides.  At every round the GPU's
     choice must equal the oracle's or be an accepted tie, and its master
     optimum's dose must lie within DOSE_TOL of the oracle's.  ``ref_case``
     (default: case) is the matrix the oracle sees: the dequantised D for 16-bit
     storage.  ``ref_free``: the oracle's (result, steps) of this case, if
-    already computed."""
+    already computed.  ``vt``: per-voxel terms of the re-optimisation mode (the
+    plan then gets the same terms through ``plan_kw['voxel_terms']``)."""
     gpu_case, case = case, (case if ref_case is None else ref_case)
     D = O.csr64(case)
+    vt = O.voxel_terms(case) if vt is None else vt
     if ref_free is not None:
         ref, steps = ref_free
     else:
         steps = []
-        ref = O.column_generation(case, K, callback=lambda k, pr, m: steps.append((pr, m)))
+        ref = O.column_generation(case, K, callback=lambda k, pr, m: steps.append((pr, m)), vt=vt)
     out = {"F_gpu": [], "F_ref": list(ref.objective), "ties": 0, "exact": 0, "worst_dose": 0.0}
     with _plan(gpu_case, torch, **(plan_kw or {})) as plan:
         zbuf = torch.empty(case.n_voxels, dtype=torch.float32, device="cuda")
@@ -70,7 +72,7 @@ def _teacher_forced(case, K, torch, plan_kw=None, ref_case=None, ref_free=None):
             else:
                 plan.k_state(zbuf, pbuf)
                 pi_gpu = pbuf.cpu().numpy()
-                pi_ref = O.gradient(ref_z_before(ref, steps, k, case), O.voxel_terms(case))
+                pi_ref = O.gradient(ref_z_before(ref, steps, k, case), vt)
                 w_ref = O.beamlet_prices(D, pi_ref)
                 v_gpu_choice = O.aperture_value(case, w_ref, b, lv)
                 win = max(1e-9 * abs(pr_ref.reduced_cost),
@@ -120,7 +122,7 @@ def test_teacher_forced_parity(torch, name, K, persistent):
     assert abs(r["F_dose"] - Fr[-1]) <= RTOL_F * Fr[-1]
 
 
-def _free_running_checked(case, K, torch, plan_kw=None, ref_case=None, ref_free=None):
+def _free_running_checked(case, K, torch, plan_kw=None, ref_case=None, ref_free=None, vt=None):
     """Free-running column generation on the device (the graph path the
     benchmark times), checked against the oracle at every round.
 
@@ -136,11 +138,12 @@ def _free_running_checked(case, K, torch, plan_kw=None, ref_case=None, ref_free=
       - the dose agrees within DOSE_TOL per voxel.
     ``ref_case`` is the matrix the oracle sees (the dequantised D for 16-bit
     storage).  ``ref_free`` (optional) is the oracle's own free run of K rounds:
-    when the GPU's sequence equals it, the oracle is not run again.
+    when the GPU's sequence equals it, the oracle is not run again.  ``vt``:
+    per-voxel terms of the re-optimisation mode (see ``_teacher_forced``).
     Returns a summary dict."""
     gpu_case, case = case, (case if ref_case is None else ref_case)
     D = O.csr64(case)
-    vt = O.voxel_terms(case)
+    vt = O.voxel_terms(case) if vt is None else vt
     V = case.n_voxels
     pis, zs, Fs = [], [], []
     with _plan(gpu_case, torch, **(plan_kw or {})) as plan:
@@ -170,7 +173,7 @@ def _free_running_checked(case, K, torch, plan_kw=None, ref_case=None, ref_free=
         ref, steps = ref_free
     else:
         steps = []
-        ref = O.column_generation(case, K, teacher=aps, callback=lambda k, pr, m: steps.append((pr, m)))
+        ref = O.column_generation(case, K, teacher=aps, callback=lambda k, pr, m: steps.append((pr, m)), vt=vt)
     ties = 0
     worst_F = worst_z = 0.0
     for k in range(K):
