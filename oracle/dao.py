@@ -154,15 +154,37 @@ class Pricing:
     row_leaves: List[np.ndarray]   # [L, R) per row, per beam
 
 
-def price(case, w: np.ndarray) -> Pricing:
+def price(case, w: np.ndarray, mlc: str = "consecutive") -> Pricing:
     """Solve Eq. 8: every MLC row of every beam runs ``kadane_row``; the per-beam
     sums of v* are compared and the beam with the smallest sum gives the new
     aperture (Sec. 2.3).  Reading: equal beam sums go to the lowest beam index,
-    and the per-beam sum adds the rows' v* in row order."""
+    and the per-beam sum adds the rows' v* in row order.
+
+    ``mlc`` other than "consecutive" prices each beam under an MLC hardware
+    constraint of Sec. 4 (``oracle.mlc``: "interdigitation", "connected",
+    "jaws"); the beam's value then takes the place of the row sum and
+    ``row_values`` holds it at the beam's first row (0 in the others)."""
     rows = np.asarray(case.rows, np.int64)
     cols = np.asarray(case.cols, np.int64)
     off = np.concatenate([[0], np.cumsum(rows * cols)])
     sums, rv, rl = [], [], []
+    if mlc != "consecutive":
+        from .mlc import MODES
+        fn = MODES[mlc]
+        for b in range(len(rows)):
+            v, lv = fn(w[off[b]:off[b + 1]], int(rows[b]), int(cols[b]))
+            vals = np.zeros(rows[b])
+            vals[0] = v
+            sums.append(v)
+            rv.append(vals)
+            rl.append(lv)
+        sums = np.array(sums)
+        best = 0
+        for b in range(1, len(sums)):
+            if sums[b] < sums[best]:
+                best = b
+        return Pricing(beam=best, leaves=rl[best].copy(), reduced_cost=float(sums[best]),
+                       beam_values=sums, row_values=rv, row_leaves=rl)
     for b in range(len(rows)):
         vals = np.zeros(rows[b])
         lv = np.zeros((rows[b], 2), dtype=np.int32)
@@ -339,7 +361,8 @@ class CGResult:
 
 
 def column_generation(case, k_max: int, normalize_by_volume: bool = True, tol_rel: float = 1e-12,
-                      tau_rel: float = 1e-12, teacher=None, callback=None, vt: Optional[VoxelTerms] = None) -> CGResult:
+                      tau_rel: float = 1e-12, teacher=None, callback=None, vt: Optional[VoxelTerms] = None,
+                      mlc: str = "consecutive") -> CGResult:
     """Column generation for DAO (Sec. 2.2-2.3): start from an empty pool (y = [],
     z = 0); each iteration prices with pi = grad F(z) (Eq. 8), stops when the
     best reduced cost is not negative (the current plan is optimal over all
@@ -352,7 +375,8 @@ def column_generation(case, k_max: int, normalize_by_volume: bool = True, tol_re
     another solver's masters on an identical aperture sequence.
     ``callback(k, pricing, result)`` is called after each iteration.
     ``vt``: per-voxel terms used in place of the case's structures (for example
-    ``reoptimisation_terms``, the re-optimisation mode of Sec. 4).
+    ``reoptimisation_terms``, the re-optimisation mode of Sec. 4).  ``mlc``:
+    the MLC constraint of the pricing (``price``).
     Reading: an aperture identical to one already in the pool ends the loop with
     status "duplicate" (its reduced cost is >= 0 at an exact master optimum).
     """
@@ -367,7 +391,7 @@ def column_generation(case, k_max: int, normalize_by_volume: bool = True, tol_re
     for k in range(k_max):
         pi = gradient(z, vt)
         w = beamlet_prices(D, pi)
-        pr = price(case, w)
+        pr = price(case, w, mlc)
         if teacher is not None:
             b, lv = teacher[k]
             lv = np.asarray(lv, dtype=np.int32)
