@@ -93,6 +93,21 @@ typedef struct dao_weights {
 
 enum { DAO_PREC_FP32 = 0, DAO_PREC_FP16 = 1, DAO_PREC_BF16 = 2 };
 
+/* MLC hardware constraint of the pricing sub-problem (Sec. 4, last
+ * paragraph).  Every mode keeps each row's open beamlets consecutive; the
+ * paper's own pricing (Sec. 2.3) is DAO_MLC_CONSECUTIVE.
+ *   DAO_MLC_INTERDIGITATION: the leaves of adjacent rows may not cross,
+ *     L_r <= R_{r+1} and L_{r+1} <= R_r in boundary positions 0..cols, a
+ *     closed row keeping its two leaves together at some position p that
+ *     takes part in the constraint;
+ *   DAO_MLC_CONNECTED: the open rows form one contiguous block of rows;
+ *   DAO_MLC_JAWS: the aperture is a rectangle, one column range open in a
+ *     contiguous block of rows (jaws-only delivery).
+ * The constrained modes need at most 64 MLC rows per beam.  Their per-row
+ * outputs (dao_k_price's row_best) hold the beam's value at the beam's first
+ * row and 0 at the others. */
+enum { DAO_MLC_CONSECUTIVE = 0, DAO_MLC_INTERDIGITATION = 1, DAO_MLC_CONNECTED = 2, DAO_MLC_JAWS = 3 };
+
 /* Solver options; dao_options_default() fills every field. */
 typedef struct dao_options {
     int32_t k_max;             /* aperture pool capacity, 1..64 (default 64) */
@@ -111,6 +126,7 @@ typedef struct dao_options {
     int32_t master_persistent; /* 1 (default): each master solve is one cooperative kernel whose blocks
                                 * iterate together (bounded grid barriers); 0, or where a cooperative
                                 * launch is not available: one launch per evaluation kernel */
+    int32_t mlc_constraint;    /* DAO_MLC_* of the pricing (default DAO_MLC_CONSECUTIVE) */
 } dao_options;
 
 typedef struct dao_ctx dao_ctx;

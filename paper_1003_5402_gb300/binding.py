@@ -19,6 +19,9 @@ LIB_PATH = os.path.join(HERE, "libdao.so")
 DAO_OK, DAO_OPTIMAL, DAO_DUPLICATE = 0, 1, 2
 DAO_EINVAL, DAO_ENOMEM, DAO_ECUDA, DAO_ETIMEOUT, DAO_EBUSY, DAO_ESTATE = -1, -2, -3, -4, -5, -6
 DAO_PREC_FP32, DAO_PREC_FP16, DAO_PREC_BF16 = 0, 1, 2
+DAO_MLC_CONSECUTIVE, DAO_MLC_INTERDIGITATION, DAO_MLC_CONNECTED, DAO_MLC_JAWS = 0, 1, 2, 3
+MLC = {"consecutive": DAO_MLC_CONSECUTIVE, "interdigitation": DAO_MLC_INTERDIGITATION,
+       "connected": DAO_MLC_CONNECTED, "jaws": DAO_MLC_JAWS}
 KC = {"dose": 0, "dt": 1, "price": 2, "column": 3, "master_pass": 4, "master_reduce": 5, "master_step": 6,
       "master_hess": 7, "other": 8, "master_solve": 9}
 
@@ -48,7 +51,7 @@ class dao_weights(C.Structure):
 class dao_options(C.Structure):
     _fields_ = [("k_max", C.c_int32), ("max_master_iters", C.c_int32), ("master_tol", C.c_double),
                 ("price_tol", C.c_double), ("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
-                ("use_graphs", C.c_int32), ("master_persistent", C.c_int32)]
+                ("use_graphs", C.c_int32), ("master_persistent", C.c_int32), ("mlc_constraint", C.c_int32)]
 
 
 class dao_tuning(C.Structure):

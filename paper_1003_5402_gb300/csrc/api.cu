@@ -78,6 +78,7 @@ struct dao_ctx {
     int* beam_off_d = nullptr;
     int* row_cnt = nullptr;          // per MLC row: tickets of the fused D^T + row search
     int max_nb = 0;                  // largest rows * cols of a beam
+    size_t mlc_smem = 0;             // shared memory of the MLC-constrained pricing kernel (0: consecutive rows)
 
     // column-generation state
     int K = 0, K_cap = 0, ld = 0;
@@ -237,6 +238,11 @@ dao_status validate(const dao_csr* D, const dao_geometry* g, const dao_structure
     if (!(opt->master_tol > 0) || !(opt->price_tol >= 0)) return fail(DAO_EINVAL, "tolerances must be positive");
     if (opt->precision != DAO_PREC_FP32 && opt->precision != DAO_PREC_FP16 && opt->precision != DAO_PREC_BF16)
         return fail(DAO_EINVAL, "precision must be DAO_PREC_FP32, DAO_PREC_FP16 or DAO_PREC_BF16");
+    if (opt->mlc_constraint < DAO_MLC_CONSECUTIVE || opt->mlc_constraint > DAO_MLC_JAWS)
+        return fail(DAO_EINVAL, "mlc_constraint must be one of DAO_MLC_*");
+    if (opt->mlc_constraint != DAO_MLC_CONSECUTIVE)
+        for (int b = 0; b < g->n_beams; ++b)
+            if (g->rows[b] > 64) return fail(DAO_EINVAL, "the MLC-constrained pricing takes at most 64 rows per beam");
     if (opt->precision != DAO_PREC_FP32 && D->n_beamlets > 65536)
         return fail(DAO_EINVAL, "16-bit storage keeps beamlet indices in 16 bits: at most 65536 beamlets");
     return DAO_OK;
@@ -527,6 +533,12 @@ dao_status alloc_state(dao_ctx* c) {
     DAO_TRY(c->dalloc(&c->row_cnt, c->R_tot));
     DAO_CU(cudaMemsetAsync(c->row_cnt, 0, (size_t)std::max(c->R_tot, 1) * sizeof(int), c->stream));
     DAO_TRY(c->dalloc(&c->price, 1));
+    if (c->opt.mlc_constraint != DAO_MLC_CONSECUTIVE) {
+        int max_cols = 0;
+        for (int b = 0; b < c->B; ++b) max_cols = std::max(max_cols, c->cols[b]);
+        c->mlc_smem = mlc_smem_bytes(c->opt.mlc_constraint, c->max_rows, max_cols);
+        DAO_CU(mlc_configure(c->opt.mlc_constraint, c->mlc_smem));
+    }
     for (int k = 0; k <= KMAX; ++k) c->mb.grid[k] = master_grid(c->V, c->num_sms, k);
     c->mb.GH = master_hess_grid(c->num_sms);
     DAO_TRY(c->dalloc(&c->mb.bar, 1));
@@ -564,6 +576,25 @@ dao_status alloc_state(dao_ctx* c) {
 }
 
 // ---- the column-generation steps ------------------------------------------------
+
+// The per-row part of pricing on w (row_v, row_lr): the paper's row search per
+// MLC row, or the beams priced under the context's MLC constraint.
+cudaError_t price_rows_any(dao_ctx* c, const float* w, const int* skip, cudaStream_t s, int* n) {
+    if (c->opt.mlc_constraint == DAO_MLC_CONSECUTIVE)
+        return launch_price_rows(w, c->row_info, c->R_tot, c->row_v, c->row_lr, skip, s, n);
+    return launch_price_mlc(c->opt.mlc_constraint, w, c->beam_off_d, c->rows_d, c->cols_d, c->beam_row0_d, c->B,
+                            c->mlc_smem, c->row_v, c->row_lr, skip, s, n);
+}
+
+// Both parts of pricing: row results, beam sums and their argmin into c->price.
+cudaError_t price_any(dao_ctx* c, const float* w, const int* skip, cudaStream_t s, int* n) {
+    if (c->opt.mlc_constraint == DAO_MLC_CONSECUTIVE)
+        return launch_price(w, c->row_info, c->R_tot, c->beam_row0_d, c->B, c->row_v, c->row_lr, c->price, skip, s,
+                            n);
+    cudaError_t e = price_rows_any(c, w, skip, s, n);
+    if (e != cudaSuccess) return e;
+    return launch_price_beams(c->row_v, c->beam_row0_d, c->B, c->price, skip, s, n);
+}
 
 // pi = grad F(z) and z at the current pool's accepted intensities (final pass).
 dao_status refresh_state(dao_ctx* c) {
@@ -632,8 +663,7 @@ dao_status master_solve(dao_ctx* c, double* F_out) {
 dao_status price_on_w(dao_ctx* c, const float* w, int32_t* beam, int32_t* leaf_lr, double* rc, double* row_best,
                       int32_t* row_lr_out) {
     c->prof_begin(DAO_KC_PRICE);
-    DAO_CU(launch_price(w, c->row_info, c->R_tot, c->beam_row0_d, c->B, c->row_v, c->row_lr, c->price, nullptr,
-                        c->stream, &c->launches_i));
+    DAO_CU(price_any(c, w, nullptr, c->stream, &c->launches_i));
     c->prof_end();
     PriceDev* pd = reinterpret_cast<PriceDev*>(c->pinned + c->off_small + 16);
     int* lr = reinterpret_cast<int*>(c->pinned + c->off_rows);
@@ -740,7 +770,7 @@ dao_status build_round_graph_persist(dao_ctx* c, int K) {
     };
     if (e == cudaSuccess) {
         check(launch_dt(c->Dt, c->pi, c->w, stop, cs, &n));
-        check(launch_price_rows(c->w, c->row_info, c->R_tot, c->row_v, c->row_lr, stop, cs, &n));
+        check(price_rows_any(c, c->w, stop, cs, &n));
         check(launch_price_commit(c->row_v, c->beam_row0_d, c->B, c->price, c->row_lr, c->rows_d, c->cols_d, c->tau,
                                   K, 2 * c->max_rows, c->ap_beam, c->ap_lr, c->mask, c->cg, cs, &n));
         check(launch_column_dev(c->D, c->seg, c->ap_beam, K, c->beam_off_d, c->rows_d, c->cols_d, c->max_nb, c->mask,
@@ -803,8 +833,11 @@ bool build_solve_graph_persist(dao_ctx* c) {
         if (e == cudaSuccess) {
             // ROUNDS_PER_ITER rounds per iteration: the while node's relaunch costs
             // about as much as a few kernels, and rounds after the stop return at entry
-            const RowTicket rt{c->binfo, c->beam_row0_d, c->cols_d, c->row_info, c->row_cnt, c->row_v, c->row_lr,
-                               c->cg};
+            // with an MLC constraint the D^T kernel only takes the round's snapshot, and
+            // the beams are priced by their own kernel before the decision
+            const bool mlc = c->opt.mlc_constraint != DAO_MLC_CONSECUTIVE;
+            const RowTicket rt{c->binfo, c->beam_row0_d, c->cols_d, c->row_info, mlc ? nullptr : c->row_cnt,
+                               c->row_v, c->row_lr, c->cg};
             CommitArgs ca{};
             ca.row_v = c->row_v;
             ca.row_lr = c->row_lr;
@@ -824,6 +857,7 @@ bool build_solve_graph_persist(dao_ctx* c) {
             ca.cond = h;
             for (int u = 0; u < ROUNDS_PER_ITER; ++u) {
                 check(launch_dt_rows(c->Dt, c->pi, c->w, rt, cs, &n));
+                if (mlc) check(price_rows_any(c, c->w, &c->cg->stop, cs, &n));
                 check(launch_commit_column(c->D, ca, c->max_nb, c->num_sms, cs, &n));
                 check(launch_master_persist(c->mb, c->slab, c->ld, c->V, 0, c->vstruct, c->tf, c->S,
                                             c->opt.max_master_iters, c->opt.master_tol, skip, c->z, c->pi, c->cg,
@@ -871,7 +905,7 @@ dao_status build_round_graph(dao_ctx* c, int K) {
         check(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         if (e == cudaSuccess) {
             check(launch_dt(c->Dt, c->pi, c->w, stop, cs, &n));
-            check(launch_price_rows(c->w, c->row_info, c->R_tot, c->row_v, c->row_lr, stop, cs, &n));
+            check(price_rows_any(c, c->w, stop, cs, &n));
             check(launch_price_commit(c->row_v, c->beam_row0_d, c->B, c->price, c->row_lr, c->rows_d, c->cols_d,
                                       c->tau, K, 2 * c->max_rows, c->ap_beam, c->ap_lr, c->mask, c->cg, cs, &n));
             check(launch_column_dev(c->D, c->seg, c->ap_beam, K, c->beam_off_d, c->rows_d, c->cols_d, c->max_nb,
@@ -1016,7 +1050,8 @@ dao_status solve_graph_end(dao_ctx* c, const GraphSolve& gs, int n_apertures, in
         // the while node ran the rounds that grew the pool and, when pricing
         // stopped the solve, the round that found it, ROUNDS_PER_ITER to an iteration
         const int rounds = K - K0 + (h->done != 0 ? 1 : 0);
-        c->launches_i += 3 * ROUNDS_PER_ITER * ((rounds + ROUNDS_PER_ITER - 1) / ROUNDS_PER_ITER);
+        const int per_round = c->opt.mlc_constraint != DAO_MLC_CONSECUTIVE ? 4 : 3;
+        c->launches_i += per_round * ROUNDS_PER_ITER * ((rounds + ROUNDS_PER_ITER - 1) / ROUNDS_PER_ITER);
     } else {
         // every queued round launches its kernels (a stopped solve's rounds return at entry)
         c->launches_i += (persist ? 5 : 7) * (K1 - K0);
@@ -1123,6 +1158,7 @@ void dao_options_default(dao_options* opt) {
     opt->stream = nullptr;
     opt->use_graphs = 1;
     opt->master_persistent = 1;
+    opt->mlc_constraint = DAO_MLC_CONSECUTIVE;
 }
 
 const char* dao_last_error(void) { return g_err.c_str(); }
@@ -1494,8 +1530,7 @@ cudaError_t time_one(dao_ctx* c, int kc, int K, cudaStream_t s, int* n) {
                                  c->rows[b] * c->cols[b], c->mask, c->dose, 1, c->num_sms, s, n);
         }
         case DAO_KC_PRICE:
-            return launch_price(c->w, c->row_info, c->R_tot, c->beam_row0_d, c->B, c->row_v, c->row_lr, c->price,
-                                nullptr, s, n);
+            return price_any(c, c->w, nullptr, s, n);
     }
     return cudaErrorInvalidValue;
 }

@@ -172,6 +172,18 @@ cudaError_t launch_price_commit(const double* row_v, const int* beam_row0, int n
                                 const int2* row_lr, const int* rows, const int* cols, double tau, int K, int lr_stride,
                                 int* ap_beam, int* ap_lr, float* mask, CGDev* cg, cudaStream_t stream, int* launches);
 
+// Only the per-beam sums of row_v and their argmin (k_price_beams).
+cudaError_t launch_price_beams(const double* row_v, const int* beam_row0, int n_beams, PriceDev* out,
+                               const int* skip, cudaStream_t stream, int* launches);
+// a3 under an MLC constraint (mlc.cu): one block per beam writes row_v (the
+// beam's value at its first row, 0 at the others) and row_lr; smem bytes from
+// mlc_smem_bytes for the largest beam, after mlc_configure with that size.
+size_t mlc_smem_bytes(int mode, int max_rows, int max_cols);
+cudaError_t mlc_configure(int mode, size_t smem);
+cudaError_t launch_price_mlc(int mode, const float* w, const int* beam_off, const int* rows, const int* cols,
+                             const int* beam_row0, int n_beams, size_t smem, double* row_v, int2* row_lr,
+                             const int* skip, cudaStream_t stream, int* launches);
+
 // The device-driven round (one graph for every round of a solve):
 //  - D^T with the MLC-row search fused: the block that completes the last
 //    beamlet of an MLC row (a per-row ticket) runs that row's search; block 0

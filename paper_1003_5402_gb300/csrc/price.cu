@@ -110,6 +110,14 @@ cudaError_t launch_price_commit(const double* row_v, const int* beam_row0, int n
     return cudaGetLastError();
 }
 
+cudaError_t launch_price_beams(const double* row_v, const int* beam_row0, int n_beams, PriceDev* out,
+                               const int* skip, cudaStream_t stream, int* launches) {
+    k_price_beams<<<1, 256, (size_t)(n_beams > 0 ? n_beams : 1) * sizeof(double), stream>>>(row_v, beam_row0,
+                                                                                           n_beams, out, skip);
+    ++*launches;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_price(const float* w, const int4* row_info, int n_rows, const int* beam_row0, int n_beams,
                          double* row_v, int2* row_lr, PriceDev* out, const int* skip, cudaStream_t stream,
                          int* launches) {

@@ -141,10 +141,10 @@ __global__ void __launch_bounds__(256) k_sum_f64(const double* __restrict__ part
 }
 
 // ---- a2 ---------------------------------------------------------------------
-// The device-driven round (rt.row_cnt != nullptr): block 0 snapshots the pool
+// The device-driven round (rt.cg != nullptr): block 0 snapshots the pool
 // size and the stop flag for the fused commit kernel that follows.
 __device__ __forceinline__ void dt_round_snapshot(const RowTicket& rt) {
-    if (rt.row_cnt != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (rt.cg != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
         rt.cg->rs_K = rt.cg->K;
         rt.cg->rs_stop = rt.cg->stop;
     }
@@ -759,7 +759,7 @@ cudaError_t launch_dt(const DevCSR& Dt, const float* pi, float* w, const int* sk
 
 cudaError_t launch_dt_rows(const DevCSR& Dt, const float* pi, float* w, const RowTicket& rt, cudaStream_t stream,
                            int* launches) {
-    if (rt.row_cnt == nullptr || rt.cg == nullptr) return cudaErrorInvalidValue;
+    if (rt.cg == nullptr) return cudaErrorInvalidValue;  // row_cnt null: the snapshot without the row search
     return dt_dispatch(Dt, pi, w, &rt.cg->stop, rt, stream, launches);
 }
 

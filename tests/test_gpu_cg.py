@@ -43,7 +43,7 @@ def _tie_window(case, D, pi_gpu, pi_ref, apertures):
     return tot
 
 
-def _teacher_forced(case, K, torch, plan_kw=None, ref_case=None, ref_free=None, vt=None):
+def _teacher_forced(case, K, torch, plan_kw=None, ref_case=None, ref_free=None, vt=None, mlc="consecutive"):
     """Teacher-forced column generation: the GPU prices from its own state, and
     the oracle's aperture is added on both sides.  At every round the GPU's
     choice must equal the oracle's or be an accepted tie, and its master
@@ -51,7 +51,9 @@ def _teacher_forced(case, K, torch, plan_kw=None, ref_case=None, ref_free=None, 
     (default: case) is the matrix the oracle sees: the dequantised D for 16-bit
     storage.  ``ref_free``: the oracle's (result, steps) of this case, if
     already computed.  ``vt``: per-voxel terms of the re-optimisation mode (the
-    plan then gets the same terms through ``plan_kw['voxel_terms']``)."""
+    plan then gets the same terms through ``plan_kw['voxel_terms']``).  ``mlc``:
+    the oracle's MLC constraint (the plan's through
+    ``plan_kw['mlc_constraint']``)."""
     gpu_case, case = case, (case if ref_case is None else ref_case)
     D = O.csr64(case)
     vt = O.voxel_terms(case) if vt is None else vt
@@ -59,7 +61,7 @@ def _teacher_forced(case, K, torch, plan_kw=None, ref_case=None, ref_free=None, 
         ref, steps = ref_free
     else:
         steps = []
-        ref = O.column_generation(case, K, callback=lambda k, pr, m: steps.append((pr, m)), vt=vt)
+        ref = O.column_generation(case, K, callback=lambda k, pr, m: steps.append((pr, m)), vt=vt, mlc=mlc)
     out = {"F_gpu": [], "F_ref": list(ref.objective), "ties": 0, "exact": 0, "worst_dose": 0.0}
     with _plan(gpu_case, torch, **(plan_kw or {})) as plan:
         zbuf = torch.empty(case.n_voxels, dtype=torch.float32, device="cuda")
@@ -122,7 +124,8 @@ def test_teacher_forced_parity(torch, name, K, persistent):
     assert abs(r["F_dose"] - Fr[-1]) <= RTOL_F * Fr[-1]
 
 
-def _free_running_checked(case, K, torch, plan_kw=None, ref_case=None, ref_free=None, vt=None):
+def _free_running_checked(case, K, torch, plan_kw=None, ref_case=None, ref_free=None, vt=None,
+                          mlc="consecutive"):
     """Free-running column generation on the device (the graph path the
     benchmark times), checked against the oracle at every round.
 
@@ -139,7 +142,8 @@ def _free_running_checked(case, K, torch, plan_kw=None, ref_case=None, ref_free=
     ``ref_case`` is the matrix the oracle sees (the dequantised D for 16-bit
     storage).  ``ref_free`` (optional) is the oracle's own free run of K rounds:
     when the GPU's sequence equals it, the oracle is not run again.  ``vt``:
-    per-voxel terms of the re-optimisation mode (see ``_teacher_forced``).
+    per-voxel terms of the re-optimisation mode, ``mlc`` the MLC constraint
+    (see ``_teacher_forced``).
     Returns a summary dict."""
     gpu_case, case = case, (case if ref_case is None else ref_case)
     D = O.csr64(case)
@@ -173,7 +177,8 @@ def _free_running_checked(case, K, torch, plan_kw=None, ref_case=None, ref_free=
         ref, steps = ref_free
     else:
         steps = []
-        ref = O.column_generation(case, K, teacher=aps, callback=lambda k, pr, m: steps.append((pr, m)), vt=vt)
+        ref = O.column_generation(case, K, teacher=aps, callback=lambda k, pr, m: steps.append((pr, m)), vt=vt,
+                                  mlc=mlc)
     ties = 0
     worst_F = worst_z = 0.0
     for k in range(K):
