@@ -230,6 +230,24 @@ dao_status dao_add_aperture(dao_ctx* ctx, int32_t beam, const int32_t* leaf_lr, 
  * early, DAO_OK otherwise. */
 dao_status dao_solve(dao_ctx* ctx, int32_t n_apertures, int32_t* n_done, double* objective_trace);
 
+/* Beamlet-level fluence map optimisation, min over x >= 0 of F(D x): the model
+ * the paper calls mathematically the same as DAO with the beamlets as the
+ * decision variables (Sec. 2.2), solved, as the paper solves its FMO, by
+ * gradient projection on the GPU (Sec. 2.3).  Its optimum bounds every DAO
+ * objective of the same problem from below.  Method: projected Newton with an
+ * epsilon-active set, the free beamlets' Newton system solved inexactly by
+ * conjugate gradients (each product one dose SpMV and one transposed SpMV on
+ * the context's D and D^T, in its storage precision), and an Armijo rule along
+ * the projection arc.  Stops when ||x - P(x - g)||_inf <= tol times its value
+ * at x = 0, or after max_iters Newton steps.  Outputs (host, each optional):
+ * x_out double[n_beamlets], *objective = F(D x) (FP64 sum of the FP32 dose
+ * epilogue), *iters Newton steps, *cg_iters CG iterations in all.  Returns
+ * DAO_OK when the tolerance was met, DAO_ESTATE when the iteration cap or a
+ * failed arc search (the FP32 noise floor) stopped it first.  The aperture
+ * pool is not changed. */
+dao_status dao_fmo(dao_ctx* ctx, int32_t max_iters, double tol, double* x_out, double* objective, int32_t* iters,
+                   int32_t* cg_iters);
+
 /* Final dose z = D x with x_i = sum_{k in K_i} y_k (Eqs. 1, 7) computed by the
  * full dose SpMV; dose (host, n_voxels floats, optional), *objective (host,
  * optional) = F(z) of Eq. 5. */

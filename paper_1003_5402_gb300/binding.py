@@ -105,6 +105,7 @@ SIGNATURES = {
     "dao_intensities": (C.c_int, [_P, _F64P, _I32P]),
     "dao_apertures": (C.c_int, [_P, _I32P, _I32P, _I32P]),
     "dao_sizes": (C.c_int, [_P, _I32P, _I32P, _I32P, _I32P, _I32P, C.POINTER(C.c_int64), _I32P]),
+    "dao_fmo": (C.c_int, [_P, C.c_int32, C.c_double, _F64P, _F64P, _I32P, _I32P]),
     "dao_k_dose": (C.c_int, [_P, _P, _P, _P, _F64P]),
     "dao_k_beamlet_prices": (C.c_int, [_P, _P, _P]),
     "dao_k_price": (C.c_int, [_P, _P, _I32P, _I32P, _F64P, _F64P, _I32P]),
@@ -343,6 +344,17 @@ class Plan:
         F = C.c_double()
         _check(load().dao_dose(self.h, _ptr(z, C.c_float), C.byref(F)), "dao_dose")
         return z, F.value
+
+    def fmo(self, max_iters: int = 200, tol: float = 1e-7):
+        """dao_fmo: beamlet-level FMO on the device.  Returns (status, x, F,
+        Newton steps, CG iterations); status DAO_OK or DAO_ESTATE (cap hit)."""
+        x = np.zeros(self.n_beamlets)
+        F = C.c_double()
+        it = C.c_int32()
+        cg = C.c_int32()
+        st = _check(load().dao_fmo(self.h, int(max_iters), float(tol), _ptr(x, C.c_double), C.byref(F), C.byref(it),
+                                   C.byref(cg)), "dao_fmo", (DAO_OK, DAO_ESTATE))
+        return st, x, F.value, it.value, cg.value
 
     def intensities(self) -> np.ndarray:
         y = np.zeros(self.k_max)

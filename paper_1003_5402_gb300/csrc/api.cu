@@ -80,6 +80,13 @@ struct dao_ctx {
     int max_nb = 0;                  // largest rows * cols of a beam
     size_t mlc_smem = 0;             // shared memory of the MLC-constrained pricing kernel (0: consecutive rows)
 
+    // beamlet-level FMO (dao_fmo), allocated on its first call
+    double *fx = nullptr, *fxt = nullptr, *fr = nullptr, *fp = nullptr, *fdF = nullptr;
+    float *fx32 = nullptr, *fp32 = nullptr, *fg = nullptr, *fAp = nullptr;
+    float *fz = nullptr, *fzt = nullptr, *fpi = nullptr, *fpit = nullptr, *fu = nullptr;
+    unsigned char* ffree = nullptr;
+    FmoScalars* fst = nullptr;
+
     // column-generation state
     int K = 0, K_cap = 0, ld = 0;
     int async_K0 = 0, async_K1 = 0;  // rounds launched by solve_async_begin
@@ -1446,6 +1453,107 @@ dao_status dao_apertures(dao_ctx* c, int32_t* beams, int32_t* leaf_lr, int32_t* 
     if (leaf_lr) std::memcpy(leaf_lr, c->ap_lr_h.data(), sizeof(int) * c->K * 2 * c->max_rows);
     if (k) *k = c->K;
     return DAO_OK;
+}
+
+dao_status dao_fmo(dao_ctx* c, int32_t max_iters, double tol, double* x_out, double* objective, int32_t* iters,
+                   int32_t* cg_iters) {
+    TraceRange range("dao_fmo");
+    DAO_TRY(check_ctx(c));
+    if (max_iters < 1 || !(tol > 0)) return fail(DAO_EINVAL, "max_iters >= 1 and tol > 0 are required");
+    const int N = c->N, V = c->V;
+    if (c->fst == nullptr) {
+        DAO_TRY(c->dalloc(&c->fx, N));
+        DAO_TRY(c->dalloc(&c->fxt, N));
+        DAO_TRY(c->dalloc(&c->fr, N));
+        DAO_TRY(c->dalloc(&c->fp, N));
+        DAO_TRY(c->dalloc(&c->fdF, N));
+        DAO_TRY(c->dalloc(&c->fx32, N));
+        DAO_TRY(c->dalloc(&c->fp32, N));
+        DAO_TRY(c->dalloc(&c->fg, N));
+        DAO_TRY(c->dalloc(&c->fAp, N));
+        DAO_TRY(c->dalloc(&c->ffree, N));
+        DAO_TRY(c->dalloc(&c->fz, V));
+        DAO_TRY(c->dalloc(&c->fzt, V));
+        DAO_TRY(c->dalloc(&c->fpi, V));
+        DAO_TRY(c->dalloc(&c->fpit, V));
+        DAO_TRY(c->dalloc(&c->fu, V));
+        DAO_TRY(c->dalloc(&c->fst, 1));
+    }
+    cudaStream_t s = c->stream;
+    FmoScalars* h = reinterpret_cast<FmoScalars*>(c->pinned + c->off_master);  // the master shadow is idle here
+    double* hF = reinterpret_cast<double*>(c->pinned + c->off_small + 8);
+    int* n = &c->launches_i;
+    // F, z and pi of x: the a1 kernel with its epilogue; g = D^T pi: the a2 kernel
+    auto evaluate = [&](const float* x32, float* z, float* pi) -> dao_status {
+        DAO_CU(launch_dose(c->D, x32, c->vstruct, c->tf, c->ts, c->S, z, pi, c->F_part, c->F_blocks, c->F_dev,
+                           c->num_sms, s, n));
+        DAO_CU(cudaMemcpyAsync(hF, c->F_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+        return DAO_OK;
+    };
+    auto read_scalars = [&]() -> dao_status {
+        DAO_CU(cudaMemcpyAsync(h, c->fst, sizeof(FmoScalars), cudaMemcpyDeviceToHost, s));
+        return sync(c);
+    };
+    DAO_CU(cudaMemsetAsync(c->fx, 0, sizeof(double) * N, s));
+    DAO_CU(cudaMemsetAsync(c->fx32, 0, sizeof(float) * N, s));
+    DAO_TRY(evaluate(c->fx32, c->fz, c->fpi));
+    DAO_CU(launch_dt(c->Dt, c->fpi, c->fg, nullptr, s, n));
+    DAO_CU(fmo_kkt(N, c->fx, c->fg, c->fst, s));
+    DAO_TRY(read_scalars());
+    double F = *hF;
+    const double res0 = h->res;
+    double res = res0;
+    int it = 0, cg_total = 0;
+    constexpr int CG_BATCH = 8, CG_MAX = 400;
+    for (; it < max_iters && res > tol * res0; ++it) {
+        const double eps = std::min(1e-3, res), eta = std::min(0.1, std::sqrt(res / res0));
+        DAO_CU(fmo_cg_init(N, c->fx, c->fg, eps, eta, c->ffree, c->fr, c->fp, c->fp32, c->fdF, c->fst, s));
+        // CG on the free beamlets: u = D p, u *= h(z), Ap = D^T u; batches of
+        // CG_BATCH iterations between reads of the stop flag (after it the
+        // SpMVs run on p = 0 and the step kernel returns at entry)
+        for (int k = 0; k < CG_MAX; k += CG_BATCH) {
+            for (int q = 0; q < CG_BATCH; ++q) {
+                DAO_CU(launch_dose(c->D, c->fp32, c->vstruct, c->tf, c->ts, c->S, c->fu, nullptr, nullptr, 0,
+                                   nullptr, c->num_sms, s, n));
+                DAO_CU(fmo_hmul(V, c->fz, c->fu, c->vstruct, c->tf, c->S, c->num_sms, s));
+                ++*n;
+                DAO_CU(launch_dt(c->Dt, c->fu, c->fAp, nullptr, s, n));
+                DAO_CU(fmo_cg_step(N, c->fAp, c->ffree, c->fr, c->fp, c->fp32, c->fdF, c->fst, s));
+                ++*n;
+            }
+            DAO_TRY(read_scalars());
+            if (h->cg_done) break;
+        }
+        cg_total += h->cg_iters;
+        // Armijo rule along the projection arc
+        bool accepted = false;
+        double a = 1.0;
+        for (int ls = 0; ls < 60 && !accepted; ++ls, a *= 0.5) {
+            DAO_CU(fmo_trial(N, c->fx, c->fg, c->ffree, c->fdF, a, c->fxt, c->fx32, c->fst, s));
+            ++*n;
+            DAO_TRY(evaluate(c->fx32, c->fzt, c->fpit));
+            DAO_TRY(read_scalars());
+            accepted = *hF <= F + 1e-4 * h->gdx;
+        }
+        if (!accepted) break;  // no decrease along the arc: the FP32 noise floor
+        F = *hF;
+        std::swap(c->fx, c->fxt);
+        std::swap(c->fz, c->fzt);
+        std::swap(c->fpi, c->fpit);
+        DAO_CU(launch_dt(c->Dt, c->fpi, c->fg, nullptr, s, n));
+        DAO_CU(fmo_kkt(N, c->fx, c->fg, c->fst, s));
+        DAO_TRY(read_scalars());
+        res = h->res;
+    }
+    if (x_out) {
+        DAO_CU(cudaMemcpyAsync(x_out, c->fx, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+        DAO_TRY(sync(c));
+    }
+    if (objective) *objective = F;
+    if (iters) *iters = it;
+    if (cg_iters) *cg_iters = cg_total;
+    c->count_launches();
+    return res <= tol * res0 ? DAO_OK : DAO_ESTATE;
 }
 
 dao_status dao_k_dose(dao_ctx* c, const float* x, float* z, float* grad, double* objective) {

@@ -184,6 +184,27 @@ cudaError_t launch_price_mlc(int mode, const float* w, const int* beam_off, cons
                              const int* beam_row0, int n_beams, size_t smem, double* row_v, int2* row_lr,
                              const int* skip, cudaStream_t stream, int* launches);
 
+// Beamlet-level FMO (fmo.cu): the scalars that steer the host loop and the
+// one-block vector kernels on the N beamlets (FP64 values).
+struct FmoScalars {
+    double res;       // KKT residual ||x - P(x - g)||_inf of the current x
+    double rr;        // r^T r of the current CG iterate
+    double bb;        // g_F^T g_F (the CG right-hand side's norm squared)
+    double eta;       // CG forcing term
+    double gdx;       // g^T (x_trial - x)
+    int cg_done;      // the CG of this Newton step has stopped
+    int cg_iters;     // CG iterations of this Newton step
+};
+cudaError_t fmo_kkt(int N, const double* x, const float* g, FmoScalars* st, cudaStream_t s);
+cudaError_t fmo_cg_init(int N, const double* x, const float* g, double eps, double eta, unsigned char* free_,
+                        double* r, double* p, float* p32, double* dF, FmoScalars* st, cudaStream_t s);
+cudaError_t fmo_hmul(int V, const float* z, float* u, const uint8_t* vstruct, const StructTermsF* tf, int S,
+                     int num_sms, cudaStream_t s);
+cudaError_t fmo_cg_step(int N, const float* Ap, const unsigned char* free_, double* r, double* p, float* p32,
+                        double* dF, FmoScalars* st, cudaStream_t s);
+cudaError_t fmo_trial(int N, const double* x, const float* g, const unsigned char* free_, const double* dF, double a,
+                      double* xt, float* xt32, FmoScalars* st, cudaStream_t s);
+
 // The device-driven round (one graph for every round of a solve):
 //  - D^T with the MLC-row search fused: the block that completes the last
 //    beamlet of an MLC row (a per-row ticket) runs that row's search; block 0
