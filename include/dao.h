@@ -170,6 +170,56 @@ typedef struct dao_voxel_terms {
 dao_status dao_create_voxelwise(const dao_csr* D, const dao_geometry* g, const dao_voxel_terms* t,
                                 const dao_options* opt, dao_ctx** out);
 
+/* ---- D generated on the device from a pencil-beam model ----
+ * The paper obtains D_ij (Eq. 2) from its GPU pencil-beam dose engine
+ * (Sec. 1); generating D on the device removes its upload from a re-plan.
+ * Model, for beam b of n_beams coplanar beams at gantry angle 2 pi b / n_beams
+ * about the z axis (direction (sin, -cos), leaf travel along (cos, sin)), a
+ * grid of rows x cols beamlets of pitch beamlet_mm centred on iso, and voxel j
+ * at p = voxel_xyz[j] - iso (mm):
+ *   D_ij = exp(-mu_per_mm depth_j) L(dv) L(du), du / dv the voxel's offsets
+ *   from the beamlet's central axis, depth_j the distance along the beam from
+ *   the body's z-invariant cross-section (DAO_BODY_BOX: half-widths
+ *   body_size; DAO_BODY_ECYL: semi-axes body_size; centred at body_center) to
+ *   the voxel; L(d) = exp(-d^2 / (2 sigma^2)) (DAO_PB_GAUSS) or a strip of
+ *   width beamlet_mm blurred by that Gaussian, normalised to 1 on the axis
+ *   (DAO_PB_STRIP);
+ *   kept when above 1e-12 and at least cutoff times the beamlet's largest
+ *   coefficient, then multiplied by 1 + jitter (2 U - 1), U the SplitMix64 draw
+ *   of counter j n_beamlets + i in stream jitter_stream (0 jitter: none), and
+ *   rounded to FP32.  Beamlet i = b rows cols + r cols + c.
+ * FP64 throughout, every product and sum rounded on its own.  The search range
+ * of a voxel is the window of beamlets within ceil(sigma sqrt(2 ln 1e7) /
+ * beamlet_mm) + 1 of its own (at most 16 per axis, else DAO_EINVAL). */
+enum { DAO_PB_GAUSS = 0, DAO_PB_STRIP = 1 };
+enum { DAO_BODY_BOX = 0, DAO_BODY_ECYL = 1 };
+typedef struct dao_pencil_beam {
+    int32_t n_voxels;
+    const float* voxel_xyz;      /* host float[n_voxels][3], mm */
+    double iso[3];
+    int32_t n_beams, rows, cols;  /* 1 <= cols <= 32 */
+    double beamlet_mm, sigma_mm, mu_per_mm, cutoff;
+    int32_t profile;              /* DAO_PB_* */
+    int32_t body_kind;            /* DAO_BODY_* */
+    double body_center[2];        /* x, y */
+    double body_size[2];
+    double jitter;                /* in [0, 1) */
+    uint64_t jitter_stream;
+} dao_pencil_beam;
+
+/* Generate D on device `device` and copy it to host buffers: voxel-major CSR,
+ * columns increasing.  *nnz (host) receives the entry count; row_ptr
+ * (int64[n_voxels + 1]), col (int32[*nnz]) and val (float[*nnz]) may be NULL
+ * (call once with NULL buffers to learn *nnz, then with buffers of that size:
+ * the generation is deterministic).  Device memory is temporary. */
+dao_status dao_pencil_generate(const dao_pencil_beam* pb, int32_t device, int64_t* nnz, int64_t* row_ptr,
+                               int32_t* col, float* val);
+
+/* As dao_create, with D generated on the context's device from the pencil-beam
+ * model instead of a host CSR (n_beams beams of rows x cols beamlets). */
+dao_status dao_create_pencil(const dao_pencil_beam* pb, const dao_structures* s, const dao_weights* w,
+                             const double* prescriptions, const dao_options* opt, dao_ctx** out);
+
 /* Release a context.  Its device memory goes back to a process-wide
  * stream-ordered pool on its device, which keeps up to min(16 GiB, 1/16 of the
  * device) of freed memory mapped for the contexts created after it; its small

@@ -69,6 +69,14 @@ class dao_voxel_terms(C.Structure):
     _fields_ = [("under_w", _F64P), ("under_t", _F64P), ("over_w", _F64P), ("over_t", _F64P)]
 
 
+class dao_pencil_beam(C.Structure):
+    _fields_ = [("n_voxels", C.c_int32), ("voxel_xyz", C.POINTER(C.c_float)), ("iso", C.c_double * 3),
+                ("n_beams", C.c_int32), ("rows", C.c_int32), ("cols", C.c_int32), ("beamlet_mm", C.c_double),
+                ("sigma_mm", C.c_double), ("mu_per_mm", C.c_double), ("cutoff", C.c_double),
+                ("profile", C.c_int32), ("body_kind", C.c_int32), ("body_center", C.c_double * 2),
+                ("body_size", C.c_double * 2), ("jitter", C.c_double), ("jitter_stream", C.c_uint64)]
+
+
 class dao_request(C.Structure):
     _fields_ = [("D", dao_csr), ("geometry", dao_geometry), ("structures", dao_structures), ("weights", dao_weights),
                 ("prescriptions", _F64P), ("n_apertures", C.c_int32), ("dose_out", C.POINTER(C.c_float)),
@@ -93,6 +101,10 @@ SIGNATURES = {
                              C.POINTER(dao_weights), _F64P, C.POINTER(dao_options), C.POINTER(_P)]),
     "dao_create_voxelwise": (C.c_int, [C.POINTER(dao_csr), C.POINTER(dao_geometry), C.POINTER(dao_voxel_terms),
                                        C.POINTER(dao_options), C.POINTER(_P)]),
+    "dao_create_pencil": (C.c_int, [C.POINTER(dao_pencil_beam), C.POINTER(dao_structures), C.POINTER(dao_weights),
+                                    _F64P, C.POINTER(dao_options), C.POINTER(_P)]),
+    "dao_pencil_generate": (C.c_int, [C.POINTER(dao_pencil_beam), C.c_int32, C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_int64), _I32P, C.POINTER(C.c_float)]),
     "dao_destroy": (None, [_P]),
     "dao_release_cached_memory": (C.c_int, [C.c_int32]),
     "dao_check_bounded_wait": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
@@ -223,6 +235,42 @@ def _case_structs(case, normalize_by_volume: bool = True):
     return D, g, s, w, rx, keep
 
 
+def pencil_beam(xyz, iso, n_beams: int, rows: int, cols: int, beamlet_mm: float, sigma_mm: float,
+                mu_per_mm: float, cutoff: float, profile: str, body_kind: str, body_center, body_size,
+                jitter: float, jitter_stream: int):
+    """A dao_pencil_beam and the array it points into (keep both alive)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32).reshape(-1, 3)
+    pb = dao_pencil_beam()
+    pb.n_voxels = xyz.shape[0]
+    pb.voxel_xyz = _ptr(xyz, C.c_float)
+    pb.iso = (C.c_double * 3)(*[float(v) for v in iso])
+    pb.n_beams, pb.rows, pb.cols = int(n_beams), int(rows), int(cols)
+    pb.beamlet_mm, pb.sigma_mm, pb.mu_per_mm, pb.cutoff = float(beamlet_mm), float(sigma_mm), float(mu_per_mm), \
+        float(cutoff)
+    pb.profile = {"gauss": 0, "strip": 1}[profile]
+    pb.body_kind = {"box": 0, "ecyl": 1}[body_kind]
+    pb.body_center = (C.c_double * 2)(*[float(v) for v in body_center[:2]])
+    pb.body_size = (C.c_double * 2)(*[float(v) for v in body_size[:2]])
+    pb.jitter = float(jitter)
+    pb.jitter_stream = int(jitter_stream) & 0xFFFFFFFFFFFFFFFF
+    return pb, xyz
+
+
+def pencil_generate(pb_args: dict, device: int = 0):
+    """dao_pencil_generate: D from the pencil-beam model on the device, returned
+    as host CSR arrays (int64 row_ptr, int32 col, float32 val)."""
+    pb, keep = pencil_beam(**pb_args)
+    lib = load()
+    nnz = C.c_int64()
+    _check(lib.dao_pencil_generate(C.byref(pb), int(device), C.byref(nnz), None, None, None), "dao_pencil_generate")
+    rp = np.zeros(pb.n_voxels + 1, np.int64)
+    col = np.zeros(max(nnz.value, 1), np.int32)
+    val = np.zeros(max(nnz.value, 1), np.float32)
+    _check(lib.dao_pencil_generate(C.byref(pb), int(device), C.byref(nnz), _ptr(rp, C.c_int64), _ptr(col, C.c_int32),
+                                   _ptr(val, C.c_float)), "dao_pencil_generate")
+    return rp, col[: nnz.value], val[: nnz.value]
+
+
 def release_cached_memory(device: int = 0) -> None:
     """Give the device pool's cached memory and the page-locked free list back
     to the system (dao_release_cached_memory)."""
@@ -238,12 +286,18 @@ class Plan:
     ``stream`` is a raw cudaStream_t (e.g. ``torch.cuda.current_stream().cuda_stream``).
     """
 
-    def __init__(self, case, normalize_by_volume: bool = True, voxel_terms=None, **opt):
+    def __init__(self, case, normalize_by_volume: bool = True, voxel_terms=None, pencil=None, **opt):
         lib = load()
         D, g, s, w, rx, self._keep = _case_structs(case, normalize_by_volume)
         o = options(**opt)
         h = C.c_void_p()
-        if voxel_terms is None:
+        if pencil is not None:
+            # D generated on the device from the pencil-beam model (keyword
+            # arguments of ``pencil_beam``); the case gives structures and weights
+            pb, xyz = pencil_beam(**pencil)
+            _check(lib.dao_create_pencil(C.byref(pb), C.byref(s), C.byref(w), _ptr(rx, C.c_double), C.byref(o),
+                                         C.byref(h)), "dao_create_pencil")
+        elif voxel_terms is None:
             _check(lib.dao_create(C.byref(D), C.byref(g), C.byref(s), C.byref(w), _ptr(rx, C.c_double), C.byref(o),
                                   C.byref(h)), "dao_create")
         else:
@@ -345,7 +399,7 @@ class Plan:
         _check(load().dao_dose(self.h, _ptr(z, C.c_float), C.byref(F)), "dao_dose")
         return z, F.value
 
-    def fmo(self, max_iters: int = 200, tol: float = 1e-7):
+    def fmo(self, max_iters: int = 200, tol: float = 1e-6):
         """dao_fmo: beamlet-level FMO on the device.  Returns (status, x, F,
         Newton steps, CG iterations); status DAO_OK or DAO_ESTATE (cap hit)."""
         x = np.zeros(self.n_beamlets)

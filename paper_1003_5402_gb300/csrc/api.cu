@@ -219,9 +219,12 @@ dao_status validate(const dao_csr* D, const dao_geometry* g, const dao_structure
                     const double* rx, const dao_options* opt) {
     if (!D || !g || !s || !w || !rx || !opt) return fail(DAO_EINVAL, "null argument");
     if (D->n_voxels < 1 || D->n_beamlets < 1) return fail(DAO_EINVAL, "need at least one voxel and one beamlet");
-    if (!D->row_ptr || !D->col || !D->val) return fail(DAO_EINVAL, "null CSR array");
-    if (D->row_ptr[0] != 0 || D->row_ptr[D->n_voxels] != D->nnz || D->nnz < 0)
-        return fail(DAO_EINVAL, "row_ptr[0] must be 0 and row_ptr[n_voxels] must equal nnz");
+    const bool generated = D->nnz == -1 && !D->row_ptr && !D->col && !D->val;  // D made on the device
+    if (!generated) {
+        if (!D->row_ptr || !D->col || !D->val) return fail(DAO_EINVAL, "null CSR array");
+        if (D->row_ptr[0] != 0 || D->row_ptr[D->n_voxels] != D->nnz || D->nnz < 0)
+            return fail(DAO_EINVAL, "row_ptr[0] must be 0 and row_ptr[n_voxels] must equal nnz");
+    }
     if (g->n_beams < 1 || !g->rows || !g->cols) return fail(DAO_EINVAL, "geometry needs at least one beam");
     int64_t total = 0;
     for (int b = 0; b < g->n_beams; ++b) {
@@ -267,8 +270,16 @@ dao_status upload(dao_ctx* c, T** dst, const T* src, size_t n) {
     return DAO_OK;
 }
 
+// D already on the device (pool memory that build() takes over and frees).
+struct DeviceCSR {
+    int64_t* rp = nullptr;
+    int* col = nullptr;
+    float* val = nullptr;
+    int64_t nnz = 0;
+};
+
 dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const dao_structures* s,
-                 const dao_weights* w, const double* rx, const dao_voxel_terms* vt) {
+                 const dao_weights* w, const double* rx, const dao_voxel_terms* vt, DeviceCSR* din) {
     const int V = c->V, N = c->N, B = c->B;
     // beam geometry
     c->rows.assign(g->rows, g->rows + B);
@@ -294,7 +305,7 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     // values, to 8 entries (one 16-byte load of values and of 16-bit columns).
     const int prec = c->opt.precision;
     const int pad_m = prec == DAO_PREC_FP32 ? 4 : 8;
-    const int64_t nnz = Din->nnz;
+    const int64_t nnz = din ? din->nnz : Din->nnz;
     const int S = s->n_structures;
     c->S = S;
     // rows of D per chunk of the transpose: the chunk-by-beamlet counters stay under 16M
@@ -335,16 +346,26 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
         free_temps();
         return fail(DAO_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
     };
-    DAO_TRY(talloc(&t_rp, sizeof(int64_t) * (V + 1)));
-    DAO_TRY(talloc(&t_col, sizeof(int) * nnz));
-    DAO_TRY(talloc(&t_val, sizeof(float) * nnz));
+    if (din) {  // generated on the device: taken over, freed with the other temporaries
+        t_rp = din->rp;
+        t_col = din->col;
+        t_val = din->val;
+        *din = DeviceCSR{};
+    } else {
+        DAO_TRY(talloc(&t_rp, sizeof(int64_t) * (V + 1)));
+        DAO_TRY(talloc(&t_col, sizeof(int) * nnz));
+        DAO_TRY(talloc(&t_val, sizeof(float) * nnz));
+    }
     DAO_TRY(talloc(&t_lab, sizeof(int) * V));
     DAO_TRY(talloc(&t_plen, sizeof(int64_t) * V));
     DAO_TRY(talloc(&t_bsum, sizeof(int64_t) * check_scan_blocks(V)));
     DAO_TRY(talloc(&t_chk, sizeof(BuildCheck)));
-    DAO_TRY(cu(cudaMemcpyAsync(t_rp, Din->row_ptr, sizeof(int64_t) * (V + 1), cudaMemcpyHostToDevice, st), "upload"));
-    DAO_TRY(cu(cudaMemcpyAsync(t_col, Din->col, sizeof(int) * nnz, cudaMemcpyHostToDevice, st), "upload"));
-    DAO_TRY(cu(cudaMemcpyAsync(t_val, Din->val, sizeof(float) * nnz, cudaMemcpyHostToDevice, st), "upload"));
+    if (Din->row_ptr) {
+        DAO_TRY(cu(cudaMemcpyAsync(t_rp, Din->row_ptr, sizeof(int64_t) * (V + 1), cudaMemcpyHostToDevice, st),
+                   "upload"));
+        DAO_TRY(cu(cudaMemcpyAsync(t_col, Din->col, sizeof(int) * nnz, cudaMemcpyHostToDevice, st), "upload"));
+        DAO_TRY(cu(cudaMemcpyAsync(t_val, Din->val, sizeof(float) * nnz, cudaMemcpyHostToDevice, st), "upload"));
+    }
     DAO_TRY(cu(cudaMemcpyAsync(t_lab, s->voxel_struct, sizeof(int) * V, cudaMemcpyHostToDevice, st), "upload"));
     DAO_TRY(c->dalloc(&c->D.rowptr, (size_t)V + 1));
     DAO_TRY(c->dalloc(&c->vstruct, V));
@@ -357,7 +378,8 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     DAO_TRY(cu(cudaStreamSynchronize(st), "input checks"));
     if (chk.bad_row > 0) {
         free_temps();
-        return fail(DAO_EINVAL, row_error(Din, V - chk.bad_row));
+        return fail(DAO_EINVAL, Din->row_ptr ? row_error(Din, V - chk.bad_row)
+                                             : "invalid generated row " + std::to_string(V - chk.bad_row));
     }
     if (chk.bad_label > 0) {
         free_temps();
@@ -1175,7 +1197,7 @@ const char* dao_last_error(void) { return g_err.c_str(); }
 namespace {
 dao_status create_common(const dao_csr* D, const dao_geometry* g, const dao_structures* s, const dao_weights* w,
                          const double* prescriptions, const dao_voxel_terms* vt, const dao_options* opt_in,
-                         dao_ctx** out) {
+                         dao_ctx** out, const dao_pencil_beam* pb = nullptr) {
     if (!out) return fail(DAO_EINVAL, "null output pointer");
     *out = nullptr;
     dao_options opt;
@@ -1207,7 +1229,20 @@ dao_status create_common(const dao_csr* D, const dao_geometry* g, const dao_stru
         e = master_configure();
         if (e != cudaSuccess) st = fail(DAO_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     }
-    if (st == DAO_OK) st = build(c, D, g, s, w, prescriptions, vt);
+    DeviceCSR gen;
+    if (st == DAO_OK && pb) {  // D from the pencil-beam model, on the device
+        TraceRange range("pencil-beam D");
+        e = pencil_generate(pb, c->device, c->stream, &gen.rp, &gen.col, &gen.val, &gen.nnz);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            st = fail(e == cudaErrorMemoryAllocation ? DAO_ENOMEM : DAO_ECUDA,
+                      std::string("pencil-beam generation: ") + cudaGetErrorString(e));
+        }
+        c->nnz = gen.nnz;
+    }
+    if (st == DAO_OK) st = build(c, D, g, s, w, prescriptions, vt, pb ? &gen : nullptr);
+    for (void* q : {(void*)gen.rp, (void*)gen.col, (void*)gen.val})  // left over when build did not run
+        if (q) pool_free(q, c->stream);
     if (st == DAO_OK) st = alloc_state(c);
     if (st == DAO_OK) st = reset_state(c);
     if (st != DAO_OK) {
@@ -1253,6 +1288,49 @@ dao_status dao_create_voxelwise(const dao_csr* D, const dao_geometry* g, const d
     const dao_structures s{1, labels.data(), &tgt};
     const dao_weights w{&zero, &zero, &zero, 0};
     return create_common(D, g, &s, &w, &zero, t, opt_in, out);
+}
+
+dao_status dao_create_pencil(const dao_pencil_beam* pb, const dao_structures* s, const dao_weights* w,
+                             const double* prescriptions, const dao_options* opt_in, dao_ctx** out) {
+    TraceRange trace("dao_create_pencil");
+    if (!out) return fail(DAO_EINVAL, "null output pointer");
+    *out = nullptr;
+    DAO_TRY(pencil_check(pb));
+    std::vector<int32_t> rows(pb->n_beams, pb->rows), cols(pb->n_beams, pb->cols);
+    const dao_geometry g{pb->n_beams, rows.data(), cols.data()};
+    dao_csr D{};
+    D.n_voxels = pb->n_voxels;
+    D.n_beamlets = pb->n_beams * pb->rows * pb->cols;
+    D.nnz = -1;  // generated on the device
+    return create_common(&D, &g, s, w, prescriptions, nullptr, opt_in, out, pb);
+}
+
+dao_status dao_pencil_generate(const dao_pencil_beam* pb, int32_t device, int64_t* nnz, int64_t* row_ptr,
+                               int32_t* col, float* val) {
+    TraceRange trace("dao_pencil_generate");
+    DAO_TRY(pencil_check(pb));
+    int n = 0;
+    DAO_CU(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(DAO_EINVAL, "no such device");
+    DAO_CU(cudaSetDevice(device));
+    cudaStream_t s = nullptr;
+    DAO_CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    int64_t* rp = nullptr;
+    int* c = nullptr;
+    float* v = nullptr;
+    int64_t m = 0;
+    cudaError_t e = pencil_generate(pb, device, s, &rp, &c, &v, &m);
+    if (e == cudaSuccess && row_ptr)
+        e = cudaMemcpyAsync(row_ptr, rp, sizeof(int64_t) * ((size_t)pb->n_voxels + 1), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && col && m > 0) e = cudaMemcpyAsync(col, c, sizeof(int) * (size_t)m, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && val && m > 0) e = cudaMemcpyAsync(val, v, sizeof(float) * (size_t)m, cudaMemcpyDeviceToHost, s);
+    for (void* q : {(void*)rp, (void*)c, (void*)v})
+        if (q) pool_free(q, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (e != cudaSuccess) return fail(DAO_ECUDA, std::string("dao_pencil_generate: ") + cudaGetErrorString(e));
+    if (nnz) *nnz = m;
+    return DAO_OK;
 }
 
 void dao_destroy(dao_ctx* c) {

@@ -205,6 +205,13 @@ cudaError_t fmo_cg_step(int N, const float* Ap, const unsigned char* free_, doub
 cudaError_t fmo_trial(int N, const double* x, const float* g, const unsigned char* free_, const double* dF, double a,
                       double* xt, float* xt32, FmoScalars* st, cudaStream_t s);
 
+// D from the pencil-beam model on the device (pencil.cu): argument checks, and
+// the voxel-major CSR (int64 row offsets, int32 columns, FP32 values) in
+// stream-ordered pool memory that the caller frees with pool_free.
+dao_status pencil_check(const dao_pencil_beam* pb);
+cudaError_t pencil_generate(const dao_pencil_beam* pb, int device, cudaStream_t s, int64_t** rp, int** col,
+                            float** val, int64_t* nnz);
+
 // The device-driven round (one graph for every round of a solve):
 //  - D^T with the MLC-row search fused: the block that completes the last
 //    beamlet of an MLC row (a per-row ticket) runs that row's search; block 0
