@@ -288,8 +288,9 @@ dao_status dao_solve(dao_ctx* ctx, int32_t n_apertures, int32_t* n_done, double*
  * epsilon-active set, the free beamlets' Newton system solved inexactly by
  * conjugate gradients (each product one dose SpMV and one transposed SpMV on
  * the context's D and D^T, in its storage precision), and an Armijo rule along
- * the projection arc.  Stops when ||x - P(x - g)||_inf <= tol times its value
- * at x = 0, or after max_iters Newton steps.  Outputs (host, each optional):
+ * the projection arc.  Stops when every |x_i - P(x_i - g_i)| is within tol times
+ * the largest such residual at x = 0 plus 64 u (D^T |grad F|)_i (u = 2^-24,
+ * the FP32 rounding of g_i), or after max_iters Newton steps.  Outputs (host, each optional):
  * x_out double[n_beamlets], *objective = F(D x) (FP64 sum of the FP32 dose
  * epilogue), *iters Newton steps, *cg_iters CG iterations in all.  Returns
  * DAO_OK when the tolerance was met, DAO_ESTATE when the iteration cap or a

@@ -399,7 +399,7 @@ class Plan:
         _check(load().dao_dose(self.h, _ptr(z, C.c_float), C.byref(F)), "dao_dose")
         return z, F.value
 
-    def fmo(self, max_iters: int = 200, tol: float = 1e-6):
+    def fmo(self, max_iters: int = 300, tol: float = 1e-7):
         """dao_fmo: beamlet-level FMO on the device.  Returns (status, x, F,
         Newton steps, CG iterations); status DAO_OK or DAO_ESTATE (cap hit)."""
         x = np.zeros(self.n_beamlets)

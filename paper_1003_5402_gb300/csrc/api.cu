@@ -1574,16 +1574,24 @@ dao_status dao_fmo(dao_ctx* c, int32_t max_iters, double tol, double* x_out, dou
     };
     DAO_CU(cudaMemsetAsync(c->fx, 0, sizeof(double) * N, s));
     DAO_CU(cudaMemsetAsync(c->fx32, 0, sizeof(float) * N, s));
+    // g = D^T pi, its rounding scale D^T |pi| (into the CG's Ap buffer) and the KKT test
+    auto gradient = [&]() -> dao_status {
+        DAO_CU(launch_dt(c->Dt, c->fpi, c->fg, nullptr, s, n));
+        DAO_CU(fmo_abs(V, c->fpi, c->fu, c->num_sms, s));
+        ++*n;
+        DAO_CU(launch_dt(c->Dt, c->fu, c->fAp, nullptr, s, n));
+        DAO_CU(fmo_kkt(N, c->fx, c->fg, c->fAp, c->fst, s));
+        ++*n;
+        return read_scalars();
+    };
     DAO_TRY(evaluate(c->fx32, c->fz, c->fpi));
-    DAO_CU(launch_dt(c->Dt, c->fpi, c->fg, nullptr, s, n));
-    DAO_CU(fmo_kkt(N, c->fx, c->fg, c->fst, s));
-    DAO_TRY(read_scalars());
+    DAO_TRY(gradient());
     double F = *hF;
     const double res0 = h->res;
-    double res = res0;
+    double res = res0, res_x = h->res_x;
     int it = 0, cg_total = 0;
     constexpr int CG_BATCH = 8, CG_MAX = 400;
-    for (; it < max_iters && res > tol * res0; ++it) {
+    for (; it < max_iters && res_x > tol * res0; ++it) {
         const double eps = std::min(1e-3, res), eta = std::min(0.1, std::sqrt(res / res0));
         DAO_CU(fmo_cg_init(N, c->fx, c->fg, eps, eta, c->ffree, c->fr, c->fp, c->fp32, c->fdF, c->fst, s));
         // CG on the free beamlets: u = D p, u *= h(z), Ap = D^T u; batches of
@@ -1618,10 +1626,9 @@ dao_status dao_fmo(dao_ctx* c, int32_t max_iters, double tol, double* x_out, dou
         std::swap(c->fx, c->fxt);
         std::swap(c->fz, c->fzt);
         std::swap(c->fpi, c->fpit);
-        DAO_CU(launch_dt(c->Dt, c->fpi, c->fg, nullptr, s, n));
-        DAO_CU(fmo_kkt(N, c->fx, c->fg, c->fst, s));
-        DAO_TRY(read_scalars());
+        DAO_TRY(gradient());
         res = h->res;
+        res_x = h->res_x;
     }
     if (x_out) {
         DAO_CU(cudaMemcpyAsync(x_out, c->fx, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
@@ -1631,7 +1638,7 @@ dao_status dao_fmo(dao_ctx* c, int32_t max_iters, double tol, double* x_out, dou
     if (iters) *iters = it;
     if (cg_iters) *cg_iters = cg_total;
     c->count_launches();
-    return res <= tol * res0 ? DAO_OK : DAO_ESTATE;
+    return res_x <= tol * res0 ? DAO_OK : DAO_ESTATE;
 }
 
 dao_status dao_k_dose(dao_ctx* c, const float* x, float* z, float* grad, double* objective) {

@@ -188,6 +188,7 @@ cudaError_t launch_price_mlc(int mode, const float* w, const int* beam_off, cons
 // one-block vector kernels on the N beamlets (FP64 values).
 struct FmoScalars {
     double res;       // KKT residual ||x - P(x - g)||_inf of the current x
+    double res_x;     // its part beyond the FP32 rounding of g (the stopping test)
     double rr;        // r^T r of the current CG iterate
     double bb;        // g_F^T g_F (the CG right-hand side's norm squared)
     double eta;       // CG forcing term
@@ -195,7 +196,8 @@ struct FmoScalars {
     int cg_done;      // the CG of this Newton step has stopped
     int cg_iters;     // CG iterations of this Newton step
 };
-cudaError_t fmo_kkt(int N, const double* x, const float* g, FmoScalars* st, cudaStream_t s);
+cudaError_t fmo_kkt(int N, const double* x, const float* g, const float* gn, FmoScalars* st, cudaStream_t s);
+cudaError_t fmo_abs(int V, const float* pi, float* out, int num_sms, cudaStream_t s);
 cudaError_t fmo_cg_init(int N, const double* x, const float* g, double eps, double eta, unsigned char* free_,
                         double* r, double* p, float* p32, double* dF, FmoScalars* st, cudaStream_t s);
 cudaError_t fmo_hmul(int V, const float* z, float* u, const uint8_t* vstruct, const StructTermsF* tf, int S,

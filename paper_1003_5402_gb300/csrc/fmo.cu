@@ -69,14 +69,28 @@ __device__ __forceinline__ double fv_block_max(double v, double* s_red) {
     return t;
 }
 
-// KKT residual ||x - P(x - g)||_inf.
+// KKT residual ||x - P(x - g)||_inf, and its part beyond the FP32 rounding of
+// g: max_i (|x_i - P(x_i - g_i)| - 64 u gn_i), gn = D^T |pi| (u = 2^-24).
 __global__ void __launch_bounds__(FV_T) k_fmo_kkt(int N, const double* __restrict__ x, const float* __restrict__ g,
-                                                  FmoScalars* __restrict__ st) {
+                                                  const float* __restrict__ gn, FmoScalars* __restrict__ st) {
     __shared__ double s_red[33];
-    double m = 0.0;
-    for (int i = threadIdx.x; i < N; i += FV_T) m = fmax(m, fabs(x[i] - fmax(x[i] - (double)g[i], 0.0)));
+    double m = 0.0, mx = 0.0;
+    for (int i = threadIdx.x; i < N; i += FV_T) {
+        const double r = fabs(x[i] - fmax(x[i] - (double)g[i], 0.0));
+        m = fmax(m, r);
+        mx = fmax(mx, r - 64.0 * 5.9604644775390625e-08 * (double)gn[i]);
+    }
     m = fv_block_max(m, s_red);
-    if (threadIdx.x == 0) st->res = m;
+    mx = fv_block_max(mx, s_red);
+    if (threadIdx.x == 0) {
+        st->res = m;
+        st->res_x = mx;
+    }
+}
+
+// |pi| for the rounding scale of g.
+__global__ void __launch_bounds__(256) k_fmo_abs(int V, const float* __restrict__ pi, float* __restrict__ out) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < V; j += gridDim.x * blockDim.x) out[j] = fabsf(pi[j]);
 }
 
 // The free set {not (x_i <= eps and g_i > 0)}, r = -g_F, p = r, d_F = 0.
@@ -187,8 +201,12 @@ __global__ void __launch_bounds__(FV_T) k_fmo_trial(int N, const double* __restr
 
 }  // namespace
 
-cudaError_t fmo_kkt(int N, const double* x, const float* g, FmoScalars* st, cudaStream_t s) {
-    k_fmo_kkt<<<1, FV_T, 0, s>>>(N, x, g, st);
+cudaError_t fmo_kkt(int N, const double* x, const float* g, const float* gn, FmoScalars* st, cudaStream_t s) {
+    k_fmo_kkt<<<1, FV_T, 0, s>>>(N, x, g, gn, st);
+    return cudaGetLastError();
+}
+cudaError_t fmo_abs(int V, const float* pi, float* out, int num_sms, cudaStream_t s) {
+    k_fmo_abs<<<num_sms * 4, 256, 0, s>>>(V, pi, out);
     return cudaGetLastError();
 }
 cudaError_t fmo_cg_init(int N, const double* x, const float* g, double eps, double eta, unsigned char* free_,

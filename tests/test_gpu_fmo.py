@@ -61,7 +61,7 @@ def test_fmo_matches_oracle(torch, name, prec):
     gold = _golden_fmo()
     ref_F = gold[name] if (prec == 0 and name in gold) else O.fmo(ref_case).F
     with _plan(case, torch, precision=prec) as plan:
-        st, x, F, its, cg = plan.fmo(max_iters=300, tol=1e-6)
+        st, x, F, its, cg = plan.fmo(max_iters=300, tol=1e-7)
     print(f"\nFMO {name} prec={prec}: F {F:.9e} oracle {ref_F:.9e} rel {(F - ref_F) / ref_F:+.2e}, "
           f"{its} Newton steps, {cg} CG iterations, status {st}")
     assert np.all(x >= 0)
@@ -89,7 +89,7 @@ def test_fmo_reoptimisation_mode(torch):
     vt = O.reoptimisation_terms(T, target_mask=np.asarray(case.is_target, bool)[case.voxel_struct])
     ref = O.fmo(case, vt=vt)
     with _plan(case, torch, voxel_terms=(vt.alpha, vt.t_under, vt.beta, vt.t_over)) as plan:
-        st, x, F, its, cg = plan.fmo(max_iters=300, tol=1e-6)
+        st, x, F, its, cg = plan.fmo(max_iters=300, tol=1e-7)
     assert ref.F > 1e-8 and abs(F - ref.F) <= RTOL_F * ref.F
     assert _kkt_rel(case, x, vt) <= 1e-4
 
