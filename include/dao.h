@@ -127,6 +127,9 @@ typedef struct dao_options {
                                 * iterate together (bounded grid barriers); 0, or where a cooperative
                                 * launch is not available: one launch per evaluation kernel */
     int32_t mlc_constraint;    /* DAO_MLC_* of the pricing (default DAO_MLC_CONSECUTIVE) */
+    int32_t master_blocks;     /* blocks of the persistent master solve; 0 (default): two per SM, the whole
+                                * GPU; fewer (raised to the least whose per-block working set fits shared
+                                * memory) leave room for other plans' solves to run side by side */
 } dao_options;
 
 typedef struct dao_ctx dao_ctx;

@@ -51,7 +51,8 @@ class dao_weights(C.Structure):
 class dao_options(C.Structure):
     _fields_ = [("k_max", C.c_int32), ("max_master_iters", C.c_int32), ("master_tol", C.c_double),
                 ("price_tol", C.c_double), ("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
-                ("use_graphs", C.c_int32), ("master_persistent", C.c_int32), ("mlc_constraint", C.c_int32)]
+                ("use_graphs", C.c_int32), ("master_persistent", C.c_int32), ("mlc_constraint", C.c_int32),
+                ("master_blocks", C.c_int32)]
 
 
 class dao_tuning(C.Structure):

@@ -248,6 +248,7 @@ dao_status validate(const dao_csr* D, const dao_geometry* g, const dao_structure
     if (!(opt->master_tol > 0) || !(opt->price_tol >= 0)) return fail(DAO_EINVAL, "tolerances must be positive");
     if (opt->precision != DAO_PREC_FP32 && opt->precision != DAO_PREC_FP16 && opt->precision != DAO_PREC_BF16)
         return fail(DAO_EINVAL, "precision must be DAO_PREC_FP32, DAO_PREC_FP16 or DAO_PREC_BF16");
+    if (opt->master_blocks < 0) return fail(DAO_EINVAL, "master_blocks must be >= 0");
     if (opt->mlc_constraint < DAO_MLC_CONSECUTIVE || opt->mlc_constraint > DAO_MLC_JAWS)
         return fail(DAO_EINVAL, "mlc_constraint must be one of DAO_MLC_*");
     if (opt->mlc_constraint != DAO_MLC_CONSECUTIVE)
@@ -572,7 +573,7 @@ dao_status alloc_state(dao_ctx* c) {
     c->mb.GH = master_hess_grid(c->num_sms);
     DAO_TRY(c->dalloc(&c->mb.bar, 1));
     DAO_CU(cudaMemsetAsync(c->mb.bar, 0, sizeof(GridBar), c->stream));
-    c->mb.GP = c->opt.master_persistent ? master_persist_grid(c->V, c->num_sms) : 0;
+    c->mb.GP = c->opt.master_persistent ? master_persist_grid(c->V, c->num_sms, c->opt.master_blocks) : 0;
     if (c->mb.GP > c->mb.GH) c->mb.GP = c->mb.GH;  // the partial arrays have GH columns
     DAO_TRY(c->dalloc(&c->mb.st, 1));
     DAO_TRY(c->dalloc(&c->mb.act_rows, (size_t)c->ld * KROW));
@@ -1188,6 +1189,7 @@ void dao_options_default(dao_options* opt) {
     opt->use_graphs = 1;
     opt->master_persistent = 1;
     opt->mlc_constraint = DAO_MLC_CONSECUTIVE;
+    opt->master_blocks = 0;
 }
 
 const char* dao_last_error(void) { return g_err.c_str(); }

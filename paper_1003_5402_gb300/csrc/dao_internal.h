@@ -380,7 +380,7 @@ size_t master_persist_smem(int V, int G);
 // grid barrier; out[0] counts the blocks whose bounded wait gave up, out[1]
 // those that passed.
 cudaError_t launch_barrier_check(GridBar* gb, int blocks, int absent, int* out, cudaStream_t stream);
-int master_persist_grid(int V, int num_sms);
+int master_persist_grid(int V, int num_sms, int want = 0);
 // Includes k_master_init's warm start, writes z and pi of the final point, and
 // (cg != nullptr) the round's record.  K = 0: the pool size is read from
 // cg->K when the kernel runs.

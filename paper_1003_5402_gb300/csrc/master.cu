@@ -1449,13 +1449,27 @@ size_t master_persist_smem(int V, int G) {
 }
 
 // Co-resident blocks of the persistent solve: 2 per SM when they fit, else 1;
-// 0 when a cooperative launch is not possible.
-int master_persist_grid(int V, int num_sms) {
+// 0 when a cooperative launch is not possible.  want > 0: that many blocks, or
+// the least number whose per-block working set fits the shared memory, if
+// more (at most the full count).
+int master_persist_grid(int V, int num_sms, int want) {
     int dev = 0, coop = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
         cudaGetLastError();
         return 0;
+    }
+    if (want > 0) {
+        int occ = 0;
+        for (int G = want; G <= 2 * num_sms; ++G) {
+            const size_t smem = master_persist_smem(V, G);
+            if (smem > PERSIST_SMEM_MAX) continue;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_master_persist, PT, smem) != cudaSuccess) {
+                cudaGetLastError();
+                return 0;
+            }
+            if (occ >= 1 && G <= occ * num_sms) return G;
+        }
     }
     for (int per = 2; per >= 1; --per) {
         const int G = per * num_sms;
