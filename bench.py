@@ -394,15 +394,16 @@ def serve_pool(n_each):
         return pool.map(_make_case_spec, specs)
 
 
-def run_serve(dev, pool, n_requests, apertures, rate_per_s=4.0, seed=9000):
+def run_serve(dev, pool, n_requests, apertures, rate_per_s=4.0, seed=9000, **plan_opt):
     """Poisson arrivals (rate 4 per second, seeded exponential gaps) of re-plan
     requests drawn from the pool; each request uploads its D and plans
-    ``apertures`` apertures.  Latency is submission to results on the host."""
+    ``apertures`` apertures.  Latency is submission to results on the host.
+    ``plan_opt``: dao_options of every plan (storage precision, master blocks)."""
     from paper_1003_5402_gb300 import Server
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate_per_s, size=n_requests)
     which = rng.integers(0, len(pool), size=n_requests)
-    with Server(max_slots=8, device=dev) as srv:
+    with Server(max_slots=8, device=dev, **plan_opt) as srv:
         # warm-up, as a long-running server is: one request of each size at
         # once, so that the library's memory pool already holds two concurrent
         # plans of the larger size (its one-time growth, tens of ms, is not a
@@ -425,9 +426,13 @@ def run_serve(dev, pool, n_requests, apertures, rate_per_s=4.0, seed=9000):
     lat = np.array([r["latency_ms"] for r in res])
     qms = np.array([r["queue_ms"] for r in res])
     ok = sum(r["status"] in (0, 1, 2) for r in res)
+    phases = {k: {"p50": round(float(np.percentile([r[k] for r in res], 50)), 3),
+                  "p99": round(float(np.percentile([r[k] for r in res], 99)), 3)}
+              for k in ("queue_ms", "create_ms", "solve_ms", "finish_ms")}
     return {"requests": n_requests, "rate_per_s": rate_per_s, "completed_ok": int(ok),
+            "plan_options": {k: v for k, v in plan_opt.items()},
             "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-            "max_ms": round(float(np.max(lat)), 3),
+            "max_ms": round(float(np.max(lat)), 3), "phases": phases,
             "queue_p99_ms": round(float(np.percentile(qms, 99)), 3), "max_active": st["max_active"],
             "plans_per_s": round(ok / makespan, 3), "makespan_s": round(makespan, 3),
             "workload": f"{len(pool) // 2} perturbed 19,200-voxel + {len(pool) // 2} perturbed prostate-shaped "

@@ -487,6 +487,9 @@ typedef struct {
     double queue_ms;       /* submission to admission */
     double run_ms;         /* admission to results in the output buffers */
     double latency_ms;     /* submission to results */
+    double create_ms;      /* of run_ms: the plan's context created (upload, checks, device build) */
+    double solve_ms;       /* of run_ms: rounds queued until the worker saw them complete */
+    double finish_ms;      /* of run_ms: results copied out and the context released */
     char error[256];       /* message of a failed request */
 } dao_result;
 

@@ -87,6 +87,7 @@ class dao_request(C.Structure):
 class dao_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("n_apertures", C.c_int32), ("objective", C.c_double),
                 ("queue_ms", C.c_double), ("run_ms", C.c_double), ("latency_ms", C.c_double),
+                ("create_ms", C.c_double), ("solve_ms", C.c_double), ("finish_ms", C.c_double),
                 ("error", C.c_char * 256)]
 
 
@@ -617,7 +618,8 @@ class Server:
     def _result(self, rid, r):
         req, keep, out = self._live.pop(rid)
         res = {"status": r.status, "n_apertures": r.n_apertures, "objective": r.objective, "queue_ms": r.queue_ms,
-               "run_ms": r.run_ms, "latency_ms": r.latency_ms, "error": r.error.decode(errors="replace")}
+               "run_ms": r.run_ms, "latency_ms": r.latency_ms, "create_ms": r.create_ms, "solve_ms": r.solve_ms,
+               "finish_ms": r.finish_ms, "error": r.error.decode(errors="replace")}
         if out:
             k = max(r.n_apertures, 0)
             res.update(dose=out["dose"], y=out["y"][:k].copy(), beams=out["beams"][:k].copy(),

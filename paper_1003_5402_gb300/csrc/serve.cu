@@ -48,6 +48,7 @@ struct Slot {
     dao_ctx* ctx = nullptr;
     cudaEvent_t done = nullptr;
     Clock::time_point sim_end;
+    Clock::time_point t_queued;  // the plan's rounds were queued
 };
 
 void set_msg(dao_result* r, const char* msg) {
@@ -94,8 +95,10 @@ struct dao_server {
         po.stream = nullptr;  // the context makes its own stream
         po.device = opt.device;
         po.use_graphs = 1;
+        const Clock::time_point t0 = Clock::now();
         dao_status st = dao_create(&q.r.D, &q.r.geometry, &q.r.structures, &q.r.weights, q.r.prescriptions, &po,
                                    &s.ctx);
+        q.res.create_ms = ms_since(t0, Clock::now());
         if (st == DAO_OK) {
             if (!s.done && cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
                 cudaGetLastError();
@@ -103,6 +106,7 @@ struct dao_server {
             }
         }
         if (st == DAO_OK) st = dao::solve_async_begin(s.ctx, q.r.n_apertures, s.done);
+        s.t_queued = Clock::now();
         if (st != DAO_OK) {
             q.res.status = st;
             set_msg(&q.res, dao_last_error());
@@ -130,6 +134,8 @@ struct dao_server {
             return;
         }
         if (s.ctx == nullptr) return;  // q.res already holds the error
+        const Clock::time_point t0 = Clock::now();
+        q.res.solve_ms = ms_since(s.t_queued, t0);
         dao_status result = DAO_OK;
         int32_t n = 0;
         dao_status st = dao::solve_async_end(s.ctx, q.r.n_apertures, &n, &result);
@@ -149,6 +155,7 @@ struct dao_server {
         q.res.objective = F;
         dao_destroy(s.ctx);
         s.ctx = nullptr;
+        q.res.finish_ms = ms_since(t0, Clock::now());
     }
 
     void run() {
