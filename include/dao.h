@@ -461,6 +461,10 @@ typedef struct {
     int32_t device;
     double simulate_ms_per_aperture;
     dao_options plan_options;      /* options of every plan; stream and device are ignored */
+    int64_t prewarm_bytes;         /* device memory taken into the library's memory pool, and page-locked
+                                      staging blocks for max_slots + 2 plans, when the server starts, so that
+                                      admitted plans do not wait for the pool to grow or for host pages to be
+                                      locked (default 2 GiB; 0: none) */
 } dao_server_options;
 void dao_server_options_default(dao_server_options* opt);
 

@@ -63,7 +63,7 @@ class dao_tuning(C.Structure):
 class dao_server_options(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("queue_capacity", C.c_int32), ("hbm_reserve_bytes", C.c_int64),
                 ("hbm_budget_bytes", C.c_int64), ("device", C.c_int32), ("simulate_ms_per_aperture", C.c_double),
-                ("plan_options", dao_options)]
+                ("plan_options", dao_options), ("prewarm_bytes", C.c_int64)]
 
 
 class dao_voxel_terms(C.Structure):
@@ -573,13 +573,16 @@ class Server:
     map to the dao_options of every plan."""
 
     def __init__(self, max_slots: int = 8, queue_capacity: int = 1024, hbm_reserve_bytes: int = 2 << 30,
-                 hbm_budget_bytes: int = 0, device: int = 0, simulate_ms_per_aperture: float = 0.0, **plan_opt):
+                 hbm_budget_bytes: int = 0, device: int = 0, simulate_ms_per_aperture: float = 0.0,
+                 prewarm_bytes: Optional[int] = None, **plan_opt):
         lib = load()
         o = dao_server_options()
         lib.dao_server_options_default(C.byref(o))
         o.max_slots, o.queue_capacity = int(max_slots), int(queue_capacity)
         o.hbm_reserve_bytes, o.hbm_budget_bytes = int(hbm_reserve_bytes), int(hbm_budget_bytes)
         o.device, o.simulate_ms_per_aperture = int(device), float(simulate_ms_per_aperture)
+        if prewarm_bytes is not None:
+            o.prewarm_bytes = int(prewarm_bytes)
         o.plan_options = options(**plan_opt)
         self.k_max = o.plan_options.k_max
         h = C.c_void_p()

@@ -478,17 +478,18 @@ __device__ __forceinline__ T lane_sum_strided(const T* __restrict__ src, int n, 
     return s;
 }
 
+// The partial arrays hold GC columns (the blocks that wrote them) at stride GH.
 __device__ __forceinline__ void master_reduce_part(const float* __restrict__ H_part,
                                                    const double* __restrict__ g_part,
                                                    const float* __restrict__ gn_part,
-                                                   const double* __restrict__ F_part, int GH, int GE, int K,
+                                                   const double* __restrict__ F_part, int GH, int GC, int GE, int K,
                                                    MasterDev* __restrict__ st) {
     const int E = K * (K + 1) / 2;
     const int lane = threadIdx.x & 31;
     const int n_out = E + 2 * K + 1;
     for (int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < n_out; o += (gridDim.x * blockDim.x) >> 5) {
         if (o < E) {  // the factorisation is FP32: so is this sum
-            float s = lane_sum_strided(H_part + (size_t)o * GH, GH, lane);
+            float s = lane_sum_strided(H_part + (size_t)o * GH, GC, lane);
             s = warp_sum_f32(s);
             if (lane == 0) {
                 int r = 0, rem = o;
@@ -502,12 +503,12 @@ __device__ __forceinline__ void master_reduce_part(const float* __restrict__ H_p
             }
         } else if (o < E + K) {
             const int k = o - E;
-            double s = lane_sum_strided(g_part + (size_t)k * GH, GH, lane);
+            double s = lane_sum_strided(g_part + (size_t)k * GH, GC, lane);
             s = warp_sum_f64(s);
             if (lane == 0) st->gt[k] = s;
         } else if (o < E + 2 * K) {
             const int k = o - E - K;
-            float s = lane_sum_strided(gn_part + (size_t)k * GH, GH, lane);
+            float s = lane_sum_strided(gn_part + (size_t)k * GH, GC, lane);
             s = warp_sum_f32(s);
             if (lane == 0) st->gn[k] = s;
         } else {
@@ -914,7 +915,7 @@ __global__ void __launch_bounds__(STEP_T, 1) k_master_reduce_step(const float* _
         if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
         return;
     }
-    master_reduce_part(H_part, g_part, gn_part, F_part, GH, GE, st->K, st);
+    master_reduce_part(H_part, g_part, gn_part, F_part, GH, GH, GE, st->K, st);
     __syncthreads();
     if (threadIdx.x == 0) s_last = atom_add_acq_rel_gpu(&st->ticket, 1u) == gridDim.x - 1;
     __syncthreads();
@@ -1259,7 +1260,7 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
             break;
         }
         // ---- B. reduction by every block, the step by the last one to finish
-        master_reduce_part(H_part, g_part, gn_part, F_part, GS, G, K, st);
+        master_reduce_part(H_part, g_part, gn_part, F_part, GS, G, G, K, st);
         __syncthreads();
         if (tid == 0) s_last = atom_add_acq_rel_gpu(&st->ticket, 1u) == (unsigned)G - 1u;
         __syncthreads();

@@ -251,6 +251,7 @@ void dao_server_options_default(dao_server_options* opt) {
     opt->device = 0;
     opt->simulate_ms_per_aperture = 0.0;
     dao_options_default(&opt->plan_options);
+    opt->prewarm_bytes = (int64_t)2 << 30;
 }
 
 int64_t dao_server_footprint(const dao_request* req, const dao_options* plan_options) {
@@ -279,7 +280,7 @@ dao_status dao_server_create(const dao_server_options* opt_in, dao_server** out)
     dao_server_options_default(&opt);
     if (opt_in) opt = *opt_in;
     if (opt.max_slots < 1 || opt.queue_capacity < 1 || opt.hbm_reserve_bytes < 0 || opt.hbm_budget_bytes < 0 ||
-        !(opt.simulate_ms_per_aperture >= 0.0))
+        !(opt.simulate_ms_per_aperture >= 0.0) || opt.prewarm_bytes < 0)
         return dao::set_error(DAO_EINVAL, "max_slots, queue_capacity >= 1; reserve, budget, simulation time >= 0");
     const bool simulate = opt.simulate_ms_per_aperture > 0.0;
     if (simulate && opt.hbm_budget_bytes <= 0)
@@ -293,6 +294,30 @@ dao_status dao_server_create(const dao_server_options* opt_in, dao_server** out)
             return dao::set_error(DAO_ECUDA, std::string("dao_server_create: ") + cudaGetErrorString(e));
         const int64_t dev_cap = (int64_t)total_b - opt.hbm_reserve_bytes;
         capacity = opt.hbm_budget_bytes > 0 ? std::min<int64_t>(opt.hbm_budget_bytes, dev_cap) : dev_cap;
+        if (opt.prewarm_bytes > 0) {
+            // the pool keeps freed memory mapped (up to its release threshold), and the
+            // staging free list keeps page-locked blocks: both taken once, here
+            cudaStream_t st = nullptr;
+            void* p = nullptr;
+            e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+            const size_t want = (size_t)std::min<int64_t>(opt.prewarm_bytes, std::max<int64_t>(capacity / 2, 0));
+            if (e == cudaSuccess && want > 0 && dao::pool_alloc(&p, want, opt.device, st) == cudaSuccess)
+                dao::pool_free(p, st);
+            if (e == cudaSuccess) cudaStreamSynchronize(st);
+            if (st) cudaStreamDestroy(st);
+            cudaGetLastError();  // prewarming is best effort
+            std::vector<std::pair<void*, size_t>> blocks;
+            for (int i = 0; i < opt.max_slots + 2; ++i) {
+                void* h = nullptr;
+                size_t b = (size_t)64 << 10;
+                if (dao::pinned_alloc(&h, &b) != cudaSuccess) {
+                    cudaGetLastError();
+                    break;
+                }
+                blocks.emplace_back(h, b);
+            }
+            for (auto& hb : blocks) dao::pinned_release(hb.first, hb.second);
+        }
     }
     dao_server* s = new (std::nothrow) dao_server();
     if (!s) return dao::set_error(DAO_ENOMEM, "host allocation failed");

@@ -315,3 +315,12 @@ def test_graph_solve_in_chunks_and_after_host_rounds(torch):
     assert len(aps) == 12
     assert all(x[0] == y_[0] and np.array_equal(x[1], y_[1]) for x, y_ in zip(aps, aps_all))
     assert np.array_equal(np.concatenate([t1, t2]), t_all[1:])
+
+
+@pytest.mark.parametrize("blocks", [19, 76])
+def test_persistent_master_on_part_of_the_gpu(torch, blocks):
+    """The persistent master solve on fewer blocks than the GPU holds
+    (master_blocks): every round within the oracle's bars, free-running."""
+    case = P.make_case(P.spec_tiny())
+    r = _free_running_checked(case, 20, torch, plan_kw={"master_blocks": blocks})
+    assert r["ties"] <= 2
