@@ -1,14 +1,15 @@
 // Re-plan serving with continuous batching on one GPU.
 //
-// One worker thread owns the GPU side.  It admits queued requests in arrival
-// order while a slot is free and the request's device footprint fits, gives
-// each admitted request its own context (and so its own stream), queues all of
-// the request's column-generation rounds as CUDA graphs at once and records an
-// event after them.  Plans run concurrently, each on its own stream; the worker
-// retires a plan when its event has completed (results into the request's
-// buffers, context destroyed) and admits the next request at once, so a new
-// request never waits for the other running plans to finish.  Submitters and
-// pollers only touch the queue and the result table under the mutex.
+// A dispatcher thread admits queued requests in arrival order while a slot is
+// free and the request's device footprint fits.  Every slot has a host thread
+// of its own: it gives its request a context (and so its own stream), queues
+// all of the request's column-generation rounds as CUDA graphs at once, waits
+// for the event recorded after them, copies the results into the request's
+// buffers and releases the context.  Plans run concurrently, each on its own
+// stream, and a plan's host work (upload, device build, read-back) never waits
+// behind another plan's: a request's latency is its own work plus its share of
+// the GPU.  Submitters and pollers only touch the queue and the result table
+// under the mutex.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -43,12 +44,15 @@ struct Request {
 };
 
 struct Slot {
-    bool busy = false;
+    bool busy = false;           // a request is assigned and not yet retired
+    bool pending = false;        // assigned, not yet picked up by the slot's thread
     int64_t id = -1;
     dao_ctx* ctx = nullptr;
     cudaEvent_t done = nullptr;
     Clock::time_point sim_end;
     Clock::time_point t_queued;  // the plan's rounds were queued
+    std::condition_variable cv;  // a request was assigned, or the server stops
+    std::thread th;
 };
 
 void set_msg(dao_result* r, const char* msg) {
@@ -67,6 +71,7 @@ struct dao_server {
     std::deque<int64_t> queue;
     std::unordered_map<int64_t, Request> reqs;
     std::vector<Slot> slots;
+    bool stop_slots = false;  // the slot threads leave once idle
     int64_t next_id = 1;
     bool stop = false;
     int64_t bytes_in_use = 0;
@@ -84,7 +89,7 @@ struct dao_server {
         return (int64_t)free_b - opt.hbm_reserve_bytes >= fp;
     }
 
-    // Runs on the worker without the lock: create the plan and queue its rounds.
+    // Slot thread, without the lock: create the plan and queue its rounds.
     void start(Slot& s, Request& q) {
         if (simulate) {
             s.sim_end = Clock::now() + std::chrono::microseconds(
@@ -115,17 +120,19 @@ struct dao_server {
         }
     }
 
-    bool finished(Slot& s, const Request& q) {
-        if (simulate) return Clock::now() >= s.sim_end;
-        if (s.ctx == nullptr) return true;  // failed at start
-        const cudaError_t e = cudaEventQuery(s.done);
-        if (e == cudaErrorNotReady) return false;
-        if (e != cudaSuccess) cudaGetLastError();  // surfaced by the read-back below
-        (void)q;
-        return true;
+    // Slot thread, without the lock: until the plan's event has completed.
+    void wait_plan(Slot& s) {
+        if (simulate) {
+            std::this_thread::sleep_until(s.sim_end);
+            return;
+        }
+        if (s.ctx == nullptr) return;  // failed at start
+        cudaError_t e;
+        while ((e = cudaEventQuery(s.done)) == cudaErrorNotReady) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        if (e != cudaSuccess) cudaGetLastError();  // surfaced by the read-back in finish
     }
 
-    // Runs on the worker without the lock: results into the caller's buffers.
+    // Slot thread, without the lock: results into the caller's buffers.
     void finish(Slot& s, Request& q) {
         if (simulate) {
             q.res.status = DAO_OK;
@@ -158,35 +165,41 @@ struct dao_server {
         q.res.finish_ms = ms_since(t0, Clock::now());
     }
 
+    // One slot's host thread: start, wait, finish and retire each request the
+    // dispatcher assigns to it.
+    void slot_main(Slot& s) {
+        if (!simulate) cudaSetDevice(opt.device);
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            s.cv.wait(lk, [&] { return s.pending || stop_slots; });
+            if (!s.pending) break;  // stopping, idle
+            s.pending = false;
+            Request& q = reqs[s.id];
+            lk.unlock();
+            start(s, q);
+            wait_plan(s);
+            finish(s, q);
+            lk.lock();
+            q.state = REQ_DONE;
+            q.t_done = Clock::now();
+            q.res.run_ms = ms_since(q.t_admit, q.t_done);
+            q.res.latency_ms = ms_since(q.t_submit, q.t_done);
+            const bool ok = q.res.status == DAO_OK || q.res.status == DAO_OPTIMAL || q.res.status == DAO_DUPLICATE;
+            if (ok) ++stats.completed; else ++stats.failed;
+            bytes_in_use -= q.footprint;
+            s.busy = false;
+            s.id = -1;
+            --stats.active;
+            cv_done.notify_all();
+            cv_work.notify_all();  // a slot and memory are free again
+        }
+    }
+
+    // The dispatcher: admission in arrival order.
     void run() {
         if (!simulate) cudaSetDevice(opt.device);
         std::unique_lock<std::mutex> lk(mu);
         for (;;) {
-            bool progressed = false;
-            // retire finished plans
-            for (Slot& s : slots) {
-                if (!s.busy) continue;
-                Request& q = reqs[s.id];
-                lk.unlock();
-                const bool fin = finished(s, q);
-                if (fin) finish(s, q);
-                lk.lock();
-                if (!fin) continue;
-                q.state = REQ_DONE;
-                q.t_done = Clock::now();
-                q.res.run_ms = ms_since(q.t_admit, q.t_done);
-                q.res.latency_ms = ms_since(q.t_submit, q.t_done);
-                const bool ok = q.res.status == DAO_OK || q.res.status == DAO_OPTIMAL ||
-                                q.res.status == DAO_DUPLICATE;
-                if (ok) ++stats.completed; else ++stats.failed;
-                bytes_in_use -= q.footprint;
-                s.busy = false;
-                s.id = -1;
-                --stats.active;
-                progressed = true;
-                cv_done.notify_all();
-            }
-            // admit in arrival order while a slot is free and the head fits
             while (!queue.empty() && !stop) {
                 Slot* free_slot = nullptr;
                 for (Slot& s : slots)
@@ -206,7 +219,6 @@ struct dao_server {
                                      " bytes exceeds what the server can ever admit").c_str());
                     q.res.queue_ms = q.res.latency_ms = ms_since(q.t_submit, q.t_done);
                     ++stats.rejected;
-                    progressed = true;
                     cv_done.notify_all();
                     continue;
                 }
@@ -216,26 +228,22 @@ struct dao_server {
                 q.t_admit = Clock::now();
                 q.res.queue_ms = ms_since(q.t_submit, q.t_admit);
                 free_slot->busy = true;
+                free_slot->pending = true;
                 free_slot->id = id;
                 bytes_in_use += q.footprint;
                 ++stats.active;
                 if (stats.active > stats.max_active) stats.max_active = stats.active;
-                lk.unlock();
-                start(*free_slot, q);
-                lk.lock();
-                progressed = true;
+                free_slot->cv.notify_one();
             }
             stats.queued = (int32_t)queue.size();
             stats.bytes_in_use = bytes_in_use;
             if (stop && stats.active == 0 && queue.empty()) break;
-            if (!progressed) {
-                // plans running: poll their events soon; idle: sleep until work arrives
-                if (stats.active > 0)
-                    cv_work.wait_for(lk, std::chrono::microseconds(100));
-                else
-                    cv_work.wait_for(lk, std::chrono::milliseconds(50));
-            }
+            // woken by a submission, a retired plan or shutdown; the timeout
+            // re-reads the free device memory while requests wait for it
+            cv_work.wait_for(lk, std::chrono::milliseconds(queue.empty() ? 50 : 1));
         }
+        stop_slots = true;
+        for (Slot& s : slots) s.cv.notify_all();
     }
 };
 
@@ -324,7 +332,8 @@ dao_status dao_server_create(const dao_server_options* opt_in, dao_server** out)
     s->opt = opt;
     s->simulate = simulate;
     s->capacity = capacity;
-    s->slots.resize(opt.max_slots);
+    s->slots = std::vector<Slot>(opt.max_slots);
+    for (Slot& sl : s->slots) sl.th = std::thread([s, &sl] { s->slot_main(sl); });
     s->worker = std::thread([s] { s->run(); });
     *out = s;
     return DAO_OK;
@@ -423,7 +432,9 @@ void dao_server_destroy(dao_server* s) {
         s->cv_work.notify_all();
         s->cv_done.notify_all();
     }
-    if (s->worker.joinable()) s->worker.join();  // the worker drains the running plans first
+    if (s->worker.joinable()) s->worker.join();  // the dispatcher waits for the running plans first
+    for (Slot& sl : s->slots)
+        if (sl.th.joinable()) sl.th.join();
     for (Slot& sl : s->slots) {
         if (sl.ctx) dao_destroy(sl.ctx);
         if (sl.done) cudaEventDestroy(sl.done);

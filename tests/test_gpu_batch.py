@@ -140,3 +140,36 @@ def test_autotune_choice_cache_and_parity(torch, tmp_path, prec):
     lines = open(cache).read().splitlines()
     assert len(lines) == 1 and lines[0].split()[1:] == [str(t1["dose_lanes"]), str(t1["column_lanes"]),
                                                        str(t1["dt_threads"])]
+
+
+def test_batch_of_full_size_instances_against_the_oracle(torch):
+    """Batched re-plans of the benchmark's sizes (a perturbed prostate-shaped
+    instance in FP32, a perturbed H&N-shaped instance in FP16 storage, the
+    small box) against the oracle: each instance alone passes the every-round
+    oracle check of the free-running path, and the batch's result is bitwise
+    that plan."""
+    from paper_1003_5402_gb300 import Plan, binding
+    from _helpers import quantized_case
+    from test_gpu_cg import _free_running_checked
+    K = 50
+    inst = [(P.make_case(P.perturb(P.spec_prostate(), 4001)), {"precision": 0}),
+            (P.make_case(P.perturb(P.spec_hn(), 4017)), {"precision": 1}),
+            (P.make_case(P.spec_tiny()), {"precision": 0})]
+    checked = []
+    for case, kw in inst:
+        ref_case = case if kw["precision"] == 0 else quantized_case(case, "fp16")
+        checked.append(_free_running_checked(case, K, torch, plan_kw=kw, ref_case=ref_case))
+    plans = [Plan(c, **kw) for c, kw in inst]
+    try:
+        res = binding.batch_solve(plans, K)
+        for p, r, ref in zip(plans, res, checked):
+            st, n, trace = r
+            assert n == K
+            aps = p.apertures()
+            assert all(x[0] == y[0] and np.array_equal(x[1], y[1]) for x, y in zip(aps, ref["apertures"]))
+            assert np.array_equal(p.intensities(), ref["y"])
+            z, F = p.dose()
+            assert np.array_equal(z, ref["z"]) and F == ref["F"]
+    finally:
+        for p in plans:
+            p.close()

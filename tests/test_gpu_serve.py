@@ -50,6 +50,29 @@ def test_server_results_equal_plans_alone(torch):
     assert stats["completed"] == len(cases) and stats["failed"] == 0 and stats["max_active"] >= 2
 
 
+def test_server_full_size_results_against_the_oracle(torch):
+    """Requests of the serving workload's sizes (a perturbed prostate-shaped
+    instance and the small box, FP16 storage, 50 apertures) through the
+    server, submitted together so that they run side by side: each result is
+    bitwise the plan that passes the every-round oracle check of the
+    free-running path."""
+    from paper_1003_5402_gb300 import Server
+    from _helpers import quantized_case
+    from test_gpu_cg import _free_running_checked
+    K = 50
+    cases = [P.make_case(P.perturb(P.spec_prostate(), 9011)), P.make_case(P.perturb(P.spec_tiny(), 9003))]
+    checked = [_free_running_checked(c, K, torch, plan_kw={"precision": 1}, ref_case=quantized_case(c, "fp16"))
+               for c in cases]
+    with Server(max_slots=4, precision=1) as s:
+        ids = [s.submit(c, K) for c in cases]
+        res = [s.wait(i, 120_000) for i in ids]
+    for r, ref in zip(res, checked):
+        assert r["status"] == 0 and r["n_apertures"] == K and r["error"] == ""
+        assert r["objective"] == ref["F"] and np.array_equal(r["dose"], ref["z"]) and np.array_equal(r["y"], ref["y"])
+        for k, (b, lv) in enumerate(ref["apertures"]):
+            assert r["beams"][k] == b and np.array_equal(r["leaves"][k][: len(lv)], lv)
+
+
 def test_footprint_bounds_the_device_memory_of_a_plan(torch):
     from paper_1003_5402_gb300 import Plan, Server, release_cached_memory
     case = P.make_case(P.spec_prostate())
