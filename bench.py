@@ -56,8 +56,10 @@ def _args():
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--skip-batch", action="store_true")
     p.add_argument("--skip-serve", action="store_true")
-    p.add_argument("--serve-requests", type=int, default=60,
-                   help="requests of the serving leg (600 for the full Poisson workload)")
+    p.add_argument("--serve-requests", type=int, default=600,
+                   help="requests of the serving leg's Poisson stream (4 per second)")
+    p.add_argument("--serve-burst", type=int, default=64,
+                   help="requests of the serving leg's burst (200 per second: the server under load)")
     p.add_argument("--batch", type=int, default=16, help="instances per workload in the batched re-plan leg")
     a = p.parse_args()
     if a.precision is None:
@@ -675,7 +677,13 @@ def run_ours(a):
         batch = run_batch(torch, dev, flush, batch_cases, a.batch, a.apertures)
     serve = None
     if serve_cases is not None:
-        serve = run_serve(dev, serve_cases, a.serve_requests, a.apertures)
+        # FP16 storage (the mixed-precision form), every request its own plan
+        serve = run_serve(dev, serve_cases, a.serve_requests, a.apertures, precision=PREC["fp16"])
+        if a.serve_burst > 0:
+            burst = run_serve(dev, serve_cases, a.serve_burst, a.apertures, rate_per_s=200.0, seed=9100,
+                              precision=PREC["fp16"])
+            serve["burst"] = {k: burst[k] for k in ("requests", "rate_per_s", "completed_ok", "p50_ms", "p99_ms",
+                                                    "max_ms", "max_active", "plans_per_s", "phases")}
 
     cpu = None
     if rank == 0 and ws == 1 and not a.skip_cpu:
