@@ -431,7 +431,8 @@ def run_serve(dev, pool, n_requests, apertures, rate_per_s=4.0, seed=9000, **pla
     phases = {k: {"p50": round(float(np.percentile([r[k] for r in res], 50)), 3),
                   "p99": round(float(np.percentile([r[k] for r in res], 99)), 3)}
               for k in ("queue_ms", "create_ms", "solve_ms", "finish_ms")}
-    return {"requests": n_requests, "rate_per_s": rate_per_s, "completed_ok": int(ok),
+    errors = sorted({f'{r["status"]}: {r["error"]}' for r in res if r["status"] not in (0, 1, 2)})
+    return {"requests": n_requests, "rate_per_s": rate_per_s, "completed_ok": int(ok), "errors": errors[:4],
             "plan_options": {k: v for k, v in plan_opt.items()},
             "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
             "max_ms": round(float(np.max(lat)), 3), "phases": phases,
@@ -682,7 +683,7 @@ def run_ours(a):
         if a.serve_burst > 0:
             burst = run_serve(dev, serve_cases, a.serve_burst, a.apertures, rate_per_s=200.0, seed=9100,
                               precision=PREC["fp16"])
-            serve["burst"] = {k: burst[k] for k in ("requests", "rate_per_s", "completed_ok", "p50_ms", "p99_ms",
+            serve["burst"] = {k: burst[k] for k in ("requests", "rate_per_s", "completed_ok", "errors", "p50_ms", "p99_ms",
                                                     "max_ms", "max_active", "plans_per_s", "phases")}
 
     cpu = None

@@ -105,7 +105,11 @@ struct dao_server {
                                    &s.ctx);
         q.res.create_ms = ms_since(t0, Clock::now());
         if (st == DAO_OK) {
-            if (!s.done && cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
+            // blocking sync: the slot's thread sleeps in the driver while its plan runs
+            // instead of polling, which would contend for the driver with the other
+            // slots' host work
+            if (!s.done &&
+                cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming | cudaEventBlockingSync) != cudaSuccess) {
                 cudaGetLastError();
                 st = dao::set_error(DAO_ECUDA, "cudaEventCreate failed");
             }
@@ -127,9 +131,7 @@ struct dao_server {
             return;
         }
         if (s.ctx == nullptr) return;  // failed at start
-        cudaError_t e;
-        while ((e = cudaEventQuery(s.done)) == cudaErrorNotReady) std::this_thread::sleep_for(std::chrono::microseconds(20));
-        if (e != cudaSuccess) cudaGetLastError();  // surfaced by the read-back in finish
+        if (cudaEventSynchronize(s.done) != cudaSuccess) cudaGetLastError();  // surfaced by the read-back
     }
 
     // Slot thread, without the lock: results into the caller's buffers.
