@@ -399,7 +399,10 @@ cudaError_t build_stats(const int64_t* rp, const int* col, const float* val, int
                         int* C, int* cnt, unsigned* smax, unsigned* dmax, int num_sms, cudaStream_t s) {
     const int n_tile = (N + TILE_N - 1) / TILE_N;
     const size_t sm_stats = 2 * sizeof(unsigned) * (size_t)std::min(N, TILE_N);
-    cudaError_t e = cudaFuncSetAttribute(k_chunk_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stats);
+    // the attribute is process-wide and plans may be created from several threads at
+    // once: always the largest size any launch asks for, never this plan's own
+    cudaError_t e = cudaFuncSetAttribute(k_chunk_stats, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * sizeof(unsigned) * TILE_N));
     if (e == cudaSuccess) e = cudaMemsetAsync(smax, 0, sizeof(unsigned) * N, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(dmax, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
@@ -434,7 +437,9 @@ cudaError_t build_transpose_place(int prec, const int64_t* rp, const int* col, c
     const int tw = std::min(TILE_N, (N + split - 1) / split);
     const int n_tile = (N + tw - 1) / tw;
     const size_t sm_place = place_smem(tw);
-    cudaError_t e = cudaFuncSetAttribute(k_chunk_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_place);
+    // process-wide: the largest size any launch asks for (see build_stats)
+    cudaError_t e = cudaFuncSetAttribute(k_chunk_place, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)place_smem(TILE_N));
     if (e != cudaSuccess) return e;
     k_chunk_place<<<dim3(n_ch, n_tile), 32, sm_place, s>>>(rp, col, val, V, CH, N, tw, C, Dt.rowptr, Dt.col, tval);
     k_pad_t<<<blocks_for((int64_t)N * 32, 256), 256, 0, s>>>(Dt.rowptr, cnt, N, Dt.col, tval);

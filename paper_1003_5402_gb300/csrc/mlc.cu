@@ -272,6 +272,11 @@ size_t mlc_smem_bytes(int mode, int max_rows, int max_cols) {
 }
 
 cudaError_t mlc_configure(int mode, size_t smem) {
+    // the attribute is process-wide and plans may be created from several threads
+    // at once: the largest size of any plan (64 rows of 32 beamlets), never this
+    // plan's own, which another thread's smaller plan could otherwise lower
+    if (smem > mlc_smem_bytes(mode, 64, 32)) return cudaErrorInvalidValue;
+    smem = mlc_smem_bytes(mode, 64, 32);
     switch (mode) {
         case DAO_MLC_INTERDIGITATION:
             return cudaFuncSetAttribute(k_price_mlc<DAO_MLC_INTERDIGITATION>,

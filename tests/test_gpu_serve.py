@@ -102,3 +102,38 @@ def test_budget_of_one_footprint_runs_plans_one_at_a_time(torch):
         ids = [s.submit(c, 6) for c in cases]
         assert all(s.wait(i, 120_000)["status"] in (0, 1, 2) for i in ids)
         assert s.stats()["max_active"] == 1
+
+
+def test_plans_created_from_several_threads_at_once(torch):
+    """Plans of different sizes and storage created at the same time from
+    several host threads (as the server's slots do): every one succeeds and
+    plans the same as when created alone.  (Process-wide kernel attributes
+    must never be set to one plan's own size.)"""
+    import threading
+    from paper_1003_5402_gb300 import Plan, binding
+    cases = [(P.make_case(P.spec_micro()), {}), (P.make_case(P.spec_tiny()), {"precision": 1}),
+             (random_case(33, 2000, rows=[4, 6], cols=[9, 30], mean_row=20.0), {}),
+             (P.make_case(P.spec_micro()), {"mlc_constraint": binding.DAO_MLC_INTERDIGITATION}),
+             (P.make_case(P.spec_tiny()), {"mlc_constraint": binding.DAO_MLC_JAWS})]
+    alone = []
+    for c, kw in cases:
+        with Plan(c, **kw) as p:
+            alone.append(p.solve(6)[2])
+    out = [None] * (3 * len(cases))
+    errs = []
+
+    def work(i):
+        try:
+            c, kw = cases[i % len(cases)]
+            with Plan(c, **kw) as p:
+                out[i] = p.solve(6)[2]
+        except Exception as e:  # noqa: BLE001 - reported below
+            errs.append(repr(e))
+    th = [threading.Thread(target=work, args=(i,)) for i in range(len(out))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs, errs
+    for i, tr in enumerate(out):
+        assert np.array_equal(tr, alone[i % len(cases)]), i
