@@ -336,12 +336,13 @@ def batch_instances(n_each):
 
 
 def run_batch(torch, dev, flush, cases, n_each, apertures):
-    """Batched re-plans: all instances through dao_batch_solve (each on its own
-    stream, rounds interleaved) against the same plans one after another; H&N
-    instances use FP16 storage.  Launch shapes come from the autotuner.  The
-    plans use the per-kernel master (master_persistent = 0): its small kernels
-    from many instances overlap on the GPU, while a persistent master solve
-    holds every SM and runs one instance at a time."""
+    """Batched re-plans in two forms, against the same plans one after another:
+      - per-stream: dao_batch_solve, each instance's rounds as its own CUDA
+        graphs on its own stream, master problems by the per-kernel path (its
+        small kernels from many instances overlap on the GPU);
+      - fused: dao_batch_solve_persistent, every round's master solves of all
+        instances in one cooperative launch, a group of blocks per instance.
+    H&N instances use FP16 storage; launch shapes come from the autotuner."""
     import tempfile
     from paper_1003_5402_gb300 import Plan, binding
     cache = os.path.join(tempfile.gettempdir(), "dao_autotune.txt")
@@ -352,32 +353,33 @@ def run_batch(torch, dev, flush, cases, n_each, apertures):
             p = Plan(c, device=dev, precision=prec, master_persistent=0)
             p.autotune(cache)
             plans.append(p)
-        binding.batch_solve(plans, apertures)                   # warm: builds every round graph
-        seq, bat = [], []
-        for _ in range(2):
-            for p in plans:
-                p.reset()
-            flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            res = binding.batch_solve(plans, apertures)
-            bat.append(time.perf_counter() - t0)
-            for p in plans:
-                p.reset()
-            flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for p in plans:
-                p.solve(apertures)
-            seq.append(time.perf_counter() - t0)
+
+        def timed(fn, reps=2):
+            best, res = float("inf"), None
+            for _ in range(reps):
+                for p in plans:
+                    p.reset()
+                flush.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                res = fn()
+                best = min(best, time.perf_counter() - t0)
+            return best, res
+        binding.batch_solve(plans, apertures)                    # warm: builds every round graph
+        t_stream, res_s = timed(lambda: binding.batch_solve(plans, apertures))
+        binding.batch_solve(plans, apertures, persistent=True)   # warm: captures the fused graph
+        t_fused, res_f = timed(lambda: binding.batch_solve(plans, apertures, persistent=True))
+        t_seq, _ = timed(lambda: [p.solve(apertures) for p in plans])
         n = len(plans)
+        best = min(t_stream, t_fused)
         return {"instances": n, "workloads": f"{n_each} prostate-shaped FP32 + {n_each} H&N-shaped FP16, "
                                              f"perturbed (seeds 4000+i), {apertures} apertures each",
-                "master": "per-kernel graph path (master_persistent = 0), so the instances overlap",
-                "batched_s": round(min(bat), 4), "sequential_s": round(min(seq), 4),
-                "plans_per_s_batched": round(n / min(bat), 2), "plans_per_s_sequential": round(n / min(seq), 2),
-                "speedup": round(min(seq) / min(bat), 3),
-                "apertures_done": [r[1] for r in res],
+                "form": "fused" if t_fused <= t_stream else "per-stream",
+                "plans_per_s_batched": round(n / best, 2),
+                "plans_per_s_fused": round(n / t_fused, 2), "plans_per_s_per_stream": round(n / t_stream, 2),
+                "plans_per_s_sequential": round(n / t_seq, 2), "speedup": round(t_seq / best, 3),
+                "fused_blocks_per_plan": int(binding.load().dao_batch_group_size(n, dev)),
+                "apertures_done": sorted({r[1] for r in res_f} | {r[1] for r in res_s}),
                 "timing": "host wall clock around the synchronous calls, L2 flushed before each, best of 2"}
     finally:
         for p in plans:

@@ -413,6 +413,25 @@ dao_status dao_master_stats(const dao_ctx* ctx, int32_t* evals, int32_t* status,
 dao_status dao_batch_solve(dao_ctx* const* ctxs, int32_t n, int32_t n_apertures, int32_t* n_done, double* traces,
                            int32_t* status);
 
+/* Column generation for n independent contexts with one persistent master
+ * launch per round for all of them: the plans' master solves run side by side
+ * in one cooperative kernel, each on its own group of blocks (two blocks per SM
+ * shared out evenly; each group with its own grid barrier, solver state and
+ * stopping), while every plan's D^T kernel and beam decision with the new
+ * column run on its own stream before it.  The rounds are captured once into
+ * a CUDA graph for the list of contexts and the round count, kept for the
+ * next call with the same list (at most four such graphs; a graph goes with
+ * its contexts' dao_destroy).  Arguments and results as dao_batch_solve; a
+ * plan's results are those of solving it alone with a persistent master of
+ * the same group size.  DAO_EINVAL when two blocks per SM do not give every
+ * plan a block (n > 2 x SMs).  Synchronous. */
+dao_status dao_batch_solve_persistent(dao_ctx* const* ctxs, int32_t n, int32_t n_apertures, int32_t* n_done,
+                                      double* traces, int32_t* status);
+/* Blocks per plan of dao_batch_solve_persistent for n plans on device `device`
+ * (0 when n plans do not fit one launch): a plan created with this
+ * master_blocks solves alone exactly as it does in the batch. */
+int32_t dao_batch_group_size(int32_t n, int32_t device);
+
 /* ---- autotuner of the SpMV launch shapes ----
  * Times the dose SpMV (a1, lanes per voxel row: 4/8/16/32, 16-bit storage up to
  * 16), the transposed SpMV (a2, threads per beamlet row: 64/128/256) and the

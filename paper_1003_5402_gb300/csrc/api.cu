@@ -2,6 +2,9 @@
 // column-generation driver (Sec. 2.2-2.3 of arXiv:1003.5402, Fig. 1) and the
 // C ABI declared in include/dao.h.
 #include <algorithm>
+#include <atomic>
+#include <map>
+#include <mutex>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -54,6 +57,7 @@ struct ProfRecord {
 };
 
 struct dao_ctx {
+    uint64_t uid = 0;                // unique for the life of the process (batch graph cache key)
     int device = 0;
     int num_sms = 0;
     cudaStream_t stream = nullptr;
@@ -184,6 +188,9 @@ struct dao_ctx {
 };
 
 namespace {
+
+// Cached batch graphs that name a context are released with it (defined with the batch solve).
+void batch_graphs_forget(uint64_t uid);
 
 dao_status check_ctx(dao_ctx* c) {
     if (c == nullptr) return fail(DAO_EINVAL, "null context");
@@ -885,6 +892,7 @@ bool build_solve_graph_persist(dao_ctx* c) {
             ca.ld = c->ld;
             ca.cg = c->cg;
             ca.cond = h;
+            ca.use_cond = 1;
             for (int u = 0; u < ROUNDS_PER_ITER; ++u) {
                 check(launch_dt_rows(c->Dt, c->pi, c->w, rt, cs, &n));
                 if (mlc) check(price_rows_any(c, c->w, &c->cg->stop, cs, &n));
@@ -1009,6 +1017,10 @@ struct GraphSolve {
     int K0 = 0, K1 = 0;
 };
 
+// The device-side round state of a solve of rounds K0+1 .. K1 (copied on the
+// context's stream); the barrier counter of the persistent master zeroed.
+dao_status solve_state_begin(dao_ctx* c, const GraphSolve* gs);
+
 dao_status solve_graph_begin(dao_ctx* c, int n_apertures, GraphSolve* gs) {
     gs->K0 = c->K;
     gs->K1 = std::min(c->K_cap, c->K + n_apertures);
@@ -1019,6 +1031,10 @@ dao_status solve_graph_begin(dao_ctx* c, int n_apertures, GraphSolve* gs) {
     if (c->solve_exec == nullptr)
         for (int k = gs->K0 + 1; k <= gs->K1; ++k)
             if (c->round_exec[k] == nullptr) DAO_TRY(build_round_graph(c, k));
+    return solve_state_begin(c, gs);
+}
+
+dao_status solve_state_begin(dao_ctx* c, const GraphSolve* gs) {
     CGDev* h = reinterpret_cast<CGDev*>(c->pinned + c->off_cg);
     h->K = gs->K0;
     h->done = 0;
@@ -1028,7 +1044,7 @@ dao_status solve_graph_begin(dao_ctx* c, int n_apertures, GraphSolve* gs) {
     h->rs_K = gs->K0;
     h->rs_stop = 0;
     DAO_CU(cudaMemcpyAsync(c->cg, h, offsetof(CGDev, pad), cudaMemcpyHostToDevice, c->stream));
-    if (c->mb.GP > 0) DAO_CU(cudaMemsetAsync(c->mb.bar, 0, sizeof(GridBar), c->stream));  // barrier counter
+    DAO_CU(cudaMemsetAsync(c->mb.bar, 0, sizeof(GridBar), c->stream));  // barrier counter
     return DAO_OK;
 }
 
@@ -1045,7 +1061,7 @@ dao_status launch_round(dao_ctx* c, const GraphSolve& gs, int k) {
 }
 
 dao_status solve_graph_end(dao_ctx* c, const GraphSolve& gs, int n_apertures, int32_t* n_done, double* trace,
-                           dao_status* result) {
+                           dao_status* result, bool count = true) {
     const int K0 = gs.K0, K1 = gs.K1;
     CGDev* h = reinterpret_cast<CGDev*>(c->pinned + c->off_cg);
     GridBar* hb = reinterpret_cast<GridBar*>(c->pinned + c->off_bar);
@@ -1076,7 +1092,8 @@ dao_status solve_graph_end(dao_ctx* c, const GraphSolve& gs, int n_apertures, in
     // the persistent solve, or init, the final pass, the record and, per pair of
     // evaluations, pass, curvature and reduce + step
     const bool persist = c->mb.GP > 0;
-    if (c->solve_exec != nullptr) {
+    if (!count) {
+    } else if (c->solve_exec != nullptr) {
         // the while node ran the rounds that grew the pool and, when pricing
         // stopped the solve, the round that found it, ROUNDS_PER_ITER to an iteration
         const int rounds = K - K0 + (h->done != 0 ? 1 : 0);
@@ -1087,7 +1104,7 @@ dao_status solve_graph_end(dao_ctx* c, const GraphSolve& gs, int n_apertures, in
         c->launches_i += (persist ? 5 : 7) * (K1 - K0);
     }
     for (int k = K0; k < K; ++k) {
-        if (!persist) c->launches_i += 6 * ((h->evals[k] + 1) / 2);  // two evaluations per while iteration
+        if (!persist && count) c->launches_i += 6 * ((h->evals[k] + 1) / 2);  // two evaluations per while iteration
         c->stat_evals.push_back(h->evals[k]);
         c->stat_status.push_back(h->status[k]);
         c->stat_kkt.push_back(h->res[k] / (h->tol[k] > 0 ? h->tol[k] / c->opt.master_tol : 1.0));
@@ -1208,6 +1225,10 @@ dao_status create_common(const dao_csr* D, const dao_geometry* g, const dao_stru
     DAO_TRY(validate(D, g, s, w, prescriptions, &opt));
     dao_ctx* c = new (std::nothrow) dao_ctx();
     if (!c) return fail(DAO_ENOMEM, "host allocation failed");
+    {
+        static std::atomic<uint64_t> next_uid{1};
+        c->uid = next_uid++;
+    }
     c->opt = opt;
     c->device = opt.device;
     c->V = D->n_voxels;
@@ -1337,6 +1358,7 @@ dao_status dao_pencil_generate(const dao_pencil_beam* pb, int32_t device, int64_
 
 void dao_destroy(dao_ctx* c) {
     if (!c) return;
+    batch_graphs_forget(c->uid);
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     drop_round_graphs(c);
@@ -1955,6 +1977,238 @@ dao_status dao_batch_solve(dao_ctx* const* ctxs, int32_t n, int32_t n_apertures,
         DAO_TRY(solve_graph_end(ctxs[i], gs[i], n_apertures, n_done ? n_done + i : nullptr,
                                 traces ? traces + (size_t)i * n_apertures : nullptr, &res));
         ctxs[i]->count_launches();
+        if (status) status[i] = res;
+    }
+    return DAO_OK;
+}
+
+}  // extern "C"
+
+// ---- batched plans with one persistent master launch per round -----------------
+namespace {
+
+// An instantiated graph of R unrolled rounds over a fixed list of contexts:
+// per round every plan's D^T kernel (with its MLC-row search) and beam
+// decision with the new column on the plan's own stream, then all the plans'
+// master solves in one cooperative launch (GB blocks each).
+struct BatchGraph {
+    std::vector<uint64_t> key;  // the contexts' ids, then R
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    MasterTask* tasks = nullptr;  // device copies of the plans' master tasks
+    std::vector<cudaEvent_t> events;
+    int GB = 0;
+};
+std::mutex g_batch_mu;
+std::vector<BatchGraph*> g_batch_graphs;  // most recently used first
+constexpr size_t BATCH_GRAPHS_KEPT = 4;
+
+void batch_graph_free(BatchGraph* bg) {
+    cudaSetDevice(bg->device);
+    if (bg->stream) cudaStreamSynchronize(bg->stream);
+    if (bg->exec) cudaGraphExecDestroy(bg->exec);
+    if (bg->graph) cudaGraphDestroy(bg->graph);
+    if (bg->tasks) pool_free(bg->tasks, bg->stream);
+    for (cudaEvent_t e : bg->events) cudaEventDestroy(e);
+    if (bg->stream) {
+        cudaStreamSynchronize(bg->stream);
+        cudaStreamDestroy(bg->stream);
+    }
+    delete bg;
+}
+
+// Graphs that name a context are dropped with it.
+void batch_graphs_forget(uint64_t uid) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (size_t i = 0; i < g_batch_graphs.size();) {
+        BatchGraph* bg = g_batch_graphs[i];
+        if (std::find(bg->key.begin(), bg->key.end() - 1, uid) != bg->key.end() - 1) {
+            batch_graph_free(bg);
+            g_batch_graphs.erase(g_batch_graphs.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+dao_status build_batch_graph(dao_ctx* const* ctxs, int n, int R, BatchGraph* bg) {
+    dao_ctx* c0 = ctxs[0];
+    bg->device = c0->device;
+    bg->GB = master_batch_group(n, c0->num_sms);
+    if (bg->GB < 1) return fail(DAO_EINVAL, "too many plans for one persistent launch (two blocks per SM each)");
+    DAO_CU(cudaStreamCreateWithFlags(&bg->stream, cudaStreamNonBlocking));
+    std::vector<MasterTask> tasks(n);
+    int max_V = 0;
+    for (int i = 0; i < n; ++i) {
+        dao_ctx* c = ctxs[i];
+        MasterTask& t = tasks[i];
+        t = MasterTask{};
+        t.slab = c->slab;
+        t.ld = c->ld;
+        t.V = c->V;
+        t.GS = c->mb.GH;
+        t.S = c->S;
+        t.max_iter = c->opt.max_master_iters;
+        t.st = c->mb.st;
+        t.gb = c->mb.bar;
+        t.H_part = c->mb.H_part;
+        t.g_part = c->mb.g_part;
+        t.gn_part = c->mb.gn_part;
+        t.F_part = c->mb.F_part;
+        t.vstruct = c->vstruct;
+        t.tf = c->tf;
+        t.tol_rel = c->opt.master_tol;
+        t.skip = &c->cg->idle;
+        t.z_out = c->z;
+        t.pi_out = c->pi;
+        t.cg = c->cg;
+        t.capw = master_persist_capw(c->V, bg->GB);
+        max_V = std::max(max_V, c->V);
+    }
+    void* tp = nullptr;
+    DAO_CU(pool_alloc(&tp, sizeof(MasterTask) * n, bg->device, bg->stream));
+    bg->tasks = static_cast<MasterTask*>(tp);
+    DAO_CU(cudaMemcpyAsync(bg->tasks, tasks.data(), sizeof(MasterTask) * n, cudaMemcpyHostToDevice, bg->stream));
+    DAO_CU(cudaStreamSynchronize(bg->stream));
+    bg->events.assign(n + 1, nullptr);
+    for (auto& e : bg->events) DAO_CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaError_t e = cudaStreamBeginCapture(bg->stream, cudaStreamCaptureModeThreadLocal);
+    auto check = [&](cudaError_t x) {
+        if (e == cudaSuccess && x != cudaSuccess) e = x;
+    };
+    int nl = 0;
+    for (int r = 0; r < R && e == cudaSuccess; ++r) {
+        check(cudaEventRecord(bg->events[n], bg->stream));
+        for (int i = 0; i < n; ++i) {
+            dao_ctx* c = ctxs[i];
+            cudaStream_t cs = c->stream;
+            check(cudaStreamWaitEvent(cs, bg->events[n], 0));
+            const bool mlc = c->opt.mlc_constraint != DAO_MLC_CONSECUTIVE;
+            const RowTicket rt{c->binfo, c->beam_row0_d, c->cols_d, c->row_info, mlc ? nullptr : c->row_cnt,
+                               c->row_v, c->row_lr, c->cg};
+            check(launch_dt_rows(c->Dt, c->pi, c->w, rt, cs, &nl));
+            if (mlc) check(price_rows_any(c, c->w, &c->cg->stop, cs, &nl));
+            CommitArgs ca{};
+            ca.row_v = c->row_v;
+            ca.row_lr = c->row_lr;
+            ca.beam_row0 = c->beam_row0_d;
+            ca.rows = c->rows_d;
+            ca.cols = c->cols_d;
+            ca.beam_off = c->beam_off_d;
+            ca.seg = c->seg;
+            ca.n_beams = c->B;
+            ca.lr_stride = 2 * c->max_rows;
+            ca.tau = c->tau;
+            ca.ap_beam = c->ap_beam;
+            ca.ap_lr = c->ap_lr;
+            ca.slab = c->slab;
+            ca.ld = c->ld;
+            ca.cg = c->cg;
+            ca.use_cond = 0;
+            check(launch_commit_column(c->D, ca, c->max_nb, c->num_sms, cs, &nl));
+            check(cudaEventRecord(bg->events[i], cs));
+            check(cudaStreamWaitEvent(bg->stream, bg->events[i], 0));
+        }
+        check(launch_master_persist_batch(bg->tasks, n, bg->GB, max_V, bg->stream, &nl));
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(bg->stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&bg->exec, g, 0);
+    bg->graph = g;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DAO_ECUDA, std::string("building the batch graph: ") + cudaGetErrorString(e));
+    }
+    return DAO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t dao_batch_group_size(int32_t n, int32_t device) {
+    int sms = 0;
+    if (n < 1 || cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return master_batch_group(n, sms);
+}
+
+dao_status dao_batch_solve_persistent(dao_ctx* const* ctxs, int32_t n, int32_t n_apertures, int32_t* n_done,
+                                      double* traces, int32_t* status) {
+    TraceRange range("dao_batch_solve_persistent");
+    if (n < 0 || n_apertures < 0 || (n > 0 && ctxs == nullptr))
+        return fail(DAO_EINVAL, "n >= 0, n_apertures >= 0 and a context array are required");
+    for (int i = 0; i < n; ++i) {
+        if (ctxs[i] == nullptr) return fail(DAO_EINVAL, "null context " + std::to_string(i));
+        if (ctxs[i]->prof_on) return fail(DAO_EINVAL, "every context needs profiling off");
+        if (ctxs[i]->device != ctxs[0]->device) return fail(DAO_EINVAL, "the contexts must be on one device");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return fail(DAO_EINVAL, "context listed twice");
+    }
+    if (n == 0) return DAO_OK;
+    DAO_TRY(check_ctx(ctxs[0]));
+    std::vector<GraphSolve> gs(n);
+    int R = 0;
+    for (int i = 0; i < n; ++i) {
+        gs[i].K0 = ctxs[i]->K;
+        gs[i].K1 = std::min(ctxs[i]->K_cap, ctxs[i]->K + n_apertures);
+        R = std::max(R, gs[i].K1 - gs[i].K0);
+        if (status) status[i] = DAO_OK;
+        if (n_done) n_done[i] = ctxs[i]->K;
+    }
+    std::vector<uint64_t> key;
+    for (int i = 0; i < n; ++i) key.push_back(ctxs[i]->uid);
+    key.push_back((uint64_t)R);
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    BatchGraph* bg = nullptr;
+    for (size_t i = 0; i < g_batch_graphs.size(); ++i)
+        if (g_batch_graphs[i]->key == key) {
+            bg = g_batch_graphs[i];
+            g_batch_graphs.erase(g_batch_graphs.begin() + i);
+            break;
+        }
+    if (bg == nullptr && R > 0) {
+        bg = new (std::nothrow) BatchGraph();
+        if (!bg) return fail(DAO_ENOMEM, "host allocation failed");
+        bg->key = key;
+        const dao_status st = build_batch_graph(ctxs, n, R, bg);
+        if (st != DAO_OK) {
+            const std::string msg = g_err;
+            batch_graph_free(bg);
+            return fail(st, msg);
+        }
+    }
+    if (bg != nullptr) {
+        g_batch_graphs.insert(g_batch_graphs.begin(), bg);
+        while (g_batch_graphs.size() > BATCH_GRAPHS_KEPT) {
+            batch_graph_free(g_batch_graphs.back());
+            g_batch_graphs.pop_back();
+        }
+        // every plan's round state on its stream, then the graph after all of them,
+        // then every plan's stream after the graph
+        for (int i = 0; i < n; ++i) {
+            DAO_TRY(solve_state_begin(ctxs[i], &gs[i]));
+            DAO_CU(cudaEventRecord(bg->events[i], ctxs[i]->stream));
+            DAO_CU(cudaStreamWaitEvent(bg->stream, bg->events[i], 0));
+        }
+        DAO_CU(cudaGraphLaunch(bg->exec, bg->stream));
+        DAO_CU(cudaEventRecord(bg->events[n], bg->stream));
+        for (int i = 0; i < n; ++i) DAO_CU(cudaStreamWaitEvent(ctxs[i]->stream, bg->events[n], 0));
+    }
+    for (int i = 0; i < n; ++i) {
+        dao_ctx* c = ctxs[i];
+        dao_status res = DAO_OK;
+        DAO_TRY(solve_graph_end(c, gs[i], n_apertures, n_done ? n_done + i : nullptr,
+                                traces ? traces + (size_t)i * n_apertures : nullptr, &res, false));
+        const int per_round = c->opt.mlc_constraint != DAO_MLC_CONSECUTIVE ? 3 : 2;
+        c->launches_i += per_round * R + (i == 0 ? R : 0);  // its round kernels; the master launches on the first
+        c->count_launches();
         if (status) status[i] = res;
     }
     return DAO_OK;

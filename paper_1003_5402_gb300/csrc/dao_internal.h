@@ -252,6 +252,7 @@ struct CommitArgs {
     int ld;
     CGDev* cg;
     cudaGraphConditionalHandle cond;
+    int use_cond;           // 0: no conditional node around the kernel (cond unused)
 };
 cudaError_t launch_commit_column(const DevCSR& D, const CommitArgs& ca, int max_nb, int num_sms, cudaStream_t stream,
                                  int* launches);
@@ -372,6 +373,35 @@ cudaError_t build_seg(const int64_t* rp, const int* col, const int* prow, int V,
 cudaError_t build_transpose_place(int prec, const int64_t* rp, const int* col, const float* val, int V, int CH, int N,
                                   int n_ch, int* C, const int* cnt, const float* scale, DevCSR& Dt, float* tval,
                                   int num_sms, cudaStream_t s);
+
+// One plan's persistent master solve as the kernel reads it: the solver state,
+// the slab and its partial arrays (stride GS), the objective terms, the
+// round's skip flag and outputs, and the device-side round state (pool size).
+struct MasterTask {
+    const float* slab;
+    int ld, V, GS, S, max_iter;
+    int capw;             // active-list slots per warp (master_persist_capw of V and the group size)
+    MasterDev* st;
+    GridBar* gb;
+    float* H_part;
+    double* g_part;
+    float* gn_part;
+    double* F_part;
+    const uint8_t* vstruct;
+    const StructTermsF* tf;
+    double tol_rel;
+    const int* skip;
+    float* z_out;
+    float* pi_out;
+    CGDev* cg;
+};
+// Several plans' master solves in one cooperative launch, GB blocks each
+// (master_batch_group: the most for n_tasks plans with two blocks per SM);
+// tasks in device memory; max_V the largest voxel count.
+int master_batch_group(int n_tasks, int num_sms);
+int master_persist_capw(int V, int G);
+cudaError_t launch_master_persist_batch(const MasterTask* tasks, int n_tasks, int GB, int max_V, cudaStream_t stream,
+                                        int* launches);
 
 // The whole master solve as one cooperative launch (GP blocks), after
 // launch_master_init; dynamic shared memory per master_persist_smem.

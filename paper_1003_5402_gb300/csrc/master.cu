@@ -29,6 +29,8 @@
 // FP32 rounding level of g.  A trial point that meets it is accepted without
 // the Armijo test: near the optimum the objective's change is below its own
 // rounding and the test would reject an optimal point.
+#include <algorithm>
+
 #include "dao_internal.h"
 
 #include <cmath>
@@ -483,11 +485,11 @@ __device__ __forceinline__ void master_reduce_part(const float* __restrict__ H_p
                                                    const double* __restrict__ g_part,
                                                    const float* __restrict__ gn_part,
                                                    const double* __restrict__ F_part, int GH, int GC, int GE, int K,
-                                                   MasterDev* __restrict__ st) {
+                                                   MasterDev* __restrict__ st, int bid, int nblocks) {
     const int E = K * (K + 1) / 2;
     const int lane = threadIdx.x & 31;
     const int n_out = E + 2 * K + 1;
-    for (int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < n_out; o += (gridDim.x * blockDim.x) >> 5) {
+    for (int o = (bid * (int)blockDim.x + (int)threadIdx.x) >> 5; o < n_out; o += (nblocks * (int)blockDim.x) >> 5) {
         if (o < E) {  // the factorisation is FP32: so is this sum
             float s = lane_sum_strided(H_part + (size_t)o * GH, GC, lane);
             s = warp_sum_f32(s);
@@ -915,7 +917,7 @@ __global__ void __launch_bounds__(STEP_T, 1) k_master_reduce_step(const float* _
         if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
         return;
     }
-    master_reduce_part(H_part, g_part, gn_part, F_part, GH, GH, GE, st->K, st);
+    master_reduce_part(H_part, g_part, gn_part, F_part, GH, GH, GE, st->K, st, blockIdx.x, gridDim.x);
     __syncthreads();
     if (threadIdx.x == 0) s_last = atom_add_acq_rel_gpu(&st->ticket, 1u) == gridDim.x - 1;
     __syncthreads();
@@ -976,16 +978,33 @@ __device__ __forceinline__ bool grid_sync(GridBar* gb, unsigned nblocks, unsigne
     return *s_flag != 0;
 }
 
-__global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restrict__ slab, int ld, int V, int K, int KP,
-                                                       int KW, int NV, int capw, MasterDev* __restrict__ st,
-                                                       GridBar* __restrict__ gb, float* __restrict__ H_part,
-                                                       double* __restrict__ g_part, float* __restrict__ gn_part,
-                                                       double* __restrict__ F_part, int GS,
-                                                       const uint8_t* __restrict__ vstruct,
-                                                       const StructTermsF* __restrict__ tf, int S, int max_iter,
-                                                       double tol_rel, double sigma, const int* __restrict__ skip,
-                                                       float* __restrict__ z_out, float* __restrict__ pi_out,
-                                                       CGDev* __restrict__ cg) {
+// BATCH: one launch for several plans, blocks [g GB, (g + 1) GB) solving the
+// master problem of tasks[g] with its own barrier and partial arrays (the
+// plans' solves run side by side, each on GB blocks); otherwise one plan, t1,
+// on the whole grid.  Every other difference is the block's index within its
+// group (bid) and the group's size (G).
+template <bool BATCH>
+__global__ void __launch_bounds__(PT, 2) k_master_persist(const MasterTask t1, const MasterTask* __restrict__ tasks,
+                                                       int GB, int K, int KP, int KW, int NV, double sigma) {
+#define DAO_TASK(f) (BATCH ? tasks[blockIdx.x / GB].f : t1.f)
+    const float* __restrict__ slab = DAO_TASK(slab);
+    const int ld = DAO_TASK(ld), V = DAO_TASK(V), GS = DAO_TASK(GS), S = DAO_TASK(S), max_iter = DAO_TASK(max_iter);
+    const int capw = DAO_TASK(capw);
+    MasterDev* __restrict__ st = DAO_TASK(st);
+    GridBar* __restrict__ gb = DAO_TASK(gb);
+    float* __restrict__ H_part = DAO_TASK(H_part);
+    double* __restrict__ g_part = DAO_TASK(g_part);
+    float* __restrict__ gn_part = DAO_TASK(gn_part);
+    double* __restrict__ F_part = DAO_TASK(F_part);
+    const uint8_t* __restrict__ vstruct = DAO_TASK(vstruct);
+    const StructTermsF* __restrict__ tf = DAO_TASK(tf);
+    const double tol_rel = DAO_TASK(tol_rel);
+    const int* __restrict__ skip = DAO_TASK(skip);
+    float* __restrict__ z_out = DAO_TASK(z_out);
+    float* __restrict__ pi_out = DAO_TASK(pi_out);
+    CGDev* __restrict__ cg = DAO_TASK(cg);
+#undef DAO_TASK
+    const int bid = BATCH ? (int)(blockIdx.x % GB) : (int)blockIdx.x;
     if (K <= 0) {  // pool size from the device (one graph for every round); KW sets the layout below
         K = __ldcg(&cg->K);
         KP = (K + 3) / 4 * 4;
@@ -1008,7 +1027,7 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
     __shared__ unsigned s_target;
     if (skip != nullptr && *skip) return;  // the same for every block
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int G = gridDim.x;
+    const int G = BATCH ? GB : (int)gridDim.x;
     if (tid == 0) {  // barrier base; a solve whose barrier broke runs no further master solve
         const unsigned c = *reinterpret_cast<volatile unsigned*>(&gb->count);
         s_target = c - c % (unsigned)G;
@@ -1024,7 +1043,7 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
     const int vl = tid % NV;
     if (tid < nb * NV) block_of(tid / NV, KB, rb, cb);
     const int n32 = (V + 31) / 32;
-    const int tiles_b = blockIdx.x < n32 ? (n32 - 1 - (int)blockIdx.x) / G + 1 : 0;
+    const int tiles_b = bid < n32 ? (n32 - 1 - bid) / G + 1 : 0;
     // warm start (every block computes it; block 0 also writes the solver
     // state): the previous optimum, the new aperture K - 1 at 0
     if (tid < KMAX) {
@@ -1032,12 +1051,12 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
         const float hi = (float)yv;
         s_yh[tid] = hi;
         s_yl[tid] = (float)(yv - (double)hi);
-        if (blockIdx.x == 0 && tid < K) {
+        if (bid == 0 && tid < K) {
             st->yt[tid] = yv;
             st->d[tid] = 0.0;
         }
     }
-    if (blockIdx.x == 0 && tid == 0) {
+    if (bid == 0 && tid == 0) {
         st->K = K;
         st->iter = 0;
         st->phase = 0;
@@ -1064,11 +1083,20 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
             if (s_stop) break;
         }
         first = false;
-        // ---- A. z, pi, h, F over this block's tiles; active voxels per warp
+        // ---- A. z, pi, h, F over this block's tiles; active voxels per warp,
+        // in batches of capw / 32 tiles per warp (one batch when the lists of all
+        // the block's tiles fit shared memory), each batch's lists folded into
+        // the block's partial H, g and scale of g before the next
         float facc = 0.f;
+        float hs[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) hs[q] = 0.f;
+        float gs[4] = {0.f, 0.f, 0.f, 0.f}, gns[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int i0 = 0; i0 < tiles_b; i0 += PW * (capw / 32)) {
+        const int i1 = min(tiles_b, i0 + PW * (capw / 32));
         int na = 0;
-        for (int i = warp; i < tiles_b; i += PW) {
-            const int j = (blockIdx.x + i * G) * 32 + lane;
+        for (int i = i0 + warp; i < i1; i += PW) {
+            const int j = (bid + i * G) * 32 + lane;
             const bool in = j < V;
             // requested with the first columns: the label, or the voxel's own terms
             const int sid = in && S >= 0 ? vstruct[j] : 0;
@@ -1122,22 +1150,11 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
             na += __popc(bal);
         }
         if (lane == 0) s_wn[warp] = na;
-        const float fw = warp_sum_f32(facc);
-        if (lane == 0) s_red[warp] = fw;
         __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < PW; ++w) t += (double)s_red[w];
-            F_part[blockIdx.x] = t;
-        }
         int total = 0;
 #pragma unroll
         for (int w = 0; w < PW; ++w) total += s_wn[w];
-        // ---- the block's partial H, g and scale of g over its active lists
-        float hs[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) hs[q] = 0.f;
-        float gs[4] = {0.f, 0.f, 0.f, 0.f}, gns[4] = {0.f, 0.f, 0.f, 0.f};
+        // ---- the block's partial H, g and scale of g over this batch's active lists
         for (int c0 = 0; c0 < total; c0 += CHP) {
             const int n = min(CHP, total - c0);
             {   // list entry c0 + i (warp lists in order) as row i of Ac
@@ -1211,6 +1228,16 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
             }
             __syncthreads();
         }
+        __syncthreads();  // every warp is done with this batch's counts and lists
+        }
+        const float fw = warp_sum_f32(facc);
+        if (lane == 0) s_red[warp] = fw;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < PW; ++w) t += (double)s_red[w];
+            F_part[bid] = t;
+        }
         float vals[24];
 #pragma unroll
         for (int q = 0; q < 16; ++q) vals[q] = hs[q];
@@ -1242,15 +1269,15 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int r = 4 * rb + q, cl = 4 * cb + e;
-                    if (r < K && cl < K && r <= cl) H_part[(size_t)tri_index(r, cl, K) * GS + blockIdx.x] = vals[q * 4 + e];
+                    if (r < K && cl < K && r <= cl) H_part[(size_t)tri_index(r, cl, K) * GS + bid] = vals[q * 4 + e];
                 }
             if (rb == cb) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int r = 4 * rb + q;
                     if (r < K) {
-                        g_part[(size_t)r * GS + blockIdx.x] = (double)vals[16 + q];
-                        gn_part[(size_t)r * GS + blockIdx.x] = vals[20 + q];
+                        g_part[(size_t)r * GS + bid] = (double)vals[16 + q];
+                        gn_part[(size_t)r * GS + bid] = vals[20 + q];
                     }
                 }
             }
@@ -1260,7 +1287,7 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
             break;
         }
         // ---- B. reduction by every block, the step by the last one to finish
-        master_reduce_part(H_part, g_part, gn_part, F_part, GS, G, G, K, st);
+        master_reduce_part(H_part, g_part, gn_part, F_part, GS, G, G, K, st, bid, G);
         __syncthreads();
         if (tid == 0) s_last = atom_add_acq_rel_gpu(&st->ticket, 1u) == (unsigned)G - 1u;
         __syncthreads();
@@ -1287,7 +1314,7 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
         }
         __syncthreads();
         for (int i = warp; i < tiles_b; i += PW) {
-            const int j = (blockIdx.x + i * G) * 32 + lane;
+            const int j = (bid + i * G) * 32 + lane;
             const bool in = j < V;
             float sc[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
             const float* col = slab + (in ? j : 0);
@@ -1314,7 +1341,7 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const float* __restric
             }
         }
     }
-    if (cg != nullptr && blockIdx.x == 0 && tid == 0) {  // the round's record
+    if (cg != nullptr && bid == 0 && tid == 0) {  // the round's record
         cg->trace[K - 1] = __ldcg(&st->F);
         cg->res[K - 1] = __ldcg(&st->res);
         cg->tol[K - 1] = __ldcg(&st->tol);
@@ -1400,7 +1427,11 @@ cudaError_t master_configure() {
     cudaError_t e = cudaFuncSetAttribute(k_master_eval, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)master_eval_smem(KMAX));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_master_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PERSIST_SMEM_MAX);
+    e = cudaFuncSetAttribute(k_master_persist<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)PERSIST_SMEM_MAX);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_master_persist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)PERSIST_SMEM_MAX);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_master_hess, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
@@ -1441,10 +1472,18 @@ cudaError_t launch_master_step(int K, const MasterBuffers& mb, int max_iter, dou
     return cudaGetLastError();
 }
 
-size_t master_persist_smem(int V, int G) {
+// Active-list slots per warp of the persistent solve: every tile of the block at
+// once when they fit (one batch), else at most CAPW_MAX, which keeps two blocks
+// per SM whatever the voxel count and grid size.
+constexpr int CAPW_MAX = 512;
+int master_persist_capw(int V, int G) {
     const int n32 = (V + 31) / 32;
     const int tiles = G > 0 ? (n32 + G - 1) / G : n32;
-    const int capw = (tiles + PW - 1) / PW * 32;
+    return std::min(CAPW_MAX, (tiles + PW - 1) / PW * 32);
+}
+
+size_t master_persist_smem(int V, int G) {
+    const int capw = master_persist_capw(V, G);
     return (size_t)PW * capw * sizeof(int) + (size_t)(PW * capw * 2 + 3) / 4 * 4 * sizeof(float) +
            (size_t)CHP * master_kw(KMAX) * sizeof(float) + 2 * CHP * sizeof(float);
 }
@@ -1465,7 +1504,7 @@ int master_persist_grid(int V, int num_sms, int want) {
         for (int G = want; G <= 2 * num_sms; ++G) {
             const size_t smem = master_persist_smem(V, G);
             if (smem > PERSIST_SMEM_MAX) continue;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_master_persist, PT, smem) != cudaSuccess) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_master_persist<false>, PT, smem) != cudaSuccess) {
                 cudaGetLastError();
                 return 0;
             }
@@ -1477,7 +1516,7 @@ int master_persist_grid(int V, int num_sms, int want) {
         const size_t smem = master_persist_smem(V, G);
         if (smem > PERSIST_SMEM_MAX) continue;
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_master_persist, PT, smem) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_master_persist<false>, PT, smem) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
@@ -1493,21 +1532,35 @@ cudaError_t launch_master_persist(const MasterBuffers& mb, const float* slab, in
     const int G = mb.GP;
     if (G < 1) return cudaErrorInvalidConfiguration;
     if (K <= 0 && cg == nullptr) return cudaErrorInvalidValue;
-    const int KP = K > 0 ? (K + 3) / 4 * 4 : 0;
-    const int n32 = (V + 31) / 32;
-    const int capw = ((n32 + G - 1) / G + PW - 1) / PW * 32;
-    int KW = K > 0 ? master_kw(K) : 0, NV = K > 0 ? master_lanes(K) : 0, GS = mb.GH;  // partial arrays: stride GH >= G
+    int KP = K > 0 ? (K + 3) / 4 * 4 : 0;
+    int capw = master_persist_capw(V, G);
+    int KW = K > 0 ? master_kw(K) : 0, NV = K > 0 ? master_lanes(K) : 0;
+    MasterTask t{};
+    t.capw = capw;
+    t.slab = slab;
+    t.ld = ld;
+    t.V = V;
+    t.GS = mb.GH;  // partial arrays: stride GH >= G
+    t.S = S;
+    t.max_iter = max_iter;
+    t.st = mb.st;
+    t.gb = mb.bar;
+    t.H_part = mb.H_part;
+    t.g_part = mb.g_part;
+    t.gn_part = mb.gn_part;
+    t.F_part = mb.F_part;
+    t.vstruct = vstruct;
+    t.tf = tf;
+    t.tol_rel = tol_rel;
+    t.skip = skip;
+    t.z_out = z_out;
+    t.pi_out = pi_out;
+    t.cg = cg;
+    const MasterTask* none = nullptr;
+    int GB = 0;
     double sigma = 1e-4;
-    MasterDev* st = mb.st;
-    GridBar* gb = mb.bar;
-    float* H_part = mb.H_part;
-    double* g_part = mb.g_part;
-    float* gn_part = mb.gn_part;
-    double* F_part = mb.F_part;
-    void* args[] = {(void*)&slab, (void*)&ld, (void*)&V, (void*)&K, (void*)&KP, (void*)&KW, (void*)&NV,
-                    (void*)&capw, (void*)&st, (void*)&gb, (void*)&H_part, (void*)&g_part, (void*)&gn_part,
-                    (void*)&F_part, (void*)&GS, (void*)&vstruct, (void*)&tf, (void*)&S, (void*)&max_iter,
-                    (void*)&tol_rel, (void*)&sigma, (void*)&skip, (void*)&z_out, (void*)&pi_out, (void*)&cg};
+    void* args[] = {(void*)&t, (void*)&none, (void*)&GB, (void*)&K, (void*)&KP, (void*)&KW, (void*)&NV,
+                    (void*)&sigma};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(G);
     cfg.blockDim = dim3(PT);
@@ -1518,7 +1571,43 @@ cudaError_t launch_master_persist(const MasterBuffers& mb, const float* slab, in
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)k_master_persist, args);
+    cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)k_master_persist<false>, args);
+    ++*launches;
+    return e;
+}
+
+int master_batch_group(int n_tasks, int num_sms) {
+    // two co-resident blocks per SM (the shared memory per block is capped)
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_master_persist<true>, PT,
+                                                      (size_t)PW * CAPW_MAX * 12 + (size_t)CHP * master_kw(KMAX) * 4 +
+                                                          2 * CHP * 4 + 16) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    occ = std::min(occ, 2);
+    return n_tasks > 0 ? occ * num_sms / n_tasks : 0;
+}
+
+cudaError_t launch_master_persist_batch(const MasterTask* tasks, int n_tasks, int GB, int max_V, cudaStream_t stream,
+                                        int* launches) {
+    if (n_tasks < 1 || GB < 1) return cudaErrorInvalidConfiguration;
+    int K = 0, KP = 0, KW = 0, NV = 0;  // each group reads its pool size from its plan's device state
+    MasterTask none{};
+    double sigma = 1e-4;
+    void* args[] = {(void*)&none, (void*)&tasks, (void*)&GB, (void*)&K, (void*)&KP, (void*)&KW, (void*)&NV,
+                    (void*)&sigma};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_tasks * GB);
+    cfg.blockDim = dim3(PT);
+    cfg.dynamicSmemBytes = master_persist_smem(max_V, GB);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)k_master_persist<true>, args);
     ++*launches;
     return e;
 }

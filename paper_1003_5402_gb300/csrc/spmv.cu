@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(256) k_commit_column(const int* __restrict__ c
         if (lead) {
             cg->idle = idle;
             cg->stop = stop;
-            cudaGraphSetConditional(ca.cond, stop ? 0u : 1u);
+            if (ca.use_cond) cudaGraphSetConditional(ca.cond, stop ? 0u : 1u);
         }
     };
     if (__ldcg(&cg->rs_stop)) {

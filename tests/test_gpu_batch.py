@@ -173,3 +173,64 @@ def test_batch_of_full_size_instances_against_the_oracle(torch):
     finally:
         for p in plans:
             p.close()
+
+
+def test_persistent_batch_equals_each_instance_alone_bitwise(torch):
+    """dao_batch_solve_persistent (every round's master solves in one
+    cooperative launch, a group of blocks per plan): each instance's results
+    are bitwise those of solving it alone on that many blocks, for instances of
+    different sizes, storage and MLC constraints, on two calls in a row (the
+    second reuses the captured graph)."""
+    from paper_1003_5402_gb300 import Plan, binding
+    K = 12
+    inst = _instances() + [("micro_interdig", P.make_case(P.spec_micro()),
+                            {"mlc_constraint": binding.DAO_MLC_INTERDIGITATION})]
+    GB = binding.load().dao_batch_group_size(len(inst), 0)
+    assert GB >= 1
+    alone = []
+    for name, case, kw in inst:
+        with Plan(case, master_blocks=GB, **kw) as p:
+            alone.append(_snapshot(p, p.solve(K)))
+    plans = [Plan(case, **kw) for name, case, kw in inst]
+    try:
+        for call in range(2):
+            for p in plans:
+                p.reset()
+            res = binding.batch_solve(plans, K, persistent=True)
+            for (name, _, _), p, r, a in zip(inst, plans, res, alone):
+                _same(_snapshot(p, r), a)
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_persistent_batch_of_full_size_instances_against_the_oracle(torch):
+    """The fused batch at the benchmark's sizes: a perturbed prostate-shaped
+    instance (FP32), a perturbed H&N-shaped instance (FP16) and the small box;
+    each plan alone on the batch's group size passes the every-round oracle
+    check, and the batch's result is bitwise that plan."""
+    from paper_1003_5402_gb300 import Plan, binding
+    from _helpers import quantized_case
+    from test_gpu_cg import _free_running_checked
+    K = 50
+    inst = [(P.make_case(P.perturb(P.spec_prostate(), 4002)), {"precision": 0}),
+            (P.make_case(P.perturb(P.spec_hn(), 4018)), {"precision": 1}),
+            (P.make_case(P.spec_tiny()), {"precision": 0})]
+    GB = binding.load().dao_batch_group_size(len(inst), 0)
+    checked = []
+    for case, kw in inst:
+        ref_case = case if kw["precision"] == 0 else quantized_case(case, "fp16")
+        checked.append(_free_running_checked(case, K, torch, plan_kw=dict(kw, master_blocks=GB), ref_case=ref_case))
+    plans = [Plan(c, **kw) for c, kw in inst]
+    try:
+        res = binding.batch_solve(plans, K, persistent=True)
+        for p, r, ref in zip(plans, res, checked):
+            assert r[1] == K
+            aps = p.apertures()
+            assert all(x[0] == y[0] and np.array_equal(x[1], y[1]) for x, y in zip(aps, ref["apertures"]))
+            assert np.array_equal(p.intensities(), ref["y"])
+            z, F = p.dose()
+            assert np.array_equal(z, ref["z"]) and F == ref["F"]
+    finally:
+        for p in plans:
+            p.close()
