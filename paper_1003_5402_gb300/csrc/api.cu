@@ -62,13 +62,6 @@ struct dao_ctx {
     int num_sms = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    // Own streams: `stream` (creation, read-back, host-driven work) at the
-    // device's highest priority, `solve_stream` (the device-driven rounds) at the
-    // lowest, so that another plan's set-up and read-back are scheduled ahead of
-    // this plan's rounds instead of waiting behind them; with a caller's stream
-    // both are that stream.
-    cudaStream_t solve_stream = nullptr;
-    cudaEvent_t ev_to_solve = nullptr, ev_from_solve = nullptr;
     dao_options opt{};
 
     int V = 0, N = 0, B = 0, R_tot = 0, max_rows = 0, S = 0;
@@ -1059,18 +1052,11 @@ dao_status solve_state_begin(dao_ctx* c, const GraphSolve* gs) {
 // first round launches every round.
 dao_status launch_round(dao_ctx* c, const GraphSolve& gs, int k) {
     if (k <= gs.K0 || k > gs.K1) return DAO_OK;
-    if (c->solve_exec != nullptr && k != gs.K0 + 1) return DAO_OK;  // the first round launched every round
-    cudaGraphExec_t ex = c->solve_exec != nullptr ? c->solve_exec : c->round_exec[k];
-    if (c->solve_stream == c->stream) {
-        DAO_CU(cudaGraphLaunch(ex, c->stream));
+    if (c->solve_exec != nullptr) {
+        if (k == gs.K0 + 1) DAO_CU(cudaGraphLaunch(c->solve_exec, c->stream));
         return DAO_OK;
     }
-    // on the low-priority stream, ordered after and before the context's own work
-    DAO_CU(cudaEventRecord(c->ev_to_solve, c->stream));
-    DAO_CU(cudaStreamWaitEvent(c->solve_stream, c->ev_to_solve, 0));
-    DAO_CU(cudaGraphLaunch(ex, c->solve_stream));
-    DAO_CU(cudaEventRecord(c->ev_from_solve, c->solve_stream));
-    DAO_CU(cudaStreamWaitEvent(c->stream, c->ev_from_solve, 0));
+    DAO_CU(cudaGraphLaunch(c->round_exec[k], c->stream));
     return DAO_OK;
 }
 
@@ -1256,18 +1242,10 @@ dao_status create_common(const dao_csr* D, const dao_geometry* g, const dao_stru
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
         if (opt.stream) {
             c->stream = static_cast<cudaStream_t>(opt.stream);
-            c->solve_stream = c->stream;
         } else {
-            int least = 0, greatest = 0;
-            e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-            if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->stream, cudaStreamNonBlocking, greatest);
-            if (e == cudaSuccess) {
-                c->own_stream = true;
-                e = cudaStreamCreateWithPriority(&c->solve_stream, cudaStreamNonBlocking, least);
-            }
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_to_solve, cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_from_solve, cudaEventDisableTiming);
+            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
             if (e != cudaSuccess) st = fail(DAO_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+            c->own_stream = true;
         }
     }
     if (st == DAO_OK) {
@@ -1389,12 +1367,6 @@ void dao_destroy(dao_ctx* c) {
     for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
     if (c->pinned) pinned_release(c->pinned, c->pinned_block);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
-    if (c->own_stream && c->solve_stream) {
-        cudaStreamSynchronize(c->solve_stream);
-        cudaStreamDestroy(c->solve_stream);
-    }
-    if (c->ev_to_solve) cudaEventDestroy(c->ev_to_solve);
-    if (c->ev_from_solve) cudaEventDestroy(c->ev_from_solve);
     delete c;
 }
 
