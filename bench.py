@@ -680,8 +680,16 @@ def run_ours(a):
         batch = run_batch(torch, dev, flush, batch_cases, a.batch, a.apertures)
     serve = None
     if serve_cases is not None:
+        # requests arrive in page-locked host buffers, as a serving process keeps
+        # them (their uploads are DMA transfers)
+        try:
+            serve_cases = [pinned_inputs(torch, c) for c in serve_cases]
+            serve_inputs = "page-locked host arrays"
+        except Exception as exc:   # no page-locked memory: ordinary host arrays
+            serve_inputs = f"pageable host arrays ({type(exc).__name__})"
         # FP16 storage (the mixed-precision form), every request its own plan
         serve = run_serve(dev, serve_cases, a.serve_requests, a.apertures, precision=PREC["fp16"])
+        serve["inputs"] = serve_inputs
         if a.serve_burst > 0:
             burst = run_serve(dev, serve_cases, a.serve_burst, a.apertures, rate_per_s=200.0, seed=9100,
                               precision=PREC["fp16"])
