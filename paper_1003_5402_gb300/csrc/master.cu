@@ -983,35 +983,17 @@ __device__ __forceinline__ bool grid_sync(GridBar* gb, unsigned nblocks, unsigne
 // plans' solves run side by side, each on GB blocks); otherwise one plan, t1,
 // on the whole grid.  Every other difference is the block's index within its
 // group (bid) and the group's size (G).
-template <bool BATCH>
-__global__ void __launch_bounds__(PT, 2) k_master_persist(const MasterTask t1, const MasterTask* __restrict__ tasks,
-                                                       int GB, int K, int KP, int KW, int NV, double sigma) {
-#define DAO_TASK(f) (BATCH ? tasks[blockIdx.x / GB].f : t1.f)
-    const float* __restrict__ slab = DAO_TASK(slab);
-    const int ld = DAO_TASK(ld), V = DAO_TASK(V), GS = DAO_TASK(GS), S = DAO_TASK(S), max_iter = DAO_TASK(max_iter);
-    const int capw = DAO_TASK(capw);
-    MasterDev* __restrict__ st = DAO_TASK(st);
-    GridBar* __restrict__ gb = DAO_TASK(gb);
-    float* __restrict__ H_part = DAO_TASK(H_part);
-    double* __restrict__ g_part = DAO_TASK(g_part);
-    float* __restrict__ gn_part = DAO_TASK(gn_part);
-    double* __restrict__ F_part = DAO_TASK(F_part);
-    const uint8_t* __restrict__ vstruct = DAO_TASK(vstruct);
-    const StructTermsF* __restrict__ tf = DAO_TASK(tf);
-    const double tol_rel = DAO_TASK(tol_rel);
-    const int* __restrict__ skip = DAO_TASK(skip);
-    float* __restrict__ z_out = DAO_TASK(z_out);
-    float* __restrict__ pi_out = DAO_TASK(pi_out);
-    CGDev* __restrict__ cg = DAO_TASK(cg);
-#undef DAO_TASK
-    const int bid = BATCH ? (int)(blockIdx.x % GB) : (int)blockIdx.x;
-    if (K <= 0) {  // pool size from the device (one graph for every round); KW sets the layout below
-        K = __ldcg(&cg->K);
-        KP = (K + 3) / 4 * 4;
-        KW = master_kw(K);
-        NV = master_lanes(K);
-    }
-    extern __shared__ __align__(16) float pm[];
+// The master solve of one plan (a task) by a group of G co-resident blocks, bid
+// the block's index in it; pm the dynamic shared memory, s_target / s_flag the
+// group barrier's shared state (s_target: the block's next target, already
+// based on the barrier counter).  Every block of the group calls it with the
+// same K.
+__device__ __forceinline__ void master_solve_group(
+    const float* __restrict__ slab, int ld, int V, int GS, int S, int max_iter, int capw, MasterDev* __restrict__ st,
+    GridBar* __restrict__ gb, float* __restrict__ H_part, double* __restrict__ g_part, float* __restrict__ gn_part,
+    double* __restrict__ F_part, const uint8_t* __restrict__ vstruct, const StructTermsF* __restrict__ tf,
+    double tol_rel, float* __restrict__ z_out, float* __restrict__ pi_out, CGDev* __restrict__ cg, int bid, int G,
+    int K, int KP, int KW, int NV, double sigma, float* pm, unsigned* s_target, int* s_flag) {
     int* s_act = reinterpret_cast<int*>(pm);          // [PW][capw] voxel indices
     float* s_hv = pm + PW * capw;                     // [PW][capw] h
     float* s_pv = s_hv + PW * capw;                   // [PW][capw] pi
@@ -1023,18 +1005,8 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const MasterTask t1, c
     __shared__ int s_wn[PW];
     __shared__ float s_red[PW];
     __shared__ float s_scr[8 * 24];
-    __shared__ int s_flag, s_last, s_stop;
-    __shared__ unsigned s_target;
-    if (skip != nullptr && *skip) return;  // the same for every block
+    __shared__ int s_last, s_stop;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int G = BATCH ? GB : (int)gridDim.x;
-    if (tid == 0) {  // barrier base; a solve whose barrier broke runs no further master solve
-        const unsigned c = *reinterpret_cast<volatile unsigned*>(&gb->count);
-        s_target = c - c % (unsigned)G;
-        s_stop = *reinterpret_cast<volatile unsigned*>(&gb->broken) != 0;
-    }
-    __syncthreads();
-    if (s_stop) return;
     for (int i = tid; i < S; i += PT) s_tf[i] = tf[i];
     const int KB = KP / 4;
     const int nb = KB * (KB + 1) / 2;
@@ -1282,7 +1254,7 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const MasterTask t1, c
                 }
             }
         }
-        if (!grid_sync(gb, G, &s_target, &s_flag)) {
+        if (!grid_sync(gb, G, s_target, s_flag)) {
             if (tid == 0) st->err = 2;
             break;
         }
@@ -1295,7 +1267,7 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const MasterTask t1, c
             if (tid == 0) st->ticket = 0;
             master_step_body(st, max_iter, tol_rel, sigma);
         }
-        if (!grid_sync(gb, G, &s_target, &s_flag)) {
+        if (!grid_sync(gb, G, s_target, s_flag)) {
             if (tid == 0) st->err = 2;
             break;
         }
@@ -1348,6 +1320,51 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const MasterTask t1, c
         cg->evals[K - 1] = __ldcg(&st->n_eval);
         cg->status[K - 1] = __ldcg(&st->status);
     }
+}
+
+
+template <bool BATCH>
+__global__ void __launch_bounds__(PT, 2) k_master_persist(const MasterTask t1, const MasterTask* __restrict__ tasks,
+                                                       int GB, int K, int KP, int KW, int NV, double sigma) {
+#define DAO_TASK(f) (BATCH ? tasks[blockIdx.x / GB].f : t1.f)
+    const float* __restrict__ slab = DAO_TASK(slab);
+    const int ld = DAO_TASK(ld), V = DAO_TASK(V), GS = DAO_TASK(GS), S = DAO_TASK(S), max_iter = DAO_TASK(max_iter);
+    const int capw = DAO_TASK(capw);
+    MasterDev* __restrict__ st = DAO_TASK(st);
+    GridBar* __restrict__ gb = DAO_TASK(gb);
+    float* __restrict__ H_part = DAO_TASK(H_part);
+    double* __restrict__ g_part = DAO_TASK(g_part);
+    float* __restrict__ gn_part = DAO_TASK(gn_part);
+    double* __restrict__ F_part = DAO_TASK(F_part);
+    const uint8_t* __restrict__ vstruct = DAO_TASK(vstruct);
+    const StructTermsF* __restrict__ tf = DAO_TASK(tf);
+    const double tol_rel = DAO_TASK(tol_rel);
+    const int* __restrict__ skip = DAO_TASK(skip);
+    float* __restrict__ z_out = DAO_TASK(z_out);
+    float* __restrict__ pi_out = DAO_TASK(pi_out);
+    CGDev* __restrict__ cg = DAO_TASK(cg);
+#undef DAO_TASK
+    const int bid = BATCH ? (int)(blockIdx.x % GB) : (int)blockIdx.x;
+    if (K <= 0) {  // pool size from the device (one graph for every round); KW sets the layout below
+        K = __ldcg(&cg->K);
+        KP = (K + 3) / 4 * 4;
+        KW = master_kw(K);
+        NV = master_lanes(K);
+    }
+    extern __shared__ __align__(16) float pm[];
+    __shared__ int s_flag, s_stop0;
+    __shared__ unsigned s_target;
+    if (skip != nullptr && *skip) return;  // the same for every block
+    const int G = BATCH ? GB : (int)gridDim.x;
+    if (threadIdx.x == 0) {  // barrier base; a solve whose barrier broke runs no further master solve
+        const unsigned c = *reinterpret_cast<volatile unsigned*>(&gb->count);
+        s_target = c - c % (unsigned)G;
+        s_stop0 = *reinterpret_cast<volatile unsigned*>(&gb->broken) != 0;
+    }
+    __syncthreads();
+    if (s_stop0) return;
+    master_solve_group(slab, ld, V, GS, S, max_iter, capw, st, gb, H_part, g_part, gn_part, F_part, vstruct, tf,
+                       tol_rel, z_out, pi_out, cg, bid, G, K, KP, KW, NV, sigma, pm, &s_target, &s_flag);
 }
 
 }  // namespace
