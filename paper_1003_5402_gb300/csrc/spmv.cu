@@ -13,6 +13,7 @@
 
 #include "dao_internal.h"
 #include "pricing.cuh"
+#include "spmv_body.cuh"
 
 namespace dao {
 
@@ -24,22 +25,6 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     return v;
-}
-
-// Sum over a block: FP32 within each warp, FP64 across the warps (FP64 issues
-// at 1/64 of the FP32 rate on this part, so it is kept to one lane per warp).
-template <int NT>
-__device__ __forceinline__ double block_sum_mixed(float v, double* s_red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) s_red[warp] = (double)v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int w = 0; w < NT / 32; ++w) t += s_red[w];
-    return t;
 }
 
 // Sum of one double per thread over the block; the result is valid in thread 0.
@@ -184,71 +169,9 @@ __global__ void __launch_bounds__(BT) k_dt(const int* __restrict__ rowptr, const
     dt_round_snapshot(rt);
     if (skip != nullptr && *skip) return;
     const int row = order[blockIdx.x];  // longest rows first: they start in the first wave
-    const int p0 = rowptr[row] >> 2, p1 = rowptr[row + 1] >> 2;
-    // software pipeline: the next group's indices and values (DRAM) are in
-    // flight while the current group's pi gathers (L2) and products run
-    float acc = 0.f;
-    int p = p0 + threadIdx.x;
-    int4 cn = make_int4(0, 0, 0, 0);
-    float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (p < p1) {
-        cn = __ldg(col4 + p);
-        vn = __ldg(val4 + p);
-    }
-    while (p < p1) {
-        const int4 c = cn;
-        const float4 v = vn;
-        p += BT;
-        if (p < p1) {
-            cn = __ldg(col4 + p);
-            vn = __ldg(val4 + p);
-        }
-        const float a0 = __ldg(pi + c.x), a1 = __ldg(pi + c.y), a2 = __ldg(pi + c.z), a3 = __ldg(pi + c.w);
-        acc = fmaf(v.x, a0, acc);
-        acc = fmaf(v.y, a1, acc);
-        acc = fmaf(v.z, a2, acc);
-        acc = fmaf(v.w, a3, acc);
-    }
-    const double s = block_sum_mixed<BT>(acc, s_red);
-    if (threadIdx.x == 0) w[row] = (float)s;
+    const float s = dt_row_sum<BT>(rowptr, col4, val4, row, pi, s_red);
+    if (threadIdx.x == 0) w[row] = s;
     dt_row_ticket(rt, row, w);
-}
-
-// ---- a4 ---------------------------------------------------------------------
-// G lanes per voxel row over the row's segment of beam b (columns base ..
-// base + nb - 1); mask[c] in {0, 1} marks the aperture's open beamlets.
-template <int G>
-__device__ __forceinline__ void column_body(const int* __restrict__ col, const float* __restrict__ val,
-                                            const int* __restrict__ seg_lo, const int* __restrict__ seg_hi,
-                                            int V, int base, const float* smask, float* __restrict__ out,
-                                            int stride) {
-    const int lane = threadIdx.x & 31;
-    const int sub = lane % G;
-    constexpr int RPW = 32 / G;
-    const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int n_warps = (gridDim.x * blockDim.x) >> 5;
-    const int n_tiles = (V + RPW - 1) / RPW;
-    // the next tile's segment bounds are loaded while this tile's entries are
-    int row = warp_global * RPW + lane / G;
-    int lo = 0, hi = 0;
-    if (warp_global < n_tiles && row < V) {
-        lo = seg_lo[row];
-        hi = seg_hi[row];
-    }
-    for (int t = warp_global; t < n_tiles; t += n_warps) {
-        const int row_c = row, lo_c = lo, hi_c = hi;
-        row = (t + n_warps) * RPW + lane / G;
-        lo = hi = 0;
-        if (t + n_warps < n_tiles && row < V) {
-            lo = seg_lo[row];
-            hi = seg_hi[row];
-        }
-        float acc = 0.f;
-        for (int p = lo_c + sub; p < hi_c; p += G) acc = fmaf(__ldg(val + p), smask[__ldg(col + p) - base], acc);
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-        if (row_c < V && sub == 0) out[(size_t)row_c * stride] = acc;
-    }
 }
 
 template <int G>
@@ -259,7 +182,7 @@ __global__ void __launch_bounds__(256) k_column(const int* __restrict__ col, con
     extern __shared__ float smask[];
     for (int i = threadIdx.x; i < nb; i += blockDim.x) smask[i] = mask[i];
     __syncthreads();
-    column_body<G>(col, val, seg_lo, seg_hi, V, base, smask, out, stride);
+    column_body<G>(col, val, seg_lo, seg_hi, V, base, smask, out, stride, (int)(blockIdx.x * blockDim.x), (int)(gridDim.x * blockDim.x));
 }
 
 // The same for the aperture at pool index K-1 of the device table, into
@@ -278,7 +201,7 @@ __global__ void __launch_bounds__(256) k_column_dev(const int* __restrict__ col,
     for (int i = threadIdx.x; i < nb; i += blockDim.x) smask[i] = mask[i];
     __syncthreads();
     column_body<G>(col, val, seg + (size_t)b * V, seg + (size_t)(b + 1) * V, V, beam_off[b], smask,
-                   slab + (size_t)(K - 1) * ld, 1);
+                   slab + (size_t)(K - 1) * ld, 1, (int)(blockIdx.x * blockDim.x), (int)(gridDim.x * blockDim.x));
 }
 
 // ---- Eq. 7 ------------------------------------------------------------------
@@ -300,32 +223,6 @@ __global__ void k_fluence(const int* __restrict__ ap_beam, const int* __restrict
 
 // ---- 16-bit storage (a6): values D_ij / s_i in FP16 or BF16, per-beamlet FP32
 // scale s_i, FP32 accumulation ------------------------------------------------
-template <bool BF>
-__device__ __forceinline__ float2 unpack2(unsigned w) {
-    if (BF) {
-        __nv_bfloat162 h;
-        *reinterpret_cast<unsigned*>(&h) = w;
-        return __bfloat1622float2(h);
-    } else {
-        __half2 h;
-        *reinterpret_cast<unsigned*>(&h) = w;
-        return __half22float2(h);
-    }
-}
-
-template <bool BF>
-__device__ __forceinline__ float unpack1(unsigned short b) {
-    if (BF) {
-        __nv_bfloat16 h;
-        *reinterpret_cast<unsigned short*>(&h) = b;
-        return __bfloat162float(h);
-    } else {
-        __half h;
-        *reinterpret_cast<unsigned short*>(&h) = b;
-        return __half2float(h);
-    }
-}
-
 // a1 with rows padded to 8 entries: uint4 loads of 8 uint16 columns and 8 values;
 // x pre-multiplied by the beamlet scale in shared memory (or, when N floats do
 // not fit in 48 KB, the product formed from global memory per entry).
@@ -415,61 +312,9 @@ __global__ void __launch_bounds__(BT) k_dt16(const int* __restrict__ rowptr, con
     dt_round_snapshot(rt);
     if (skip != nullptr && *skip) return;
     const int row = order[blockIdx.x];  // longest rows first
-    const int p0 = rowptr[row] >> 3, p1 = rowptr[row + 1] >> 3;
-    float acc = 0.f;
-    for (int p = p0 + threadIdx.x; p < p1; p += BT) {
-        const int4 c0 = __ldg(col4 + 2 * p);
-        const int4 c1 = __ldg(col4 + 2 * p + 1);
-        const uint4 vw = __ldg(val8 + p);
-        const float2 a = unpack2<BF>(vw.x), b = unpack2<BF>(vw.y), c = unpack2<BF>(vw.z), d = unpack2<BF>(vw.w);
-        acc = fmaf(a.x, __ldg(pi + c0.x), acc);
-        acc = fmaf(a.y, __ldg(pi + c0.y), acc);
-        acc = fmaf(b.x, __ldg(pi + c0.z), acc);
-        acc = fmaf(b.y, __ldg(pi + c0.w), acc);
-        acc = fmaf(c.x, __ldg(pi + c1.x), acc);
-        acc = fmaf(c.y, __ldg(pi + c1.y), acc);
-        acc = fmaf(d.x, __ldg(pi + c1.z), acc);
-        acc = fmaf(d.y, __ldg(pi + c1.w), acc);
-    }
-    const double sres = block_sum_mixed<BT>(acc, s_red);
-    if (threadIdx.x == 0) w[row] = (float)(sres * (double)scale[row]);
+    const float s = dt16_row_sum<BT, BF>(rowptr, col4, val8, scale, row, pi, s_red);
+    if (threadIdx.x == 0) w[row] = s;
     dt_row_ticket(rt, row, w);
-}
-
-// a4 over beam b's segment of each row; the mask is pre-multiplied by the scales.
-template <int G, bool BF>
-__device__ __forceinline__ void column16_body(const unsigned short* __restrict__ col,
-                                              const unsigned short* __restrict__ val,
-                                              const int* __restrict__ seg_lo, const int* __restrict__ seg_hi, int V,
-                                              int base, const float* smask, float* __restrict__ out, int stride) {
-    const int lane = threadIdx.x & 31;
-    const int sub = lane % G;
-    constexpr int RPW = 32 / G;
-    const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int n_warps = (gridDim.x * blockDim.x) >> 5;
-    const int n_tiles = (V + RPW - 1) / RPW;
-    // the next tile's segment bounds are loaded while this tile's entries are
-    int row = warp_global * RPW + lane / G;
-    int lo = 0, hi = 0;
-    if (warp_global < n_tiles && row < V) {
-        lo = seg_lo[row];
-        hi = seg_hi[row];
-    }
-    for (int t = warp_global; t < n_tiles; t += n_warps) {
-        const int row_c = row, lo_c = lo, hi_c = hi;
-        row = (t + n_warps) * RPW + lane / G;
-        lo = hi = 0;
-        if (t + n_warps < n_tiles && row < V) {
-            lo = seg_lo[row];
-            hi = seg_hi[row];
-        }
-        float acc = 0.f;
-        for (int p = lo_c + sub; p < hi_c; p += G)
-            acc = fmaf(unpack1<BF>(__ldg(val + p)), smask[__ldg(col + p) - base], acc);
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-        if (row_c < V && sub == 0) out[(size_t)row_c * stride] = acc;
-    }
 }
 
 template <int G, bool BF>
@@ -482,7 +327,7 @@ __global__ void __launch_bounds__(256) k_column16(const unsigned short* __restri
     extern __shared__ float smask[];
     for (int i = threadIdx.x; i < nb; i += blockDim.x) smask[i] = mask[i] * scale[base + i];
     __syncthreads();
-    column16_body<G, BF>(col, val, seg_lo, seg_hi, V, base, smask, out, stride);
+    column16_body<G, BF>(col, val, seg_lo, seg_hi, V, base, smask, out, stride, (int)(blockIdx.x * blockDim.x), (int)(gridDim.x * blockDim.x));
 }
 
 template <int G, bool BF>
@@ -503,7 +348,8 @@ __global__ void __launch_bounds__(256) k_column16_dev(const unsigned short* __re
     for (int i = threadIdx.x; i < nb; i += blockDim.x) smask[i] = mask[i] * scale[base + i];
     __syncthreads();
     column16_body<G, BF>(col, val, seg + (size_t)b * V, seg + (size_t)(b + 1) * V, V, base, smask,
-                         slab + (size_t)(K - 1) * ld, 1);
+                         slab + (size_t)(K - 1) * ld, 1, (int)(blockIdx.x * blockDim.x),
+                         (int)(gridDim.x * blockDim.x));
 }
 
 // The device-driven round's beam decision fused with the new aperture's
@@ -571,9 +417,9 @@ __global__ void __launch_bounds__(256) k_commit_column(const int* __restrict__ c
     const int* seg_lo = ca.seg + (size_t)b * V;
     const int* seg_hi = ca.seg + (size_t)(b + 1) * V;
     if constexpr (PREC == DAO_PREC_FP32)
-        column_body<G>(col, val, seg_lo, seg_hi, V, base, smask, out, 1);
+        column_body<G>(col, val, seg_lo, seg_hi, V, base, smask, out, 1, (int)(blockIdx.x * blockDim.x), (int)(gridDim.x * blockDim.x));
     else
-        column16_body<G, PREC == DAO_PREC_BF16>(col16, val16, seg_lo, seg_hi, V, base, smask, out, 1);
+        column16_body<G, PREC == DAO_PREC_BF16>(col16, val16, seg_lo, seg_hi, V, base, smask, out, 1, (int)(blockIdx.x * blockDim.x), (int)(gridDim.x * blockDim.x));
 }
 
 // Blocks of a grid-stride kernel that are all resident at once (every block

@@ -1,0 +1,205 @@
+// Device bodies of the sparse kernels shared by the stand-alone kernels
+// (spmv.cu) and the plan-per-group kernel (master.cu): the block sum of the
+// transposed SpMV, one beamlet row of D^T (a2, the bracketed sum of Eq. 8),
+// the aperture column over a beam's segment of each voxel row (a4, Eq. 2),
+// and the 16-bit unpacking.  Fixed summation orders: a row's result depends
+// only on the block size (a2) or on the lanes per voxel row (a4), not on
+// which block or warp computes it.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "dao_internal.h"
+
+namespace dao {
+namespace {
+
+// Sum over a block: FP32 within each warp, FP64 across the warps (FP64 issues
+// at 1/64 of the FP32 rate on this part, so it is kept to one lane per warp).
+template <int NT>
+__device__ __forceinline__ double block_sum_mixed(float v, double* s_red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) s_red[warp] = (double)v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) t += s_red[w];
+    return t;
+}
+
+template <bool BF>
+__device__ __forceinline__ float2 unpack2(unsigned w) {
+    if (BF) {
+        __nv_bfloat162 h;
+        *reinterpret_cast<unsigned*>(&h) = w;
+        return __bfloat1622float2(h);
+    } else {
+        __half2 h;
+        *reinterpret_cast<unsigned*>(&h) = w;
+        return __half22float2(h);
+    }
+}
+
+template <bool BF>
+__device__ __forceinline__ float unpack1(unsigned short b) {
+    if (BF) {
+        __nv_bfloat16 h;
+        *reinterpret_cast<unsigned short*>(&h) = b;
+        return __bfloat162float(h);
+    } else {
+        __half h;
+        *reinterpret_cast<unsigned short*>(&h) = b;
+        return __half2float(h);
+    }
+}
+
+// a2, one beamlet row of D^T by a block of BT threads (every thread calls it);
+// the result is valid in thread 0.  Software pipeline: the next group's indices
+// and values (DRAM) are in flight while the current group's pi gathers (L2)
+// and products run.
+// COHERENT: pi is read through L2 (__ldcg), for a kernel in which other blocks
+// wrote it; otherwise through the read-only path.
+template <bool COHERENT>
+__device__ __forceinline__ float dt_gather(const float* __restrict__ pi, int j) {
+    return COHERENT ? __ldcg(pi + j) : __ldg(pi + j);
+}
+
+template <int BT, bool COHERENT = false>
+__device__ __forceinline__ float dt_row_sum(const int* __restrict__ rowptr, const int4* __restrict__ col4,
+                                            const float4* __restrict__ val4, int row, const float* __restrict__ pi,
+                                            double* s_red) {
+    const int p0 = rowptr[row] >> 2, p1 = rowptr[row + 1] >> 2;
+    float acc = 0.f;
+    int p = p0 + (int)threadIdx.x;
+    int4 cn = make_int4(0, 0, 0, 0);
+    float4 vn = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (p < p1) {
+        cn = __ldg(col4 + p);
+        vn = __ldg(val4 + p);
+    }
+    while (p < p1) {
+        const int4 c = cn;
+        const float4 v = vn;
+        p += BT;
+        if (p < p1) {
+            cn = __ldg(col4 + p);
+            vn = __ldg(val4 + p);
+        }
+        const float a0 = dt_gather<COHERENT>(pi, c.x), a1 = dt_gather<COHERENT>(pi, c.y),
+                    a2 = dt_gather<COHERENT>(pi, c.z), a3 = dt_gather<COHERENT>(pi, c.w);
+        acc = fmaf(v.x, a0, acc);
+        acc = fmaf(v.y, a1, acc);
+        acc = fmaf(v.z, a2, acc);
+        acc = fmaf(v.w, a3, acc);
+    }
+    return (float)block_sum_mixed<BT>(acc, s_red);
+}
+
+// a2 with rows padded to 8 entries: two int4 loads of voxel indices and one uint4
+// of values per 8 entries; the row's scale is applied once at the end.
+template <int BT, bool BF, bool COHERENT = false>
+__device__ __forceinline__ float dt16_row_sum(const int* __restrict__ rowptr, const int4* __restrict__ col4,
+                                              const uint4* __restrict__ val8, const float* __restrict__ scale, int row,
+                                              const float* __restrict__ pi, double* s_red) {
+    const int p0 = rowptr[row] >> 3, p1 = rowptr[row + 1] >> 3;
+    float acc = 0.f;
+    for (int p = p0 + (int)threadIdx.x; p < p1; p += BT) {
+        const int4 c0 = __ldg(col4 + 2 * p);
+        const int4 c1 = __ldg(col4 + 2 * p + 1);
+        const uint4 vw = __ldg(val8 + p);
+        const float2 a = unpack2<BF>(vw.x), b = unpack2<BF>(vw.y), c = unpack2<BF>(vw.z), d = unpack2<BF>(vw.w);
+        acc = fmaf(a.x, dt_gather<COHERENT>(pi, c0.x), acc);
+        acc = fmaf(a.y, dt_gather<COHERENT>(pi, c0.y), acc);
+        acc = fmaf(b.x, dt_gather<COHERENT>(pi, c0.z), acc);
+        acc = fmaf(b.y, dt_gather<COHERENT>(pi, c0.w), acc);
+        acc = fmaf(c.x, dt_gather<COHERENT>(pi, c1.x), acc);
+        acc = fmaf(c.y, dt_gather<COHERENT>(pi, c1.y), acc);
+        acc = fmaf(d.x, dt_gather<COHERENT>(pi, c1.z), acc);
+        acc = fmaf(d.y, dt_gather<COHERENT>(pi, c1.w), acc);
+    }
+    const double sres = block_sum_mixed<BT>(acc, s_red);
+    return (float)(sres * (double)scale[row]);
+}
+
+// ---- a4 ---------------------------------------------------------------------
+// The caller's threads are [wbase, wbase + blockDim) of wcount threads sharing
+// the rows (a grid, or a group of blocks).
+// G lanes per voxel row over the row's segment of beam b (columns base ..
+// base + nb - 1); mask[c] in {0, 1} marks the aperture's open beamlets.
+template <int G>
+__device__ __forceinline__ void column_body(const int* __restrict__ col, const float* __restrict__ val,
+                                            const int* __restrict__ seg_lo, const int* __restrict__ seg_hi,
+                                            int V, int base, const float* smask, float* __restrict__ out,
+                                            int stride, int wbase, int wcount) {
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % G;
+    constexpr int RPW = 32 / G;
+    const int warp_global = (wbase + (int)threadIdx.x) >> 5;
+    const int n_warps = wcount >> 5;
+    const int n_tiles = (V + RPW - 1) / RPW;
+    // the next tile's segment bounds are loaded while this tile's entries are
+    int row = warp_global * RPW + lane / G;
+    int lo = 0, hi = 0;
+    if (warp_global < n_tiles && row < V) {
+        lo = seg_lo[row];
+        hi = seg_hi[row];
+    }
+    for (int t = warp_global; t < n_tiles; t += n_warps) {
+        const int row_c = row, lo_c = lo, hi_c = hi;
+        row = (t + n_warps) * RPW + lane / G;
+        lo = hi = 0;
+        if (t + n_warps < n_tiles && row < V) {
+            lo = seg_lo[row];
+            hi = seg_hi[row];
+        }
+        float acc = 0.f;
+        for (int p = lo_c + sub; p < hi_c; p += G) acc = fmaf(__ldg(val + p), smask[__ldg(col + p) - base], acc);
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (row_c < V && sub == 0) out[(size_t)row_c * stride] = acc;
+    }
+}
+
+// a4 over beam b's segment of each row; the mask is pre-multiplied by the scales.
+template <int G, bool BF>
+__device__ __forceinline__ void column16_body(const unsigned short* __restrict__ col,
+                                              const unsigned short* __restrict__ val,
+                                              const int* __restrict__ seg_lo, const int* __restrict__ seg_hi, int V,
+                                              int base, const float* smask, float* __restrict__ out, int stride,
+                                              int wbase, int wcount) {
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % G;
+    constexpr int RPW = 32 / G;
+    const int warp_global = (wbase + (int)threadIdx.x) >> 5;
+    const int n_warps = wcount >> 5;
+    const int n_tiles = (V + RPW - 1) / RPW;
+    // the next tile's segment bounds are loaded while this tile's entries are
+    int row = warp_global * RPW + lane / G;
+    int lo = 0, hi = 0;
+    if (warp_global < n_tiles && row < V) {
+        lo = seg_lo[row];
+        hi = seg_hi[row];
+    }
+    for (int t = warp_global; t < n_tiles; t += n_warps) {
+        const int row_c = row, lo_c = lo, hi_c = hi;
+        row = (t + n_warps) * RPW + lane / G;
+        lo = hi = 0;
+        if (t + n_warps < n_tiles && row < V) {
+            lo = seg_lo[row];
+            hi = seg_hi[row];
+        }
+        float acc = 0.f;
+        for (int p = lo_c + sub; p < hi_c; p += G)
+            acc = fmaf(unpack1<BF>(__ldg(val + p)), smask[__ldg(col + p) - base], acc);
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (row_c < V && sub == 0) out[(size_t)row_c * stride] = acc;
+    }
+}
+
+}  // namespace
+}  // namespace dao
