@@ -336,14 +336,12 @@ def batch_instances(n_each):
 
 
 def run_batch(torch, dev, flush, cases, n_each, apertures):
-    """Batched re-plans in three forms, against the same plans one after another:
+    """Batched re-plans in two forms, against the same plans one after another:
       - per-stream: dao_batch_solve, each instance's rounds as its own CUDA
         graphs on its own stream, master problems by the per-kernel path (its
         small kernels from many instances overlap on the GPU);
       - fused: dao_batch_solve_persistent, every round's master solves of all
-        instances in one cooperative launch, a group of blocks per instance;
-      - grouped: dao_batch_solve_grouped, every instance's whole column
-        generation in one cooperative launch, a group of blocks per instance.
+        instances in one cooperative launch, a group of blocks per instance.
     H&N instances use FP16 storage; launch shapes come from the autotuner."""
     import tempfile
     from paper_1003_5402_gb300 import Plan, binding
@@ -371,21 +369,19 @@ def run_batch(torch, dev, flush, cases, n_each, apertures):
         t_stream, res_s = timed(lambda: binding.batch_solve(plans, apertures))
         binding.batch_solve(plans, apertures, persistent=True)   # warm: captures the fused graph
         t_fused, res_f = timed(lambda: binding.batch_solve(plans, apertures, persistent=True))
-        binding.batch_solve(plans, apertures, grouped=True)
-        t_group, res_g = timed(lambda: binding.batch_solve(plans, apertures, grouped=True))
         t_seq, _ = timed(lambda: [p.solve(apertures) for p in plans])
         n = len(plans)
-        forms = {"per-stream": t_stream, "fused": t_fused, "grouped": t_group}
+        forms = {"per-stream": t_stream, "fused": t_fused}
         best_form = min(forms, key=forms.get)
         best = forms[best_form]
         return {"instances": n, "workloads": f"{n_each} prostate-shaped FP32 + {n_each} H&N-shaped FP16, "
                                              f"perturbed (seeds 4000+i), {apertures} apertures each",
                 "form": best_form,
-                "plans_per_s_batched": round(n / best, 2), "plans_per_s_grouped": round(n / t_group, 2),
+                "plans_per_s_batched": round(n / best, 2),
                 "plans_per_s_fused": round(n / t_fused, 2), "plans_per_s_per_stream": round(n / t_stream, 2),
                 "plans_per_s_sequential": round(n / t_seq, 2), "speedup": round(t_seq / best, 3),
                 "fused_blocks_per_plan": int(binding.load().dao_batch_group_size(n, dev)),
-                "apertures_done": sorted({r[1] for r in res_f} | {r[1] for r in res_s} | {r[1] for r in res_g}),
+                "apertures_done": sorted({r[1] for r in res_f} | {r[1] for r in res_s}),
                 "timing": "host wall clock around the synchronous calls, L2 flushed before each, best of 2"}
     finally:
         for p in plans:

@@ -429,19 +429,8 @@ dao_status dao_batch_solve(dao_ctx* const* ctxs, int32_t n, int32_t n_apertures,
  * plan a block (n > 2 x SMs).  Synchronous. */
 dao_status dao_batch_solve_persistent(dao_ctx* const* ctxs, int32_t n, int32_t n_apertures, int32_t* n_done,
                                       double* traces, int32_t* status);
-/* Column generation for n independent contexts in ONE cooperative launch: plan
- * g runs every one of its rounds (D^T with 256 threads per beamlet row, the
- * MLC-row search, the beam decision and new column, the master solve) on its
- * own group of blocks with its own barriers, so no plan waits for another
- * between rounds.  Consecutive-leaf pricing only (DAO_MLC_CONSECUTIVE), at
- * most 64 beams per plan.  Arguments and results as dao_batch_solve; a plan's
- * results are those of solving it alone with master_blocks =
- * dao_batch_group_size(n) and dt_threads = 256.  Synchronous. */
-dao_status dao_batch_solve_grouped(dao_ctx* const* ctxs, int32_t n, int32_t n_apertures, int32_t* n_done,
-                                   double* traces, int32_t* status);
 
-/* Blocks per plan of dao_batch_solve_persistent and dao_batch_solve_grouped for
- * n plans on device `device` (0 when n plans do not fit one launch): a plan
+/* Blocks per plan of dao_batch_solve_persistent for n plans on device `device` (0 when n plans do not fit one launch): a plan
  * created with this master_blocks solves alone exactly as it does in the
  * batch. */
 int32_t dao_batch_group_size(int32_t n, int32_t device);

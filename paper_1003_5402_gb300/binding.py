@@ -136,7 +136,6 @@ SIGNATURES = {
     "dao_batch_solve": (C.c_int, [C.POINTER(_P), C.c_int32, C.c_int32, _I32P, _F64P, _I32P]),
     "dao_batch_solve_persistent": (C.c_int, [C.POINTER(_P), C.c_int32, C.c_int32, _I32P, _F64P, _I32P]),
     "dao_batch_group_size": (C.c_int32, [C.c_int32, C.c_int32]),
-    "dao_batch_solve_grouped": (C.c_int, [C.POINTER(_P), C.c_int32, C.c_int32, _I32P, _F64P, _I32P]),
     "dao_autotune": (C.c_int, [_P, C.c_char_p, C.POINTER(dao_tuning)]),
     "dao_server_options_default": (None, [C.POINTER(dao_server_options)]),
     "dao_server_create": (C.c_int, [C.POINTER(dao_server_options), C.POINTER(_P)]),
@@ -555,19 +554,17 @@ def dose_objective_noalloc(row_ptr, col, val, x, voxel_struct, terms, z, grad=No
     return _check(st, "dao_dose_objective_noalloc")
 
 
-def batch_solve(plans: Sequence["Plan"], n_apertures: int, persistent: bool = False, grouped: bool = False):
+def batch_solve(plans: Sequence["Plan"], n_apertures: int, persistent: bool = False):
     """dao_batch_solve: column generation for several plans at once (each on its
     own stream); ``persistent``: dao_batch_solve_persistent, every round's master
-    solves in one launch; ``grouped``: dao_batch_solve_grouped, every plan's
-    whole column generation on its own group of blocks in one launch.  Returns [(status, pool size, objective trace)] per plan, as
-    Plan.solve returns them (the trace NaN past the apertures added)."""
+    solves in one launch.  Returns [(status, pool size, objective trace)] per
+    plan, as Plan.solve returns them (the trace NaN past the apertures added)."""
     n = len(plans)
     arr = (C.c_void_p * max(n, 1))(*[p.h.value for p in plans])
     n_done = np.zeros(max(n, 1), dtype=np.int32)
     status = np.zeros(max(n, 1), dtype=np.int32)
     traces = np.full((max(n, 1), max(n_apertures, 1)), np.nan)
-    fn = (load().dao_batch_solve_grouped if grouped else
-          load().dao_batch_solve_persistent if persistent else load().dao_batch_solve)
+    fn = load().dao_batch_solve_persistent if persistent else load().dao_batch_solve
     _check(fn(C.cast(arr, C.POINTER(C.c_void_p)), n, int(n_apertures), _ptr(n_done, C.c_int32),
               _ptr(traces, C.c_double), _ptr(status, C.c_int32)), "dao_batch_solve")
     return [(int(status[i]), int(n_done[i]), traces[i, :n_apertures].copy()) for i in range(n)]

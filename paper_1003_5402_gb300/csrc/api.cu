@@ -2218,135 +2218,6 @@ dao_status dao_batch_solve_persistent(dao_ctx* const* ctxs, int32_t n, int32_t n
     return DAO_OK;
 }
 
-dao_status dao_batch_solve_grouped(dao_ctx* const* ctxs, int32_t n, int32_t n_apertures, int32_t* n_done,
-                                   double* traces, int32_t* status) {
-    TraceRange range("dao_batch_solve_grouped");
-    if (n < 0 || n_apertures < 0 || (n > 0 && ctxs == nullptr))
-        return fail(DAO_EINVAL, "n >= 0, n_apertures >= 0 and a context array are required");
-    for (int i = 0; i < n; ++i) {
-        if (ctxs[i] == nullptr) return fail(DAO_EINVAL, "null context " + std::to_string(i));
-        if (ctxs[i]->prof_on) return fail(DAO_EINVAL, "every context needs profiling off");
-        if (ctxs[i]->device != ctxs[0]->device) return fail(DAO_EINVAL, "the contexts must be on one device");
-        if (ctxs[i]->opt.mlc_constraint != DAO_MLC_CONSECUTIVE)
-            return fail(DAO_EINVAL, "the grouped batch prices with consecutive leaves only (dao_batch_solve_persistent "
-                                    "takes MLC constraints)");
-        if (ctxs[i]->B > 64) return fail(DAO_EINVAL, "the grouped batch takes at most 64 beams per plan");
-        for (int j = 0; j < i; ++j)
-            if (ctxs[j] == ctxs[i]) return fail(DAO_EINVAL, "context listed twice");
-    }
-    if (n == 0) return DAO_OK;
-    dao_ctx* c0 = ctxs[0];
-    DAO_TRY(check_ctx(c0));
-    const int GB = master_batch_group(n, c0->num_sms);
-    if (GB < 1) return fail(DAO_EINVAL, "too many plans for one launch (two blocks per SM each)");
-    std::vector<GraphSolve> gs(n);
-    std::vector<MasterTask> mt(n);
-    std::vector<RoundTask> rt(n);
-    int max_V = 0;
-    for (int i = 0; i < n; ++i) {
-        dao_ctx* c = ctxs[i];
-        gs[i].K0 = c->K;
-        gs[i].K1 = std::min(c->K_cap, c->K + n_apertures);
-        if (status) status[i] = DAO_OK;
-        if (n_done) n_done[i] = c->K;
-        MasterTask& t = mt[i];
-        t = MasterTask{};
-        t.slab = c->slab;
-        t.ld = c->ld;
-        t.V = c->V;
-        t.GS = c->mb.GH;
-        t.S = c->S;
-        t.max_iter = c->opt.max_master_iters;
-        t.capw = master_persist_capw(c->V, GB);
-        t.st = c->mb.st;
-        t.gb = c->mb.bar;
-        t.H_part = c->mb.H_part;
-        t.g_part = c->mb.g_part;
-        t.gn_part = c->mb.gn_part;
-        t.F_part = c->mb.F_part;
-        t.vstruct = c->vstruct;
-        t.tf = c->tf;
-        t.tol_rel = c->opt.master_tol;
-        t.skip = nullptr;
-        t.z_out = c->z;
-        t.pi_out = c->pi;
-        t.cg = c->cg;
-        RoundTask& r = rt[i];
-        r = RoundTask{};
-        r.prec = c->opt.precision;
-        r.N = c->N;
-        r.V = c->V;
-        r.n_beams = c->B;
-        r.R_tot = c->R_tot;
-        r.lr_stride = 2 * c->max_rows;
-        r.max_nb = c->max_nb;
-        r.tau = c->tau;
-        r.dt_rowptr = c->Dt.rowptr;
-        r.dt_col = c->Dt.col;
-        r.dt_val = c->Dt.val;
-        r.dt_val16 = c->Dt.val16;
-        r.dt_order = c->Dt.order;
-        r.scale = c->D.scale;
-        r.d_col = c->D.col;
-        r.d_val = c->D.val;
-        r.d_col16 = c->D.col16;
-        r.d_val16 = c->D.val16;
-        r.seg = c->seg;
-        r.row_info = c->row_info;
-        r.beam_row0 = c->beam_row0_d;
-        r.rows = c->rows_d;
-        r.cols = c->cols_d;
-        r.beam_off = c->beam_off_d;
-        r.w = c->w;
-        r.row_v = c->row_v;
-        r.row_lr = c->row_lr;
-        r.ap_beam = c->ap_beam;
-        r.ap_lr = c->ap_lr;
-        max_V = std::max(max_V, c->V);
-        DAO_TRY(solve_state_begin(c, &gs[i]));
-    }
-    // the plans' state on their own streams, then the launch on the first plan's
-    // stream after all of them, then every plan's stream after the launch
-    cudaStream_t s0 = c0->stream;
-    cudaEvent_t ev = nullptr;
-    DAO_CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    struct EventGuard {
-        cudaEvent_t e;
-        ~EventGuard() { cudaEventDestroy(e); }
-    } guard{ev};
-    for (int i = 1; i < n; ++i) {
-        DAO_CU(cudaEventRecord(ev, ctxs[i]->stream));
-        DAO_CU(cudaStreamWaitEvent(s0, ev, 0));
-    }
-    void* dm = nullptr;
-    void* dr = nullptr;
-    DAO_CU(pool_alloc(&dm, sizeof(MasterTask) * n, c0->device, s0));
-    DAO_CU(pool_alloc(&dr, sizeof(RoundTask) * n, c0->device, s0));
-    DAO_CU(cudaMemcpyAsync(dm, mt.data(), sizeof(MasterTask) * n, cudaMemcpyHostToDevice, s0));
-    DAO_CU(cudaMemcpyAsync(dr, rt.data(), sizeof(RoundTask) * n, cudaMemcpyHostToDevice, s0));
-    int nl = 0;
-    const cudaError_t e = launch_plan_groups(static_cast<MasterTask*>(dm), static_cast<RoundTask*>(dr), n, GB, max_V,
-                                             s0, &nl);
-    pool_free(dm, s0);
-    pool_free(dr, s0);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(DAO_ECUDA, std::string("dao_batch_solve_grouped: ") + cudaGetErrorString(e));
-    }
-    DAO_CU(cudaEventRecord(ev, s0));
-    for (int i = 1; i < n; ++i) DAO_CU(cudaStreamWaitEvent(ctxs[i]->stream, ev, 0));
-    for (int i = 0; i < n; ++i) {
-        dao_ctx* c = ctxs[i];
-        dao_status res = DAO_OK;
-        DAO_TRY(solve_graph_end(c, gs[i], n_apertures, n_done ? n_done + i : nullptr,
-                                traces ? traces + (size_t)i * n_apertures : nullptr, &res, false));
-        if (i == 0) c->launches_i += nl;
-        c->count_launches();
-        if (status) status[i] = res;
-    }
-    return DAO_OK;
-}
-
 dao_status dao_autotune(dao_ctx* c, const char* cache_path, dao_tuning* out) {
     TraceRange range("dao_autotune");
     DAO_TRY(check_ctx(c));

@@ -398,38 +398,6 @@ struct MasterTask {
 // The rest of a plan's round for the kernel that runs whole plans, one per
 // group of blocks: D^T and its rows, the pricing data, D's beam segments for
 // the new column, the aperture table (consecutive-leaf pricing only).
-struct RoundTask {
-    int prec, N, V, n_beams, R_tot, lr_stride, max_nb;
-    double tau;
-    const int* dt_rowptr;
-    const int* dt_col;
-    const float* dt_val;
-    const unsigned short* dt_val16;
-    const int* dt_order;
-    const float* scale;
-    const int* d_col;
-    const float* d_val;
-    const unsigned short* d_col16;
-    const unsigned short* d_val16;
-    const int* seg;
-    const int4* row_info;
-    const int* beam_row0;
-    const int* rows;
-    const int* cols;
-    const int* beam_off;
-    float* w;
-    double* row_v;
-    int2* row_lr;
-    int* ap_beam;
-    int* ap_lr;
-};
-// Whole column generations of several plans in one cooperative launch: group
-// g (GB blocks) runs every round of plan g (D^T with 256 threads per row, the
-// row search, the beam decision and new column, the master solve) from the
-// pool size in its device state to K_end, with its own group barriers.
-cudaError_t launch_plan_groups(const MasterTask* tasks, const RoundTask* rtasks, int n_tasks, int GB, int max_V,
-                               cudaStream_t stream, int* launches);
-
 // Several plans' master solves in one cooperative launch, GB blocks each
 // (master_batch_group: the most for n_tasks plans with two blocks per SM);
 // tasks in device memory; max_V the largest voxel count.

@@ -32,8 +32,6 @@
 #include <algorithm>
 
 #include "dao_internal.h"
-#include "pricing.cuh"
-#include "spmv_body.cuh"
 
 #include <cmath>
 
@@ -1370,132 +1368,6 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const MasterTask t1, c
 }
 
 
-// Whole plans, one per group of GB blocks (the plan-per-group form of batched
-// re-plans): every round of plan g runs inside the launch with the group's own
-// barriers, so the plans do not wait for one another between rounds.  A round:
-//   1. w = D^T pi, beamlet rows (longest first) shared out over the group's
-//      blocks, each row by a whole block (the stand-alone kernel's arithmetic
-//      with 256 threads per row);
-//   2. the MLC-row search, one warp per row;
-//   3. the beam decision in every block (the same result everywhere), the
-//      aperture committed by the group's first block, the new column computed
-//      by all (8 lanes per voxel row, as the stand-alone column kernel);
-//   4. the master solve (master_solve_group).
-// Barriers between the steps are the group's bounded grid barriers.
-__global__ void __launch_bounds__(PT, 2) k_plan_group(const MasterTask* __restrict__ tasks,
-                                                   const RoundTask* __restrict__ rtasks, int GB) {
-    const int g = blockIdx.x / GB, bid = blockIdx.x % GB, G = GB;
-    const MasterTask& T = tasks[g];
-    const RoundTask& R = rtasks[g];
-    MasterDev* __restrict__ st = T.st;
-    GridBar* __restrict__ gb = T.gb;
-    CGDev* __restrict__ cg = T.cg;
-    extern __shared__ __align__(16) float pm[];
-    __shared__ unsigned s_target;
-    __shared__ int s_flag, s_go;
-    __shared__ double s_red[PT / 32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        const unsigned c = *reinterpret_cast<volatile unsigned*>(&gb->count);
-        s_target = c - c % (unsigned)G;
-        s_go = *reinterpret_cast<volatile unsigned*>(&gb->broken) == 0 && __ldcg(&cg->stop) == 0;
-    }
-    __syncthreads();
-    if (!s_go) return;
-    int K = __ldcg(&cg->K);
-    const int K_end = __ldcg(&cg->K_end);
-    auto fail_barrier = [&]() {
-        if (tid == 0) st->err = 2;
-    };
-    while (K < K_end) {
-        // 1. D^T
-        for (int i = bid; i < R.N; i += G) {
-            const int row = R.dt_order[i];
-            float v;
-            if (R.prec == DAO_PREC_FP32)
-                v = dt_row_sum<PT, true>(R.dt_rowptr, reinterpret_cast<const int4*>(R.dt_col),
-                                   reinterpret_cast<const float4*>(R.dt_val), row, T.pi_out, s_red);
-            else if (R.prec == DAO_PREC_FP16)
-                v = dt16_row_sum<PT, false, true>(R.dt_rowptr, reinterpret_cast<const int4*>(R.dt_col),
-                                            reinterpret_cast<const uint4*>(R.dt_val16), R.scale, row, T.pi_out, s_red);
-            else
-                v = dt16_row_sum<PT, true, true>(R.dt_rowptr, reinterpret_cast<const int4*>(R.dt_col),
-                                           reinterpret_cast<const uint4*>(R.dt_val16), R.scale, row, T.pi_out, s_red);
-            if (tid == 0) R.w[row] = v;
-            __syncthreads();  // s_red reused by the next row
-        }
-        if (!grid_sync(gb, G, &s_target, &s_flag)) {
-            fail_barrier();
-            break;
-        }
-        // 2. the row search, one warp per MLC row (w read through L2)
-        for (int r = bid * PW + warp; r < R.R_tot; r += G * PW) pricing::row_best(R.w, R.row_info[r], r, R.row_v, R.row_lr);
-        if (!grid_sync(gb, G, &s_target, &s_flag)) {
-            fail_barrier();
-            break;
-        }
-        // 3. the decision (identical in every block), the commit, the column
-        double* s_sum = reinterpret_cast<double*>(pm);              // n_beams
-        float* smask = reinterpret_cast<float*>(s_sum + R.n_beams);  // max_nb
-        int b = 0;
-        double rc = 0.0;
-        const int outcome = pricing::decide(R.row_v, R.beam_row0, R.n_beams, R.row_lr, R.rows, R.tau, K + 1,
-                                            R.lr_stride, R.ap_beam, R.ap_lr, s_sum, &b, &rc);
-        if (outcome != pricing::OUTCOME_NEW) {
-            if (bid == 0 && tid == 0) {
-                cg->done = outcome;
-                cg->stop = 1;
-            }
-            break;
-        }
-        K += 1;
-        const int Rb = R.rows[b], Cb = R.cols[b], r0 = R.beam_row0[b], base = R.beam_off[b];
-        if (bid == 0) {
-            if (tid == 0) R.ap_beam[K - 1] = b;
-            for (int r = tid; r < Rb; r += PT) {
-                const int2 lr = __ldcg(R.row_lr + r0 + r);
-                R.ap_lr[(K - 1) * R.lr_stride + 2 * r] = lr.x;
-                R.ap_lr[(K - 1) * R.lr_stride + 2 * r + 1] = lr.y;
-            }
-            if (tid == 0) cg->K = K;
-        }
-        for (int i = tid; i < Rb * Cb; i += PT) {
-            const int2 lr = __ldcg(R.row_lr + r0 + i / Cb);
-            const int c = i % Cb;
-            const float m = (c >= lr.x && c < lr.y) ? 1.f : 0.f;
-            smask[i] = R.prec == DAO_PREC_FP32 ? m : m * R.scale[base + i];
-        }
-        __syncthreads();
-        float* out = const_cast<float*>(T.slab) + (size_t)(K - 1) * T.ld;
-        const int* seg_lo = R.seg + (size_t)b * R.V;
-        const int* seg_hi = R.seg + (size_t)(b + 1) * R.V;
-        if (R.prec == DAO_PREC_FP32)
-            column_body<8>(R.d_col, R.d_val, seg_lo, seg_hi, R.V, base, smask, out, 1, bid * PT, G * PT);
-        else if (R.prec == DAO_PREC_FP16)
-            column16_body<8, false>(R.d_col16, R.d_val16, seg_lo, seg_hi, R.V, base, smask, out, 1, bid * PT, G * PT);
-        else
-            column16_body<8, true>(R.d_col16, R.d_val16, seg_lo, seg_hi, R.V, base, smask, out, 1, bid * PT, G * PT);
-        if (!grid_sync(gb, G, &s_target, &s_flag)) {
-            fail_barrier();
-            break;
-        }
-        // 4. the master solve at pool size K
-        const int KP = (K + 3) / 4 * 4;
-        master_solve_group(T.slab, T.ld, T.V, T.GS, T.S, T.max_iter, T.capw, st, gb, T.H_part, T.g_part, T.gn_part,
-                           T.F_part, T.vstruct, T.tf, T.tol_rel, T.z_out, T.pi_out, cg, bid, G, K, KP, master_kw(K),
-                           master_lanes(K), 1e-4, pm, &s_target, &s_flag);
-        if (tid == 0) s_go = __ldcg(&st->err) != 2;
-        __syncthreads();
-        if (!s_go) break;
-        // z and pi of every block's tiles are written: the next round's D^T reads pi
-        if (!grid_sync(gb, G, &s_target, &s_flag)) {
-            fail_barrier();
-            break;
-        }
-    }
-    if (bid == 0 && tid == 0 && K >= K_end) cg->stop = 1;
-}
-
 }  // namespace
 
 __host__ __device__ int master_kw(int K) {
@@ -1718,32 +1590,6 @@ cudaError_t launch_master_persist(const MasterBuffers& mb, const float* slab, in
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)k_master_persist<false>, args);
-    ++*launches;
-    return e;
-}
-
-cudaError_t launch_plan_groups(const MasterTask* tasks, const RoundTask* rtasks, int n_tasks, int GB, int max_V,
-                               cudaStream_t stream, int* launches) {
-    if (n_tasks < 1 || GB < 1) return cudaErrorInvalidConfiguration;
-    static bool configured = false;  // the attribute is the same for every launch
-    if (!configured) {
-        const cudaError_t e = cudaFuncSetAttribute(k_plan_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)PERSIST_SMEM_MAX);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    void* args[] = {(void*)&tasks, (void*)&rtasks, (void*)&GB};
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(n_tasks * GB);
-    cfg.blockDim = dim3(PT);
-    cfg.dynamicSmemBytes = master_persist_smem(max_V, GB);
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)k_plan_group, args);
     ++*launches;
     return e;
 }

@@ -105,7 +105,7 @@ __device__ __forceinline__ int decide(const double* __restrict__ row_v, const in
     const int tid = threadIdx.x;
     for (int b = tid; b < n_beams; b += blockDim.x) {
         double t = 0.0;
-        for (int r = beam_row0[b]; r < beam_row0[b + 1]; ++r) t = t + __ldcg(row_v + r);
+        for (int r = beam_row0[b]; r < beam_row0[b + 1]; ++r) t = t + row_v[r];
         s_sum[b] = t;
     }
     __syncthreads();
@@ -123,14 +123,12 @@ __device__ __forceinline__ int decide(const double* __restrict__ row_v, const in
     *rc_out = s_rc;
     if (!(s_rc < -tau)) return OUTCOME_OPTIMAL;
     const int R = rows[b], r0 = beam_row0[b];
-    // through L2 (__ldcg): in a kernel that runs whole plans, other blocks wrote
-    // the row results and the aperture table earlier in the same launch
     for (int k = tid; k < K - 1; k += blockDim.x) {
-        if (__ldcg(ap_beam + k) != b) continue;
+        if (ap_beam[k] != b) continue;
         bool same = true;
         for (int r = 0; r < R && same; ++r) {
-            const int2 lr = __ldcg(row_lr + r0 + r);
-            same = __ldcg(ap_lr + k * lr_stride + 2 * r) == lr.x && __ldcg(ap_lr + k * lr_stride + 2 * r + 1) == lr.y;
+            const int2 lr = row_lr[r0 + r];
+            same = ap_lr[k * lr_stride + 2 * r] == lr.x && ap_lr[k * lr_stride + 2 * r + 1] == lr.y;
         }
         if (same) s_dup = 1;
     }

@@ -1,5 +1,5 @@
-// Device bodies of the sparse kernels shared by the stand-alone kernels
-// (spmv.cu) and the plan-per-group kernel (master.cu): the block sum of the
+// Device bodies of the sparse kernels of spmv.cu (the stand-alone kernels and
+// the fused kernels of the device-driven round): the block sum of the
 // transposed SpMV, one beamlet row of D^T (a2, the bracketed sum of Eq. 8),
 // the aperture column over a beam's segment of each voxel row (a4, Eq. 2),
 // and the 16-bit unpacking.  Fixed summation orders: a row's result depends
@@ -61,14 +61,7 @@ __device__ __forceinline__ float unpack1(unsigned short b) {
 // the result is valid in thread 0.  Software pipeline: the next group's indices
 // and values (DRAM) are in flight while the current group's pi gathers (L2)
 // and products run.
-// COHERENT: pi is read through L2 (__ldcg), for a kernel in which other blocks
-// wrote it; otherwise through the read-only path.
-template <bool COHERENT>
-__device__ __forceinline__ float dt_gather(const float* __restrict__ pi, int j) {
-    return COHERENT ? __ldcg(pi + j) : __ldg(pi + j);
-}
-
-template <int BT, bool COHERENT = false>
+template <int BT>
 __device__ __forceinline__ float dt_row_sum(const int* __restrict__ rowptr, const int4* __restrict__ col4,
                                             const float4* __restrict__ val4, int row, const float* __restrict__ pi,
                                             double* s_red) {
@@ -89,8 +82,8 @@ __device__ __forceinline__ float dt_row_sum(const int* __restrict__ rowptr, cons
             cn = __ldg(col4 + p);
             vn = __ldg(val4 + p);
         }
-        const float a0 = dt_gather<COHERENT>(pi, c.x), a1 = dt_gather<COHERENT>(pi, c.y),
-                    a2 = dt_gather<COHERENT>(pi, c.z), a3 = dt_gather<COHERENT>(pi, c.w);
+        const float a0 = __ldg(pi + c.x), a1 = __ldg(pi + c.y),
+                    a2 = __ldg(pi + c.z), a3 = __ldg(pi + c.w);
         acc = fmaf(v.x, a0, acc);
         acc = fmaf(v.y, a1, acc);
         acc = fmaf(v.z, a2, acc);
@@ -101,7 +94,7 @@ __device__ __forceinline__ float dt_row_sum(const int* __restrict__ rowptr, cons
 
 // a2 with rows padded to 8 entries: two int4 loads of voxel indices and one uint4
 // of values per 8 entries; the row's scale is applied once at the end.
-template <int BT, bool BF, bool COHERENT = false>
+template <int BT, bool BF>
 __device__ __forceinline__ float dt16_row_sum(const int* __restrict__ rowptr, const int4* __restrict__ col4,
                                               const uint4* __restrict__ val8, const float* __restrict__ scale, int row,
                                               const float* __restrict__ pi, double* s_red) {
@@ -112,14 +105,14 @@ __device__ __forceinline__ float dt16_row_sum(const int* __restrict__ rowptr, co
         const int4 c1 = __ldg(col4 + 2 * p + 1);
         const uint4 vw = __ldg(val8 + p);
         const float2 a = unpack2<BF>(vw.x), b = unpack2<BF>(vw.y), c = unpack2<BF>(vw.z), d = unpack2<BF>(vw.w);
-        acc = fmaf(a.x, dt_gather<COHERENT>(pi, c0.x), acc);
-        acc = fmaf(a.y, dt_gather<COHERENT>(pi, c0.y), acc);
-        acc = fmaf(b.x, dt_gather<COHERENT>(pi, c0.z), acc);
-        acc = fmaf(b.y, dt_gather<COHERENT>(pi, c0.w), acc);
-        acc = fmaf(c.x, dt_gather<COHERENT>(pi, c1.x), acc);
-        acc = fmaf(c.y, dt_gather<COHERENT>(pi, c1.y), acc);
-        acc = fmaf(d.x, dt_gather<COHERENT>(pi, c1.z), acc);
-        acc = fmaf(d.y, dt_gather<COHERENT>(pi, c1.w), acc);
+        acc = fmaf(a.x, __ldg(pi + c0.x), acc);
+        acc = fmaf(a.y, __ldg(pi + c0.y), acc);
+        acc = fmaf(b.x, __ldg(pi + c0.z), acc);
+        acc = fmaf(b.y, __ldg(pi + c0.w), acc);
+        acc = fmaf(c.x, __ldg(pi + c1.x), acc);
+        acc = fmaf(c.y, __ldg(pi + c1.y), acc);
+        acc = fmaf(d.x, __ldg(pi + c1.z), acc);
+        acc = fmaf(d.y, __ldg(pi + c1.w), acc);
     }
     const double sres = block_sum_mixed<BT>(acc, s_red);
     return (float)(sres * (double)scale[row]);

@@ -235,70 +235,3 @@ def test_persistent_batch_of_full_size_instances_against_the_oracle(torch):
         for p in plans:
             p.close()
 
-
-def test_grouped_batch_equals_each_instance_alone_bitwise(torch):
-    """dao_batch_solve_grouped (every plan's whole column generation in one
-    cooperative launch, a group of blocks per plan): each instance's results
-    are bitwise those of solving it alone with the same group size and 256
-    threads per D^T row, for instances of different sizes and storage, on two
-    calls in a row."""
-    from paper_1003_5402_gb300 import Plan, binding
-    K = 12
-    inst = _instances()
-    GB = binding.load().dao_batch_group_size(len(inst), 0)
-    alone = []
-    for name, case, kw in inst:
-        with Plan(case, master_blocks=GB, dt_threads=256, **kw) as p:
-            alone.append(_snapshot(p, p.solve(K)))
-    plans = [Plan(case, **kw) for name, case, kw in inst]
-    try:
-        for call in range(2):
-            for p in plans:
-                p.reset()
-            res = binding.batch_solve(plans, K, grouped=True)
-            for (name, _, _), p, r, a in zip(inst, plans, res, alone):
-                _same(_snapshot(p, r), a)
-    finally:
-        for p in plans:
-            p.close()
-
-
-def test_grouped_batch_of_full_size_instances_against_the_oracle(torch):
-    """The grouped one-launch batch at the benchmark's sizes against the oracle:
-    each plan alone on the batch's group size (and 256 threads per D^T row)
-    passes the every-round oracle check, and the batch's result is bitwise that
-    plan; a pool limit (K_end) below the requested count stops each plan."""
-    from paper_1003_5402_gb300 import Plan, binding
-    from _helpers import quantized_case
-    from test_gpu_cg import _free_running_checked
-    K = 50
-    inst = [(P.make_case(P.perturb(P.spec_prostate(), 4003)), {"precision": 0}),
-            (P.make_case(P.perturb(P.spec_hn(), 4019)), {"precision": 1}),
-            (P.make_case(P.spec_tiny()), {"precision": 0})]
-    GB = binding.load().dao_batch_group_size(len(inst), 0)
-    checked = []
-    for case, kw in inst:
-        ref_case = case if kw["precision"] == 0 else quantized_case(case, "fp16")
-        checked.append(_free_running_checked(case, K, torch, plan_kw=dict(kw, master_blocks=GB, dt_threads=256),
-                                             ref_case=ref_case))
-    plans = [Plan(c, **kw) for c, kw in inst]
-    try:
-        res = binding.batch_solve(plans, K, grouped=True)
-        for p, r, ref in zip(plans, res, checked):
-            assert r[1] == K
-            aps = p.apertures()
-            assert all(x[0] == y[0] and np.array_equal(x[1], y[1]) for x, y in zip(aps, ref["apertures"]))
-            assert np.array_equal(p.intensities(), ref["y"])
-            z, F = p.dose()
-            assert np.array_equal(z, ref["z"]) and F == ref["F"]
-    finally:
-        for p in plans:
-            p.close()
-
-
-def test_grouped_batch_refuses_mlc_constraints(torch):
-    from paper_1003_5402_gb300 import DaoError, Plan, binding
-    with Plan(P.make_case(P.spec_micro()), mlc_constraint=binding.DAO_MLC_JAWS) as p:
-        with pytest.raises(DaoError) as e:
-            binding.batch_solve([p], 4, grouped=True)
-        assert e.value.status == -1

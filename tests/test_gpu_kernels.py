@@ -32,9 +32,9 @@ def torch():
     return t
 
 
-def _plan(case, torch):
+def _plan(case, torch, **opt):
     from paper_1003_5402_gb300 import Plan
-    return Plan(case, stream=torch.cuda.current_stream().cuda_stream)
+    return Plan(case, stream=torch.cuda.current_stream().cuda_stream, **opt)
 
 
 @pytest.mark.parametrize("name,case", CASES, ids=[c[0] for c in CASES])
@@ -66,11 +66,15 @@ def test_dose_spmv_and_epilogue(torch, name, case):
     assert abs(F - Fex) <= 1e-5 * abs(Fex) + 1e-300
 
 
+@pytest.mark.parametrize("dt_threads", [0, 128, 256])
 @pytest.mark.parametrize("name,case", CASES, ids=[c[0] for c in CASES])
-def test_transposed_spmv(torch, name, case):
+def test_transposed_spmv(torch, name, case, dt_threads):
+    """a2 with the default block size and with 128 or 256 threads per beamlet row
+    (dao_options.dt_threads): a thread's chain only gets shorter with more
+    threads, so the 64-thread bound holds for all."""
     rng = np.random.default_rng(2)
     pi = rng.normal(size=case.n_voxels).astype(np.float32)
-    with _plan(case, torch) as plan:
+    with _plan(case, torch, dt_threads=dt_threads) as plan:
         pd = torch.from_numpy(pi).cuda()
         wd = torch.empty(case.n_beamlets, dtype=torch.float32, device="cuda")
         plan.k_beamlet_prices(pd, wd)
