@@ -543,6 +543,16 @@ dao_status make_tensor_maps(dao_ctx* c) {
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(DAO_ECUDA, "cuTensorMapEncodeTiled failed with " + std::to_string((int)r));
     }
+    {  // the persistent solve's map: boxes of 128 voxels x 16 columns (x = 128 c, y = 16 q, both in range)
+        const cuuint64_t dims[2] = {(cuuint64_t)c->ld, (cuuint64_t)KMAX};
+        const cuuint64_t strides[1] = {(cuuint64_t)c->ld * sizeof(float)};
+        const cuuint32_t box[2] = {128u, 16u};
+        const cuuint32_t estr[2] = {1, 1};
+        CUresult r = encode(&c->mb.tmap_p, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->slab, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(DAO_ECUDA, "cuTensorMapEncodeTiled failed with " + std::to_string((int)r));
+    }
     return DAO_OK;
 }
 
@@ -582,6 +592,7 @@ dao_status alloc_state(dao_ctx* c) {
     for (int k = 0; k <= KMAX; ++k) c->mb.grid[k] = master_grid(c->V, c->num_sms, k);
     c->mb.GH = master_hess_grid(c->num_sms);
     DAO_TRY(c->dalloc(&c->mb.bar, 1));
+    DAO_TRY(c->dalloc(&c->mb.vstate, (size_t)std::max(c->V, 1)));
     DAO_CU(cudaMemsetAsync(c->mb.bar, 0, sizeof(GridBar), c->stream));
     c->mb.GP = c->opt.master_persistent ? master_persist_grid(c->V, c->num_sms, c->opt.master_blocks) : 0;
     if (c->mb.GP > c->mb.GH) c->mb.GP = c->mb.GH;  // the partial arrays have GH columns
@@ -593,6 +604,7 @@ dao_status alloc_state(dao_ctx* c) {
     DAO_TRY(c->dalloc(&c->mb.H_part, (size_t)KMAX * (KMAX + 1) / 2 * c->mb.GH));
     DAO_TRY(c->dalloc(&c->mb.g_part, (size_t)KMAX * c->mb.GH));
     DAO_TRY(c->dalloc(&c->mb.gn_part, (size_t)KMAX * c->mb.GH));
+    DAO_TRY(c->dalloc(&c->mb.H_keep, (size_t)KMAX * (KMAX + 1) / 2 * c->mb.GH));
     DAO_TRY(c->dalloc(&c->mb.F_part, (size_t)master_grid_max(c->num_sms)));
     c->F_blocks = dose_grid(c->V, c->num_sms);
     DAO_TRY(c->dalloc(&c->F_part, c->F_blocks));
@@ -2068,7 +2080,9 @@ dao_status build_batch_graph(dao_ctx* const* ctxs, int n, int R, BatchGraph* bg)
         t.z_out = c->z;
         t.pi_out = c->pi;
         t.cg = c->cg;
-        t.capw = master_persist_capw(c->V, bg->GB);
+        t.tmap = c->mb.tmap_p;
+        t.vstate = c->mb.vstate;
+        t.H_keep = c->mb.H_keep;
         max_V = std::max(max_V, c->V);
     }
     void* tp = nullptr;

@@ -100,6 +100,8 @@ struct MasterDev {
     int err;              // set when a tile copy of an evaluation never completed
     unsigned ticket;      // blocks of the reduce + step kernel that finished their share (0 between launches)
     int final_pending;    // the solve stopped at an accepted point other than the last one evaluated
+    int inc_G;            // persistent solve: group size whose kept partial H and voxel states are valid (0: none)
+    int inc_K;            // the pool size they were kept at
 };
 
 enum { MASTER_RUNNING = 0, MASTER_CONVERGED = 1, MASTER_MAXITER = 2, MASTER_STALLED = 3, MASTER_ERROR = 4 };
@@ -302,10 +304,14 @@ struct MasterBuffers {
     int GP = 0;                 // blocks of the persistent solve (co-resident), 0: not available
     int grid[KMAX + 1] = {};    // blocks of the evaluation kernel for each pool size
     CUtensorMap tmap[KMAX / 4 + 1];  // slab tile maps, indexed by columns / 4
+    CUtensorMap tmap_p;              // slab map of the persistent solve: boxes of 128 voxels x 16 columns
+    uint8_t* vstate = nullptr;       // [V] persistent solve: each voxel's curvature state at the last evaluation
+    float* H_keep = nullptr;         // [GH][KMAX*(KMAX+1)/2] persistent solve: each block's kept partial H
 };
 enum { PASS_EVAL = 0, PASS_FINAL = 1, PASS_TIMING = 2 };
 __host__ __device__ int master_kw(int K);
 __host__ __device__ int master_lanes(int K);
+__host__ __device__ int persist_lanes(int K);
 int master_grid(int V, int num_sms, int K);
 int master_grid_max(int num_sms);
 int master_hess_grid(int num_sms);
@@ -378,9 +384,9 @@ cudaError_t build_transpose_place(int prec, const int64_t* rp, const int* col, c
 // the slab and its partial arrays (stride GS), the objective terms, the
 // round's skip flag and outputs, and the device-side round state (pool size).
 struct MasterTask {
+    CUtensorMap tmap;     // the slab in boxes of 128 voxels x 16 columns (MasterBuffers::tmap_p)
     const float* slab;
     int ld, V, GS, S, max_iter;
-    int capw;             // active-list slots per warp (master_persist_capw of V and the group size)
     MasterDev* st;
     GridBar* gb;
     float* H_part;
@@ -394,15 +400,13 @@ struct MasterTask {
     float* z_out;
     float* pi_out;
     CGDev* cg;
+    uint8_t* vstate;      // MasterBuffers::vstate
+    float* H_keep;        // MasterBuffers::H_keep
 };
-// The rest of a plan's round for the kernel that runs whole plans, one per
-// group of blocks: D^T and its rows, the pricing data, D's beam segments for
-// the new column, the aperture table (consecutive-leaf pricing only).
 // Several plans' master solves in one cooperative launch, GB blocks each
 // (master_batch_group: the most for n_tasks plans with two blocks per SM);
 // tasks in device memory; max_V the largest voxel count.
 int master_batch_group(int n_tasks, int num_sms);
-int master_persist_capw(int V, int G);
 cudaError_t launch_master_persist_batch(const MasterTask* tasks, int n_tasks, int GB, int max_V, cudaStream_t stream,
                                         int* launches);
 

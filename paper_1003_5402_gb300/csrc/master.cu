@@ -45,6 +45,7 @@ constexpr int CH = 128;             // active voxels per Hessian sub-chunk
 constexpr float U32 = 5.9604645e-8f;  // 2^-24
 constexpr double NOISE = 64.0;
 constexpr int WAIT_LIMIT = 1 << 20;   // mbarrier polls before a copy is declared lost
+constexpr int HSTRIDE = KMAX * (KMAX + 1) / 2;  // packed curvature entries per block of the kept partial H
 
 __device__ __forceinline__ double warp_sum_f64(double v) {
 #pragma unroll
@@ -119,8 +120,13 @@ __device__ __forceinline__ void block_of(int eb, int KB, int& rb, int& cb) {
     cb = r + rem;
 }
 
-// Packed index of entry (r, c), r <= c, of the upper triangle of a K x K matrix.
-__device__ __forceinline__ int tri_index(int r, int c, int K) { return r * K - (r * (r - 1)) / 2 + (c - r); }
+// Packed index of entry (r, c), r <= c, of the upper triangle, column by column:
+// c (c + 1) / 2 + r, the same for every pool size K (a partial H kept from one
+// pool size to the next keeps its entries in place).
+__device__ __forceinline__ int tri_index(int r, int c, int K) {
+    (void)K;
+    return c * (c + 1) / 2 + r;
+}
 
 __global__ void k_master_init(MasterDev* __restrict__ st, int K, const int* __restrict__ skip,
                               cudaGraphConditionalHandle cond, int use_cond, GridBar* __restrict__ gb) {
@@ -300,6 +306,8 @@ __global__ void __launch_bounds__(256) k_master_hess(const float* __restrict__ a
                                                      double* __restrict__ g_part, float* __restrict__ gn_part, int G,
                                                      int mode) {
     if (mode == PASS_EVAL && st->done) return;
+    // the partial arrays are overwritten: the persistent solve's kept partial H is gone
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->inc_G = 0;
     extern __shared__ __align__(16) float smem[];
     int* s_pref = reinterpret_cast<int*>(smem);                        // [n_tiles + 1]
     float* Ac = smem + ((n_tiles + 1 + 3) / 4) * 4;                    // [CH][KW]
@@ -493,13 +501,11 @@ __device__ __forceinline__ void master_reduce_part(const float* __restrict__ H_p
         if (o < E) {  // the factorisation is FP32: so is this sum
             float s = lane_sum_strided(H_part + (size_t)o * GH, GC, lane);
             s = warp_sum_f32(s);
-            if (lane == 0) {
-                int r = 0, rem = o;
-                while (rem >= K - r) {
-                    rem -= K - r;
-                    ++r;
-                }
-                const int c = r + rem;
+            if (lane == 0) {  // o = c (c + 1) / 2 + r, r <= c
+                int c = (int)((sqrtf(8.f * (float)o + 1.f) - 1.f) * 0.5f);
+                while ((c + 1) * (c + 2) / 2 <= o) ++c;
+                while (c * (c + 1) / 2 > o) --c;
+                const int r = o - c * (c + 1) / 2;
                 st->Ht[r * KMAX + c] = s;
                 st->Ht[c * KMAX + r] = s;
             }
@@ -928,14 +934,20 @@ __global__ void __launch_bounds__(STEP_T, 1) k_master_reduce_step(const float* _
 }
 
 // ---- the master solve as one persistent cooperative kernel -------------------
-// All blocks are co-resident (cooperative launch).  Block b owns the 32-voxel
-// tiles b, b + G, b + 2G, ... of the slab (interleaved, so the active voxels of
-// a compact target spread evenly over the blocks).  Per Newton iteration:
-//   A. warp w of every block streams its tiles' slab columns from L2 (lane v =
-//      voxel v of the tile) into the compensated z, then pi, h, F; the active
-//      voxels (h > 0) go to the warp's list; the block accumulates its partial
-//      H, g and the rounding scale of g over its lists (rows re-read from L2 in
-//      chunks of CHP) and writes them to column b of the partial arrays;
+// All blocks are co-resident (cooperative launch).  Block b owns the chunks of
+// CHV = 128 voxels b, b + G, b + 2G, ... of the slab (interleaved, so the active
+// voxels of a compact target spread evenly over the blocks).  Per Newton
+// iteration:
+//   A. the chunk's slab columns arrive in shared memory by TMA (boxes of 128
+//      voxels x 16 columns, one mbarrier; the next chunk's copy is in flight
+//      while the current one is folded in, and the block's first chunk is
+//      fetched again for the next iteration as soon as its last one has been
+//      read: the slab does not change during a solve); warps 0-3 (lane = voxel)
+//      compute the compensated z, then pi, h, F, and copy the rows of the
+//      voxels with h > 0 to a compacted row-major buffer; every thread then
+//      accumulates its 4x4 block of the partial H (and g and the rounding
+//      scale of g) over those rows; after its chunks the block writes its
+//      partials to column b of the partial arrays;
 //   grid barrier;
 //   B. every block reduces its share of the outputs in a fixed order; the block
 //      that finishes last (ticket after a fence) takes the Newton step;
@@ -945,7 +957,10 @@ __global__ void __launch_bounds__(STEP_T, 1) k_master_reduce_step(const float* _
 // entry) and every block leaves at the next barrier or check.
 constexpr int PT = STEP_T;         // threads per block (the step body's layout)
 constexpr int PW = PT / 32;
-constexpr int CHP = 64;            // active voxels per H chunk
+constexpr int CHV = 128;           // voxels per chunk of the persistent pass
+constexpr int BOXC = 16;           // slab columns per TMA box of the persistent pass
+constexpr int NST_MAX = 4;         // copies in flight per block (when the pool is small enough)
+enum { MODE_FULL = 0, MODE_EXT = 1, MODE_INC = 2 };  // the kept partial H: rebuilt, extended by a column, updated
 constexpr int GRID_WAIT_LIMIT = 1 << 22;
 constexpr size_t PERSIST_SMEM_MAX = 150 * 1024;  // dynamic shared memory the kernel is configured for
 
@@ -989,20 +1004,27 @@ __device__ __forceinline__ bool grid_sync(GridBar* gb, unsigned nblocks, unsigne
 // based on the barrier counter).  Every block of the group calls it with the
 // same K.
 __device__ __forceinline__ void master_solve_group(
-    const float* __restrict__ slab, int ld, int V, int GS, int S, int max_iter, int capw, MasterDev* __restrict__ st,
+    const float* __restrict__ slab, const CUtensorMap* tmap, int ld, int V, int GS, int S, int max_iter,
+    MasterDev* __restrict__ st,
     GridBar* __restrict__ gb, float* __restrict__ H_part, double* __restrict__ g_part, float* __restrict__ gn_part,
     double* __restrict__ F_part, const uint8_t* __restrict__ vstruct, const StructTermsF* __restrict__ tf,
-    double tol_rel, float* __restrict__ z_out, float* __restrict__ pi_out, CGDev* __restrict__ cg, int bid, int G,
-    int K, int KP, int KW, int NV, double sigma, float* pm, unsigned* s_target, int* s_flag) {
-    int* s_act = reinterpret_cast<int*>(pm);          // [PW][capw] voxel indices
-    float* s_hv = pm + PW * capw;                     // [PW][capw] h
-    float* s_pv = s_hv + PW * capw;                   // [PW][capw] pi
-    float* Ac = s_pv + ((PW * capw + 3) / 4) * 4;     // [CHP][KW]
-    float* s_ch = Ac + CHP * KW;                      // [CHP] h of the chunk
-    float* s_cp = s_ch + CHP;                         // [CHP] pi of the chunk
+    double tol_rel, float* __restrict__ z_out, float* __restrict__ pi_out, CGDev* __restrict__ cg,
+    uint8_t* __restrict__ vstate, float* __restrict__ H_keep, int bid, int G, int K, int KP, int KW, int NV,
+    double sigma, float* pm,
+    unsigned* s_target, int* s_flag) {
+    float* stage = pm;                                // [KMAX][CHV] slab columns of a chunk (TMA, 128-byte aligned)
+    float* Arow = stage + KMAX * CHV;                 // [CHV][KW] rows of the chunk's active voxels
+    float* s_ch = Arow + CHV * KW;                    // [CHV] their change of h
+    float* s_cp = s_ch + CHV;                         // [CHV] their pi
+    float* s_ho = s_cp + CHV;                         // [CHV] their previous h (first evaluation after a new column)
+    int* s_dl = reinterpret_cast<int*>(s_ho + CHV);   // [CHV] slots of the rows whose h changed
+    __shared__ float s_zs[CHV], s_zc[CHV];
+    __shared__ unsigned s_bu[CHV / 32], s_bd[CHV / 32];
+    __shared__ float s_ga[4][64], s_gna[4][64], s_ea[4][64];
+    __shared__ int s_mode0;
+    __shared__ __align__(8) unsigned long long s_bars[NST_MAX];
     __shared__ float s_yh[KMAX], s_yl[KMAX];
     __shared__ StructTermsF s_tf[SMAX];
-    __shared__ int s_wn[PW];
     __shared__ float s_red[PW];
     __shared__ float s_scr[8 * 24];
     __shared__ int s_last, s_stop;
@@ -1010,12 +1032,36 @@ __device__ __forceinline__ void master_solve_group(
     for (int i = tid; i < S; i += PT) s_tf[i] = tf[i];
     const int KB = KP / 4;
     const int nb = KB * (KB + 1) / 2;
-    const int nq = KP / 4;
     int rb = -1, cb = -1;
     const int vl = tid % NV;
     if (tid < nb * NV) block_of(tid / NV, KB, rb, cb);
     const int n32 = (V + 31) / 32;
     const int tiles_b = bid < n32 ? (n32 - 1 - bid) / G + 1 : 0;
+    // the block's chunks: bid, bid + G, bid + 2G, ...
+    const int n_ch = (V + CHV - 1) / CHV;
+    const int chunks_b = bid < n_ch ? (n_ch - 1 - bid) / G + 1 : 0;
+    auto chunk_of = [&](int m) { return bid + m * G; };
+    // copies in flight: nst stages of nbox boxes each, copy n (n = 0, 1, ... over
+    // the launch) holding position n mod chunks_b in stage n mod nst
+    const int nbox = (KP + BOXC - 1) / BOXC;
+    const int nst = max(1, min(NST_MAX, (KMAX / BOXC) / nbox));
+    const int stage_floats = nbox * BOXC * CHV;
+    int n_use = 0, n_iss = 0;  // copies consumed (every thread), issued (thread 0)
+    bool lost = false;
+    // z by column halves: thread (half, v), columns [k0h, k1h); g by column kq
+    // and lane set ls
+    const int half = tid / CHV, v = tid % CHV;
+    const int KH = KP / 8 * 4;
+    const int k0h = half ? KH : 0, k1h = half ? KP : KH;
+    const int kq = tid & 63, ls = tid >> 6;
+    int n_ev = 0;  // evaluations of this solve so far
+    auto issue = [&](int n) {  // thread 0
+        const int sidx = n % nst;
+        float* dst = stage + sidx * stage_floats;
+        mbar_expect_tx(&s_bars[sidx], (unsigned)(stage_floats * sizeof(float)));
+        const int c = chunk_of(n % chunks_b);
+        for (int q = 0; q < nbox; ++q) tma_load_2d(dst + q * BOXC * CHV, tmap, c * CHV, q * BOXC, &s_bars[sidx]);
+    };
     // warm start (every block computes it; block 0 also writes the solver
     // state): the previous optimum, the new aperture K - 1 at 0
     if (tid < KMAX) {
@@ -1040,7 +1086,15 @@ __device__ __forceinline__ void master_solve_group(
         st->ticket = 0;
         st->final_pending = 0;
     }
+    if (tid < NST_MAX) mbar_init(&s_bars[tid], 1);
+    if (tid == 0) {  // the kept partial H: extend it by the new column, keep it, or rebuild it
+        const int iG = __ldcg(&st->inc_G), iK = __ldcg(&st->inc_K);
+        s_mode0 = iG == G && iK == K - 1 ? MODE_EXT : iG == G && iK == K ? MODE_INC : MODE_FULL;
+    }
     __syncthreads();
+    if (tid == 0 && chunks_b > 0)  // the first nst copies; the slab does not change during the solve
+        for (; n_iss < nst; ++n_iss) issue(n_iss);
+    const int mode0 = s_mode0;
     bool first = true;
     for (;;) {
         if (!first) {  // the state of the previous step (all blocks read it after the barrier)
@@ -1055,40 +1109,48 @@ __device__ __forceinline__ void master_solve_group(
             if (s_stop) break;
         }
         first = false;
-        // ---- A. z, pi, h, F over this block's tiles; active voxels per warp,
-        // in batches of capw / 32 tiles per warp (one batch when the lists of all
-        // the block's tiles fit shared memory), each batch's lists folded into
-        // the block's partial H, g and scale of g before the next
+        // ---- A. the block's chunks of CHV voxels in turn.  The chunk's slab
+        // columns arrive in a stage buffer ([16 q][CHV] per box of 16 columns,
+        // TMA, copies in flight ahead).  Per chunk:
+        //   z: thread (half, v) takes the compensated products of voxel v over
+        //      its half of the columns (four chains); half 1 hands its pair to
+        //      half 0, which forms z, pi, h, F and the voxel's curvature state;
+        //   rows: the rows of the voxels with h > 0 now or at the previous
+        //      evaluation go, compacted, to Arow (each half copies its own
+        //      columns), with pi, the change of h and (first evaluation after a
+        //      new column) the previous h; then the next copy is issued;
+        //   every thread folds the rows in: g, the rounding scale of g and the
+        //      new column's curvature row by column (four lane sets), and the
+        //      change of H by 4x4 blocks over the rows whose h changed.
+        // The block's partial H is kept from one evaluation to the next (it is
+        // updated by the changes of h only); the first evaluation of a solve
+        // extends it by the new column, or rebuilds it when it is not valid.
+        const int mode = n_ev == 0 ? mode0 : MODE_INC;
         float facc = 0.f;
         float hs[16];
 #pragma unroll
         for (int q = 0; q < 16; ++q) hs[q] = 0.f;
-        float gs[4] = {0.f, 0.f, 0.f, 0.f}, gns[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int i0 = 0; i0 < tiles_b; i0 += PW * (capw / 32)) {
-        const int i1 = min(tiles_b, i0 + PW * (capw / 32));
-        int na = 0;
-        for (int i = i0 + warp; i < i1; i += PW) {
-            const int j = (bid + i * G) * 32 + lane;
-            const bool in = j < V;
-            // requested with the first columns: the label, or the voxel's own terms
-            const int sid = in && S >= 0 ? vstruct[j] : 0;
-            const StructTermsF tv = in && S < 0 ? voxel_terms(tf, j) : StructTermsF{0.f, 0.f, 0.f, 0.f};
+        float ga = 0.f, gna = 0.f, ea = 0.f;
+        int nd_blk = 0;  // rows of the block whose h changed (uniform)
+        for (int m = 0; m < chunks_b && !lost; ++m) {
+            const int sidx = n_use % nst;
+            const float* stage_c = stage + sidx * stage_floats;
+            const int j = chunk_of(m) * CHV + v;
+            // the voxel's label and curvature state, requested before the wait
+            const bool own = !half && j < V;
+            const int lab = own && S >= 0 ? (int)vstruct[j] : 0;
+            const unsigned osv = own && mode != MODE_FULL ? (unsigned)vstate[j] : 0u;
+            const bool got = mbar_wait(&s_bars[sidx], (unsigned)((n_use / nst) & 1));
+            if (__syncthreads_or(!got)) {  // a copy never arrived: stop issuing, report it
+                lost = true;
+                break;
+            }
             float sc[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
-            const float* col = slab + (in ? j : 0);
-            // PB columns in flight per lane (one coalesced 128-byte row each), then
-            // their four compensated chains; columns K..KP-1 are zero and meet y = 0
-            constexpr int PB = 16;
-            for (int k0 = 0; k0 < KP; k0 += PB) {
-                float a[PB];
-#pragma unroll
-                for (int q = 0; q < PB; ++q) a[q] = k0 + q < KP ? __ldcg(col + (size_t)(k0 + q) * ld) : 0.f;
-#pragma unroll
-                for (int q = 0; q < PB; q += 4) {
-                    dot2_step(sc[0], cc[0], a[q], s_yh[k0 + q], s_yl[k0 + q]);
-                    dot2_step(sc[1], cc[1], a[q + 1], s_yh[k0 + q + 1], s_yl[k0 + q + 1]);
-                    dot2_step(sc[2], cc[2], a[q + 2], s_yh[k0 + q + 2], s_yl[k0 + q + 2]);
-                    dot2_step(sc[3], cc[3], a[q + 3], s_yh[k0 + q + 3], s_yl[k0 + q + 3]);
-                }
+            for (int k = k0h; k < k1h; k += 4) {  // columns K..KP-1 are zero and meet y = 0
+                dot2_step(sc[0], cc[0], stage_c[k * CHV + v], s_yh[k], s_yl[k]);
+                dot2_step(sc[1], cc[1], stage_c[(k + 1) * CHV + v], s_yh[k + 1], s_yl[k + 1]);
+                dot2_step(sc[2], cc[2], stage_c[(k + 2) * CHV + v], s_yh[k + 2], s_yl[k + 2]);
+                dot2_step(sc[3], cc[3], stage_c[(k + 3) * CHV + v], s_yh[k + 3], s_yl[k + 3]);
             }
             float s = sc[0], c = cc[0];
 #pragma unroll
@@ -1099,74 +1161,98 @@ __device__ __forceinline__ void master_solve_group(
                 s = t2;
                 c += e + cc[q];
             }
-            float h = 0.f, p = 0.f;
-            if (in) {
-                const StructTermsF t = S >= 0 ? s_tf[sid] : tv;
-                const float du = (t.tu - s) - c;
-                const float dov = (s - t.to) + c;
-                const float u = fmaxf(du, 0.f), o = fmaxf(dov, 0.f);
-                p = 2.f * (t.b * o - t.a * u);
-                h = 2.f * ((du > 0.f ? t.a : 0.f) + (dov > 0.f ? t.b : 0.f));
-                facc = fmaf(t.a * u, u, fmaf(t.b * o, o, facc));
-                z_out[j] = s + c;  // the state of the round when this point is the final one
-                pi_out[j] = p;
+            if (half) {
+                s_zs[v] = s;
+                s_zc[v] = c;
             }
-            const bool act = h > 0.f;
-            const unsigned bal = __ballot_sync(FULL, act);
-            if (act) {
-                const int slot = warp * capw + na + __popc(bal & ((1u << lane) - 1u));
-                s_act[slot] = j;
-                s_hv[slot] = h;
-                s_pv[slot] = p;
-            }
-            na += __popc(bal);
-        }
-        if (lane == 0) s_wn[warp] = na;
-        __syncthreads();
-        int total = 0;
-#pragma unroll
-        for (int w = 0; w < PW; ++w) total += s_wn[w];
-        // ---- the block's partial H, g and scale of g over this batch's active lists
-        for (int c0 = 0; c0 < total; c0 += CHP) {
-            const int n = min(CHP, total - c0);
-            {   // list entry c0 + i (warp lists in order) as row i of Ac
-                const int i = tid & (CHP - 1);
-                if (i < n) {
-                    int m = c0 + i, w = 0;
-                    while (m >= s_wn[w]) {
-                        m -= s_wn[w];
-                        ++w;
-                    }
-                    const int slot = w * capw + m;
-                    const int j = s_act[slot];
-                    if (tid < CHP) {
-                        s_ch[i] = s_hv[slot];
-                        s_cp[i] = s_pv[slot];
-                    }
-                    // this thread's column groups q = tid / CHP + 4 it of the row,
-                    // all loads issued before the first store
-                    float4 v[KMAX / 4 / (PT / CHP)];
-#pragma unroll
-                    for (int it = 0; it < KMAX / 4 / (PT / CHP); ++it) {
-                        const int q = tid / CHP + it * (PT / CHP);
-                        if (q < nq)
-                            v[it] = make_float4(__ldcg(slab + (size_t)(4 * q) * ld + j),
-                                                __ldcg(slab + (size_t)(4 * q + 1) * ld + j),
-                                                __ldcg(slab + (size_t)(4 * q + 2) * ld + j),
-                                                __ldcg(slab + (size_t)(4 * q + 3) * ld + j));
-                    }
-#pragma unroll
-                    for (int it = 0; it < KMAX / 4 / (PT / CHP); ++it) {
-                        const int q = tid / CHP + it * (PT / CHP);
-                        if (q < nq) *reinterpret_cast<float4*>(Ac + i * KW + 4 * q) = v[it];
-                    }
+            __syncthreads();
+            float p = 0.f, dh = 0.f, hold = 0.f;
+            bool uni = false;
+            if (!half) {
+                {  // TwoSum of the halves' sums
+                    const float s1 = s_zs[v];
+                    const float t2 = s + s1;
+                    const float bb = t2 - s;
+                    const float e = (s - (t2 - bb)) + (s1 - bb);
+                    s = t2;
+                    c += e + s_zc[v];
+                }
+                float h = 0.f;
+                if (j < V) {
+                    const StructTermsF t = S >= 0 ? s_tf[lab] : voxel_terms(tf, j);
+                    const float du = (t.tu - s) - c;
+                    const float dov = (s - t.to) + c;
+                    const float u = fmaxf(du, 0.f), o = fmaxf(dov, 0.f);
+                    p = 2.f * (t.b * o - t.a * u);
+                    h = 2.f * ((du > 0.f ? t.a : 0.f) + (dov > 0.f ? t.b : 0.f));
+                    facc = fmaf(t.a * u, u, fmaf(t.b * o, o, facc));
+                    z_out[j] = s + c;  // the state of the round when this point is the final one
+                    pi_out[j] = p;
+                    const unsigned nsv = (du > 0.f ? 1u : 0u) | (dov > 0.f ? 2u : 0u);
+                    hold = 2.f * (((osv & 1u) ? t.a : 0.f) + ((osv & 2u) ? t.b : 0.f));
+                    dh = h - hold;
+                    if (nsv != osv || mode == MODE_FULL) vstate[j] = (uint8_t)nsv;
+                }
+                uni = h > 0.f || hold > 0.f;
+                const unsigned bu = __ballot_sync(FULL, uni);
+                const unsigned bd = __ballot_sync(FULL, uni && dh != 0.f);
+                if (lane == 0) {
+                    s_bu[warp] = bu;
+                    s_bd[warp] = bd;
                 }
             }
             __syncthreads();
+            int n_u = 0, base = 0, n_d = 0, based = 0;
+            const int wv = v >> 5;  // the voxel's warp in half 0
+#pragma unroll
+            for (int w = 0; w < CHV / 32; ++w) {
+                const int cu = __popc(s_bu[w]), cd = __popc(s_bd[w]);
+                base += w < wv ? cu : 0;
+                based += w < wv ? cd : 0;
+                n_u += cu;
+                n_d += cd;
+            }
+            const unsigned lt = (1u << lane) - 1u;
+            if ((s_bu[wv] >> lane) & 1u) {
+                const int slot = base + __popc(s_bu[wv] & lt);
+                float4* dst = reinterpret_cast<float4*>(Arow + slot * KW);
+                for (int q = k0h / 4; q < k1h / 4; ++q)
+                    dst[q] = make_float4(stage_c[(4 * q) * CHV + v], stage_c[(4 * q + 1) * CHV + v],
+                                         stage_c[(4 * q + 2) * CHV + v], stage_c[(4 * q + 3) * CHV + v]);
+                if (!half) {
+                    s_cp[slot] = p;
+                    s_ch[slot] = dh;
+                    s_ho[slot] = mode == MODE_EXT ? hold : 0.f;
+                    if ((s_bd[wv] >> lane) & 1u) s_dl[based + __popc(s_bd[wv] & lt)] = slot;
+                }
+            }
+            __syncthreads();  // the stage is free, the chunk's rows are in Arow
+            if (tid == 0) issue(n_iss++);  // copy n_use + nst into the freed stage
+            ++n_use;
+            nd_blk += n_d;
+            // g, the rounding scale of g and the new column's curvature row
+            if (kq < K) {
+                if (mode == MODE_EXT) {
+                    for (int i = ls; i < n_u; i += 4) {
+                        const float a = Arow[i * KW + kq], pv = s_cp[i];
+                        ga = fmaf(a, pv, ga);
+                        gna = fmaf(fabsf(a), fabsf(pv), gna);
+                        ea = fmaf(a * s_ho[i], Arow[i * KW + K - 1], ea);
+                    }
+                } else {
+                    for (int i = ls; i < n_u; i += 4) {
+                        const float a = Arow[i * KW + kq], pv = s_cp[i];
+                        ga = fmaf(a, pv, ga);
+                        gna = fmaf(fabsf(a), fabsf(pv), gna);
+                    }
+                }
+            }
+            // the change of H over the rows whose h changed
             if (rb >= 0) {
-                for (int i = vl; i < n; i += NV) {
-                    const float4 ra = *reinterpret_cast<const float4*>(Ac + i * KW + 4 * rb);
-                    const float4 rc = *reinterpret_cast<const float4*>(Ac + i * KW + 4 * cb);
+                for (int ii = vl; ii < n_d; ii += NV) {
+                    const int i = s_dl[ii];
+                    const float4 ra = *reinterpret_cast<const float4*>(Arow + i * KW + 4 * rb);
+                    const float4 rc = *reinterpret_cast<const float4*>(Arow + i * KW + 4 * cb);
                     const float hv = s_ch[i];
                     const float a0 = ra.x * hv, a1 = ra.y * hv, a2 = ra.z * hv, a3 = ra.w * hv;
                     hs[0] = fmaf(a0, rc.x, hs[0]);
@@ -1185,73 +1271,77 @@ __device__ __forceinline__ void master_solve_group(
                     hs[13] = fmaf(a3, rc.y, hs[13]);
                     hs[14] = fmaf(a3, rc.z, hs[14]);
                     hs[15] = fmaf(a3, rc.w, hs[15]);
-                    if (rb == cb) {
-                        const float pv = s_cp[i], pa = fabsf(pv);
-                        gs[0] = fmaf(ra.x, pv, gs[0]);
-                        gs[1] = fmaf(ra.y, pv, gs[1]);
-                        gs[2] = fmaf(ra.z, pv, gs[2]);
-                        gs[3] = fmaf(ra.w, pv, gs[3]);
-                        gns[0] = fmaf(fabsf(ra.x), pa, gns[0]);
-                        gns[1] = fmaf(fabsf(ra.y), pa, gns[1]);
-                        gns[2] = fmaf(fabsf(ra.z), pa, gns[2]);
-                        gns[3] = fmaf(fabsf(ra.w), pa, gns[3]);
-                    }
                 }
             }
-            __syncthreads();
+            __syncthreads();  // Arow and the chunk's lists are free
         }
-        __syncthreads();  // every warp is done with this batch's counts and lists
-        }
+        ++n_ev;
+        // ---- the block's partials: F; g, the rounding scale of g and the new
+        // column's curvature row (lane sets added in order); H in place
         const float fw = warp_sum_f32(facc);
         if (lane == 0) s_red[warp] = fw;
+        s_ga[ls][kq] = ga;
+        s_gna[ls][kq] = gna;
+        s_ea[ls][kq] = ea;
         __syncthreads();
         if (tid == 0) {
             double t = 0.0;
             for (int w = 0; w < PW; ++w) t += (double)s_red[w];
             F_part[bid] = t;
+            if (lost) st->err = 1;  // the step stops the solve at the last accepted point
         }
-        float vals[24];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) vals[q] = hs[q];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            vals[16 + q] = gs[q];
-            vals[20 + q] = gns[q];
-        }
-        const int span = NV < 32 ? NV : 32;
-        for (int o = span / 2; o > 0; o >>= 1)
-#pragma unroll
-            for (int q = 0; q < 24; ++q) vals[q] += __shfl_xor_sync(FULL, vals[q], o);
-        if (NV > 32 && lane == 0)
-#pragma unroll
-            for (int q = 0; q < 24; ++q) s_scr[warp * 24 + q] = vals[q];
-        __syncthreads();
-        if ((tid % NV) == 0 && tid < nb * NV) {
-            if (NV > 32) {
-                const int w0 = tid >> 5, nw = NV >> 5;
-#pragma unroll
-                for (int q = 0; q < 24; ++q) {
-                    float t = 0.f;
-                    for (int w = 0; w < nw; ++w) t += s_scr[(w0 + w) * 24 + q];
-                    vals[q] = t;
-                }
+        if (tid < K) {
+            const float g4 = ((s_ga[0][tid] + s_ga[1][tid]) + s_ga[2][tid]) + s_ga[3][tid];
+            const float gn4 = ((s_gna[0][tid] + s_gna[1][tid]) + s_gna[2][tid]) + s_gna[3][tid];
+            g_part[(size_t)tid * GS + bid] = (double)g4;
+            gn_part[(size_t)tid * GS + bid] = gn4;
+            if (mode == MODE_EXT) {
+                const float ext = ((s_ea[0][tid] + s_ea[1][tid]) + s_ea[2][tid]) + s_ea[3][tid];
+                H_keep[(size_t)bid * HSTRIDE + tri_index(tid, K - 1, K)] = ext;
+                if (nd_blk == 0) H_part[(size_t)tri_index(tid, K - 1, K) * GS + bid] = ext;
             }
+        }
+        __syncthreads();  // the new column's row is in place before the changes are added
+        if (mode == MODE_FULL || nd_blk > 0) {
+            const int span = NV < 32 ? NV : 32;
+            for (int o = span / 2; o > 0; o >>= 1)
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+                for (int q = 0; q < 16; ++q) hs[q] += __shfl_xor_sync(FULL, hs[q], o);
+            if (NV > 32 && lane == 0)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int r = 4 * rb + q, cl = 4 * cb + e;
-                    if (r < K && cl < K && r <= cl) H_part[(size_t)tri_index(r, cl, K) * GS + bid] = vals[q * 4 + e];
-                }
-            if (rb == cb) {
+                for (int q = 0; q < 16; ++q) s_scr[warp * 24 + q] = hs[q];
+            __syncthreads();
+            if ((tid % NV) == 0 && tid < nb * NV) {
+                if (NV > 32) {
+                    const int w0 = tid >> 5, nw = NV >> 5;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int r = 4 * rb + q;
-                    if (r < K) {
-                        g_part[(size_t)r * GS + bid] = (double)vals[16 + q];
-                        gn_part[(size_t)r * GS + bid] = vals[20 + q];
+                    for (int q = 0; q < 16; ++q) {
+                        float t = 0.f;
+                        for (int w = 0; w < nw; ++w) t += s_scr[(w0 + w) * 24 + q];
+                        hs[q] = t;
                     }
                 }
+                float old[16];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int r = 4 * rb + q, cl = 4 * cb + e;
+                        old[q * 4 + e] = mode != MODE_FULL && r < K && cl < K && r <= cl
+                                             ? H_keep[(size_t)bid * HSTRIDE + tri_index(r, cl, K)]
+                                             : 0.f;
+                    }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int r = 4 * rb + q, cl = 4 * cb + e;
+                        if (r < K && cl < K && r <= cl) {
+                            const float nv = old[q * 4 + e] + hs[q * 4 + e];
+                            H_keep[(size_t)bid * HSTRIDE + tri_index(r, cl, K)] = nv;
+                            H_part[(size_t)tri_index(r, cl, K) * GS + bid] = nv;
+                        }
+                    }
             }
         }
         if (!grid_sync(gb, G, s_target, s_flag)) {
@@ -1272,7 +1362,15 @@ __device__ __forceinline__ void master_solve_group(
             break;
         }
     }
-    if (tid == 0) s_stop = __ldcg(&st->err) == 2;
+    if (tid == 0) {
+        // no copy of this block outlives the launch (a lost one is not waited for again)
+        for (int n = lost ? n_use + 1 : n_use; n < n_iss; ++n) mbar_wait(&s_bars[n % nst], (unsigned)((n / nst) & 1));
+        s_stop = __ldcg(&st->err) == 2;
+        if (bid == 0) {  // the kept partial H and voxel states are those of the last evaluation
+            st->inc_G = __ldcg(&st->err) == 0 ? G : 0;
+            st->inc_K = K;
+        }
+    }
     __syncthreads();
     if (s_stop) return;  // a barrier timed out: the host reports it
     // the solve stopped at an accepted point other than the last one evaluated:
@@ -1324,12 +1422,13 @@ __device__ __forceinline__ void master_solve_group(
 
 
 template <bool BATCH>
-__global__ void __launch_bounds__(PT, 2) k_master_persist(const MasterTask t1, const MasterTask* __restrict__ tasks,
+__global__ void __launch_bounds__(PT, 2) k_master_persist(const __grid_constant__ MasterTask t1,
+                                                          const MasterTask* __restrict__ tasks,
                                                        int GB, int K, int KP, int KW, int NV, double sigma) {
 #define DAO_TASK(f) (BATCH ? tasks[blockIdx.x / GB].f : t1.f)
     const float* __restrict__ slab = DAO_TASK(slab);
     const int ld = DAO_TASK(ld), V = DAO_TASK(V), GS = DAO_TASK(GS), S = DAO_TASK(S), max_iter = DAO_TASK(max_iter);
-    const int capw = DAO_TASK(capw);
+    const CUtensorMap* tmap = BATCH ? &tasks[blockIdx.x / GB].tmap : &t1.tmap;
     MasterDev* __restrict__ st = DAO_TASK(st);
     GridBar* __restrict__ gb = DAO_TASK(gb);
     float* __restrict__ H_part = DAO_TASK(H_part);
@@ -1343,15 +1442,17 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const MasterTask t1, c
     float* __restrict__ z_out = DAO_TASK(z_out);
     float* __restrict__ pi_out = DAO_TASK(pi_out);
     CGDev* __restrict__ cg = DAO_TASK(cg);
+    uint8_t* __restrict__ vstate = DAO_TASK(vstate);
+    float* __restrict__ H_keep = DAO_TASK(H_keep);
 #undef DAO_TASK
     const int bid = BATCH ? (int)(blockIdx.x % GB) : (int)blockIdx.x;
     if (K <= 0) {  // pool size from the device (one graph for every round); KW sets the layout below
         K = __ldcg(&cg->K);
         KP = (K + 3) / 4 * 4;
         KW = master_kw(K);
-        NV = master_lanes(K);
+        NV = persist_lanes(K);
     }
-    extern __shared__ __align__(16) float pm[];
+    extern __shared__ __align__(128) float pm[];
     __shared__ int s_flag, s_stop0;
     __shared__ unsigned s_target;
     if (skip != nullptr && *skip) return;  // the same for every block
@@ -1363,8 +1464,9 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const MasterTask t1, c
     }
     __syncthreads();
     if (s_stop0) return;
-    master_solve_group(slab, ld, V, GS, S, max_iter, capw, st, gb, H_part, g_part, gn_part, F_part, vstruct, tf,
-                       tol_rel, z_out, pi_out, cg, bid, G, K, KP, KW, NV, sigma, pm, &s_target, &s_flag);
+    master_solve_group(slab, tmap, ld, V, GS, S, max_iter, st, gb, H_part, g_part, gn_part, F_part, vstruct, tf,
+                       tol_rel, z_out, pi_out, cg, vstate, H_keep, bid, G, K, KP, KW, NV, sigma, pm, &s_target,
+                       &s_flag);
 }
 
 
@@ -1385,6 +1487,17 @@ size_t master_eval_smem(int K) {
 size_t master_hess_smem(int K, int n_tiles) {
     return (size_t)((n_tiles + 1 + 3) / 4 * 4) * sizeof(int) + (size_t)CH * master_kw(K) * sizeof(float) +
            2 * CH * sizeof(float);
+}
+
+// Voxel lanes per 4x4 block of H in the persistent solve: the most (a power of
+// two) for which every block of the triangle has its lanes among the 256 threads.
+__host__ __device__ int persist_lanes(int K) {
+    const int KP = (K + 3) / 4 * 4;
+    const int KB = KP / 4;
+    const int nb = KB * (KB + 1) / 2;
+    int nv = 1;
+    while (nb > 0 && nv * 2 * nb <= PT) nv *= 2;
+    return nv;
 }
 
 __host__ __device__ int master_lanes(int K) {
@@ -1490,20 +1603,14 @@ cudaError_t launch_master_step(int K, const MasterBuffers& mb, int max_iter, dou
     return cudaGetLastError();
 }
 
-// Active-list slots per warp of the persistent solve: every tile of the block at
-// once when they fit (one batch), else at most CAPW_MAX, which keeps two blocks
-// per SM whatever the voxel count and grid size.
-constexpr int CAPW_MAX = 512;
-int master_persist_capw(int V, int G) {
-    const int n32 = (V + 31) / 32;
-    const int tiles = G > 0 ? (n32 + G - 1) / G : n32;
-    return std::min(CAPW_MAX, (tiles + PW - 1) / PW * 32);
-}
-
+// Dynamic shared memory of the persistent solve, the same for every voxel count
+// and grid size: the TMA stage (KMAX columns of a chunk), the chunk's active
+// rows at the widest row stride, their h and pi.
 size_t master_persist_smem(int V, int G) {
-    const int capw = master_persist_capw(V, G);
-    return (size_t)PW * capw * sizeof(int) + (size_t)(PW * capw * 2 + 3) / 4 * 4 * sizeof(float) +
-           (size_t)CHP * master_kw(KMAX) * sizeof(float) + 2 * CHP * sizeof(float);
+    (void)V;
+    (void)G;
+    return (size_t)KMAX * CHV * sizeof(float) + (size_t)CHV * master_kw(KMAX) * sizeof(float) +
+           4 * (size_t)CHV * sizeof(float);
 }
 
 // Co-resident blocks of the persistent solve: 2 per SM when they fit, else 1;
@@ -1551,10 +1658,11 @@ cudaError_t launch_master_persist(const MasterBuffers& mb, const float* slab, in
     if (G < 1) return cudaErrorInvalidConfiguration;
     if (K <= 0 && cg == nullptr) return cudaErrorInvalidValue;
     int KP = K > 0 ? (K + 3) / 4 * 4 : 0;
-    int capw = master_persist_capw(V, G);
-    int KW = K > 0 ? master_kw(K) : 0, NV = K > 0 ? master_lanes(K) : 0;
+    int KW = K > 0 ? master_kw(K) : 0, NV = K > 0 ? persist_lanes(K) : 0;
     MasterTask t{};
-    t.capw = capw;
+    t.tmap = mb.tmap_p;
+    t.vstate = mb.vstate;
+    t.H_keep = mb.H_keep;
     t.slab = slab;
     t.ld = ld;
     t.V = V;
@@ -1597,9 +1705,8 @@ cudaError_t launch_master_persist(const MasterBuffers& mb, const float* slab, in
 int master_batch_group(int n_tasks, int num_sms) {
     // two co-resident blocks per SM (the shared memory per block is capped)
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_master_persist<true>, PT,
-                                                      (size_t)PW * CAPW_MAX * 12 + (size_t)CHP * master_kw(KMAX) * 4 +
-                                                          2 * CHP * 4 + 16) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_master_persist<true>, PT, master_persist_smem(0, 0)) !=
+        cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
