@@ -1020,7 +1020,7 @@ __device__ __forceinline__ void master_solve_group(
     int* s_dl = reinterpret_cast<int*>(s_ho + CHV);   // [CHV] slots of the rows whose h changed
     __shared__ float s_zs[CHV], s_zc[CHV];
     __shared__ unsigned s_bu[CHV / 32], s_bd[CHV / 32];
-    __shared__ float s_ga[4][64], s_gna[4][64], s_ea[4][64];
+    __shared__ float s_ga[PT], s_gna[PT], s_ea[PT];  // [lane set][column]
     __shared__ int s_mode0;
     __shared__ __align__(8) unsigned long long s_bars[NST_MAX];
     __shared__ float s_yh[KMAX], s_yl[KMAX];
@@ -1049,11 +1049,13 @@ __device__ __forceinline__ void master_solve_group(
     int n_use = 0, n_iss = 0;  // copies consumed (every thread), issued (thread 0)
     bool lost = false;
     // z by column halves: thread (half, v), columns [k0h, k1h); g by column kq
-    // and lane set ls
+    // and lane set ls (PT / KP lane sets: the fewer the columns, the more rows
+    // each column's sums are split over)
     const int half = tid / CHV, v = tid % CHV;
     const int KH = KP / 8 * 4;
     const int k0h = half ? KH : 0, k1h = half ? KP : KH;
-    const int kq = tid & 63, ls = tid >> 6;
+    const int nls = PT / KP;
+    const int kq = tid % KP, ls = tid / KP;
     int n_ev = 0;  // evaluations of this solve so far
     auto issue = [&](int n) {  // thread 0
         const int sidx = n % nst;
@@ -1132,19 +1134,25 @@ __device__ __forceinline__ void master_solve_group(
         for (int q = 0; q < 16; ++q) hs[q] = 0.f;
         float ga = 0.f, gna = 0.f, ea = 0.f;
         int nd_blk = 0;  // rows of the block whose h changed (uniform)
+        // the voxel's label and curvature state, one chunk ahead (their latency
+        // passes behind the previous chunk's work)
+        auto voxel_in = [&](int m, int& lab_, unsigned& osv_) {
+            const int jj = chunk_of(m) * CHV + v;
+            const bool own = !half && m < chunks_b && jj < V;
+            lab_ = own && S >= 0 ? (int)vstruct[jj] : 0;
+            osv_ = own && mode != MODE_FULL ? (unsigned)vstate[jj] : 0u;
+        };
+        int lab_n = 0;
+        unsigned osv_n = 0u;
+        voxel_in(0, lab_n, osv_n);
         for (int m = 0; m < chunks_b && !lost; ++m) {
             const int sidx = n_use % nst;
             const float* stage_c = stage + sidx * stage_floats;
             const int j = chunk_of(m) * CHV + v;
-            // the voxel's label and curvature state, requested before the wait
-            const bool own = !half && j < V;
-            const int lab = own && S >= 0 ? (int)vstruct[j] : 0;
-            const unsigned osv = own && mode != MODE_FULL ? (unsigned)vstate[j] : 0u;
+            const int lab = lab_n;
+            const unsigned osv = osv_n;
+            voxel_in(m + 1, lab_n, osv_n);
             const bool got = mbar_wait(&s_bars[sidx], (unsigned)((n_use / nst) & 1));
-            if (__syncthreads_or(!got)) {  // a copy never arrived: stop issuing, report it
-                lost = true;
-                break;
-            }
             float sc[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
             for (int k = k0h; k < k1h; k += 4) {  // columns K..KP-1 are zero and meet y = 0
                 dot2_step(sc[0], cc[0], stage_c[k * CHV + v], s_yh[k], s_yl[k]);
@@ -1165,7 +1173,10 @@ __device__ __forceinline__ void master_solve_group(
                 s_zs[v] = s;
                 s_zc[v] = c;
             }
-            __syncthreads();
+            if (__syncthreads_or(!got)) {  // a copy never arrived: stop issuing, report it
+                lost = true;
+                break;
+            }
             float p = 0.f, dh = 0.f, hold = 0.f;
             bool uni = false;
             if (!half) {
@@ -1231,16 +1242,16 @@ __device__ __forceinline__ void master_solve_group(
             ++n_use;
             nd_blk += n_d;
             // g, the rounding scale of g and the new column's curvature row
-            if (kq < K) {
+            if (kq < K && ls < nls) {
                 if (mode == MODE_EXT) {
-                    for (int i = ls; i < n_u; i += 4) {
+                    for (int i = ls; i < n_u; i += nls) {
                         const float a = Arow[i * KW + kq], pv = s_cp[i];
                         ga = fmaf(a, pv, ga);
                         gna = fmaf(fabsf(a), fabsf(pv), gna);
                         ea = fmaf(a * s_ho[i], Arow[i * KW + K - 1], ea);
                     }
                 } else {
-                    for (int i = ls; i < n_u; i += 4) {
+                    for (int i = ls; i < n_u; i += nls) {
                         const float a = Arow[i * KW + kq], pv = s_cp[i];
                         ga = fmaf(a, pv, ga);
                         gna = fmaf(fabsf(a), fabsf(pv), gna);
@@ -1273,16 +1284,19 @@ __device__ __forceinline__ void master_solve_group(
                     hs[15] = fmaf(a3, rc.w, hs[15]);
                 }
             }
-            __syncthreads();  // Arow and the chunk's lists are free
+            // Arow and the lists are next written after the next chunk's first two
+            // barriers, which every thread reaches only when done with this chunk
         }
         ++n_ev;
         // ---- the block's partials: F; g, the rounding scale of g and the new
         // column's curvature row (lane sets added in order); H in place
         const float fw = warp_sum_f32(facc);
         if (lane == 0) s_red[warp] = fw;
-        s_ga[ls][kq] = ga;
-        s_gna[ls][kq] = gna;
-        s_ea[ls][kq] = ea;
+        if (ls < nls) {
+            s_ga[ls * KP + kq] = ga;
+            s_gna[ls * KP + kq] = gna;
+            s_ea[ls * KP + kq] = ea;
+        }
         __syncthreads();
         if (tid == 0) {
             double t = 0.0;
@@ -1291,12 +1305,15 @@ __device__ __forceinline__ void master_solve_group(
             if (lost) st->err = 1;  // the step stops the solve at the last accepted point
         }
         if (tid < K) {
-            const float g4 = ((s_ga[0][tid] + s_ga[1][tid]) + s_ga[2][tid]) + s_ga[3][tid];
-            const float gn4 = ((s_gna[0][tid] + s_gna[1][tid]) + s_gna[2][tid]) + s_gna[3][tid];
+            float g4 = 0.f, gn4 = 0.f, ext = 0.f;  // lane sets in order
+            for (int l = 0; l < nls; ++l) {
+                g4 += s_ga[l * KP + tid];
+                gn4 += s_gna[l * KP + tid];
+                ext += s_ea[l * KP + tid];
+            }
             g_part[(size_t)tid * GS + bid] = (double)g4;
             gn_part[(size_t)tid * GS + bid] = gn4;
             if (mode == MODE_EXT) {
-                const float ext = ((s_ea[0][tid] + s_ea[1][tid]) + s_ea[2][tid]) + s_ea[3][tid];
                 H_keep[(size_t)bid * HSTRIDE + tri_index(tid, K - 1, K)] = ext;
                 if (nd_blk == 0) H_part[(size_t)tri_index(tid, K - 1, K) * GS + bid] = ext;
             }
