@@ -538,6 +538,9 @@ def run_ours(a):
     from paper_1003_5402_gb300 import binding
     PREC = {"fp32": binding.DAO_PREC_FP32, "fp16": binding.DAO_PREC_FP16, "bf16": binding.DAO_PREC_BF16}
     plan = Plan(case, device=dev, stream=stream.cuda_stream, precision=PREC[a.precision])
+    # SpMV launch shapes chosen on a cold cache, outside the timed region
+    import tempfile
+    tuning = plan.autotune(os.path.join(tempfile.gettempdir(), "dao_autotune.txt"))
     sampler = ClockSampler(dev, enabled=not a.no_clocks)
     sampler.wait_first_sample()
     for _ in range(a.warmup):
@@ -729,6 +732,7 @@ def run_ours(a):
             "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
                            "p99": round(float(np.percentile(lat, 99)), 4)},
             "spmv": spmv, "mixed_precision": mixed, "batch": batch, "serve": serve, "kernel_ms_host_driven_plan": kernel_ms, "kernel_launches_host_driven_plan": kernel_launches,
+            "spmv_launch_shapes": tuning,
             "objective_final": F_final, "apertures_done": int(n), "master_evals": int(np.sum(ev)),
             "host_wall_s": round(t_host, 3), "device": torch.cuda.get_device_name(dev),
         }

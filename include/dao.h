@@ -439,8 +439,10 @@ int32_t dao_batch_group_size(int32_t n, int32_t device);
  * Times the dose SpMV (a1, lanes per voxel row: 4/8/16/32, 16-bit storage up to
  * 16), the transposed SpMV (a2, threads per beamlet row: 64/128/256) and the
  * aperture column (a4, lanes per voxel row: 4/8/16) on the context's own
- * matrices (10 launches per candidate, captured into a CUDA graph, timed with
- * events) and keeps the fastest of each for this context.  cache_path (or
+ * matrices (10 launches per candidate, each after a read of a buffer twice the
+ * L2 size, so that it runs on a cold cache as in a plan; median of the
+ * per-launch event times) and keeps the fastest of each for this context.
+ * Needs 2 x L2 bytes of device memory for the duration of the call.  cache_path (or
  * NULL): a text file of "key dose column dt" lines, key = device name,
  * precision and the log2 size class of voxels, beamlets and the mean row
  * lengths of D and D^T; a matching entry is applied without timing, a new

@@ -1801,6 +1801,61 @@ dao_status time_graph(dao_ctx* c, int reps, F&& launch, double* us, const char* 
     return DAO_OK;
 }
 
+// Cold timing of `launch` as the plan meets it: before each of reps launches a
+// read of a buffer twice the L2 size (clean lines only) leaves none of the
+// kernel's data in L2; the median of the per-launch event times (graph replay,
+// external event records).  The buffer is stream-ordered pool memory, freed
+// before the return.
+template <class F>
+dao_status time_cold(dao_ctx* c, int reps, F&& launch, double* us, const char* what) {
+    DAO_TRY(sync(c));
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device) != cudaSuccess || l2 <= 0) {
+        cudaGetLastError();
+        l2 = 128 << 20;
+    }
+    const size_t fbytes = (size_t)2 * l2;
+    void* flush = nullptr;
+    DAO_CU(pool_alloc(&flush, fbytes, c->device, c->stream));
+    std::vector<cudaEvent_t> ev(2 * (size_t)reps, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (auto& x : ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&x);
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    int n = 0;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+            e = launch_l2_evict(flush, fbytes, c->w, c->num_sms, c->stream);
+            if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2 * r], c->stream, cudaEventRecordExternal);
+            if (e == cudaSuccess) e = launch(&n);
+            if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[2 * r + 1], c->stream, cudaEventRecordExternal);
+        }
+        const cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ex, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    std::vector<float> ms(reps, 0.f);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaEventElapsedTime(&ms[r], ev[2 * r], ev[2 * r + 1]);
+    if (ex) cudaGraphExecDestroy(ex);
+    if (g) cudaGraphDestroy(g);
+    for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+    pool_free(flush, c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DAO_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    c->launches_i += 2 * n;
+    c->count_launches();
+    std::sort(ms.begin(), ms.end());
+    *us = 1e3 * ms[reps / 2];
+    return DAO_OK;
+}
+
 // Autotuner cache key: device, storage and the size class of the problem
 // (log2 buckets of voxels, beamlets and the mean row lengths of D and D^T).
 std::string tune_key(const dao_ctx* c) {
@@ -1811,7 +1866,8 @@ std::string tune_key(const dao_ctx* c) {
     auto lb = [](double v) { return (int)std::lround(std::log2(std::max(v, 1.0))); };
     const double row_d = c->V > 0 ? (double)c->nnz / c->V : 0.0, row_t = c->N > 0 ? (double)c->nnz / c->N : 0.0;
     return dev + "|prec=" + std::to_string(c->opt.precision) + "|V=" + std::to_string(lb(c->V)) + "|N=" +
-           std::to_string(lb(c->N)) + "|rowD=" + std::to_string(lb(row_d)) + "|rowDt=" + std::to_string(lb(row_t));
+           std::to_string(lb(c->N)) + "|rowD=" + std::to_string(lb(row_d)) + "|rowDt=" + std::to_string(lb(row_t)) +
+           "|cold";
 }
 
 bool tune_cache_read(const char* path, const std::string& key, int* dose_g, int* col_g, int* dt_t) {
@@ -2247,7 +2303,7 @@ dao_status dao_autotune(dao_ctx* c, const char* cache_path, dao_tuning* out) {
             if (c->opt.precision != DAO_PREC_FP32 && g > 16) continue;
             c->D.tune_dose_g = g;
             double us = 0.0;
-            DAO_TRY(time_graph(c, reps, [&](int* nl) {
+            DAO_TRY(time_cold(c, reps, [&](int* nl) {
                 return launch_dose(c->D, c->x, c->vstruct, c->tf, c->ts, c->S, c->dose, nullptr, nullptr, 0, nullptr,
                                    c->num_sms, c->stream, nl);
             }, &us, "dao_autotune"));
@@ -2260,7 +2316,7 @@ dao_status dao_autotune(dao_ctx* c, const char* cache_path, dao_tuning* out) {
         for (int t : TUNE_DT_THREADS) {  // a2: threads per beamlet row
             c->Dt.tune_dt_threads = t;
             double us = 0.0;
-            DAO_TRY(time_graph(c, reps, [&](int* nl) { return launch_dt(c->Dt, c->pi, c->w, nullptr, c->stream, nl); },
+            DAO_TRY(time_cold(c, reps, [&](int* nl) { return launch_dt(c->Dt, c->pi, c->w, nullptr, c->stream, nl); },
                                &us, "dao_autotune"));
             if (us < best) {
                 best = us;
@@ -2271,7 +2327,7 @@ dao_status dao_autotune(dao_ctx* c, const char* cache_path, dao_tuning* out) {
         for (int g : TUNE_COL_G) {  // a4: lanes per voxel row over beam 0's segment
             c->D.tune_col_g = g;
             double us = 0.0;
-            DAO_TRY(time_graph(c, reps, [&](int* nl) {
+            DAO_TRY(time_cold(c, reps, [&](int* nl) {
                 return launch_column(c->D, c->seg, c->seg + (size_t)c->V, c->beam_off[0], c->rows[0] * c->cols[0],
                                      c->mask, c->dose, 1, c->num_sms, c->stream, nl);
             }, &us, "dao_autotune"));

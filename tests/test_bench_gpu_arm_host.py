@@ -71,6 +71,9 @@ class _Plan:
     def close(self):
         pass
 
+    def autotune(self, cache_path=None):
+        return {"dose_lanes": 8, "column_lanes": 8, "dt_threads": 64, "from_cache": False}
+
     def reset(self):
         self.k = 0
 
