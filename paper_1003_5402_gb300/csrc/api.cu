@@ -543,12 +543,12 @@ dao_status make_tensor_maps(dao_ctx* c) {
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(DAO_ECUDA, "cuTensorMapEncodeTiled failed with " + std::to_string((int)r));
     }
-    {  // the persistent solve's map: boxes of 128 voxels x 16 columns (x = 128 c, y = 16 q, both in range)
+    for (int m = 0; m < 2; ++m) {  // the persistent solve's maps: boxes of 128 voxels x 16, x 4 columns
         const cuuint64_t dims[2] = {(cuuint64_t)c->ld, (cuuint64_t)KMAX};
         const cuuint64_t strides[1] = {(cuuint64_t)c->ld * sizeof(float)};
-        const cuuint32_t box[2] = {128u, 16u};
+        const cuuint32_t box[2] = {128u, m == 0 ? 16u : 4u};
         const cuuint32_t estr[2] = {1, 1};
-        CUresult r = encode(&c->mb.tmap_p, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->slab, dims, strides, box, estr,
+        CUresult r = encode(&c->mb.tmap_p[m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->slab, dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(DAO_ECUDA, "cuTensorMapEncodeTiled failed with " + std::to_string((int)r));
@@ -2136,7 +2136,8 @@ dao_status build_batch_graph(dao_ctx* const* ctxs, int n, int R, BatchGraph* bg)
         t.z_out = c->z;
         t.pi_out = c->pi;
         t.cg = c->cg;
-        t.tmap = c->mb.tmap_p;
+        t.tmap[0] = c->mb.tmap_p[0];
+        t.tmap[1] = c->mb.tmap_p[1];
         t.vstate = c->mb.vstate;
         t.H_keep = c->mb.H_keep;
         max_V = std::max(max_V, c->V);

@@ -304,7 +304,7 @@ struct MasterBuffers {
     int GP = 0;                 // blocks of the persistent solve (co-resident), 0: not available
     int grid[KMAX + 1] = {};    // blocks of the evaluation kernel for each pool size
     CUtensorMap tmap[KMAX / 4 + 1];  // slab tile maps, indexed by columns / 4
-    CUtensorMap tmap_p;              // slab map of the persistent solve: boxes of 128 voxels x 16 columns
+    CUtensorMap tmap_p[2];           // slab maps of the persistent solve: boxes of 128 voxels x 16, x 4 columns
     uint8_t* vstate = nullptr;       // [V] persistent solve: each voxel's curvature state at the last evaluation
     float* H_keep = nullptr;         // [GH][KMAX*(KMAX+1)/2] persistent solve: each block's kept partial H
 };
@@ -384,7 +384,7 @@ cudaError_t build_transpose_place(int prec, const int64_t* rp, const int* col, c
 // the slab and its partial arrays (stride GS), the objective terms, the
 // round's skip flag and outputs, and the device-side round state (pool size).
 struct MasterTask {
-    CUtensorMap tmap;     // the slab in boxes of 128 voxels x 16 columns (MasterBuffers::tmap_p)
+    CUtensorMap tmap[2];  // the slab in boxes of 128 voxels x 16, x 4 columns (MasterBuffers::tmap_p)
     const float* slab;
     int ld, V, GS, S, max_iter;
     MasterDev* st;

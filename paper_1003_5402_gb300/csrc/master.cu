@@ -1043,9 +1043,10 @@ __device__ __forceinline__ void master_solve_group(
     auto chunk_of = [&](int m) { return bid + m * G; };
     // copies in flight: nst stages of nbox boxes each, copy n (n = 0, 1, ... over
     // the launch) holding position n mod chunks_b in stage n mod nst
-    const int nbox = (KP + BOXC - 1) / BOXC;
-    const int nst = max(1, min(NST_MAX, (KMAX / BOXC) / nbox));
-    const int stage_floats = nbox * BOXC * CHV;
+    // a copy: KP / 16 boxes of 16 columns, then (KP mod 16) / 4 of 4 columns
+    const int nbox = KP / BOXC, nbox4 = (KP % BOXC) / 4;
+    const int nst = max(1, min(NST_MAX, KMAX / KP));
+    const int stage_floats = KP * CHV;
     int n_use = 0, n_iss = 0;  // copies consumed (every thread), issued (thread 0)
     bool lost = false;
     // z by column halves: thread (half, v), columns [k0h, k1h); g by column kq
@@ -1063,6 +1064,8 @@ __device__ __forceinline__ void master_solve_group(
         mbar_expect_tx(&s_bars[sidx], (unsigned)(stage_floats * sizeof(float)));
         const int c = chunk_of(n % chunks_b);
         for (int q = 0; q < nbox; ++q) tma_load_2d(dst + q * BOXC * CHV, tmap, c * CHV, q * BOXC, &s_bars[sidx]);
+        for (int q = 0; q < nbox4; ++q)
+            tma_load_2d(dst + (nbox * BOXC + 4 * q) * CHV, tmap + 1, c * CHV, nbox * BOXC + 4 * q, &s_bars[sidx]);
     };
     // warm start (every block computes it; block 0 also writes the solver
     // state): the previous optimum, the new aperture K - 1 at 0
@@ -1445,7 +1448,7 @@ __global__ void __launch_bounds__(PT, 2) k_master_persist(const __grid_constant_
 #define DAO_TASK(f) (BATCH ? tasks[blockIdx.x / GB].f : t1.f)
     const float* __restrict__ slab = DAO_TASK(slab);
     const int ld = DAO_TASK(ld), V = DAO_TASK(V), GS = DAO_TASK(GS), S = DAO_TASK(S), max_iter = DAO_TASK(max_iter);
-    const CUtensorMap* tmap = BATCH ? &tasks[blockIdx.x / GB].tmap : &t1.tmap;
+    const CUtensorMap* tmap = BATCH ? tasks[blockIdx.x / GB].tmap : t1.tmap;
     MasterDev* __restrict__ st = DAO_TASK(st);
     GridBar* __restrict__ gb = DAO_TASK(gb);
     float* __restrict__ H_part = DAO_TASK(H_part);
@@ -1677,7 +1680,8 @@ cudaError_t launch_master_persist(const MasterBuffers& mb, const float* slab, in
     int KP = K > 0 ? (K + 3) / 4 * 4 : 0;
     int KW = K > 0 ? master_kw(K) : 0, NV = K > 0 ? persist_lanes(K) : 0;
     MasterTask t{};
-    t.tmap = mb.tmap_p;
+    t.tmap[0] = mb.tmap_p[0];
+    t.tmap[1] = mb.tmap_p[1];
     t.vstate = mb.vstate;
     t.H_keep = mb.H_keep;
     t.slab = slab;
