@@ -53,6 +53,7 @@ def _args():
     p.add_argument("--skip-cpu", action="store_true")
     p.add_argument("--skip-e2e", action="store_true")
     p.add_argument("--skip-spmv", action="store_true")
+    p.add_argument("--skip-strip", action="store_true", help="no SpMV leg on the strip-profile matrix")
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--skip-batch", action="store_true")
     p.add_argument("--skip-serve", action="store_true")
@@ -319,6 +320,21 @@ def run_reference(a):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def strip_case(case):
+    """The case's anatomy with D from the strip lateral profile, generated on
+    the device by the library's pencil-beam model (dao_pencil_generate)."""
+    import dataclasses
+    from paper_1003_5402_gb300 import binding
+    spec = dataclasses.replace(case.spec, profile="strip")
+    args = dict(xyz=case.voxel_xyz, iso=case.iso, n_beams=spec.n_beams, rows=spec.rows, cols=spec.cols,
+                beamlet_mm=spec.beamlet_mm, sigma_mm=spec.sigma_mm, mu_per_mm=spec.mu_per_mm, cutoff=spec.cutoff,
+                profile="strip", body_kind=spec.body.kind, body_center=spec.body.center[:2],
+                body_size=spec.body.size[:2], jitter=spec.jitter,
+                jitter_stream=(spec.seed * 0x100000001 + 0x5EED) & 0xFFFFFFFFFFFFFFFF)
+    rp, col, val = binding.pencil_generate(args)
+    return dataclasses.replace(case, spec=spec, indptr=rp, indices=col, data=val)
+
+
 def _make_case_spec(spec):
     return phantom.make_case(spec)
 
@@ -473,10 +489,14 @@ def pinned_inputs(torch, case):
     return c
 
 
-def spmv_bandwidth(torch, plan, case, prec, flush, hbm_peak):
+def spmv_bandwidth(torch, plan, case, prec, flush, hbm_peak, tuning=None):
     """Cold-L2 a1 and a2 alone: median of 20 runs, each timed with CUDA events;
-    the fraction of the measured copy peak and of the nominal 7.9 TB/s."""
+    the fraction of the measured copy peak and of the nominal 7.9 TB/s, and the
+    kernel form the plan runs (the autotuner's choice when ``tuning`` is given)."""
     out = {}
+    if tuning is not None:
+        out["form"] = {"dose": tuning["dose_form"], "dose_lanes": tuning["dose_lanes"], "dt_map": tuning["dt_map"],
+                       "dt_threads": tuning["dt_threads"]}
     x = torch.rand(case.n_beamlets, device="cuda")
     z = torch.empty(case.n_voxels, device="cuda")
     g = torch.empty_like(z)
@@ -631,9 +651,10 @@ def run_ours(a):
     spmv = mixed = None
     if not a.skip_spmv:
         other = "fp32" if a.precision != "fp32" else "fp16"
-        spmv = {a.precision: spmv_bandwidth(torch, plan, case, a.precision, flush, hbm_peak)}
+        spmv = {a.precision: spmv_bandwidth(torch, plan, case, a.precision, flush, hbm_peak, tuning)}
         with Plan(case, device=dev, stream=stream.cuda_stream, precision=PREC[other]) as p2:
-            spmv[other] = spmv_bandwidth(torch, p2, case, other, flush, hbm_peak)
+            t_other = p2.autotune(os.path.join(tempfile.gettempdir(), "dao_autotune.txt"))
+            spmv[other] = spmv_bandwidth(torch, p2, case, other, flush, hbm_peak, t_other)
             for _ in range(2):
                 p2.reset()
                 p2.solve(a.apertures)
@@ -652,6 +673,20 @@ def run_ours(a):
                  "other_ms_per_plan": round(statistics.median(t2), 4),
                  "other_objective_final": float(tr2[n2 - 1]) if n2 else None,
                  "objective_rel_diff": (abs(float(tr2[n2 - 1]) - F_final) / F_final if n2 and F_final else None)}
+
+    # SpMV bandwidth on the same anatomy with the strip lateral profile (a 5 mm
+    # strip blurred by the Gaussian, closer to a finite-size pencil beam): more
+    # entries per row; D generated on the device from the model, then planned
+    spmv_strip = None
+    if not a.skip_spmv and not a.skip_strip:
+        spmv_strip = {}
+        scase = strip_case(case)
+        spmv_strip["nnz"] = int(scase.nnz)
+        spmv_strip["nnz_gauss"] = int(case.nnz)
+        for prec in (a.precision, "fp32" if a.precision != "fp32" else "fp16"):
+            with Plan(scase, device=dev, stream=stream.cuda_stream, precision=PREC[prec]) as ps:
+                ts = ps.autotune(os.path.join(tempfile.gettempdir(), "dao_autotune.txt"))
+                spmv_strip[prec] = spmv_bandwidth(torch, ps, scase, prec, flush, hbm_peak, ts)
 
     # end to end through the public API from host buffers
     e2e = None
@@ -731,7 +766,7 @@ def run_ours(a):
             "roofline": roof, "roofline_eval_kernel": roof_eval, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
             "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
                            "p99": round(float(np.percentile(lat, 99)), 4)},
-            "spmv": spmv, "mixed_precision": mixed, "batch": batch, "serve": serve, "kernel_ms_host_driven_plan": kernel_ms, "kernel_launches_host_driven_plan": kernel_launches,
+            "spmv": spmv, "spmv_strip_profile": spmv_strip, "mixed_precision": mixed, "batch": batch, "serve": serve, "kernel_ms_host_driven_plan": kernel_ms, "kernel_launches_host_driven_plan": kernel_launches,
             "spmv_launch_shapes": tuning,
             "objective_final": F_final, "apertures_done": int(n), "master_evals": int(np.sum(ev)),
             "host_wall_s": round(t_host, 3), "device": torch.cuda.get_device_name(dev),

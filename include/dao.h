@@ -132,7 +132,18 @@ typedef struct dao_options {
                                 * memory) leave room for other plans' solves to run side by side */
     int32_t dt_threads;        /* threads per beamlet row of the transposed SpMV: 0 (default: 64, or the
                                 * autotuner's choice), 64, 128 or 256 */
+    int32_t dt_map;            /* lane mapping of the transposed SpMV: 0 (default: DAO_DT_CONSECUTIVE, or
+                                * the autotuner's choice), DAO_DT_GROUPED (a thread per 4 or 8 consecutive
+                                * entries, 16-byte loads) or DAO_DT_CONSECUTIVE (consecutive entries on
+                                * consecutive threads: the pi gathers of a warp fall on few cache lines) */
+    int32_t dose_form;         /* form of the dose SpMV: 0 (default: DAO_DOSE_UNITS where its shared memory
+                                * fits, or the autotuner's choice), DAO_DOSE_LANES (2 to 32 lanes per voxel
+                                * row) or DAO_DOSE_UNITS (one warp per 32 consecutive rows, their entries
+                                * requested at once) */
 } dao_options;
+
+enum { DAO_DT_GROUPED = 1, DAO_DT_CONSECUTIVE = 2 };
+enum { DAO_DOSE_LANES = 1, DAO_DOSE_UNITS = 2 };
 
 typedef struct dao_ctx dao_ctx;
 
@@ -436,24 +447,27 @@ dao_status dao_batch_solve_persistent(dao_ctx* const* ctxs, int32_t n, int32_t n
 int32_t dao_batch_group_size(int32_t n, int32_t device);
 
 /* ---- autotuner of the SpMV launch shapes ----
- * Times the dose SpMV (a1, lanes per voxel row: 4/8/16/32, 16-bit storage up to
- * 16), the transposed SpMV (a2, threads per beamlet row: 64/128/256) and the
+ * Times the dose SpMV (a1: the lane form with 4/8/16/32 lanes per voxel row,
+ * 16-bit storage up to 16, and the unit form), the transposed SpMV (a2, threads
+ * per beamlet row: 64/128/256, each with both lane mappings) and the
  * aperture column (a4, lanes per voxel row: 4/8/16) on the context's own
  * matrices (10 launches per candidate, each after a read of a buffer twice the
  * L2 size, so that it runs on a cold cache as in a plan; median of the
  * per-launch event times) and keeps the fastest of each for this context.
  * Needs 2 x L2 bytes of device memory for the duration of the call.  cache_path (or
- * NULL): a text file of "key dose column dt" lines, key = device name,
+ * NULL): a text file of "key dose column dt form map" lines, key = device name,
  * precision and the log2 size class of voxels, beamlets and the mean row
  * lengths of D and D^T; a matching entry is applied without timing, a new
  * choice is appended.  out (or NULL) receives the choice and whether it came
  * from the cache.  Cached round graphs are rebuilt on the next solve.  Results
  * are unchanged up to the FP32 summation order of the SpMVs. */
 typedef struct {
-    int32_t dose_lanes;    /* a1 lanes per voxel row */
+    int32_t dose_lanes;    /* a1 lanes per voxel row (lane form) */
     int32_t column_lanes;  /* a4 lanes per voxel row */
     int32_t dt_threads;    /* a2 threads per beamlet row */
     int32_t from_cache;    /* 1 when read from cache_path, 0 when timed */
+    int32_t dose_form;     /* a1 form: DAO_DOSE_LANES or DAO_DOSE_UNITS */
+    int32_t dt_map;        /* a2 lane mapping: DAO_DT_GROUPED or DAO_DT_CONSECUTIVE */
 } dao_tuning;
 dao_status dao_autotune(dao_ctx* ctx, const char* cache_path, dao_tuning* out);
 

@@ -22,6 +22,10 @@ DAO_PREC_FP32, DAO_PREC_FP16, DAO_PREC_BF16 = 0, 1, 2
 DAO_MLC_CONSECUTIVE, DAO_MLC_INTERDIGITATION, DAO_MLC_CONNECTED, DAO_MLC_JAWS = 0, 1, 2, 3
 MLC = {"consecutive": DAO_MLC_CONSECUTIVE, "interdigitation": DAO_MLC_INTERDIGITATION,
        "connected": DAO_MLC_CONNECTED, "jaws": DAO_MLC_JAWS}
+DAO_DT_GROUPED, DAO_DT_CONSECUTIVE = 1, 2
+DAO_DOSE_LANES, DAO_DOSE_UNITS = 1, 2
+DT_MAPS = {DAO_DT_GROUPED: "grouped", DAO_DT_CONSECUTIVE: "consecutive"}
+DOSE_FORMS = {DAO_DOSE_LANES: "lanes", DAO_DOSE_UNITS: "units"}
 KC = {"dose": 0, "dt": 1, "price": 2, "column": 3, "master_pass": 4, "master_reduce": 5, "master_step": 6,
       "master_hess": 7, "other": 8, "master_solve": 9}
 
@@ -52,12 +56,13 @@ class dao_options(C.Structure):
     _fields_ = [("k_max", C.c_int32), ("max_master_iters", C.c_int32), ("master_tol", C.c_double),
                 ("price_tol", C.c_double), ("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
                 ("use_graphs", C.c_int32), ("master_persistent", C.c_int32), ("mlc_constraint", C.c_int32),
-                ("master_blocks", C.c_int32), ("dt_threads", C.c_int32)]
+                ("master_blocks", C.c_int32), ("dt_threads", C.c_int32), ("dt_map", C.c_int32),
+                ("dose_form", C.c_int32)]
 
 
 class dao_tuning(C.Structure):
     _fields_ = [("dose_lanes", C.c_int32), ("column_lanes", C.c_int32), ("dt_threads", C.c_int32),
-                ("from_cache", C.c_int32)]
+                ("from_cache", C.c_int32), ("dose_form", C.c_int32), ("dt_map", C.c_int32)]
 
 
 class dao_server_options(C.Structure):
@@ -212,6 +217,10 @@ def options(**kw) -> dao_options:
     for k, v in kw.items():
         if k == "stream":
             v = C.c_void_p(v)
+        elif k == "dt_map" and isinstance(v, str):
+            v = {n: c for c, n in DT_MAPS.items()}[v]
+        elif k == "dose_form" and isinstance(v, str):
+            v = {n: c for c, n in DOSE_FORMS.items()}[v]
         setattr(o, k, v)
     return o
 
@@ -502,6 +511,7 @@ class Plan:
         path = cache_path.encode() if cache_path else None
         _check(load().dao_autotune(self.h, path, C.byref(t)), "dao_autotune")
         return {"dose_lanes": t.dose_lanes, "column_lanes": t.column_lanes, "dt_threads": t.dt_threads,
+                "dose_form": DOSE_FORMS.get(t.dose_form, t.dose_form), "dt_map": DT_MAPS.get(t.dt_map, t.dt_map),
                 "from_cache": bool(t.from_cache)}
 
     def master_stats(self):

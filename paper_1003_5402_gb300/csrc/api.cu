@@ -258,6 +258,10 @@ dao_status validate(const dao_csr* D, const dao_geometry* g, const dao_structure
     if (opt->master_blocks < 0) return fail(DAO_EINVAL, "master_blocks must be >= 0");
     if (opt->dt_threads != 0 && opt->dt_threads != 64 && opt->dt_threads != 128 && opt->dt_threads != 256)
         return fail(DAO_EINVAL, "dt_threads must be 0, 64, 128 or 256");
+    if (opt->dt_map < 0 || opt->dt_map > DT_MAP_CONSECUTIVE)
+        return fail(DAO_EINVAL, "dt_map must be 0, DAO_DT_GROUPED or DAO_DT_CONSECUTIVE");
+    if (opt->dose_form < 0 || opt->dose_form > DOSE_FORM_UNITS)
+        return fail(DAO_EINVAL, "dose_form must be 0, DAO_DOSE_LANES or DAO_DOSE_UNITS");
     if (opt->mlc_constraint < DAO_MLC_CONSECUTIVE || opt->mlc_constraint > DAO_MLC_JAWS)
         return fail(DAO_EINVAL, "mlc_constraint must be one of DAO_MLC_*");
     if (opt->mlc_constraint != DAO_MLC_CONSECUTIVE)
@@ -333,10 +337,11 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     int* t_C = nullptr;
     int* t_cnt = nullptr;
     unsigned* t_dmax = nullptr;
+    int* t_umax = nullptr;
     float* t_tval = nullptr;
     auto free_temps = [&]() {
         for (void* q : {(void*)t_rp, (void*)t_col, (void*)t_val, (void*)t_lab, (void*)t_plen, (void*)t_bsum,
-                        (void*)t_chk, (void*)t_C, (void*)t_cnt, (void*)t_dmax,
+                        (void*)t_chk, (void*)t_C, (void*)t_cnt, (void*)t_dmax, (void*)t_umax,
                         (void*)(prec == DAO_PREC_FP32 ? nullptr : t_tval)})
             if (q) pool_free(q, st);
     };
@@ -403,6 +408,7 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     DAO_TRY(talloc(&t_C, sizeof(int) * (size_t)n_ch * N));
     DAO_TRY(talloc(&t_cnt, sizeof(int) * N));
     DAO_TRY(talloc(&t_dmax, sizeof(unsigned)));
+    DAO_TRY(talloc(&t_umax, sizeof(int)));
     c->D.n_rows = V;
     c->D.n_cols = N;
     c->D.nnz_stored = padded;
@@ -411,6 +417,8 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     c->Dt.n_cols = V;
     c->Dt.prec = prec;
     c->Dt.tune_dt_threads = c->opt.dt_threads;
+    c->Dt.tune_dt_map = c->opt.dt_map;
+    c->D.tune_dose_form = c->opt.dose_form;
     float* scale = nullptr;
     DAO_TRY(c->dalloc(&scale, N));
     c->D.scale = scale;
@@ -428,12 +436,17 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
                            c->num_sms, st), "transpose counts and scales"));
     DAO_TRY(cu(build_fill_d(prec, t_rp, t_col, t_val, c->D.rowptr, V, scale, c->D, st), "padded D"));
     DAO_TRY(cu(build_seg(t_rp, t_col, c->D.rowptr, V, c->beam_off_d, B, c->seg, st), "beam segments"));
-    // counts and the largest |D_ij| back to the host: row offsets of D^T, tau
+    DAO_TRY(cu(build_unit_max(c->D.rowptr, V, pad_m, t_umax, st), "row units"));
+    // counts, the largest |D_ij| and the largest row unit back to the host: row
+    // offsets of D^T, tau, the dose SpMV's shared partials
     std::vector<int> cnt(N);
     unsigned dmax_bits = 0;
+    int umax = 0;
     DAO_TRY(cu(cudaMemcpyAsync(cnt.data(), t_cnt, sizeof(int) * N, cudaMemcpyDeviceToHost, st), "counts"));
     DAO_TRY(cu(cudaMemcpyAsync(&dmax_bits, t_dmax, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "max"));
+    DAO_TRY(cu(cudaMemcpyAsync(&umax, t_umax, sizeof(int), cudaMemcpyDeviceToHost, st), "units"));
     DAO_TRY(cu(cudaStreamSynchronize(st), "device build"));
+    c->D.unit_groups_max = std::max(umax, 1);
     std::vector<int> trow(N + 1, 0);
     int64_t tpadded = 0;
     for (int i = 0; i < N; ++i) {
@@ -1223,6 +1236,8 @@ void dao_options_default(dao_options* opt) {
     opt->mlc_constraint = DAO_MLC_CONSECUTIVE;
     opt->master_blocks = 0;
     opt->dt_threads = 0;
+    opt->dt_map = 0;
+    opt->dose_form = 0;
 }
 
 const char* dao_last_error(void) { return g_err.c_str(); }
@@ -1266,6 +1281,7 @@ dao_status create_common(const dao_csr* D, const dao_geometry* g, const dao_stru
     }
     if (st == DAO_OK) {
         e = master_configure();
+        if (e == cudaSuccess) e = spmv_configure();
         if (e != cudaSuccess) st = fail(DAO_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     }
     DeviceCSR gen;
@@ -1867,10 +1883,12 @@ std::string tune_key(const dao_ctx* c) {
     const double row_d = c->V > 0 ? (double)c->nnz / c->V : 0.0, row_t = c->N > 0 ? (double)c->nnz / c->N : 0.0;
     return dev + "|prec=" + std::to_string(c->opt.precision) + "|V=" + std::to_string(lb(c->V)) + "|N=" +
            std::to_string(lb(c->N)) + "|rowD=" + std::to_string(lb(row_d)) + "|rowDt=" + std::to_string(lb(row_t)) +
-           "|cold";
+           "|cold|forms";
 }
 
-bool tune_cache_read(const char* path, const std::string& key, int* dose_g, int* col_g, int* dt_t) {
+// One line per choice: "key dose_lanes column_lanes dt_threads dose_form dt_map".
+bool tune_cache_read(const char* path, const std::string& key, int* dose_g, int* col_g, int* dt_t, int* form,
+                     int* map) {
     if (!path) return false;
     FILE* f = std::fopen(path, "r");
     if (!f) return false;
@@ -1878,11 +1896,13 @@ bool tune_cache_read(const char* path, const std::string& key, int* dose_g, int*
     bool found = false;
     while (std::fgets(line, sizeof(line), f)) {  // the last entry for a key wins
         char k[400];
-        int a = 0, b = 0, t = 0;
-        if (std::sscanf(line, "%399s %d %d %d", k, &a, &b, &t) == 4 && key == k) {
+        int a = 0, b = 0, t = 0, fm = 0, mp = 0;
+        if (std::sscanf(line, "%399s %d %d %d %d %d", k, &a, &b, &t, &fm, &mp) == 6 && key == k) {
             *dose_g = a;
             *col_g = b;
             *dt_t = t;
+            *form = fm;
+            *map = mp;
             found = true;
         }
     }
@@ -2293,37 +2313,57 @@ dao_status dao_autotune(dao_ctx* c, const char* cache_path, dao_tuning* out) {
     TraceRange range("dao_autotune");
     DAO_TRY(check_ctx(c));
     const std::string key = tune_key(c);
-    int dg = 0, cg = 0, dt = 0;
-    bool cached = tune_cache_read(cache_path, key, &dg, &cg, &dt) && tune_allowed(TUNE_DOSE_G, dg) &&
-                  tune_allowed(TUNE_COL_G, cg) && tune_allowed(TUNE_DT_THREADS, dt);
+    int dg = 0, cg = 0, dt = 0, form = 0, map = 0;
+    const bool units_ok = dose_units_available(c->D);
+    bool cached = tune_cache_read(cache_path, key, &dg, &cg, &dt, &form, &map) && tune_allowed(TUNE_DOSE_G, dg) &&
+                  tune_allowed(TUNE_COL_G, cg) && tune_allowed(TUNE_DT_THREADS, dt) &&
+                  (form == DOSE_FORM_LANES || (form == DOSE_FORM_UNITS && units_ok)) &&
+                  (map == DT_MAP_GROUPED || map == DT_MAP_CONSECUTIVE);
     if (cached && c->opt.precision != DAO_PREC_FP32 && dg > 16) cached = false;
     if (!cached) {
         const int reps = 10;
+        auto time_dose = [&](double* us) {
+            return time_cold(c, reps, [&](int* nl) {
+                return launch_dose(c->D, c->x, c->vstruct, c->tf, c->ts, c->S, c->dose, nullptr, nullptr, 0, nullptr,
+                                   c->num_sms, c->stream, nl);
+            }, us, "dao_autotune");
+        };
+        // a1: lanes per voxel row of the lane form (the lane count is kept for
+        // the aperture column's defaults), then the unit form against the best
         double best = 1e300;
-        for (int g : TUNE_DOSE_G) {  // a1: lanes per voxel row
+        c->D.tune_dose_form = DOSE_FORM_LANES;
+        for (int g : TUNE_DOSE_G) {
             if (c->opt.precision != DAO_PREC_FP32 && g > 16) continue;
             c->D.tune_dose_g = g;
             double us = 0.0;
-            DAO_TRY(time_cold(c, reps, [&](int* nl) {
-                return launch_dose(c->D, c->x, c->vstruct, c->tf, c->ts, c->S, c->dose, nullptr, nullptr, 0, nullptr,
-                                   c->num_sms, c->stream, nl);
-            }, &us, "dao_autotune"));
+            DAO_TRY(time_dose(&us));
             if (us < best) {
                 best = us;
                 dg = g;
             }
         }
-        best = 1e300;
-        for (int t : TUNE_DT_THREADS) {  // a2: threads per beamlet row
-            c->Dt.tune_dt_threads = t;
+        form = DOSE_FORM_LANES;
+        if (units_ok) {
+            c->D.tune_dose_form = DOSE_FORM_UNITS;
             double us = 0.0;
-            DAO_TRY(time_cold(c, reps, [&](int* nl) { return launch_dt(c->Dt, c->pi, c->w, nullptr, c->stream, nl); },
-                               &us, "dao_autotune"));
-            if (us < best) {
-                best = us;
-                dt = t;
-            }
+            DAO_TRY(time_dose(&us));
+            if (us < best) form = DOSE_FORM_UNITS;
         }
+        best = 1e300;
+        for (int m : {DT_MAP_GROUPED, DT_MAP_CONSECUTIVE})  // a2: lane mapping x threads per beamlet row
+            for (int t : TUNE_DT_THREADS) {
+                c->Dt.tune_dt_threads = t;
+                c->Dt.tune_dt_map = m;
+                double us = 0.0;
+                DAO_TRY(time_cold(c, reps,
+                                  [&](int* nl) { return launch_dt(c->Dt, c->pi, c->w, nullptr, c->stream, nl); }, &us,
+                                  "dao_autotune"));
+                if (us < best) {
+                    best = us;
+                    dt = t;
+                    map = m;
+                }
+            }
         best = 1e300;
         for (int g : TUNE_COL_G) {  // a4: lanes per voxel row over beam 0's segment
             c->D.tune_col_g = g;
@@ -2340,20 +2380,24 @@ dao_status dao_autotune(dao_ctx* c, const char* cache_path, dao_tuning* out) {
         if (cache_path) {
             FILE* f = std::fopen(cache_path, "a");
             if (f) {
-                std::fprintf(f, "%s %d %d %d\n", key.c_str(), dg, cg, dt);
+                std::fprintf(f, "%s %d %d %d %d %d\n", key.c_str(), dg, cg, dt, form, map);
                 std::fclose(f);
             }
         }
     }
     c->D.tune_dose_g = dg;
+    c->D.tune_dose_form = form;
     c->D.tune_col_g = cg;
     c->Dt.tune_dt_threads = dt;
+    c->Dt.tune_dt_map = map;
     drop_round_graphs(c);
     if (out) {
         out->dose_lanes = dg;
         out->column_lanes = cg;
         out->dt_threads = dt;
         out->from_cache = cached ? 1 : 0;
+        out->dose_form = form;
+        out->dt_map = map;
     }
     return DAO_OK;
 }

@@ -430,6 +430,25 @@ cudaError_t build_seg(const int64_t* rp, const int* col, const int* prow, int V,
     return cudaGetLastError();
 }
 
+namespace {
+// One thread per unit of 32 rows: its group count, the largest into *out.
+__global__ void k_unit_max(const int* __restrict__ prow, int V, int epg, int* __restrict__ out) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r0 = u * 32;
+    if (r0 >= V) return;
+    const int r1 = min(r0 + 32, V);
+    atomicMax(out, (prow[r1] - prow[r0]) / epg);
+}
+}  // namespace
+
+cudaError_t build_unit_max(const int* prow, int V, int epg, int* out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int), s);
+    if (e != cudaSuccess || V < 1) return e;
+    const int units = (V + 31) / 32;
+    k_unit_max<<<(units + 255) / 256, 256, 0, s>>>(prow, V, epg, out);
+    return cudaGetLastError();
+}
+
 cudaError_t build_transpose_place(int prec, const int64_t* rp, const int* col, const float* val, int V, int CH, int N,
                                   int n_ch, int* C, const int* cnt, const float* scale, DevCSR& Dt, float* tval,
                                   int num_sms, cudaStream_t s) {

@@ -69,7 +69,21 @@ struct DevCSR {
     int tune_dose_g = 0;
     int tune_col_g = 0;
     int tune_dt_threads = 0;
+    // form of the dose SpMV (DOSE_FORM_*) and lane mapping of the transposed
+    // SpMV (DT_MAP_*); 0: the built-in rule
+    int tune_dose_form = 0;
+    int tune_dt_map = 0;
+    // D: the most groups (8 entries of 16-bit storage, 4 of FP32) in one unit of
+    // 32 consecutive rows; sizes the unit form's shared partials (0: not known)
+    int unit_groups_max = 0;
 };
+
+// Forms of the dose SpMV (a1): G lanes per voxel row over the row's groups,
+// or one warp per unit of 32 rows (the default where its shared memory fits).
+enum { DOSE_FORM_LANES = DAO_DOSE_LANES, DOSE_FORM_UNITS = DAO_DOSE_UNITS };
+// Lane mappings of the transposed SpMV (a2): a thread per group of 4 or 8
+// consecutive entries, or consecutive entries on consecutive threads (default).
+enum { DT_MAP_GROUPED = DAO_DT_GROUPED, DT_MAP_CONSECUTIVE = DAO_DT_CONSECUTIVE };
 
 // Launch shapes the autotuner may choose from.
 constexpr int TUNE_DOSE_G[] = {4, 8, 16, 32};
@@ -138,6 +152,11 @@ cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct,
                         float* z, float* grad, double* F_part, int F_blocks, double* F_out,
                         int num_sms, cudaStream_t stream, int* launches);
 int dose_grid(int n_rows, int num_sms);
+// The unit form of a1 fits shared memory for this matrix.
+bool dose_units_available(const DevCSR& D);
+// Process-wide dynamic shared-memory limits of the SpMV kernels (set once per
+// device, to a fixed size).
+cudaError_t spmv_configure();
 
 // a2: w = D^T pi over the beamlet-major transpose (skipped when *skip != 0).
 cudaError_t launch_dt(const DevCSR& Dt, const float* pi, float* w, const int* skip, cudaStream_t stream,
@@ -376,6 +395,9 @@ cudaError_t build_fill_d(int prec, const int64_t* rp, const int* col, const floa
                          const float* scale, DevCSR& D, cudaStream_t s);
 cudaError_t build_seg(const int64_t* rp, const int* col, const int* prow, int V, const int* beam_off, int B, int* seg,
                       cudaStream_t s);
+// The most groups of epg entries in one unit of 32 consecutive rows of the
+// padded D (row offsets prow), into *out (zeroed by the call).
+cudaError_t build_unit_max(const int* prow, int V, int epg, int* out, cudaStream_t s);
 cudaError_t build_transpose_place(int prec, const int64_t* rp, const int* col, const float* val, int V, int CH, int N,
                                   int n_ch, int* C, const int* cnt, const float* scale, DevCSR& Dt, float* tval,
                                   int num_sms, cudaStream_t s);

@@ -159,7 +159,9 @@ __device__ __forceinline__ void dt_row_ticket(const RowTicket& rt, int row, cons
 
 // One block per beamlet row of D^T; int4/float4 loads of (voxel, value),
 // gathered pi from L2; FP32 products, FP64 combination across threads.
-template <int BT>
+// LC: consecutive entries on consecutive threads (dt_row_sum_lc), else groups of
+// four entries per thread (dt_row_sum).
+template <int BT, bool LC>
 __global__ void __launch_bounds__(BT) k_dt(const int* __restrict__ rowptr, const int4* __restrict__ col4,
                                            const float4* __restrict__ val4, int N,
                                            const int* __restrict__ order,
@@ -169,7 +171,9 @@ __global__ void __launch_bounds__(BT) k_dt(const int* __restrict__ rowptr, const
     dt_round_snapshot(rt);
     if (skip != nullptr && *skip) return;
     const int row = order[blockIdx.x];  // longest rows first: they start in the first wave
-    const float s = dt_row_sum<BT>(rowptr, col4, val4, row, pi, s_red);
+    const float s = LC ? dt_row_sum_lc<BT>(rowptr, reinterpret_cast<const int*>(col4),
+                                           reinterpret_cast<const float*>(val4), row, pi, s_red)
+                       : dt_row_sum<BT>(rowptr, col4, val4, row, pi, s_red);
     if (threadIdx.x == 0) w[row] = s;
     dt_row_ticket(rt, row, w);
 }
@@ -300,9 +304,141 @@ __global__ void __launch_bounds__(256) k_dose16(const int* __restrict__ rowptr, 
     }
 }
 
+// ---- a1 in units of 32 voxel rows ------------------------------------------
+// One warp per unit of 32 consecutive rows (grid-stride over the units, every
+// block resident): the unit's entries are one contiguous range of groups (8
+// entries of 16-bit storage, 4 of FP32), which the lanes request together,
+// lane l the groups l, l + 32, ..., up to UB per lane at a time, so that the
+// whole unit is in flight at once and every request is a full 512-byte
+// warp access.  Each lane forms the dot product of its groups with x (staged
+// in shared memory, pre-multiplied by the beamlet scale) and writes it to
+// the warp's row of shared partials; then lane r sums row r's partials in
+// group order and applies the epilogue, so z, grad F and the labels are
+// accessed as 32 consecutive words.  The next unit's row offsets and labels
+// are requested before this unit's entries.  Fixed summation order: a row's
+// z is its groups' sequential FMA chains (from 0) summed in group order, the
+// same whichever warp or block computes it.
+constexpr int UNIT_ROWS = 32;
+constexpr int UNIT_THREADS = 512;
+
+template <bool L16, bool BF>
+__device__ __forceinline__ float group_dot(const uint4 c, const uint4 v, const float* __restrict__ sx) {
+    float p = 0.f;
+    if constexpr (L16) {
+        const unsigned cs[4] = {c.x, c.y, c.z, c.w};
+        const unsigned vs[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 f = unpack2<BF>(vs[q]);
+            p = fmaf(f.x, sx[cs[q] & 0xffffu], p);
+            p = fmaf(f.y, sx[cs[q] >> 16], p);
+        }
+    } else {
+        p = fmaf(__uint_as_float(v.x), sx[c.x], p);
+        p = fmaf(__uint_as_float(v.y), sx[c.y], p);
+        p = fmaf(__uint_as_float(v.z), sx[c.z], p);
+        p = fmaf(__uint_as_float(v.w), sx[c.w], p);
+    }
+    return p;
+}
+
+template <bool L16, bool BF>
+__global__ void __launch_bounds__(UNIT_THREADS, 2) k_dose_units(
+    const int* __restrict__ rowptr, const uint4* __restrict__ colg, const uint4* __restrict__ valg, int V,
+    const float* __restrict__ x, const float* __restrict__ scale, int N, const uint8_t* __restrict__ vstruct,
+    const StructTermsS* __restrict__ ts, int S, float* __restrict__ z, float* __restrict__ grad,
+    double* __restrict__ F_part, int part_cap) {
+    constexpr int EPG = L16 ? 8 : 4;  // entries per group (one 16-byte load of columns and of values)
+    constexpr int UB = 4;             // groups per lane in flight
+    constexpr int NW = UNIT_THREADS / 32;
+    extern __shared__ __align__(16) float s_dyn_units[];
+    __shared__ StructTermsS s_ts[SMAX];
+    __shared__ double s_red[NW];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float* sx = s_dyn_units;
+    float* spart = s_dyn_units + ((N + 3) & ~3) + wib * part_cap;
+    const int n_units = (V + UNIT_ROWS - 1) / UNIT_ROWS;
+    const int W = gridDim.x * NW;
+    int u = blockIdx.x * NW + wib;
+    // this unit's row offsets and labels first, so that they are in flight
+    // while x is staged
+    int rs = 0, re = 0, lab = 0;
+    auto meta = [&](int uu, int& a, int& b, int& l) {
+        const int row = uu * UNIT_ROWS + lane;
+        a = b = 0;
+        l = 0;
+        if (uu < n_units && row < V) {
+            a = __ldg(rowptr + row);
+            b = __ldg(rowptr + row + 1);
+            if (S >= 0) l = __ldg(vstruct + row);
+        }
+    };
+    meta(u, rs, re, lab);
+    for (int i = threadIdx.x; i < N; i += UNIT_THREADS) sx[i] = L16 ? __ldg(x + i) * __ldg(scale + i) : __ldg(x + i);
+    for (int i = threadIdx.x; i < S; i += UNIT_THREADS) s_ts[i] = ts[i];
+    __syncthreads();
+    float facc = 0.f;
+    for (; u < n_units; u += W) {
+        const int row0 = u * UNIT_ROWS;
+        const int nrow = min(UNIT_ROWS, V - row0);
+        const int e0 = __shfl_sync(FULL, rs, 0);
+        const int e1 = __shfl_sync(FULL, re, nrow - 1);
+        int rs_n, re_n, lab_n;
+        meta(u + W, rs_n, re_n, lab_n);
+        const int g0 = e0 / EPG, ng = (e1 - e0) / EPG;
+        float acc = 0.f;
+        if (ng <= part_cap) {
+            for (int k0 = 0; k0 < ng; k0 += 32 * UB) {
+                uint4 c[UB], v[UB];
+#pragma unroll
+                for (int q = 0; q < UB; ++q) {
+                    const int g = k0 + q * 32 + lane;
+                    if (g < ng) {
+                        c[q] = __ldg(colg + g0 + g);
+                        v[q] = __ldg(valg + g0 + g);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < UB; ++q) {
+                    const int g = k0 + q * 32 + lane;
+                    if (g < ng) spart[g] = group_dot<L16, BF>(c[q], v[q], sx);
+                }
+            }
+            __syncwarp();
+            if (lane < nrow)
+                for (int g = (rs - e0) / EPG, gh = (re - e0) / EPG; g < gh; ++g) acc += spart[g];
+            __syncwarp();  // the partials are rewritten by the next unit
+        } else if (lane < nrow) {
+            // a unit larger than the partial row (not produced by a plan's
+            // layout, whose largest unit sizes part_cap): the same sums, the
+            // groups read by the row's own lane
+            for (int g = rs / EPG, gh = re / EPG; g < gh; ++g) acc += group_dot<L16, BF>(__ldg(colg + g), __ldg(valg + g), sx);
+        }
+        if (lane < nrow) {
+            const int row = row0 + lane;
+            z[row] = acc;
+            if (grad != nullptr || F_part != nullptr) {
+                const StructTermsS tt = S >= 0 ? s_ts[lab] : ts[row];
+                const float uu = fmaxf((tt.tu_hi - acc) + tt.tu_lo, 0.f);  // T^- - z
+                const float o = fmaxf((acc - tt.to_hi) - tt.to_lo, 0.f);   // z - T^+
+                if (grad != nullptr) grad[row] = 2.f * (tt.b * o - tt.a * uu);
+                facc = fmaf(tt.a * uu, uu, fmaf(tt.b * o, o, facc));
+            }
+        }
+        rs = rs_n;
+        re = re_n;
+        lab = lab_n;
+    }
+    if (F_part != nullptr) {
+        const double sres = block_sum_mixed<UNIT_THREADS>(facc, s_red);
+        if (threadIdx.x == 0) F_part[blockIdx.x] = sres;
+    }
+}
+
 // a2 with rows padded to 8 entries: two int4 loads of voxel indices and one uint4
-// of values per 8 entries; the row's scale is applied once at the end.
-template <int BT, bool BF>
+// of values per 8 entries (LC: consecutive entries on consecutive threads);
+// the row's scale is applied once at the end.
+template <int BT, bool BF, bool LC>
 __global__ void __launch_bounds__(BT) k_dt16(const int* __restrict__ rowptr, const int4* __restrict__ col4,
                                              const uint4* __restrict__ val8, const float* __restrict__ scale, int N,
                                              const int* __restrict__ order,
@@ -312,7 +448,9 @@ __global__ void __launch_bounds__(BT) k_dt16(const int* __restrict__ rowptr, con
     dt_round_snapshot(rt);
     if (skip != nullptr && *skip) return;
     const int row = order[blockIdx.x];  // longest rows first
-    const float s = dt16_row_sum<BT, BF>(rowptr, col4, val8, scale, row, pi, s_red);
+    const float s = LC ? dt16_row_sum_lc<BT, BF>(rowptr, reinterpret_cast<const int*>(col4),
+                                                 reinterpret_cast<const unsigned short*>(val8), scale, row, pi, s_red)
+                       : dt16_row_sum<BT, BF>(rowptr, col4, val8, scale, row, pi, s_red);
     if (threadIdx.x == 0) w[row] = s;
     dt_row_ticket(rt, row, w);
 }
@@ -454,6 +592,33 @@ cudaError_t dose16_g(const DevCSR& D, const float* x, const uint8_t* vstruct, co
     return cudaGetLastError();
 }
 
+// Dynamic shared memory of the unit form: x (N floats) and one row of
+// part_cap partials per warp.
+constexpr int UNITS_SMEM_MAX = 200 * 1024;
+size_t units_smem(int N, int part_cap) {
+    return (size_t)((N + 3) & ~3) * sizeof(float) + (size_t)(UNIT_THREADS / 32) * part_cap * sizeof(float);
+}
+
+template <bool L16, bool BF>
+cudaError_t dose_units(const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsS* ts, int S,
+                       float* z, float* grad, double* F_part, int& grid, int num_sms, cudaStream_t stream) {
+    const size_t smem = units_smem(D.n_cols, D.unit_groups_max);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_dose_units<L16, BF>, UNIT_THREADS, smem) !=
+            cudaSuccess ||
+        occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    grid = std::min(grid, occ * num_sms);
+    const void* colp = L16 ? static_cast<const void*>(D.col16) : static_cast<const void*>(D.col);
+    const void* valp = L16 ? static_cast<const void*>(D.val16) : static_cast<const void*>(D.val);
+    k_dose_units<L16, BF><<<grid, UNIT_THREADS, smem, stream>>>(
+        D.rowptr, static_cast<const uint4*>(colp), static_cast<const uint4*>(valp), D.n_rows, x, D.scale, D.n_cols,
+        vstruct, ts, S, z, grad, F_part, D.unit_groups_max);
+    return cudaGetLastError();
+}
+
 template <int G>
 cudaError_t dose_g(const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsS* ts, int S,
                    float* z, float* grad, double* F_part, int& grid, int num_sms, cudaStream_t stream) {
@@ -508,21 +673,30 @@ cudaError_t dose16_any(int g, const DevCSR& D, const float* x, const uint8_t* vs
     }
 }
 
-template <int BT>
+template <int BT, bool LC>
 void dt_launch(const DevCSR& Dt, const float* pi, float* w, const int* skip, const RowTicket& rt,
                cudaStream_t stream) {
     if (Dt.prec == DAO_PREC_FP16)
-        k_dt16<BT, false><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
-                                                        reinterpret_cast<const uint4*>(Dt.val16), Dt.scale,
-                                                        Dt.n_rows, Dt.order, pi, w, skip, rt);
+        k_dt16<BT, false, LC><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
+                                                            reinterpret_cast<const uint4*>(Dt.val16), Dt.scale,
+                                                            Dt.n_rows, Dt.order, pi, w, skip, rt);
     else if (Dt.prec == DAO_PREC_BF16)
-        k_dt16<BT, true><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
-                                                       reinterpret_cast<const uint4*>(Dt.val16), Dt.scale,
-                                                       Dt.n_rows, Dt.order, pi, w, skip, rt);
+        k_dt16<BT, true, LC><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
+                                                           reinterpret_cast<const uint4*>(Dt.val16), Dt.scale,
+                                                           Dt.n_rows, Dt.order, pi, w, skip, rt);
     else
-        k_dt<BT><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
-                                                reinterpret_cast<const float4*>(Dt.val), Dt.n_rows, Dt.order, pi, w,
-                                                skip, rt);
+        k_dt<BT, LC><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
+                                                    reinterpret_cast<const float4*>(Dt.val), Dt.n_rows, Dt.order, pi,
+                                                    w, skip, rt);
+}
+
+template <int BT>
+void dt_launch_map(const DevCSR& Dt, const float* pi, float* w, const int* skip, const RowTicket& rt,
+                   cudaStream_t stream) {
+    if (Dt.tune_dt_map == DT_MAP_GROUPED)
+        dt_launch<BT, false>(Dt, pi, w, skip, rt, stream);
+    else
+        dt_launch<BT, true>(Dt, pi, w, skip, rt, stream);
 }
 
 template <int G>
@@ -557,6 +731,18 @@ void column_dev_launch(const DevCSR& D, const int* seg, const int* ap_beam, int 
 
 }  // namespace
 
+bool dose_units_available(const DevCSR& D) {
+    return D.unit_groups_max > 0 && units_smem(D.n_cols, D.unit_groups_max) <= (size_t)UNITS_SMEM_MAX;
+}
+
+cudaError_t spmv_configure() {
+    cudaError_t e = cudaSuccess;
+    for (const void* k : {(const void*)k_dose_units<false, false>, (const void*)k_dose_units<true, false>,
+                          (const void*)k_dose_units<true, true>})
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, UNITS_SMEM_MAX);
+    return e;
+}
+
 cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsF* tf,
                         const StructTermsS* ts, int S, float* z, float* grad, double* F_part, int F_blocks,
                         double* F_out, int num_sms, cudaStream_t stream, int* launches) {
@@ -564,8 +750,15 @@ cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct,
     int grid = dose_grid(D.n_rows, num_sms);  // at most this many; resident_grid trims it
     if (F_part != nullptr && F_blocks < grid) return cudaErrorInvalidValue;
     const int g = dose_lanes(D);
+    const bool units = D.tune_dose_form != DOSE_FORM_LANES && dose_units_available(D);
     cudaError_t e;
-    if (D.prec == DAO_PREC_BF16)
+    if (units && D.prec == DAO_PREC_FP32)
+        e = dose_units<false, false>(D, x, vstruct, ts, S, z, grad, F_part, grid, num_sms, stream);
+    else if (units && D.prec == DAO_PREC_FP16)
+        e = dose_units<true, false>(D, x, vstruct, ts, S, z, grad, F_part, grid, num_sms, stream);
+    else if (units)
+        e = dose_units<true, true>(D, x, vstruct, ts, S, z, grad, F_part, grid, num_sms, stream);
+    else if (D.prec == DAO_PREC_BF16)
         e = dose16_any<true>(g, D, x, vstruct, ts, S, z, grad, F_part, grid, num_sms, stream);
     else if (D.prec == DAO_PREC_FP16)
         e = dose16_any<false>(g, D, x, vstruct, ts, S, z, grad, F_part, grid, num_sms, stream);
@@ -590,9 +783,9 @@ static cudaError_t dt_dispatch(const DevCSR& Dt, const float* pi, float* w, cons
     // one block per beamlet row; 64 threads by default, so that up to 32 blocks
     // per SM keep every row resident in one wave
     switch (Dt.tune_dt_threads) {
-        case 128: dt_launch<128>(Dt, pi, w, skip, rt, stream); break;
-        case 256: dt_launch<256>(Dt, pi, w, skip, rt, stream); break;
-        default: dt_launch<64>(Dt, pi, w, skip, rt, stream); break;
+        case 128: dt_launch_map<128>(Dt, pi, w, skip, rt, stream); break;
+        case 256: dt_launch_map<256>(Dt, pi, w, skip, rt, stream); break;
+        default: dt_launch_map<64>(Dt, pi, w, skip, rt, stream); break;
     }
     ++*launches;
     return cudaGetLastError();

@@ -118,6 +118,70 @@ __device__ __forceinline__ float dt16_row_sum(const int* __restrict__ rowptr, co
     return (float)(sres * (double)scale[row]);
 }
 
+// a2 with consecutive entries on consecutive threads: thread t takes entries
+// e0 + t, e0 + t + BT, ... of the row, U at a time, the next U requested while
+// the current U's pi gathers run.  A row of D^T lists its voxels in increasing
+// order, so the 32 gathers of one warp instruction fall on a few cache lines
+// (the grouped form above spreads them over 8 x 32 entries).  Scalar loads of
+// the voxel index (and the 16-bit value); padding entries (value 0, a valid
+// voxel) are summed like the others.
+template <int BT, int U, class LoadV>
+__device__ __forceinline__ float dt_row_consecutive(int e0, int e1, const int* __restrict__ col, LoadV loadv,
+                                                    const float* __restrict__ pi) {
+    float acc = 0.f;
+    int e = e0 + (int)threadIdx.x;
+    int cn[U];
+    float vn[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+        const int p = e + q * BT;
+        cn[q] = p < e1 ? __ldg(col + p) : -1;
+        vn[q] = p < e1 ? loadv(p) : 0.f;
+    }
+    while (e < e1) {
+        int c[U];
+        float v[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            c[q] = cn[q];
+            v[q] = vn[q];
+        }
+        e += BT * U;
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int p = e + q * BT;
+            cn[q] = p < e1 ? __ldg(col + p) : -1;
+            vn[q] = p < e1 ? loadv(p) : 0.f;
+        }
+        float a[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) a[q] = c[q] >= 0 ? __ldg(pi + c[q]) : 0.f;
+#pragma unroll
+        for (int q = 0; q < U; ++q) acc = fmaf(v[q], a[q], acc);
+    }
+    return acc;
+}
+
+template <int BT>
+__device__ __forceinline__ float dt_row_sum_lc(const int* __restrict__ rowptr, const int* __restrict__ col,
+                                               const float* __restrict__ val, int row, const float* __restrict__ pi,
+                                               double* s_red) {
+    const float acc = dt_row_consecutive<BT, 4>(rowptr[row], rowptr[row + 1], col,
+                                                [&](int p) { return __ldg(val + p); }, pi);
+    return (float)block_sum_mixed<BT>(acc, s_red);
+}
+
+template <int BT, bool BF>
+__device__ __forceinline__ float dt16_row_sum_lc(const int* __restrict__ rowptr, const int* __restrict__ col,
+                                                 const unsigned short* __restrict__ val,
+                                                 const float* __restrict__ scale, int row,
+                                                 const float* __restrict__ pi, double* s_red) {
+    const float acc = dt_row_consecutive<BT, 4>(rowptr[row], rowptr[row + 1], col,
+                                                [&](int p) { return unpack1<BF>(__ldg(val + p)); }, pi);
+    const double sres = block_sum_mixed<BT>(acc, s_red);
+    return (float)(sres * (double)scale[row]);
+}
+
 // ---- a4 ---------------------------------------------------------------------
 // The caller's threads are [wbase, wbase + blockDim) of wcount threads sharing
 // the rows (a grid, or a group of blocks).

@@ -49,6 +49,9 @@ def test_options_default_on_host(lib):
     o = binding.options()
     assert o.k_max == 64 and o.max_master_iters == 50 and o.precision == 0
     assert o.master_tol == 1e-6
+    assert o.dt_map == 0 and o.dose_form == 0
+    assert binding.options(dt_map="grouped", dose_form="units").dt_map == binding.DAO_DT_GROUPED
+    assert binding.options(dose_form="lanes").dose_form == binding.DAO_DOSE_LANES
 
 
 def _tiny_inputs():
@@ -110,6 +113,13 @@ def test_create_rejects_wide_rows_and_pool_sizes(lib):
     d["N"] = 40
     st, msg = _create(lib, d)
     assert st == -1 and "[1, 32]" in msg
+
+
+@pytest.mark.parametrize("opt,needle", [({"dt_map": 3}, "dt_map"), ({"dt_map": -1}, "dt_map"),
+                                        ({"dose_form": 3}, "dose_form"), ({"dt_threads": 96}, "dt_threads")])
+def test_create_rejects_unknown_kernel_forms(lib, opt, needle):
+    st, msg = _create(lib, _tiny_inputs(), **opt)
+    assert st == -1 and needle in msg, (st, msg)
 
 
 def test_null_arguments(lib):

@@ -72,7 +72,8 @@ class _Plan:
         pass
 
     def autotune(self, cache_path=None):
-        return {"dose_lanes": 8, "column_lanes": 8, "dt_threads": 64, "from_cache": False}
+        return {"dose_lanes": 8, "column_lanes": 8, "dt_threads": 64, "dose_form": "units", "dt_map": "consecutive",
+                "from_cache": False}
 
     def reset(self):
         self.k = 0
@@ -117,6 +118,7 @@ def test_gpu_arm_runs_on_stand_ins_and_prints_the_contract_line(monkeypatch, cap
     monkeypatch.setitem(sys.modules, "torch", _fake_torch())
     monkeypatch.setattr(pkg, "Plan", _Plan)
     monkeypatch.setattr(build, "build", lambda *a, **k: None)
+    monkeypatch.setattr(bench, "strip_case", lambda case: case)   # no device generation here
     monkeypatch.setenv("PATH", str(tmp_path))            # no nvidia-smi: the clock record is null
     monkeypatch.setenv("DAO_BENCH_CLOCKS_DIR", str(tmp_path))
     for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
@@ -139,6 +141,9 @@ def test_gpu_arm_runs_on_stand_ins_and_prints_the_contract_line(monkeypatch, cap
     r = d["roofline"]
     assert r["kernel"] == "k_master_persist" and r["unit"] == "GB/s" and 0 < r["frac"] < 10
     assert set(d["spmv"]) == {"fp32", "fp16"} and d["spmv"]["fp32"]["dose"]["us"] == 22.5
+    assert d["spmv"]["fp32"]["form"]["dose"] == "units" and d["spmv"]["fp32"]["form"]["dt_map"] == "consecutive"
+    st = d["spmv_strip_profile"]
+    assert set(st) == {"nnz", "nnz_gauss", "fp32", "fp16"} and st["fp16"]["dt"]["us"] == 19.5
     assert d["mixed_precision"]["other_ms_per_plan"] == 8.5
     e = d["e2e"]
     assert e["inputs"] == "page-locked host arrays" and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0

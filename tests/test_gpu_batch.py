@@ -121,6 +121,7 @@ def test_autotune_choice_cache_and_parity(torch, tmp_path, prec):
         assert not t1["from_cache"]
         assert t1["dose_lanes"] in ((4, 8, 16, 32) if prec == 0 else (4, 8, 16))
         assert t1["column_lanes"] in (4, 8, 16) and t1["dt_threads"] in (64, 128, 256)
+        assert t1["dose_form"] in ("lanes", "units") and t1["dt_map"] in ("grouped", "consecutive")
         x = np.random.default_rng(1).uniform(0.0, 2.0, size=case.n_beamlets).astype(np.float32)
         zd = torch.empty(case.n_voxels, dtype=torch.float32, device="cuda")
         p.k_dose(torch.from_numpy(x).cuda(), zd)
@@ -138,8 +139,10 @@ def test_autotune_choice_cache_and_parity(torch, tmp_path, prec):
     assert t2["from_cache"] and {k: t2[k] for k in t1 if k != "from_cache"} == \
         {k: t1[k] for k in t1 if k != "from_cache"}
     lines = open(cache).read().splitlines()
+    forms = {"lanes": "1", "units": "2", "grouped": "1", "consecutive": "2"}
     assert len(lines) == 1 and lines[0].split()[1:] == [str(t1["dose_lanes"]), str(t1["column_lanes"]),
-                                                       str(t1["dt_threads"])]
+                                                       str(t1["dt_threads"]), forms[t1["dose_form"]],
+                                                       forms[t1["dt_map"]]]
 
 
 def test_batch_of_full_size_instances_against_the_oracle(torch):

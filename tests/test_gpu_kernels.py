@@ -37,11 +37,15 @@ def _plan(case, torch, **opt):
     return Plan(case, stream=torch.cuda.current_stream().cuda_stream, **opt)
 
 
+@pytest.mark.parametrize("form", ["lanes", "units"])
 @pytest.mark.parametrize("name,case", CASES, ids=[c[0] for c in CASES])
-def test_dose_spmv_and_epilogue(torch, name, case):
+def test_dose_spmv_and_epilogue(torch, name, case, form):
+    """a1 in both forms (dao_options.dose_form).  The unit form sums each group
+    of 4 (FP32) or 8 entries in order and then the row's groups in order: no
+    term passes through more than min(n, 8) + groups - 1 <= n + 6 roundings."""
     rng = np.random.default_rng(1)
     x = rng.uniform(0.0, 2.0, size=case.n_beamlets).astype(np.float32)
-    with _plan(case, torch) as plan:
+    with _plan(case, torch, dose_form=form) as plan:
         xd = torch.from_numpy(x).cuda()
         zd = torch.empty(case.n_voxels, dtype=torch.float32, device="cuda")
         gd = torch.empty_like(zd)
@@ -66,15 +70,18 @@ def test_dose_spmv_and_epilogue(torch, name, case):
     assert abs(F - Fex) <= 1e-5 * abs(Fex) + 1e-300
 
 
+@pytest.mark.parametrize("dt_map", ["grouped", "consecutive"])
 @pytest.mark.parametrize("dt_threads", [0, 128, 256])
 @pytest.mark.parametrize("name,case", CASES, ids=[c[0] for c in CASES])
-def test_transposed_spmv(torch, name, case, dt_threads):
+def test_transposed_spmv(torch, name, case, dt_threads, dt_map):
     """a2 with the default block size and with 128 or 256 threads per beamlet row
-    (dao_options.dt_threads): a thread's chain only gets shorter with more
-    threads, so the 64-thread bound holds for all."""
+    (dao_options.dt_threads), in both lane mappings (dao_options.dt_map): a
+    thread's chain only gets shorter with more threads, and the consecutive
+    mapping's chain (ceil(n / threads) entries) is no longer than the grouped
+    one's, so the 64-thread grouped bound holds for all."""
     rng = np.random.default_rng(2)
     pi = rng.normal(size=case.n_voxels).astype(np.float32)
-    with _plan(case, torch, dt_threads=dt_threads) as plan:
+    with _plan(case, torch, dt_threads=dt_threads, dt_map=dt_map) as plan:
         pd = torch.from_numpy(pi).cuda()
         wd = torch.empty(case.n_beamlets, dtype=torch.float32, device="cuda")
         plan.k_beamlet_prices(pd, wd)
