@@ -61,6 +61,9 @@ def _args():
                    help="requests of the serving leg's Poisson stream (4 per second)")
     p.add_argument("--serve-burst", type=int, default=64,
                    help="requests of the serving leg's burst (200 per second: the server under load)")
+    p.add_argument("--serve-fp32-single", type=int, default=600,
+                   help="requests of the same Poisson stream served by the plain form (FP32, one plan at a time); "
+                        "0: skip")
     p.add_argument("--batch", type=int, default=16, help="instances per workload in the batched re-plan leg")
     a = p.parse_args()
     if a.precision is None:
@@ -416,16 +419,17 @@ def serve_pool(n_each):
         return pool.map(_make_case_spec, specs)
 
 
-def run_serve(dev, pool, n_requests, apertures, rate_per_s=4.0, seed=9000, **plan_opt):
+def run_serve(dev, pool, n_requests, apertures, rate_per_s=4.0, seed=9000, max_slots=8, **plan_opt):
     """Poisson arrivals (rate 4 per second, seeded exponential gaps) of re-plan
     requests drawn from the pool; each request uploads its D and plans
     ``apertures`` apertures.  Latency is submission to results on the host.
-    ``plan_opt``: dao_options of every plan (storage precision, master blocks)."""
+    ``plan_opt``: dao_options of every plan (storage precision, master blocks);
+    ``max_slots`` 1 serves one plan at a time in arrival order."""
     from paper_1003_5402_gb300 import Server
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate_per_s, size=n_requests)
     which = rng.integers(0, len(pool), size=n_requests)
-    with Server(max_slots=8, device=dev, **plan_opt) as srv:
+    with Server(max_slots=max_slots, device=dev, **plan_opt) as srv:
         # warm-up, as a long-running server is: one request of each size at
         # once, so that the library's memory pool already holds two concurrent
         # plans of the larger size (its one-time growth, tens of ms, is not a
@@ -452,7 +456,8 @@ def run_serve(dev, pool, n_requests, apertures, rate_per_s=4.0, seed=9000, **pla
                   "p99": round(float(np.percentile([r[k] for r in res], 99)), 3)}
               for k in ("queue_ms", "create_ms", "solve_ms", "finish_ms")}
     errors = sorted({f'{r["status"]}: {r["error"]}' for r in res if r["status"] not in (0, 1, 2)})
-    return {"requests": n_requests, "rate_per_s": rate_per_s, "completed_ok": int(ok), "errors": errors[:4],
+    return {"requests": n_requests, "rate_per_s": rate_per_s, "max_slots": max_slots, "completed_ok": int(ok),
+            "errors": errors[:4],
             "plan_options": {k: v for k, v in plan_opt.items()},
             "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
             "max_ms": round(float(np.max(lat)), 3), "phases": phases,
@@ -735,6 +740,15 @@ def run_ours(a):
                               precision=PREC["fp16"])
             serve["burst"] = {k: burst[k] for k in ("requests", "rate_per_s", "completed_ok", "errors", "p50_ms", "p99_ms",
                                                     "max_ms", "max_active", "plans_per_s", "phases")}
+        if a.serve_fp32_single > 0:
+            # the plain form on the same Poisson stream: FP32 storage, one plan
+            # at a time in arrival order (a request that arrives while a plan
+            # runs waits for it)
+            single = run_serve(dev, serve_cases, a.serve_fp32_single, a.apertures, max_slots=1,
+                               precision=PREC["fp32"])
+            serve["fp32_single_slot"] = {k: single[k] for k in ("requests", "rate_per_s", "max_slots", "completed_ok",
+                                                                "errors", "p50_ms", "p99_ms", "max_ms", "plans_per_s",
+                                                                "phases", "queue_p99_ms")}
 
     cpu = None
     if rank == 0 and ws == 1 and not a.skip_cpu:

@@ -140,6 +140,8 @@ typedef struct dao_options {
                                 * fits, or the autotuner's choice), DAO_DOSE_LANES (2 to 32 lanes per voxel
                                 * row) or DAO_DOSE_UNITS (one warp per 32 consecutive rows, their entries
                                 * requested at once) */
+    int32_t column_lanes;      /* lanes per voxel row of the aperture column (a4): 0 (default: 8, or the
+                                * autotuner's choice), 1, 2, 4, 8 or 16 */
 } dao_options;
 
 enum { DAO_DT_GROUPED = 1, DAO_DT_CONSECUTIVE = 2 };
@@ -450,7 +452,7 @@ int32_t dao_batch_group_size(int32_t n, int32_t device);
  * Times the dose SpMV (a1: the lane form with 4/8/16/32 lanes per voxel row,
  * 16-bit storage up to 16, and the unit form), the transposed SpMV (a2, threads
  * per beamlet row: 64/128/256, each with both lane mappings) and the
- * aperture column (a4, lanes per voxel row: 4/8/16) on the context's own
+ * aperture column (a4, lanes per voxel row: 1/2/4/8/16) on the context's own
  * matrices (10 launches per candidate, each after a read of a buffer twice the
  * L2 size, so that it runs on a cold cache as in a plan; median of the
  * per-launch event times) and keeps the fastest of each for this context.

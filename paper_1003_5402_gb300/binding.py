@@ -57,7 +57,7 @@ class dao_options(C.Structure):
                 ("price_tol", C.c_double), ("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
                 ("use_graphs", C.c_int32), ("master_persistent", C.c_int32), ("mlc_constraint", C.c_int32),
                 ("master_blocks", C.c_int32), ("dt_threads", C.c_int32), ("dt_map", C.c_int32),
-                ("dose_form", C.c_int32)]
+                ("dose_form", C.c_int32), ("column_lanes", C.c_int32)]
 
 
 class dao_tuning(C.Structure):

@@ -262,6 +262,9 @@ dao_status validate(const dao_csr* D, const dao_geometry* g, const dao_structure
         return fail(DAO_EINVAL, "dt_map must be 0, DAO_DT_GROUPED or DAO_DT_CONSECUTIVE");
     if (opt->dose_form < 0 || opt->dose_form > DOSE_FORM_UNITS)
         return fail(DAO_EINVAL, "dose_form must be 0, DAO_DOSE_LANES or DAO_DOSE_UNITS");
+    if (opt->column_lanes != 0 && opt->column_lanes != 1 && opt->column_lanes != 2 && opt->column_lanes != 4 &&
+        opt->column_lanes != 8 && opt->column_lanes != 16)
+        return fail(DAO_EINVAL, "column_lanes must be 0, 1, 2, 4, 8 or 16");
     if (opt->mlc_constraint < DAO_MLC_CONSECUTIVE || opt->mlc_constraint > DAO_MLC_JAWS)
         return fail(DAO_EINVAL, "mlc_constraint must be one of DAO_MLC_*");
     if (opt->mlc_constraint != DAO_MLC_CONSECUTIVE)
@@ -419,6 +422,7 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     c->Dt.tune_dt_threads = c->opt.dt_threads;
     c->Dt.tune_dt_map = c->opt.dt_map;
     c->D.tune_dose_form = c->opt.dose_form;
+    c->D.tune_col_g = c->opt.column_lanes;
     float* scale = nullptr;
     DAO_TRY(c->dalloc(&scale, N));
     c->D.scale = scale;
@@ -1238,6 +1242,7 @@ void dao_options_default(dao_options* opt) {
     opt->dt_threads = 0;
     opt->dt_map = 0;
     opt->dose_form = 0;
+    opt->column_lanes = 0;
 }
 
 const char* dao_last_error(void) { return g_err.c_str(); }

@@ -87,7 +87,7 @@ enum { DT_MAP_GROUPED = DAO_DT_GROUPED, DT_MAP_CONSECUTIVE = DAO_DT_CONSECUTIVE 
 
 // Launch shapes the autotuner may choose from.
 constexpr int TUNE_DOSE_G[] = {4, 8, 16, 32};
-constexpr int TUNE_COL_G[] = {4, 8, 16};
+constexpr int TUNE_COL_G[] = {1, 2, 4, 8, 16};
 constexpr int TUNE_DT_THREADS[] = {64, 128, 256};
 
 // Projected-Newton master state (device memory, one per context).

@@ -807,6 +807,8 @@ cudaError_t launch_column(const DevCSR& D, const int* seg_lo, const int* seg_hi,
     if (D.n_rows == 0) return cudaSuccess;
     const int grid = num_sms * 8;
     switch (D.tune_col_g) {
+        case 1: column_launch<1>(D, seg_lo, seg_hi, base, nb, mask, out, stride, grid, stream); break;
+        case 2: column_launch<2>(D, seg_lo, seg_hi, base, nb, mask, out, stride, grid, stream); break;
         case 4: column_launch<4>(D, seg_lo, seg_hi, base, nb, mask, out, stride, grid, stream); break;
         case 16: column_launch<16>(D, seg_lo, seg_hi, base, nb, mask, out, stride, grid, stream); break;
         default: column_launch<8>(D, seg_lo, seg_hi, base, nb, mask, out, stride, grid, stream); break;
@@ -821,6 +823,12 @@ cudaError_t launch_column_dev(const DevCSR& D, const int* seg, const int* ap_bea
     if (D.n_rows == 0) return cudaSuccess;
     const int grid = num_sms * 8;
     switch (D.tune_col_g) {
+        case 1:
+            column_dev_launch<1>(D, seg, ap_beam, K, beam_off, rows, cols, max_nb, mask, slab, ld, cg, grid, stream);
+            break;
+        case 2:
+            column_dev_launch<2>(D, seg, ap_beam, K, beam_off, rows, cols, max_nb, mask, slab, ld, cg, grid, stream);
+            break;
         case 4:
             column_dev_launch<4>(D, seg, ap_beam, K, beam_off, rows, cols, max_nb, mask, slab, ld, cg, grid, stream);
             break;
@@ -854,6 +862,8 @@ cudaError_t launch_commit_column(const DevCSR& D, const CommitArgs& ca, int max_
     const int grid = num_sms * 8;
     const size_t sm = (size_t)std::max(ca.n_beams, 1) * sizeof(double) + (size_t)std::max(max_nb, 1) * sizeof(float);
     switch (D.tune_col_g) {
+        case 1: commit_column_launch<1>(D, ca, sm, grid, stream); break;
+        case 2: commit_column_launch<2>(D, ca, sm, grid, stream); break;
         case 4: commit_column_launch<4>(D, ca, sm, grid, stream); break;
         case 16: commit_column_launch<16>(D, ca, sm, grid, stream); break;
         default: commit_column_launch<8>(D, ca, sm, grid, stream); break;

@@ -125,11 +125,16 @@ def test_pricing_bit_exact_lockstep(torch, name, case, kind):
     assert np.array_equal(row_lr, np.concatenate(ref.row_leaves))
 
 
+@pytest.mark.parametrize("lanes", [0, 1, 2, 16])
 @pytest.mark.parametrize("name,case", CASES, ids=[c[0] for c in CASES])
-def test_aperture_column(torch, name, case):
+def test_aperture_column(torch, name, case, lanes):
+    """a4 with the default 8 lanes per voxel row and with 1, 2 or 16
+    (dao_options.column_lanes): a lane sums ceil(n / lanes) entries in order,
+    then a shuffle tree of log2(lanes) levels."""
     rng = np.random.default_rng(4)
     D = O.csr64(case)
-    with _plan(case, torch) as plan:
+    G = lanes or 8
+    with _plan(case, torch, column_lanes=lanes) as plan:
         out = torch.empty(case.n_voxels, dtype=torch.float32, device="cuda")
         for b in range(case.n_beams):
             R, Cn = int(case.rows[b]), int(case.cols[b])
@@ -145,7 +150,7 @@ def test_aperture_column(torch, name, case):
             ref = O.aperture_column(D, case, b, lv)
             mask = O.aperture_mask(case, b, lv)
             bound, n = sum_abs_rows(case, mask)
-            assert np.all(np.abs(got - ref) <= (n / 8.0 + 8) * U32 * bound + U32 * np.abs(ref)), b
+            assert np.all(np.abs(got - ref) <= (np.ceil(n / G) + 8) * U32 * bound + U32 * np.abs(ref)), b
 
 
 def test_unit_beamlet_aperture_is_column(torch):
