@@ -132,19 +132,26 @@ typedef struct dao_options {
                                 * memory) leave room for other plans' solves to run side by side */
     int32_t dt_threads;        /* threads per beamlet row of the transposed SpMV: 0 (default: 64, or the
                                 * autotuner's choice), 64, 128 or 256 */
-    int32_t dt_map;            /* lane mapping of the transposed SpMV: 0 (default: DAO_DT_CONSECUTIVE, or
-                                * the autotuner's choice), DAO_DT_GROUPED (a thread per 4 or 8 consecutive
-                                * entries, 16-byte loads) or DAO_DT_CONSECUTIVE (consecutive entries on
-                                * consecutive threads: the pi gathers of a warp fall on few cache lines) */
+    int32_t dt_map;            /* form of the transposed SpMV: 0 (default: DAO_DT_SPLIT where every row of
+                                * D^T has at least 32 stored entries, else DAO_DT_CONSECUTIVE; or the
+                                * autotuner's choice); DAO_DT_GROUPED (a block per beamlet row, a thread per
+                                * 4 or 8 consecutive entries, 16-byte loads), DAO_DT_CONSECUTIVE (a block per
+                                * row, consecutive entries on consecutive threads: the pi gathers of a warp
+                                * fall on few cache lines) or DAO_DT_SPLIT (all entries split evenly over a
+                                * fixed set of warps, consecutive entries on consecutive lanes; a row covered
+                                * by several warps adds their partial sums in warp order; falls back to
+                                * DAO_DT_CONSECUTIVE where a row is shorter than 32 entries) */
     int32_t dose_form;         /* form of the dose SpMV: 0 (default: DAO_DOSE_UNITS where its shared memory
                                 * fits, or the autotuner's choice), DAO_DOSE_LANES (2 to 32 lanes per voxel
                                 * row) or DAO_DOSE_UNITS (one warp per 32 consecutive rows, their entries
                                 * requested at once) */
     int32_t column_lanes;      /* lanes per voxel row of the aperture column (a4): 0 (default: 8, or the
                                 * autotuner's choice), 1, 2, 4, 8 or 16 */
+    int32_t dt_split_warps;    /* warps of the split form of the transposed SpMV: 0 (default: 32 per SM) or
+                                * any positive count (fewer warps take longer chunks of entries) */
 } dao_options;
 
-enum { DAO_DT_GROUPED = 1, DAO_DT_CONSECUTIVE = 2 };
+enum { DAO_DT_GROUPED = 1, DAO_DT_CONSECUTIVE = 2, DAO_DT_SPLIT = 3 };
 enum { DAO_DOSE_LANES = 1, DAO_DOSE_UNITS = 2 };
 
 typedef struct dao_ctx dao_ctx;
@@ -451,7 +458,8 @@ int32_t dao_batch_group_size(int32_t n, int32_t device);
 /* ---- autotuner of the SpMV launch shapes ----
  * Times the dose SpMV (a1: the lane form with 4/8/16/32 lanes per voxel row,
  * 16-bit storage up to 16, and the unit form), the transposed SpMV (a2, threads
- * per beamlet row: 64/128/256, each with both lane mappings) and the
+ * per beamlet row: 64/128/256, each with both lane mappings, and the split
+ * form) and the
  * aperture column (a4, lanes per voxel row: 1/2/4/8/16) on the context's own
  * matrices (10 launches per candidate, each after a read of a buffer twice the
  * L2 size, so that it runs on a cold cache as in a plan; median of the
@@ -469,9 +477,16 @@ typedef struct {
     int32_t dt_threads;    /* a2 threads per beamlet row */
     int32_t from_cache;    /* 1 when read from cache_path, 0 when timed */
     int32_t dose_form;     /* a1 form: DAO_DOSE_LANES or DAO_DOSE_UNITS */
-    int32_t dt_map;        /* a2 lane mapping: DAO_DT_GROUPED or DAO_DT_CONSECUTIVE */
+    int32_t dt_map;        /* a2 form: DAO_DT_GROUPED, DAO_DT_CONSECUTIVE or DAO_DT_SPLIT */
 } dao_tuning;
 dao_status dao_autotune(dao_ctx* ctx, const char* cache_path, dao_tuning* out);
+
+/* The SpMV forms and launch shapes the context's kernels run with now (after
+ * options, the autotuner's choice and the fallbacks: the unit form of a1 where
+ * its shared memory fits, the split form of a2 where every row of D^T has at
+ * least 32 entries); dt_threads is 0 for the split form; from_cache is 0.
+ * Host only, no CUDA call. */
+dao_status dao_kernel_forms(const dao_ctx* ctx, dao_tuning* out);
 
 /* ---- re-plan serving (continuous batching) ----
  * A server plans requests as they arrive (the paper's motivation: re-planning

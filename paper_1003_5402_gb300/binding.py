@@ -22,9 +22,9 @@ DAO_PREC_FP32, DAO_PREC_FP16, DAO_PREC_BF16 = 0, 1, 2
 DAO_MLC_CONSECUTIVE, DAO_MLC_INTERDIGITATION, DAO_MLC_CONNECTED, DAO_MLC_JAWS = 0, 1, 2, 3
 MLC = {"consecutive": DAO_MLC_CONSECUTIVE, "interdigitation": DAO_MLC_INTERDIGITATION,
        "connected": DAO_MLC_CONNECTED, "jaws": DAO_MLC_JAWS}
-DAO_DT_GROUPED, DAO_DT_CONSECUTIVE = 1, 2
+DAO_DT_GROUPED, DAO_DT_CONSECUTIVE, DAO_DT_SPLIT = 1, 2, 3
 DAO_DOSE_LANES, DAO_DOSE_UNITS = 1, 2
-DT_MAPS = {DAO_DT_GROUPED: "grouped", DAO_DT_CONSECUTIVE: "consecutive"}
+DT_MAPS = {DAO_DT_GROUPED: "grouped", DAO_DT_CONSECUTIVE: "consecutive", DAO_DT_SPLIT: "split"}
 DOSE_FORMS = {DAO_DOSE_LANES: "lanes", DAO_DOSE_UNITS: "units"}
 KC = {"dose": 0, "dt": 1, "price": 2, "column": 3, "master_pass": 4, "master_reduce": 5, "master_step": 6,
       "master_hess": 7, "other": 8, "master_solve": 9}
@@ -57,7 +57,8 @@ class dao_options(C.Structure):
                 ("price_tol", C.c_double), ("precision", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
                 ("use_graphs", C.c_int32), ("master_persistent", C.c_int32), ("mlc_constraint", C.c_int32),
                 ("master_blocks", C.c_int32), ("dt_threads", C.c_int32), ("dt_map", C.c_int32),
-                ("dose_form", C.c_int32), ("column_lanes", C.c_int32)]
+                ("dose_form", C.c_int32), ("column_lanes", C.c_int32),
+                ("dt_split_warps", C.c_int32)]
 
 
 class dao_tuning(C.Structure):
@@ -142,6 +143,7 @@ SIGNATURES = {
     "dao_batch_solve_persistent": (C.c_int, [C.POINTER(_P), C.c_int32, C.c_int32, _I32P, _F64P, _I32P]),
     "dao_batch_group_size": (C.c_int32, [C.c_int32, C.c_int32]),
     "dao_autotune": (C.c_int, [_P, C.c_char_p, C.POINTER(dao_tuning)]),
+    "dao_kernel_forms": (C.c_int, [_P, C.POINTER(dao_tuning)]),
     "dao_server_options_default": (None, [C.POINTER(dao_server_options)]),
     "dao_server_create": (C.c_int, [C.POINTER(dao_server_options), C.POINTER(_P)]),
     "dao_server_submit": (C.c_int, [_P, C.POINTER(dao_request), C.POINTER(C.c_int64)]),
@@ -513,6 +515,13 @@ class Plan:
         return {"dose_lanes": t.dose_lanes, "column_lanes": t.column_lanes, "dt_threads": t.dt_threads,
                 "dose_form": DOSE_FORMS.get(t.dose_form, t.dose_form), "dt_map": DT_MAPS.get(t.dt_map, t.dt_map),
                 "from_cache": bool(t.from_cache)}
+
+    def kernel_forms(self) -> dict:
+        """dao_kernel_forms: the SpMV forms and launch shapes this plan runs with."""
+        t = dao_tuning()
+        _check(load().dao_kernel_forms(self.h, C.byref(t)), "dao_kernel_forms")
+        return {"dose_form": DOSE_FORMS.get(t.dose_form, t.dose_form), "dose_lanes": t.dose_lanes,
+                "column_lanes": t.column_lanes, "dt_map": DT_MAPS.get(t.dt_map, t.dt_map), "dt_threads": t.dt_threads}
 
     def master_stats(self):
         """(evaluations, status, relative KKT residual) per master solve since the last reset."""

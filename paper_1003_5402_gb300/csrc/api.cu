@@ -258,13 +258,14 @@ dao_status validate(const dao_csr* D, const dao_geometry* g, const dao_structure
     if (opt->master_blocks < 0) return fail(DAO_EINVAL, "master_blocks must be >= 0");
     if (opt->dt_threads != 0 && opt->dt_threads != 64 && opt->dt_threads != 128 && opt->dt_threads != 256)
         return fail(DAO_EINVAL, "dt_threads must be 0, 64, 128 or 256");
-    if (opt->dt_map < 0 || opt->dt_map > DT_MAP_CONSECUTIVE)
-        return fail(DAO_EINVAL, "dt_map must be 0, DAO_DT_GROUPED or DAO_DT_CONSECUTIVE");
+    if (opt->dt_map < 0 || opt->dt_map > DT_MAP_SPLIT)
+        return fail(DAO_EINVAL, "dt_map must be 0, DAO_DT_GROUPED, DAO_DT_CONSECUTIVE or DAO_DT_SPLIT");
     if (opt->dose_form < 0 || opt->dose_form > DOSE_FORM_UNITS)
         return fail(DAO_EINVAL, "dose_form must be 0, DAO_DOSE_LANES or DAO_DOSE_UNITS");
     if (opt->column_lanes != 0 && opt->column_lanes != 1 && opt->column_lanes != 2 && opt->column_lanes != 4 &&
         opt->column_lanes != 8 && opt->column_lanes != 16)
         return fail(DAO_EINVAL, "column_lanes must be 0, 1, 2, 4, 8 or 16");
+    if (opt->dt_split_warps < 0) return fail(DAO_EINVAL, "dt_split_warps must be >= 0");
     if (opt->mlc_constraint < DAO_MLC_CONSECUTIVE || opt->mlc_constraint > DAO_MLC_JAWS)
         return fail(DAO_EINVAL, "mlc_constraint must be one of DAO_MLC_*");
     if (opt->mlc_constraint != DAO_MLC_CONSECUTIVE)
@@ -473,6 +474,38 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
         int* od = nullptr;
         DAO_TRY(upload(c, &od, order.data(), order.size()));
         c->Dt.order = od;
+    }
+    // the split form of a2 (every row of D^T at least 32 stored entries): the
+    // entries in equal chunks (multiples of 32) over a fixed set of warps, the
+    // row holding each chunk's first entry, and the most warps one row spans
+    std::vector<int> srow;
+    {
+        int min_len = INT32_MAX;
+        for (int i = 0; i < N; ++i) min_len = std::min(min_len, trow[i + 1] - trow[i]);
+        const int64_t warps =
+            c->opt.dt_split_warps > 0 ? (int64_t)c->opt.dt_split_warps : (int64_t)c->num_sms * SPLIT_WARPS_PER_SM;
+        if (N > 0 && min_len >= 32 && tpadded > 0) {
+            const int64_t chunk = std::max<int64_t>(32, ((tpadded + warps - 1) / warps + 31) / 32 * 32);
+            const int nw = (int)((tpadded + chunk - 1) / chunk);
+            srow.resize(nw);
+            int ps = 1;
+            for (int v = 0, r = 0; v < nw; ++v) {
+                const int64_t e = (int64_t)v * chunk;
+                while (trow[r + 1] <= e) ++r;
+                srow[v] = r;
+            }
+            for (int i = 0; i < N; ++i)
+                ps = std::max(ps, (int)((trow[i + 1] - 1) / chunk - trow[i] / chunk + 1));
+            int* sr = nullptr;
+            DAO_TRY(upload(c, &sr, srow.data(), srow.size()));
+            DAO_TRY(c->dalloc(&c->Dt.split_part, (size_t)N * ps));
+            DAO_TRY(c->dalloc(&c->Dt.split_cnt, (size_t)N));
+            DAO_CU(cudaMemsetAsync(c->Dt.split_cnt, 0, sizeof(int) * (size_t)N, st));
+            c->Dt.split_row = sr;
+            c->Dt.split_chunk = (int)chunk;
+            c->Dt.split_warps = nw;
+            c->Dt.split_ps = ps;
+        }
     }
     DAO_TRY(c->dalloc(&c->Dt.col, tpadded));
     if (prec == DAO_PREC_FP32) {
@@ -1243,6 +1276,7 @@ void dao_options_default(dao_options* opt) {
     opt->dt_map = 0;
     opt->dose_form = 0;
     opt->column_lanes = 0;
+    opt->dt_split_warps = 0;
 }
 
 const char* dao_last_error(void) { return g_err.c_str(); }
@@ -2314,6 +2348,21 @@ dao_status dao_batch_solve_persistent(dao_ctx* const* ctxs, int32_t n, int32_t n
     return DAO_OK;
 }
 
+dao_status dao_kernel_forms(const dao_ctx* c, dao_tuning* out) {
+    if (!c || !out) return fail(DAO_EINVAL, "null argument");
+    const DevCSR& D = c->D;
+    const DevCSR& Dt = c->Dt;
+    const bool units = D.tune_dose_form != DOSE_FORM_LANES && dose_units_available(D);
+    const bool split = (Dt.tune_dt_map == 0 || Dt.tune_dt_map == DT_MAP_SPLIT) && Dt.split_chunk > 0;
+    out->dose_form = units ? DOSE_FORM_UNITS : DOSE_FORM_LANES;
+    out->dose_lanes = D.tune_dose_g;
+    out->column_lanes = D.tune_col_g ? D.tune_col_g : 8;
+    out->dt_map = split ? DT_MAP_SPLIT : Dt.tune_dt_map == DT_MAP_GROUPED ? DT_MAP_GROUPED : DT_MAP_CONSECUTIVE;
+    out->dt_threads = split ? 0 : (Dt.tune_dt_threads ? Dt.tune_dt_threads : 64);
+    out->from_cache = 0;
+    return DAO_OK;
+}
+
 dao_status dao_autotune(dao_ctx* c, const char* cache_path, dao_tuning* out) {
     TraceRange range("dao_autotune");
     DAO_TRY(check_ctx(c));
@@ -2323,7 +2372,8 @@ dao_status dao_autotune(dao_ctx* c, const char* cache_path, dao_tuning* out) {
     bool cached = tune_cache_read(cache_path, key, &dg, &cg, &dt, &form, &map) && tune_allowed(TUNE_DOSE_G, dg) &&
                   tune_allowed(TUNE_COL_G, cg) && tune_allowed(TUNE_DT_THREADS, dt) &&
                   (form == DOSE_FORM_LANES || (form == DOSE_FORM_UNITS && units_ok)) &&
-                  (map == DT_MAP_GROUPED || map == DT_MAP_CONSECUTIVE);
+                  (map == DT_MAP_GROUPED || map == DT_MAP_CONSECUTIVE ||
+                   (map == DT_MAP_SPLIT && c->Dt.split_chunk > 0));
     if (cached && c->opt.precision != DAO_PREC_FP32 && dg > 16) cached = false;
     if (!cached) {
         const int reps = 10;
@@ -2355,7 +2405,17 @@ dao_status dao_autotune(dao_ctx* c, const char* cache_path, dao_tuning* out) {
             if (us < best) form = DOSE_FORM_UNITS;
         }
         best = 1e300;
-        for (int m : {DT_MAP_GROUPED, DT_MAP_CONSECUTIVE})  // a2: lane mapping x threads per beamlet row
+        if (c->Dt.split_chunk > 0) {  // a2: the split form, then a block per row in both lane mappings
+            c->Dt.tune_dt_map = DT_MAP_SPLIT;
+            double us = 0.0;
+            DAO_TRY(time_cold(c, reps,
+                              [&](int* nl) { return launch_dt(c->Dt, c->pi, c->w, nullptr, c->stream, nl); }, &us,
+                              "dao_autotune"));
+            best = us;
+            dt = 64;
+            map = DT_MAP_SPLIT;
+        }
+        for (int m : {DT_MAP_GROUPED, DT_MAP_CONSECUTIVE})
             for (int t : TUNE_DT_THREADS) {
                 c->Dt.tune_dt_threads = t;
                 c->Dt.tune_dt_map = m;

@@ -76,6 +76,17 @@ struct DevCSR {
     // D: the most groups (8 entries of 16-bit storage, 4 of FP32) in one unit of
     // 32 consecutive rows; sizes the unit form's shared partials (0: not known)
     int unit_groups_max = 0;
+    // D^T split over warps by entries (DT_MAP_SPLIT, rows of at least 32
+    // entries): warp v takes entries [v chunk, (v + 1) chunk), split_row[v] is
+    // the row holding its first entry; a row covered by several warps adds their
+    // partial sums (split_part, split_ps slots per row) in warp order, on a
+    // per-row ticket (split_cnt, zero between launches)
+    int split_chunk = 0;     // 0: the split form is not available
+    int split_warps = 0;
+    int split_ps = 0;
+    const int* split_row = nullptr;
+    float* split_part = nullptr;
+    int* split_cnt = nullptr;
 };
 
 // Forms of the dose SpMV (a1): G lanes per voxel row over the row's groups,
@@ -83,7 +94,9 @@ struct DevCSR {
 enum { DOSE_FORM_LANES = DAO_DOSE_LANES, DOSE_FORM_UNITS = DAO_DOSE_UNITS };
 // Lane mappings of the transposed SpMV (a2): a thread per group of 4 or 8
 // consecutive entries, or consecutive entries on consecutive threads (default).
-enum { DT_MAP_GROUPED = DAO_DT_GROUPED, DT_MAP_CONSECUTIVE = DAO_DT_CONSECUTIVE };
+enum { DT_MAP_GROUPED = DAO_DT_GROUPED, DT_MAP_CONSECUTIVE = DAO_DT_CONSECUTIVE, DT_MAP_SPLIT = DAO_DT_SPLIT };
+// Warps of the split form of a2 per SM (blocks of 8 warps).
+constexpr int SPLIT_WARPS_PER_SM = 32;
 
 // Launch shapes the autotuner may choose from.
 constexpr int TUNE_DOSE_G[] = {4, 8, 16, 32};

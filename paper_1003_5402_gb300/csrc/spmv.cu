@@ -27,6 +27,12 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
     return v;
 }
 
+__device__ __forceinline__ float warp_sum_f32(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
 // Sum of one double per thread over the block; the result is valid in thread 0.
 template <int NT>
 __device__ __forceinline__ double block_sum_f64(double v, double* s_red) {
@@ -176,6 +182,136 @@ __global__ void __launch_bounds__(BT) k_dt(const int* __restrict__ rowptr, const
                        : dt_row_sum<BT>(rowptr, col4, val4, row, pi, s_red);
     if (threadIdx.x == 0) w[row] = s;
     dt_row_ticket(rt, row, w);
+}
+
+// The fused MLC-row search taken by one warp (all lanes): lane 0 has published
+// w[row]; as dt_row_ticket, with the warp's lanes ordered by __syncwarp.
+__device__ __forceinline__ void dt_row_ticket_warp(const RowTicket& rt, int row, const float* w) {
+    if (rt.row_cnt == nullptr) return;  // uniform
+    int g = -1;
+    if ((threadIdx.x & 31) == 0) {
+        const int4 bi = rt.binfo[row];
+        const int gg = rt.beam_row0[bi.x] + bi.y;
+        const bool last = (int)atom_add_acq_rel_gpu(reinterpret_cast<unsigned*>(&rt.row_cnt[gg]), 1u) ==
+                          rt.cols[bi.x] - 1;
+        if (last) rt.row_cnt[gg] = 0;
+        g = last ? gg : -1;
+    }
+    g = __shfl_sync(FULL, g, 0);
+    __syncwarp();
+    if (g >= 0) pricing::row_best(w, rt.row_info[g], g, rt.row_v, rt.row_lr);
+}
+
+// a2 with D^T's entries split evenly over a fixed set of warps: warp v takes
+// the entries [v chunk, (v + 1) chunk) in steps of 32 consecutive entries
+// (lane l the entry t + l, U steps requested ahead of their pi gathers), so
+// every warp streams the same number of bytes whatever the row lengths, and
+// the 32 gathers of a step fall on a few cache lines.  Every row has at least
+// 32 entries, so a step crosses at most one row end.  At a row end the warp
+// sums its lanes (fixed butterfly) into the row's partial for this warp; a
+// row within one warp is final at once, a row covered by warps v0 .. v1
+// stores its partial at slot v - v0 and the last of them to take the row's
+// ticket adds the slots in order in FP64.  Lane 0 writes w[row] (times the
+// beamlet scale for 16-bit values) and takes the fused MLC-row ticket.
+constexpr int SPLIT_THREADS = 256;
+
+template <int VK>  // 0: FP32 values, 1: FP16, 2: BF16
+__global__ void __launch_bounds__(SPLIT_THREADS) k_dt_split(
+    const int* __restrict__ rowptr, const int* __restrict__ col, const void* __restrict__ valv,
+    const float* __restrict__ scale, int N, int E, int chunk, int n_warps, const int* __restrict__ split_row,
+    float* __restrict__ part, int PS, int* __restrict__ cnt, const float* __restrict__ pi, float* __restrict__ w,
+    const int* __restrict__ skip, RowTicket rt) {
+    constexpr int U = 4;
+    dt_round_snapshot(rt);
+    if (skip != nullptr && *skip) return;
+    const int lane = threadIdx.x & 31;
+    const int wg = blockIdx.x * (SPLIT_THREADS / 32) + (threadIdx.x >> 5);
+    if (wg >= n_warps) return;  // uniform per warp
+    const int e_begin = wg * chunk;
+    const int e_end = min(e_begin + chunk, E);
+    auto loadv = [&](int e) -> float {
+        if constexpr (VK == 0)
+            return __ldg(static_cast<const float*>(valv) + e);
+        else
+            return unpack1<VK == 2>(__ldg(static_cast<const unsigned short*>(valv) + e));
+    };
+    int cn[U];
+    float vn[U];
+    auto load_batch = [&](int s0) {
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int e = s0 + 32 * q + lane;
+            cn[q] = e < e_end ? __ldg(col + e) : -1;
+            vn[q] = e < e_end ? loadv(e) : 0.f;
+        }
+    };
+    load_batch(e_begin);
+    // a window of 32 row offsets, lane l holding rowptr[rbase + l]
+    int rbase = __ldg(split_row + wg);
+    int rp = __ldg(rowptr + min(rbase + lane, N));
+    int ri = 0;
+    int rstart = __shfl_sync(FULL, rp, 0);
+    int rend = __shfl_sync(FULL, rp, 1);
+    auto flush = [&](int r, int rs, int re, float a) {
+        const float p = warp_sum_f32(a);
+        int fin = -1;
+        if (lane == 0) {
+            const int v0 = rs / chunk, v1 = (re - 1) / chunk;
+            double tot = (double)p;
+            bool done = true;
+            if (v1 > v0) {
+                part[(size_t)r * PS + (wg - v0)] = p;
+                done = (int)atom_add_acq_rel_gpu(reinterpret_cast<unsigned*>(cnt + r), 1u) == v1 - v0;
+                if (done) {
+                    cnt[r] = 0;  // every warp of the row has taken its ticket
+                    tot = 0.0;
+                    for (int k = 0; k <= v1 - v0; ++k) tot += (double)__ldcg(part + (size_t)r * PS + k);
+                }
+            }
+            if (done) {
+                w[r] = VK == 0 ? (float)tot : (float)(tot * (double)__ldg(scale + r));
+                fin = r;
+            }
+        }
+        fin = __shfl_sync(FULL, fin, 0);
+        if (fin >= 0) dt_row_ticket_warp(rt, fin, w);
+    };
+    float acc = 0.f;
+    for (int s0 = e_begin; s0 < e_end; s0 += 32 * U) {
+        int c[U];
+        float v[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            c[q] = cn[q];
+            v[q] = vn[q];
+        }
+        load_batch(s0 + 32 * U);
+        float a[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) a[q] = c[q] >= 0 ? __ldg(pi + c[q]) : 0.f;
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int t = s0 + 32 * q;
+            if (t >= e_end) break;  // uniform
+            if (rend >= t + 32 || rend >= e_end) {
+                acc = fmaf(v[q], a[q], acc);  // lanes past e_end add 0 * 0
+            } else {
+                // the row ends inside this step: lanes below rend finish it
+                const int e = t + lane;
+                if (e < rend) acc = fmaf(v[q], a[q], acc);
+                flush(rbase + ri, rstart, rend, acc);
+                if (++ri == 31) {  // next window of row offsets
+                    rbase += 31;
+                    rp = __ldg(rowptr + min(rbase + lane, N));
+                    ri = 0;
+                }
+                rstart = rend;
+                rend = __shfl_sync(FULL, rp, ri + 1);
+                acc = (e >= rstart && e < e_end) ? fmaf(v[q], a[q], 0.f) : 0.f;
+            }
+        }
+    }
+    flush(rbase + ri, rstart, rend, acc);  // the row this warp's range ends in
 }
 
 template <int G>
@@ -780,6 +916,27 @@ cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct,
 static cudaError_t dt_dispatch(const DevCSR& Dt, const float* pi, float* w, const int* skip, const RowTicket& rt,
                         cudaStream_t stream, int* launches) {
     if (Dt.n_rows == 0) return cudaSuccess;
+    if ((Dt.tune_dt_map == 0 || Dt.tune_dt_map == DT_MAP_SPLIT) && Dt.split_chunk > 0) {
+        const int grid = (Dt.split_warps + SPLIT_THREADS / 32 - 1) / (SPLIT_THREADS / 32);
+        const int E = (int)Dt.nnz_stored;
+        if (Dt.prec == DAO_PREC_FP16)
+            k_dt_split<1><<<grid, SPLIT_THREADS, 0, stream>>>(Dt.rowptr, Dt.col, Dt.val16, Dt.scale, Dt.n_rows, E,
+                                                              Dt.split_chunk, Dt.split_warps, Dt.split_row,
+                                                              Dt.split_part, Dt.split_ps, Dt.split_cnt, pi, w, skip,
+                                                              rt);
+        else if (Dt.prec == DAO_PREC_BF16)
+            k_dt_split<2><<<grid, SPLIT_THREADS, 0, stream>>>(Dt.rowptr, Dt.col, Dt.val16, Dt.scale, Dt.n_rows, E,
+                                                              Dt.split_chunk, Dt.split_warps, Dt.split_row,
+                                                              Dt.split_part, Dt.split_ps, Dt.split_cnt, pi, w, skip,
+                                                              rt);
+        else
+            k_dt_split<0><<<grid, SPLIT_THREADS, 0, stream>>>(Dt.rowptr, Dt.col, Dt.val, Dt.scale, Dt.n_rows, E,
+                                                              Dt.split_chunk, Dt.split_warps, Dt.split_row,
+                                                              Dt.split_part, Dt.split_ps, Dt.split_cnt, pi, w, skip,
+                                                              rt);
+        ++*launches;
+        return cudaGetLastError();
+    }
     // one block per beamlet row; 64 threads by default, so that up to 32 blocks
     // per SM keep every row resident in one wave
     switch (Dt.tune_dt_threads) {

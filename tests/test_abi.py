@@ -115,7 +115,7 @@ def test_create_rejects_wide_rows_and_pool_sizes(lib):
     assert st == -1 and "[1, 32]" in msg
 
 
-@pytest.mark.parametrize("opt,needle", [({"dt_map": 3}, "dt_map"), ({"dt_map": -1}, "dt_map"),
+@pytest.mark.parametrize("opt,needle", [({"dt_map": 4}, "dt_map"), ({"dt_map": -1}, "dt_map"),
                                         ({"dose_form": 3}, "dose_form"), ({"dt_threads": 96}, "dt_threads"),
                                         ({"column_lanes": 3}, "column_lanes"), ({"column_lanes": 32}, "column_lanes")])
 def test_create_rejects_unknown_kernel_forms(lib, opt, needle):

@@ -46,6 +46,7 @@ def test_dose_spmv_and_epilogue(torch, name, case, form):
     rng = np.random.default_rng(1)
     x = rng.uniform(0.0, 2.0, size=case.n_beamlets).astype(np.float32)
     with _plan(case, torch, dose_form=form) as plan:
+        assert plan.kernel_forms()["dose_form"] == form
         xd = torch.from_numpy(x).cuda()
         zd = torch.empty(case.n_voxels, dtype=torch.float32, device="cuda")
         gd = torch.empty_like(zd)
@@ -70,18 +71,25 @@ def test_dose_spmv_and_epilogue(torch, name, case, form):
     assert abs(F - Fex) <= 1e-5 * abs(Fex) + 1e-300
 
 
-@pytest.mark.parametrize("dt_map", ["grouped", "consecutive"])
-@pytest.mark.parametrize("dt_threads", [0, 128, 256])
+@pytest.mark.parametrize("dt_map,dt_threads", [("grouped", 0), ("grouped", 128), ("grouped", 256),
+                                               ("consecutive", 0), ("consecutive", 128), ("consecutive", 256),
+                                               ("split", 0)])
 @pytest.mark.parametrize("name,case", CASES, ids=[c[0] for c in CASES])
 def test_transposed_spmv(torch, name, case, dt_threads, dt_map):
-    """a2 with the default block size and with 128 or 256 threads per beamlet row
-    (dao_options.dt_threads), in both lane mappings (dao_options.dt_map): a
-    thread's chain only gets shorter with more threads, and the consecutive
-    mapping's chain (ceil(n / threads) entries) is no longer than the grouped
-    one's, so the 64-thread grouped bound holds for all."""
+    """a2 with a block per beamlet row (64 threads by default, or 128 or 256:
+    dao_options.dt_threads) in both lane mappings, and split evenly over warps
+    (dao_options.dt_map; where a row of D^T holds fewer than 32 stored entries
+    the split form falls back to the consecutive one).  A thread's chain only
+    gets shorter with more threads; the consecutive mapping's chain
+    (ceil(n / threads) entries) is no longer than the grouped one's; a lane of
+    the split form sums at most ceil(n / 32) entries, then a 5-level warp tree,
+    then the warps' partials in FP64: the 64-thread grouped bound holds for all."""
     rng = np.random.default_rng(2)
     pi = rng.normal(size=case.n_voxels).astype(np.float32)
+    counts = np.bincount(case.indices, minlength=case.n_beamlets)
+    split_ok = int(((counts + 3) // 4 * 4).min()) >= 32
     with _plan(case, torch, dt_threads=dt_threads, dt_map=dt_map) as plan:
+        assert plan.kernel_forms()["dt_map"] == (dt_map if dt_map != "split" or split_ok else "consecutive")
         pd = torch.from_numpy(pi).cuda()
         wd = torch.empty(case.n_beamlets, dtype=torch.float32, device="cuda")
         plan.k_beamlet_prices(pd, wd)
@@ -91,6 +99,29 @@ def test_transposed_spmv(torch, name, case, dt_threads, dt_map):
     err = np.abs(w.astype(np.float64) - ref)
     allowed = (np.ceil(n / 128.0) * 4 + 8) * U32 * bound + U32 * np.abs(ref)
     assert np.all(err <= allowed), float(np.max(err - allowed))
+
+
+@pytest.mark.parametrize("warps", [1, 2, 7, 100000])
+def test_transposed_spmv_split_chunks(torch, warps):
+    """The split form of a2 with few warps (each warp's chunk spans dozens of
+    rows, so its window of row offsets is refilled, and a row straddles two
+    warps) and with a warp per 32 entries (every row spread over several
+    warps, combined on its ticket); a second call checks that the tickets
+    were left at zero."""
+    case = CASES[2][1]  # ragged: rows of D^T with 44 .. ~700 entries
+    rng = np.random.default_rng(5)
+    pi = rng.normal(size=case.n_voxels).astype(np.float32)
+    ref = O.beamlet_prices(O.csr64(case), pi.astype(np.float64))
+    bound, n = sum_abs_cols(case, pi)
+    allowed = (np.ceil(n / 128.0) * 4 + 8) * U32 * bound + U32 * np.abs(ref)
+    with _plan(case, torch, dt_map="split", dt_split_warps=warps) as plan:
+        assert plan.kernel_forms()["dt_map"] == "split"
+        pd = torch.from_numpy(pi).cuda()
+        for _ in range(2):
+            wd = torch.full((case.n_beamlets,), float("nan"), dtype=torch.float32, device="cuda")
+            plan.k_beamlet_prices(pd, wd)
+            w = wd.cpu().numpy().astype(np.float64)
+            assert np.all(np.abs(w - ref) <= allowed), float(np.nanmax(np.abs(w - ref) - allowed))
 
 
 def _price_inputs(case, kind, seed):

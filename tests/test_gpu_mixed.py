@@ -40,17 +40,19 @@ def _prec(name):
     return {"fp16": binding.DAO_PREC_FP16, "bf16": binding.DAO_PREC_BF16}[name]
 
 
-def _plan(case, torch, prec):
+def _plan(case, torch, prec, **opt):
     from paper_1003_5402_gb300 import Plan
-    return Plan(case, stream=torch.cuda.current_stream().cuda_stream, precision=_prec(prec))
+    return Plan(case, stream=torch.cuda.current_stream().cuda_stream, precision=_prec(prec), **opt)
 
 
+@pytest.mark.parametrize("form", ["lanes", "units"])
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("name,case", CASES, ids=[c[0] for c in CASES])
-def test_dose_16bit(torch, name, case, prec):
+def test_dose_16bit(torch, name, case, prec, form):
     q = quantized_case(case, prec)
     x = np.random.default_rng(1).uniform(0.0, 2.0, size=case.n_beamlets).astype(np.float32)
-    with _plan(case, torch, prec) as plan:
+    with _plan(case, torch, prec, dose_form=form) as plan:
+        assert plan.kernel_forms()["dose_form"] == form
         zd = torch.empty(case.n_voxels, dtype=torch.float32, device="cuda")
         gd = torch.empty_like(zd)
         F = plan.k_dose(torch.from_numpy(x).cuda(), zd, gd)
@@ -63,12 +65,18 @@ def test_dose_16bit(torch, name, case, prec):
     assert abs(F - O.objective(ref, vt)) <= 1e-5 * abs(O.objective(ref, vt)) + 1e-300
 
 
+@pytest.mark.parametrize("dt_map", ["grouped", "consecutive", "split"])
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("name,case", CASES, ids=[c[0] for c in CASES])
-def test_transposed_16bit(torch, name, case, prec):
+def test_transposed_16bit(torch, name, case, prec, dt_map):
+    """Every form of a2; the split form where every row of D^T holds at least
+    32 stored entries (rows padded to 8), else the consecutive one."""
     q = quantized_case(case, prec)
     pi = np.random.default_rng(2).normal(size=case.n_voxels).astype(np.float32)
-    with _plan(case, torch, prec) as plan:
+    counts = np.bincount(case.indices, minlength=case.n_beamlets)
+    split_ok = int(((counts + 7) // 8 * 8).min()) >= 32
+    with _plan(case, torch, prec, dt_map=dt_map) as plan:
+        assert plan.kernel_forms()["dt_map"] == (dt_map if dt_map != "split" or split_ok else "consecutive")
         wd = torch.empty(case.n_beamlets, dtype=torch.float32, device="cuda")
         plan.k_beamlet_prices(torch.from_numpy(pi).cuda(), wd)
         w = wd.cpu().numpy().astype(np.float64)
