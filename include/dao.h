@@ -141,18 +141,22 @@ typedef struct dao_options {
                                 * fixed set of warps, consecutive entries on consecutive lanes; a row covered
                                 * by several warps adds their partial sums in warp order; falls back to
                                 * DAO_DT_CONSECUTIVE where a row is shorter than 32 entries) */
-    int32_t dose_form;         /* form of the dose SpMV: 0 (default: DAO_DOSE_UNITS where its shared memory
-                                * fits, or the autotuner's choice), DAO_DOSE_LANES (2 to 32 lanes per voxel
-                                * row) or DAO_DOSE_UNITS (one warp per 32 consecutive rows, their entries
-                                * requested at once) */
+    int32_t dose_form;         /* form of the dose SpMV: 0 (default: DAO_DOSE_MERGE, else DAO_DOSE_UNITS, where
+                                * its shared memory fits; or the autotuner's choice), DAO_DOSE_LANES (4 to 32
+                                * lanes per voxel row), DAO_DOSE_UNITS (one warp per 32 consecutive rows, their
+                                * entries requested at once) or DAO_DOSE_MERGE (the stored entries split
+                                * evenly over a fixed set of warps, requested before any row offset; a row
+                                * crossing two warps' ranges is finished by the later of the two) */
     int32_t column_lanes;      /* lanes per voxel row of the aperture column (a4): 0 (default: 8, or the
                                 * autotuner's choice), 1, 2, 4, 8 or 16 */
-    int32_t dt_split_warps;    /* warps of the split form of the transposed SpMV: 0 (default: 32 per SM) or
-                                * any positive count (fewer warps take longer chunks of entries) */
+    int32_t split_warps;       /* warps of the forms that split D's or D^T's stored entries evenly over warps
+                                * (DAO_DOSE_MERGE, DAO_DT_SPLIT): 0 (default: 32 per SM) or any positive count
+                                * (fewer warps take longer chunks; the dose form's chunk stays longer than
+                                * the longest row and at most 1024 groups) */
 } dao_options;
 
 enum { DAO_DT_GROUPED = 1, DAO_DT_CONSECUTIVE = 2, DAO_DT_SPLIT = 3 };
-enum { DAO_DOSE_LANES = 1, DAO_DOSE_UNITS = 2 };
+enum { DAO_DOSE_LANES = 1, DAO_DOSE_UNITS = 2, DAO_DOSE_MERGE = 3 };
 
 typedef struct dao_ctx dao_ctx;
 
@@ -476,7 +480,7 @@ typedef struct {
     int32_t column_lanes;  /* a4 lanes per voxel row */
     int32_t dt_threads;    /* a2 threads per beamlet row */
     int32_t from_cache;    /* 1 when read from cache_path, 0 when timed */
-    int32_t dose_form;     /* a1 form: DAO_DOSE_LANES or DAO_DOSE_UNITS */
+    int32_t dose_form;     /* a1 form: DAO_DOSE_LANES, DAO_DOSE_UNITS or DAO_DOSE_MERGE */
     int32_t dt_map;        /* a2 form: DAO_DT_GROUPED, DAO_DT_CONSECUTIVE or DAO_DT_SPLIT */
 } dao_tuning;
 dao_status dao_autotune(dao_ctx* ctx, const char* cache_path, dao_tuning* out);

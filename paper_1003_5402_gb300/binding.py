@@ -23,9 +23,9 @@ DAO_MLC_CONSECUTIVE, DAO_MLC_INTERDIGITATION, DAO_MLC_CONNECTED, DAO_MLC_JAWS = 
 MLC = {"consecutive": DAO_MLC_CONSECUTIVE, "interdigitation": DAO_MLC_INTERDIGITATION,
        "connected": DAO_MLC_CONNECTED, "jaws": DAO_MLC_JAWS}
 DAO_DT_GROUPED, DAO_DT_CONSECUTIVE, DAO_DT_SPLIT = 1, 2, 3
-DAO_DOSE_LANES, DAO_DOSE_UNITS = 1, 2
+DAO_DOSE_LANES, DAO_DOSE_UNITS, DAO_DOSE_MERGE = 1, 2, 3
 DT_MAPS = {DAO_DT_GROUPED: "grouped", DAO_DT_CONSECUTIVE: "consecutive", DAO_DT_SPLIT: "split"}
-DOSE_FORMS = {DAO_DOSE_LANES: "lanes", DAO_DOSE_UNITS: "units"}
+DOSE_FORMS = {DAO_DOSE_LANES: "lanes", DAO_DOSE_UNITS: "units", DAO_DOSE_MERGE: "merge"}
 KC = {"dose": 0, "dt": 1, "price": 2, "column": 3, "master_pass": 4, "master_reduce": 5, "master_step": 6,
       "master_hess": 7, "other": 8, "master_solve": 9}
 
@@ -58,7 +58,7 @@ class dao_options(C.Structure):
                 ("use_graphs", C.c_int32), ("master_persistent", C.c_int32), ("mlc_constraint", C.c_int32),
                 ("master_blocks", C.c_int32), ("dt_threads", C.c_int32), ("dt_map", C.c_int32),
                 ("dose_form", C.c_int32), ("column_lanes", C.c_int32),
-                ("dt_split_warps", C.c_int32)]
+                ("split_warps", C.c_int32)]
 
 
 class dao_tuning(C.Structure):

@@ -260,12 +260,12 @@ dao_status validate(const dao_csr* D, const dao_geometry* g, const dao_structure
         return fail(DAO_EINVAL, "dt_threads must be 0, 64, 128 or 256");
     if (opt->dt_map < 0 || opt->dt_map > DT_MAP_SPLIT)
         return fail(DAO_EINVAL, "dt_map must be 0, DAO_DT_GROUPED, DAO_DT_CONSECUTIVE or DAO_DT_SPLIT");
-    if (opt->dose_form < 0 || opt->dose_form > DOSE_FORM_UNITS)
-        return fail(DAO_EINVAL, "dose_form must be 0, DAO_DOSE_LANES or DAO_DOSE_UNITS");
+    if (opt->dose_form < 0 || opt->dose_form > DOSE_FORM_MERGE)
+        return fail(DAO_EINVAL, "dose_form must be 0, DAO_DOSE_LANES, DAO_DOSE_UNITS or DAO_DOSE_MERGE");
     if (opt->column_lanes != 0 && opt->column_lanes != 1 && opt->column_lanes != 2 && opt->column_lanes != 4 &&
         opt->column_lanes != 8 && opt->column_lanes != 16)
         return fail(DAO_EINVAL, "column_lanes must be 0, 1, 2, 4, 8 or 16");
-    if (opt->dt_split_warps < 0) return fail(DAO_EINVAL, "dt_split_warps must be >= 0");
+    if (opt->split_warps < 0) return fail(DAO_EINVAL, "split_warps must be >= 0");
     if (opt->mlc_constraint < DAO_MLC_CONSECUTIVE || opt->mlc_constraint > DAO_MLC_JAWS)
         return fail(DAO_EINVAL, "mlc_constraint must be one of DAO_MLC_*");
     if (opt->mlc_constraint != DAO_MLC_CONSECUTIVE)
@@ -412,7 +412,7 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     DAO_TRY(talloc(&t_C, sizeof(int) * (size_t)n_ch * N));
     DAO_TRY(talloc(&t_cnt, sizeof(int) * N));
     DAO_TRY(talloc(&t_dmax, sizeof(unsigned)));
-    DAO_TRY(talloc(&t_umax, sizeof(int)));
+    DAO_TRY(talloc(&t_umax, 2 * sizeof(int)));
     c->D.n_rows = V;
     c->D.n_cols = N;
     c->D.nnz_stored = padded;
@@ -446,12 +446,33 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     // offsets of D^T, tau, the dose SpMV's shared partials
     std::vector<int> cnt(N);
     unsigned dmax_bits = 0;
-    int umax = 0;
+    int umax[2] = {0, 0};
     DAO_TRY(cu(cudaMemcpyAsync(cnt.data(), t_cnt, sizeof(int) * N, cudaMemcpyDeviceToHost, st), "counts"));
     DAO_TRY(cu(cudaMemcpyAsync(&dmax_bits, t_dmax, sizeof(unsigned), cudaMemcpyDeviceToHost, st), "max"));
-    DAO_TRY(cu(cudaMemcpyAsync(&umax, t_umax, sizeof(int), cudaMemcpyDeviceToHost, st), "units"));
+    DAO_TRY(cu(cudaMemcpyAsync(umax, t_umax, 2 * sizeof(int), cudaMemcpyDeviceToHost, st), "units"));
     DAO_TRY(cu(cudaStreamSynchronize(st), "device build"));
-    c->D.unit_groups_max = std::max(umax, 1);
+    c->D.unit_groups_max = std::max(umax[0], 1);
+    {
+        // the merge form of a1: the stored entries in equal chunks of groups
+        // (longer than the longest row) over a fixed set of warps
+        const int64_t G_tot = padded / pad_m;
+        const int64_t warps =
+            c->opt.split_warps > 0 ? (int64_t)c->opt.split_warps : (int64_t)c->num_sms * MERGE_WARPS_PER_SM;
+        int64_t chunk = std::max<int64_t>((G_tot + warps - 1) / warps, (int64_t)umax[1] + 1);
+        if (chunk > MERGE_CHUNK_MAX) chunk = std::max<int64_t>(MERGE_CHUNK_MAX, (int64_t)umax[1] + 1);
+        if (G_tot > 0 && chunk <= MERGE_CHUNK_MAX) {
+            const int nw = (int)((G_tot + chunk - 1) / chunk);
+            int* mr = nullptr;
+            DAO_TRY(c->dalloc(&mr, (size_t)nw + 1));
+            DAO_TRY(c->dalloc(&c->D.merge_slot, 2 * (size_t)nw));
+            DAO_TRY(c->dalloc(&c->D.merge_cnt, (size_t)nw));
+            DAO_TRY(cu(cudaMemsetAsync(c->D.merge_cnt, 0, sizeof(int) * (size_t)nw, st), "merge tickets"));
+            DAO_TRY(cu(build_merge_rows(c->D.rowptr, V, pad_m, (int)chunk, nw, mr, st), "merge rows"));
+            c->D.merge_rows = mr;
+            c->D.merge_chunk = (int)chunk;
+            c->D.merge_warps = nw;
+        }
+    }
     std::vector<int> trow(N + 1, 0);
     int64_t tpadded = 0;
     for (int i = 0; i < N; ++i) {
@@ -483,7 +504,7 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
         int min_len = INT32_MAX;
         for (int i = 0; i < N; ++i) min_len = std::min(min_len, trow[i + 1] - trow[i]);
         const int64_t warps =
-            c->opt.dt_split_warps > 0 ? (int64_t)c->opt.dt_split_warps : (int64_t)c->num_sms * SPLIT_WARPS_PER_SM;
+            c->opt.split_warps > 0 ? (int64_t)c->opt.split_warps : (int64_t)c->num_sms * SPLIT_WARPS_PER_SM;
         if (N > 0 && min_len >= 32 && tpadded > 0) {
             const int64_t chunk = std::max<int64_t>(32, ((tpadded + warps - 1) / warps + 31) / 32 * 32);
             const int nw = (int)((tpadded + chunk - 1) / chunk);
@@ -656,7 +677,7 @@ dao_status alloc_state(dao_ctx* c) {
     DAO_TRY(c->dalloc(&c->mb.gn_part, (size_t)KMAX * c->mb.GH));
     DAO_TRY(c->dalloc(&c->mb.H_keep, (size_t)KMAX * (KMAX + 1) / 2 * c->mb.GH));
     DAO_TRY(c->dalloc(&c->mb.F_part, (size_t)master_grid_max(c->num_sms)));
-    c->F_blocks = dose_grid(c->V, c->num_sms);
+    c->F_blocks = std::max(dose_grid(c->V, c->num_sms), dose_merge_f_slots(c->D));
     DAO_TRY(c->dalloc(&c->F_part, c->F_blocks));
     DAO_TRY(c->dalloc(&c->F_dev, 1));
     DAO_CU(cudaMemsetAsync(c->mb.st, 0, sizeof(MasterDev), c->stream));
@@ -1276,7 +1297,7 @@ void dao_options_default(dao_options* opt) {
     opt->dt_map = 0;
     opt->dose_form = 0;
     opt->column_lanes = 0;
-    opt->dt_split_warps = 0;
+    opt->split_warps = 0;
 }
 
 const char* dao_last_error(void) { return g_err.c_str(); }
@@ -2352,9 +2373,8 @@ dao_status dao_kernel_forms(const dao_ctx* c, dao_tuning* out) {
     if (!c || !out) return fail(DAO_EINVAL, "null argument");
     const DevCSR& D = c->D;
     const DevCSR& Dt = c->Dt;
-    const bool units = D.tune_dose_form != DOSE_FORM_LANES && dose_units_available(D);
     const bool split = (Dt.tune_dt_map == 0 || Dt.tune_dt_map == DT_MAP_SPLIT) && Dt.split_chunk > 0;
-    out->dose_form = units ? DOSE_FORM_UNITS : DOSE_FORM_LANES;
+    out->dose_form = dose_form_effective(D);
     out->dose_lanes = D.tune_dose_g;
     out->column_lanes = D.tune_col_g ? D.tune_col_g : 8;
     out->dt_map = split ? DT_MAP_SPLIT : Dt.tune_dt_map == DT_MAP_GROUPED ? DT_MAP_GROUPED : DT_MAP_CONSECUTIVE;
@@ -2371,7 +2391,8 @@ dao_status dao_autotune(dao_ctx* c, const char* cache_path, dao_tuning* out) {
     const bool units_ok = dose_units_available(c->D);
     bool cached = tune_cache_read(cache_path, key, &dg, &cg, &dt, &form, &map) && tune_allowed(TUNE_DOSE_G, dg) &&
                   tune_allowed(TUNE_COL_G, cg) && tune_allowed(TUNE_DT_THREADS, dt) &&
-                  (form == DOSE_FORM_LANES || (form == DOSE_FORM_UNITS && units_ok)) &&
+                  (form == DOSE_FORM_LANES || (form == DOSE_FORM_UNITS && units_ok) ||
+                   (form == DOSE_FORM_MERGE && c->D.merge_chunk > 0)) &&
                   (map == DT_MAP_GROUPED || map == DT_MAP_CONSECUTIVE ||
                    (map == DT_MAP_SPLIT && c->Dt.split_chunk > 0));
     if (cached && c->opt.precision != DAO_PREC_FP32 && dg > 16) cached = false;
@@ -2398,11 +2419,15 @@ dao_status dao_autotune(dao_ctx* c, const char* cache_path, dao_tuning* out) {
             }
         }
         form = DOSE_FORM_LANES;
-        if (units_ok) {
-            c->D.tune_dose_form = DOSE_FORM_UNITS;
+        for (int f : {DOSE_FORM_UNITS, DOSE_FORM_MERGE}) {
+            c->D.tune_dose_form = f;
+            if (dose_form_effective(c->D) != f) continue;  // not available for this matrix
             double us = 0.0;
             DAO_TRY(time_dose(&us));
-            if (us < best) form = DOSE_FORM_UNITS;
+            if (us < best) {
+                best = us;
+                form = f;
+            }
         }
         best = 1e300;
         if (c->Dt.split_chunk > 0) {  // a2: the split form, then a block per row in both lane mappings

@@ -431,18 +431,49 @@ cudaError_t build_seg(const int64_t* rp, const int* col, const int* prow, int V,
 }
 
 namespace {
-// One thread per unit of 32 rows: its group count, the largest into *out.
+// One thread per unit of 32 rows: its group count, the largest into out[0];
+// the largest row into out[1].
 __global__ void k_unit_max(const int* __restrict__ prow, int V, int epg, int* __restrict__ out) {
     const int u = blockIdx.x * blockDim.x + threadIdx.x;
     const int r0 = u * 32;
     if (r0 >= V) return;
     const int r1 = min(r0 + 32, V);
     atomicMax(out, (prow[r1] - prow[r0]) / epg);
+    int m = 0;
+    for (int r = r0; r < r1; ++r) m = max(m, prow[r + 1] - prow[r]);
+    atomicMax(out + 1, m / epg);
+}
+
+// One thread per warp of the merge form: the first row whose offset is at
+// least the warp's first entry (binary search over the row offsets).
+__global__ void k_merge_rows(const int* __restrict__ prow, int V, int epg, int chunk, int n_warps,
+                             int* __restrict__ out) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v > n_warps) return;
+    if (v == n_warps) {
+        out[v] = V;
+        return;
+    }
+    const long long e = (long long)v * chunk * epg;
+    int lo = 0, hi = V;  // the first r in [0, V] with prow[r] >= e
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((long long)prow[mid] >= e)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    out[v] = lo;
 }
 }  // namespace
 
+cudaError_t build_merge_rows(const int* prow, int V, int epg, int chunk, int n_warps, int* out, cudaStream_t s) {
+    k_merge_rows<<<(n_warps + 1 + 255) / 256, 256, 0, s>>>(prow, V, epg, chunk, n_warps, out);
+    return cudaGetLastError();
+}
+
 cudaError_t build_unit_max(const int* prow, int V, int epg, int* out, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess || V < 1) return e;
     const int units = (V + 31) / 32;
     k_unit_max<<<(units + 255) / 256, 256, 0, s>>>(prow, V, epg, out);

@@ -81,6 +81,16 @@ struct DevCSR {
     // the row holding its first entry; a row covered by several warps adds their
     // partial sums (split_part, split_ps slots per row) in warp order, on a
     // per-row ticket (split_cnt, zero between launches)
+    // D split over warps by entries (DOSE_FORM_MERGE): warp v takes groups
+    // [v merge_chunk, (v + 1) merge_chunk) and owns the rows merge_rows[v] ..
+    // merge_rows[v + 1] - 1 (those starting in its range); a row crossing the
+    // boundary before warp v is finished from merge_slot[2v], merge_slot[2v + 1]
+    // on the ticket merge_cnt[v] (zero between launches)
+    int merge_chunk = 0;     // 0: the merge form is not available
+    int merge_warps = 0;
+    const int* merge_rows = nullptr;
+    float* merge_slot = nullptr;
+    int* merge_cnt = nullptr;
     int split_chunk = 0;     // 0: the split form is not available
     int split_warps = 0;
     int split_ps = 0;
@@ -91,7 +101,11 @@ struct DevCSR {
 
 // Forms of the dose SpMV (a1): G lanes per voxel row over the row's groups,
 // or one warp per unit of 32 rows (the default where its shared memory fits).
-enum { DOSE_FORM_LANES = DAO_DOSE_LANES, DOSE_FORM_UNITS = DAO_DOSE_UNITS };
+enum { DOSE_FORM_LANES = DAO_DOSE_LANES, DOSE_FORM_UNITS = DAO_DOSE_UNITS, DOSE_FORM_MERGE = DAO_DOSE_MERGE };
+// Warps of the merge form of a1 per SM (blocks of 8 warps), and its most
+// groups per warp.
+constexpr int MERGE_WARPS_PER_SM = 32;
+constexpr int MERGE_CHUNK_MAX = 1024;
 // Lane mappings of the transposed SpMV (a2): a thread per group of 4 or 8
 // consecutive entries, or consecutive entries on consecutive threads (default).
 enum { DT_MAP_GROUPED = DAO_DT_GROUPED, DT_MAP_CONSECUTIVE = DAO_DT_CONSECUTIVE, DT_MAP_SPLIT = DAO_DT_SPLIT };
@@ -167,6 +181,10 @@ cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct,
 int dose_grid(int n_rows, int num_sms);
 // The unit form of a1 fits shared memory for this matrix.
 bool dose_units_available(const DevCSR& D);
+// The form of a1 a launch takes (DOSE_FORM_*), and the objective partial
+// slots the merge form writes (0 when it is not available).
+int dose_form_effective(const DevCSR& D);
+int dose_merge_f_slots(const DevCSR& D);
 // Process-wide dynamic shared-memory limits of the SpMV kernels (set once per
 // device, to a fixed size).
 cudaError_t spmv_configure();
@@ -409,8 +427,12 @@ cudaError_t build_fill_d(int prec, const int64_t* rp, const int* col, const floa
 cudaError_t build_seg(const int64_t* rp, const int* col, const int* prow, int V, const int* beam_off, int B, int* seg,
                       cudaStream_t s);
 // The most groups of epg entries in one unit of 32 consecutive rows of the
-// padded D (row offsets prow), into *out (zeroed by the call).
+// padded D (row offsets prow) into out[0], the most in one row into out[1]
+// (both zeroed by the call).
 cudaError_t build_unit_max(const int* prow, int V, int epg, int* out, cudaStream_t s);
+// Rows owned by each warp of the merge form: out[v] = the first row starting
+// at or after entry v * chunk * epg (v < n_warps), out[n_warps] = V.
+cudaError_t build_merge_rows(const int* prow, int V, int epg, int chunk, int n_warps, int* out, cudaStream_t s);
 cudaError_t build_transpose_place(int prec, const int64_t* rp, const int* col, const float* val, int V, int CH, int N,
                                   int n_ch, int* C, const int* cnt, const float* scale, DevCSR& Dt, float* tval,
                                   int num_sms, cudaStream_t s);

@@ -571,6 +571,143 @@ __global__ void __launch_bounds__(UNIT_THREADS, 2) k_dose_units(
     }
 }
 
+// ---- a1 split evenly over warps by entries ---------------------------------
+// Warp v takes the groups [v chunk, (v + 1) chunk) of D's stored entries (8
+// per group with 16-bit storage, 4 with FP32) and requests its first UB
+// groups per lane before anything else (their addresses need no row offset);
+// group dot products go to the warp's row of shared partials.  The warp owns
+// the rows that start in its range (mrows[v] .. mrows[v + 1] - 1, empty rows
+// included): lane l sums row l's partials in group order and applies the
+// epilogue, 32 rows at a time.  chunk exceeds the longest row, so a row
+// extends into at most the next warp: its owner stores the sum of its groups
+// (slot 0 of the boundary), the next warp the sum of the row's groups in its
+// range (slot 1), and the second of the two to take the boundary's ticket
+// forms z = slot 0 + slot 1, applies the epilogue and writes the row's
+// objective term to F_part[F_stride + boundary] (0 where no row crosses the
+// boundary), so that F is a fixed-order sum whichever warp finishes first.
+constexpr int MERGE_THREADS = 256;
+constexpr int MERGE_CAP = 1024;  // groups per warp (its row of shared partials)
+
+template <bool L16, bool BF>
+__global__ void __launch_bounds__(MERGE_THREADS, 4) k_dose_merge(
+    const int* __restrict__ rowptr, const uint4* __restrict__ colg, const uint4* __restrict__ valg, int V, int G_tot,
+    const float* __restrict__ x, const float* __restrict__ scale, int N, const uint8_t* __restrict__ vstruct,
+    const StructTermsS* __restrict__ ts, int S, float* __restrict__ z, float* __restrict__ grad,
+    double* __restrict__ F_part, int F_stride, int chunk, int n_warps, const int* __restrict__ mrows,
+    float* __restrict__ slot, int* __restrict__ cnt) {
+    constexpr int EPG = L16 ? 8 : 4;
+    constexpr int UB = 4;
+    constexpr int NW = MERGE_THREADS / 32;
+    extern __shared__ __align__(16) float s_dyn_merge[];
+    __shared__ StructTermsS s_ts[SMAX];
+    __shared__ double s_red[NW];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int wg = blockIdx.x * NW + wib;
+    const bool active = wg < n_warps;  // uniform per warp; idle warps still meet the block barrier
+    float* sx = s_dyn_merge;
+    float* spart = s_dyn_merge + ((N + 3) & ~3) + wib * chunk;
+    const int g_begin = wg * chunk;
+    const int g_end = active ? min(g_begin + chunk, G_tot) : g_begin;
+    const int ng = g_end - g_begin;
+    uint4 c[UB], v[UB];
+    auto load_batch = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < UB; ++q) {
+            const int g = k0 + q * 32 + lane;
+            if (g < ng) {
+                c[q] = __ldg(colg + g_begin + g);
+                v[q] = __ldg(valg + g_begin + g);
+            }
+        }
+    };
+    load_batch(0);
+    // the owned rows and the first 32 of them
+    int r0 = 0, r1 = 0;
+    if (active) {
+        r0 = __ldg(mrows + wg);
+        r1 = __ldg(mrows + wg + 1);
+    }
+    int rs = 0, re = 0, lab = 0;
+    auto row_meta = [&](int r) {
+        rs = re = 0;
+        lab = 0;
+        if (r < r1) {
+            rs = __ldg(rowptr + r);
+            re = __ldg(rowptr + r + 1);
+            if (S >= 0) lab = __ldg(vstruct + r);
+        }
+    };
+    row_meta(r0 + lane);
+    const int rs0 = active ? __ldg(rowptr + r0) : 0;  // start of the first owned row
+    for (int i = threadIdx.x; i < N; i += MERGE_THREADS) sx[i] = L16 ? __ldg(x + i) * __ldg(scale + i) : __ldg(x + i);
+    for (int i = threadIdx.x; i < S; i += MERGE_THREADS) s_ts[i] = ts[i];
+    __syncthreads();
+    for (int k0 = 0; k0 < ng; k0 += 32 * UB) {
+        if (k0 > 0) load_batch(k0);
+#pragma unroll
+        for (int q = 0; q < UB; ++q) {
+            const int g = k0 + q * 32 + lane;
+            if (g < ng) spart[g] = group_dot<L16, BF>(c[q], v[q], sx);
+        }
+    }
+    __syncwarp();
+    // epilogue of row r at z = acc; returns its objective term
+    auto epilogue = [&](int r, float acc, int l) -> float {
+        z[r] = acc;
+        float f = 0.f;
+        if (grad != nullptr || F_part != nullptr) {
+            const StructTermsS tt = S >= 0 ? s_ts[l] : ts[r];
+            const float uu = fmaxf((tt.tu_hi - acc) + tt.tu_lo, 0.f);  // T^- - z
+            const float o = fmaxf((acc - tt.to_hi) - tt.to_lo, 0.f);   // z - T^+
+            if (grad != nullptr) grad[r] = 2.f * (tt.b * o - tt.a * uu);
+            f = fmaf(tt.a * uu, uu, tt.b * o * o);
+        }
+        return f;
+    };
+    // a row across boundary b: this lane's part into slot s; the second to arrive finishes the row
+    auto cross = [&](int b, int s, float part_sum, int r, int l) {
+        slot[2 * b + s] = part_sum;
+        if ((int)atom_add_acq_rel_gpu(reinterpret_cast<unsigned*>(cnt + b), 1u) == 1) {
+            cnt[b] = 0;
+            const float a0 = s == 0 ? part_sum : __ldcg(slot + 2 * b);
+            const float a1 = s == 1 ? part_sum : __ldcg(slot + 2 * b + 1);
+            const float f = epilogue(r, a0 + a1, l);
+            if (F_part != nullptr) F_part[F_stride + b] = (double)f;
+        }
+    };
+    float facc = 0.f;
+    if (active && lane == 0) {
+        // the groups before the first owned row belong to the previous warp's last row
+        const int gh = rs0 / EPG - g_begin;
+        if (gh > 0) {
+            float a = 0.f;
+            for (int g = 0; g < gh; ++g) a += spart[g];
+            cross(wg, 1, a, r0 - 1, S >= 0 ? __ldg(vstruct + r0 - 1) : 0);
+        } else if (F_part != nullptr) {
+            F_part[F_stride + wg] = 0.0;  // no row crosses the boundary at this warp's first group
+        }
+    }
+    for (int rb = r0; rb < r1; rb += 32) {
+        const int r = rb + lane;
+        const int crs = rs, cre = re, cl = lab;
+        if (rb + 32 < r1) row_meta(rb + 32 + lane);  // the next 32 owned rows
+        if (r < r1) {
+            const int gs = crs / EPG - g_begin, ge_full = cre / EPG - g_begin;
+            const int ge = min(ge_full, ng);
+            float acc = 0.f;
+            for (int g = gs; g < ge; ++g) acc += spart[g];
+            if (ge_full > ng)
+                cross(wg + 1, 0, acc, r, cl);  // continues in the next warp
+            else
+                facc += epilogue(r, acc, cl);
+        }
+    }
+    if (F_part != nullptr) {
+        const double sres = block_sum_mixed<MERGE_THREADS>(facc, s_red);
+        if (threadIdx.x == 0) F_part[blockIdx.x] = sres;
+    }
+}
+
 // a2 with rows padded to 8 entries: two int4 loads of voxel indices and one uint4
 // of values per 8 entries (LC: consecutive entries on consecutive threads);
 // the row's scale is applied once at the end.
@@ -867,14 +1004,50 @@ void column_dev_launch(const DevCSR& D, const int* seg, const int* ap_beam, int 
 
 }  // namespace
 
+size_t merge_smem(int N, int chunk) {
+    return (size_t)((N + 3) & ~3) * sizeof(float) + (size_t)(MERGE_THREADS / 32) * chunk * sizeof(float);
+}
+
+template <bool L16, bool BF>
+cudaError_t dose_merge(const DevCSR& D, const float* x, const uint8_t* vstruct, const StructTermsS* ts, int S,
+                       float* z, float* grad, double* F_part, int& grid, int& F_used, cudaStream_t stream) {
+    const size_t smem = merge_smem(D.n_cols, D.merge_chunk);
+    grid = (D.merge_warps + MERGE_THREADS / 32 - 1) / (MERGE_THREADS / 32);
+    F_used = grid + D.merge_warps;
+    const void* colp = L16 ? static_cast<const void*>(D.col16) : static_cast<const void*>(D.col);
+    const void* valp = L16 ? static_cast<const void*>(D.val16) : static_cast<const void*>(D.val);
+    const int G_tot = (int)(D.nnz_stored / (L16 ? 8 : 4));
+    k_dose_merge<L16, BF><<<grid, MERGE_THREADS, smem, stream>>>(
+        D.rowptr, static_cast<const uint4*>(colp), static_cast<const uint4*>(valp), D.n_rows, G_tot, x, D.scale,
+        D.n_cols, vstruct, ts, S, z, grad, F_part, grid, D.merge_chunk, D.merge_warps, D.merge_rows, D.merge_slot,
+        D.merge_cnt);
+    return cudaGetLastError();
+}
+
+bool dose_merge_available(const DevCSR& D) {
+    return D.merge_chunk > 0 && merge_smem(D.n_cols, D.merge_chunk) <= (size_t)UNITS_SMEM_MAX;
+}
+
+int dose_merge_f_slots(const DevCSR& D) {
+    return D.merge_chunk > 0 ? (D.merge_warps + MERGE_THREADS / 32 - 1) / (MERGE_THREADS / 32) + D.merge_warps : 0;
+}
+
 bool dose_units_available(const DevCSR& D) {
     return D.unit_groups_max > 0 && units_smem(D.n_cols, D.unit_groups_max) <= (size_t)UNITS_SMEM_MAX;
+}
+
+int dose_form_effective(const DevCSR& D) {
+    const int f = D.tune_dose_form;
+    if ((f == 0 || f == DOSE_FORM_MERGE) && dose_merge_available(D)) return DOSE_FORM_MERGE;
+    if (f != DOSE_FORM_LANES && dose_units_available(D)) return DOSE_FORM_UNITS;
+    return DOSE_FORM_LANES;
 }
 
 cudaError_t spmv_configure() {
     cudaError_t e = cudaSuccess;
     for (const void* k : {(const void*)k_dose_units<false, false>, (const void*)k_dose_units<true, false>,
-                          (const void*)k_dose_units<true, true>})
+                          (const void*)k_dose_units<true, true>, (const void*)k_dose_merge<false, false>,
+                          (const void*)k_dose_merge<true, false>, (const void*)k_dose_merge<true, true>})
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, UNITS_SMEM_MAX);
     return e;
 }
@@ -884,10 +1057,26 @@ cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct,
                         double* F_out, int num_sms, cudaStream_t stream, int* launches) {
     (void)tf;
     int grid = dose_grid(D.n_rows, num_sms);  // at most this many; resident_grid trims it
-    if (F_part != nullptr && F_blocks < grid) return cudaErrorInvalidValue;
+    const int form = dose_form_effective(D);
+    if (F_part != nullptr && form != DOSE_FORM_MERGE && F_blocks < grid) return cudaErrorInvalidValue;
     const int g = dose_lanes(D);
-    const bool units = D.tune_dose_form != DOSE_FORM_LANES && dose_units_available(D);
+    const bool units = form == DOSE_FORM_UNITS;
     cudaError_t e;
+    if (form == DOSE_FORM_MERGE) {
+        int F_used = dose_merge_f_slots(D);
+        if (F_part != nullptr && F_blocks < F_used) return cudaErrorInvalidValue;  // sized at creation
+        if (D.prec == DAO_PREC_FP32)
+            e = dose_merge<false, false>(D, x, vstruct, ts, S, z, grad, F_part, grid, F_used, stream);
+        else if (D.prec == DAO_PREC_FP16)
+            e = dose_merge<true, false>(D, x, vstruct, ts, S, z, grad, F_part, grid, F_used, stream);
+        else
+            e = dose_merge<true, true>(D, x, vstruct, ts, S, z, grad, F_part, grid, F_used, stream);
+        ++*launches;
+        if (e != cudaSuccess || F_part == nullptr || F_out == nullptr) return e;
+        k_sum_f64<<<1, 256, 0, stream>>>(F_part, F_used, F_out);
+        ++*launches;
+        return cudaGetLastError();
+    }
     if (units && D.prec == DAO_PREC_FP32)
         e = dose_units<false, false>(D, x, vstruct, ts, S, z, grad, F_part, grid, num_sms, stream);
     else if (units && D.prec == DAO_PREC_FP16)

@@ -116,8 +116,9 @@ def test_create_rejects_wide_rows_and_pool_sizes(lib):
 
 
 @pytest.mark.parametrize("opt,needle", [({"dt_map": 4}, "dt_map"), ({"dt_map": -1}, "dt_map"),
-                                        ({"dose_form": 3}, "dose_form"), ({"dt_threads": 96}, "dt_threads"),
-                                        ({"column_lanes": 3}, "column_lanes"), ({"column_lanes": 32}, "column_lanes")])
+                                        ({"dose_form": 4}, "dose_form"), ({"dt_threads": 96}, "dt_threads"),
+                                        ({"column_lanes": 3}, "column_lanes"), ({"column_lanes": 32}, "column_lanes"),
+                                        ({"split_warps": -1}, "split_warps")])
 def test_create_rejects_unknown_kernel_forms(lib, opt, needle):
     st, msg = _create(lib, _tiny_inputs(), **opt)
     assert st == -1 and needle in msg, (st, msg)

@@ -37,12 +37,13 @@ def _plan(case, torch, **opt):
     return Plan(case, stream=torch.cuda.current_stream().cuda_stream, **opt)
 
 
-@pytest.mark.parametrize("form", ["lanes", "units"])
+@pytest.mark.parametrize("form", ["lanes", "units", "merge"])
 @pytest.mark.parametrize("name,case", CASES, ids=[c[0] for c in CASES])
 def test_dose_spmv_and_epilogue(torch, name, case, form):
-    """a1 in both forms (dao_options.dose_form).  The unit form sums each group
-    of 4 (FP32) or 8 entries in order and then the row's groups in order: no
-    term passes through more than min(n, 8) + groups - 1 <= n + 6 roundings."""
+    """a1 in every form (dao_options.dose_form).  The unit and merge forms sum
+    each group of 4 (FP32) or 8 entries in order and then the row's groups in
+    order (a row across two warps: the two partial sums added once more): no
+    term passes through more than min(n, 8) + groups <= n + 6 roundings."""
     rng = np.random.default_rng(1)
     x = rng.uniform(0.0, 2.0, size=case.n_beamlets).astype(np.float32)
     with _plan(case, torch, dose_form=form) as plan:
@@ -101,6 +102,34 @@ def test_transposed_spmv(torch, name, case, dt_threads, dt_map):
     assert np.all(err <= allowed), float(np.max(err - allowed))
 
 
+@pytest.mark.parametrize("warps", [1, 3, 100000])
+@pytest.mark.parametrize("name,case", [CASES[2], CASES[3]], ids=["ragged", "heavy"])
+def test_dose_merge_chunks(torch, name, case, warps):
+    """The merge form of a1 with one warp (one chunk of every group), three
+    warps, and a warp per chunk just longer than the longest row (most rows
+    cross a boundary and are finished on its ticket; empty rows included), twice
+    in a row (the tickets return to zero); z, grad F and F against the oracle."""
+    rng = np.random.default_rng(6)
+    x = rng.uniform(0.0, 2.0, size=case.n_beamlets).astype(np.float32)
+    ref = O.dose(O.csr64(case), x.astype(np.float64))
+    bound, n = sum_abs_rows(case, x)
+    vt = O.voxel_terms(case)
+    with _plan(case, torch, dose_form="merge", split_warps=warps) as plan:
+        assert plan.kernel_forms()["dose_form"] == "merge"
+        xd = torch.from_numpy(x).cuda()
+        for _ in range(2):
+            zd = torch.full((case.n_voxels,), float("nan"), dtype=torch.float32, device="cuda")
+            gd = torch.full_like(zd, float("nan"))
+            F = plan.k_dose(xd, zd, gd)
+            z = zd.cpu().numpy().astype(np.float64)
+            g = gd.cpu().numpy()
+            assert np.all(np.abs(z - ref) <= (n + 6) * U32 * bound + U32 * np.abs(ref))
+            gref = O.gradient(z, vt)
+            assert np.all(np.abs(g - gref) <= 4 * U32 * np.abs(gref) + 1e-45)
+            Fref = O.objective(z, vt)
+            assert abs(F - Fref) <= 4e-6 * abs(Fref) + 1e-300
+
+
 @pytest.mark.parametrize("warps", [1, 2, 7, 100000])
 def test_transposed_spmv_split_chunks(torch, warps):
     """The split form of a2 with few warps (each warp's chunk spans dozens of
@@ -114,7 +143,7 @@ def test_transposed_spmv_split_chunks(torch, warps):
     ref = O.beamlet_prices(O.csr64(case), pi.astype(np.float64))
     bound, n = sum_abs_cols(case, pi)
     allowed = (np.ceil(n / 128.0) * 4 + 8) * U32 * bound + U32 * np.abs(ref)
-    with _plan(case, torch, dt_map="split", dt_split_warps=warps) as plan:
+    with _plan(case, torch, dt_map="split", split_warps=warps) as plan:
         assert plan.kernel_forms()["dt_map"] == "split"
         pd = torch.from_numpy(pi).cuda()
         for _ in range(2):

@@ -45,7 +45,7 @@ def _plan(case, torch, prec, **opt):
     return Plan(case, stream=torch.cuda.current_stream().cuda_stream, precision=_prec(prec), **opt)
 
 
-@pytest.mark.parametrize("form", ["lanes", "units"])
+@pytest.mark.parametrize("form", ["lanes", "units", "merge"])
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("name,case", CASES, ids=[c[0] for c in CASES])
 def test_dose_16bit(torch, name, case, prec, form):
