@@ -208,11 +208,13 @@ __device__ __forceinline__ void dt_row_ticket_warp(const RowTicket& rt, int row,
 // every warp streams the same number of bytes whatever the row lengths, and
 // the 32 gathers of a step fall on a few cache lines.  Every row has at least
 // 32 entries, so a step crosses at most one row end.  At a row end the warp
-// sums its lanes (fixed butterfly) into the row's partial for this warp; a
-// row within one warp is final at once, a row covered by warps v0 .. v1
-// stores its partial at slot v - v0 and the last of them to take the row's
-// ticket adds the slots in order in FP64.  Lane 0 writes w[row] (times the
-// beamlet scale for 16-bit values) and takes the fused MLC-row ticket.
+// sums its lanes (fixed butterfly): a row within the warp's range is final
+// (lane 0 writes w[row], times the beamlet scale for 16-bit values); a row
+// covered by warps v0 .. v1 stores this warp's sum at slot v - v0.  Only after
+// its range does the warp take the tickets of its rows (an acquire-release
+// atomic waits for the warp's loads in flight, so none is taken while the
+// stream runs): the last of a row's warps adds the slots in order in FP64 and
+// writes w[row]; then the fused MLC-row ticket.
 constexpr int SPLIT_THREADS = 256;
 
 template <int VK>  // 0: FP32 values, 1: FP16, 2: BF16
@@ -235,6 +237,9 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_dt_split(
         else
             return unpack1<VK == 2>(__ldg(static_cast<const unsigned short*>(valv) + e));
     };
+    auto finish = [&](int r, double tot) {
+        w[r] = VK == 0 ? (float)tot : (float)(tot * (double)__ldg(scale + r));
+    };
     int cn[U];
     float vn[U];
     auto load_batch = [&](int s0) {
@@ -247,34 +252,22 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_dt_split(
     };
     load_batch(e_begin);
     // a window of 32 row offsets, lane l holding rowptr[rbase + l]
-    int rbase = __ldg(split_row + wg);
+    const int r_first = __ldg(split_row + wg);
+    int rbase = r_first;
     int rp = __ldg(rowptr + min(rbase + lane, N));
     int ri = 0;
     int rstart = __shfl_sync(FULL, rp, 0);
     int rend = __shfl_sync(FULL, rp, 1);
-    auto flush = [&](int r, int rs, int re, float a) {
+    // a row's sum over this warp's entries: final, or this warp's slot
+    auto store = [&](int r, int rs, int re, float a) {
         const float p = warp_sum_f32(a);
-        int fin = -1;
         if (lane == 0) {
             const int v0 = rs / chunk, v1 = (re - 1) / chunk;
-            double tot = (double)p;
-            bool done = true;
-            if (v1 > v0) {
+            if (v1 > v0)
                 part[(size_t)r * PS + (wg - v0)] = p;
-                done = (int)atom_add_acq_rel_gpu(reinterpret_cast<unsigned*>(cnt + r), 1u) == v1 - v0;
-                if (done) {
-                    cnt[r] = 0;  // every warp of the row has taken its ticket
-                    tot = 0.0;
-                    for (int k = 0; k <= v1 - v0; ++k) tot += (double)__ldcg(part + (size_t)r * PS + k);
-                }
-            }
-            if (done) {
-                w[r] = VK == 0 ? (float)tot : (float)(tot * (double)__ldg(scale + r));
-                fin = r;
-            }
+            else
+                finish(r, (double)p);
         }
-        fin = __shfl_sync(FULL, fin, 0);
-        if (fin >= 0) dt_row_ticket_warp(rt, fin, w);
     };
     float acc = 0.f;
     for (int s0 = e_begin; s0 < e_end; s0 += 32 * U) {
@@ -299,7 +292,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_dt_split(
                 // the row ends inside this step: lanes below rend finish it
                 const int e = t + lane;
                 if (e < rend) acc = fmaf(v[q], a[q], acc);
-                flush(rbase + ri, rstart, rend, acc);
+                store(rbase + ri, rstart, rend, acc);
                 if (++ri == 31) {  // next window of row offsets
                     rbase += 31;
                     rp = __ldg(rowptr + min(rbase + lane, N));
@@ -311,7 +304,29 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_dt_split(
             }
         }
     }
-    flush(rbase + ri, rstart, rend, acc);  // the row this warp's range ends in
+    const int r_last = rbase + ri;
+    store(r_last, rstart, rend, acc);  // the row this warp's range ends in
+    // tickets of the rows, in order
+    for (int r = r_first; r <= r_last; ++r) {
+        int fin = -1;
+        if (lane == 0) {
+            const int rs = __ldg(rowptr + r), re = __ldg(rowptr + r + 1);
+            const int v0 = rs / chunk, v1 = (re - 1) / chunk;
+            bool done = true;
+            if (v1 > v0) {
+                done = (int)atom_add_acq_rel_gpu(reinterpret_cast<unsigned*>(cnt + r), 1u) == v1 - v0;
+                if (done) {
+                    cnt[r] = 0;  // every warp of the row has taken its ticket
+                    double tot = 0.0;
+                    for (int k = 0; k <= v1 - v0; ++k) tot += (double)__ldcg(part + (size_t)r * PS + k);
+                    finish(r, tot);
+                }
+            }
+            fin = done ? r : -1;
+        }
+        fin = __shfl_sync(FULL, fin, 0);
+        if (fin >= 0) dt_row_ticket_warp(rt, fin, w);
+    }
 }
 
 template <int G>
