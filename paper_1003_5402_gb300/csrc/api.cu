@@ -453,22 +453,22 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     DAO_TRY(cu(cudaStreamSynchronize(st), "device build"));
     c->D.unit_groups_max = std::max(umax[0], 1);
     {
-        // the merge form of a1: the stored entries in equal chunks of groups
-        // (longer than the longest row) over a fixed set of warps
-        const int64_t G_tot = padded / pad_m;
+        // the merge form of a1: the merge of D's groups and row ends in equal
+        // stretches (longer than the longest row) over a fixed set of warps
+        const int64_t items = padded / pad_m + V;
         const int64_t warps =
             c->opt.split_warps > 0 ? (int64_t)c->opt.split_warps : (int64_t)c->num_sms * MERGE_WARPS_PER_SM;
-        int64_t chunk = std::max<int64_t>((G_tot + warps - 1) / warps, (int64_t)umax[1] + 1);
+        int64_t chunk = std::max<int64_t>((items + warps - 1) / warps, (int64_t)umax[1] + 1);
         if (chunk > MERGE_CHUNK_MAX) chunk = std::max<int64_t>(MERGE_CHUNK_MAX, (int64_t)umax[1] + 1);
-        if (G_tot > 0 && chunk <= MERGE_CHUNK_MAX) {
-            const int nw = (int)((G_tot + chunk - 1) / chunk);
-            int* mr = nullptr;
-            DAO_TRY(c->dalloc(&mr, (size_t)nw + 1));
+        if (padded > 0 && chunk <= MERGE_CHUNK_MAX) {
+            const int nw = (int)((items + chunk - 1) / chunk);
+            int2* mp = nullptr;
+            DAO_TRY(c->dalloc(&mp, (size_t)nw + 1));
             DAO_TRY(c->dalloc(&c->D.merge_slot, 2 * (size_t)nw));
             DAO_TRY(c->dalloc(&c->D.merge_cnt, (size_t)nw));
             DAO_TRY(cu(cudaMemsetAsync(c->D.merge_cnt, 0, sizeof(int) * (size_t)nw, st), "merge tickets"));
-            DAO_TRY(cu(build_merge_rows(c->D.rowptr, V, pad_m, (int)chunk, nw, mr, st), "merge rows"));
-            c->D.merge_rows = mr;
+            DAO_TRY(cu(build_merge_path(c->D.rowptr, V, pad_m, (int)chunk, nw, mp, st), "merge path"));
+            c->D.merge_path = mp;
             c->D.merge_chunk = (int)chunk;
             c->D.merge_warps = nw;
         }

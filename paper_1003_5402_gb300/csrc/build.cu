@@ -444,31 +444,29 @@ __global__ void k_unit_max(const int* __restrict__ prow, int V, int epg, int* __
     atomicMax(out + 1, m / epg);
 }
 
-// One thread per warp of the merge form: the first row whose offset is at
-// least the warp's first entry (binary search over the row offsets).
-__global__ void k_merge_rows(const int* __restrict__ prow, int V, int epg, int chunk, int n_warps,
-                             int* __restrict__ out) {
+// One thread per split of the merge form: at diagonal d the largest i in
+// [max(0, d - G), min(d, V)] whose row i - 1 ends within the first d - i groups
+// (binary search: the condition holds up to that i and fails after it).
+__global__ void k_merge_path(const int* __restrict__ prow, int V, int epg, int chunk, int n_warps,
+                             int2* __restrict__ out) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v > n_warps) return;
-    if (v == n_warps) {
-        out[v] = V;
-        return;
-    }
-    const long long e = (long long)v * chunk * epg;
-    int lo = 0, hi = V;  // the first r in [0, V] with prow[r] >= e
+    const long long G = prow[V] / epg;
+    const long long d = min((long long)v * chunk, (long long)V + G);
+    long long lo = max(0LL, d - G), hi = min(d, (long long)V);
     while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((long long)prow[mid] >= e)
-            hi = mid;
+        const long long mid = (lo + hi + 1) >> 1;
+        if ((long long)(prow[mid] / epg) <= d - mid)  // row mid - 1 ends within d - mid groups
+            lo = mid;
         else
-            lo = mid + 1;
+            hi = mid - 1;
     }
-    out[v] = lo;
+    out[v] = make_int2((int)lo, (int)(d - lo));
 }
 }  // namespace
 
-cudaError_t build_merge_rows(const int* prow, int V, int epg, int chunk, int n_warps, int* out, cudaStream_t s) {
-    k_merge_rows<<<(n_warps + 1 + 255) / 256, 256, 0, s>>>(prow, V, epg, chunk, n_warps, out);
+cudaError_t build_merge_path(const int* prow, int V, int epg, int chunk, int n_warps, int2* out, cudaStream_t s) {
+    k_merge_path<<<(n_warps + 1 + 255) / 256, 256, 0, s>>>(prow, V, epg, chunk, n_warps, out);
     return cudaGetLastError();
 }
 

@@ -81,14 +81,15 @@ struct DevCSR {
     // the row holding its first entry; a row covered by several warps adds their
     // partial sums (split_part, split_ps slots per row) in warp order, on a
     // per-row ticket (split_cnt, zero between launches)
-    // D split over warps by entries (DOSE_FORM_MERGE): warp v takes groups
-    // [v merge_chunk, (v + 1) merge_chunk) and owns the rows merge_rows[v] ..
-    // merge_rows[v + 1] - 1 (those starting in its range); a row crossing the
-    // boundary before warp v is finished from merge_slot[2v], merge_slot[2v + 1]
-    // on the ticket merge_cnt[v] (zero between launches)
-    int merge_chunk = 0;     // 0: the merge form is not available
+    // D split over warps along the merge path of its groups and row ends
+    // (DOSE_FORM_MERGE): warp v takes the stretch between merge_path[v] and
+    // merge_path[v + 1] (rows finished, groups consumed), merge_chunk items,
+    // more than the longest row; a row crossing the boundary before warp v is
+    // finished from merge_slot[2v], merge_slot[2v + 1] on the ticket
+    // merge_cnt[v] (zero between launches)
+    int merge_chunk = 0;     // items per warp (its most groups); 0: the merge form is not available
     int merge_warps = 0;
-    const int* merge_rows = nullptr;
+    const int2* merge_path = nullptr;
     float* merge_slot = nullptr;
     int* merge_cnt = nullptr;
     int split_chunk = 0;     // 0: the split form is not available
@@ -430,9 +431,10 @@ cudaError_t build_seg(const int64_t* rp, const int* col, const int* prow, int V,
 // padded D (row offsets prow) into out[0], the most in one row into out[1]
 // (both zeroed by the call).
 cudaError_t build_unit_max(const int* prow, int V, int epg, int* out, cudaStream_t s);
-// Rows owned by each warp of the merge form: out[v] = the first row starting
-// at or after entry v * chunk * epg (v < n_warps), out[n_warps] = V.
-cudaError_t build_merge_rows(const int* prow, int V, int epg, int chunk, int n_warps, int* out, cudaStream_t s);
+// Merge-path splits of the merge form: out[v] = (rows done, groups consumed)
+// at diagonal min(v * chunk, V + groups), rows finished as soon as their groups
+// are (prow in entries, epg entries per group), v = 0 .. n_warps.
+cudaError_t build_merge_path(const int* prow, int V, int epg, int chunk, int n_warps, int2* out, cudaStream_t s);
 cudaError_t build_transpose_place(int prec, const int64_t* rp, const int* col, const float* val, int V, int CH, int N,
                                   int n_ch, int* C, const int* cnt, const float* scale, DevCSR& Dt, float* tval,
                                   int num_sms, cudaStream_t s);

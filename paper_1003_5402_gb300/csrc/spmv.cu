@@ -240,17 +240,28 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_dt_split(
     auto finish = [&](int r, double tot) {
         w[r] = VK == 0 ? (float)tot : (float)(tot * (double)__ldg(scale + r));
     };
-    int cn[U];
-    float vn[U];
-    auto load_batch = [&](int s0) {
+    // three stages in flight: the indices and values of batch k + 2, the pi
+    // gathers of batch k + 1, the products of batch k
+    int c1[U], c2[U];
+    float v0[U], v1[U], v2[U], a0[U], a1[U];
+    auto load_batch = [&](int s0, int* cc, float* vv) {
 #pragma unroll
         for (int q = 0; q < U; ++q) {
             const int e = s0 + 32 * q + lane;
-            cn[q] = e < e_end ? __ldg(col + e) : -1;
-            vn[q] = e < e_end ? loadv(e) : 0.f;
+            cc[q] = e < e_end ? __ldg(col + e) : -1;
+            vv[q] = e < e_end ? loadv(e) : 0.f;
         }
     };
-    load_batch(e_begin);
+    auto gather = [&](const int* cc, float* aa) {
+#pragma unroll
+        for (int q = 0; q < U; ++q) aa[q] = cc[q] >= 0 ? __ldg(pi + cc[q]) : 0.f;
+    };
+    {
+        int c0[U];
+        load_batch(e_begin, c0, v0);
+        load_batch(e_begin + 32 * U, c1, v1);
+        gather(c0, a0);
+    }
     // a window of 32 row offsets, lane l holding rowptr[rbase + l]
     const int r_first = __ldg(split_row + wg);
     int rbase = r_first;
@@ -262,36 +273,27 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_dt_split(
     auto store = [&](int r, int rs, int re, float a) {
         const float p = warp_sum_f32(a);
         if (lane == 0) {
-            const int v0 = rs / chunk, v1 = (re - 1) / chunk;
-            if (v1 > v0)
-                part[(size_t)r * PS + (wg - v0)] = p;
+            const int wa = rs / chunk, wb = (re - 1) / chunk;  // the row's first and last warps
+            if (wb > wa)
+                part[(size_t)r * PS + (wg - wa)] = p;
             else
                 finish(r, (double)p);
         }
     };
     float acc = 0.f;
     for (int s0 = e_begin; s0 < e_end; s0 += 32 * U) {
-        int c[U];
-        float v[U];
-#pragma unroll
-        for (int q = 0; q < U; ++q) {
-            c[q] = cn[q];
-            v[q] = vn[q];
-        }
-        load_batch(s0 + 32 * U);
-        float a[U];
-#pragma unroll
-        for (int q = 0; q < U; ++q) a[q] = c[q] >= 0 ? __ldg(pi + c[q]) : 0.f;
+        load_batch(s0 + 64 * U, c2, v2);
+        gather(c1, a1);
 #pragma unroll
         for (int q = 0; q < U; ++q) {
             const int t = s0 + 32 * q;
             if (t >= e_end) break;  // uniform
             if (rend >= t + 32 || rend >= e_end) {
-                acc = fmaf(v[q], a[q], acc);  // lanes past e_end add 0 * 0
+                acc = fmaf(v0[q], a0[q], acc);  // lanes past e_end add 0 * 0
             } else {
                 // the row ends inside this step: lanes below rend finish it
                 const int e = t + lane;
-                if (e < rend) acc = fmaf(v[q], a[q], acc);
+                if (e < rend) acc = fmaf(v0[q], a0[q], acc);
                 store(rbase + ri, rstart, rend, acc);
                 if (++ri == 31) {  // next window of row offsets
                     rbase += 31;
@@ -300,8 +302,15 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_dt_split(
                 }
                 rstart = rend;
                 rend = __shfl_sync(FULL, rp, ri + 1);
-                acc = (e >= rstart && e < e_end) ? fmaf(v[q], a[q], 0.f) : 0.f;
+                acc = (e >= rstart && e < e_end) ? fmaf(v0[q], a0[q], 0.f) : 0.f;
             }
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            v0[q] = v1[q];
+            a0[q] = a1[q];
+            c1[q] = c2[q];
+            v1[q] = v2[q];
         }
     }
     const int r_last = rbase + ri;
@@ -311,14 +320,14 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_dt_split(
         int fin = -1;
         if (lane == 0) {
             const int rs = __ldg(rowptr + r), re = __ldg(rowptr + r + 1);
-            const int v0 = rs / chunk, v1 = (re - 1) / chunk;
+            const int wa = rs / chunk, wb = (re - 1) / chunk;
             bool done = true;
-            if (v1 > v0) {
-                done = (int)atom_add_acq_rel_gpu(reinterpret_cast<unsigned*>(cnt + r), 1u) == v1 - v0;
+            if (wb > wa) {
+                done = (int)atom_add_acq_rel_gpu(reinterpret_cast<unsigned*>(cnt + r), 1u) == wb - wa;
                 if (done) {
                     cnt[r] = 0;  // every warp of the row has taken its ticket
                     double tot = 0.0;
-                    for (int k = 0; k <= v1 - v0; ++k) tot += (double)__ldcg(part + (size_t)r * PS + k);
+                    for (int k = 0; k <= wb - wa; ++k) tot += (double)__ldcg(part + (size_t)r * PS + k);
                     finish(r, tot);
                 }
             }
@@ -586,29 +595,33 @@ __global__ void __launch_bounds__(UNIT_THREADS, 2) k_dose_units(
     }
 }
 
-// ---- a1 split evenly over warps by entries ---------------------------------
-// Warp v takes the groups [v chunk, (v + 1) chunk) of D's stored entries (8
-// per group with 16-bit storage, 4 with FP32) and requests its first UB
-// groups per lane before anything else (their addresses need no row offset);
-// group dot products go to the warp's row of shared partials.  The warp owns
-// the rows that start in its range (mrows[v] .. mrows[v + 1] - 1, empty rows
-// included): lane l sums row l's partials in group order and applies the
-// epilogue, 32 rows at a time.  chunk exceeds the longest row, so a row
-// extends into at most the next warp: its owner stores the sum of its groups
-// (slot 0 of the boundary), the next warp the sum of the row's groups in its
-// range (slot 1), and the second of the two to take the boundary's ticket
-// forms z = slot 0 + slot 1, applies the epilogue and writes the row's
-// objective term to F_part[F_stride + boundary] (0 where no row crosses the
-// boundary), so that F is a fixed-order sum whichever warp finishes first.
+// ---- a1 split evenly over warps along the merge path ------------------------
+// The work of a1 is the merge of two sequences, D's groups of stored entries
+// (8 per group with 16-bit storage, 4 with FP32) and the row ends (a row is
+// done once its groups are): warp v takes the stretch of that merge between
+// the splits path[v] = (rows done, groups consumed) and path[v + 1], the
+// same number of items for every warp (Merrill & Garland's merge-path
+// split), so empty rows (one item each) spread over the warps like entries.
+// The warp requests its first UB groups per lane as soon as it has its
+// split, puts each group's dot product with x (staged in shared memory) in its
+// row of shared partials, and finishes the rows that end in its stretch: lane
+// l sums row l's partials in group order and applies the epilogue, 32 rows at
+// a time.  Every stretch is longer than the longest row, so a row has groups
+// in at most two stretches: the earlier warp stores the sum of the row's
+// groups it holds (slot 0 of the boundary), the warp that finishes the row
+// the sum of the rest (slot 1), and the second of the two to take the
+// boundary's ticket forms z = slot 0 + slot 1, applies the epilogue and writes
+// the row's objective term to F_part[F_stride + boundary] (0 where no row
+// crosses the boundary), so that F is a fixed-order sum whichever warp
+// finishes first.
 constexpr int MERGE_THREADS = 256;
-constexpr int MERGE_CAP = 1024;  // groups per warp (its row of shared partials)
 
 template <bool L16, bool BF>
 __global__ void __launch_bounds__(MERGE_THREADS, 4) k_dose_merge(
-    const int* __restrict__ rowptr, const uint4* __restrict__ colg, const uint4* __restrict__ valg, int V, int G_tot,
+    const int* __restrict__ rowptr, const uint4* __restrict__ colg, const uint4* __restrict__ valg, int V,
     const float* __restrict__ x, const float* __restrict__ scale, int N, const uint8_t* __restrict__ vstruct,
     const StructTermsS* __restrict__ ts, int S, float* __restrict__ z, float* __restrict__ grad,
-    double* __restrict__ F_part, int F_stride, int chunk, int n_warps, const int* __restrict__ mrows,
+    double* __restrict__ F_part, int F_stride, int cap, int n_warps, const int2* __restrict__ path,
     float* __restrict__ slot, int* __restrict__ cnt) {
     constexpr int EPG = L16 ? 8 : 4;
     constexpr int UB = 4;
@@ -620,10 +633,13 @@ __global__ void __launch_bounds__(MERGE_THREADS, 4) k_dose_merge(
     const int wg = blockIdx.x * NW + wib;
     const bool active = wg < n_warps;  // uniform per warp; idle warps still meet the block barrier
     float* sx = s_dyn_merge;
-    float* spart = s_dyn_merge + ((N + 3) & ~3) + wib * chunk;
-    const int g_begin = wg * chunk;
-    const int g_end = active ? min(g_begin + chunk, G_tot) : g_begin;
-    const int ng = g_end - g_begin;
+    float* spart = s_dyn_merge + ((N + 3) & ~3) + wib * cap;
+    int2 p0 = make_int2(0, 0), p1 = make_int2(0, 0);
+    if (active) {
+        p0 = __ldg(path + wg);
+        p1 = __ldg(path + wg + 1);
+    }
+    const int r0 = p0.x, r1 = p1.x, g_begin = p0.y, ng = p1.y - p0.y;
     uint4 c[UB], v[UB];
     auto load_batch = [&](int k0) {
 #pragma unroll
@@ -636,12 +652,8 @@ __global__ void __launch_bounds__(MERGE_THREADS, 4) k_dose_merge(
         }
     };
     load_batch(0);
-    // the owned rows and the first 32 of them
-    int r0 = 0, r1 = 0;
-    if (active) {
-        r0 = __ldg(mrows + wg);
-        r1 = __ldg(mrows + wg + 1);
-    }
+    // the rows this warp finishes (r0 .. r1 - 1), 32 at a time, and the row it
+    // leaves unfinished (r1, when it holds some of its groups)
     int rs = 0, re = 0, lab = 0;
     auto row_meta = [&](int r) {
         rs = re = 0;
@@ -653,7 +665,7 @@ __global__ void __launch_bounds__(MERGE_THREADS, 4) k_dose_merge(
         }
     };
     row_meta(r0 + lane);
-    const int rs0 = active ? __ldg(rowptr + r0) : 0;  // start of the first owned row
+    const int rs_out = active && r1 < V ? __ldg(rowptr + r1) : 0;
     for (int i = threadIdx.x; i < N; i += MERGE_THREADS) sx[i] = L16 ? __ldg(x + i) * __ldg(scale + i) : __ldg(x + i);
     for (int i = threadIdx.x; i < S; i += MERGE_THREADS) s_ts[i] = ts[i];
     __syncthreads();
@@ -691,30 +703,30 @@ __global__ void __launch_bounds__(MERGE_THREADS, 4) k_dose_merge(
         }
     };
     float facc = 0.f;
-    if (active && lane == 0) {
-        // the groups before the first owned row belong to the previous warp's last row
-        const int gh = rs0 / EPG - g_begin;
-        if (gh > 0) {
-            float a = 0.f;
-            for (int g = 0; g < gh; ++g) a += spart[g];
-            cross(wg, 1, a, r0 - 1, S >= 0 ? __ldg(vstruct + r0 - 1) : 0);
-        } else if (F_part != nullptr) {
-            F_part[F_stride + wg] = 0.0;  // no row crosses the boundary at this warp's first group
-        }
-    }
+    bool crossed_in = false;  // (lane 0) the first row began in the previous stretch
     for (int rb = r0; rb < r1; rb += 32) {
         const int r = rb + lane;
         const int crs = rs, cre = re, cl = lab;
-        if (rb + 32 < r1) row_meta(rb + 32 + lane);  // the next 32 owned rows
+        if (rb + 32 < r1) row_meta(rb + 32 + lane);  // the next 32 rows
         if (r < r1) {
-            const int gs = crs / EPG - g_begin, ge_full = cre / EPG - g_begin;
-            const int ge = min(ge_full, ng);
+            const int gs = max(crs / EPG - g_begin, 0), ge = cre / EPG - g_begin;
             float acc = 0.f;
             for (int g = gs; g < ge; ++g) acc += spart[g];
-            if (ge_full > ng)
-                cross(wg + 1, 0, acc, r, cl);  // continues in the next warp
-            else
+            if (crs / EPG < g_begin) {  // only the first row: its other groups are the previous warp's
+                crossed_in = true;
+                cross(wg, 1, acc, r, cl);
+            } else {
                 facc += epilogue(r, acc, cl);
+            }
+        }
+    }
+    if (active && lane == 0) {
+        if (!crossed_in && F_part != nullptr) F_part[F_stride + wg] = 0.0;  // no row crosses into this stretch
+        if (r1 < V && rs_out / EPG < g_begin + ng) {
+            // row r1 continues in the next stretch: the sum of its groups here
+            float a = 0.f;
+            for (int g = rs_out / EPG - g_begin; g < ng; ++g) a += spart[g];
+            cross(wg + 1, 0, a, r1, S >= 0 ? __ldg(vstruct + r1) : 0);
         }
     }
     if (F_part != nullptr) {
@@ -1019,8 +1031,8 @@ void column_dev_launch(const DevCSR& D, const int* seg, const int* ap_beam, int 
 
 }  // namespace
 
-size_t merge_smem(int N, int chunk) {
-    return (size_t)((N + 3) & ~3) * sizeof(float) + (size_t)(MERGE_THREADS / 32) * chunk * sizeof(float);
+size_t merge_smem(int N, int cap) {
+    return (size_t)((N + 3) & ~3) * sizeof(float) + (size_t)(MERGE_THREADS / 32) * cap * sizeof(float);
 }
 
 template <bool L16, bool BF>
@@ -1031,10 +1043,9 @@ cudaError_t dose_merge(const DevCSR& D, const float* x, const uint8_t* vstruct, 
     F_used = grid + D.merge_warps;
     const void* colp = L16 ? static_cast<const void*>(D.col16) : static_cast<const void*>(D.col);
     const void* valp = L16 ? static_cast<const void*>(D.val16) : static_cast<const void*>(D.val);
-    const int G_tot = (int)(D.nnz_stored / (L16 ? 8 : 4));
     k_dose_merge<L16, BF><<<grid, MERGE_THREADS, smem, stream>>>(
-        D.rowptr, static_cast<const uint4*>(colp), static_cast<const uint4*>(valp), D.n_rows, G_tot, x, D.scale,
-        D.n_cols, vstruct, ts, S, z, grad, F_part, grid, D.merge_chunk, D.merge_warps, D.merge_rows, D.merge_slot,
+        D.rowptr, static_cast<const uint4*>(colp), static_cast<const uint4*>(valp), D.n_rows, x, D.scale, D.n_cols,
+        vstruct, ts, S, z, grad, F_part, grid, D.merge_chunk, D.merge_warps, D.merge_path, D.merge_slot,
         D.merge_cnt);
     return cudaGetLastError();
 }
