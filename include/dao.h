@@ -132,8 +132,7 @@ typedef struct dao_options {
                                 * memory) leave room for other plans' solves to run side by side */
     int32_t dt_threads;        /* threads per beamlet row of the transposed SpMV: 0 (default: 64, or the
                                 * autotuner's choice), 64, 128 or 256 */
-    int32_t dt_map;            /* form of the transposed SpMV: 0 (default: DAO_DT_SPLIT where every row of
-                                * D^T has at least 32 stored entries, else DAO_DT_CONSECUTIVE; or the
+    int32_t dt_map;            /* form of the transposed SpMV: 0 (default: DAO_DT_CONSECUTIVE, or the
                                 * autotuner's choice); DAO_DT_GROUPED (a block per beamlet row, a thread per
                                 * 4 or 8 consecutive entries, 16-byte loads), DAO_DT_CONSECUTIVE (a block per
                                 * row, consecutive entries on consecutive threads: the pi gathers of a warp
@@ -141,12 +140,13 @@ typedef struct dao_options {
                                 * fixed set of warps, consecutive entries on consecutive lanes; a row covered
                                 * by several warps adds their partial sums in warp order; falls back to
                                 * DAO_DT_CONSECUTIVE where a row is shorter than 32 entries) */
-    int32_t dose_form;         /* form of the dose SpMV: 0 (default: DAO_DOSE_MERGE, else DAO_DOSE_UNITS, where
-                                * its shared memory fits; or the autotuner's choice), DAO_DOSE_LANES (4 to 32
-                                * lanes per voxel row), DAO_DOSE_UNITS (one warp per 32 consecutive rows, their
-                                * entries requested at once) or DAO_DOSE_MERGE (the stored entries split
-                                * evenly over a fixed set of warps, requested before any row offset; a row
-                                * crossing two warps' ranges is finished by the later of the two) */
+    int32_t dose_form;         /* form of the dose SpMV: 0 (default: DAO_DOSE_UNITS where its shared memory
+                                * fits, or the autotuner's choice), DAO_DOSE_LANES (4 to 32 lanes per voxel
+                                * row), DAO_DOSE_UNITS (one warp per 32 consecutive rows, their entries
+                                * requested at once) or DAO_DOSE_MERGE (the merge of the stored entries and
+                                * the row ends split evenly over a fixed set of warps, entries requested
+                                * before any row offset; a row across two warps' stretches is finished by
+                                * the later of the two) */
     int32_t column_lanes;      /* lanes per voxel row of the aperture column (a4): 0 (default: 8, or the
                                 * autotuner's choice), 1, 2, 4, 8 or 16 */
     int32_t split_warps;       /* warps of the forms that split D's or D^T's stored entries evenly over warps

@@ -2373,7 +2373,7 @@ dao_status dao_kernel_forms(const dao_ctx* c, dao_tuning* out) {
     if (!c || !out) return fail(DAO_EINVAL, "null argument");
     const DevCSR& D = c->D;
     const DevCSR& Dt = c->Dt;
-    const bool split = (Dt.tune_dt_map == 0 || Dt.tune_dt_map == DT_MAP_SPLIT) && Dt.split_chunk > 0;
+    const bool split = Dt.tune_dt_map == DT_MAP_SPLIT && Dt.split_chunk > 0;
     out->dose_form = dose_form_effective(D);
     out->dose_lanes = D.tune_dose_g;
     out->column_lanes = D.tune_col_g ? D.tune_col_g : 8;

@@ -1064,7 +1064,7 @@ bool dose_units_available(const DevCSR& D) {
 
 int dose_form_effective(const DevCSR& D) {
     const int f = D.tune_dose_form;
-    if ((f == 0 || f == DOSE_FORM_MERGE) && dose_merge_available(D)) return DOSE_FORM_MERGE;
+    if (f == DOSE_FORM_MERGE && dose_merge_available(D)) return DOSE_FORM_MERGE;
     if (f != DOSE_FORM_LANES && dose_units_available(D)) return DOSE_FORM_UNITS;
     return DOSE_FORM_LANES;
 }
@@ -1131,7 +1131,7 @@ cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct,
 static cudaError_t dt_dispatch(const DevCSR& Dt, const float* pi, float* w, const int* skip, const RowTicket& rt,
                         cudaStream_t stream, int* launches) {
     if (Dt.n_rows == 0) return cudaSuccess;
-    if ((Dt.tune_dt_map == 0 || Dt.tune_dt_map == DT_MAP_SPLIT) && Dt.split_chunk > 0) {
+    if (Dt.tune_dt_map == DT_MAP_SPLIT && Dt.split_chunk > 0) {
         const int grid = (Dt.split_warps + SPLIT_THREADS / 32 - 1) / (SPLIT_THREADS / 32);
         const int E = (int)Dt.nnz_stored;
         if (Dt.prec == DAO_PREC_FP16)

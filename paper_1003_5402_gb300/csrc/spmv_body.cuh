@@ -119,9 +119,10 @@ __device__ __forceinline__ float dt16_row_sum(const int* __restrict__ rowptr, co
 }
 
 // a2 with consecutive entries on consecutive threads: thread t takes entries
-// e0 + t, e0 + t + BT, ... of the row, U at a time, with the indices and values
-// of two batches and the pi gathers of one batch in flight ahead of the
-// products of the current one.  A row of D^T lists its voxels in increasing
+// e0 + t, e0 + t + BT, ... of the row, U at a time, the next U requested while
+// the current U's pi gathers run (a deeper pipeline needs more registers, and
+// then the 64-thread blocks of every row no longer fit one wave).  A row of D^T
+// lists its voxels in increasing
 // order, so the 32 gathers of one warp instruction fall on a few cache lines
 // (the grouped form above spreads them over 8 x 32 entries).  Scalar loads of
 // the voxel index (and the 16-bit value); padding entries (value 0, a valid
@@ -129,42 +130,36 @@ __device__ __forceinline__ float dt16_row_sum(const int* __restrict__ rowptr, co
 template <int BT, int U, class LoadV>
 __device__ __forceinline__ float dt_row_consecutive(int e0, int e1, const int* __restrict__ col, LoadV loadv,
                                                     const float* __restrict__ pi) {
-    // three stages in flight: indices and values of batch k + 2, the pi
-    // gathers of batch k + 1, the products of batch k
-    int c1[U], c2[U];
-    float v0[U], v1[U], v2[U], a0[U], a1[U];
-    auto load_batch = [&](int e, int* cc, float* vv) {
+    float acc = 0.f;
+    int e = e0 + (int)threadIdx.x;
+    int cn[U];
+    float vn[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+        const int p = e + q * BT;
+        cn[q] = p < e1 ? __ldg(col + p) : -1;
+        vn[q] = p < e1 ? loadv(p) : 0.f;
+    }
+    while (e < e1) {
+        int c[U];
+        float v[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            c[q] = cn[q];
+            v[q] = vn[q];
+        }
+        e += BT * U;
 #pragma unroll
         for (int q = 0; q < U; ++q) {
             const int p = e + q * BT;
-            cc[q] = p < e1 ? __ldg(col + p) : -1;
-            vv[q] = p < e1 ? loadv(p) : 0.f;
+            cn[q] = p < e1 ? __ldg(col + p) : -1;
+            vn[q] = p < e1 ? loadv(p) : 0.f;
         }
-    };
-    auto gather = [&](const int* cc, float* aa) {
+        float a[U];
 #pragma unroll
-        for (int q = 0; q < U; ++q) aa[q] = cc[q] >= 0 ? __ldg(pi + cc[q]) : 0.f;
-    };
-    int e = e0 + (int)threadIdx.x;
-    {
-        int c0[U];
-        load_batch(e, c0, v0);
-        load_batch(e + BT * U, c1, v1);
-        gather(c0, a0);
-    }
-    float acc = 0.f;
-    for (; e < e1; e += BT * U) {
-        load_batch(e + 2 * BT * U, c2, v2);
-        gather(c1, a1);
+        for (int q = 0; q < U; ++q) a[q] = c[q] >= 0 ? __ldg(pi + c[q]) : 0.f;
 #pragma unroll
-        for (int q = 0; q < U; ++q) acc = fmaf(v0[q], a0[q], acc);
-#pragma unroll
-        for (int q = 0; q < U; ++q) {
-            v0[q] = v1[q];
-            a0[q] = a1[q];
-            c1[q] = c2[q];
-            v1[q] = v2[q];
-        }
+        for (int q = 0; q < U; ++q) acc = fmaf(v[q], a[q], acc);
     }
     return acc;
 }
