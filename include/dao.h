@@ -153,10 +153,6 @@ typedef struct dao_options {
                                 * (DAO_DOSE_MERGE, DAO_DT_SPLIT): 0 (default: 32 per SM) or any positive count
                                 * (fewer warps take longer chunks; the dose form's chunk stays longer than
                                 * the longest row and at most 1024 groups) */
-    int32_t pdl;               /* 1 (default): in the device-driven solve graph each round's D^T, decision and
-                                * column, and master kernels follow one another by programmatic dependent
-                                * launch (a kernel's blocks are scheduled while its predecessor finishes and
-                                * wait for its completion before they read or write); 0: plain order */
 } dao_options;
 
 enum { DAO_DT_GROUPED = 1, DAO_DT_CONSECUTIVE = 2, DAO_DT_SPLIT = 3 };

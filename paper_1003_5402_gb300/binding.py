@@ -58,7 +58,7 @@ class dao_options(C.Structure):
                 ("use_graphs", C.c_int32), ("master_persistent", C.c_int32), ("mlc_constraint", C.c_int32),
                 ("master_blocks", C.c_int32), ("dt_threads", C.c_int32), ("dt_map", C.c_int32),
                 ("dose_form", C.c_int32), ("column_lanes", C.c_int32),
-                ("split_warps", C.c_int32), ("pdl", C.c_int32)]
+                ("split_warps", C.c_int32)]
 
 
 class dao_tuning(C.Structure):

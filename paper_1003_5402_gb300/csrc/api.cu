@@ -266,7 +266,6 @@ dao_status validate(const dao_csr* D, const dao_geometry* g, const dao_structure
         opt->column_lanes != 8 && opt->column_lanes != 16)
         return fail(DAO_EINVAL, "column_lanes must be 0, 1, 2, 4, 8 or 16");
     if (opt->split_warps < 0) return fail(DAO_EINVAL, "split_warps must be >= 0");
-    if (opt->pdl != 0 && opt->pdl != 1) return fail(DAO_EINVAL, "pdl must be 0 or 1");
     if (opt->mlc_constraint < DAO_MLC_CONSECUTIVE || opt->mlc_constraint > DAO_MLC_JAWS)
         return fail(DAO_EINVAL, "mlc_constraint must be one of DAO_MLC_*");
     if (opt->mlc_constraint != DAO_MLC_CONSECUTIVE)
@@ -980,9 +979,6 @@ bool build_solve_graph_persist(dao_ctx* c) {
             ca.cg = c->cg;
             ca.cond = h;
             ca.use_cond = 1;
-            // the round's kernels after the first with programmatic dependent
-            // launch (no MLC-constrained pricing between them)
-            pdl_capture() = !mlc && c->opt.pdl != 0;
             for (int u = 0; u < ROUNDS_PER_ITER; ++u) {
                 check(launch_dt_rows(c->Dt, c->pi, c->w, rt, cs, &n));
                 if (mlc) check(price_rows_any(c, c->w, &c->cg->stop, cs, &n));
@@ -991,7 +987,6 @@ bool build_solve_graph_persist(dao_ctx* c) {
                                             c->opt.max_master_iters, c->opt.master_tol, skip, c->z, c->pi, c->cg,
                                             cs, &n));
             }
-            pdl_capture() = false;
             cudaGraph_t out = nullptr;
             const cudaError_t e2 = cudaStreamEndCapture(cs, &out);
             check(e2);
@@ -1303,7 +1298,6 @@ void dao_options_default(dao_options* opt) {
     opt->dose_form = 0;
     opt->column_lanes = 0;
     opt->split_warps = 0;
-    opt->pdl = 1;
 }
 
 const char* dao_last_error(void) { return g_err.c_str(); }

@@ -174,18 +174,6 @@ struct CGDev {
 
 // ---- kernel launchers (all on `stream`; return the launch error) ----------
 
-// Programmatic dependent launch between the kernels of a device-driven round:
-// while set (per thread, around the capture of the solve graph's rounds), the
-// round kernels are launched with programmatic stream serialisation, so a
-// kernel's blocks are scheduled as soon as every block of the one before it
-// has started; each of them waits (griddepcontrol.wait) for its predecessor's
-// completion and memory before it reads or writes anything.
-bool& pdl_capture();
-__device__ __forceinline__ void pdl_entry() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
 // a1: z = D x, optional grad F(z), FP64 F partials (one per block) reduced into *F_out.
 cudaError_t launch_dose(const DevCSR& D, const float* x, const uint8_t* vstruct,
                         const StructTermsF* tf, const StructTermsS* ts, int S,

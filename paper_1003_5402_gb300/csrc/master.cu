@@ -1445,7 +1445,6 @@ template <bool BATCH>
 __global__ void __launch_bounds__(PT, 2) k_master_persist(const __grid_constant__ MasterTask t1,
                                                           const MasterTask* __restrict__ tasks,
                                                        int GB, int K, int KP, int KW, int NV, double sigma) {
-    pdl_entry();
 #define DAO_TASK(f) (BATCH ? tasks[blockIdx.x / GB].f : t1.f)
     const float* __restrict__ slab = DAO_TASK(slab);
     const int ld = DAO_TASK(ld), V = DAO_TASK(V), GS = DAO_TASK(GS), S = DAO_TASK(S), max_iter = DAO_TASK(max_iter);
@@ -1714,13 +1713,11 @@ cudaError_t launch_master_persist(const MasterBuffers& mb, const float* slab, in
     cfg.blockDim = dim3(PT);
     cfg.dynamicSmemBytes = master_persist_smem(V, G);
     cfg.stream = stream;
-    cudaLaunchAttribute attr[2];
+    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
-    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = pdl_capture() ? 2 : 1;
+    cfg.numAttrs = 1;
     cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)k_master_persist<false>, args);
     ++*launches;
     return e;

@@ -174,7 +174,6 @@ __global__ void __launch_bounds__(BT) k_dt(const int* __restrict__ rowptr, const
                                            const float* __restrict__ pi, float* __restrict__ w,
                                            const int* __restrict__ skip, RowTicket rt) {
     __shared__ double s_red[BT / 32];
-    pdl_entry();
     dt_round_snapshot(rt);
     if (skip != nullptr && *skip) return;
     const int row = order[blockIdx.x];  // longest rows first: they start in the first wave
@@ -225,7 +224,6 @@ __global__ void __launch_bounds__(SPLIT_THREADS) k_dt_split(
     float* __restrict__ part, int PS, int* __restrict__ cnt, const float* __restrict__ pi, float* __restrict__ w,
     const int* __restrict__ skip, RowTicket rt) {
     constexpr int U = 4;
-    pdl_entry();
     dt_round_snapshot(rt);
     if (skip != nullptr && *skip) return;
     const int lane = threadIdx.x & 31;
@@ -747,7 +745,6 @@ __global__ void __launch_bounds__(BT) k_dt16(const int* __restrict__ rowptr, con
                                              const float* __restrict__ pi, float* __restrict__ w,
                                              const int* __restrict__ skip, RowTicket rt) {
     __shared__ double s_red[BT / 32];
-    pdl_entry();
     dt_round_snapshot(rt);
     if (skip != nullptr && *skip) return;
     const int row = order[blockIdx.x];  // longest rows first
@@ -809,7 +806,6 @@ __global__ void __launch_bounds__(256) k_commit_column(const int* __restrict__ c
     extern __shared__ double s_dyn[];
     double* s_sum = s_dyn;                                        // n_beams
     float* smask = reinterpret_cast<float*>(s_dyn + ca.n_beams);  // max_nb
-    pdl_entry();
     CGDev* cg = ca.cg;
     const int tid = threadIdx.x;
     const bool lead = blockIdx.x == 0 && tid == 0;
@@ -862,25 +858,6 @@ __global__ void __launch_bounds__(256) k_commit_column(const int* __restrict__ c
         column_body<G>(col, val, seg_lo, seg_hi, V, base, smask, out, 1, (int)(blockIdx.x * blockDim.x), (int)(gridDim.x * blockDim.x));
     else
         column16_body<G, PREC == DAO_PREC_BF16>(col16, val16, seg_lo, seg_hi, V, base, smask, out, 1, (int)(blockIdx.x * blockDim.x), (int)(gridDim.x * blockDim.x));
-}
-
-// A launch with programmatic stream serialisation while pdl_capture() is set.
-template <class... KArgs, class... Args>
-cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
-                       Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = stream;
-    cudaLaunchAttribute at[1];
-    if (pdl_capture()) {
-        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        at[0].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-    }
-    return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 // Blocks of a grid-stride kernel that are all resident at once (every block
@@ -964,11 +941,6 @@ cudaError_t dose_g(const DevCSR& D, const float* x, const uint8_t* vstruct, cons
 
 }  // namespace
 
-bool& pdl_capture() {
-    thread_local bool on = false;
-    return on;
-}
-
 int dose_grid(int n_rows, int num_sms) {
     (void)n_rows;
     return num_sms * 8;
@@ -1002,29 +974,29 @@ cudaError_t dose16_any(int g, const DevCSR& D, const float* x, const uint8_t* vs
 }
 
 template <int BT, bool LC>
-cudaError_t dt_launch(const DevCSR& Dt, const float* pi, float* w, const int* skip, const RowTicket& rt,
-                      cudaStream_t stream) {
-    const int4* col4 = reinterpret_cast<const int4*>(Dt.col);
-    const uint4* val8 = reinterpret_cast<const uint4*>(Dt.val16);
-    cudaError_t e;
+void dt_launch(const DevCSR& Dt, const float* pi, float* w, const int* skip, const RowTicket& rt,
+               cudaStream_t stream) {
     if (Dt.prec == DAO_PREC_FP16)
-        e = launch_pdl(k_dt16<BT, false, LC>, dim3(Dt.n_rows), dim3(BT), 0, stream, (const int*)Dt.rowptr, col4, val8,
-                       (const float*)Dt.scale, Dt.n_rows, (const int*)Dt.order, pi, w, skip, rt);
+        k_dt16<BT, false, LC><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
+                                                            reinterpret_cast<const uint4*>(Dt.val16), Dt.scale,
+                                                            Dt.n_rows, Dt.order, pi, w, skip, rt);
     else if (Dt.prec == DAO_PREC_BF16)
-        e = launch_pdl(k_dt16<BT, true, LC>, dim3(Dt.n_rows), dim3(BT), 0, stream, (const int*)Dt.rowptr, col4, val8,
-                       (const float*)Dt.scale, Dt.n_rows, (const int*)Dt.order, pi, w, skip, rt);
+        k_dt16<BT, true, LC><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
+                                                           reinterpret_cast<const uint4*>(Dt.val16), Dt.scale,
+                                                           Dt.n_rows, Dt.order, pi, w, skip, rt);
     else
-        e = launch_pdl(k_dt<BT, LC>, dim3(Dt.n_rows), dim3(BT), 0, stream, (const int*)Dt.rowptr, col4,
-                       reinterpret_cast<const float4*>(Dt.val), Dt.n_rows, (const int*)Dt.order, pi, w, skip, rt);
-    if (e != cudaSuccess) cudaGetLastError();
-    return e;
+        k_dt<BT, LC><<<Dt.n_rows, BT, 0, stream>>>(Dt.rowptr, reinterpret_cast<const int4*>(Dt.col),
+                                                    reinterpret_cast<const float4*>(Dt.val), Dt.n_rows, Dt.order, pi,
+                                                    w, skip, rt);
 }
 
 template <int BT>
-cudaError_t dt_launch_map(const DevCSR& Dt, const float* pi, float* w, const int* skip, const RowTicket& rt,
-                          cudaStream_t stream) {
-    if (Dt.tune_dt_map == DT_MAP_GROUPED) return dt_launch<BT, false>(Dt, pi, w, skip, rt, stream);
-    return dt_launch<BT, true>(Dt, pi, w, skip, rt, stream);
+void dt_launch_map(const DevCSR& Dt, const float* pi, float* w, const int* skip, const RowTicket& rt,
+                   cudaStream_t stream) {
+    if (Dt.tune_dt_map == DT_MAP_GROUPED)
+        dt_launch<BT, false>(Dt, pi, w, skip, rt, stream);
+    else
+        dt_launch<BT, true>(Dt, pi, w, skip, rt, stream);
 }
 
 template <int G>
@@ -1162,26 +1134,33 @@ static cudaError_t dt_dispatch(const DevCSR& Dt, const float* pi, float* w, cons
     if (Dt.tune_dt_map == DT_MAP_SPLIT && Dt.split_chunk > 0) {
         const int grid = (Dt.split_warps + SPLIT_THREADS / 32 - 1) / (SPLIT_THREADS / 32);
         const int E = (int)Dt.nnz_stored;
-        const void* vals = Dt.prec == DAO_PREC_FP32 ? static_cast<const void*>(Dt.val) : static_cast<const void*>(Dt.val16);
-        auto kern = Dt.prec == DAO_PREC_FP16 ? k_dt_split<1> : Dt.prec == DAO_PREC_BF16 ? k_dt_split<2> : k_dt_split<0>;
-        const cudaError_t e = launch_pdl(kern, dim3(grid), dim3(SPLIT_THREADS), 0, stream, (const int*)Dt.rowptr,
-                                         (const int*)Dt.col, vals, (const float*)Dt.scale, Dt.n_rows, E, Dt.split_chunk,
-                                         Dt.split_warps, (const int*)Dt.split_row, Dt.split_part, Dt.split_ps,
-                                         Dt.split_cnt, pi, w, skip, rt);
-        if (e != cudaSuccess) cudaGetLastError();
+        if (Dt.prec == DAO_PREC_FP16)
+            k_dt_split<1><<<grid, SPLIT_THREADS, 0, stream>>>(Dt.rowptr, Dt.col, Dt.val16, Dt.scale, Dt.n_rows, E,
+                                                              Dt.split_chunk, Dt.split_warps, Dt.split_row,
+                                                              Dt.split_part, Dt.split_ps, Dt.split_cnt, pi, w, skip,
+                                                              rt);
+        else if (Dt.prec == DAO_PREC_BF16)
+            k_dt_split<2><<<grid, SPLIT_THREADS, 0, stream>>>(Dt.rowptr, Dt.col, Dt.val16, Dt.scale, Dt.n_rows, E,
+                                                              Dt.split_chunk, Dt.split_warps, Dt.split_row,
+                                                              Dt.split_part, Dt.split_ps, Dt.split_cnt, pi, w, skip,
+                                                              rt);
+        else
+            k_dt_split<0><<<grid, SPLIT_THREADS, 0, stream>>>(Dt.rowptr, Dt.col, Dt.val, Dt.scale, Dt.n_rows, E,
+                                                              Dt.split_chunk, Dt.split_warps, Dt.split_row,
+                                                              Dt.split_part, Dt.split_ps, Dt.split_cnt, pi, w, skip,
+                                                              rt);
         ++*launches;
-        return e;
+        return cudaGetLastError();
     }
     // one block per beamlet row; 64 threads by default, so that up to 32 blocks
     // per SM keep every row resident in one wave
-    cudaError_t e;
     switch (Dt.tune_dt_threads) {
-        case 128: e = dt_launch_map<128>(Dt, pi, w, skip, rt, stream); break;
-        case 256: e = dt_launch_map<256>(Dt, pi, w, skip, rt, stream); break;
-        default: e = dt_launch_map<64>(Dt, pi, w, skip, rt, stream); break;
+        case 128: dt_launch_map<128>(Dt, pi, w, skip, rt, stream); break;
+        case 256: dt_launch_map<256>(Dt, pi, w, skip, rt, stream); break;
+        default: dt_launch_map<64>(Dt, pi, w, skip, rt, stream); break;
     }
     ++*launches;
-    return e;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dt(const DevCSR& Dt, const float* pi, float* w, const int* skip, cudaStream_t stream,
@@ -1237,23 +1216,16 @@ cudaError_t launch_column_dev(const DevCSR& D, const int* seg, const int* ap_bea
 }
 
 template <int G>
-static cudaError_t commit_column_launch(const DevCSR& D, const CommitArgs& ca, size_t sm, int grid,
-                                        cudaStream_t stream) {
-    cudaError_t e;
+static void commit_column_launch(const DevCSR& D, const CommitArgs& ca, size_t sm, int grid, cudaStream_t stream) {
     if (D.prec == DAO_PREC_FP16)
-        e = launch_pdl(k_commit_column<G, DAO_PREC_FP16>, dim3(grid), dim3(256), sm, stream, (const int*)nullptr,
-                       (const float*)nullptr, (const unsigned short*)D.col16, (const unsigned short*)D.val16,
-                       (const float*)D.scale, D.n_rows, ca);
+        k_commit_column<G, DAO_PREC_FP16><<<grid, 256, sm, stream>>>(nullptr, nullptr, D.col16, D.val16, D.scale,
+                                                                      D.n_rows, ca);
     else if (D.prec == DAO_PREC_BF16)
-        e = launch_pdl(k_commit_column<G, DAO_PREC_BF16>, dim3(grid), dim3(256), sm, stream, (const int*)nullptr,
-                       (const float*)nullptr, (const unsigned short*)D.col16, (const unsigned short*)D.val16,
-                       (const float*)D.scale, D.n_rows, ca);
+        k_commit_column<G, DAO_PREC_BF16><<<grid, 256, sm, stream>>>(nullptr, nullptr, D.col16, D.val16, D.scale,
+                                                                      D.n_rows, ca);
     else
-        e = launch_pdl(k_commit_column<G, DAO_PREC_FP32>, dim3(grid), dim3(256), sm, stream, (const int*)D.col,
-                       (const float*)D.val, (const unsigned short*)nullptr, (const unsigned short*)nullptr,
-                       (const float*)D.scale, D.n_rows, ca);
-    if (e != cudaSuccess) cudaGetLastError();
-    return e;
+        k_commit_column<G, DAO_PREC_FP32><<<grid, 256, sm, stream>>>(D.col, D.val, nullptr, nullptr, D.scale,
+                                                                      D.n_rows, ca);
 }
 
 cudaError_t launch_commit_column(const DevCSR& D, const CommitArgs& ca, int max_nb, int num_sms, cudaStream_t stream,
@@ -1261,16 +1233,15 @@ cudaError_t launch_commit_column(const DevCSR& D, const CommitArgs& ca, int max_
     if (D.n_rows == 0 || ca.cg == nullptr) return cudaErrorInvalidValue;
     const int grid = num_sms * 8;
     const size_t sm = (size_t)std::max(ca.n_beams, 1) * sizeof(double) + (size_t)std::max(max_nb, 1) * sizeof(float);
-    cudaError_t e;
     switch (D.tune_col_g) {
-        case 1: e = commit_column_launch<1>(D, ca, sm, grid, stream); break;
-        case 2: e = commit_column_launch<2>(D, ca, sm, grid, stream); break;
-        case 4: e = commit_column_launch<4>(D, ca, sm, grid, stream); break;
-        case 16: e = commit_column_launch<16>(D, ca, sm, grid, stream); break;
-        default: e = commit_column_launch<8>(D, ca, sm, grid, stream); break;
+        case 1: commit_column_launch<1>(D, ca, sm, grid, stream); break;
+        case 2: commit_column_launch<2>(D, ca, sm, grid, stream); break;
+        case 4: commit_column_launch<4>(D, ca, sm, grid, stream); break;
+        case 16: commit_column_launch<16>(D, ca, sm, grid, stream); break;
+        default: commit_column_launch<8>(D, ca, sm, grid, stream); break;
     }
     ++*launches;
-    return e;
+    return cudaGetLastError();
 }
 
 namespace {

@@ -49,7 +49,7 @@ def test_options_default_on_host(lib):
     o = binding.options()
     assert o.k_max == 64 and o.max_master_iters == 50 and o.precision == 0
     assert o.master_tol == 1e-6
-    assert o.dt_map == 0 and o.dose_form == 0 and o.pdl == 1
+    assert o.dt_map == 0 and o.dose_form == 0
     assert binding.options(dt_map="grouped", dose_form="units").dt_map == binding.DAO_DT_GROUPED
     assert binding.options(dose_form="lanes").dose_form == binding.DAO_DOSE_LANES
 
@@ -118,7 +118,7 @@ def test_create_rejects_wide_rows_and_pool_sizes(lib):
 @pytest.mark.parametrize("opt,needle", [({"dt_map": 4}, "dt_map"), ({"dt_map": -1}, "dt_map"),
                                         ({"dose_form": 4}, "dose_form"), ({"dt_threads": 96}, "dt_threads"),
                                         ({"column_lanes": 3}, "column_lanes"), ({"column_lanes": 32}, "column_lanes"),
-                                        ({"split_warps": -1}, "split_warps"), ({"pdl": 2}, "pdl")])
+                                        ({"split_warps": -1}, "split_warps")])
 def test_create_rejects_unknown_kernel_forms(lib, opt, needle):
     st, msg = _create(lib, _tiny_inputs(), **opt)
     assert st == -1 and needle in msg, (st, msg)

@@ -299,26 +299,6 @@ def test_graph_rounds_equal_host_driven_rounds(torch, name, K, prec, persistent)
     assert np.array_equal(a[7], b[7]) and np.array_equal(a[8], b[8])
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_programmatic_launch_changes_nothing(torch, prec):
-    """The device-driven solve graph with programmatic dependent launch between
-    a round's kernels (dao_options.pdl, the default) and without it: bitwise
-    the same plan."""
-    case = P.make_case(P.spec_tiny())
-    out = []
-    for pdl in (1, 0):
-        with _plan(case, torch, pdl=pdl, precision=prec) as plan:
-            st, n, trace = plan.solve(20)
-            aps = plan.apertures()
-            y = plan.intensities()
-            z, F = plan.dose()
-            out.append((st, n, trace, aps, y, z, F))
-    a, b = out
-    assert a[0] == b[0] and a[1] == b[1] == 20 and a[6] == b[6]
-    assert np.array_equal(a[2], b[2]) and np.array_equal(a[4], b[4]) and np.array_equal(a[5], b[5])
-    assert all(x[0] == y_[0] and np.array_equal(x[1], y_[1]) for x, y_ in zip(a[3], b[3]))
-
-
 def test_graph_solve_in_chunks_and_after_host_rounds(torch):
     """Rounds split across calls, and graph rounds after host-driven ones, continue
     the same column generation."""
