@@ -140,6 +140,7 @@ def test_gpu_arm_runs_on_stand_ins_and_prints_the_contract_line(monkeypatch, cap
     assert d["config"]["storage"] == "fp32"
     r = d["roofline"]
     assert r["kernel"] == "k_master_persist" and r["unit"] == "GB/s" and 0 < r["frac"] < 10
+    assert r["l2"]["us_per_evaluation"] > 0 and r["l2"]["slab_gbs"] > 0
     assert set(d["spmv"]) == {"fp32", "fp16"} and d["spmv"]["fp32"]["dose"]["us"] == 22.5
     assert d["spmv"]["fp32"]["form"]["dose"] == "units" and d["spmv"]["fp32"]["form"]["dt_map"] == "consecutive"
     st = d["spmv_strip_profile"]
