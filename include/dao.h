@@ -147,8 +147,10 @@ typedef struct dao_options {
                                 * the row ends split evenly over a fixed set of warps, entries requested
                                 * before any row offset; a row across two warps' stretches is finished by
                                 * the later of the two) */
-    int32_t column_lanes;      /* lanes per voxel row of the aperture column (a4): 0 (default: 8, or the
-                                * autotuner's choice), 1, 2, 4, 8 or 16 */
+    int32_t column_lanes;      /* the aperture column (a4): 0 (default, or the autotuner's choice): one lane per
+                                * voxel row over a copy of D stored by beams (each beam's part of every row in
+                                * one contiguous range); 1, 2, 4, 8 or 16: lanes per voxel row over the row's
+                                * segment of the beam in D */
     int32_t split_warps;       /* warps of the forms that split D's or D^T's stored entries evenly over warps
                                 * (DAO_DOSE_MERGE, DAO_DT_SPLIT): 0 (default: 32 per SM) or any positive count
                                 * (fewer warps take longer chunks; the dose form's chunk stays longer than
@@ -464,7 +466,7 @@ int32_t dao_batch_group_size(int32_t n, int32_t device);
  * 16-bit storage up to 16, and the unit form), the transposed SpMV (a2, threads
  * per beamlet row: 64/128/256, each with both lane mappings, and the split
  * form) and the
- * aperture column (a4, lanes per voxel row: 1/2/4/8/16) on the context's own
+ * aperture column (a4: D by beams, or 1/2/4/8/16 lanes per voxel row over D) on the context's own
  * matrices (10 launches per candidate, each after a read of a buffer twice the
  * L2 size, so that it runs on a cold cache as in a plan; median of the
  * per-launch event times) and keeps the fastest of each for this context.
@@ -477,7 +479,7 @@ int32_t dao_batch_group_size(int32_t n, int32_t device);
  * are unchanged up to the FP32 summation order of the SpMVs. */
 typedef struct {
     int32_t dose_lanes;    /* a1 lanes per voxel row (lane form) */
-    int32_t column_lanes;  /* a4 lanes per voxel row */
+    int32_t column_lanes;  /* a4: 0 D by beams, else lanes per voxel row over D */
     int32_t dt_threads;    /* a2 threads per beamlet row */
     int32_t from_cache;    /* 1 when read from cache_path, 0 when timed */
     int32_t dose_form;     /* a1 form: DAO_DOSE_LANES, DAO_DOSE_UNITS or DAO_DOSE_MERGE */

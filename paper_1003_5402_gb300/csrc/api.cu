@@ -263,7 +263,7 @@ dao_status validate(const dao_csr* D, const dao_geometry* g, const dao_structure
     if (opt->dose_form < 0 || opt->dose_form > DOSE_FORM_MERGE)
         return fail(DAO_EINVAL, "dose_form must be 0, DAO_DOSE_LANES, DAO_DOSE_UNITS or DAO_DOSE_MERGE");
     if (opt->column_lanes != 0 && opt->column_lanes != 1 && opt->column_lanes != 2 && opt->column_lanes != 4 &&
-        opt->column_lanes != 8 && opt->column_lanes != 16)
+        opt->column_lanes != 8 && opt->column_lanes != 16)  // 0: D by beams, one lane per voxel row
         return fail(DAO_EINVAL, "column_lanes must be 0, 1, 2, 4, 8 or 16");
     if (opt->split_warps < 0) return fail(DAO_EINVAL, "split_warps must be >= 0");
     if (opt->mlc_constraint < DAO_MLC_CONSECUTIVE || opt->mlc_constraint > DAO_MLC_JAWS)
@@ -441,6 +441,16 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
                            c->num_sms, st), "transpose counts and scales"));
     DAO_TRY(cu(build_fill_d(prec, t_rp, t_col, t_val, c->D.rowptr, V, scale, c->D, st), "padded D"));
     DAO_TRY(cu(build_seg(t_rp, t_col, c->D.rowptr, V, c->beam_off_d, B, c->seg, st), "beam segments"));
+    // D by beams for the aperture column (a4): each beam's part of every row
+    // in one contiguous range
+    DAO_TRY(c->dalloc(&c->D.beam_rowptr, (size_t)B * (V + 1)));
+    DAO_TRY(c->dalloc(&c->D.beam_col, (size_t)nnz));
+    if (prec == DAO_PREC_FP32)
+        DAO_TRY(c->dalloc(&c->D.beam_val32, (size_t)nnz));
+    else
+        DAO_TRY(c->dalloc(&c->D.beam_val16, (size_t)nnz));
+    DAO_TRY(cu(build_beam_rows(c->seg, V, B, c->D.beam_rowptr, st), "beam rows"));
+    DAO_TRY(cu(build_beam_fill(prec, c->seg, V, B, c->beam_off_d, c->D, st), "beam layout"));
     DAO_TRY(cu(build_unit_max(c->D.rowptr, V, pad_m, t_umax, st), "row units"));
     // counts, the largest |D_ij| and the largest row unit back to the host: row
     // offsets of D^T, tau, the dose SpMV's shared partials
@@ -842,8 +852,8 @@ dao_status add_column(dao_ctx* c, int beam, const int32_t* lr, float* out, int s
         for (int q = lr[2 * r]; q < lr[2 * r + 1]; ++q) m[r * c->cols[beam] + q] = 1.f;
     DAO_CU(cudaMemcpyAsync(c->mask, m, sizeof(float) * nb, cudaMemcpyHostToDevice, c->stream));
     c->prof_begin(DAO_KC_COLUMN);
-    DAO_CU(launch_column(c->D, c->seg + (size_t)beam * c->V, c->seg + (size_t)(beam + 1) * c->V, c->beam_off[beam],
-                         nb, c->mask, out, stride, c->num_sms, c->stream, &c->launches_i));
+    DAO_CU(launch_column(c->D, c->seg, beam, c->beam_off[beam], nb, c->mask, out, stride, c->num_sms, c->stream,
+                         &c->launches_i));
     c->prof_end();
     return DAO_OK;
 }
@@ -1835,8 +1845,8 @@ cudaError_t time_one(dao_ctx* c, int kc, int K, cudaStream_t s, int* n) {
                                c->num_sms, s, n);
         case DAO_KC_COLUMN: {
             const int b = c->ap_beam_h[0];
-            return launch_column(c->D, c->seg + (size_t)b * c->V, c->seg + (size_t)(b + 1) * c->V, c->beam_off[b],
-                                 c->rows[b] * c->cols[b], c->mask, c->dose, 1, c->num_sms, s, n);
+            return launch_column(c->D, c->seg, b, c->beam_off[b], c->rows[b] * c->cols[b], c->mask, c->dose, 1,
+                                 c->num_sms, s, n);
         }
         case DAO_KC_PRICE:
             return price_any(c, c->w, nullptr, s, n);
@@ -2376,7 +2386,7 @@ dao_status dao_kernel_forms(const dao_ctx* c, dao_tuning* out) {
     const bool split = Dt.tune_dt_map == DT_MAP_SPLIT && Dt.split_chunk > 0;
     out->dose_form = dose_form_effective(D);
     out->dose_lanes = D.tune_dose_g;
-    out->column_lanes = D.tune_col_g ? D.tune_col_g : 8;
+    out->column_lanes = D.tune_col_g;  // 0: the beam layout
     out->dt_map = split ? DT_MAP_SPLIT : Dt.tune_dt_map == DT_MAP_GROUPED ? DT_MAP_GROUPED : DT_MAP_CONSECUTIVE;
     out->dt_threads = split ? 0 : (Dt.tune_dt_threads ? Dt.tune_dt_threads : 64);
     out->from_cache = 0;
@@ -2455,12 +2465,12 @@ dao_status dao_autotune(dao_ctx* c, const char* cache_path, dao_tuning* out) {
                 }
             }
         best = 1e300;
-        for (int g : TUNE_COL_G) {  // a4: lanes per voxel row over beam 0's segment
+        for (int g : TUNE_COL_G) {  // a4: the beam layout (0), or lanes per voxel row over beam 0's segment
             c->D.tune_col_g = g;
             double us = 0.0;
             DAO_TRY(time_cold(c, reps, [&](int* nl) {
-                return launch_column(c->D, c->seg, c->seg + (size_t)c->V, c->beam_off[0], c->rows[0] * c->cols[0],
-                                     c->mask, c->dose, 1, c->num_sms, c->stream, nl);
+                return launch_column(c->D, c->seg, 0, c->beam_off[0], c->rows[0] * c->cols[0], c->mask, c->dose, 1,
+                                     c->num_sms, c->stream, nl);
             }, &us, "dao_autotune"));
             if (us < best) {
                 best = us;

@@ -465,6 +465,87 @@ __global__ void k_merge_path(const int* __restrict__ prow, int V, int epg, int c
 }
 }  // namespace
 
+namespace {
+constexpr int BEAM_SCAN_T = 1024;
+// One block per beam: the lengths of the beam's row segments, scanned into
+// the beam's row offsets, counted from the beam's first entry (each thread a
+// contiguous run of rows, then a block scan of the runs' sums); beam b's
+// entries follow those of beams 0 .. b - 1 (the totals brp[b'][V]).
+__global__ void __launch_bounds__(BEAM_SCAN_T) k_beam_scan(const int* __restrict__ seg, int V,
+                                                          int* __restrict__ brp) {
+    __shared__ int s_sum[BEAM_SCAN_T];
+    const int b = blockIdx.x, t = threadIdx.x;
+    const int* lo = seg + (size_t)b * V;
+    const int* hi = seg + (size_t)(b + 1) * V;
+    const int per = (V + BEAM_SCAN_T - 1) / BEAM_SCAN_T;
+    const int j0 = min(t * per, V), j1 = min(j0 + per, V);
+    int run = 0;
+    for (int j = j0; j < j1; ++j) run += hi[j] - lo[j];
+    s_sum[t] = run;
+    __syncthreads();
+    for (int o = 1; o < BEAM_SCAN_T; o <<= 1) {  // inclusive scan of the runs
+        const int add = t >= o ? s_sum[t - o] : 0;
+        __syncthreads();
+        s_sum[t] += add;
+        __syncthreads();
+    }
+    int off = s_sum[t] - run;
+    int* out = brp + (size_t)b * (V + 1);
+    for (int j = j0; j < j1; ++j) {
+        out[j] = off;
+        off += hi[j] - lo[j];
+    }
+    if (t == BEAM_SCAN_T - 1) out[V] = s_sum[t];
+}
+
+// One thread per (beam, row): the row's segment of the beam, with the beamlet
+// index made local to the beam.
+template <int PREC>
+__global__ void k_beam_fill(const int* __restrict__ seg, int V, int B, const int* __restrict__ beam_off,
+                            const int* __restrict__ brp, const int* __restrict__ col, const float* __restrict__ val,
+                            const unsigned short* __restrict__ col16, const unsigned short* __restrict__ val16,
+                            unsigned short* __restrict__ bcol, float* __restrict__ bval32,
+                            unsigned short* __restrict__ bval16) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)B * V) return;
+    const int b = (int)(i / V), j = (int)(i % V);
+    const int q0 = seg[(size_t)b * V + j], q1 = seg[(size_t)(b + 1) * V + j];
+    const int base = beam_off[b];
+    int64_t d0 = brp[(size_t)b * (V + 1) + j];
+    for (int bb = 0; bb < b; ++bb) d0 += brp[(size_t)bb * (V + 1) + V];  // the beams before b
+    for (int q = q0; q < q1; ++q) {
+        const int64_t d = d0 + (q - q0);
+        if constexpr (PREC == DAO_PREC_FP32) {
+            bcol[d] = (unsigned short)(col[q] - base);
+            bval32[d] = val[q];
+        } else {
+            bcol[d] = (unsigned short)(col16[q] - base);
+            bval16[d] = val16[q];
+        }
+    }
+}
+}  // namespace
+
+cudaError_t build_beam_rows(const int* seg, int V, int B, int* brp, cudaStream_t s) {
+    if (B < 1 || V < 1) return cudaSuccess;
+    k_beam_scan<<<B, BEAM_SCAN_T, 0, s>>>(seg, V, brp);
+    return cudaGetLastError();
+}
+
+cudaError_t build_beam_fill(int prec, const int* seg, int V, int B, const int* beam_off, const DevCSR& D,
+                            cudaStream_t s) {
+    const int64_t n = (int64_t)B * V;
+    if (n == 0) return cudaSuccess;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    if (prec == DAO_PREC_FP32)
+        k_beam_fill<DAO_PREC_FP32><<<g, 256, 0, s>>>(seg, V, B, beam_off, D.beam_rowptr, D.col, D.val, nullptr,
+                                                     nullptr, D.beam_col, D.beam_val32, nullptr);
+    else
+        k_beam_fill<DAO_PREC_FP16><<<g, 256, 0, s>>>(seg, V, B, beam_off, D.beam_rowptr, nullptr, nullptr, D.col16,
+                                                     D.val16, D.beam_col, nullptr, D.beam_val16);
+    return cudaGetLastError();
+}
+
 cudaError_t build_merge_path(const int* prow, int V, int epg, int chunk, int n_warps, int2* out, cudaStream_t s) {
     k_merge_path<<<(n_warps + 1 + 255) / 256, 256, 0, s>>>(prow, V, epg, chunk, n_warps, out);
     return cudaGetLastError();

@@ -81,6 +81,14 @@ struct DevCSR {
     // the row holding its first entry; a row covered by several warps adds their
     // partial sums (split_part, split_ps slots per row) in warp order, on a
     // per-row ticket (split_cnt, zero between launches)
+    // D by beams (the aperture column's layout): beam b's part of row j is
+    // entries [beam_rowptr[b (V + 1) + j], beam_rowptr[b (V + 1) + j + 1]) of
+    // beam_col (beamlet index within the beam) and beam_val32 (FP32) or
+    // beam_val16 (16-bit values, as in D); nullptr: not built
+    int* beam_rowptr = nullptr;
+    unsigned short* beam_col = nullptr;
+    float* beam_val32 = nullptr;
+    unsigned short* beam_val16 = nullptr;
     // D split over warps along the merge path of its groups and row ends
     // (DOSE_FORM_MERGE): warp v takes the stretch between merge_path[v] and
     // merge_path[v + 1] (rows finished, groups consumed), merge_chunk items,
@@ -115,7 +123,7 @@ constexpr int SPLIT_WARPS_PER_SM = 32;
 
 // Launch shapes the autotuner may choose from.
 constexpr int TUNE_DOSE_G[] = {4, 8, 16, 32};
-constexpr int TUNE_COL_G[] = {1, 2, 4, 8, 16};
+constexpr int TUNE_COL_G[] = {0, 1, 2, 4, 8, 16};  // 0: D by beams, one lane per voxel row
 constexpr int TUNE_DT_THREADS[] = {64, 128, 256};
 
 // Projected-Newton master state (device memory, one per context).
@@ -194,10 +202,10 @@ cudaError_t spmv_configure();
 cudaError_t launch_dt(const DevCSR& Dt, const float* pi, float* w, const int* skip, cudaStream_t stream,
                       int* launches);
 
-// a4: out[j * stride] = sum over beam b's entries of row j with mask[col - base] (0/1).
-cudaError_t launch_column(const DevCSR& D, const int* seg_lo, const int* seg_hi, int base,
-                          int n_beamlets_b, const float* mask, float* out, int stride, int num_sms,
-                          cudaStream_t stream, int* launches);
+// a4: out[j * stride] = sum over beam b's entries of row j with mask[col - base] (0/1);
+// seg: the (B + 1) x V beam segments of D's rows.
+cudaError_t launch_column(const DevCSR& D, const int* seg, int b, int base, int n_beamlets_b, const float* mask,
+                          float* out, int stride, int num_sms, cudaStream_t stream, int* launches);
 
 // a4 for the aperture the device just committed at pool index K-1 (graph
 // path), written to column K-1 of the slab (column stride ld).
@@ -431,6 +439,11 @@ cudaError_t build_seg(const int64_t* rp, const int* col, const int* prow, int V,
 // padded D (row offsets prow) into out[0], the most in one row into out[1]
 // (both zeroed by the call).
 cudaError_t build_unit_max(const int* prow, int V, int epg, int* out, cudaStream_t s);
+// D by beams: the row offsets of every beam's part (B x (V + 1), from the beam
+// segments seg), then the entries (beamlet index within the beam, value).
+cudaError_t build_beam_rows(const int* seg, int V, int B, int* brp, cudaStream_t s);
+cudaError_t build_beam_fill(int prec, const int* seg, int V, int B, const int* beam_off, const DevCSR& D,
+                            cudaStream_t s);
 // Merge-path splits of the merge form: out[v] = (rows done, groups consumed)
 // at diagonal min(v * chunk, V + groups), rows finished as soon as their groups
 // are (prow in entries, epg entries per group), v = 0 .. n_warps.

@@ -280,7 +280,8 @@ int64_t dao_server_footprint(const dao_request* req, const dao_options* plan_opt
     const int64_t CH = std::max<int64_t>(256, (V * N / (16 << 20) + 31) / 32 * 32);
     const int64_t build = (V + 1) * 8 + nnz * 8 + V * 12 + ((V + CH - 1) / CH) * N * 4 + N * 8 +
                           (wide ? 0 : (nnz + N * (pad - 1)) * 4);
-    return d_bytes + t_bytes + (B + 1) * V * 4 + V + master + N * 64 + build + ((int64_t)40 << 20);
+    const int64_t by_beams = B * (V + 1) * 4 + nnz * (wide ? 6 : 4);  // D by beams for the aperture column
+    return d_bytes + t_bytes + (B + 1) * V * 4 + by_beams + V + master + N * 64 + build + ((int64_t)40 << 20);
 }
 
 dao_status dao_server_create(const dao_server_options* opt_in, dao_server** out) {

@@ -368,6 +368,32 @@ __global__ void __launch_bounds__(256) k_column_dev(const int* __restrict__ col,
                    slab + (size_t)(K - 1) * ld, 1, (int)(blockIdx.x * blockDim.x), (int)(gridDim.x * blockDim.x));
 }
 
+// a4 from D by beams, for beam b (b_dev: the beam read from the device's
+// aperture table, the graph path's k_column_dev).
+template <bool W16, bool BF>
+__global__ void __launch_bounds__(256) k_column_beam(const int* __restrict__ brp_all,
+                                                     const unsigned short* __restrict__ bcol,
+                                                     const float* __restrict__ bval32,
+                                                     const unsigned short* __restrict__ bval16, int V, int b, int nb,
+                                                     int base, const int* __restrict__ ap_beam, int K,
+                                                     const int* __restrict__ beam_off, const int* __restrict__ rows,
+                                                     const int* __restrict__ cols, const float* __restrict__ mask,
+                                                     const float* __restrict__ scale, float* __restrict__ out,
+                                                     int stride, int ld, const CGDev* __restrict__ cg) {
+    extern __shared__ float smask[];
+    if (cg != nullptr) {  // the device-table form: aperture K - 1 into column K - 1 of the slab
+        if (cg->idle) return;
+        b = ap_beam[K - 1];
+        nb = rows[b] * cols[b];
+        base = beam_off[b];
+        out += (size_t)(K - 1) * ld;
+    }
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) smask[i] = W16 ? mask[i] * scale[base + i] : mask[i];
+    __syncthreads();
+    column_beam_body<W16, BF>(brp_all + (size_t)b * (V + 1), beam_entry_base(brp_all, V, b), bcol, bval32, bval16, V,
+                              smask, out, stride, (int)(blockIdx.x * blockDim.x), (int)(gridDim.x * blockDim.x));
+}
+
 // ---- Eq. 7 ------------------------------------------------------------------
 __global__ void k_fluence(const int* __restrict__ ap_beam, const int* __restrict__ ap_lr, int lr_stride,
                           const double* __restrict__ y, int K, const int4* __restrict__ binfo, int N,
@@ -802,7 +828,11 @@ template <int G, int PREC>
 __global__ void __launch_bounds__(256) k_commit_column(const int* __restrict__ col, const float* __restrict__ val,
                                                        const unsigned short* __restrict__ col16,
                                                        const unsigned short* __restrict__ val16,
-                                                       const float* __restrict__ scale, int V, CommitArgs ca) {
+                                                       const float* __restrict__ scale, int V, CommitArgs ca,
+                                                       const int* __restrict__ brp_all,
+                                                       const unsigned short* __restrict__ bcol,
+                                                       const float* __restrict__ bval32,
+                                                       const unsigned short* __restrict__ bval16) {
     extern __shared__ double s_dyn[];
     double* s_sum = s_dyn;                                        // n_beams
     float* smask = reinterpret_cast<float*>(s_dyn + ca.n_beams);  // max_nb
@@ -854,7 +884,11 @@ __global__ void __launch_bounds__(256) k_commit_column(const int* __restrict__ c
     float* out = ca.slab + (size_t)(K - 1) * ca.ld;
     const int* seg_lo = ca.seg + (size_t)b * V;
     const int* seg_hi = ca.seg + (size_t)(b + 1) * V;
-    if constexpr (PREC == DAO_PREC_FP32)
+    if constexpr (G == 0)  // D by beams
+        column_beam_body<PREC != DAO_PREC_FP32, PREC == DAO_PREC_BF16>(
+            brp_all + (size_t)b * (V + 1), beam_entry_base(brp_all, V, b), bcol, bval32, bval16, V, smask, out, 1,
+            (int)(blockIdx.x * blockDim.x), (int)(gridDim.x * blockDim.x));
+    else if constexpr (PREC == DAO_PREC_FP32)
         column_body<G>(col, val, seg_lo, seg_hi, V, base, smask, out, 1, (int)(blockIdx.x * blockDim.x), (int)(gridDim.x * blockDim.x));
     else
         column16_body<G, PREC == DAO_PREC_BF16>(col16, val16, seg_lo, seg_hi, V, base, smask, out, 1, (int)(blockIdx.x * blockDim.x), (int)(gridDim.x * blockDim.x));
@@ -1174,10 +1208,44 @@ cudaError_t launch_dt_rows(const DevCSR& Dt, const float* pi, float* w, const Ro
     return dt_dispatch(Dt, pi, w, &rt.cg->stop, rt, stream, launches);
 }
 
-cudaError_t launch_column(const DevCSR& D, const int* seg_lo, const int* seg_hi, int base, int nb,
-                          const float* mask, float* out, int stride, int num_sms, cudaStream_t stream, int* launches) {
+// The aperture column runs on D by beams when the launch shape is 0 (the
+// default) and the layout was built.
+static bool column_by_beams(const DevCSR& D) { return D.tune_col_g == 0 && D.beam_rowptr != nullptr; }
+
+// b, nb, base: the beam, its beamlets and its first beamlet (cg == nullptr);
+// else the beam of aperture K - 1 of the device table, into column K - 1 of
+// the slab (stride ld).
+static void column_beam_launch(const DevCSR& D, int b, int nb, int base, const int* ap_beam, int K,
+                               const int* beam_off, const int* rows, const int* cols, int max_nb, const float* mask,
+                               float* out, int stride, int ld, const CGDev* cg, int grid, cudaStream_t stream) {
+    const size_t sm = (size_t)std::max(max_nb, 1) * sizeof(float);
+    if (D.prec == DAO_PREC_FP16)
+        k_column_beam<true, false><<<grid, 256, sm, stream>>>(D.beam_rowptr, D.beam_col, nullptr, D.beam_val16,
+                                                               D.n_rows, b, nb, base, ap_beam, K, beam_off, rows,
+                                                               cols, mask, D.scale, out, stride, ld, cg);
+    else if (D.prec == DAO_PREC_BF16)
+        k_column_beam<true, true><<<grid, 256, sm, stream>>>(D.beam_rowptr, D.beam_col, nullptr, D.beam_val16,
+                                                              D.n_rows, b, nb, base, ap_beam, K, beam_off, rows,
+                                                              cols, mask, D.scale, out, stride, ld, cg);
+    else
+        k_column_beam<false, false><<<grid, 256, sm, stream>>>(D.beam_rowptr, D.beam_col, D.beam_val32, nullptr,
+                                                                D.n_rows, b, nb, base, ap_beam, K, beam_off, rows,
+                                                                cols, mask, D.scale, out, stride, ld, cg);
+}
+
+cudaError_t launch_column(const DevCSR& D, const int* seg, int b, int base, int nb, const float* mask, float* out,
+                          int stride, int num_sms, cudaStream_t stream, int* launches) {
     if (D.n_rows == 0) return cudaSuccess;
     const int grid = num_sms * 8;
+    const int V = D.n_rows;
+    const int* seg_lo = seg + (size_t)b * V;
+    const int* seg_hi = seg + (size_t)(b + 1) * V;
+    if (column_by_beams(D)) {
+        column_beam_launch(D, b, nb, base, nullptr, 0, nullptr, nullptr, nullptr, nb, mask, out, stride, 0, nullptr,
+                           grid, stream);
+        ++*launches;
+        return cudaGetLastError();
+    }
     switch (D.tune_col_g) {
         case 1: column_launch<1>(D, seg_lo, seg_hi, base, nb, mask, out, stride, grid, stream); break;
         case 2: column_launch<2>(D, seg_lo, seg_hi, base, nb, mask, out, stride, grid, stream); break;
@@ -1194,6 +1262,12 @@ cudaError_t launch_column_dev(const DevCSR& D, const int* seg, const int* ap_bea
                               const CGDev* cg, int num_sms, cudaStream_t stream, int* launches) {
     if (D.n_rows == 0) return cudaSuccess;
     const int grid = num_sms * 8;
+    if (column_by_beams(D)) {
+        column_beam_launch(D, 0, 0, 0, ap_beam, K, beam_off, rows, cols, max_nb, mask, slab, 1, ld, cg, grid,
+                           stream);
+        ++*launches;
+        return cudaGetLastError();
+    }
     switch (D.tune_col_g) {
         case 1:
             column_dev_launch<1>(D, seg, ap_beam, K, beam_off, rows, cols, max_nb, mask, slab, ld, cg, grid, stream);
@@ -1219,13 +1293,16 @@ template <int G>
 static void commit_column_launch(const DevCSR& D, const CommitArgs& ca, size_t sm, int grid, cudaStream_t stream) {
     if (D.prec == DAO_PREC_FP16)
         k_commit_column<G, DAO_PREC_FP16><<<grid, 256, sm, stream>>>(nullptr, nullptr, D.col16, D.val16, D.scale,
-                                                                      D.n_rows, ca);
+                                                                      D.n_rows, ca, D.beam_rowptr, D.beam_col,
+                                                                      nullptr, D.beam_val16);
     else if (D.prec == DAO_PREC_BF16)
         k_commit_column<G, DAO_PREC_BF16><<<grid, 256, sm, stream>>>(nullptr, nullptr, D.col16, D.val16, D.scale,
-                                                                      D.n_rows, ca);
+                                                                      D.n_rows, ca, D.beam_rowptr, D.beam_col,
+                                                                      nullptr, D.beam_val16);
     else
         k_commit_column<G, DAO_PREC_FP32><<<grid, 256, sm, stream>>>(D.col, D.val, nullptr, nullptr, D.scale,
-                                                                      D.n_rows, ca);
+                                                                      D.n_rows, ca, D.beam_rowptr, D.beam_col,
+                                                                      D.beam_val32, nullptr);
 }
 
 cudaError_t launch_commit_column(const DevCSR& D, const CommitArgs& ca, int max_nb, int num_sms, cudaStream_t stream,
@@ -1233,6 +1310,11 @@ cudaError_t launch_commit_column(const DevCSR& D, const CommitArgs& ca, int max_
     if (D.n_rows == 0 || ca.cg == nullptr) return cudaErrorInvalidValue;
     const int grid = num_sms * 8;
     const size_t sm = (size_t)std::max(ca.n_beams, 1) * sizeof(double) + (size_t)std::max(max_nb, 1) * sizeof(float);
+    if (column_by_beams(D)) {
+        commit_column_launch<0>(D, ca, sm, grid, stream);
+        ++*launches;
+        return cudaGetLastError();
+    }
     switch (D.tune_col_g) {
         case 1: commit_column_launch<1>(D, ca, sm, grid, stream); break;
         case 2: commit_column_launch<2>(D, ca, sm, grid, stream); break;

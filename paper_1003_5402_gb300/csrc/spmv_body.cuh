@@ -185,6 +185,48 @@ __device__ __forceinline__ float dt16_row_sum_lc(const int* __restrict__ rowptr,
 }
 
 // ---- a4 ---------------------------------------------------------------------
+// The first entry of beam b in D by beams: the totals of the beams before it.
+__device__ __forceinline__ int beam_entry_base(const int* __restrict__ brp_all, int V, int b) {
+    int e = 0;
+    for (int bb = 0; bb < b; ++bb) e += __ldg(brp_all + (size_t)bb * (V + 1) + V);
+    return e;
+}
+
+// a4 from D by beams: one lane per voxel row over the row's part of beam b
+// (entries e_base + brp[j] .. e_base + brp[j + 1] - 1, one contiguous range, so the lanes of a
+// warp read consecutive bytes), summed in order from 0 as the one-lane form
+// over D's segments sums them; the mask is pre-multiplied by the scales for
+// 16-bit values.  Four entries requested ahead of their products.
+template <bool W16, bool BF>
+__device__ __forceinline__ void column_beam_body(const int* __restrict__ brp, int e_base,
+                                                 const unsigned short* __restrict__ bcol,
+                                                 const float* __restrict__ bval32,
+                                                 const unsigned short* __restrict__ bval16, int V,
+                                                 const float* smask, float* __restrict__ out, int stride, int wbase,
+                                                 int wcount) {
+    for (int j = wbase + (int)threadIdx.x; j < V; j += wcount) {
+        const int p0 = __ldg(brp + j) + e_base, p1 = __ldg(brp + j + 1) + e_base;
+        float acc = 0.f;
+        for (int p = p0; p < p1; p += 4) {
+            unsigned short c[4];
+            float v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool in = p + q < p1;
+                c[q] = in ? __ldg(bcol + p + q) : (unsigned short)0;
+                if constexpr (W16)
+                    v[q] = in ? unpack1<BF>(__ldg(bval16 + p + q)) : 0.f;
+                else
+                    v[q] = in ? __ldg(bval32 + p + q) : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (p + q < p1) acc = fmaf(v[q], smask[c[q]], acc);
+        }
+        out[(size_t)j * stride] = acc;
+    }
+}
+
 // The caller's threads are [wbase, wbase + blockDim) of wcount threads sharing
 // the rows (a grid, or a group of blocks).
 // G lanes per voxel row over the row's segment of beam b (columns base ..

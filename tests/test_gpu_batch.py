@@ -120,7 +120,7 @@ def test_autotune_choice_cache_and_parity(torch, tmp_path, prec):
         t1 = p.autotune(cache)
         assert not t1["from_cache"]
         assert t1["dose_lanes"] in ((4, 8, 16, 32) if prec == 0 else (4, 8, 16))
-        assert t1["column_lanes"] in (1, 2, 4, 8, 16) and t1["dt_threads"] in (64, 128, 256)
+        assert t1["column_lanes"] in (0, 1, 2, 4, 8, 16) and t1["dt_threads"] in (64, 128, 256)
         assert t1["dose_form"] in ("lanes", "units") and t1["dt_map"] in ("grouped", "consecutive")
         x = np.random.default_rng(1).uniform(0.0, 2.0, size=case.n_beamlets).astype(np.float32)
         zd = torch.empty(case.n_voxels, dtype=torch.float32, device="cuda")

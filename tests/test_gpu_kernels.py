@@ -188,12 +188,13 @@ def test_pricing_bit_exact_lockstep(torch, name, case, kind):
 @pytest.mark.parametrize("lanes", [0, 1, 2, 16])
 @pytest.mark.parametrize("name,case", CASES, ids=[c[0] for c in CASES])
 def test_aperture_column(torch, name, case, lanes):
-    """a4 with the default 8 lanes per voxel row and with 1, 2 or 16
-    (dao_options.column_lanes): a lane sums ceil(n / lanes) entries in order,
-    then a shuffle tree of log2(lanes) levels."""
+    """a4 on D by beams (the default, dao_options.column_lanes 0: one lane per
+    voxel row over the row's part of the beam, in order) and over D's row
+    segments with 1, 2 or 16 lanes per row: a lane sums ceil(n / lanes)
+    entries in order, then a shuffle tree of log2(lanes) levels."""
     rng = np.random.default_rng(4)
     D = O.csr64(case)
-    G = lanes or 8
+    G = lanes or 1
     with _plan(case, torch, column_lanes=lanes) as plan:
         out = torch.empty(case.n_voxels, dtype=torch.float32, device="cuda")
         for b in range(case.n_beams):
