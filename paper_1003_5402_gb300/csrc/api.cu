@@ -342,10 +342,11 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
     int* t_cnt = nullptr;
     unsigned* t_dmax = nullptr;
     int* t_umax = nullptr;
+    int* t_bscan = nullptr;
     float* t_tval = nullptr;
     auto free_temps = [&]() {
         for (void* q : {(void*)t_rp, (void*)t_col, (void*)t_val, (void*)t_lab, (void*)t_plen, (void*)t_bsum,
-                        (void*)t_chk, (void*)t_C, (void*)t_cnt, (void*)t_dmax, (void*)t_umax,
+                        (void*)t_chk, (void*)t_C, (void*)t_cnt, (void*)t_dmax, (void*)t_umax, (void*)t_bscan,
                         (void*)(prec == DAO_PREC_FP32 ? nullptr : t_tval)})
             if (q) pool_free(q, st);
     };
@@ -449,7 +450,8 @@ dao_status build(dao_ctx* c, const dao_csr* Din, const dao_geometry* g, const da
         DAO_TRY(c->dalloc(&c->D.beam_val32, (size_t)nnz));
     else
         DAO_TRY(c->dalloc(&c->D.beam_val16, (size_t)nnz));
-    DAO_TRY(cu(build_beam_rows(c->seg, V, B, c->D.beam_rowptr, st), "beam rows"));
+    DAO_TRY(talloc(&t_bscan, sizeof(int) * (size_t)B * beam_scan_tiles(V)));
+    DAO_TRY(cu(build_beam_rows(c->seg, V, B, c->D.beam_rowptr, t_bscan, st), "beam rows"));
     DAO_TRY(cu(build_beam_fill(prec, c->seg, V, B, c->beam_off_d, c->D, st), "beam layout"));
     DAO_TRY(cu(build_unit_max(c->D.rowptr, V, pad_m, t_umax, st), "row units"));
     // counts, the largest |D_ij| and the largest row unit back to the host: row

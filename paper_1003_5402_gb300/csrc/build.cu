@@ -466,36 +466,79 @@ __global__ void k_merge_path(const int* __restrict__ prow, int V, int epg, int c
 }  // namespace
 
 namespace {
-constexpr int BEAM_SCAN_T = 1024;
-// One block per beam: the lengths of the beam's row segments, scanned into
-// the beam's row offsets, counted from the beam's first entry (each thread a
-// contiguous run of rows, then a block scan of the runs' sums); beam b's
-// entries follow those of beams 0 .. b - 1 (the totals brp[b'][V]).
-__global__ void __launch_bounds__(BEAM_SCAN_T) k_beam_scan(const int* __restrict__ seg, int V,
-                                                          int* __restrict__ brp) {
-    __shared__ int s_sum[BEAM_SCAN_T];
-    const int b = blockIdx.x, t = threadIdx.x;
-    const int* lo = seg + (size_t)b * V;
-    const int* hi = seg + (size_t)(b + 1) * V;
-    const int per = (V + BEAM_SCAN_T - 1) / BEAM_SCAN_T;
-    const int j0 = min(t * per, V), j1 = min(j0 + per, V);
-    int run = 0;
-    for (int j = j0; j < j1; ++j) run += hi[j] - lo[j];
-    s_sum[t] = run;
+constexpr int BEAM_TILE = 1024;  // rows per tile of the beams' row-offset scan
+
+// Inclusive sum over the block of one int per thread (BEAM_TILE threads);
+// *total receives the block's sum.
+__device__ __forceinline__ int block_scan_incl(int v, int* s_w, int* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    if (lane == 31) s_w[w] = v;
     __syncthreads();
-    for (int o = 1; o < BEAM_SCAN_T; o <<= 1) {  // inclusive scan of the runs
-        const int add = t >= o ? s_sum[t - o] : 0;
-        __syncthreads();
-        s_sum[t] += add;
-        __syncthreads();
+    if (w == 0) {
+        int x = s_w[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        s_w[lane] = x;  // inclusive sums of the warps' totals
     }
-    int off = s_sum[t] - run;
-    int* out = brp + (size_t)b * (V + 1);
-    for (int j = j0; j < j1; ++j) {
-        out[j] = off;
-        off += hi[j] - lo[j];
+    __syncthreads();
+    const int r = v + (w > 0 ? s_w[w - 1] : 0);
+    *total = s_w[BEAM_TILE / 32 - 1];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ int beam_seg_len(const int* __restrict__ seg, int V, int b, int j) {
+    return j < V ? seg[(size_t)(b + 1) * V + j] - seg[(size_t)b * V + j] : 0;
+}
+
+// Per (tile, beam): the sum of the tile's segment lengths of the beam.
+__global__ void __launch_bounds__(BEAM_TILE) k_beam_tiles(const int* __restrict__ seg, int V, int n_tiles,
+                                                         int* __restrict__ tsum) {
+    __shared__ int s_w[BEAM_TILE / 32];
+    const int b = blockIdx.y, t = blockIdx.x;
+    int total = 0;
+    block_scan_incl(beam_seg_len(seg, V, b, t * BEAM_TILE + (int)threadIdx.x), s_w, &total);
+    if (threadIdx.x == 0) tsum[(size_t)b * n_tiles + t] = total;
+}
+
+// Per beam: the tile sums turned into the tiles' first offsets (in place),
+// the beam's total into brp[b][V].
+__global__ void __launch_bounds__(BEAM_TILE) k_beam_tile_scan(int* __restrict__ tsum, int n_tiles, int V,
+                                                             int* __restrict__ brp) {
+    __shared__ int s_w[BEAM_TILE / 32];
+    const int b = blockIdx.x;
+    int carry = 0;
+    for (int c0 = 0; c0 < n_tiles; c0 += BEAM_TILE) {
+        const int i = c0 + (int)threadIdx.x;
+        const int v = i < n_tiles ? tsum[(size_t)b * n_tiles + i] : 0;
+        int total = 0;
+        const int incl = block_scan_incl(v, s_w, &total);
+        if (i < n_tiles) tsum[(size_t)b * n_tiles + i] = carry + incl - v;
+        carry += total;
     }
-    if (t == BEAM_SCAN_T - 1) out[V] = s_sum[t];
+    if (threadIdx.x == 0) brp[(size_t)b * (V + 1) + V] = carry;
+}
+
+// Per (tile, beam): the row offsets of the tile's rows, counted from the
+// beam's first entry; beam b's entries follow those of beams 0 .. b - 1 (the
+// totals brp[b'][V]).
+__global__ void __launch_bounds__(BEAM_TILE) k_beam_offsets(const int* __restrict__ seg, int V, int n_tiles,
+                                                           const int* __restrict__ toff, int* __restrict__ brp) {
+    __shared__ int s_w[BEAM_TILE / 32];
+    const int b = blockIdx.y, t = blockIdx.x;
+    const int j = t * BEAM_TILE + (int)threadIdx.x;
+    const int len = beam_seg_len(seg, V, b, j);
+    int total = 0;
+    const int incl = block_scan_incl(len, s_w, &total);
+    if (j < V) brp[(size_t)b * (V + 1) + j] = toff[(size_t)b * n_tiles + t] + incl - len;
 }
 
 // One thread per (beam, row): the row's segment of the beam, with the beamlet
@@ -526,9 +569,14 @@ __global__ void k_beam_fill(const int* __restrict__ seg, int V, int B, const int
 }
 }  // namespace
 
-cudaError_t build_beam_rows(const int* seg, int V, int B, int* brp, cudaStream_t s) {
+int beam_scan_tiles(int V) { return (V + BEAM_TILE - 1) / BEAM_TILE; }
+
+cudaError_t build_beam_rows(const int* seg, int V, int B, int* brp, int* tmp, cudaStream_t s) {
     if (B < 1 || V < 1) return cudaSuccess;
-    k_beam_scan<<<B, BEAM_SCAN_T, 0, s>>>(seg, V, brp);
+    const int nt = beam_scan_tiles(V);
+    k_beam_tiles<<<dim3(nt, B), BEAM_TILE, 0, s>>>(seg, V, nt, tmp);
+    k_beam_tile_scan<<<B, BEAM_TILE, 0, s>>>(tmp, nt, V, brp);
+    k_beam_offsets<<<dim3(nt, B), BEAM_TILE, 0, s>>>(seg, V, nt, tmp, brp);
     return cudaGetLastError();
 }
 

@@ -441,7 +441,9 @@ cudaError_t build_seg(const int64_t* rp, const int* col, const int* prow, int V,
 cudaError_t build_unit_max(const int* prow, int V, int epg, int* out, cudaStream_t s);
 // D by beams: the row offsets of every beam's part (B x (V + 1), from the beam
 // segments seg), then the entries (beamlet index within the beam, value).
-cudaError_t build_beam_rows(const int* seg, int V, int B, int* brp, cudaStream_t s);
+// tmp: B x beam_scan_tiles(V) ints of scratch.
+int beam_scan_tiles(int V);
+cudaError_t build_beam_rows(const int* seg, int V, int B, int* brp, int* tmp, cudaStream_t s);
 cudaError_t build_beam_fill(int prec, const int* seg, int V, int B, const int* beam_off, const DevCSR& D,
                             cudaStream_t s);
 // Merge-path splits of the merge form: out[v] = (rows done, groups consumed)
