@@ -61,6 +61,8 @@ def _args():
                    help="requests of the serving leg's Poisson stream (4 per second)")
     p.add_argument("--serve-burst", type=int, default=64,
                    help="requests of the serving leg's burst (200 per second: the server under load)")
+    p.add_argument("--serve-solve-slots", type=int, default=1,
+                   help="plans whose rounds the server puts on the GPU at once (0: every admitted plan)")
     p.add_argument("--serve-fp32-single", type=int, default=600,
                    help="requests of the same Poisson stream served by the plain form (FP32, one plan at a time); "
                         "0: skip")
@@ -438,17 +440,19 @@ def serve_pool(n_each):
         return pool.map(_make_case_spec, specs)
 
 
-def run_serve(dev, pool, n_requests, apertures, rate_per_s=4.0, seed=9000, max_slots=8, **plan_opt):
+def run_serve(dev, pool, n_requests, apertures, rate_per_s=4.0, seed=9000, max_slots=8, solve_slots=0, **plan_opt):
     """Poisson arrivals (rate 4 per second, seeded exponential gaps) of re-plan
     requests drawn from the pool; each request uploads its D and plans
     ``apertures`` apertures.  Latency is submission to results on the host.
     ``plan_opt``: dao_options of every plan (storage precision, master blocks);
-    ``max_slots`` 1 serves one plan at a time in arrival order."""
+    ``max_slots`` 1 serves one plan at a time in arrival order; ``solve_slots``
+    1 lets admitted requests create their plans alongside the running one but
+    queue their rounds one plan at a time."""
     from paper_1003_5402_gb300 import Server
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate_per_s, size=n_requests)
     which = rng.integers(0, len(pool), size=n_requests)
-    with Server(max_slots=max_slots, device=dev, **plan_opt) as srv:
+    with Server(max_slots=max_slots, device=dev, solve_slots=solve_slots, **plan_opt) as srv:
         # warm-up, as a long-running server is: one request of each size at
         # once, so that the library's memory pool already holds two concurrent
         # plans of the larger size (its one-time growth, tens of ms, is not a
@@ -473,9 +477,10 @@ def run_serve(dev, pool, n_requests, apertures, rate_per_s=4.0, seed=9000, max_s
     ok = sum(r["status"] in (0, 1, 2) for r in res)
     phases = {k: {"p50": round(float(np.percentile([r[k] for r in res], 50)), 3),
                   "p99": round(float(np.percentile([r[k] for r in res], 99)), 3)}
-              for k in ("queue_ms", "create_ms", "solve_ms", "finish_ms")}
+              for k in ("queue_ms", "create_ms", "gpu_wait_ms", "solve_ms", "finish_ms")}
     errors = sorted({f'{r["status"]}: {r["error"]}' for r in res if r["status"] not in (0, 1, 2)})
-    return {"requests": n_requests, "rate_per_s": rate_per_s, "max_slots": max_slots, "completed_ok": int(ok),
+    return {"requests": n_requests, "rate_per_s": rate_per_s, "max_slots": max_slots, "solve_slots": solve_slots,
+            "completed_ok": int(ok),
             "errors": errors[:4],
             "plan_options": {k: v for k, v in plan_opt.items()},
             "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
@@ -754,14 +759,18 @@ def run_ours(a):
             serve_inputs = "page-locked host arrays"
         except Exception as exc:   # no page-locked memory: ordinary host arrays
             serve_inputs = f"pageable host arrays ({type(exc).__name__})"
-        # FP16 storage (the mixed-precision form), every request its own plan
-        serve = run_serve(dev, serve_cases, a.serve_requests, a.apertures, precision=PREC["fp16"])
+        # FP16 storage (the mixed-precision form), every request its own plan:
+        # up to 8 admitted at once, creating their plans alongside the running
+        # one, their rounds on the GPU one plan at a time in admission order
+        serve = run_serve(dev, serve_cases, a.serve_requests, a.apertures, solve_slots=a.serve_solve_slots,
+                          precision=PREC["fp16"])
         serve["inputs"] = serve_inputs
         if a.serve_burst > 0:
             burst = run_serve(dev, serve_cases, a.serve_burst, a.apertures, rate_per_s=200.0, seed=9100,
-                              precision=PREC["fp16"])
-            serve["burst"] = {k: burst[k] for k in ("requests", "rate_per_s", "completed_ok", "errors", "p50_ms", "p99_ms",
-                                                    "max_ms", "max_active", "plans_per_s", "phases")}
+                              solve_slots=a.serve_solve_slots, precision=PREC["fp16"])
+            serve["burst"] = {k: burst[k] for k in ("requests", "rate_per_s", "solve_slots", "completed_ok", "errors",
+                                                    "p50_ms", "p99_ms", "max_ms", "max_active", "plans_per_s",
+                                                    "phases")}
         if a.serve_fp32_single > 0:
             # the plain form on the same Poisson stream: FP32 storage, one plan
             # at a time in arrival order (a request that arrives while a plan

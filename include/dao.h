@@ -526,6 +526,10 @@ typedef struct {
                                       staging blocks for max_slots + 2 plans, when the server starts, so that
                                       admitted plans do not wait for the pool to grow or for host pages to be
                                       locked (default 2 GiB; 0: none) */
+    int32_t solve_slots;           /* plans whose column-generation rounds are on the GPU at once: 0 (default)
+                                      as many as max_slots; n > 0: admitted requests create their contexts
+                                      (upload, checks, device build) alongside the running plans, then queue
+                                      their rounds in admission order, at most n plans' rounds at a time */
 } dao_server_options;
 void dao_server_options_default(dao_server_options* opt);
 
@@ -555,6 +559,7 @@ typedef struct {
     double create_ms;      /* of run_ms: the plan's context created (upload, checks, device build) */
     double solve_ms;       /* of run_ms: rounds queued until the worker saw them complete */
     double finish_ms;      /* of run_ms: results copied out and the context released */
+    double gpu_wait_ms;    /* of run_ms: created, waiting for its turn to queue its rounds (solve_slots) */
     char error[256];       /* message of a failed request */
 } dao_result;
 

@@ -69,7 +69,7 @@ class dao_tuning(C.Structure):
 class dao_server_options(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("queue_capacity", C.c_int32), ("hbm_reserve_bytes", C.c_int64),
                 ("hbm_budget_bytes", C.c_int64), ("device", C.c_int32), ("simulate_ms_per_aperture", C.c_double),
-                ("plan_options", dao_options), ("prewarm_bytes", C.c_int64)]
+                ("plan_options", dao_options), ("prewarm_bytes", C.c_int64), ("solve_slots", C.c_int32)]
 
 
 class dao_voxel_terms(C.Structure):
@@ -94,7 +94,7 @@ class dao_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("n_apertures", C.c_int32), ("objective", C.c_double),
                 ("queue_ms", C.c_double), ("run_ms", C.c_double), ("latency_ms", C.c_double),
                 ("create_ms", C.c_double), ("solve_ms", C.c_double), ("finish_ms", C.c_double),
-                ("error", C.c_char * 256)]
+                ("gpu_wait_ms", C.c_double), ("error", C.c_char * 256)]
 
 
 class dao_server_stats(C.Structure):
@@ -597,7 +597,7 @@ class Server:
 
     def __init__(self, max_slots: int = 8, queue_capacity: int = 1024, hbm_reserve_bytes: int = 2 << 30,
                  hbm_budget_bytes: int = 0, device: int = 0, simulate_ms_per_aperture: float = 0.0,
-                 prewarm_bytes: Optional[int] = None, **plan_opt):
+                 prewarm_bytes: Optional[int] = None, solve_slots: int = 0, **plan_opt):
         lib = load()
         o = dao_server_options()
         lib.dao_server_options_default(C.byref(o))
@@ -606,6 +606,7 @@ class Server:
         o.device, o.simulate_ms_per_aperture = int(device), float(simulate_ms_per_aperture)
         if prewarm_bytes is not None:
             o.prewarm_bytes = int(prewarm_bytes)
+        o.solve_slots = int(solve_slots)
         o.plan_options = options(**plan_opt)
         self.k_max = o.plan_options.k_max
         h = C.c_void_p()
@@ -645,7 +646,7 @@ class Server:
         req, keep, out = self._live.pop(rid)
         res = {"status": r.status, "n_apertures": r.n_apertures, "objective": r.objective, "queue_ms": r.queue_ms,
                "run_ms": r.run_ms, "latency_ms": r.latency_ms, "create_ms": r.create_ms, "solve_ms": r.solve_ms,
-               "finish_ms": r.finish_ms, "error": r.error.decode(errors="replace")}
+               "finish_ms": r.finish_ms, "gpu_wait_ms": r.gpu_wait_ms, "error": r.error.decode(errors="replace")}
         if out:
             k = max(r.n_apertures, 0)
             res.update(dose=out["dose"], y=out["y"][:k].copy(), beams=out["beams"][:k].copy(),

@@ -8,7 +8,11 @@
 // buffers and releases the context.  Plans run concurrently, each on its own
 // stream, and a plan's host work (upload, device build, read-back) never waits
 // behind another plan's: a request's latency is its own work plus its share of
-// the GPU.  Submitters and pollers only touch the queue and the result table
+// the GPU.  With solve_slots = n > 0 the admitted requests still create their
+// contexts alongside the running plans, but queue their rounds in admission
+// order, at most n plans' rounds on the GPU at a time (a plan's persistent
+// master solve occupies every SM, so two plans' rounds interleave rather than
+// overlap).  Submitters and pollers only touch the queue and the result table
 // under the mutex.
 #include <algorithm>
 #include <chrono>
@@ -38,6 +42,7 @@ enum { REQ_QUEUED = 0, REQ_RUNNING = 1, REQ_DONE = 2 };
 struct Request {
     dao_request r{};
     int64_t footprint = 0;
+    int64_t order = 0;           // admission order: the turn of its rounds on the GPU
     int state = REQ_QUEUED;
     Clock::time_point t_submit, t_admit, t_done;
     dao_result res{};
@@ -76,6 +81,13 @@ struct dao_server {
     bool stop = false;
     int64_t bytes_in_use = 0;
     int64_t capacity = 0;  // the most a single plan may ever hold
+    // plans whose rounds are on the GPU (opt.solve_slots > 0 bounds them):
+    // requests take their turn in admission order once their context exists
+    std::mutex mu_solve;
+    std::condition_variable cv_solve;
+    int solves_on_gpu = 0;
+    int64_t next_turn = 0;   // admission order of the next request to take its turn
+    int64_t next_order = 0;  // admission counter
     dao_server_stats stats{};
     std::thread worker;
 
@@ -89,9 +101,33 @@ struct dao_server {
         return (int64_t)free_b - opt.hbm_reserve_bytes >= fp;
     }
 
-    // Slot thread, without the lock: create the plan and queue its rounds.
+    // Slot thread, without the lock: this request's turn to put its rounds on
+    // the GPU (in admission order, while fewer than solve_slots plans' rounds
+    // are there); every admitted request takes its turn, a failed one too.
+    void take_turn(Request& q) {
+        if (opt.solve_slots <= 0) return;
+        std::unique_lock<std::mutex> l(mu_solve);
+        cv_solve.wait(l, [&] { return next_turn == q.order && solves_on_gpu < opt.solve_slots; });
+        ++next_turn;
+        ++solves_on_gpu;
+        cv_solve.notify_all();  // the next turn may already be free
+    }
+    void end_turn() {
+        if (opt.solve_slots <= 0) return;
+        {
+            std::lock_guard<std::mutex> l(mu_solve);
+            --solves_on_gpu;
+        }
+        cv_solve.notify_all();
+    }
+
+    // Slot thread, without the lock: create the plan, take the request's turn,
+    // queue its rounds.
     void start(Slot& s, Request& q) {
         if (simulate) {
+            const Clock::time_point t0 = Clock::now();
+            take_turn(q);
+            q.res.gpu_wait_ms = ms_since(t0, Clock::now());
             s.sim_end = Clock::now() + std::chrono::microseconds(
                                            (int64_t)std::llround(1e3 * opt.simulate_ms_per_aperture * q.r.n_apertures));
             return;
@@ -103,7 +139,10 @@ struct dao_server {
         const Clock::time_point t0 = Clock::now();
         dao_status st = dao_create(&q.r.D, &q.r.geometry, &q.r.structures, &q.r.weights, q.r.prescriptions, &po,
                                    &s.ctx);
-        q.res.create_ms = ms_since(t0, Clock::now());
+        const Clock::time_point t1 = Clock::now();
+        q.res.create_ms = ms_since(t0, t1);
+        take_turn(q);
+        q.res.gpu_wait_ms = ms_since(t1, Clock::now());
         if (st == DAO_OK) {
             // blocking sync: the slot's thread sleeps in the driver while its plan runs
             // instead of polling, which would contend for the driver with the other
@@ -180,6 +219,7 @@ struct dao_server {
             lk.unlock();
             start(s, q);
             wait_plan(s);
+            end_turn();  // the plan's rounds have left the GPU
             finish(s, q);
             lk.lock();
             q.state = REQ_DONE;
@@ -227,6 +267,7 @@ struct dao_server {
                 if (!fits(q.footprint)) break;  // wait for a running plan to retire
                 queue.pop_front();
                 q.state = REQ_RUNNING;
+                q.order = next_order++;
                 q.t_admit = Clock::now();
                 q.res.queue_ms = ms_since(q.t_submit, q.t_admit);
                 free_slot->busy = true;
@@ -291,8 +332,9 @@ dao_status dao_server_create(const dao_server_options* opt_in, dao_server** out)
     dao_server_options_default(&opt);
     if (opt_in) opt = *opt_in;
     if (opt.max_slots < 1 || opt.queue_capacity < 1 || opt.hbm_reserve_bytes < 0 || opt.hbm_budget_bytes < 0 ||
-        !(opt.simulate_ms_per_aperture >= 0.0) || opt.prewarm_bytes < 0)
-        return dao::set_error(DAO_EINVAL, "max_slots, queue_capacity >= 1; reserve, budget, simulation time >= 0");
+        !(opt.simulate_ms_per_aperture >= 0.0) || opt.prewarm_bytes < 0 || opt.solve_slots < 0)
+        return dao::set_error(DAO_EINVAL,
+                              "max_slots, queue_capacity >= 1; reserve, budget, simulation time, solve_slots >= 0");
     const bool simulate = opt.simulate_ms_per_aperture > 0.0;
     if (simulate && opt.hbm_budget_bytes <= 0)
         return dao::set_error(DAO_EINVAL, "simulation needs hbm_budget_bytes > 0 as its device memory");

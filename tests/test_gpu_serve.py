@@ -27,7 +27,11 @@ def _cases():
             P.make_case(P.perturb(micro, 9002))]
 
 
-def test_server_results_equal_plans_alone(torch):
+@pytest.mark.parametrize("solve_slots", [0, 1])
+def test_server_results_equal_plans_alone(torch, solve_slots):
+    """Every request's plan bitwise the plan alone, with all admitted plans'
+    rounds on the GPU at once (solve_slots 0) and one plan's at a time in
+    admission order (solve_slots 1)."""
     from paper_1003_5402_gb300 import Plan, Server
     cases = _cases()
     K = 10
@@ -38,7 +42,7 @@ def test_server_results_equal_plans_alone(torch):
             z, F = p.dose()
             aps = p.apertures()
             alone.append((st, n, F, z, p.intensities(), aps))
-    with Server(max_slots=3) as s:
+    with Server(max_slots=3, solve_slots=solve_slots) as s:
         ids = [s.submit(c, K) for c in cases]
         res = [s.wait(i, 120_000) for i in ids]
         stats = s.stats()

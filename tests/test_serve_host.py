@@ -62,6 +62,30 @@ def test_arrival_order_with_one_slot(lib, small):
     assert all(a < b for a, b in zip(done_at, done_at[1:]))      # admitted in submission order
 
 
+def test_solve_slots_queue_rounds_in_admission_order(lib, small):
+    """solve_slots 1: four slots admit and create at once, but the plans' rounds
+    (5 ms each in simulation) take the GPU one plan at a time, in admission
+    order; without it the four run side by side."""
+    import time
+    with _server(max_slots=4, solve_slots=1, simulate_ms_per_aperture=1.0) as s:
+        t0 = time.perf_counter()
+        ids = [s.submit(small, 5) for _ in range(6)]
+        res = [s.wait(i, 10_000) for i in ids]
+        span = 1e3 * (time.perf_counter() - t0)
+        st = s.stats()
+    assert all(r["status"] == 0 for r in res) and st["max_active"] == 4
+    assert span >= 6 * 5.0 - 1.0                                   # the six solves one after another
+    lat = [r["latency_ms"] for r in res]
+    assert all(b > a for a, b in zip(lat, lat[1:]))                 # finished in admission order
+    assert res[0]["gpu_wait_ms"] < 2.0 and res[2]["gpu_wait_ms"] >= 2 * 5.0 - 1.0
+    with _server(max_slots=4, simulate_ms_per_aperture=1.0) as s:
+        t0 = time.perf_counter()
+        ids = [s.submit(small, 5) for _ in range(4)]
+        res = [s.wait(i, 10_000) for i in ids]
+        span = 1e3 * (time.perf_counter() - t0)
+    assert span < 4 * 5.0 and all(r["gpu_wait_ms"] < 2.0 for r in res)
+
+
 def test_memory_budget_admits_one_plan_at_a_time(lib, small):
     with _server(max_slots=4) as probe:
         fp = probe.footprint(small)
