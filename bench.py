@@ -61,7 +61,7 @@ def _args():
                    help="requests of the serving leg's Poisson stream (4 per second)")
     p.add_argument("--serve-burst", type=int, default=64,
                    help="requests of the serving leg's burst (200 per second: the server under load)")
-    p.add_argument("--serve-solve-slots", type=int, default=1,
+    p.add_argument("--serve-solve-slots", type=int, default=0,
                    help="plans whose rounds the server puts on the GPU at once (0: every admitted plan)")
     p.add_argument("--serve-fp32-single", type=int, default=600,
                    help="requests of the same Poisson stream served by the plain form (FP32, one plan at a time); "
@@ -759,9 +759,9 @@ def run_ours(a):
             serve_inputs = "page-locked host arrays"
         except Exception as exc:   # no page-locked memory: ordinary host arrays
             serve_inputs = f"pageable host arrays ({type(exc).__name__})"
-        # FP16 storage (the mixed-precision form), every request its own plan:
-        # up to 8 admitted at once, creating their plans alongside the running
-        # one, their rounds on the GPU one plan at a time in admission order
+        # FP16 storage (the mixed-precision form), every request its own plan,
+        # up to 8 admitted at once (--serve-solve-slots 1: their rounds on the
+        # GPU one plan at a time in admission order)
         serve = run_serve(dev, serve_cases, a.serve_requests, a.apertures, solve_slots=a.serve_solve_slots,
                           precision=PREC["fp16"])
         serve["inputs"] = serve_inputs
