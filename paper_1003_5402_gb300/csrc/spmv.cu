@@ -5,7 +5,9 @@
 //   and the beamlet fluence x_i = sum_{k in K_i} y_k (Eq. 7).
 // All reductions have a fixed order (per-lane sequential, then a fixed
 // shuffle tree, then fixed-order shared-memory combination), so every result
-// is bitwise reproducible for a given launch shape.  No atomics.
+// is bitwise reproducible for a given launch shape.  No atomic accumulation:
+// the forms that split rows between warps add the warps' partial sums in a
+// fixed order, whichever warp takes the row's last ticket (an atomic counter).
 #include <algorithm>
 
 #include <cuda_bf16.h>
