@@ -63,7 +63,7 @@ def _args():
                    help="requests of the serving leg's burst (200 per second: the server under load)")
     p.add_argument("--serve-solve-slots", type=int, default=0,
                    help="plans whose rounds the server puts on the GPU at once (0: every admitted plan)")
-    p.add_argument("--serve-fp32-single", type=int, default=600,
+    p.add_argument("--serve-fp32-single", type=int, default=300,
                    help="requests of the same Poisson stream served by the plain form (FP32, one plan at a time); "
                         "0: skip")
     p.add_argument("--batch", type=int, default=16, help="instances per workload in the batched re-plan leg")
