@@ -449,9 +449,10 @@ def run_serve(dev, pool, n_requests, apertures, rate_per_s=4.0, seed=9000, max_s
     1 lets admitted requests create their plans alongside the running one but
     queue their rounds one plan at a time."""
     from paper_1003_5402_gb300 import Server
-    rng = np.random.default_rng(seed)
-    gaps = rng.exponential(1.0 / rate_per_s, size=n_requests)
-    which = rng.integers(0, len(pool), size=n_requests)
+    # gaps and pool draws from their own streams: the first n requests are the
+    # same whatever the stream's length
+    gaps = np.random.default_rng(seed).exponential(1.0 / rate_per_s, size=n_requests)
+    which = np.random.default_rng(seed + 1).integers(0, len(pool), size=n_requests)
     with Server(max_slots=max_slots, device=dev, solve_slots=solve_slots, **plan_opt) as srv:
         # warm-up, as a long-running server is: one request of each size at
         # once, so that the library's memory pool already holds two concurrent
