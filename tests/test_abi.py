@@ -198,3 +198,40 @@ def test_leaf_arrays_cover_the_rows_the_library_reads():
     assert binding._leaves([(0, 2), (1, 3)], 4).tolist() == [0, 2, 1, 3]
     with pytest.raises(ValueError, match="expected 3"):
         binding._leaves([(0, 2), (1, 3)], 6)
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding passes across the boundary has the size and
+    field offsets that a C compiler gives the declaration in include/dao.h
+    (a field added on one side only would shift every field after it)."""
+    import shutil
+    import subprocess
+    from paper_1003_5402_gb300 import binding as b
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = ["dao_csr", "dao_geometry", "dao_structures", "dao_weights", "dao_options", "dao_tuning",
+               "dao_server_options", "dao_voxel_terms", "dao_pencil_beam", "dao_request", "dao_result",
+               "dao_server_stats"]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "dao.h"', "int main(void) {"]
+    for name in structs:
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in getattr(b, name)._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_layout = {}
+    for ln in out:
+        if ln:
+            parts = ln.split()
+            c_layout[(parts[0], parts[1])] = int(parts[2])
+    for name in structs:
+        cls = getattr(b, name)
+        assert C.sizeof(cls) == c_layout[(name, "size")], name
+        for field, _ in cls._fields_:
+            assert getattr(cls, field).offset == c_layout[(name, field)], (name, field)
