@@ -141,6 +141,7 @@ def test_batch_and_autotune_validate_on_host(lib):
     assert b"null context" in lib.dao_last_error()
     assert lib.dao_batch_solve(None, 0, 5, None, None, None) == binding.DAO_OK
     assert lib.dao_autotune(None, None, None) == binding.DAO_EINVAL
+    assert lib.dao_kernel_forms(None, None) == binding.DAO_EINVAL
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

@@ -180,3 +180,5 @@ def test_server_options_are_validated(lib):
         _server(max_slots=0)
     with pytest.raises(DaoError):
         _server(hbm_budget_bytes=0)                                # simulation needs a budget
+    with pytest.raises(DaoError):
+        _server(solve_slots=-1)
